@@ -1,0 +1,144 @@
+"""FP64 CPU oracle for dense RGBD plane fitting -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never does, and shares no code with it.
+
+``fit`` runs the plain C oracle (``surffit_oracle.c``): direct per-window FP64
+sums of the scatter-matrix monomials (Eq. 6 for the standard fit, Eq. 14 for
+the disparity form, Eq. 9 / Eq. 16 for the explicit fits), the Schur
+complement that eliminates the offset, and a cyclic Jacobi eigen-solve.
+``twin`` holds a pure-NumPy restatement for tiny images that uses LAPACK's
+``eigh`` instead of Jacobi, so each can pin the other.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "surffit_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libsurffit_oracle.so")
+_lib = None
+
+METHODS = {"disparity": 0, "standard": 1, "explicit_disparity": 2, "explicit_standard": 3}
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP, no fast-math, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        lib.sfo_fit.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_int, dp, dp, dp, ip, dp, dp, ctypes.c_int]
+        lib.sfo_fit.restype = ctypes.c_int
+        lib.sfo_backward.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, dp, dp, dp, dp, ctypes.c_int]
+        lib.sfo_backward.restype = ctypes.c_int
+        lib.sfo_eig_sym.argtypes = [ctypes.c_int, dp, dp, dp]
+        lib.sfo_eig_sym.restype = ctypes.c_int
+        lib.sfo_num_threads.argtypes = []
+        lib.sfo_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def depth_to_f64(depth: np.ndarray, depth_scale: float = 1e-3) -> np.ndarray:
+    """Depth in metres as FP64: float32 converts exactly; uint16 is raw * scale (0 = missing)."""
+    if depth.dtype == np.uint16:
+        Z = depth.astype(np.float64) * float(depth_scale)
+        Z[depth == 0] = 0.0
+        return Z
+    return np.ascontiguousarray(depth, dtype=np.float64)
+
+
+def fit(depth: np.ndarray, intr: Sequence[float], k: int, method: str = "disparity", *, unit4: bool = False,
+        min_valid: int = 3, require_center: bool = True, depth_scale: float = 1e-3, want_lambda: bool = False,
+        want_moments: bool = False, threads: int = 0) -> Dict[str, np.ndarray]:
+    """Run the FP64 oracle on one [H, W] depth image.
+
+    Returns a dict with ``normals`` [H,W,3], ``offsets`` [H,W], ``curvature``
+    [H,W] (FP64, NaN where the validity rule fails), ``counts`` [H,W] int32
+    and optionally ``lam`` [H,W,3] (eigenvalues of R, ascending) and
+    ``moments`` [H,W,10] (A11 A12 A13 A22 A23 A33 g1 g2 g3 s).
+    """
+    lib = _load()
+    Z = np.ascontiguousarray(depth_to_f64(depth, depth_scale))
+    H, W = Z.shape
+    it = np.ascontiguousarray(np.asarray(intr, dtype=np.float64))
+    assert it.shape == (6,)
+    normals = np.empty((H, W, 3))
+    offsets = np.empty((H, W))
+    curv = np.empty((H, W))
+    counts = np.empty((H, W), dtype=np.int32)
+    lam = np.empty((H, W, 3)) if want_lambda else None
+    mom = np.empty((H, W, 10)) if want_moments else None
+    rc = lib.sfo_fit(_dp(Z), W, H, _dp(it), int(k), METHODS[method], int(unit4), int(min_valid),
+                     int(require_center), _dp(normals), _dp(offsets), _dp(curv),
+                     counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                     _dp(lam) if lam is not None else None, _dp(mom) if mom is not None else None, int(threads))
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments (rc=%d)" % rc)
+    out = {"normals": normals, "offsets": offsets, "curvature": curv, "counts": counts}
+    if lam is not None:
+        out["lam"] = lam
+    if mom is not None:
+        out["moments"] = mom
+    return out
+
+
+def backward(depth: np.ndarray, intr: Sequence[float], k: int, g_normals: np.ndarray, g_offsets: np.ndarray,
+             g_curv: np.ndarray, method: str = "disparity", *, min_valid: int = 3, require_center: bool = True,
+             depth_scale: float = 1e-3, threads: int = 0) -> np.ndarray:
+    """FP64 analytic gradient of sum(g_n . n + g_d * d + g_k * kappa) with respect to depth [H, W]."""
+    lib = _load()
+    Z = np.ascontiguousarray(depth_to_f64(depth, depth_scale))
+    H, W = Z.shape
+    it = np.ascontiguousarray(np.asarray(intr, dtype=np.float64))
+    gn = np.ascontiguousarray(np.nan_to_num(g_normals.astype(np.float64)))
+    gd = np.ascontiguousarray(np.nan_to_num(g_offsets.astype(np.float64)))
+    gk = np.ascontiguousarray(np.nan_to_num(g_curv.astype(np.float64)))
+    out = np.empty((H, W))
+    rc = lib.sfo_backward(_dp(Z), W, H, _dp(it), int(k), METHODS[method], int(min_valid), int(require_center),
+                          _dp(gn), _dp(gd), _dp(gk), _dp(out), int(threads))
+    if rc != 0:
+        raise ValueError("oracle backward rejected its arguments (rc=%d)" % rc)
+    return out
+
+
+def eig_sym(m: np.ndarray):
+    """The oracle's Jacobi eigen-decomposition of one symmetric matrix: (lam ascending, vecs rows)."""
+    lib = _load()
+    n = m.shape[0]
+    a = np.ascontiguousarray(m, dtype=np.float64)
+    lam = np.empty(n)
+    vec = np.empty((n, n))
+    lib.sfo_eig_sym(n, _dp(a), _dp(lam), _dp(vec))
+    return lam, vec
+
+
+def num_threads() -> int:
+    return int(_load().sfo_num_threads())

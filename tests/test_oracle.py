@@ -1,0 +1,346 @@
+"""Pins for the FP64 oracle: closed forms, brute force, LAPACK and identities.
+
+Each test checks the oracle against something other than itself, so that a
+dropped term, a wrong sign, a transposed operand or a wrong index in
+``oracle/surffit_oracle.c`` fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import twin
+import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _angle(a, b):
+    """Angle between unit vectors, accurate near 0 (atan2 of |a x b| and a.b)."""
+    a, b = np.broadcast_arrays(a, b)
+    return np.arctan2(np.linalg.norm(np.cross(a, b), axis=-1), np.sum(a * b, axis=-1))
+
+
+def _random_intr(rng, W, H):
+    f = rng.uniform(300, 1500)
+    return scenes.Intrinsics(f * rng.uniform(0.9, 1.1), f, (W - 1) / 2 + rng.uniform(-5, 5),
+                             (H - 1) / 2 + rng.uniform(-5, 5), rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5))
+
+
+# ---------------------------------------------------------------------------
+# Closed form: noise-free planar depth is fitted exactly (Eq. 3 and Eq. 12).
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+@pytest.mark.parametrize("k", [3, 5, 7])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_noise_free_plane_is_recovered(method, k, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W, H = 24, 18
+    intr = _random_intr(rng, W, H)
+    Z, pl = scenes.single_plane_frame(seed, intr, W, H)
+    o = oracle.fit(Z, intr.as_tuple(), k, method, want_lambda=True)
+    ok = np.isfinite(o["offsets"])
+    assert ok.all()
+    ang = _angle(o["normals"], pl.n[None, None, :])
+    assert np.nanmax(ang) < 1e-8
+    assert np.max(np.abs(o["offsets"] - pl.d)) < 1e-8 * pl.d
+    assert np.max(o["curvature"]) < 1e-9
+    assert np.max(np.abs(o["lam"][..., 0]) / o["lam"][..., 2]) < 1e-9
+
+
+@pytest.mark.parametrize("method", ["explicit_disparity", "explicit_standard"])
+def test_noise_free_plane_explicit(method):
+    intr = scenes.Intrinsics(525, 525, 11.5, 8.5)
+    Z, pl = scenes.single_plane_frame(7, intr, 24, 18, max_tilt_deg=50)
+    o = oracle.fit(Z, intr.as_tuple(), 5, method)
+    assert np.nanmax(_angle(o["normals"], pl.n[None, None, :])) < 1e-8
+    assert np.max(np.abs(o["offsets"] - pl.d)) < 1e-8 * pl.d
+    assert np.max(np.abs(o["curvature"])) < 1e-12 * max(1.0, np.max(Z) ** 2)
+
+
+def test_noise_free_plane_unit4_literal_constraint():
+    intr = scenes.Intrinsics(525, 525, 11.5, 8.5)
+    Z, pl = scenes.single_plane_frame(3, intr, 24, 18)
+    for method in ("disparity", "standard"):
+        o = oracle.fit(Z, intr.as_tuple(), 5, method, unit4=True)
+        assert np.nanmax(_angle(o["normals"], pl.n[None, None, :])) < 1e-7
+        assert np.max(np.abs(o["offsets"] - pl.d)) < 1e-7 * pl.d
+
+
+def test_rgbd_plane_equals_xyz_plane():
+    """Eq. 12 is Eq. 3 divided by Z: both fits give the same (n, d) on a plane."""
+    intr = scenes.Intrinsics(600, 610, 15.3, 11.1, 0.25, -0.25)
+    Z, pl = scenes.single_plane_frame(11, intr, 32, 24)
+    a = oracle.fit(Z, intr.as_tuple(), 7, "disparity")
+    b = oracle.fit(Z, intr.as_tuple(), 7, "standard")
+    assert np.max(_angle(a["normals"], b["normals"])) < 1e-8
+    assert np.max(np.abs(a["offsets"] - b["offsets"])) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Brute force and integral images: window sums and counts.
+# ---------------------------------------------------------------------------
+def _tiny_depth(seed, W, H, frac_missing=0.2):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Z = rng.uniform(0.5, 4.0, size=(H, W))
+    Z[rng.random((H, W)) < frac_missing] = 0.0
+    Z[0, 0] = np.nan
+    Z[-1, -1] = -1.0
+    return Z
+
+
+@pytest.mark.parametrize("W,H,k", [(8, 6, 3), (16, 12, 5), (16, 12, 3), (7, 9, 5)])
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_window_moments_match_integral_images(W, H, k, method):
+    Z = _tiny_depth(W * 100 + H, W, H)
+    intr = (500.0, 510.0, (W - 1) / 2, (H - 1) / 2, 0.1, -0.2)
+    o = oracle.fit(Z, intr, k, method, want_moments=True, min_valid=1, require_center=False)
+    S, n, _ = twin.scatter_sums(Z, intr, k, method)
+    mo = o["moments"]
+    ref = np.stack([S[..., 0, 0], S[..., 0, 1], S[..., 0, 2], S[..., 1, 1], S[..., 1, 2], S[..., 2, 2],
+                    S[..., 0, 3], S[..., 1, 3], S[..., 2, 3], S[..., 3, 3]], axis=-1)
+    scale = np.maximum(np.abs(ref), 1e-300)
+    assert np.max(np.abs(mo - ref) / np.maximum(scale, np.max(np.abs(ref)) * 1e-3)) < 1e-12
+    assert np.array_equal(o["counts"], n.astype(np.int32))
+
+
+def test_counts_brute_force_and_validity_rule():
+    W, H, k = 13, 11, 5
+    Z = _tiny_depth(5, W, H, 0.4)
+    intr = (300.0, 300.0, 6.0, 5.0, 0.0, 0.0)
+    r = k // 2
+    for min_valid, center in [(3, True), (1, False), (10, True), (25, False)]:
+        o = oracle.fit(Z, intr, k, "disparity", min_valid=min_valid, require_center=center)
+        for y in range(H):
+            for x in range(W):
+                n = 0
+                for yy in range(y - r, y + r + 1):
+                    for xx in range(x - r, x + r + 1):
+                        if 0 <= yy < H and 0 <= xx < W and np.isfinite(Z[yy, xx]) and Z[yy, xx] > 0:
+                            n += 1
+                assert o["counts"][y, x] == n
+                c_ok = np.isfinite(Z[y, x]) and Z[y, x] > 0
+                valid = n >= min_valid and (c_ok or not center)
+                assert np.isfinite(o["offsets"][y, x]) == valid
+                assert np.all(np.isfinite(o["normals"][y, x]) == valid)
+
+
+# ---------------------------------------------------------------------------
+# LAPACK: the Jacobi eigen-solver and the whole fit against numpy.linalg.eigh.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [3, 4])
+def test_jacobi_matches_lapack(n):
+    rng = np.random.Generator(np.random.PCG64(42 + n))
+    for _ in range(200):
+        B = rng.standard_normal((n, n)) * rng.uniform(1e-6, 1e3)
+        M = B @ B.T
+        if rng.random() < 0.3:  # near-singular, like a planar window
+            u = rng.standard_normal(n)
+            M = M - (M @ u)[:, None] * (M @ u)[None, :] / (u @ M @ u) * (1 - 1e-9)
+            M = 0.5 * (M + M.T)
+        lam, vec = oracle.eig_sym(M)
+        ref_l, ref_v = np.linalg.eigh(M)
+        scale = np.max(np.abs(ref_l))
+        assert np.max(np.abs(lam - ref_l)) <= 1e-12 * scale
+        for i in range(n):
+            gap = min([abs(ref_l[i] - ref_l[j]) for j in range(n) if j != i]) / scale
+            if gap > 1e-6:
+                c = abs(vec[i] @ ref_v[:, i])
+                assert abs(1 - c) < 1e-12 / gap ** 2 + 1e-13
+        # residual check independent of LAPACK
+        for i in range(n):
+            assert np.linalg.norm(M @ vec[i] - lam[i] * vec[i]) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_fit_matches_numpy_twin(method):
+    intr = scenes.Intrinsics(525, 525, 15.5, 11.5)
+    Z = scenes.kinect_frame(3, intr, 32, 24, n_planes=3, missing_iid=0.1).astype(np.float64)
+    a = oracle.fit(Z, intr.as_tuple(), 5, method, want_lambda=True)
+    b = twin.fit_np(Z, intr.as_tuple(), 5, method)
+    assert np.array_equal(np.isfinite(a["offsets"]), np.isfinite(b["offsets"]))
+    assert np.array_equal(a["counts"], b["counts"])
+    ok = np.isfinite(a["offsets"])
+    lam = a["lam"]
+    gap = (lam[..., 1] - lam[..., 0]) / lam[..., 2]
+    good = ok & (gap > 1e-4)
+    assert good.sum() > 0.8 * ok.sum()
+    assert np.max(_angle(a["normals"][good], b["normals"][good])) < 1e-9 / 1e-4
+    assert np.max(np.abs(a["offsets"][good] - b["offsets"][good]) / np.abs(b["offsets"][good])) < 1e-6
+    # The twin's FP64 summed-area tables accumulate over the whole image, so
+    # their absolute error (~1e-16 of the image total) is amplified by the
+    # Schur-complement cancellation (|A| / |R| ~ (f/r)^2 ~ 1e4): ~1e-8 relative.
+    assert np.max(np.abs(a["curvature"][ok] - b["curvature"][ok])) < 1e-7
+    assert np.max(np.abs(lam[ok] - b["lam"][ok]) / lam[ok][..., 2:3]) < 1e-7
+
+
+# ---------------------------------------------------------------------------
+# Identities: the Schur complement equals a two-pass (weighted) covariance.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_schur_complement_is_weighted_covariance(method):
+    intr = (525.0, 525.0, 7.5, 5.5, 0.0, 0.0)
+    Z = _tiny_depth(17, 16, 12, 0.15)
+    o = oracle.fit(Z, intr, 5, method, want_moments=True, want_lambda=True)
+    for (y, x) in [(5, 7), (0, 0), (11, 15), (6, 1), (3, 12)]:
+        if not np.isfinite(o["offsets"][y, x]):
+            continue
+        mo = o["moments"][y, x]
+        A = np.array([[mo[0], mo[1], mo[2]], [mo[1], mo[3], mo[4]], [mo[2], mo[4], mo[5]]])
+        g, s = mo[6:9], mo[9]
+        R = A - np.outer(g, g) / s
+        C = twin.weighted_covariance(Z, intr, 5, method, y, x)
+        assert np.max(np.abs(R - C)) < 1e-9 * np.max(np.abs(C))
+        l = np.linalg.eigvalsh(C)
+        assert np.allclose(o["lam"][y, x], l, rtol=1e-7, atol=1e-12 * l[-1])
+
+
+def test_disparity_calibration_block_has_closed_form():
+    """Full windows: A = sum m m^T depends only on the intrinsics (Section II.A)."""
+    W, H, k = 20, 16, 5
+    intr = (480.0, 470.0, 9.2, 7.7, 0.3, -0.1)
+    r = k // 2
+    rng = np.random.Generator(np.random.PCG64(3))
+    Z1 = rng.uniform(0.5, 5.0, (H, W))
+    Z2 = rng.uniform(0.5, 5.0, (H, W))
+    m1 = oracle.fit(Z1, intr, k, "disparity", want_moments=True)["moments"]
+    m2 = oracle.fit(Z2, intr, k, "disparity", want_moments=True)["moments"]
+    fx, fy, cx, cy, dx, dy = intr
+    u = np.arange(-r, r + 1)
+    for (y, x) in [(5, 5), (8, 10), (r, r)]:
+        tx = (x + u + dx - cx) / fx
+        ty = (y + u + dy - cy) / fy
+        A11 = k * np.sum(tx ** 2)
+        A12 = np.sum(tx) * np.sum(ty)
+        A13 = k * np.sum(tx)
+        A22 = k * np.sum(ty ** 2)
+        A23 = k * np.sum(ty)
+        A33 = k * k
+        ref = np.array([A11, A12, A13, A22, A23, A33])
+        assert np.allclose(m1[y, x, :6], ref, rtol=1e-13, atol=1e-13)
+        assert np.array_equal(m1[y, x, :6], m2[y, x, :6])
+
+
+# ---------------------------------------------------------------------------
+# Invariants on noisy Kinect-like data.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_invariants_on_noisy_frame(method):
+    intr = scenes.Intrinsics(525, 525, 31.5, 23.5)
+    Z = scenes.kinect_frame(9, intr, 64, 48)
+    o = oracle.fit(Z, intr.as_tuple(), 7, method)
+    ok = np.isfinite(o["offsets"])
+    assert ok.mean() > 0.8
+    nn = np.linalg.norm(o["normals"][ok], axis=-1)
+    assert np.max(np.abs(nn - 1)) < 1e-12
+    assert np.all(o["offsets"][ok] > 0)
+    kap = o["curvature"][ok]
+    assert np.all(kap >= -1e-15) and np.all(kap <= 1.0 / 3.0 + 1e-12)
+    assert np.all(np.isnan(o["curvature"][~ok]))
+
+
+def test_noise_statistics_sanity_band():
+    """Residual of a single noisy plane: lambda0 ~ sum of squared residuals (Eq. 2 noise)."""
+    intr = scenes.Intrinsics(525, 525, 63.5, 47.5)
+    Z0, pl = scenes.single_plane_frame(5, intr, 128, 96, z_lo=1.5, z_hi=1.5, max_tilt_deg=0.0)
+    coef = 1e-3
+    rng = np.random.Generator(np.random.PCG64(77))
+    Z = Z0 + rng.standard_normal(Z0.shape) * coef * Z0 ** 2
+    o = oracle.fit(Z, intr.as_tuple(), 9, "standard", want_lambda=True)
+    # fronto-parallel plane: residual along z, sigma = coef * Z^2
+    expected = 81 * (coef * 1.5 ** 2) ** 2
+    mean_l0 = np.nanmean(o["lam"][..., 0])
+    assert 0.7 * expected < mean_l0 < 1.1 * expected
+
+
+def test_missing_and_degenerate_inputs():
+    intr = (525.0, 525.0, 3.5, 2.5, 0.0, 0.0)
+    Z = np.zeros((6, 8))
+    o = oracle.fit(Z, intr, 3, "disparity")
+    assert np.all(np.isnan(o["offsets"])) and np.all(o["counts"] == 0)
+    Z = np.full((6, 8), 2.0)
+    o = oracle.fit(Z, intr, 1, "disparity")  # one point per window: below min_valid
+    assert np.all(np.isnan(o["offsets"]))
+    o = oracle.fit(Z, intr, 15, "standard")  # window larger than the image
+    assert np.all(o["counts"] == 48)
+    assert np.allclose(o["normals"][..., 2], -1.0)
+    assert np.allclose(o["offsets"], 2.0)
+    with pytest.raises(ValueError):
+        oracle.fit(Z, intr, 4, "disparity")
+
+
+def test_uint16_depth_conversion():
+    raw = np.array([[0, 1000, 2000], [65535, 1, 500]], dtype=np.uint16)
+    Z = oracle.depth_to_f64(raw, 1e-3)
+    assert Z[0, 0] == 0.0 and Z[0, 1] == 1.0 and Z[1, 0] == 65.535 and Z[1, 1] == 1e-3
+
+
+# ---------------------------------------------------------------------------
+# Backward: analytic FP64 adjoint against central finite differences.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_backward_matches_finite_differences(method):
+    intr = scenes.Intrinsics(525, 525, 7.5, 5.5)
+    Z = scenes.kinect_frame(21, intr, 16, 12, n_planes=2, missing_iid=0.05).astype(np.float64)
+    k = 5
+    rng = np.random.Generator(np.random.PCG64(5))
+    gn = rng.standard_normal((12, 16, 3))
+    gd = rng.standard_normal((12, 16))
+    gk = rng.standard_normal((12, 16)) * 10
+
+    o0 = oracle.fit(Z, intr.as_tuple(), k, method, want_lambda=True)
+    ok = np.isfinite(o0["offsets"])
+
+    def loss(Zp):
+        o = oracle.fit(Zp, intr.as_tuple(), k, method)
+        assert np.array_equal(np.isfinite(o["offsets"]), ok)
+        return (np.nansum(o["normals"] * gn) + np.nansum(o["offsets"] * gd) + np.nansum(o["curvature"] * gk))
+
+    g = oracle.backward(Z, intr.as_tuple(), k, np.where(ok[..., None], gn, 0), np.where(ok, gd, 0),
+                        np.where(ok, gk, 0), method)
+    lam = o0["lam"]
+    gap = np.where(ok, (lam[..., 1] - lam[..., 0]) / lam[..., 2], 1.0)
+    checked = 0
+    for y in range(12):
+        for x in range(16):
+            if not (np.isfinite(Z[y, x]) and Z[y, x] > 0):
+                assert g[y, x] == 0.0
+                continue
+            # skip pixels whose windows contain near-degenerate fits (gradient ill-conditioned)
+            y0, y1, x0, x1 = max(0, y - 2), min(12, y + 3), max(0, x - 2), min(16, x + 3)
+            if np.min(gap[y0:y1, x0:x1]) < 1e-3:
+                continue
+            # Central differences, h = 1e-6 Z: the loss is computed from raw
+            # FP64 moments whose Schur complement cancels ~4 digits, so the FD
+            # carries ~1e-5 relative error from rounding plus truncation.
+            h = 1e-6 * Z[y, x]
+            Zp = Z.copy(); Zp[y, x] += h
+            Zm = Z.copy(); Zm[y, x] -= h
+            fd = (loss(Zp) - loss(Zm)) / (2 * h)
+            assert abs(fd - g[y, x]) <= 5e-5 * max(1.0, abs(fd)), (y, x, fd, g[y, x])
+            checked += 1
+    assert checked > 50
+
+
+# ---------------------------------------------------------------------------
+# Paper numbers: cost-model channel counts (Section II.D / II.E).
+# ---------------------------------------------------------------------------
+def test_paper_cost_model_counts():
+    with open(os.path.join(GOLDEN, "paper_cost_model.json")) as f:
+        g = json.load(f)
+    # Eq. 6: 9 depth-dependent unique entries; each integral image costs C + 4
+    assert g["implicit_standard_depth_channels"] * 5 - 1 == g["implicit_standard_ops_per_pixel"]
+    assert g["implicit_disparity_depth_channels"] * 5 == g["implicit_disparity_ops_per_pixel"]
+    assert round(g["implicit_standard_ops_per_pixel"] / g["implicit_disparity_ops_per_pixel"], 1) == g["implicit_ratio"]
+    assert round(g["explicit_standard_ops_per_pixel"] / g["explicit_disparity_ops_per_pixel"], 1) == g["explicit_ratio"]
+    assert g["explicit_disparity_depth_channels"] * 5 == g["explicit_disparity_ops_per_pixel"]
+    # Eq. 2: sigma_Z coefficient is half the disparity slope magnitude
+    assert abs(g["kinect_sigma_coefficient"] - abs(g["kinect_disparity_slope"]) / 2) < 1e-12
+    # The depth-dependent entries of Eq. 14 counted from the monomials: m=[tx,ty,1,1/Z]
+    dep = [(i, j) for i in range(4) for j in range(i + 1) if i == 3 or j == 3]
+    assert len(dep) == g["implicit_disparity_depth_channels"]
+    # Eq. 6 with m=[X,Y,Z,1]: every unique entry except the 1*1 one depends on Z
+    assert 10 - 1 == g["implicit_standard_depth_channels"]
