@@ -1,0 +1,158 @@
+/*
+ * surffit.h -- C ABI of the GB300 dense RGBD plane-fitting library (libsurffit.so).
+ *
+ * Method: "Real-Time Surface Fitting to RGBD Sensor Data" (Papadakis & Willis).
+ * For every pixel p of a depth image and a k x k window centred on it, the
+ * library fits the plane n.P + d = 0 (|n| = 1, d > 0) to the window's valid
+ * 3D points and returns the unit normal n, the offset d (metres, the distance
+ * of the plane from the camera centre) and the curvature
+ * lambda0 / (lambda0 + lambda1 + lambda2) of the fit's 3x3 scatter matrix.
+ *
+ *   - SF_METHOD_DISPARITY: the implicit fit in RGBD space, Eq. 12 and Eq. 14:
+ *     monomials [tan(theta_x), tan(theta_y), 1, 1/Z].  Only the four 1/Z
+ *     entries of the scatter matrix depend on the depth (Section II.A).
+ *   - SF_METHOD_STANDARD: the implicit algebraic fit of Eq. 3-6 with monomials
+ *     [X, Y, Z, 1], X and Y from Eq. 1 -- the comparison fit.
+ *   - SF_METHOD_EXPLICIT_DISPARITY / SF_METHOD_EXPLICIT_STANDARD: the explicit
+ *     fits of Eq. 15-16 and Eq. 7-9; their third output is the mean squared
+ *     residual in the fit's own units instead of the curvature.
+ *
+ * Rays follow Eq. 10: tan(theta_x) = (x + dx - cx)/fx, tan(theta_y) =
+ * (y + dy - cy)/fy, with x the column and y the row, both 0-based.
+ * A pixel is missing when its depth is not finite or <= 0 (uint16: raw == 0).
+ * Windows are clipped at the image border.  The fit is written for p when at
+ * least min_valid window pixels are valid and (if require_center_valid) p
+ * itself is; otherwise normal, offset and curvature are NaN.
+ *
+ * The implicit fits use the constraint |(a, b, c)| = 1: the offset is
+ * eliminated (Schur complement of the 4x4 scatter matrix) and the normal is
+ * the eigenvector of the smallest eigenvalue of the remaining 3x3 matrix
+ * (Eq. 4-5).
+ *
+ * Conventions for every call:
+ *   - Device pointers are CUDA device memory of the device current at
+ *     sf_create; host pointers are ordinary host memory.  Images are dense,
+ *     row-major, pitch = W elements; normals are [H][W][3] float.
+ *   - The caller owns every buffer it passes.  A context owns its scratch and
+ *     tables and frees them in sf_destroy.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device calls
+ *     enqueue work and return without synchronising the host.
+ *   - Every call returns SF_OK or an error status; argument errors are found
+ *     before any launch and leave the outputs untouched.  sf_last_error()
+ *     returns a message for the calling thread's last failure.
+ *   - A context is not safe for concurrent use from several streams: its
+ *     scratch is shared by all its calls.
+ */
+#ifndef SURFFIT_H_
+#define SURFFIT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SF_OK = 0,
+    SF_ERR_INVALID_ARG = 1, /* null pointer, bad size, even or too large window ... */
+    SF_ERR_UNSUPPORTED = 2, /* a valid request this build does not implement     */
+    SF_ERR_ALLOC = 3,       /* device or host allocation failed                  */
+    SF_ERR_CUDA = 4,        /* a CUDA runtime call failed                         */
+    SF_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up                 */
+} sf_status;
+
+typedef enum { SF_DEPTH_F32 = 0, SF_DEPTH_U16 = 1 } sf_depth_type;
+
+typedef enum {
+    SF_METHOD_DISPARITY = 0,
+    SF_METHOD_STANDARD = 1,
+    SF_METHOD_EXPLICIT_DISPARITY = 2,
+    SF_METHOD_EXPLICIT_STANDARD = 3
+} sf_method;
+
+/* Pinhole intrinsics of Eq. 1: focal lengths and principal point in pixels,
+ * (dx, dy) the constant pixel-coordinate adjustment. */
+typedef struct {
+    double fx, fy, cx, cy, dx, dy;
+} sf_intrinsics;
+
+typedef struct sf_ctx sf_ctx;
+
+/* Largest supported window: k <= SF_MAX_WINDOW (the exact integer window sums
+ * are sized for at most 31 x 31 = 961 pixels). */
+#define SF_MAX_WINDOW 31
+
+/*
+ * sf_create -- precompute the calibration tables for one camera, image size
+ * and window (Section II.A: the ray terms depend only on the intrinsics, so
+ * they are computed once, before any depth is seen) and allocate scratch.
+ *   K        intrinsics (host pointer, read during the call)
+ *   W, H     image size in pixels, >= 1
+ *   window   odd k, 1 <= k <= SF_MAX_WINDOW
+ *   out      receives the new context
+ * Defaults: disparity method, float32 metres, min_valid 3, centre required.
+ * Synchronises the device once.  Errors: SF_ERR_INVALID_ARG, SF_ERR_ALLOC,
+ * SF_ERR_CUDA.
+ */
+sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** out);
+
+/*
+ * sf_set_params -- choose the fit and the depth encoding.
+ *   method        an sf_method value
+ *   depth_type    SF_DEPTH_F32 (metres) or SF_DEPTH_U16 (raw units, 0 = missing)
+ *   depth_scale   metres per raw unit for SF_DEPTH_U16 (ignored for f32), > 0
+ *   min_valid     minimum number of valid window pixels, >= 1
+ *   require_center_valid  nonzero: the centre pixel must be valid
+ */
+sf_status sf_set_params(sf_ctx* ctx, int method, int depth_type, float depth_scale, int min_valid,
+                        int require_center_valid);
+
+/*
+ * sf_fit -- fit every pixel of one frame.
+ *   depth      device [H][W] float32 metres or uint16 raw (per sf_set_params)
+ *   normals    device [H][W][3] float32, out
+ *   offsets    device [H][W] float32, out
+ *   curvature  device [H][W] float32, out (mean squared residual for explicit fits)
+ * Asynchronous on `stream`.
+ */
+sf_status sf_fit(sf_ctx* ctx, const void* depth, float* normals, float* offsets, float* curvature, void* stream);
+
+/*
+ * sf_fit_ex -- sf_fit for n_frames frames of the context's size stored back to
+ * back ([n_frames][H][W] in, [n_frames][H][W][3] / [n_frames][H][W] out), with
+ * optional per-pixel valid-window counts (device int32 [n_frames][H][W] or NULL).
+ */
+sf_status sf_fit_ex(sf_ctx* ctx, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
+                    int32_t* counts, void* stream);
+
+/*
+ * sf_fit_host -- sf_fit_ex on HOST buffers: copies the depth in, fits and
+ * copies the results out through the context's pinned staging buffers, then
+ * synchronises `stream`.  Same layouts as sf_fit_ex; counts may be NULL.
+ */
+sf_status sf_fit_host(sf_ctx* ctx, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
+                      int32_t* counts, void* stream);
+
+/* sf_destroy -- free the context and everything it owns (NULL is a no-op). */
+sf_status sf_destroy(sf_ctx* ctx);
+
+/* Message for the calling thread's most recent error ("" if none). */
+const char* sf_last_error(void);
+
+/*
+ * sf_channel_counts -- how many per-pixel depth-dependent channels the
+ * method's window sums carry, and how many depend on the validity mask only
+ * (the paper's calibration-only terms, Section II.D).  Host-only, no device
+ * work.  Returns SF_ERR_INVALID_ARG for an unknown method.
+ */
+sf_status sf_channel_counts(int method, int* depth_channels, int* mask_channels);
+
+/* Library version as a static string. */
+const char* sf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SURFFIT_H_ */

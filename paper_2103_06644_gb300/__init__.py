@@ -1,0 +1,138 @@
+"""GB300-native dense RGBD plane fitting (Papadakis & Willis, "Real-Time Surface
+Fitting to RGBD Sensor Data").
+
+Thin PyTorch binding over the C ABI of ``libsurffit.so`` (``include/surffit.h``):
+PyTorch supplies device memory and streams; every step of the fit runs in the
+library's CUDA kernels.  There is no CPU fallback: on a machine without the
+built library or without a GPU, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence, Tuple, Union
+
+import numpy as np
+
+from . import _native
+from ._native import SurfFitError
+
+__all__ = ["SurfaceFitter", "SurfFitError", "METHODS", "DEPTH_TYPES", "channel_counts", "version"]
+
+METHODS = {"disparity": 0, "standard": 1, "explicit_disparity": 2, "explicit_standard": 3}
+DEPTH_TYPES = {"f32": 0, "u16": 1}
+
+
+def version() -> str:
+    return _native.lib().sf_version().decode()
+
+
+def channel_counts(method: str) -> Tuple[int, int]:
+    """(depth-dependent channels, mask-only channels) of the method's window sums."""
+    d = ctypes.c_int()
+    m = ctypes.c_int()
+    _native.check(_native.lib().sf_channel_counts(METHODS[method], ctypes.byref(d), ctypes.byref(m)))
+    return d.value, m.value
+
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class SurfaceFitter:
+    """One camera, image size and window: the library context of ``sf_create``.
+
+    ``intrinsics`` is (fx, fy, cx, cy) or (fx, fy, cx, cy, dx, dy) as in Eq. 1.
+    """
+
+    def __init__(self, intrinsics: Sequence[float], W: int, H: int, window: int, method: str = "disparity",
+                 depth_type: str = "f32", depth_scale: float = 1e-3, min_valid: int = 3,
+                 require_center: bool = True):
+        it = tuple(float(v) for v in intrinsics)
+        if len(it) == 4:
+            it = it + (0.0, 0.0)
+        if len(it) != 6:
+            raise ValueError("intrinsics must have 4 or 6 entries")
+        self.W, self.H, self.window = int(W), int(H), int(window)
+        self.method, self.depth_type = method, depth_type
+        self.depth_scale = float(depth_scale)
+        L = _native.lib()
+        h = ctypes.c_void_p()
+        _native.check(L.sf_create(ctypes.byref(_native.Intrinsics(*it)), self.W, self.H, self.window, ctypes.byref(h)))
+        self._h = h
+        self.set_params(method, depth_type, depth_scale, min_valid, require_center)
+
+    def set_params(self, method: str, depth_type: str = "f32", depth_scale: float = 1e-3, min_valid: int = 3,
+                   require_center: bool = True) -> None:
+        _native.check(_native.lib().sf_set_params(self._h, METHODS[method], DEPTH_TYPES[depth_type],
+                                                  float(depth_scale), int(min_valid), int(bool(require_center))))
+        self.method, self.depth_type, self.depth_scale = method, depth_type, float(depth_scale)
+
+    # -- device API -------------------------------------------------------------
+    def _check_depth(self, depth):
+        import torch
+
+        want = torch.float32 if self.depth_type == "f32" else torch.uint16
+        if depth.dtype != want and not (want == torch.uint16 and depth.dtype == torch.int16):
+            raise TypeError("depth must be %s for depth_type %s" % (want, self.depth_type))
+        if not depth.is_cuda or not depth.is_contiguous():
+            raise ValueError("depth must be a contiguous CUDA tensor")
+        if depth.shape[-2:] != (self.H, self.W):
+            raise ValueError("depth shape %s does not match %dx%d" % (tuple(depth.shape), self.H, self.W))
+
+    def fit(self, depth, out=None, counts: bool = False, stream=None):
+        """Fit every pixel of [H, W] or [N, H, W] depth; returns (normals, offsets, curvature[, counts])."""
+        import torch
+
+        self._check_depth(depth)
+        batched = depth.dim() == 3
+        n = depth.shape[0] if batched else 1
+        shape = (n, self.H, self.W) if batched else (self.H, self.W)
+        dev = depth.device
+        if out is None:
+            normals = torch.empty(shape + (3,), dtype=torch.float32, device=dev)
+            offsets = torch.empty(shape, dtype=torch.float32, device=dev)
+            curv = torch.empty(shape, dtype=torch.float32, device=dev)
+        else:
+            normals, offsets, curv = out
+        cnt = torch.empty(shape, dtype=torch.int32, device=dev) if counts else None
+        _native.check(_native.lib().sf_fit_ex(self._h, n, depth.data_ptr(), normals.data_ptr(), offsets.data_ptr(),
+                                              curv.data_ptr(), cnt.data_ptr() if cnt is not None else None,
+                                              _stream_handle(stream)))
+        return (normals, offsets, curv, cnt) if counts else (normals, offsets, curv)
+
+    # -- host API (copies inside the library call) --------------------------------
+    def fit_host(self, depth: np.ndarray, counts: bool = False):
+        """Fit host depth [H, W] or [N, H, W] through ``sf_fit_host``; returns numpy arrays."""
+        want = np.float32 if self.depth_type == "f32" else np.uint16
+        d = np.ascontiguousarray(depth, dtype=want)
+        batched = d.ndim == 3
+        n = d.shape[0] if batched else 1
+        shape = (n, self.H, self.W) if batched else (self.H, self.W)
+        normals = np.empty(shape + (3,), np.float32)
+        offsets = np.empty(shape, np.float32)
+        curv = np.empty(shape, np.float32)
+        cnt = np.empty(shape, np.int32) if counts else None
+        _native.check(_native.lib().sf_fit_host(self._h, n, d.ctypes.data, normals.ctypes.data, offsets.ctypes.data,
+                                                curv.ctypes.data, cnt.ctypes.data if cnt is not None else None, None))
+        return (normals, offsets, curv, cnt) if counts else (normals, offsets, curv)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _native.lib().sf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

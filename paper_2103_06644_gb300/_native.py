@@ -1,0 +1,70 @@
+"""ctypes binding of libsurffit.so: argument marshalling only.
+
+Every computation runs in the CUDA library.  Loading fails loudly when the
+library has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SF_OK = 0
+STATUS = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_UNSUPPORTED", 3: "SF_ERR_ALLOC", 4: "SF_ERR_CUDA",
+          5: "SF_ERR_TIMEOUT"}
+
+
+class SurfFitError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+class Intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double),
+                ("cy", ctypes.c_double), ("dx", ctypes.c_double), ("dy", ctypes.c_double)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+SIGNATURES = {
+    "sf_create": (_I, [ctypes.POINTER(Intrinsics), _I, _I, _I, ctypes.POINTER(_VP)]),
+    "sf_set_params": (_I, [_VP, _I, _I, _F, _I, _I]),
+    "sf_fit": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "sf_fit_ex": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sf_fit_host": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sf_destroy": (_I, [_VP]),
+    "sf_last_error": (ctypes.c_char_p, []),
+    "sf_channel_counts": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "sf_version": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libsurffit.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libsurffit.so is not built (%s); run paper_2103_06644_gb300.build.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != SF_OK:
+        raise SurfFitError(status, lib().sf_last_error().decode())

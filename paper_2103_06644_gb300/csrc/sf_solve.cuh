@@ -1,0 +1,214 @@
+// sf_solve.cuh -- per-pixel solve of the window plane fit from exact integer
+// window moments (device code, included by the kernels).
+//
+// The window sums reaching this file are exact integers (fixed-point depth or
+// disparity, window-relative pixel offsets j = x_q - x_p, i = y_q - y_p), so
+// they can be re-centred on the window's own mean without rounding.  Every
+// floating-point step below works on centred, well-scaled quantities; no raw
+// second moment is ever subtracted in floating point.
+#pragma once
+#include <cstdint>
+
+namespace sf {
+
+struct FitOut {
+    float nx, ny, nz, d, curv;
+    float gap;  // (lambda1 - lambda0) / lambda2 of the normalised 3x3 matrix
+};
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Cross product of the two rows of (R - l I) with the largest norm: it spans
+// the null space of R - l I, i.e. the eigenvector of eigenvalue l.
+__device__ __forceinline__ void null_vector(float r11, float r12, float r13, float r22, float r23, float r33, float l,
+                                            float& v0, float& v1, float& v2) {
+    const float a11 = r11 - l, a22 = r22 - l, a33 = r33 - l;
+    // rows: m1 = (a11, r12, r13), m2 = (r12, a22, r23), m3 = (r13, r23, a33)
+    const float c0 = r12 * r23 - r13 * a22, c1 = r13 * r12 - a11 * r23, c2 = a11 * a22 - r12 * r12;  // m1 x m2
+    const float e0 = r12 * a33 - r13 * r23, e1 = r13 * r13 - a11 * a33, e2 = a11 * r23 - r12 * r13;  // m1 x m3
+    const float f0 = a22 * a33 - r23 * r23, f1 = r23 * r13 - r12 * a33, f2 = r12 * r23 - a22 * r13;  // m2 x m3
+    const float nc = c0 * c0 + c1 * c1 + c2 * c2;
+    const float ne = e0 * e0 + e1 * e1 + e2 * e2;
+    const float nf = f0 * f0 + f1 * f1 + f2 * f2;
+    float b0 = c0, b1 = c1, b2 = c2, nb = nc;
+    if (ne > nb) { b0 = e0; b1 = e1; b2 = e2; nb = ne; }
+    if (nf > nb) { b0 = f0; b1 = f1; b2 = f2; nb = nf; }
+    if (!(nb > 1e-36f)) {  // l is (numerically) a double root: any unit vector of the null space
+        // fall back to the coordinate axis of the smallest diagonal entry of R - l I
+        b0 = 0.f; b1 = 0.f; b2 = 0.f;
+        if (a11 <= a22 && a11 <= a33) b0 = 1.f; else if (a22 <= a33) b1 = 1.f; else b2 = 1.f;
+        nb = 1.f;
+    }
+    const float s = rsqrt_approx(nb);
+    v0 = b0 * s; v1 = b1 * s; v2 = b2 * s;
+}
+
+// Smallest eigenpair of a symmetric positive semi-definite 3x3 matrix R
+// (upper triangle r11..r33).  Eigenvalues by the trigonometric solution of the
+// characteristic cubic (Smith, CACM 4(4):168, 1961), the eigenvector as a
+// cross product of rows of R - lambda I, then one Rayleigh-quotient
+// refinement of lambda and a second cross product.  Returns the normalised
+// eigenvalues (trace scaled to 1) through l0 / gap.
+__device__ __forceinline__ void smallest_eigpair(float r11, float r12, float r13, float r22, float r23, float r33,
+                                                 float& v0, float& v1, float& v2, float& l0, float& gap) {
+    const float tr = r11 + r22 + r33;
+    const float s = rcp_approx(tr);
+    r11 *= s; r12 *= s; r13 *= s; r22 *= s; r23 *= s; r33 *= s;
+    const float third = 0.33333333f;
+    const float b11 = r11 - third, b22 = r22 - third, b33 = r33 - third;
+    const float p2 = (b11 * b11 + b22 * b22 + b33 * b33 + 2.f * (r12 * r12 + r13 * r13 + r23 * r23)) * (1.f / 6.f);
+    float lmin, lmid, lmax;
+    if (p2 < 1e-20f) {
+        lmin = lmid = lmax = third;
+    } else {
+        const float p = sqrtf(p2);
+        const float detB = b11 * (b22 * b33 - r23 * r23) - r12 * (r12 * b33 - r23 * r13) + r13 * (r12 * r23 - b22 * r13);
+        float q = 0.5f * detB / (p2 * p);
+        q = fminf(1.f, fmaxf(-1.f, q));
+        const float phi = acosf(q) * third;
+        float sn, cs;
+        sincosf(phi, &sn, &cs);
+        lmax = third + 2.f * p * cs;
+        lmin = third - p * (cs + 1.7320508f * sn);
+        lmid = 1.f - lmax - lmin;
+    }
+    float a0, a1, a2;
+    null_vector(r11, r12, r13, r22, r23, r33, lmin, a0, a1, a2);
+    // Rayleigh quotient a^T R a
+    const float t0 = r11 * a0 + r12 * a1 + r13 * a2;
+    const float t1 = r12 * a0 + r22 * a1 + r23 * a2;
+    const float t2 = r13 * a0 + r23 * a1 + r33 * a2;
+    const float lr = a0 * t0 + a1 * t1 + a2 * t2;
+    null_vector(r11, r12, r13, r22, r23, r33, lr, v0, v1, v2);
+    l0 = fmaxf(lr, 0.f);
+    gap = (lmax > 0.f) ? (lmid - lmin) / lmax : 0.f;
+}
+
+// Orientation: d > 0 (the camera centre lies on the positive side); d == 0
+// is broken toward n_z < 0, then toward a negative first nonzero component.
+__device__ __forceinline__ void orient(float& nx, float& ny, float& nz, float& d) {
+    bool flip = d < 0.f;
+    if (d == 0.f) flip = (nz > 0.f) || (nz == 0.f && (nx > 0.f || (nx == 0.f && ny > 0.f)));
+    if (flip) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
+}
+
+// Disparity (RGBD-space) implicit fit of one window, Eq. 12 / Eq. 14.
+//
+// Inputs are exact window sums over the valid pixels q of the window:
+//   n, Sj = sum j, Si = sum i, Sjj = sum j^2, Sji = sum j i, Sii = sum i^2
+//   Sw = sum w, Swj = sum w j, Swi = sum w i, Sww = sum w^2
+// where w = 1/Z is stored as an integer in units of qw (w_metric = qw * w).
+// tx, ty are the ray tangents of the window centre, a = 1/fx, b = 1/fy.
+//
+// With m_q = [tx + a j, ty + b i, 1] the Schur complement of the 4x4 scatter
+// [[sum m m^T, sum w m], [., sum w^2]] is the 1/Z^2-weighted covariance of
+// the window's 3D points.  Writing the weighted centroid ray
+// mhat = [tx + a jhat, ty + b ihat, 1] with jhat = sum w j / sum w and
+// what = sum w^2 / sum w, that complement equals K Y K^T with
+//   K = [[a, 0, mhat_x], [0, b, mhat_y], [0, 0, 1]],
+//   Y = sum y y^T over y = [j - jhat, i - ihat, (what - w)/what],
+// and every entry of Y follows from the centred integer moments below.
+// The offset is d = -(n . mhat) / what.
+__device__ __forceinline__ FitOut solve_disparity(int n, int Sj, int Si, int Sjj, int Sji, int Sii, int64_t Sw,
+                                                  int64_t Swj, int64_t Swi, int64_t Sww, float qw, float tx, float ty,
+                                                  float a, float b) {
+    const float nf = (float)n;
+    const float inv_n = rcp_approx(nf);
+    // exact re-centring on an integer near the mean disparity
+    const int64_t m = (int64_t)rintf((float)Sw * inv_n);
+    const int64_t T0 = Sw - (int64_t)n * m;
+    const int64_t Tww = Sww - 2 * m * Sw + (int64_t)n * m * m;  // sum (w - m)^2
+    const int64_t Twj = Swj - m * (int64_t)Sj;                   // sum (w - m) j
+    const int64_t Twi = Swi - m * (int64_t)Si;                   // sum (w - m) i
+    const float fT0 = (float)T0;
+    const float t0 = fT0 * inv_n;
+    const float jb = (float)Sj * inv_n, ib = (float)Si * inv_n;
+    const float Cjj = (float)Sjj - (float)Sj * jb;
+    const float Cji = (float)Sji - (float)Sj * ib;
+    const float Cii = (float)Sii - (float)Si * ib;
+    const float Cjw = (float)Twj - (float)Sj * t0;
+    const float Ciw = (float)Twi - (float)Si * t0;
+    const float Cww = (float)Tww - fT0 * t0;
+    const float wbar = (float)m + t0;  // mean disparity (units of qw)
+    const float inv_nw = rcp_approx(nf * wbar);
+    const float dj = Cjw * inv_nw;     // jhat - jbar
+    const float di = Ciw * inv_nw;     // ihat - ibar
+    const float e = Cww * inv_nw;      // what - wbar
+    const float what = wbar + e;
+    const float Yjj = Cjj + nf * dj * dj;
+    const float Yji = Cji + nf * dj * di;
+    const float Yii = Cii + nf * di * di;
+    const float Yjr = -nf * dj;
+    const float Yir = -nf * di;
+    const float iw = rcp_approx(what);
+    const float Yrr = (Cww + nf * e * e) * iw * iw;
+    const float mx = tx + a * (jb + dj);
+    const float my = ty + b * (ib + di);
+    const float R11 = a * a * Yjj + 2.f * a * mx * Yjr + mx * mx * Yrr;
+    const float R12 = a * b * Yji + a * my * Yjr + b * mx * Yir + mx * my * Yrr;
+    const float R13 = a * Yjr + mx * Yrr;
+    const float R22 = b * b * Yii + 2.f * b * my * Yir + my * my * Yrr;
+    const float R23 = b * Yir + my * Yrr;
+    const float R33 = Yrr;
+    FitOut o;
+    float l0;
+    smallest_eigpair(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, l0, o.gap);
+    o.curv = l0;
+    o.d = -(o.nx * mx + o.ny * my + o.nz) * iw / qw;
+    orient(o.nx, o.ny, o.nz, o.d);
+    return o;
+}
+
+// Standard implicit fit of one window, Eq. 3-6, from exact integer sums of
+// z = Z / qz (fixed point) with window-relative offsets j, i:
+//   n, Sz, Szj, Szi, Szz, Szzj, Szzi, Szzjj, Szzji, Szzii.
+// P_q = Z_q m_q = T [Z j, Z i, Z] with T = [[a, 0, tx], [0, b, ty], [0, 0, 1]],
+// so the covariance of the points is T C T^T, C the covariance of
+// [z j, z i, z] (re-centred on an integer near the mean depth first).
+__device__ __forceinline__ FitOut solve_standard(int n, int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
+                                                 int64_t Szzj, int64_t Szzi, int64_t Szzjj, int64_t Szzji,
+                                                 int64_t Szzii, float qz, float tx, float ty, float a, float b) {
+    const float nf = (float)n;
+    const float inv_n = rcp_approx(nf);
+    const int64_t m = (int64_t)rintf((float)Sz * inv_n);
+    const int64_t T0 = Sz - (int64_t)n * m;
+    const int64_t Tzz = Szz - 2 * m * Sz + (int64_t)n * m * m;  // sum (z - m)^2
+    const int64_t Tzj = Szzj - m * Szj;                         // sum z j (z - m)
+    const int64_t Tzi = Szzi - m * Szi;                         // sum z i (z - m)
+    const float t0 = (float)T0 * inv_n;                         // zbar - m
+    const float fSzj = (float)Szj, fSzi = (float)Szi;
+    const float Czz = (float)Tzz - (float)T0 * t0;
+    const float Cjz = (float)Tzj - fSzj * t0;
+    const float Ciz = (float)Tzi - fSzi * t0;
+    const float qj = fSzj * inv_n, qi = fSzi * inv_n;           // means of z j, z i
+    const float Cjj = (float)Szzjj - fSzj * qj;
+    const float Cji = (float)Szzji - fSzj * qi;
+    const float Cii = (float)Szzii - fSzi * qi;
+    const float R11 = a * a * Cjj + 2.f * a * tx * Cjz + tx * tx * Czz;
+    const float R12 = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
+    const float R13 = a * Cjz + tx * Czz;
+    const float R22 = b * b * Cii + 2.f * b * ty * Ciz + ty * ty * Czz;
+    const float R23 = b * Ciz + ty * Czz;
+    const float R33 = Czz;
+    FitOut o;
+    float l0;
+    smallest_eigpair(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, l0, o.gap);
+    o.curv = l0;
+    const float zb = (float)m + t0;
+    const float px = a * qj + tx * zb, py = b * qi + ty * zb;
+    o.d = -(o.nx * px + o.ny * py + o.nz * zb) * qz;
+    orient(o.nx, o.ny, o.nz, o.d);
+    return o;
+}
+
+}  // namespace sf

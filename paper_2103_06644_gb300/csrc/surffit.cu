@@ -1,0 +1,715 @@
+// surffit.cu -- GB300 (sm_103a) kernels and C ABI for dense RGBD plane fitting.
+//
+// Pipeline for one frame (all device work, no host synchronisation):
+//   1. range     max of the fixed-point variable over the frame's valid pixels
+//                (1/Z for the disparity form, Z for the standard form), giving
+//                a power-of-two quantum so that every value fits in `bits`
+//                bits (26-28 for the disparity form, 23-28 for the standard
+//                form: the most that keeps every exact sum inside int64).
+//   2. hpass     one thread per image row slides a k-wide window along the row
+//                and writes exact integer horizontal window moments
+//                (sums of v, v*j, v*j^2 for the mask, w and w^2 ...) to scratch.
+//   3. vpass     one thread per image column slides the window down the
+//                column over those moments (plus the i-weighted sums), which
+//                yields the exact 2D window moments of every pixel, and solves
+//                the plane fit in registers (sf_solve.cuh).
+//
+// The integral-image idea of Section II.C appears here as running sums: every
+// window sum costs O(1) per pixel regardless of k.  All sums are integers, so
+// they are exact and the result does not depend on the image size or on the
+// order of summation (no floating-point summed-area table is ever formed).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "surffit.h"
+#include "sf_solve.cuh"
+
+namespace sf {
+
+constexpr int kMaxR = (SF_MAX_WINDOW - 1) / 2;
+constexpr int kHThreads = 128;   // rows per hpass block
+constexpr int kHSeg = 64;        // output columns per hpass thread
+constexpr int kVThreads = 128;   // columns per vpass block
+constexpr int kVBand = 64;       // output rows per vpass thread
+
+// ---------------------------------------------------------------------------
+// Depth decoding.
+// ---------------------------------------------------------------------------
+template <int DT>
+__device__ __forceinline__ float load_depth(const void* base, size_t idx, float scale);
+
+template <>
+__device__ __forceinline__ float load_depth<SF_DEPTH_F32>(const void* base, size_t idx, float) {
+    return __ldg(reinterpret_cast<const float*>(base) + idx);
+}
+template <>
+__device__ __forceinline__ float load_depth<SF_DEPTH_U16>(const void* base, size_t idx, float scale) {
+    const unsigned short raw = __ldg(reinterpret_cast<const unsigned short*>(base) + idx);
+    return raw ? (float)raw * scale : 0.f;
+}
+
+__device__ __forceinline__ bool depth_valid(float z) { return z > 0.f && z < INFINITY; }
+
+// The variable summed by each method, before fixed-point scaling:
+//   disparity 1/Z (float32 depth) or 1/raw (uint16 depth; the metric scale is
+//   folded into the quantum), standard Z (float32) or raw (uint16).
+template <int DT, int M>
+__device__ __forceinline__ float fit_variable_of(float zin) {
+    if (M == SF_METHOD_DISPARITY) return rcp_approx(zin);
+    return zin;
+}
+
+// Raw stored value: metres for float32, raw units for uint16 (0 = missing).
+template <int DT>
+__device__ __forceinline__ float load_raw(const void* base, size_t idx) {
+    if (DT == SF_DEPTH_F32) return __ldg(reinterpret_cast<const float*>(base) + idx);
+    return (float)__ldg(reinterpret_cast<const unsigned short*>(base) + idx);
+}
+
+// round(sc / z) to the nearest integer for sc = 2^e, without the 24-bit limit
+// of a float32 reciprocal: y = rcp(z) is refined by the exact FMA residual
+// e = 1 - z*y (exact in float32 for |e| <= 2^-22), so 1/z = y + y*e to about
+// 2^-44; the integer is assembled from the two parts without re-rounding.
+__device__ __forceinline__ int quant_recip(float z, float sc) {
+    const float y = rcp_approx(z);
+    const float e = fmaf(-z, y, 1.f);
+    const float hi = y * sc;           // exact: power-of-two scaling
+    const float lo = (y * e) * sc;
+    const float hr = rintf(hi);
+    return (int)hr + (int)rintf((hi - hr) + lo);
+}
+
+// Exponent e such that v * 2^e <= 2^bits for all v <= vmax.
+__device__ __forceinline__ int quant_exponent(unsigned vmax_bits, int bits) {
+    const float vmax = __uint_as_float(vmax_bits);
+    if (!(vmax > 0.f)) return 0;
+    int E;
+    frexpf(vmax, &E);
+    return bits - E;
+}
+
+// Fixed-point value of a valid pixel (>= 0), or -1 for a missing one.
+template <int DT, int M>
+__device__ __forceinline__ int quantize(const void* depth, size_t idx, float sc) {
+    const float zin = load_raw<DT>(depth, idx);
+    if (!depth_valid(zin)) return -1;
+    if (DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD) return (int)zin;
+    if (M == SF_METHOD_DISPARITY) return quant_recip(zin, sc);
+    return __float2int_rn(zin * sc);
+}
+
+// Metric size of one fixed-point unit.
+template <int DT, int M>
+__device__ __forceinline__ float quantum(unsigned vmax_bits, int bits, float scale) {
+    if (DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD) return scale;
+    const float q = ldexpf(1.f, -quant_exponent(vmax_bits, bits));
+    if (DT == SF_DEPTH_U16 && M == SF_METHOD_DISPARITY) return q / scale;
+    return q;
+}
+
+// ---------------------------------------------------------------------------
+// 1. range
+// ---------------------------------------------------------------------------
+template <int DT, int M>
+__global__ void __launch_bounds__(256) range_kernel(const void* __restrict__ depth, size_t frame_elems, float scale,
+                                                    unsigned* __restrict__ vmax_bits) {
+    const int f = blockIdx.y;
+    const size_t base = (size_t)f * frame_elems;
+    float vmax = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < frame_elems;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float z = load_raw<DT>(depth, base + i);
+        if (depth_valid(z)) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z));
+    }
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    __shared__ float red[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = vmax;
+    __syncthreads();
+    if (warp == 0) {
+        vmax = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if (lane == 0 && vmax > 0.f) atomicMax(vmax_bits + f, __float_as_uint(vmax));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scratch layout of the horizontal moments (pitch Wp, a multiple of 64).
+// ---------------------------------------------------------------------------
+// Disparity planes, each a block of n_frames * plane_elems entries, in order:
+//   hm int32 packed mask moments: count | (sum j + 512) << 6 | sum j^2 << 16
+//   g0 int64 sum w,  g1 int64 sum w j,  q0 int64 sum w^2
+// Standard planes:
+//   hc int32 count, z0 int64 sum z, z1 int64 sum z j,
+//   b0 int64 sum z^2, b1 int64 sum z^2 j, b2 int64 sum z^2 j^2
+struct Planes {
+    int32_t* p32;       // the int32 plane
+    int64_t* p64;       // first int64 plane; plane c is p64 + c * stride
+    size_t stride;      // n_frames * plane_elems
+    __host__ __device__ Planes(void* base, size_t nf, size_t plane_elems)
+        : p32(reinterpret_cast<int32_t*>(base)),
+          p64(reinterpret_cast<int64_t*>(reinterpret_cast<int32_t*>(base) + nf * plane_elems)),
+          stride(nf * plane_elems) {}
+    __device__ __forceinline__ int64_t* c64(int c) const { return p64 + (size_t)c * stride; }
+};
+
+__device__ __forceinline__ int32_t pack_mask(int h0, int h1, int h2) {
+    return h0 | ((h1 + 512) << 6) | (h2 << 16);
+}
+__device__ __forceinline__ void unpack_mask(int32_t v, int& h0, int& h1, int& h2) {
+    h0 = v & 63;
+    h1 = ((v >> 6) & 1023) - 512;
+    h2 = (int)((uint32_t)v >> 16);
+}
+
+// Running sums of c, c*j, c*j^2 over j in [-r, r] slide by one column with
+//   S0' = S0 - out + in
+//   S1' = S1 + r*out + (r+1)*in - S0'
+//   S2' = S2 - r(r+2)*out + (r+1)(r-1)*in - 2*S1 + S0'
+// (out leaves at j = -r, in enters at j = r + 1; S1 on the right is the old one).
+template <typename T>
+__device__ __forceinline__ void slide3(T& S0, T& S1, T& S2, T out, T in, int r) {
+    const T n0 = S0 - out + in;
+    const T n1 = S1 + (T)r * out + (T)(r + 1) * in - n0;
+    const T n2 = S2 - (T)(r * (r + 2)) * out + (T)((r + 1) * (r - 1)) * in - 2 * S1 + n0;
+    S0 = n0; S1 = n1; S2 = n2;
+}
+template <typename T>
+__device__ __forceinline__ void slide2(T& S0, T& S1, T out, T in, int r) {
+    const T n0 = S0 - out + in;
+    S1 = S1 + (T)r * out + (T)(r + 1) * in - n0;
+    S0 = n0;
+}
+
+// ---------------------------------------------------------------------------
+// 2. hpass: block = 128 rows x 64 output columns, tile of fixed-point values
+//    staged in shared memory with coalesced loads, one thread per row.
+// ---------------------------------------------------------------------------
+template <int DT, int M>
+__global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict__ depth, int W, int H, int r,
+                                                          float scale, const unsigned* __restrict__ vmax_bits,
+                                                          int bits, int raw_z, int Wp, size_t plane_elems,
+                                                          void* planes_base) {
+    extern __shared__ int tile[];
+    const int f = blockIdx.z;
+    const int x0 = blockIdx.x * kHSeg;
+    const int y0 = blockIdx.y * kHThreads;
+    const int IW = kHSeg + 2 * r;
+    const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
+    const float sc = ldexpf(1.f, quant_exponent(vmax_bits[f], bits));  // 2^e, exact
+    const size_t fbase = (size_t)f * W * H;
+    const int rows = min(kHThreads, H - y0);
+    for (int idx = threadIdx.x; idx < rows * IW; idx += kHThreads) {
+        const int ry = idx / IW, cx = idx - ry * IW;
+        const int x = x0 - r + cx, y = y0 + ry;
+        int v = -1;
+        if (x >= 0 && x < W) v = quantize<DT, M>(depth, fbase + (size_t)y * W + x, sc);
+        tile[ry * pitch + cx] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x >= rows) return;
+    const int y = y0 + threadIdx.x;
+    const int* row = tile + threadIdx.x * pitch;
+    const int xend = min(x0 + kHSeg, W);
+    const size_t obase = (size_t)f * plane_elems + (size_t)y * Wp;
+
+    // channel state: mask moments (count, sum j, sum j^2) and value moments
+    int h0 = 0, h1 = 0, h2 = 0;
+    int64_t a0 = 0, a1 = 0;          // sum v, sum v j
+    int64_t s0 = 0, s1 = 0, s2 = 0;  // sum v^2, sum v^2 j, sum v^2 j^2 (s1, s2: standard only)
+    for (int j = -r; j <= r; ++j) {
+        const int v = row[j + r];
+        if (v >= 0) {
+            const int64_t vv = (int64_t)v * v;
+            h0 += 1; h1 += j; h2 += j * j;
+            a0 += v; a1 += (int64_t)v * j;
+            s0 += vv;
+            if (M == SF_METHOD_STANDARD) { s1 += vv * j; s2 += vv * (j * j); }
+        }
+    }
+    const Planes P(planes_base, gridDim.z, plane_elems);
+    for (int x = x0; x < xend; ++x) {
+        const size_t o = obase + x;
+        if (M == SF_METHOD_DISPARITY) {
+            P.p32[o] = pack_mask(h0, h1, h2);
+            P.c64(0)[o] = a0; P.c64(1)[o] = a1; P.c64(2)[o] = s0;
+        } else {
+            P.p32[o] = h0;
+            P.c64(0)[o] = a0; P.c64(1)[o] = a1; P.c64(2)[o] = s0; P.c64(3)[o] = s1; P.c64(4)[o] = s2;
+        }
+        if (x + 1 < xend) {
+            const int vo = row[x - x0];              // column x - r leaves
+            const int vi = row[x - x0 + 2 * r + 1];  // column x + r + 1 enters
+            const int mo = vo >= 0, mi = vi >= 0;
+            slide3(h0, h1, h2, mo, mi, r);
+            const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
+            slide2(a0, a1, co, ci, r);
+            const int64_t qo = co * co, qi = ci * ci;
+            if (M == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
+            else s0 = s0 - qo + qi;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. vpass + solve: one thread per column, band of kVBand output rows.
+// ---------------------------------------------------------------------------
+struct Calib {
+    const float* tx;  // [W] ray tangent per column
+    const float* ty;  // [H] ray tangent per row
+    float a, b;       // 1/fx, 1/fy
+};
+
+template <int DT, int M>
+__global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
+                                                          float scale, const unsigned* __restrict__ vmax_bits,
+                                                          int bits, int raw_z, int Wp, size_t plane_elems,
+                                                          void* __restrict__ planes_base, Calib cal,
+                                                          int min_valid, int require_center, float* __restrict__ normals,
+                                                          float* __restrict__ offsets, float* __restrict__ curvature,
+                                                          int32_t* __restrict__ counts) {
+    const int f = blockIdx.z;
+    const int x = blockIdx.x * kVThreads + threadIdx.x;
+    if (x >= W) return;
+    const int y0 = blockIdx.y * kVBand;
+    const int y1 = min(y0 + kVBand, H);
+    const size_t nf = gridDim.z;
+    const size_t pb = (size_t)f * plane_elems + x;
+    const float q = quantum<DT, M>(vmax_bits[f], bits, scale);  // metric value of one fixed-point unit
+    const float tx = cal.tx[x];
+    const size_t fo = (size_t)f * W * H;
+
+    if (M == SF_METHOD_DISPARITY) {
+        const Planes P(planes_base, nf, plane_elems);
+        const int32_t* hm = P.p32;
+        const int64_t* g0 = P.c64(0);
+        const int64_t* g1 = P.c64(1);
+        const int64_t* q0 = P.c64(2);
+        int n = 0, Sj = 0, Sjj = 0, Si = 0, Sji = 0, Sii = 0;
+        int64_t Sw = 0, Swj = 0, Swi = 0, Sww = 0;
+        for (int yy = y0 - r; yy <= y0 + r; ++yy) {
+            if (yy < 0 || yy >= H) continue;
+            const size_t o = pb + (size_t)yy * Wp;
+            int c0, c1, c2;
+            unpack_mask(__ldg(hm + o), c0, c1, c2);
+            const int i = yy - y0;
+            n += c0; Sj += c1; Sjj += c2; Si += i * c0; Sji += i * c1; Sii += i * i * c0;
+            const int64_t w0 = __ldg(g0 + o);
+            Sw += w0; Swj += __ldg(g1 + o); Swi += (int64_t)i * w0; Sww += __ldg(q0 + o);
+        }
+        for (int y = y0; y < y1; ++y) {
+            const size_t oi = fo + (size_t)y * W + x;
+            const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
+            const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
+            float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
+            if (ok) {
+                const FitOut fo_ = solve_disparity(n, Sj, Si, Sjj, Sji, Sii, Sw, Swj, Swi, Sww, q, tx, cal.ty[y],
+                                                   cal.a, cal.b);
+                nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
+            }
+            normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
+            offsets[oi] = d; curvature[oi] = cu;
+            if (counts) counts[oi] = n;
+            if (y + 1 < y1) {
+                const int yo = y - r, yi = y + r + 1;
+                int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
+                int64_t wo = 0, wjo = 0, wwo = 0, wi = 0, wji = 0, wwi = 0;
+                if (yo >= 0) {
+                    const size_t o = pb + (size_t)yo * Wp;
+                    unpack_mask(__ldg(hm + o), o0, o1, o2);
+                    wo = __ldg(g0 + o); wjo = __ldg(g1 + o); wwo = __ldg(q0 + o);
+                }
+                if (yi < H) {
+                    const size_t o = pb + (size_t)yi * Wp;
+                    unpack_mask(__ldg(hm + o), i0, i1, i2);
+                    wi = __ldg(g0 + o); wji = __ldg(g1 + o); wwi = __ldg(q0 + o);
+                }
+                // vertical moments: (n, Si, Sii) from the counts, (Sj, Sji) from sum j, Sjj plain
+                slide3(n, Si, Sii, o0, i0, r);
+                slide2(Sj, Sji, o1, i1, r);
+                Sjj += i2 - o2;
+                slide2(Sw, Swi, wo, wi, r);
+                Swj += wji - wjo;
+                Sww += wwi - wwo;
+            }
+        }
+    } else {
+        const Planes P(planes_base, nf, plane_elems);
+        const int32_t* hc = P.p32;
+        const int64_t* z0 = P.c64(0);
+        const int64_t* z1 = P.c64(1);
+        const int64_t* b0 = P.c64(2);
+        const int64_t* b1 = P.c64(3);
+        const int64_t* b2 = P.c64(4);
+        int n = 0;
+        int64_t Sz = 0, Szi = 0, Szj = 0, Szz = 0, Szzi = 0, Szzii = 0, Szzj = 0, Szzji = 0, Szzjj = 0;
+        for (int yy = y0 - r; yy <= y0 + r; ++yy) {
+            if (yy < 0 || yy >= H) continue;
+            const size_t o = pb + (size_t)yy * Wp;
+            const int64_t i = yy - y0;
+            n += __ldg(hc + o);
+            const int64_t c0 = __ldg(z0 + o), q0v = __ldg(b0 + o), q1v = __ldg(b1 + o);
+            Sz += c0; Szi += i * c0; Szj += __ldg(z1 + o);
+            Szz += q0v; Szzi += i * q0v; Szzii += i * i * q0v;
+            Szzj += q1v; Szzji += i * q1v; Szzjj += __ldg(b2 + o);
+        }
+        for (int y = y0; y < y1; ++y) {
+            const size_t oi = fo + (size_t)y * W + x;
+            const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
+            const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
+            float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
+            if (ok) {
+                const FitOut fo_ = solve_standard(n, Sz, Szj, Szi, Szz, Szzj, Szzi, Szzjj, Szzji, Szzii, q, tx,
+                                                  cal.ty[y], cal.a, cal.b);
+                nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
+            }
+            normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
+            offsets[oi] = d; curvature[oi] = cu;
+            if (counts) counts[oi] = n;
+            if (y + 1 < y1) {
+                const int yo = y - r, yi = y + r + 1;
+                int co = 0, ci = 0;
+                int64_t zo = 0, zjo = 0, qo0 = 0, qo1 = 0, qo2 = 0, zi = 0, zji = 0, qi0 = 0, qi1 = 0, qi2 = 0;
+                if (yo >= 0) {
+                    const size_t o = pb + (size_t)yo * Wp;
+                    co = __ldg(hc + o); zo = __ldg(z0 + o); zjo = __ldg(z1 + o);
+                    qo0 = __ldg(b0 + o); qo1 = __ldg(b1 + o); qo2 = __ldg(b2 + o);
+                }
+                if (yi < H) {
+                    const size_t o = pb + (size_t)yi * Wp;
+                    ci = __ldg(hc + o); zi = __ldg(z0 + o); zji = __ldg(z1 + o);
+                    qi0 = __ldg(b0 + o); qi1 = __ldg(b1 + o); qi2 = __ldg(b2 + o);
+                }
+                n += ci - co;
+                slide2(Sz, Szi, zo, zi, r);
+                Szj += zji - zjo;
+                slide3(Szz, Szzi, Szzii, qo0, qi0, r);
+                slide2(Szzj, Szzji, qo1, qi1, r);
+                Szzjj += qi2 - qo2;
+            }
+        }
+    }
+}
+
+}  // namespace sf
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+namespace {
+
+thread_local std::string g_last_error;
+
+sf_status fail(sf_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+sf_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(SF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SF_CUDA(call)                                        \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);  \
+    } while (0)
+
+size_t plane_bytes_per_frame(int method, size_t plane_elems) {
+    // disparity: 1 x int32 + 3 x int64 ; standard: 1 x int32 + 5 x int64
+    return plane_elems * (method == SF_METHOD_STANDARD ? (4 + 5 * 8) : (4 + 3 * 8));
+}
+
+// Fixed-point bits for a method and window: the most that keeps every exact
+// window sum and every re-centring product below 2^63.
+//   disparity: 2 * m * sum w <= 2 k^2 2^(2b)                 -> b < 31 - log2 k
+//   standard:  sum z^2 j^2   <= k * sum_{|j|<=r} j^2 * 2^(2b) and 2 k^2 2^(2b)
+int quant_bits(int method, int k) {
+    const int r = (k - 1) / 2;
+    double weight = 2.0 * k * k;
+    if (method == SF_METHOD_STANDARD || method == SF_METHOD_EXPLICIT_STANDARD) {
+        const double wjj = (double)k * (double)r * (r + 1) * (2 * r + 1) / 3.0;
+        weight = std::max(weight, wjj);
+    }
+    int b = (int)std::floor((63.0 - std::log2(weight)) / 2.0 - 1e-9);
+    return std::min(28, std::max(16, b));
+}
+
+}  // namespace
+
+struct sf_ctx {
+    sf_intrinsics K;
+    int W, H, k, r;
+    int Wp;
+    size_t plane_elems;
+    int method = SF_METHOD_DISPARITY;
+    int depth_type = SF_DEPTH_F32;
+    float depth_scale = 1e-3f;
+    int min_valid = 3;
+    int require_center = 1;
+    int device = 0;
+    float* tx = nullptr;  // [W]
+    float* ty = nullptr;  // [H]
+    unsigned* vmax = nullptr;  // [max_frames]
+    void* planes = nullptr;
+    int planes_frames = 0;     // frames the planes buffer holds
+    size_t planes_bytes = 0;
+    int max_frames_per_pass = 1;
+    // pinned host staging for sf_fit_host
+    void* h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    void* d_io = nullptr;
+    size_t d_io_bytes = 0;
+};
+
+static sf_status ensure_planes(sf_ctx* c, int frames) {
+    const size_t need = plane_bytes_per_frame(SF_METHOD_STANDARD, c->plane_elems) * (size_t)frames;
+    if (c->planes && c->planes_bytes >= need && c->planes_frames >= frames) return SF_OK;
+    if (c->planes) cudaFree(c->planes);
+    c->planes = nullptr;
+    c->planes_bytes = 0;
+    c->planes_frames = 0;
+    cudaError_t e = cudaMalloc(&c->planes, need);
+    if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "scratch allocation of %zu bytes failed: %s", need,
+                                      cudaGetErrorString(e));
+    c->planes_bytes = need;
+    c->planes_frames = frames;
+    return SF_OK;
+}
+
+template <int DT, int M>
+static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,
+                             int32_t* counts, cudaStream_t st) {
+    const size_t fe = (size_t)c->W * c->H;
+    const int raw_z = (DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD) ? 1 : 0;
+    const int bits = quant_bits(M, c->k);
+    SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
+    if (!raw_z) {
+        int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
+        blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
+        sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, c->depth_scale, c->vmax);
+    }
+    {
+        dim3 grid((c->W + sf::kHSeg - 1) / sf::kHSeg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
+        const int IW = sf::kHSeg + 2 * c->r;
+        const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
+        sf::hpass_kernel<DT, M><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
+                                                                  bits, raw_z, c->Wp, c->plane_elems, c->planes);
+    }
+    {
+        dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + sf::kVBand - 1) / sf::kVBand, nfr);
+        sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
+        sf::vpass_kernel<DT, M><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
+                                                               bits, raw_z, c->Wp, c->plane_elems, c->planes, cal,
+                                                               c->min_valid, c->require_center, normals, offsets,
+                                                               curv, counts);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SF_OK;
+}
+
+extern "C" {
+
+const char* sf_last_error(void) { return g_last_error.c_str(); }
+
+const char* sf_version(void) { return "surffit-gb300 0.1 (sm_103a)"; }
+
+sf_status sf_channel_counts(int method, int* depth_channels, int* mask_channels) {
+    if (!depth_channels || !mask_channels) return fail(SF_ERR_INVALID_ARG, "null output pointer");
+    switch (method) {
+        case SF_METHOD_DISPARITY:  // sum w, sum w j, sum w i, sum w^2 ; mask n, j, i, j^2, ji, i^2
+            *depth_channels = 4; *mask_channels = 6; return SF_OK;
+        case SF_METHOD_STANDARD:   // z, zj, zi, z^2, z^2 j, z^2 i, z^2 j^2, z^2 ji, z^2 i^2 ; mask n
+            *depth_channels = 9; *mask_channels = 1; return SF_OK;
+        case SF_METHOD_EXPLICIT_DISPARITY:  // w, w j, w i ; mask n, j, i, j^2, ji, i^2
+            *depth_channels = 3; *mask_channels = 6; return SF_OK;
+        case SF_METHOD_EXPLICIT_STANDARD:   // X^2, XY, X, Y^2, Y, ZX, ZY, Z in window-relative form
+            *depth_channels = 8; *mask_channels = 1; return SF_OK;
+        default:
+            return fail(SF_ERR_INVALID_ARG, "unknown method %d", method);
+    }
+}
+
+sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** out) {
+    if (!K || !out) return fail(SF_ERR_INVALID_ARG, "null intrinsics or output pointer");
+    *out = nullptr;
+    if (W < 1 || H < 1) return fail(SF_ERR_INVALID_ARG, "image size %dx%d must be positive", W, H);
+    if ((size_t)W * (size_t)H > ((size_t)1 << 31)) return fail(SF_ERR_INVALID_ARG, "image too large");
+    if (window < 1 || (window & 1) == 0 || window > SF_MAX_WINDOW)
+        return fail(SF_ERR_INVALID_ARG, "window %d must be odd and in [1, %d]", window, SF_MAX_WINDOW);
+    if (!(K->fx != 0.0) || !(K->fy != 0.0) || !std::isfinite(K->fx) || !std::isfinite(K->fy) ||
+        !std::isfinite(K->cx) || !std::isfinite(K->cy) || !std::isfinite(K->dx) || !std::isfinite(K->dy))
+        return fail(SF_ERR_INVALID_ARG, "intrinsics must be finite with nonzero focal lengths");
+    sf_ctx* c = new (std::nothrow) sf_ctx();
+    if (!c) return fail(SF_ERR_ALLOC, "context allocation failed");
+    c->K = *K;
+    c->W = W; c->H = H; c->k = window; c->r = (window - 1) / 2;
+    c->Wp = (W + 63) / 64 * 64;
+    c->plane_elems = (size_t)c->Wp * H;
+    cudaGetDevice(&c->device);
+    // Calibration tables (Eq. 10), computed in FP64 on the host, stored as FP32.
+    float* htx = (float*)malloc(sizeof(float) * W);
+    float* hty = (float*)malloc(sizeof(float) * H);
+    if (!htx || !hty) { free(htx); free(hty); delete c; return fail(SF_ERR_ALLOC, "host table allocation failed"); }
+    for (int x = 0; x < W; ++x) htx[x] = (float)((x + K->dx - K->cx) / K->fx);
+    for (int y = 0; y < H; ++y) hty[y] = (float)((y + K->dy - K->cy) / K->fy);
+    cudaError_t e = cudaMalloc(&c->tx, sizeof(float) * W);
+    if (e == cudaSuccess) e = cudaMalloc(&c->ty, sizeof(float) * H);
+    if (e == cudaSuccess) e = cudaMemcpy(c->tx, htx, sizeof(float) * W, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->ty, hty, sizeof(float) * H, cudaMemcpyHostToDevice);
+    free(htx); free(hty);
+    if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create tables"); }
+    // Frames per pass: keep the scratch moments (<= 36 B/px) near 48 MB so
+    // that they stay resident in L2 between the two passes.
+    const size_t per = plane_bytes_per_frame(SF_METHOD_STANDARD, c->plane_elems);
+    c->max_frames_per_pass = (int)std::max<size_t>(1, ((size_t)48 << 20) / per);
+    if (c->max_frames_per_pass > 64) c->max_frames_per_pass = 64;
+    e = cudaMalloc(&c->vmax, sizeof(unsigned) * 64);
+    if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create vmax"); }
+    sf_status s = ensure_planes(c, 1);
+    if (s != SF_OK) { sf_destroy(c); return s; }
+    {
+        const int IW = sf::kHSeg + 2 * sf::kMaxR;
+        const int smem = (int)(sizeof(int) * sf::kHThreads * (size_t)(IW | 1));
+        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_F32, SF_METHOD_DISPARITY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_F32, SF_METHOD_STANDARD>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_U16, SF_METHOD_DISPARITY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_U16, SF_METHOD_STANDARD>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create kernel attributes"); }
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create synchronise"); }
+    *out = c;
+    return SF_OK;
+}
+
+sf_status sf_set_params(sf_ctx* c, int method, int depth_type, float depth_scale, int min_valid,
+                        int require_center_valid) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    if (method < SF_METHOD_DISPARITY || method > SF_METHOD_EXPLICIT_STANDARD)
+        return fail(SF_ERR_INVALID_ARG, "unknown method %d", method);
+    if (depth_type != SF_DEPTH_F32 && depth_type != SF_DEPTH_U16)
+        return fail(SF_ERR_INVALID_ARG, "unknown depth type %d", depth_type);
+    if (depth_type == SF_DEPTH_U16 && !(depth_scale > 0.f && std::isfinite(depth_scale)))
+        return fail(SF_ERR_INVALID_ARG, "depth_scale must be positive and finite");
+    if (min_valid < 1) return fail(SF_ERR_INVALID_ARG, "min_valid must be >= 1");
+    c->method = method;
+    c->depth_type = depth_type;
+    c->depth_scale = depth_scale;
+    c->min_valid = min_valid;
+    c->require_center = require_center_valid ? 1 : 0;
+    return SF_OK;
+}
+
+sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
+                    int32_t* counts, void* stream) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
+    if (n_frames == 0) return SF_OK;
+    if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
+    if (c->method == SF_METHOD_EXPLICIT_DISPARITY || c->method == SF_METHOD_EXPLICIT_STANDARD)
+        return fail(SF_ERR_UNSUPPORTED, "explicit fits are not built in this library version");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t fe = (size_t)c->W * c->H;
+    const size_t dbytes = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
+    int per = std::min(c->max_frames_per_pass, 64);
+    sf_status s = ensure_planes(c, std::min(per, n_frames));
+    if (s != SF_OK) return s;
+    for (int f0 = 0; f0 < n_frames; f0 += per) {
+        const int nfr = std::min(per, n_frames - f0);
+        const void* dp = static_cast<const char*>(depth) + dbytes * fe * f0;
+        float* np_ = normals + 3 * fe * f0;
+        float* op = offsets + fe * f0;
+        float* cp = curvature + fe * f0;
+        int32_t* kp = counts ? counts + fe * f0 : nullptr;
+        if (c->depth_type == SF_DEPTH_F32) {
+            s = c->method == SF_METHOD_DISPARITY
+                    ? launch_pass<SF_DEPTH_F32, SF_METHOD_DISPARITY>(c, nfr, dp, np_, op, cp, kp, st)
+                    : launch_pass<SF_DEPTH_F32, SF_METHOD_STANDARD>(c, nfr, dp, np_, op, cp, kp, st);
+        } else {
+            s = c->method == SF_METHOD_DISPARITY
+                    ? launch_pass<SF_DEPTH_U16, SF_METHOD_DISPARITY>(c, nfr, dp, np_, op, cp, kp, st)
+                    : launch_pass<SF_DEPTH_U16, SF_METHOD_STANDARD>(c, nfr, dp, np_, op, cp, kp, st);
+        }
+        if (s != SF_OK) return s;
+    }
+    return SF_OK;
+}
+
+sf_status sf_fit(sf_ctx* c, const void* depth, float* normals, float* offsets, float* curvature, void* stream) {
+    return sf_fit_ex(c, 1, depth, normals, offsets, curvature, nullptr, stream);
+}
+
+sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
+                      int32_t* counts, void* stream) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
+    if (n_frames == 0) return SF_OK;
+    if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t fe = (size_t)c->W * c->H;
+    const size_t dbytes = (c->depth_type == SF_DEPTH_U16 ? 2 : 4) * fe * n_frames;
+    const size_t obytes = 20 * fe * n_frames + (counts ? 4 * fe * n_frames : 0);
+    const size_t need = dbytes + obytes;
+    if (c->d_io_bytes < need) {
+        if (c->d_io) cudaFree(c->d_io);
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->d_io = nullptr; c->h_stage = nullptr; c->d_io_bytes = c->h_stage_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->d_io, need);
+        if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "device staging of %zu bytes failed", need);
+        e = cudaMallocHost(&c->h_stage, need);
+        if (e != cudaSuccess) { cudaFree(c->d_io); c->d_io = nullptr; return fail(SF_ERR_ALLOC, "pinned staging failed"); }
+        c->d_io_bytes = c->h_stage_bytes = need;
+    }
+    char* hs = static_cast<char*>(c->h_stage);
+    char* ds = static_cast<char*>(c->d_io);
+    memcpy(hs, depth, dbytes);
+    SF_CUDA(cudaMemcpyAsync(ds, hs, dbytes, cudaMemcpyHostToDevice, st));
+    float* dn = reinterpret_cast<float*>(ds + dbytes);
+    float* dof = dn + 3 * fe * n_frames;
+    float* dc = dof + fe * n_frames;
+    int32_t* dk = counts ? reinterpret_cast<int32_t*>(dc + fe * n_frames) : nullptr;
+    sf_status s = sf_fit_ex(c, n_frames, ds, dn, dof, dc, dk, stream);
+    if (s != SF_OK) return s;
+    SF_CUDA(cudaMemcpyAsync(hs + dbytes, ds + dbytes, obytes, cudaMemcpyDeviceToHost, st));
+    SF_CUDA(cudaStreamSynchronize(st));
+    const char* ho = hs + dbytes;
+    memcpy(normals, ho, 12 * fe * n_frames);
+    memcpy(offsets, ho + 12 * fe * n_frames, 4 * fe * n_frames);
+    memcpy(curvature, ho + 16 * fe * n_frames, 4 * fe * n_frames);
+    if (counts) memcpy(counts, ho + 20 * fe * n_frames, 4 * fe * n_frames);
+    return SF_OK;
+}
+
+sf_status sf_destroy(sf_ctx* c) {
+    if (!c) return SF_OK;
+    if (c->tx) cudaFree(c->tx);
+    if (c->ty) cudaFree(c->ty);
+    if (c->vmax) cudaFree(c->vmax);
+    if (c->planes) cudaFree(c->planes);
+    if (c->d_io) cudaFree(c->d_io);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    delete c;
+    return SF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Counts and validity masks must match bit for bit; normals within 1e-3 rad and
+offsets within 1e-4 relative on non-degenerate windows (tests/parity.py).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import scenes
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2103_06644_gb300 import SurfaceFitter  # noqa: E402
+
+
+def run_gpu(depth, intr, k, method, depth_type="f32", depth_scale=1e-3, **kw):
+    H, W = depth.shape[-2:]
+    f = SurfaceFitter(intr, W, H, k, method=method, depth_type=depth_type, depth_scale=depth_scale, **kw)
+    t = torch.from_numpy(depth.view(np.int16) if depth.dtype == np.uint16 else depth).cuda()
+    if depth.dtype == np.uint16:
+        t = t.view(torch.uint16)
+    n, d, c, cnt = f.fit(t, counts=True)
+    torch.cuda.synchronize()
+    out = (n.cpu().numpy(), d.cpu().numpy(), c.cpu().numpy(), cnt.cpu().numpy())
+    f.close()
+    return out
+
+
+def run_ref(depth, intr, k, method, depth_scale=1e-3, **kw):
+    return oracle.fit(depth, intr, k, method, want_lambda=True, want_moments=True, depth_scale=depth_scale, **kw)
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_kinect_640x480_k7(method):
+    """One 640x480 float32 frame: 3 planes at 0.8-4 m, sigma 0.0012 Z^2, 5% missing, 7x7."""
+    intr = scenes.Intrinsics(525.0, 525.0, 319.5, 239.5)
+    depth = scenes.kinect_frame(scenes.BASE_SEED, intr, 640, 480)
+    s = compare(run_gpu(depth, intr.as_tuple(), 7, method), run_ref(depth, intr.as_tuple(), 7, method),
+                label="640x480 " + method)
+    assert s["good"] > 0.9 * s["valid"]
+    print(method, s)
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 40), (40, 1), (37, 23), (200, 150), (130, 257)])
+@pytest.mark.parametrize("k", [1, 3, 7, 15, 31])
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_ragged_sizes_and_windows(W, H, k, method):
+    intr = scenes.Intrinsics.scaled(W, H) if W > 1 else scenes.Intrinsics(525.0, 525.0, 0.0, (H - 1) / 2)
+    depth = scenes.kinect_frame(1000 + W * 7 + H, intr, W, H)
+    compare(run_gpu(depth, intr.as_tuple(), k, method), run_ref(depth, intr.as_tuple(), k, method),
+            label="%dx%d k=%d %s" % (W, H, k, method))
+
+
+@pytest.mark.parametrize("k", [5, 9, 15])
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_uint16_structured_light(k, method):
+    """uint16 millimetres, 4-8 planes + sphere, disparity-quantised, blob holes."""
+    W, H = 320, 180
+    intr = scenes.Intrinsics(920.0 / 4, 920.0 / 4, 159.5, 89.5)
+    depth = scenes.structured_light_frame(scenes.BASE_SEED + 1, intr, W, H)
+    compare(run_gpu(depth, intr.as_tuple(), k, method, depth_type="u16"),
+            run_ref(depth, intr.as_tuple(), k, method), label="u16 k=%d %s" % (k, method))
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_wide_depth_range_k31(method):
+    """Depths 0.3-10 m, sigma 0.0015 Z^2, 31x31 windows."""
+    W, H = 480, 270
+    intr = scenes.Intrinsics.scaled(W, H, f640=525.0)
+    depth = scenes.wide_range_frame(scenes.BASE_SEED + 2, intr, W, H)
+    s = compare(run_gpu(depth, intr.as_tuple(), 31, method), run_ref(depth, intr.as_tuple(), 31, method),
+                label="wide k=31 " + method)
+    print(method, s)
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_noise_free_plane(method):
+    W, H = 160, 120
+    intr = scenes.Intrinsics(300.0, 310.0, 80.2, 59.7, 0.3, -0.2)
+    Z, pl = scenes.single_plane_frame(5, intr, W, H)
+    depth = scenes.to_f32_metres(Z)
+    n, d, c, cnt = run_gpu(depth, intr.as_tuple(), 5, method)
+    from parity import angle
+    assert np.max(angle(n, pl.n[None, None, :])) < 2e-4
+    assert np.max(np.abs(d - pl.d)) < 1e-4 * pl.d
+    assert np.max(c) < 1e-5
+
+
+def test_all_missing_and_flags():
+    W, H = 70, 50
+    intr = (525.0, 525.0, 34.5, 24.5, 0.0, 0.0)
+    depth = np.zeros((H, W), np.float32)
+    n, d, c, cnt = run_gpu(depth, intr, 5, "disparity")
+    assert np.all(np.isnan(d)) and np.all(cnt == 0)
+    depth = scenes.kinect_frame(3, scenes.Intrinsics.scaled(W, H), W, H, missing_iid=0.3)
+    for mv, rc in [(1, False), (10, True), (25, False)]:
+        compare(run_gpu(depth, intr, 5, "disparity", min_valid=mv, require_center=rc),
+                run_ref(depth, intr, 5, "disparity", min_valid=mv, require_center=rc), label="flags")
+
+
+def test_batched_frames_match_single():
+    W, H, k = 200, 120, 9
+    intr = scenes.Intrinsics.scaled(W, H)
+    frames = np.stack([scenes.kinect_frame(50 + i, intr, W, H) for i in range(5)])
+    f = SurfaceFitter(intr.as_tuple(), W, H, k)
+    nb, db, cb = f.fit(torch.from_numpy(frames).cuda())
+    for i in range(5):
+        n1, d1, c1 = f.fit(torch.from_numpy(frames[i]).cuda())
+        torch.cuda.synchronize()
+        assert torch.equal(torch.nan_to_num(nb[i], 7.0), torch.nan_to_num(n1, 7.0))
+        assert torch.equal(torch.nan_to_num(db[i], 7.0), torch.nan_to_num(d1, 7.0))
+    f.close()
+
+
+def test_host_api_matches_device():
+    W, H, k = 128, 96, 7
+    intr = scenes.Intrinsics.scaled(W, H)
+    frames = np.stack([scenes.kinect_frame(80 + i, intr, W, H) for i in range(3)])
+    f = SurfaceFitter(intr.as_tuple(), W, H, k)
+    nh, dh, ch, kh = f.fit_host(frames, counts=True)
+    nd, dd, cd, kd = f.fit(torch.from_numpy(frames).cuda(), counts=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(np.nan_to_num(nh, nan=7.0), np.nan_to_num(nd.cpu().numpy(), nan=7.0))
+    assert np.array_equal(kh, kd.cpu().numpy())
+    f.close()
