@@ -1,0 +1,343 @@
+"""Benchmark: dense RGBD plane fitting on GB300.
+
+One step = one pass of the whole hot path (fixed-point quantum, window
+moments, per-pixel solve) over the batch
+  8 x 1920x1080 + 2 x 4096x3072 float32 depth frames, 0.3-10 m,
+  sigma_Z = 0.0015 Z^2, 5 % missing, 31 x 31 windows, disparity form,
+with the inputs resident in HBM (167 MB of depth in, 834 MB of results out:
+both larger than the 129 MB L2, so no flush is needed between steps).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "Mpix plane-fits/s at 640x480 & 1080p, % HBM peak, vs plain fit on same GPU"
+UNIT = "Mpix/s"
+BYTES_PER_PIXEL = 24  # algorithmic: 4 B depth in + 12 B normal + 4 B offset + 4 B curvature out
+WORKLOAD = "8x1920x1080+2x4096x3072 f32 depth, 0.3-10 m, sigma 0.0015 Z^2, 5% missing, 31x31 windows, disparity form"
+K = 31
+
+
+def workload_frames():
+    """[(W, H, intrinsics, [frames])] of the benchmark batch (seeded, synthetic)."""
+    groups = []
+    for (W, H, n, seed0) in [(1920, 1080, 8, scenes.BASE_SEED + 300), (4096, 3072, 2, scenes.BASE_SEED + 400)]:
+        intr = scenes.Intrinsics.scaled(W, H)
+        frames = [scenes.wide_range_frame(seed0 + i, intr, W, H) for i in range(n)]
+        groups.append((W, H, intr, frames))
+    return groups
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        smi = shutil.which("nvidia-smi")
+        if smi:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen([smi, "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(time_budget_s: float = 15.0):
+    """Time the FP64 oracle on the benchmark's 1080p frames (bounded sample, ~10-30 s)."""
+    import oracle
+
+    W, H = 1920, 1080
+    intr = scenes.Intrinsics.scaled(W, H)
+    frames = [scenes.wide_range_frame(scenes.BASE_SEED + 300 + i, intr, W, H) for i in range(8)]
+    t0 = time.perf_counter()
+    oracle.fit(frames[0], intr.as_tuple(), K, "disparity")
+    dt0 = time.perf_counter() - t0
+    n = int(max(1, min(8, time_budget_s / max(dt0, 1e-3))))
+    t0 = time.perf_counter()
+    for f in frames[:n]:
+        oracle.fit(f, intr.as_tuple(), K, "disparity")
+    dt = time.perf_counter() - t0
+    px = n * W * H
+    return {"value": px / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d of the 8 1920x1080 frames of the benchmark batch (%d px), k=31, disparity form, "
+                      "FP64 direct window sums, OpenMP over rows" % (n, px), "seconds": dt}
+
+
+def run_single_case(args):
+    """One seeded 1920x1080 frame of the benchmark batch fitted --steps times (for ncu captures)."""
+    import torch
+
+    from paper_2103_06644_gb300 import SurfaceFitter
+
+    W, H = 1920, 1080
+    intr = scenes.Intrinsics.scaled(W, H)
+    d = torch.from_numpy(scenes.wide_range_frame(scenes.BASE_SEED + 300, intr, W, H)).cuda()
+    f = SurfaceFitter(intr.as_tuple(), W, H, K, method=args.method)
+    for _ in range(max(1, args.steps)):
+        f.fit(d)
+    torch.cuda.synchronize()
+    f.close()
+    print(json.dumps({"case": "single1080", "method": args.method, "fits": max(1, args.steps)}))
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    W, H = 1920, 1080
+    intr = scenes.Intrinsics.scaled(W, H)
+    frame = scenes.wide_range_frame(scenes.BASE_SEED + 300, intr, W, H)
+    rows = 24
+    band = frame[:rows + K - 1]
+    for _ in range(args.warmup):
+        oracle.fit(band[:K + 1], intr.as_tuple(), K, "disparity")
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.fit(band, intr.as_tuple(), K, "disparity")
+        times.append(time.perf_counter() - t0)
+    px = band.shape[0] * W
+    ms = 1000 * statistics.mean(times)
+    value = px / (ms / 1000) / 1e6
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "each step: rows 0-%d of one 1920x1080 frame" % (
+                band.shape[0] - 1)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "rows 0-%d of one 1920x1080 frame, k=31" % (band.shape[0] - 1)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="few steps, no extras (for ncu)")
+    ap.add_argument("--case", default=None, choices=["single1080"],
+                    help="small profiling case instead of the benchmark: one 1920x1080 frame, --steps fits")
+    ap.add_argument("--method", default="disparity", choices=["disparity", "standard"])
+    args = ap.parse_args()
+    if args.case == "single1080":
+        run_single_case(args)
+        return
+    args.warmup = max(args.warmup, 3) if not args.profile_only else args.warmup
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2103_06644_gb300 import SurfaceFitter
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    groups = workload_frames()
+    fitters, inputs, outputs = [], [], []
+    total_px = 0
+    for (W, H, intr, frames) in groups:
+        f = SurfaceFitter(intr.as_tuple(), W, H, K, method="disparity")
+        d = torch.from_numpy(np.stack(frames)).to(dev)
+        n = len(frames)
+        out = (torch.empty((n, H, W, 3), device=dev), torch.empty((n, H, W), device=dev),
+               torch.empty((n, H, W), device=dev))
+        fitters.append(f)
+        inputs.append(d)
+        outputs.append(out)
+        total_px += n * W * H
+
+    def step(fs=fitters):
+        for f, d, o in zip(fs, inputs, outputs):
+            f.fit(d, out=o)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(nsteps, fn):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(nsteps):
+            fn()
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1) / nsteps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    for f in fitters:
+        f.profile(True)
+    sampler = ClockSampler(local)
+    ms = timed(args.steps, step)
+    clocks = sampler.stop()
+    prof = {}
+    for f in fitters:
+        for stage, (t, n) in f.profile_read().items():
+            a = prof.setdefault(stage, [0.0, 0, 0])
+            a[0] += t
+            a[1] += n
+        f.profile(False)
+    # pixels processed per launch of each stage (every launch covers a whole group)
+    px_per_launch = {}
+    value = world * total_px / (ms / 1000.0) / 1e6
+    peak, peak_kind = load_peaks()
+    dom = max(prof, key=lambda s: prof[s][0])
+    dom_ms, dom_n = prof[dom][0], prof[dom][1]
+    launches_per_step = sum(v[1] for v in prof.values()) / max(1, args.steps)
+    dom_avg_ms = dom_ms / max(1, dom_n)
+    px_per_dom_launch = total_px * args.steps / max(1, dom_n)
+    achieved = BYTES_PER_PIXEL * px_per_dom_launch / (dom_avg_ms / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": 10, "pixels_per_step_per_gpu": total_px, "window": K,
+                   "l2": "inputs (167 MB) and outputs (834 MB) larger than L2; no flush"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_pixel": BYTES_PER_PIXEL,
+                     "stage_ms_per_step": {s: v[0] / args.steps for s, v in prof.items()}},
+        "path_hbm_frac": BYTES_PER_PIXEL * total_px / (ms / 1000.0) / 1e9 / peak,
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "clocks": clocks,
+    }
+    if not args.profile_only:
+        # the plain (standard) algebraic fit on the same batch and GPU
+        std = []
+        for (W, H, intr, frames) in groups:
+            std.append(SurfaceFitter(intr.as_tuple(), W, H, K, method="standard"))
+        for _ in range(3):
+            step(std)
+        ms_std = timed(max(3, args.steps // 2), lambda: step(std))
+        line["standard_fit"] = {"value": world * total_px / (ms_std / 1000.0) / 1e6, "unit": UNIT,
+                                "ms_per_step": ms_std, "speedup_of_disparity_form": ms_std / ms}
+        for f in std:
+            f.close()
+        # 640x480, 7x7: the small single-frame case (launch-bound)
+        intr = scenes.Intrinsics(525.0, 525.0, 319.5, 239.5)
+        vga = torch.from_numpy(scenes.kinect_frame(scenes.BASE_SEED, intr, 640, 480)).to(dev)
+        vres = {}
+        for method in ("disparity", "standard"):
+            fv = SurfaceFitter(intr.as_tuple(), 640, 480, 7, method=method)
+            ov = (torch.empty((480, 640, 3), device=dev), torch.empty((480, 640), device=dev),
+                  torch.empty((480, 640), device=dev))
+            for _ in range(5):
+                fv.fit(vga, out=ov)
+            t = timed(50, lambda: fv.fit(vga, out=ov))
+            vres[method] = {"us_per_frame": 1000 * t, "value": 307200 / (t / 1000) / 1e6, "unit": UNIT}
+            fv.close()
+        line["vga_k7"] = vres
+    if not args.no_e2e and not args.profile_only:
+        host = [np.stack(frames) for (_, _, _, frames) in groups]
+        for f, h in zip(fitters, host):
+            f.fit_host(h)  # allocate staging
+        barrier()
+        ne = 3
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            for f, h in zip(fitters, host):
+                f.fit_host(h)
+        dt = (time.perf_counter() - t0) / ne
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        line["e2e"] = {"value": world * total_px / dt / 1e6, "unit": UNIT,
+                       "h2d_bytes_per_step": int(sum(h.nbytes for h in host)),
+                       "d2h_bytes_per_step": int(20 * total_px), "ms_per_step": 1000 * dt,
+                       "api": "sf_fit_host (host buffers, copies inside the call)"}
+    if rank == 0 and world == 1 and not args.no_cpu and not args.profile_only:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for f in fitters:
+        f.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

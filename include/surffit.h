@@ -148,6 +148,20 @@ const char* sf_last_error(void);
  */
 sf_status sf_channel_counts(int method, int* depth_channels, int* mask_channels);
 
+/*
+ * sf_profile_enable / sf_profile_read -- per-stage CUDA-event timing of the
+ * context's own launches, for benchmarks.  While enabled, every kernel launch
+ * of the context is bracketed by two events on its stream.  sf_profile_read
+ * waits for the recorded events, writes for each stage s < n_stages the
+ * summed milliseconds ms[s] and the launch count launches[s], and clears the
+ * record.  Stages: 0 range (quantum), 1 horizontal moments, 2 vertical
+ * moments + solve.  Enabling again clears the record.
+ */
+sf_status sf_profile_enable(sf_ctx* ctx, int on);
+sf_status sf_profile_read(sf_ctx* ctx, int n_stages, double* ms, int* launches);
+
+#define SF_NUM_STAGES 3
+
 /* Library version as a static string. */
 const char* sf_version(void);
 

@@ -120,6 +120,20 @@ class SurfaceFitter:
                                                 curv.ctypes.data, cnt.ctypes.data if cnt is not None else None, None))
         return (normals, offsets, curv, cnt) if counts else (normals, offsets, curv)
 
+    # -- profiling (CUDA events around the library's own launches) ---------------
+    STAGES = ("range", "hpass", "vpass_solve")
+
+    def profile(self, on: bool = True) -> None:
+        _native.check(_native.lib().sf_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self):
+        """{stage: (total ms, launches)} since profiling was enabled; clears the record."""
+        n = len(self.STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int * n)()
+        _native.check(_native.lib().sf_profile_read(self._h, n, ms, cnt))
+        return {s: (ms[i], cnt[i]) for i, s in enumerate(self.STAGES)}
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             _native.lib().sf_destroy(self._h)

@@ -42,6 +42,8 @@ SIGNATURES = {
     "sf_last_error": (ctypes.c_char_p, []),
     "sf_channel_counts": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "sf_version": (ctypes.c_char_p, []),
+    "sf_profile_enable": (_I, [_VP, _I]),
+    "sf_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)]),
 }
 
 

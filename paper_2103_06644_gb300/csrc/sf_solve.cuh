@@ -28,23 +28,22 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return y;
 }
 
-// Cross product of the two rows of (R - l I) with the largest norm: it spans
-// the null space of R - l I, i.e. the eigenvector of eigenvalue l.
+// Null vector of the symmetric matrix M = R - l I: the column of the
+// cofactor matrix adj(M) with the largest norm (each column is a cross
+// product of two rows of M, and adj(M) = det(M) M^{-1} is dominated by the
+// eigenvector of the eigenvalue nearest l).
 __device__ __forceinline__ void null_vector(float r11, float r12, float r13, float r22, float r23, float r33, float l,
                                             float& v0, float& v1, float& v2) {
     const float a11 = r11 - l, a22 = r22 - l, a33 = r33 - l;
-    // rows: m1 = (a11, r12, r13), m2 = (r12, a22, r23), m3 = (r13, r23, a33)
-    const float c0 = r12 * r23 - r13 * a22, c1 = r13 * r12 - a11 * r23, c2 = a11 * a22 - r12 * r12;  // m1 x m2
-    const float e0 = r12 * a33 - r13 * r23, e1 = r13 * r13 - a11 * a33, e2 = a11 * r23 - r12 * r13;  // m1 x m3
-    const float f0 = a22 * a33 - r23 * r23, f1 = r23 * r13 - r12 * a33, f2 = r12 * r23 - a22 * r13;  // m2 x m3
-    const float nc = c0 * c0 + c1 * c1 + c2 * c2;
-    const float ne = e0 * e0 + e1 * e1 + e2 * e2;
-    const float nf = f0 * f0 + f1 * f1 + f2 * f2;
-    float b0 = c0, b1 = c1, b2 = c2, nb = nc;
-    if (ne > nb) { b0 = e0; b1 = e1; b2 = e2; nb = ne; }
-    if (nf > nb) { b0 = f0; b1 = f1; b2 = f2; nb = nf; }
+    const float c11 = a22 * a33 - r23 * r23, c22 = a11 * a33 - r13 * r13, c33 = a11 * a22 - r12 * r12;
+    const float c12 = r13 * r23 - r12 * a33, c13 = r12 * r23 - r13 * a22, c23 = r12 * r13 - a11 * r23;
+    const float n1 = c11 * c11 + c12 * c12 + c13 * c13;
+    const float n2 = c12 * c12 + c22 * c22 + c23 * c23;
+    const float n3 = c13 * c13 + c23 * c23 + c33 * c33;
+    float b0 = c11, b1 = c12, b2 = c13, nb = n1;
+    if (n2 > nb) { b0 = c12; b1 = c22; b2 = c23; nb = n2; }
+    if (n3 > nb) { b0 = c13; b1 = c23; b2 = c33; nb = n3; }
     if (!(nb > 1e-36f)) {  // l is (numerically) a double root: any unit vector of the null space
-        // fall back to the coordinate axis of the smallest diagonal entry of R - l I
         b0 = 0.f; b1 = 0.f; b2 = 0.f;
         if (a11 <= a22 && a11 <= a33) b0 = 1.f; else if (a22 <= a33) b1 = 1.f; else b2 = 1.f;
         nb = 1.f;
@@ -54,11 +53,14 @@ __device__ __forceinline__ void null_vector(float r11, float r12, float r13, flo
 }
 
 // Smallest eigenpair of a symmetric positive semi-definite 3x3 matrix R
-// (upper triangle r11..r33).  Eigenvalues by the trigonometric solution of the
-// characteristic cubic (Smith, CACM 4(4):168, 1961), the eigenvector as a
-// cross product of rows of R - lambda I, then one Rayleigh-quotient
-// refinement of lambda and a second cross product.  Returns the normalised
-// eigenvalues (trace scaled to 1) through l0 / gap.
+// (upper triangle r11..r33), scaled to unit trace.
+//  1. lambda estimate: trigonometric solution of the characteristic cubic
+//     (Smith, CACM 4(4):168, 1961).  It stays accurate (~1e-6 absolute) when
+//     lambda0 and lambda1 cluster, where Newton's method on the cubic crawls.
+//  2. v = null vector of R - lambda I (cofactor column, above).
+//  3. Rayleigh quotient lr = v^T R v (insensitive to the cancellation in det R).
+//  4. one step of inverse iteration with shift lr: v <- adj(R - lr I) v.
+// The eigenvector error left is ~|dR| / (lambda1 - lambda0).
 __device__ __forceinline__ void smallest_eigpair(float r11, float r12, float r13, float r22, float r23, float r33,
                                                  float& v0, float& v1, float& v2, float& l0, float& gap) {
     const float tr = r11 + r22 + r33;
@@ -67,29 +69,40 @@ __device__ __forceinline__ void smallest_eigpair(float r11, float r12, float r13
     const float third = 0.33333333f;
     const float b11 = r11 - third, b22 = r22 - third, b33 = r33 - third;
     const float p2 = (b11 * b11 + b22 * b22 + b33 * b33 + 2.f * (r12 * r12 + r13 * r13 + r23 * r23)) * (1.f / 6.f);
-    float lmin, lmid, lmax;
-    if (p2 < 1e-20f) {
-        lmin = lmid = lmax = third;
-    } else {
+    float lmin = third, lmid = third, lmax = third;
+    if (p2 > 1e-20f) {
         const float p = sqrtf(p2);
         const float detB = b11 * (b22 * b33 - r23 * r23) - r12 * (r12 * b33 - r23 * r13) + r13 * (r12 * r23 - b22 * r13);
-        float q = 0.5f * detB / (p2 * p);
-        q = fminf(1.f, fmaxf(-1.f, q));
-        const float phi = acosf(q) * third;
+        const float q = fminf(1.f, fmaxf(-1.f, 0.5f * detB * rcp_approx(p2 * p)));
+        const float phi = acosf(q) * third;  // in [0, pi/3]
         float sn, cs;
-        sincosf(phi, &sn, &cs);
+        __sincosf(phi, &sn, &cs);
         lmax = third + 2.f * p * cs;
         lmin = third - p * (cs + 1.7320508f * sn);
         lmid = 1.f - lmax - lmin;
     }
     float a0, a1, a2;
     null_vector(r11, r12, r13, r22, r23, r33, lmin, a0, a1, a2);
-    // Rayleigh quotient a^T R a
     const float t0 = r11 * a0 + r12 * a1 + r13 * a2;
     const float t1 = r12 * a0 + r22 * a1 + r23 * a2;
     const float t2 = r13 * a0 + r23 * a1 + r33 * a2;
     const float lr = a0 * t0 + a1 * t1 + a2 * t2;
-    null_vector(r11, r12, r13, r22, r23, r33, lr, v0, v1, v2);
+    // inverse iteration: w = adj(R - lr I) a
+    {
+        const float c11 = (r22 - lr) * (r33 - lr) - r23 * r23, c22 = (r11 - lr) * (r33 - lr) - r13 * r13;
+        const float c33 = (r11 - lr) * (r22 - lr) - r12 * r12;
+        const float c12 = r13 * r23 - r12 * (r33 - lr), c13 = r12 * r23 - r13 * (r22 - lr);
+        const float c23 = r12 * r13 - (r11 - lr) * r23;
+        const float w0 = c11 * a0 + c12 * a1 + c13 * a2;
+        const float w1 = c12 * a0 + c22 * a1 + c23 * a2;
+        const float w2 = c13 * a0 + c23 * a1 + c33 * a2;
+        const float nw = w0 * w0 + w1 * w1 + w2 * w2;
+        if (nw > 1e-36f) {
+            const float q = rsqrt_approx(nw);
+            a0 = w0 * q; a1 = w1 * q; a2 = w2 * q;
+        }
+    }
+    v0 = a0; v1 = a1; v2 = a2;
     l0 = fmaxf(lr, 0.f);
     gap = (lmax > 0.f) ? (lmid - lmin) / lmax : 0.f;
 }
@@ -119,25 +132,26 @@ __device__ __forceinline__ void orient(float& nx, float& ny, float& nz, float& d
 //   Y = sum y y^T over y = [j - jhat, i - ihat, (what - w)/what],
 // and every entry of Y follows from the centred integer moments below.
 // The offset is d = -(n . mhat) / what.
-__device__ __forceinline__ FitOut solve_disparity(int n, int Sj, int Si, int Sjj, int Sji, int Sii, int64_t Sw,
-                                                  int64_t Swj, int64_t Swi, int64_t Sww, float qw, float tx, float ty,
-                                                  float a, float b) {
-    const float nf = (float)n;
+__device__ __forceinline__ FitOut solve_disparity(float nf, float fSj, float fSi, float fSjj, float fSji, float fSii,
+                                                  int64_t Sw, int64_t Swj, int64_t Swi, int64_t Sww, float qw, float tx,
+                                                  float ty, float a, float b) {
+    // the mask moments are exact integers held in float32 (all < 2^24)
     const float inv_n = rcp_approx(nf);
-    // exact re-centring on an integer near the mean disparity
-    const int64_t m = (int64_t)rintf((float)Sw * inv_n);
+    const int n = (int)nf, Sj = (int)fSj, Si = (int)fSi;
+    // exact re-centring on an integer m near the mean disparity (m < 2^31)
+    const int m = __float2int_rn((float)Sw * inv_n);
     const int64_t T0 = Sw - (int64_t)n * m;
-    const int64_t Tww = Sww - 2 * m * Sw + (int64_t)n * m * m;  // sum (w - m)^2
-    const int64_t Twj = Swj - m * (int64_t)Sj;                   // sum (w - m) j
-    const int64_t Twi = Swi - m * (int64_t)Si;                   // sum (w - m) i
-    const float fT0 = (float)T0;
+    const int64_t Tww = Sww - (int64_t)m * (Sw + T0);            // sum (w - m)^2
+    const int64_t Twj = Swj - (int64_t)m * Sj;                   // sum (w - m) j
+    const int64_t Twi = Swi - (int64_t)m * Si;                   // sum (w - m) i
+    const float fT0 = (float)(int)T0;                            // |T0| < 2^31
     const float t0 = fT0 * inv_n;
-    const float jb = (float)Sj * inv_n, ib = (float)Si * inv_n;
-    const float Cjj = (float)Sjj - (float)Sj * jb;
-    const float Cji = (float)Sji - (float)Sj * ib;
-    const float Cii = (float)Sii - (float)Si * ib;
-    const float Cjw = (float)Twj - (float)Sj * t0;
-    const float Ciw = (float)Twi - (float)Si * t0;
+    const float jb = fSj * inv_n, ib = fSi * inv_n;
+    const float Cjj = fSjj - fSj * jb;
+    const float Cji = fSji - fSj * ib;
+    const float Cii = fSii - fSi * ib;
+    const float Cjw = (float)Twj - fSj * t0;
+    const float Ciw = (float)Twi - fSi * t0;
     const float Cww = (float)Tww - fT0 * t0;
     const float wbar = (float)m + t0;  // mean disparity (units of qw)
     const float inv_nw = rcp_approx(nf * wbar);
@@ -175,19 +189,19 @@ __device__ __forceinline__ FitOut solve_disparity(int n, int Sj, int Si, int Sjj
 // P_q = Z_q m_q = T [Z j, Z i, Z] with T = [[a, 0, tx], [0, b, ty], [0, 0, 1]],
 // so the covariance of the points is T C T^T, C the covariance of
 // [z j, z i, z] (re-centred on an integer near the mean depth first).
-__device__ __forceinline__ FitOut solve_standard(int n, int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
+__device__ __forceinline__ FitOut solve_standard(float nf, int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
                                                  int64_t Szzj, int64_t Szzi, int64_t Szzjj, int64_t Szzji,
                                                  int64_t Szzii, float qz, float tx, float ty, float a, float b) {
-    const float nf = (float)n;
     const float inv_n = rcp_approx(nf);
-    const int64_t m = (int64_t)rintf((float)Sz * inv_n);
+    const int n = (int)nf;
+    const int m = __float2int_rn((float)Sz * inv_n);            // m < 2^31
     const int64_t T0 = Sz - (int64_t)n * m;
-    const int64_t Tzz = Szz - 2 * m * Sz + (int64_t)n * m * m;  // sum (z - m)^2
-    const int64_t Tzj = Szzj - m * Szj;                         // sum z j (z - m)
-    const int64_t Tzi = Szzi - m * Szi;                         // sum z i (z - m)
-    const float t0 = (float)T0 * inv_n;                         // zbar - m
+    const int64_t Tzz = Szz - (int64_t)m * (Sz + T0);           // sum (z - m)^2
+    const int64_t Tzj = Szzj - (int64_t)m * Szj;                // sum z j (z - m)
+    const int64_t Tzi = Szzi - (int64_t)m * Szi;                // sum z i (z - m)
+    const float t0 = (float)(int)T0 * inv_n;                    // zbar - m
     const float fSzj = (float)Szj, fSzi = (float)Szi;
-    const float Czz = (float)Tzz - (float)T0 * t0;
+    const float Czz = (float)Tzz - (float)(int)T0 * t0;
     const float Cjz = (float)Tzj - fSzj * t0;
     const float Ciz = (float)Tzi - fSzi * t0;
     const float qj = fSzj * inv_n, qi = fSzi * inv_n;           // means of z j, z i

@@ -28,6 +28,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "surffit.h"
 #include "sf_solve.cuh"
@@ -38,7 +39,6 @@ constexpr int kMaxR = (SF_MAX_WINDOW - 1) / 2;
 constexpr int kHThreads = 128;   // rows per hpass block
 constexpr int kHSeg = 64;        // output columns per hpass thread
 constexpr int kVThreads = 128;   // columns per vpass block
-constexpr int kVBand = 64;       // output rows per vpass thread
 
 // ---------------------------------------------------------------------------
 // Depth decoding.
@@ -177,6 +177,7 @@ __device__ __forceinline__ void unpack_mask(int32_t v, int& h0, int& h1, int& h2
 // (out leaves at j = -r, in enters at j = r + 1; S1 on the right is the old one).
 template <typename T>
 __device__ __forceinline__ void slide3(T& S0, T& S1, T& S2, T out, T in, int r) {
+    // exact for integers, and for float32 while every value stays below 2^24
     const T n0 = S0 - out + in;
     const T n1 = S1 + (T)r * out + (T)(r + 1) * in - n0;
     const T n2 = S2 - (T)(r * (r + 2)) * out + (T)((r + 1) * (r - 1)) * in - 2 * S1 + n0;
@@ -207,12 +208,18 @@ __global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict
     const float sc = ldexpf(1.f, quant_exponent(vmax_bits[f], bits));  // 2^e, exact
     const size_t fbase = (size_t)f * W * H;
     const int rows = min(kHThreads, H - y0);
-    for (int idx = threadIdx.x; idx < rows * IW; idx += kHThreads) {
-        const int ry = idx / IW, cx = idx - ry * IW;
-        const int x = x0 - r + cx, y = y0 + ry;
-        int v = -1;
-        if (x >= 0 && x < W) v = quantize<DT, M>(depth, fbase + (size_t)y * W + x, sc);
-        tile[ry * pitch + cx] = v;
+    {
+        // warp w loads rows w, w + 4, ...; lanes sweep the row (coalesced)
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int ry = warp; ry < rows; ry += kHThreads / 32) {
+            const size_t rbase = fbase + (size_t)(y0 + ry) * W;
+            for (int cx = lane; cx < IW; cx += 32) {
+                const int x = x0 - r + cx;
+                int v = -1;
+                if (x >= 0 && x < W) v = quantize<DT, M>(depth, rbase + x, sc);
+                tile[ry * pitch + cx] = v;
+            }
+        }
     }
     __syncthreads();
     if ((int)threadIdx.x >= rows) return;
@@ -236,31 +243,59 @@ __global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict
         }
     }
     const Planes P(planes_base, gridDim.z, plane_elems);
-    for (int x = x0; x < xend; ++x) {
-        const size_t o = obase + x;
-        if (M == SF_METHOD_DISPARITY) {
-            P.p32[o] = pack_mask(h0, h1, h2);
-            P.c64(0)[o] = a0; P.c64(1)[o] = a1; P.c64(2)[o] = s0;
-        } else {
-            P.p32[o] = h0;
-            P.c64(0)[o] = a0; P.c64(1)[o] = a1; P.c64(2)[o] = s0; P.c64(3)[o] = s1; P.c64(4)[o] = s2;
+    for (int xb = x0; xb < xend; xb += 4) {
+        int32_t hmv[4];
+        int64_t c0v[4], c1v[4], c2v[4], c3v[4], c4v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int x = xb + u;
+            if (M == SF_METHOD_DISPARITY) hmv[u] = pack_mask(h0, h1, h2);
+            else hmv[u] = h0;
+            c0v[u] = a0; c1v[u] = a1; c2v[u] = s0; c3v[u] = s1; c4v[u] = s2;
+            if (x + 1 < xend) {
+                const int vo = row[x - x0];              // column x - r leaves
+                const int vi = row[x - x0 + 2 * r + 1];  // column x + r + 1 enters
+                const int mo = vo >= 0, mi = vi >= 0;
+                slide3(h0, h1, h2, mo, mi, r);
+                const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
+                slide2(a0, a1, co, ci, r);
+                const int64_t qo = co * co, qi = ci * ci;
+                if (M == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
+                else s0 = s0 - qo + qi;
+            }
         }
-        if (x + 1 < xend) {
-            const int vo = row[x - x0];              // column x - r leaves
-            const int vi = row[x - x0 + 2 * r + 1];  // column x + r + 1 enters
-            const int mo = vo >= 0, mi = vi >= 0;
-            slide3(h0, h1, h2, mo, mi, r);
-            const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
-            slide2(a0, a1, co, ci, r);
-            const int64_t qo = co * co, qi = ci * ci;
-            if (M == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
-            else s0 = s0 - qo + qi;
+        const size_t o = obase + xb;
+        if (xb + 4 <= xend) {
+            *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
+            int64_t* c0 = P.c64(0) + o;
+            int64_t* c1 = P.c64(1) + o;
+            int64_t* c2 = P.c64(2) + o;
+            *reinterpret_cast<longlong2*>(c0) = make_longlong2(c0v[0], c0v[1]);
+            *reinterpret_cast<longlong2*>(c0 + 2) = make_longlong2(c0v[2], c0v[3]);
+            *reinterpret_cast<longlong2*>(c1) = make_longlong2(c1v[0], c1v[1]);
+            *reinterpret_cast<longlong2*>(c1 + 2) = make_longlong2(c1v[2], c1v[3]);
+            *reinterpret_cast<longlong2*>(c2) = make_longlong2(c2v[0], c2v[1]);
+            *reinterpret_cast<longlong2*>(c2 + 2) = make_longlong2(c2v[2], c2v[3]);
+            if (M == SF_METHOD_STANDARD) {
+                int64_t* c3 = P.c64(3) + o;
+                int64_t* c4 = P.c64(4) + o;
+                *reinterpret_cast<longlong2*>(c3) = make_longlong2(c3v[0], c3v[1]);
+                *reinterpret_cast<longlong2*>(c3 + 2) = make_longlong2(c3v[2], c3v[3]);
+                *reinterpret_cast<longlong2*>(c4) = make_longlong2(c4v[0], c4v[1]);
+                *reinterpret_cast<longlong2*>(c4 + 2) = make_longlong2(c4v[2], c4v[3]);
+            }
+        } else {
+            for (int u = 0; u < 4 && xb + u < xend; ++u) {
+                P.p32[o + u] = hmv[u];
+                P.c64(0)[o + u] = c0v[u]; P.c64(1)[o + u] = c1v[u]; P.c64(2)[o + u] = c2v[u];
+                if (M == SF_METHOD_STANDARD) { P.c64(3)[o + u] = c3v[u]; P.c64(4)[o + u] = c4v[u]; }
+            }
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// 3. vpass + solve: one thread per column, band of kVBand output rows.
+// 3. vpass + solve: one thread per column, band of `band` output rows.
 // ---------------------------------------------------------------------------
 struct Calib {
     const float* tx;  // [W] ray tangent per column
@@ -273,14 +308,14 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
                                                           float scale, const unsigned* __restrict__ vmax_bits,
                                                           int bits, int raw_z, int Wp, size_t plane_elems,
                                                           void* __restrict__ planes_base, Calib cal,
-                                                          int min_valid, int require_center, float* __restrict__ normals,
-                                                          float* __restrict__ offsets, float* __restrict__ curvature,
-                                                          int32_t* __restrict__ counts) {
+                                                          int min_valid, int require_center, int band,
+                                                          float* __restrict__ normals, float* __restrict__ offsets,
+                                                          float* __restrict__ curvature, int32_t* __restrict__ counts) {
     const int f = blockIdx.z;
     const int x = blockIdx.x * kVThreads + threadIdx.x;
     if (x >= W) return;
-    const int y0 = blockIdx.y * kVBand;
-    const int y1 = min(y0 + kVBand, H);
+    const int y0 = blockIdx.y * band;
+    const int y1 = min(y0 + band, H);
     const size_t nf = gridDim.z;
     const size_t pb = (size_t)f * plane_elems + x;
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);  // metric value of one fixed-point unit
@@ -293,7 +328,8 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
         const int64_t* g0 = P.c64(0);
         const int64_t* g1 = P.c64(1);
         const int64_t* q0 = P.c64(2);
-        int n = 0, Sj = 0, Sjj = 0, Si = 0, Sji = 0, Sii = 0;
+        // mask moments: exact small integers, kept in float32 (all < 2^24)
+        float n = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;
         int64_t Sw = 0, Swj = 0, Swi = 0, Sww = 0;
         for (int yy = y0 - r; yy <= y0 + r; ++yy) {
             if (yy < 0 || yy >= H) continue;
@@ -301,14 +337,15 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
             int c0, c1, c2;
             unpack_mask(__ldg(hm + o), c0, c1, c2);
             const int i = yy - y0;
-            n += c0; Sj += c1; Sjj += c2; Si += i * c0; Sji += i * c1; Sii += i * i * c0;
+            const float f0 = (float)c0, f1 = (float)c1, fi = (float)i;
+            n += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
             const int64_t w0 = __ldg(g0 + o);
             Sw += w0; Swj += __ldg(g1 + o); Swi += (int64_t)i * w0; Sww += __ldg(q0 + o);
         }
         for (int y = y0; y < y1; ++y) {
             const size_t oi = fo + (size_t)y * W + x;
             const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
-            const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
+            const bool ok = n >= (float)min_valid && n > 0.f && (cvalid || !require_center);
             float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
             if (ok) {
                 const FitOut fo_ = solve_disparity(n, Sj, Si, Sjj, Sji, Sii, Sw, Swj, Swi, Sww, q, tx, cal.ty[y],
@@ -317,7 +354,7 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
             }
             normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
             offsets[oi] = d; curvature[oi] = cu;
-            if (counts) counts[oi] = n;
+            if (counts) counts[oi] = (int)n;
             if (y + 1 < y1) {
                 const int yo = y - r, yi = y + r + 1;
                 int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
@@ -333,9 +370,9 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
                     wi = __ldg(g0 + o); wji = __ldg(g1 + o); wwi = __ldg(q0 + o);
                 }
                 // vertical moments: (n, Si, Sii) from the counts, (Sj, Sji) from sum j, Sjj plain
-                slide3(n, Si, Sii, o0, i0, r);
-                slide2(Sj, Sji, o1, i1, r);
-                Sjj += i2 - o2;
+                slide3(n, Si, Sii, (float)o0, (float)i0, r);
+                slide2(Sj, Sji, (float)o1, (float)i1, r);
+                Sjj += (float)(i2 - o2);
                 slide2(Sw, Swi, wo, wi, r);
                 Swj += wji - wjo;
                 Sww += wwi - wwo;
@@ -349,7 +386,7 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
         const int64_t* b0 = P.c64(2);
         const int64_t* b1 = P.c64(3);
         const int64_t* b2 = P.c64(4);
-        int n = 0;
+        int n = 0;  // window count
         int64_t Sz = 0, Szi = 0, Szj = 0, Szz = 0, Szzi = 0, Szzii = 0, Szzj = 0, Szzji = 0, Szzjj = 0;
         for (int yy = y0 - r; yy <= y0 + r; ++yy) {
             if (yy < 0 || yy >= H) continue;
@@ -367,7 +404,7 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
             const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
             float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
             if (ok) {
-                const FitOut fo_ = solve_standard(n, Sz, Szj, Szi, Szz, Szzj, Szzi, Szzjj, Szzji, Szzii, q, tx,
+                const FitOut fo_ = solve_standard((float)n, Sz, Szj, Szi, Szz, Szzj, Szzi, Szzjj, Szzji, Szzii, q, tx,
                                                   cal.ty[y], cal.a, cal.b);
                 nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
             }
@@ -473,7 +510,39 @@ struct sf_ctx {
     size_t h_stage_bytes = 0;
     void* d_io = nullptr;
     size_t d_io_bytes = 0;
+    // profiling: (stage, start event, stop event) per recorded launch
+    bool profiling = false;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> event_pool;
 };
+
+namespace {
+cudaEvent_t take_event(sf_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+// Bracket one launch with events when profiling is on.
+struct StageTimer {
+    sf_ctx* c; int stage; cudaStream_t st; cudaEvent_t a = nullptr;
+    StageTimer(sf_ctx* c_, int s_, cudaStream_t st_) : c(c_), stage(s_), st(st_) {
+        if (c->profiling) { a = take_event(c); cudaEventRecord(a, st); }
+    }
+    ~StageTimer() {
+        if (a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, st);
+            c->recs.push_back({stage, a, b});
+        }
+    }
+};
+}  // namespace
 
 static sf_status ensure_planes(sf_ctx* c, int frames) {
     const size_t need = plane_bytes_per_frame(SF_METHOD_STANDARD, c->plane_elems) * (size_t)frames;
@@ -498,11 +567,13 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
     const int bits = quant_bits(M, c->k);
     SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
     if (!raw_z) {
+        StageTimer t(c, 0, st);
         int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
         blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
         sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, c->depth_scale, c->vmax);
     }
     {
+        StageTimer t(c, 1, st);
         dim3 grid((c->W + sf::kHSeg - 1) / sf::kHSeg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
         const int IW = sf::kHSeg + 2 * c->r;
         const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
@@ -510,12 +581,18 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
                                                                   bits, raw_z, c->Wp, c->plane_elems, c->planes);
     }
     {
-        dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + sf::kVBand - 1) / sf::kVBand, nfr);
+        StageTimer t(c, 2, st);
+        // band height: long bands amortise the 2r-row warm-up; short bands give
+        // enough threads to fill the GPU (target >= 24 warps per SM).
+        const size_t cols = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * sf::kVThreads * nfr;
+        int band = 256;
+        while (band > 16 && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 24 * 32) band /= 2;
+        dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
         sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
         sf::vpass_kernel<DT, M><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
                                                                bits, raw_z, c->Wp, c->plane_elems, c->planes, cal,
-                                                               c->min_valid, c->require_center, normals, offsets,
-                                                               curv, counts);
+                                                               c->min_valid, c->require_center, band, normals,
+                                                               offsets, curv, counts);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -573,11 +650,9 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
     if (e == cudaSuccess) e = cudaMemcpy(c->ty, hty, sizeof(float) * H, cudaMemcpyHostToDevice);
     free(htx); free(hty);
     if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create tables"); }
-    // Frames per pass: keep the scratch moments (<= 36 B/px) near 48 MB so
-    // that they stay resident in L2 between the two passes.
-    const size_t per = plane_bytes_per_frame(SF_METHOD_STANDARD, c->plane_elems);
-    c->max_frames_per_pass = (int)std::max<size_t>(1, ((size_t)48 << 20) / per);
-    if (c->max_frames_per_pass > 64) c->max_frames_per_pass = 64;
+    // Frames per pass: every frame of a call in one launch (up to 64), so the
+    // grid fills the GPU; the scratch moments are sized for them on demand.
+    c->max_frames_per_pass = 64;
     e = cudaMalloc(&c->vmax, sizeof(unsigned) * 64);
     if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create vmax"); }
     sf_status s = ensure_planes(c, 1);
@@ -700,8 +775,35 @@ sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals
     return SF_OK;
 }
 
+sf_status sf_profile_enable(sf_ctx* c, int on) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    for (auto& r : c->recs) { c->event_pool.push_back(r.a); c->event_pool.push_back(r.b); }
+    c->recs.clear();
+    c->profiling = on != 0;
+    return SF_OK;
+}
+
+sf_status sf_profile_read(sf_ctx* c, int n_stages, double* ms, int* launches) {
+    if (!c || n_stages < 0 || (n_stages > 0 && (!ms || !launches)))
+        return fail(SF_ERR_INVALID_ARG, "bad profile_read arguments");
+    for (int s = 0; s < n_stages; ++s) { ms[s] = 0.0; launches[s] = 0; }
+    for (auto& r : c->recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "profile event");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, r.a, r.b);
+        if (r.stage < n_stages) { ms[r.stage] += t; launches[r.stage] += 1; }
+        c->event_pool.push_back(r.a);
+        c->event_pool.push_back(r.b);
+    }
+    c->recs.clear();
+    return SF_OK;
+}
+
 sf_status sf_destroy(sf_ctx* c) {
     if (!c) return SF_OK;
+    for (auto& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->tx) cudaFree(c->tx);
     if (c->ty) cudaFree(c->ty);
     if (c->vmax) cudaFree(c->vmax);
