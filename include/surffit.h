@@ -162,6 +162,36 @@ sf_status sf_profile_read(sf_ctx* ctx, int n_stages, double* ms, int* launches);
 
 #define SF_NUM_STAGES 3
 
+/*
+ * sf_fit_static -- the fit of sf_fit for one frame, without a context and
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate when they need a fit
+ * (work recorded while a CUDA graph is being captured, real-time loops that
+ * forbid allocator calls after start-up, hosts whose own allocator owns the
+ * GPU's memory).  Its scratch lives in one device array of
+ * SF_STATIC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   K, W, H, window          as for sf_create
+ *   method                   SF_METHOD_DISPARITY or SF_METHOD_STANDARD
+ *   depth_type, depth_scale, min_valid, require_center_valid   as for sf_set_params
+ *   depth, normals, offsets, curvature, stream                 as for sf_fit
+ * Limits and errors: the frame's scratch (about 28 B per pixel for the
+ * disparity form, 44 B for the standard form, plus the ray tables) must fit
+ * in SF_STATIC_SCRATCH_BYTES, e.g. 1280x720 disparity or 640x480 standard;
+ * larger frames are rejected with SF_ERR_INVALID_ARG and a message, before
+ * any device work.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) and sets kernel attributes; make that
+ * first call before any stream capture.  All calls on a device share the one
+ * array and it keeps the previous call's contents (the kernels clear what
+ * must start at zero), so calls whose work overlaps on the GPU -- on
+ * different streams, or from several host threads -- race and corrupt each
+ * other's results: serialise them.
+ */
+#define SF_STATIC_SCRATCH_BYTES (32u << 20)
+sf_status sf_fit_static(const sf_intrinsics* K, int W, int H, int window, int method, int depth_type,
+                        float depth_scale, int min_valid, int require_center_valid, const void* depth,
+                        float* normals, float* offsets, float* curvature, void* stream);
+
 /* Library version as a static string. */
 const char* sf_version(void);
 

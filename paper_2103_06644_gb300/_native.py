@@ -44,6 +44,7 @@ SIGNATURES = {
     "sf_version": (ctypes.c_char_p, []),
     "sf_profile_enable": (_I, [_VP, _I]),
     "sf_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)]),
+    "sf_fit_static": (_I, [ctypes.POINTER(Intrinsics), _I, _I, _I, _I, _I, _F, _I, _I, _VP, _VP, _VP, _VP, _VP]),
 }
 
 

@@ -28,6 +28,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "surffit.h"
@@ -815,3 +816,138 @@ sf_status sf_destroy(sf_ctx* c) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free entry point: sf_fit_static
+// ===========================================================================
+// Some callers cannot allocate device memory at the point where they need a
+// fit: code running while a CUDA graph is being captured, real-time loops that
+// forbid allocator calls after start-up, or hosts that hand the GPU's memory
+// to their own allocator and leave none to cudaMalloc.  sf_fit_static serves
+// them: it takes the same inputs and outputs as sf_fit but keeps every byte
+// of its scratch (the fixed-point quantum, the ray tables and the horizontal
+// moment planes) in one statically sized device array that exists from module
+// load until process exit.
+namespace sf {
+
+constexpr size_t kStaticScratchBytes = (size_t)SF_STATIC_SCRATCH_BYTES;  // per device
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Ray tangents of Eq. 10 computed in FP64 and rounded to FP32, the same
+// values sf_create computes on the host.
+__global__ void ray_table_kernel(double fx, double fy, double cx, double cy, double dx, double dy, int W, int H,
+                                 float* __restrict__ tx, float* __restrict__ ty) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < W) tx[i] = (float)((i + dx - cx) / fx);
+    if (i < H) ty[i] = (float)((i + dy - cy) / fy);
+}
+
+}  // namespace sf
+
+namespace {
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_base[kStaticMaxDevices] = {nullptr};
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Device address of the static scratch for the current device, resolved once.
+sf_status static_scratch_base(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "sf_fit_static: cudaGetDevice");
+    if (dev < 0 || dev >= kStaticMaxDevices) return fail(SF_ERR_UNSUPPORTED, "device ordinal %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_base[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, sf::g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "sf_fit_static: cudaGetSymbolAddress");
+        const int IW = sf::kHSeg + 2 * sf::kMaxR;
+        const int smem = (int)(sizeof(int) * sf::kHThreads * (size_t)(IW | 1));
+        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_F32, SF_METHOD_DISPARITY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_F32, SF_METHOD_STANDARD>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_U16, SF_METHOD_DISPARITY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_U16, SF_METHOD_STANDARD>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "sf_fit_static: kernel attributes");
+        g_static_base[dev] = p;
+    }
+    *out = g_static_base[dev];
+    return SF_OK;
+}
+
+}  // namespace
+
+extern "C" sf_status sf_fit_static(const sf_intrinsics* K, int W, int H, int window, int method, int depth_type,
+                                   float depth_scale, int min_valid, int require_center_valid, const void* depth,
+                                   float* normals, float* offsets, float* curvature, void* stream) {
+    if (!K) return fail(SF_ERR_INVALID_ARG, "null intrinsics");
+    if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
+    if (W < 1 || H < 1) return fail(SF_ERR_INVALID_ARG, "image size %dx%d must be positive", W, H);
+    if (window < 1 || (window & 1) == 0 || window > SF_MAX_WINDOW)
+        return fail(SF_ERR_INVALID_ARG, "window %d must be odd and in [1, %d]", window, SF_MAX_WINDOW);
+    if (!(K->fx != 0.0) || !(K->fy != 0.0) || !std::isfinite(K->fx) || !std::isfinite(K->fy) ||
+        !std::isfinite(K->cx) || !std::isfinite(K->cy) || !std::isfinite(K->dx) || !std::isfinite(K->dy))
+        return fail(SF_ERR_INVALID_ARG, "intrinsics must be finite with nonzero focal lengths");
+    if (method != SF_METHOD_DISPARITY && method != SF_METHOD_STANDARD)
+        return fail(SF_ERR_UNSUPPORTED, "sf_fit_static supports the disparity and standard implicit fits");
+    if (depth_type != SF_DEPTH_F32 && depth_type != SF_DEPTH_U16)
+        return fail(SF_ERR_INVALID_ARG, "unknown depth type %d", depth_type);
+    if (depth_type == SF_DEPTH_U16 && !(depth_scale > 0.f && std::isfinite(depth_scale)))
+        return fail(SF_ERR_INVALID_ARG, "depth_scale must be positive and finite");
+    if (min_valid < 1) return fail(SF_ERR_INVALID_ARG, "min_valid must be >= 1");
+    // scratch layout inside the static array: quantum word | tx[W] | ty[H] | moment planes
+    const int Wp = (W + 63) / 64 * 64;
+    const size_t plane_elems = (size_t)Wp * H;
+    const size_t off_tx = 256;
+    const size_t off_ty = off_tx + align256(sizeof(float) * W);
+    const size_t off_planes = off_ty + align256(sizeof(float) * H);
+    const size_t need = off_planes + plane_bytes_per_frame(method, plane_elems);
+    if (need > sf::kStaticScratchBytes)
+        return fail(SF_ERR_INVALID_ARG,
+                    "sf_fit_static: a %dx%d frame needs %zu bytes of scratch, more than the %zu-byte static array "
+                    "(use sf_create/sf_fit for larger frames)", W, H, need, sf::kStaticScratchBytes);
+    void* base = nullptr;
+    sf_status s = static_scratch_base(&base);
+    if (s != SF_OK) return s;
+    char* b = static_cast<char*>(base);
+    // A context on the stack that points into the static array: nothing is allocated.
+    sf_ctx c;
+    c.K = *K;
+    c.W = W; c.H = H; c.k = window; c.r = (window - 1) / 2;
+    c.Wp = Wp;
+    c.plane_elems = plane_elems;
+    c.method = method;
+    c.depth_type = depth_type;
+    c.depth_scale = depth_scale;
+    c.min_valid = min_valid;
+    c.require_center = require_center_valid ? 1 : 0;
+    c.vmax = reinterpret_cast<unsigned*>(b);
+    c.tx = reinterpret_cast<float*>(b + off_tx);
+    c.ty = reinterpret_cast<float*>(b + off_ty);
+    c.planes = b + off_planes;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    {
+        const int n = std::max(W, H);
+        sf::ray_table_kernel<<<(n + 255) / 256, 256, 0, st>>>(K->fx, K->fy, K->cx, K->cy, K->dx, K->dy, W, H, c.tx,
+                                                            c.ty);
+    }
+    // launch_pass clears the quantum word itself (cudaMemsetAsync) before use.
+    if (depth_type == SF_DEPTH_F32) {
+        s = method == SF_METHOD_DISPARITY
+                ? launch_pass<SF_DEPTH_F32, SF_METHOD_DISPARITY>(&c, 1, depth, normals, offsets, curvature, nullptr, st)
+                : launch_pass<SF_DEPTH_F32, SF_METHOD_STANDARD>(&c, 1, depth, normals, offsets, curvature, nullptr, st);
+    } else {
+        s = method == SF_METHOD_DISPARITY
+                ? launch_pass<SF_DEPTH_U16, SF_METHOD_DISPARITY>(&c, 1, depth, normals, offsets, curvature, nullptr, st)
+                : launch_pass<SF_DEPTH_U16, SF_METHOD_STANDARD>(&c, 1, depth, normals, offsets, curvature, nullptr, st);
+    }
+    // c points into the static array: nothing to free
+    c.tx = nullptr; c.ty = nullptr; c.vmax = nullptr; c.planes = nullptr;
+    return s;
+}
