@@ -310,6 +310,31 @@ def main():
             vres[method] = {"us_per_frame": 1000 * t, "value": 307200 / (t / 1000) / 1e6, "unit": UNIT}
             fv.close()
         line["vga_k7"] = vres
+        # differentiation: 16 x 640x480 f32, k=9, loss = sum |n - n*|^2 + 0.1 kappa over valid pixels;
+        # one step = forward + upstream gradient + backward to the depth
+        nd = 16
+        dd = torch.from_numpy(np.stack([scenes.kinect_frame(scenes.BASE_SEED + 600 + i, intr, 640, 480)
+                                        for i in range(nd)])).to(dev)
+        tgt = torch.from_numpy(np.stack([scenes.target_normals(scenes.BASE_SEED + 700 + i, 480, 640)
+                                         for i in range(nd)]).astype(np.float32)).to(dev)
+        fd = SurfaceFitter(intr.as_tuple(), 640, 480, 9, method="disparity")
+        zero = torch.zeros((nd, 480, 640), device=dev)
+
+        def diff_step():
+            n_, o_, c_ = fd.fit(dd)
+            valid = torch.isfinite(o_)
+            gn = torch.where(valid[..., None], 2.0 * (n_ - tgt), torch.zeros_like(n_))
+            gk = torch.where(valid, torch.full_like(c_, 0.1), torch.zeros_like(c_))
+            return fd.backward(dd, gn, zero, gk)
+
+        for _ in range(3):
+            diff_step()
+        t_fb = timed(20, diff_step)
+        t_f = timed(20, lambda: fd.fit(dd))
+        line["differentiation_k9"] = {"workload": "16x640x480 f32, k=9, loss |n-n*|^2 + 0.1 kappa",
+                                      "value": nd * 307200 / (t_fb / 1000) / 1e6, "unit": UNIT,
+                                      "ms_per_step_fwd_bwd": t_fb, "ms_forward": t_f}
+        fd.close()
     if not args.no_e2e and not args.profile_only:
         host = [np.stack(frames) for (_, _, _, frames) in groups]
         for f, h in zip(fitters, host):

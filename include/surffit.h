@@ -134,6 +134,26 @@ sf_status sf_fit_ex(sf_ctx* ctx, int n_frames, const void* depth, float* normals
 sf_status sf_fit_host(sf_ctx* ctx, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
                       int32_t* counts, void* stream);
 
+/*
+ * sf_fit_backward -- gradient of L = sum_p (g_normals_p . n_p + g_offsets_p d_p
+ * + g_curvature_p kappa_p) with respect to the depth, for the implicit fits
+ * (SF_METHOD_DISPARITY, SF_METHOD_STANDARD).  The fit is differentiated as the
+ * paper defines it: the Schur complement of the scatter matrix (Eq. 6 / Eq. 14
+ * with the offset eliminated), its smallest eigenvector (Eq. 4-5), the offset
+ * and the curvature; dL/dZ at a pixel collects the contributions of every
+ * window containing it.  Invalid windows contribute nothing; missing pixels
+ * get 0.  The normal's sign is treated as locally constant (the orientation
+ * rule), and the gradient is undefined where lambda0 == lambda1.
+ *   depth                      device, as for sf_fit_ex ([n_frames][H][W])
+ *   g_normals                  device float [n_frames][H][W][3] (NaN-free)
+ *   g_offsets, g_curvature     device float [n_frames][H][W]
+ *   g_depth                    device float [n_frames][H][W], out: dL/dZ with Z in metres
+ *                              (for uint16 input, times depth_scale gives dL/d(raw))
+ * Errors: SF_ERR_UNSUPPORTED for the explicit fits.  Asynchronous on `stream`.
+ */
+sf_status sf_fit_backward(sf_ctx* ctx, int n_frames, const void* depth, const float* g_normals, const float* g_offsets,
+                          const float* g_curvature, float* g_depth, void* stream);
+
 /* sf_destroy -- free the context and everything it owns (NULL is a no-op). */
 sf_status sf_destroy(sf_ctx* ctx);
 

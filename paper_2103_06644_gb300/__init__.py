@@ -104,6 +104,24 @@ class SurfaceFitter:
                                               _stream_handle(stream)))
         return (normals, offsets, curv, cnt) if counts else (normals, offsets, curv)
 
+    def backward(self, depth, g_normals, g_offsets, g_curvature, stream=None):
+        """dL/dZ [.., H, W] for L = sum(g_normals . n + g_offsets d + g_curvature kappa) (``sf_fit_backward``)."""
+        import torch
+
+        self._check_depth(depth)
+        n = depth.shape[0] if depth.dim() == 3 else 1
+        gn = torch.nan_to_num(g_normals.float()).contiguous()
+        gd = torch.nan_to_num(g_offsets.float()).contiguous()
+        gk = torch.nan_to_num(g_curvature.float()).contiguous()
+        g = torch.empty(depth.shape, dtype=torch.float32, device=depth.device)
+        _native.check(_native.lib().sf_fit_backward(self._h, n, depth.data_ptr(), gn.data_ptr(), gd.data_ptr(),
+                                                    gk.data_ptr(), g.data_ptr(), _stream_handle(stream)))
+        return g
+
+    def fit_differentiable(self, depth):
+        """(normals, offsets, curvature) with a backward to the float32 depth (torch.autograd)."""
+        return _FitFunction.apply(depth, self)
+
     # -- host API (copies inside the library call) --------------------------------
     def fit_host(self, depth: np.ndarray, counts: bool = False):
         """Fit host depth [H, W] or [N, H, W] through ``sf_fit_host``; returns numpy arrays."""
@@ -150,3 +168,46 @@ class SurfaceFitter:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _make_function():
+    import torch
+
+    class FitFunction(torch.autograd.Function):
+        """Autograd wrapper: forward = sf_fit_ex, backward = sf_fit_backward (both in the CUDA library)."""
+
+        @staticmethod
+        def forward(ctx, depth, fitter):
+            normals, offsets, curv = fitter.fit(depth)
+            ctx.save_for_backward(depth)
+            ctx.fitter = fitter
+            return normals, offsets, curv
+
+        @staticmethod
+        def backward(ctx, g_normals, g_offsets, g_curv):
+            (depth,) = ctx.saved_tensors
+            shape = depth.shape
+            if g_normals is None:
+                g_normals = torch.zeros(shape + (3,), device=depth.device)
+            if g_offsets is None:
+                g_offsets = torch.zeros(shape, device=depth.device)
+            if g_curv is None:
+                g_curv = torch.zeros(shape, device=depth.device)
+            return ctx.fitter.backward(depth, g_normals, g_offsets, g_curv), None
+
+    return FitFunction
+
+
+class _Lazy:
+    fn = None
+
+
+class _FitFunctionProxy:
+    @staticmethod
+    def apply(depth, fitter):
+        if _Lazy.fn is None:
+            _Lazy.fn = _make_function()
+        return _Lazy.fn.apply(depth, fitter)
+
+
+_FitFunction = _FitFunctionProxy

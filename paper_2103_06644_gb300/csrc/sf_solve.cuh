@@ -132,9 +132,16 @@ __device__ __forceinline__ void orient(float& nx, float& ny, float& nz, float& d
 //   Y = sum y y^T over y = [j - jhat, i - ihat, (what - w)/what],
 // and every entry of Y follows from the centred integer moments below.
 // The offset is d = -(n . mhat) / what.
-__device__ __forceinline__ FitOut solve_disparity(float nf, float fSj, float fSi, float fSjj, float fSji, float fSii,
-                                                  int64_t Sw, int64_t Swj, int64_t Swi, int64_t Sww, float qw, float tx,
-                                                  float ty, float a, float b) {
+struct DispWindow {
+    float R11, R12, R13, R22, R23, R33;  // Schur complement in ray units (K Y K^T)
+    float mx, my;                        // weighted centroid ray mhat = [mx, my, 1]
+    float what;                          // sum w^2 / sum w, in units of qw
+    float wbar;                          // mean w, in units of qw
+};
+
+__device__ __forceinline__ DispWindow build_disparity(float nf, float fSj, float fSi, float fSjj, float fSji,
+                                                      float fSii, int64_t Sw, int64_t Swj, int64_t Swi, int64_t Sww,
+                                                      float tx, float ty, float a, float b) {
     // the mask moments are exact integers held in float32 (all < 2^24)
     const float inv_n = rcp_approx(nf);
     const int n = (int)nf, Sj = (int)fSj, Si = (int)fSi;
@@ -166,19 +173,29 @@ __device__ __forceinline__ FitOut solve_disparity(float nf, float fSj, float fSi
     const float Yir = -nf * di;
     const float iw = rcp_approx(what);
     const float Yrr = (Cww + nf * e * e) * iw * iw;
-    const float mx = tx + a * (jb + dj);
-    const float my = ty + b * (ib + di);
-    const float R11 = a * a * Yjj + 2.f * a * mx * Yjr + mx * mx * Yrr;
-    const float R12 = a * b * Yji + a * my * Yjr + b * mx * Yir + mx * my * Yrr;
-    const float R13 = a * Yjr + mx * Yrr;
-    const float R22 = b * b * Yii + 2.f * b * my * Yir + my * my * Yrr;
-    const float R23 = b * Yir + my * Yrr;
-    const float R33 = Yrr;
+    DispWindow w;
+    w.mx = tx + a * (jb + dj);
+    w.my = ty + b * (ib + di);
+    w.R11 = a * a * Yjj + 2.f * a * w.mx * Yjr + w.mx * w.mx * Yrr;
+    w.R12 = a * b * Yji + a * w.my * Yjr + b * w.mx * Yir + w.mx * w.my * Yrr;
+    w.R13 = a * Yjr + w.mx * Yrr;
+    w.R22 = b * b * Yii + 2.f * b * w.my * Yir + w.my * w.my * Yrr;
+    w.R23 = b * Yir + w.my * Yrr;
+    w.R33 = Yrr;
+    w.what = what;
+    w.wbar = wbar;
+    return w;
+}
+
+__device__ __forceinline__ FitOut solve_disparity(float nf, float fSj, float fSi, float fSjj, float fSji, float fSii,
+                                                  int64_t Sw, int64_t Swj, int64_t Swi, int64_t Sww, float qw, float tx,
+                                                  float ty, float a, float b) {
+    const DispWindow w = build_disparity(nf, fSj, fSi, fSjj, fSji, fSii, Sw, Swj, Swi, Sww, tx, ty, a, b);
     FitOut o;
     float l0;
-    smallest_eigpair(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, l0, o.gap);
+    smallest_eigpair(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, l0, o.gap);
     o.curv = l0;
-    o.d = -(o.nx * mx + o.ny * my + o.nz) * iw / qw;
+    o.d = -(o.nx * w.mx + o.ny * w.my + o.nz) * rcp_approx(w.what) / qw;
     orient(o.nx, o.ny, o.nz, o.d);
     return o;
 }
@@ -222,6 +239,51 @@ __device__ __forceinline__ FitOut solve_standard(float nf, int64_t Sz, int64_t S
     const float px = a * qj + tx * zb, py = b * qi + ty * zb;
     o.d = -(o.nx * px + o.ny * py + o.nz * zb) * qz;
     orient(o.nx, o.ny, o.nz, o.d);
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// Backward: adjoint of the implicit fit of one window with respect to its
+// Schur complement R (any units), for upstream gradients gn (normal), gk
+// (curvature).  n = sigma v0 with the orientation sign sigma locally constant.
+//   eigenvector:  dv0 = -(R - l0 I)^+ dR v0, so Rbar = -sym(x v0^T) with
+//                 x = (R - l0 I + c v0 v0^T)^{-1} vbar_perp (c > 0 any: the
+//                 v0 direction is projected out of vbar);
+//   curvature:    kappa = l0 / tr R: Rbar += gk (v0 v0^T / tr - l0 / tr^2 I).
+// Returns Rbar (symmetric, upper triangle).  vbar must already hold the
+// gradient with respect to the oriented normal, including the offset term.
+// ---------------------------------------------------------------------------
+struct Sym3 { float a11, a12, a13, a22, a23, a33; };
+
+__device__ __forceinline__ Sym3 eig_adjoint(float r11, float r12, float r13, float r22, float r23, float r33,
+                                            float v0, float v1, float v2, float l0, float tr, float b0, float b1,
+                                            float b2, float gk) {
+    // project vbar onto the complement of v0
+    const float pv = b0 * v0 + b1 * v1 + b2 * v2;
+    b0 -= pv * v0; b1 -= pv * v1; b2 -= pv * v2;
+    // M = R - l0 I + tr v0 v0^T (symmetric, positive on the complement)
+    const float m11 = r11 - l0 + tr * v0 * v0, m12 = r12 + tr * v0 * v1, m13 = r13 + tr * v0 * v2;
+    const float m22 = r22 - l0 + tr * v1 * v1, m23 = r23 + tr * v1 * v2, m33 = r33 - l0 + tr * v2 * v2;
+    const float c11 = m22 * m33 - m23 * m23, c12 = m13 * m23 - m12 * m33, c13 = m12 * m23 - m13 * m22;
+    const float c22 = m11 * m33 - m13 * m13, c23 = m12 * m13 - m11 * m23, c33 = m11 * m22 - m12 * m12;
+    const float det = m11 * c11 + m12 * c12 + m13 * c13;
+    Sym3 o;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    if (det != 0.f) {
+        const float id = 1.f / det;
+        x0 = (c11 * b0 + c12 * b1 + c13 * b2) * id;
+        x1 = (c12 * b0 + c22 * b1 + c23 * b2) * id;
+        x2 = (c13 * b0 + c23 * b1 + c33 * b2) * id;
+    }
+    o.a11 = -x0 * v0; o.a22 = -x1 * v1; o.a33 = -x2 * v2;
+    o.a12 = -0.5f * (x0 * v1 + x1 * v0);
+    o.a13 = -0.5f * (x0 * v2 + x2 * v0);
+    o.a23 = -0.5f * (x1 * v2 + x2 * v1);
+    if (tr > 0.f) {
+        const float it = 1.f / tr, li = l0 * it * it;
+        o.a11 += gk * (v0 * v0 * it - li); o.a22 += gk * (v1 * v1 * it - li); o.a33 += gk * (v2 * v2 * it - li);
+        o.a12 += gk * v0 * v1 * it; o.a13 += gk * v0 * v2 * it; o.a23 += gk * v1 * v2 * it;
+    }
     return o;
 }
 

@@ -29,6 +29,7 @@
 #include <cstring>
 #include <string>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "surffit.h"
@@ -304,6 +305,96 @@ struct Calib {
     float a, b;       // 1/fx, 1/fy
 };
 
+// Vertical running sums of the disparity form's moments for one column.
+struct DispState {
+    const int32_t* hm; const int64_t* g0; const int64_t* g1; const int64_t* q0;
+    // mask moments: exact small integers, kept in float32 (all < 2^24)
+    float n = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;
+    int64_t Sw = 0, Swj = 0, Swi = 0, Sww = 0;
+    __device__ DispState(const Planes& P) : hm(P.p32), g0(P.c64(0)), g1(P.c64(1)), q0(P.c64(2)) {}
+    // window of output row y0 from rows y0 - r .. y0 + r
+    __device__ __forceinline__ void init(size_t pb, int Wp, int H, int y0, int r) {
+        for (int yy = y0 - r; yy <= y0 + r; ++yy) {
+            if (yy < 0 || yy >= H) continue;
+            const size_t o = pb + (size_t)yy * Wp;
+            int c0, c1, c2;
+            unpack_mask(__ldg(hm + o), c0, c1, c2);
+            const int i = yy - y0;
+            const float f0 = (float)c0, f1 = (float)c1, fi = (float)i;
+            n += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
+            const int64_t w0 = __ldg(g0 + o);
+            Sw += w0; Swj += __ldg(g1 + o); Swi += (int64_t)i * w0; Sww += __ldg(q0 + o);
+        }
+    }
+    // slide from output row y to y + 1
+    __device__ __forceinline__ void slide(size_t pb, int Wp, int H, int y, int r) {
+        const int yo = y - r, yi = y + r + 1;
+        int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
+        int64_t wo = 0, wjo = 0, wwo = 0, wi = 0, wji = 0, wwi = 0;
+        if (yo >= 0) {
+            const size_t o = pb + (size_t)yo * Wp;
+            unpack_mask(__ldg(hm + o), o0, o1, o2);
+            wo = __ldg(g0 + o); wjo = __ldg(g1 + o); wwo = __ldg(q0 + o);
+        }
+        if (yi < H) {
+            const size_t o = pb + (size_t)yi * Wp;
+            unpack_mask(__ldg(hm + o), i0, i1, i2);
+            wi = __ldg(g0 + o); wji = __ldg(g1 + o); wwi = __ldg(q0 + o);
+        }
+        // vertical moments: (n, Si, Sii) from the counts, (Sj, Sji) from sum j, Sjj plain
+        slide3(n, Si, Sii, (float)o0, (float)i0, r);
+        slide2(Sj, Sji, (float)o1, (float)i1, r);
+        Sjj += (float)(i2 - o2);
+        slide2(Sw, Swi, wo, wi, r);
+        Swj += wji - wjo;
+        Sww += wwi - wwo;
+    }
+    __device__ __forceinline__ int count() const { return (int)n; }
+};
+
+// Vertical running sums of the standard form's moments for one column.
+struct StdState {
+    const int32_t* hc; const int64_t* z0; const int64_t* z1; const int64_t* b0; const int64_t* b1; const int64_t* b2;
+    int n = 0;
+    int64_t Sz = 0, Szi = 0, Szj = 0, Szz = 0, Szzi = 0, Szzii = 0, Szzj = 0, Szzji = 0, Szzjj = 0;
+    __device__ StdState(const Planes& P)
+        : hc(P.p32), z0(P.c64(0)), z1(P.c64(1)), b0(P.c64(2)), b1(P.c64(3)), b2(P.c64(4)) {}
+    __device__ __forceinline__ void init(size_t pb, int Wp, int H, int y0, int r) {
+        for (int yy = y0 - r; yy <= y0 + r; ++yy) {
+            if (yy < 0 || yy >= H) continue;
+            const size_t o = pb + (size_t)yy * Wp;
+            const int64_t i = yy - y0;
+            n += __ldg(hc + o);
+            const int64_t c0 = __ldg(z0 + o), q0v = __ldg(b0 + o), q1v = __ldg(b1 + o);
+            Sz += c0; Szi += i * c0; Szj += __ldg(z1 + o);
+            Szz += q0v; Szzi += i * q0v; Szzii += i * i * q0v;
+            Szzj += q1v; Szzji += i * q1v; Szzjj += __ldg(b2 + o);
+        }
+    }
+    __device__ __forceinline__ void slide(size_t pb, int Wp, int H, int y, int r) {
+        const int yo = y - r, yi = y + r + 1;
+        int co = 0, ci = 0;
+        int64_t zo = 0, zjo = 0, qo0 = 0, qo1 = 0, qo2 = 0, zi = 0, zji = 0, qi0 = 0, qi1 = 0, qi2 = 0;
+        if (yo >= 0) {
+            const size_t o = pb + (size_t)yo * Wp;
+            co = __ldg(hc + o); zo = __ldg(z0 + o); zjo = __ldg(z1 + o);
+            qo0 = __ldg(b0 + o); qo1 = __ldg(b1 + o); qo2 = __ldg(b2 + o);
+        }
+        if (yi < H) {
+            const size_t o = pb + (size_t)yi * Wp;
+            ci = __ldg(hc + o); zi = __ldg(z0 + o); zji = __ldg(z1 + o);
+            qi0 = __ldg(b0 + o); qi1 = __ldg(b1 + o); qi2 = __ldg(b2 + o);
+        }
+        n += ci - co;
+        slide2(Sz, Szi, zo, zi, r);
+        Szj += zji - zjo;
+        slide3(Szz, Szzi, Szzii, qo0, qi0, r);
+        slide2(Szzj, Szzji, qo1, qi1, r);
+        Szzjj += qi2 - qo2;
+    }
+    __device__ __forceinline__ int count() const { return n; }
+};
+
 template <int DT, int M>
 __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
                                                           float scale, const unsigned* __restrict__ vmax_bits,
@@ -322,118 +413,220 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);  // metric value of one fixed-point unit
     const float tx = cal.tx[x];
     const size_t fo = (size_t)f * W * H;
+    const Planes P(planes_base, nf, plane_elems);
+    typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
+    S.init(pb, Wp, H, y0, r);
+    for (int y = y0; y < y1; ++y) {
+        const size_t oi = fo + (size_t)y * W + x;
+        const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
+        const int n = S.count();
+        const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
+        float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
+        if (ok) {
+            FitOut fo_;
+            if constexpr (M == SF_METHOD_DISPARITY)
+                fo_ = solve_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx,
+                                      cal.ty[y], cal.a, cal.b);
+            else
+                fo_ = solve_standard((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
+                                     S.Szzii, q, tx, cal.ty[y], cal.a, cal.b);
+            nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
+        }
+        normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
+        offsets[oi] = d; curvature[oi] = cu;
+        if (counts) counts[oi] = n;
+        if (y + 1 < y1) S.slide(pb, Wp, H, y, r);
+    }
+}
 
-    if (M == SF_METHOD_DISPARITY) {
-        const Planes P(planes_base, nf, plane_elems);
-        const int32_t* hm = P.p32;
-        const int64_t* g0 = P.c64(0);
-        const int64_t* g1 = P.c64(1);
-        const int64_t* q0 = P.c64(2);
-        // mask moments: exact small integers, kept in float32 (all < 2^24)
-        float n = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;
-        int64_t Sw = 0, Swj = 0, Swi = 0, Sww = 0;
-        for (int yy = y0 - r; yy <= y0 + r; ++yy) {
-            if (yy < 0 || yy >= H) continue;
-            const size_t o = pb + (size_t)yy * Wp;
-            int c0, c1, c2;
-            unpack_mask(__ldg(hm + o), c0, c1, c2);
-            const int i = yy - y0;
-            const float f0 = (float)c0, f1 = (float)c1, fi = (float)i;
-            n += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
-            const int64_t w0 = __ldg(g0 + o);
-            Sw += w0; Swj += __ldg(g1 + o); Swi += (int64_t)i * w0; Sww += __ldg(q0 + o);
-        }
-        for (int y = y0; y < y1; ++y) {
-            const size_t oi = fo + (size_t)y * W + x;
-            const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
-            const bool ok = n >= (float)min_valid && n > 0.f && (cvalid || !require_center);
-            float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
-            if (ok) {
-                const FitOut fo_ = solve_disparity(n, Sj, Si, Sjj, Sji, Sii, Sw, Swj, Swi, Sww, q, tx, cal.ty[y],
-                                                   cal.a, cal.b);
-                nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
+// ---------------------------------------------------------------------------
+// Backward, step 1: per-window adjoint.  For every valid window p, from the
+// same exact moments as the forward pass and the upstream gradients
+// (gn, gd, gk) of (normal, offset, curvature), write the quantities that
+// carry the window's contribution to each of its pixels q:
+//   disparity: dL_p/dw_q = w_q [(P_q - mu_p) . gbar_p - c_p]   (7 floats: gbar, mu, c)
+//   standard:  dL_p/dP_q = 2 Rbar_p (P_q - mu_p) - e_p         (12 floats: 2Rbar, mu, e)
+// with mu_p the window's (weighted) centroid.  The disparity form follows
+// from R = A - g g^T / s, g = sum w m, s = sum w^2: gbar = -2 Rbar mu - gd n/s,
+// sbar = g^T Rbar g / s^2 + gd n.g / s^2, and mu.gbar + 2 sbar = -gd d / s,
+// so the contribution gbar.m_q + 2 w_q sbar is centred on the window and
+// never subtracts two large numbers.  Invalid windows write zeros.
+// Adjoint planes: channel c of frame f at adj + (c * nf + f) * fe.
+// ---------------------------------------------------------------------------
+template <int DT, int M>
+__global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restrict__ depth, int W, int H, int r,
+                                                             float scale, const unsigned* __restrict__ vmax_bits,
+                                                             int bits, int Wp, size_t plane_elems,
+                                                             void* __restrict__ planes_base, Calib cal, int min_valid,
+                                                             int require_center, int band,
+                                                             const float* __restrict__ g_normals,
+                                                             const float* __restrict__ g_offsets,
+                                                             const float* __restrict__ g_curv,
+                                                             float* __restrict__ adj) {
+    const int f = blockIdx.z;
+    const int x = blockIdx.x * kVThreads + threadIdx.x;
+    if (x >= W) return;
+    const int y0 = blockIdx.y * band;
+    const int y1 = min(y0 + band, H);
+    const size_t nf = gridDim.z;
+    const size_t fe = (size_t)W * H;
+    const size_t pb = (size_t)f * plane_elems + x;
+    const float q = quantum<DT, M>(vmax_bits[f], bits, scale);
+    const float tx = cal.tx[x];
+    const size_t fo = (size_t)f * fe;
+    const Planes P(planes_base, nf, plane_elems);
+    constexpr int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
+    typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
+    S.init(pb, Wp, H, y0, r);
+    for (int y = y0; y < y1; ++y) {
+        const size_t oi = fo + (size_t)y * W + x;
+        const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
+        const int n = S.count();
+        const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
+        float out[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) out[c] = 0.f;
+        if (ok) {
+            const float gnx = g_normals[3 * oi], gny = g_normals[3 * oi + 1], gnz = g_normals[3 * oi + 2];
+            const float gd = g_offsets[oi], gk = g_curv[oi];
+            float R11, R12, R13, R22, R23, R33, mux, muy, muz, s_or_n;
+            if constexpr (M == SF_METHOD_DISPARITY) {
+                const DispWindow w = build_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi,
+                                                     S.Sww, tx, cal.ty[y], cal.a, cal.b);
+                R11 = w.R11; R12 = w.R12; R13 = w.R13; R22 = w.R22; R23 = w.R23; R33 = w.R33;
+                const float iwm = 1.f / (w.what * q);  // 1 / what_metric
+                mux = w.mx * iwm; muy = w.my * iwm; muz = iwm;
+                s_or_n = S.n * (w.wbar * q) * (w.what * q);  // sum w^2 = n wbar what
+            } else {
+                // covariance of the points in metric units (see solve_standard)
+                const float nf = (float)S.n, inv_n = 1.f / nf;
+                const int m = __float2int_rn((float)S.Sz * inv_n);
+                const int64_t T0 = S.Sz - (int64_t)S.n * m;
+                const int64_t Tzz = S.Szz - (int64_t)m * (S.Sz + T0);
+                const int64_t Tzj = S.Szzj - (int64_t)m * S.Szj;
+                const int64_t Tzi = S.Szzi - (int64_t)m * S.Szi;
+                const float t0 = (float)(int)T0 * inv_n;
+                const float fSzj = (float)S.Szj, fSzi = (float)S.Szi;
+                const float q2 = q * q;
+                const float Czz = ((float)Tzz - (float)(int)T0 * t0) * q2;
+                const float Cjz = ((float)Tzj - fSzj * t0) * q2;
+                const float Ciz = ((float)Tzi - fSzi * t0) * q2;
+                const float qj = fSzj * inv_n, qi = fSzi * inv_n;
+                const float Cjj = ((float)S.Szzjj - fSzj * qj) * q2;
+                const float Cji = ((float)S.Szzji - fSzj * qi) * q2;
+                const float Cii = ((float)S.Szzii - fSzi * qi) * q2;
+                const float a = cal.a, b = cal.b, ty = cal.ty[y];
+                R11 = a * a * Cjj + 2.f * a * tx * Cjz + tx * tx * Czz;
+                R12 = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
+                R13 = a * Cjz + tx * Czz;
+                R22 = b * b * Cii + 2.f * b * ty * Ciz + ty * ty * Czz;
+                R23 = b * Ciz + ty * Czz;
+                R33 = Czz;
+                const float zb = ((float)m + t0) * q;
+                mux = a * qj * q + tx * zb; muy = b * qi * q + ty * zb; muz = zb;
+                s_or_n = nf;
             }
-            normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
-            offsets[oi] = d; curvature[oi] = cu;
-            if (counts) counts[oi] = (int)n;
-            if (y + 1 < y1) {
-                const int yo = y - r, yi = y + r + 1;
-                int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
-                int64_t wo = 0, wjo = 0, wwo = 0, wi = 0, wji = 0, wwi = 0;
-                if (yo >= 0) {
-                    const size_t o = pb + (size_t)yo * Wp;
-                    unpack_mask(__ldg(hm + o), o0, o1, o2);
-                    wo = __ldg(g0 + o); wjo = __ldg(g1 + o); wwo = __ldg(q0 + o);
-                }
-                if (yi < H) {
-                    const size_t o = pb + (size_t)yi * Wp;
-                    unpack_mask(__ldg(hm + o), i0, i1, i2);
-                    wi = __ldg(g0 + o); wji = __ldg(g1 + o); wwi = __ldg(q0 + o);
-                }
-                // vertical moments: (n, Si, Sii) from the counts, (Sj, Sji) from sum j, Sjj plain
-                slide3(n, Si, Sii, (float)o0, (float)i0, r);
-                slide2(Sj, Sji, (float)o1, (float)i1, r);
-                Sjj += (float)(i2 - o2);
-                slide2(Sw, Swi, wo, wi, r);
-                Swj += wji - wjo;
-                Sww += wwi - wwo;
+            float v0, v1, v2, l0n, gap;
+            smallest_eigpair(R11, R12, R13, R22, R23, R33, v0, v1, v2, l0n, gap);
+            const float tr = R11 + R22 + R33;
+            const float d0 = -(v0 * mux + v1 * muy + v2 * muz);
+            float nx = v0, ny = v1, nz = v2, d = d0;
+            orient(nx, ny, nz, d);
+            const float sg = (nx * v0 + ny * v1 + nz * v2) >= 0.f ? 1.f : -1.f;
+            // d = -n . mu: gradient wrt the oriented normal, then wrt v0
+            const float bx = sg * (gnx - gd * mux), by = sg * (gny - gd * muy), bz = sg * (gnz - gd * muz);
+            const Sym3 Rb = eig_adjoint(R11, R12, R13, R22, R23, R33, v0, v1, v2, l0n * tr, tr, bx, by, bz, gk);
+            if constexpr (M == SF_METHOD_DISPARITY) {
+                const float is = 1.f / s_or_n;
+                out[0] = -2.f * (Rb.a11 * mux + Rb.a12 * muy + Rb.a13 * muz) - gd * nx * is;
+                out[1] = -2.f * (Rb.a12 * mux + Rb.a22 * muy + Rb.a23 * muz) - gd * ny * is;
+                out[2] = -2.f * (Rb.a13 * mux + Rb.a23 * muy + Rb.a33 * muz) - gd * nz * is;
+                out[3] = mux; out[4] = muy; out[5] = muz;
+                out[6] = gd * d * is;
+            } else {
+                const float in = 1.f / s_or_n;
+                out[0] = 2.f * Rb.a11; out[1] = 2.f * Rb.a12; out[2] = 2.f * Rb.a13;
+                out[3] = 2.f * Rb.a22; out[4] = 2.f * Rb.a23; out[5] = 2.f * Rb.a33;
+                out[6] = mux; out[7] = muy; out[8] = muz;
+                out[9] = gd * nx * in; out[10] = gd * ny * in; out[11] = gd * nz * in;
             }
         }
-    } else {
-        const Planes P(planes_base, nf, plane_elems);
-        const int32_t* hc = P.p32;
-        const int64_t* z0 = P.c64(0);
-        const int64_t* z1 = P.c64(1);
-        const int64_t* b0 = P.c64(2);
-        const int64_t* b1 = P.c64(3);
-        const int64_t* b2 = P.c64(4);
-        int n = 0;  // window count
-        int64_t Sz = 0, Szi = 0, Szj = 0, Szz = 0, Szzi = 0, Szzii = 0, Szzj = 0, Szzji = 0, Szzjj = 0;
-        for (int yy = y0 - r; yy <= y0 + r; ++yy) {
-            if (yy < 0 || yy >= H) continue;
-            const size_t o = pb + (size_t)yy * Wp;
-            const int64_t i = yy - y0;
-            n += __ldg(hc + o);
-            const int64_t c0 = __ldg(z0 + o), q0v = __ldg(b0 + o), q1v = __ldg(b1 + o);
-            Sz += c0; Szi += i * c0; Szj += __ldg(z1 + o);
-            Szz += q0v; Szzi += i * q0v; Szzii += i * i * q0v;
-            Szzj += q1v; Szzji += i * q1v; Szzjj += __ldg(b2 + o);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) adj[((size_t)c * nf + f) * fe + (size_t)y * W + x] = out[c];
+        if (y + 1 < y1) S.slide(pb, Wp, H, y, r);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward, step 2: every pixel q gathers the contributions of the windows
+// p that contain it (p in the k x k window around q, by symmetry) from a
+// shared-memory tile of the adjoint planes, and applies the chain rule
+//   disparity: dL/dZ_q = -w_q^3 sum_p [(P_q - mu_p) . gbar_p - c_p]
+//   standard:  dL/dZ_q = m_q . sum_p [2 Rbar_p (P_q - mu_p) - e_p]
+// Missing pixels get 0.  Block: 32 x 8 threads, 32 x 32 output tile.
+// ---------------------------------------------------------------------------
+constexpr int kGTile = 32;
+
+template <int DT, int M>
+__global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ depth, int W, int H, int r, float scale,
+                                                     Calib cal, const float* __restrict__ adj,
+                                                     float* __restrict__ g_depth) {
+    extern __shared__ float sadj[];
+    constexpr int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
+    const int f = blockIdx.z;
+    const size_t nf = gridDim.z;
+    const size_t fe = (size_t)W * H;
+    const int x0 = blockIdx.x * kGTile, y0 = blockIdx.y * kGTile;
+    const int T = kGTile + 2 * r;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int c = 0; c < NC; ++c) {
+        const float* src = adj + ((size_t)c * nf + f) * fe;
+        for (int idx = tid; idx < T * T; idx += 256) {
+            const int ty_ = idx / T, tx_ = idx - ty_ * T;
+            const int xx = x0 - r + tx_, yy = y0 - r + ty_;
+            float v = 0.f;
+            if (xx >= 0 && xx < W && yy >= 0 && yy < H) v = src[(size_t)yy * W + xx];
+            sadj[(c * T + ty_) * T + tx_] = v;
         }
-        for (int y = y0; y < y1; ++y) {
-            const size_t oi = fo + (size_t)y * W + x;
-            const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
-            const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
-            float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
-            if (ok) {
-                const FitOut fo_ = solve_standard((float)n, Sz, Szj, Szi, Szz, Szzj, Szzi, Szzjj, Szzji, Szzii, q, tx,
-                                                  cal.ty[y], cal.a, cal.b);
-                nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    if (x >= W) return;
+    const float tx = cal.tx[x];
+    for (int yr = threadIdx.y; yr < kGTile; yr += 8) {
+        const int y = y0 + yr;
+        if (y >= H) break;
+        const size_t oi = (size_t)f * fe + (size_t)y * W + x;
+        const float z = load_depth<DT>(depth, oi, scale);
+        float g = 0.f;
+        if (depth_valid(z)) {
+            const float px = z * tx, py = z * cal.ty[y], pz = z;
+            float acc = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+            for (int dy = 0; dy <= 2 * r; ++dy) {
+                const int row = yr + dy;
+                for (int dx = 0; dx <= 2 * r; ++dx) {
+                    const int col = threadIdx.x + dx;
+                    const float* sp = sadj + row * T + col;
+                    const size_t cs = (size_t)T * T;
+                    if constexpr (M == SF_METHOD_DISPARITY) {
+                        acc += (px - sp[3 * cs]) * sp[0] + (py - sp[4 * cs]) * sp[cs] + (pz - sp[5 * cs]) * sp[2 * cs] -
+                               sp[6 * cs];
+                    } else {
+                        const float ux = px - sp[6 * cs], uy = py - sp[7 * cs], uz = pz - sp[8 * cs];
+                        ax += sp[0] * ux + sp[cs] * uy + sp[2 * cs] * uz - sp[9 * cs];
+                        ay += sp[cs] * ux + sp[3 * cs] * uy + sp[4 * cs] * uz - sp[10 * cs];
+                        az += sp[2 * cs] * ux + sp[4 * cs] * uy + sp[5 * cs] * uz - sp[11 * cs];
+                    }
+                }
             }
-            normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
-            offsets[oi] = d; curvature[oi] = cu;
-            if (counts) counts[oi] = n;
-            if (y + 1 < y1) {
-                const int yo = y - r, yi = y + r + 1;
-                int co = 0, ci = 0;
-                int64_t zo = 0, zjo = 0, qo0 = 0, qo1 = 0, qo2 = 0, zi = 0, zji = 0, qi0 = 0, qi1 = 0, qi2 = 0;
-                if (yo >= 0) {
-                    const size_t o = pb + (size_t)yo * Wp;
-                    co = __ldg(hc + o); zo = __ldg(z0 + o); zjo = __ldg(z1 + o);
-                    qo0 = __ldg(b0 + o); qo1 = __ldg(b1 + o); qo2 = __ldg(b2 + o);
-                }
-                if (yi < H) {
-                    const size_t o = pb + (size_t)yi * Wp;
-                    ci = __ldg(hc + o); zi = __ldg(z0 + o); zji = __ldg(z1 + o);
-                    qi0 = __ldg(b0 + o); qi1 = __ldg(b1 + o); qi2 = __ldg(b2 + o);
-                }
-                n += ci - co;
-                slide2(Sz, Szi, zo, zi, r);
-                Szj += zji - zjo;
-                slide3(Szz, Szzi, Szzii, qo0, qi0, r);
-                slide2(Szzj, Szzji, qo1, qi1, r);
-                Szzjj += qi2 - qo2;
+            if constexpr (M == SF_METHOD_DISPARITY) {
+                const float w = 1.f / z;
+                g = -w * w * w * acc;
+            } else {
+                g = tx * ax + cal.ty[y] * ay + az;
             }
         }
+        g_depth[oi] = g;
     }
 }
 
@@ -511,6 +704,8 @@ struct sf_ctx {
     size_t h_stage_bytes = 0;
     void* d_io = nullptr;
     size_t d_io_bytes = 0;
+    float* adj = nullptr;      // backward: per-window adjoint planes
+    size_t adj_bytes = 0;
     // profiling: (stage, start event, stop event) per recorded launch
     bool profiling = false;
     struct Rec { int stage; cudaEvent_t a, b; };
@@ -560,6 +755,15 @@ static sf_status ensure_planes(sf_ctx* c, int frames) {
     return SF_OK;
 }
 
+// Band height of the vertical pass: long bands amortise the 2r-row warm-up,
+// short bands give enough threads to fill the GPU (>= 24 warps per SM).
+static int vertical_band(const sf_ctx* c, int nfr) {
+    const size_t cols = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * sf::kVThreads * nfr;
+    int band = 256;
+    while (band > 16 && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 24 * 32) band /= 2;
+    return band;
+}
+
 template <int DT, int M>
 static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,
                              int32_t* counts, cudaStream_t st) {
@@ -583,11 +787,7 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
     }
     {
         StageTimer t(c, 2, st);
-        // band height: long bands amortise the 2r-row warm-up; short bands give
-        // enough threads to fill the GPU (target >= 24 warps per SM).
-        const size_t cols = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * sf::kVThreads * nfr;
-        int band = 256;
-        while (band > 16 && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 24 * 32) band /= 2;
+        const int band = vertical_band(c, nfr);
         dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
         sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
         sf::vpass_kernel<DT, M><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
@@ -597,6 +797,47 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SF_OK;
+}
+
+template <int DT, int M>
+static sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const float* gn, const float* gd,
+                                 const float* gk, float* g_depth, cudaStream_t st) {
+    const size_t fe = (size_t)c->W * c->H;
+    const int raw_z = (DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD) ? 1 : 0;
+    const int bits = quant_bits(M, c->k);
+    SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
+    if (!raw_z) {
+        int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
+        blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
+        sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, c->depth_scale, c->vmax);
+    }
+    {
+        dim3 grid((c->W + sf::kHSeg - 1) / sf::kHSeg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
+        const int IW = sf::kHSeg + 2 * c->r;
+        const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
+        sf::hpass_kernel<DT, M><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
+                                                                  bits, raw_z, c->Wp, c->plane_elems, c->planes);
+    }
+    sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
+    {
+        const int band = vertical_band(c, nfr);
+        dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
+        sf::vadjoint_kernel<DT, M><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
+                                                                  bits, c->Wp, c->plane_elems, c->planes, cal,
+                                                                  c->min_valid, c->require_center, band, gn, gd, gk,
+                                                                  c->adj);
+    }
+    {
+        const int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
+        const int T = sf::kGTile + 2 * c->r;
+        const size_t smem = sizeof(float) * NC * (size_t)T * T;
+        dim3 grid((c->W + sf::kGTile - 1) / sf::kGTile, (c->H + sf::kGTile - 1) / sf::kGTile, nfr);
+        sf::gather_kernel<DT, M><<<grid, dim3(32, 8), smem, st>>>(depth, c->W, c->H, c->r, c->depth_scale, cal,
+                                                                   c->adj, g_depth);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "backward kernel launch");
     return SF_OK;
 }
 
@@ -669,6 +910,16 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_U16, SF_METHOD_STANDARD>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        const int T = sf::kGTile + 2 * sf::kMaxR;
+        const int gs7 = (int)(sizeof(float) * 7 * T * T), gs12 = (int)(sizeof(float) * 12 * T * T);
+        cudaFuncSetAttribute(sf::gather_kernel<SF_DEPTH_F32, SF_METHOD_DISPARITY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, gs7);
+        cudaFuncSetAttribute(sf::gather_kernel<SF_DEPTH_U16, SF_METHOD_DISPARITY>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, gs7);
+        cudaFuncSetAttribute(sf::gather_kernel<SF_DEPTH_F32, SF_METHOD_STANDARD>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, gs12);
+        cudaFuncSetAttribute(sf::gather_kernel<SF_DEPTH_U16, SF_METHOD_STANDARD>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, gs12);
         e = cudaGetLastError();
         if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create kernel attributes"); }
     }
@@ -776,6 +1027,52 @@ sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals
     return SF_OK;
 }
 
+sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const float* g_normals, const float* g_offsets,
+                          const float* g_curvature, float* g_depth, void* stream) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
+    if (n_frames == 0) return SF_OK;
+    if (!depth || !g_normals || !g_offsets || !g_curvature || !g_depth)
+        return fail(SF_ERR_INVALID_ARG, "null buffer");
+    if (c->method != SF_METHOD_DISPARITY && c->method != SF_METHOD_STANDARD)
+        return fail(SF_ERR_UNSUPPORTED, "the backward covers the implicit fits only");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t fe = (size_t)c->W * c->H;
+    const size_t dbytes = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
+    const int per = std::min(c->max_frames_per_pass, 64);
+    const int first = std::min(per, n_frames);
+    sf_status s = ensure_planes(c, first);
+    if (s != SF_OK) return s;
+    const size_t need = sizeof(float) * 12 * fe * (size_t)first;
+    if (c->adj_bytes < need) {
+        if (c->adj) cudaFree(c->adj);
+        c->adj = nullptr;
+        c->adj_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->adj, need);
+        if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "adjoint scratch of %zu bytes failed", need);
+        c->adj_bytes = need;
+    }
+    for (int f0 = 0; f0 < n_frames; f0 += per) {
+        const int nfr = std::min(per, n_frames - f0);
+        const void* dp = static_cast<const char*>(depth) + dbytes * fe * f0;
+        const float* gn = g_normals + 3 * fe * f0;
+        const float* gd = g_offsets + fe * f0;
+        const float* gk = g_curvature + fe * f0;
+        float* gz = g_depth + fe * f0;
+        if (c->depth_type == SF_DEPTH_F32) {
+            s = c->method == SF_METHOD_DISPARITY
+                    ? launch_backward<SF_DEPTH_F32, SF_METHOD_DISPARITY>(c, nfr, dp, gn, gd, gk, gz, st)
+                    : launch_backward<SF_DEPTH_F32, SF_METHOD_STANDARD>(c, nfr, dp, gn, gd, gk, gz, st);
+        } else {
+            s = c->method == SF_METHOD_DISPARITY
+                    ? launch_backward<SF_DEPTH_U16, SF_METHOD_DISPARITY>(c, nfr, dp, gn, gd, gk, gz, st)
+                    : launch_backward<SF_DEPTH_U16, SF_METHOD_STANDARD>(c, nfr, dp, gn, gd, gk, gz, st);
+        }
+        if (s != SF_OK) return s;
+    }
+    return SF_OK;
+}
+
 sf_status sf_profile_enable(sf_ctx* c, int on) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     for (auto& r : c->recs) { c->event_pool.push_back(r.a); c->event_pool.push_back(r.b); }
@@ -811,6 +1108,7 @@ sf_status sf_destroy(sf_ctx* c) {
     if (c->planes) cudaFree(c->planes);
     if (c->d_io) cudaFree(c->d_io);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->adj) cudaFree(c->adj);
     delete c;
     return SF_OK;
 }

@@ -1,0 +1,110 @@
+"""GPU backward (sf_fit_backward) against the FP64 oracle's analytic adjoint.
+
+The oracle's adjoint is itself pinned to central finite differences of the
+oracle forward on the CPU (tests/test_oracle.py).  Pixels whose gradient
+involves a near-degenerate window (gamma < 1e-2 anywhere in their k x k
+neighbourhood) are excluded: there the eigenvector derivative scales with
+1 / (lambda1 - lambda0) and the gradient is ill-posed.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2103_06644_gb300 import SurfaceFitter  # noqa: E402
+
+GAP_MIN = 1e-2
+REL_TOL = 2e-3  # of the largest gradient magnitude in the frame
+
+
+def _box_min(a, r):
+    H, W = a.shape
+    out = np.full_like(a, np.inf)
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            sh = np.full_like(a, np.inf)
+            ys, yd = (slice(max(0, dy), H + min(0, dy)), slice(max(0, -dy), H + min(0, -dy)))
+            xs, xd = (slice(max(0, dx), W + min(0, dx)), slice(max(0, -dx), W + min(0, -dx)))
+            sh[yd, xd] = a[ys, xs]
+            out = np.minimum(out, sh)
+    return out
+
+
+def _compare(depth, intr, k, method, gn, gd, gk):
+    H, W = depth.shape
+    ref_fwd = oracle.fit(depth, intr, k, method, want_lambda=True)
+    ok = np.isfinite(ref_fwd["offsets"])
+    gn = np.where(ok[..., None], gn, 0.0)
+    gd = np.where(ok, gd, 0.0)
+    gk = np.where(ok, gk, 0.0)
+    ref = oracle.backward(depth, intr, k, gn, gd, gk, method)
+    f = SurfaceFitter(intr, W, H, k, method=method)
+    g = f.backward(torch.from_numpy(depth).cuda(), torch.from_numpy(gn.astype(np.float32)).cuda(),
+                   torch.from_numpy(gd.astype(np.float32)).cuda(), torch.from_numpy(gk.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    g = g.cpu().numpy().astype(np.float64)
+    f.close()
+    lam = ref_fwd["lam"]
+    gap = np.where(ok, (lam[..., 1] - lam[..., 0]) / np.where(ok, lam[..., 2], 1.0), np.inf)
+    good = _box_min(gap, k // 2) >= GAP_MIN
+    valid = depth > 0
+    assert np.all(g[~valid] == 0.0)
+    sel = good & valid
+    scale = np.abs(ref[sel]).max()
+    err = np.abs(g[sel] - ref[sel]).max() / scale
+    assert sel.mean() > 0.5
+    assert err < REL_TOL, err
+    return err, sel.mean()
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+@pytest.mark.parametrize("k", [5, 9])
+def test_backward_matches_oracle_adjoint(method, k):
+    W, H = 96, 72
+    intr = scenes.Intrinsics.scaled(W, H)
+    depth = scenes.kinect_frame(scenes.BASE_SEED + 60 + k, intr, W, H, n_planes=2)
+    rng = np.random.Generator(np.random.PCG64(7))
+    err, frac = _compare(depth, intr.as_tuple(), k, method, rng.standard_normal((H, W, 3)),
+                         rng.standard_normal((H, W)), rng.standard_normal((H, W)) * 10)
+    print(method, k, err, frac)
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_backward_normal_and_curvature_loss_640x480_k9(method):
+    """Loss = sum over valid pixels of |n - n*|^2 + 0.1 kappa, seeded targets n* (n*_z < 0)."""
+    W, H, k = 640, 480, 9
+    intr = scenes.Intrinsics(525.0, 525.0, 319.5, 239.5)
+    depth = scenes.kinect_frame(scenes.BASE_SEED + 500, intr, W, H)
+    ref_fwd = oracle.fit(depth, intr.as_tuple(), k, method)
+    tgt = scenes.target_normals(scenes.BASE_SEED + 501, H, W)
+    gn = 2.0 * (np.nan_to_num(ref_fwd["normals"]) - tgt)
+    err, frac = _compare(depth, intr.as_tuple(), k, method, gn, np.zeros((H, W)), np.full((H, W), 0.1))
+    print(method, err, frac)
+
+
+def test_autograd_function_matches_direct_backward():
+    W, H, k = 128, 96, 9
+    intr = scenes.Intrinsics.scaled(W, H)
+    frames = np.stack([scenes.kinect_frame(70 + i, intr, W, H) for i in range(2)])
+    f = SurfaceFitter(intr.as_tuple(), W, H, k)
+    d = torch.from_numpy(frames).cuda().requires_grad_(True)
+    n, off, cu = f.fit_differentiable(d)
+    tgt = torch.from_numpy(np.stack([scenes.target_normals(80 + i, H, W) for i in range(2)]).astype(np.float32)).cuda()
+    valid = torch.isfinite(off)
+    diff = torch.where(valid[..., None], n - tgt, torch.zeros_like(n))
+    loss = (diff ** 2).sum() + 0.1 * torch.where(valid, cu, torch.zeros_like(cu)).sum()
+    loss.backward()
+    gn = torch.where(valid[..., None], 2 * (n.detach() - tgt), torch.zeros_like(n))
+    gk = torch.where(valid, torch.full_like(cu, 0.1), torch.zeros_like(cu))
+    direct = f.backward(d.detach(), gn, torch.zeros_like(off), gk)
+    torch.cuda.synchronize()
+    assert torch.allclose(d.grad, direct, rtol=1e-5, atol=1e-6 * direct.abs().max().item())
+    f.close()
