@@ -121,6 +121,54 @@ def cpu_oracle_sample(time_budget_s: float = 15.0):
                       "FP64 direct window sums, OpenMP over rows" % (n, px), "seconds": dt}
 
 
+def precision_report(group, dev):
+    """Errors per output against the FP64 oracle on the first 1080p frame, for the float32 solve
+    (mode 0), the FP64 re-solve of windows with gamma < 1e-2 (mode 1) and the FP64 solve (mode 2).
+    Also the throughput of mode 1 on that frame."""
+    import torch
+
+    import oracle
+    from paper_2103_06644_gb300 import SurfaceFitter
+
+    W, H, intr, frames = group
+    depth = frames[0]
+    ref = oracle.fit(depth, intr.as_tuple(), K, "disparity", want_lambda=True, want_moments=True)
+    ok = np.isfinite(ref["offsets"])
+    lam = ref["lam"]
+    gap = np.where(ok, (lam[..., 1] - lam[..., 0]) / np.where(ok, lam[..., 2], 1), 0)
+    mu = np.linalg.norm(ref["moments"][..., 6:9] / np.where(ok[..., None], ref["moments"][..., 9:10], 1), axis=-1)
+    d = torch.from_numpy(depth).to(dev)
+    rep = {"frame": "first 1920x1080 frame of the batch, k=31, disparity form", "valid": int(ok.sum())}
+    for mode in (0, 1, 2):
+        f = SurfaceFitter(intr.as_tuple(), W, H, K)
+        f.set_precision(mode, 1e-2)
+        n, o, c = [t.cpu().numpy().astype(np.float64) for t in f.fit(d)]
+        torch.cuda.synchronize()
+        ent = {}
+        for name, gmin in (("gamma>=1e-3", 1e-3), ("gamma>=1e-5", 1e-5)):
+            sel = ok & (gap >= gmin)
+            a, b = n[sel], ref["normals"][sel]
+            ang = np.arctan2(np.linalg.norm(np.cross(a, b), axis=-1), np.sum(a * b, -1))
+            ent[name] = {"max_normal_angle_rad": float(ang.max()),
+                         "max_offset_err_rel_centroid": float((np.abs(o[sel] - ref["offsets"][sel]) / mu[sel]).max()),
+                         "max_curvature_err": float(np.abs(c[sel] - ref["curvature"][sel]).max()),
+                         "windows": int(sel.sum())}
+        if mode == 1:
+            for _ in range(3):
+                f.fit(d)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                f.fit(d)
+            e1.record()
+            torch.cuda.synchronize()
+            ent["value"] = W * H / (e0.elapsed_time(e1) / 20 / 1000) / 1e6
+        rep["mode%d" % mode] = ent
+        f.close()
+    return rep
+
+
 def run_single_case(args):
     """One seeded 1920x1080 frame of the benchmark batch fitted --steps times (for ncu captures)."""
     import torch
@@ -356,6 +404,10 @@ def main():
                        "api": "sf_fit_host (host buffers, copies inside the call)"}
     if rank == 0 and world == 1 and not args.no_cpu and not args.profile_only:
         line["cpu_baseline"] = cpu_oracle_sample()
+        try:
+            line["precision_vs_oracle"] = precision_report(groups[0], dev)
+        except Exception as exc:  # a report failure must not lose the benchmark line
+            line["precision_vs_oracle"] = {"error": repr(exc)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     for f in fitters:

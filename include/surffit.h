@@ -109,6 +109,20 @@ sf_status sf_set_params(sf_ctx* ctx, int method, int depth_type, float depth_sca
                         int require_center_valid);
 
 /*
+ * sf_set_precision -- precision of the per-pixel solve.  The window sums are
+ * exact integers in every mode; the modes differ in the solve:
+ *   0  float32 solve (default).  Normal error ~ 4e-7 / gamma rad against an
+ *      FP64 fit of the same data, gamma = (lambda1 - lambda0) / lambda2.
+ *   1  float32 solve, then every window with gamma < tau is queued and solved
+ *      again in FP64 from the same exact moments (overwriting its outputs).
+ *   2  FP64 solve for every window (slow: FP64 runs at ~1/64 of the float32
+ *      rate on GB300).
+ * tau in (0, 1] (mode 1; default 1e-2).  Modes 1 and 2 allocate a queue of
+ * 8 bytes per pixel on the next fit.
+ */
+sf_status sf_set_precision(sf_ctx* ctx, int mode, float tau);
+
+/*
  * sf_fit -- fit every pixel of one frame.
  *   depth      device [H][W] float32 metres or uint16 raw (per sf_set_params)
  *   normals    device [H][W][3] float32, out
@@ -175,12 +189,13 @@ sf_status sf_channel_counts(int method, int* depth_channels, int* mask_channels)
  * waits for the recorded events, writes for each stage s < n_stages the
  * summed milliseconds ms[s] and the launch count launches[s], and clears the
  * record.  Stages: 0 range (quantum), 1 horizontal moments, 2 vertical
- * moments + solve.  Enabling again clears the record.
+ * moments + solve, 3 FP64 re-solve (precision modes 1-2).  Enabling again
+ * clears the record.
  */
 sf_status sf_profile_enable(sf_ctx* ctx, int on);
 sf_status sf_profile_read(sf_ctx* ctx, int n_stages, double* ms, int* launches);
 
-#define SF_NUM_STAGES 3
+#define SF_NUM_STAGES 4
 
 /*
  * sf_fit_static -- the fit of sf_fit for one frame, without a context and

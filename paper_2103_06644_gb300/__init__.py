@@ -71,6 +71,10 @@ class SurfaceFitter:
                                                   float(depth_scale), int(min_valid), int(bool(require_center))))
         self.method, self.depth_type, self.depth_scale = method, depth_type, float(depth_scale)
 
+    def set_precision(self, mode: int, tau: float = 1e-2) -> None:
+        """0: float32 solve; 1: + FP64 re-solve where gamma < tau; 2: FP64 solve everywhere."""
+        _native.check(_native.lib().sf_set_precision(self._h, int(mode), float(tau)))
+
     # -- device API -------------------------------------------------------------
     def _check_depth(self, depth):
         import torch
@@ -139,7 +143,7 @@ class SurfaceFitter:
         return (normals, offsets, curv, cnt) if counts else (normals, offsets, curv)
 
     # -- profiling (CUDA events around the library's own launches) ---------------
-    STAGES = ("range", "hpass", "vpass_solve")
+    STAGES = ("range", "hpass", "vpass_solve", "fp64_resolve")
 
     def profile(self, on: bool = True) -> None:
         _native.check(_native.lib().sf_profile_enable(self._h, int(bool(on))))

@@ -39,6 +39,7 @@ SIGNATURES = {
     "sf_fit_ex": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sf_fit_host": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sf_destroy": (_I, [_VP]),
+    "sf_set_precision": (_I, [_VP, _I, _F]),
     "sf_fit_backward": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sf_last_error": (ctypes.c_char_p, []),
     "sf_channel_counts": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),

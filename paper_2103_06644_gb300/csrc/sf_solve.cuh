@@ -11,10 +11,12 @@
 
 namespace sf {
 
-struct FitOut {
-    float nx, ny, nz, d, curv;
-    float gap;  // (lambda1 - lambda0) / lambda2 of the normalised 3x3 matrix
+template <typename T>
+struct FitOutT {
+    T nx, ny, nz, d, curv;
+    T gap;  // (lambda1 - lambda0) / lambda2 of the normalised 3x3 matrix
 };
+using FitOut = FitOutT<float>;
 
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;
@@ -28,27 +30,49 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return y;
 }
 
+// Elementary functions for the two solve precisions: fast approximations in
+// float32 (the refinement steps absorb their error), IEEE operations in FP64.
+template <typename T> struct Fn;
+template <> struct Fn<float> {
+    static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
+    static __device__ __forceinline__ float rsqrt(float x) { return rsqrt_approx(x); }
+    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float acos(float x) { return acosf(x); }
+    static __device__ __forceinline__ void sincos(float x, float* s, float* c) { __sincosf(x, s, c); }
+    static __device__ __forceinline__ float tiny() { return 1e-36f; }
+    static __device__ __forceinline__ float p2min() { return 1e-20f; }
+};
+template <> struct Fn<double> {
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / ::sqrt(x); }
+    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ double acos(double x) { return ::acos(x); }
+    static __device__ __forceinline__ void sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
+    static __device__ __forceinline__ double tiny() { return 1e-280; }
+    static __device__ __forceinline__ double p2min() { return 1e-40; }
+};
+
 // Null vector of the symmetric matrix M = R - l I: the column of the
 // cofactor matrix adj(M) with the largest norm (each column is a cross
 // product of two rows of M, and adj(M) = det(M) M^{-1} is dominated by the
 // eigenvector of the eigenvalue nearest l).
-__device__ __forceinline__ void null_vector(float r11, float r12, float r13, float r22, float r23, float r33, float l,
-                                            float& v0, float& v1, float& v2) {
-    const float a11 = r11 - l, a22 = r22 - l, a33 = r33 - l;
-    const float c11 = a22 * a33 - r23 * r23, c22 = a11 * a33 - r13 * r13, c33 = a11 * a22 - r12 * r12;
-    const float c12 = r13 * r23 - r12 * a33, c13 = r12 * r23 - r13 * a22, c23 = r12 * r13 - a11 * r23;
-    const float n1 = c11 * c11 + c12 * c12 + c13 * c13;
-    const float n2 = c12 * c12 + c22 * c22 + c23 * c23;
-    const float n3 = c13 * c13 + c23 * c23 + c33 * c33;
-    float b0 = c11, b1 = c12, b2 = c13, nb = n1;
+template <typename T>
+__device__ __forceinline__ void null_vector(T r11, T r12, T r13, T r22, T r23, T r33, T l, T& v0, T& v1, T& v2) {
+    const T a11 = r11 - l, a22 = r22 - l, a33 = r33 - l;
+    const T c11 = a22 * a33 - r23 * r23, c22 = a11 * a33 - r13 * r13, c33 = a11 * a22 - r12 * r12;
+    const T c12 = r13 * r23 - r12 * a33, c13 = r12 * r23 - r13 * a22, c23 = r12 * r13 - a11 * r23;
+    const T n1 = c11 * c11 + c12 * c12 + c13 * c13;
+    const T n2 = c12 * c12 + c22 * c22 + c23 * c23;
+    const T n3 = c13 * c13 + c23 * c23 + c33 * c33;
+    T b0 = c11, b1 = c12, b2 = c13, nb = n1;
     if (n2 > nb) { b0 = c12; b1 = c22; b2 = c23; nb = n2; }
     if (n3 > nb) { b0 = c13; b1 = c23; b2 = c33; nb = n3; }
-    if (!(nb > 1e-36f)) {  // l is (numerically) a double root: any unit vector of the null space
-        b0 = 0.f; b1 = 0.f; b2 = 0.f;
-        if (a11 <= a22 && a11 <= a33) b0 = 1.f; else if (a22 <= a33) b1 = 1.f; else b2 = 1.f;
-        nb = 1.f;
+    if (!(nb > Fn<T>::tiny())) {  // l is (numerically) a double root: any unit vector of the null space
+        b0 = T(0); b1 = T(0); b2 = T(0);
+        if (a11 <= a22 && a11 <= a33) b0 = T(1); else if (a22 <= a33) b1 = T(1); else b2 = T(1);
+        nb = T(1);
     }
-    const float s = rsqrt_approx(nb);
+    const T s = Fn<T>::rsqrt(nb);
     v0 = b0 * s; v1 = b1 * s; v2 = b2 * s;
 }
 
@@ -61,57 +85,60 @@ __device__ __forceinline__ void null_vector(float r11, float r12, float r13, flo
 //  3. Rayleigh quotient lr = v^T R v (insensitive to the cancellation in det R).
 //  4. one step of inverse iteration with shift lr: v <- adj(R - lr I) v.
 // The eigenvector error left is ~|dR| / (lambda1 - lambda0).
-__device__ __forceinline__ void smallest_eigpair(float r11, float r12, float r13, float r22, float r23, float r33,
-                                                 float& v0, float& v1, float& v2, float& l0, float& gap) {
-    const float tr = r11 + r22 + r33;
-    const float s = rcp_approx(tr);
+template <typename T>
+__device__ __forceinline__ void smallest_eigpair(T r11, T r12, T r13, T r22, T r23, T r33, T& v0, T& v1, T& v2, T& l0,
+                                                 T& gap) {
+    const T tr = r11 + r22 + r33;
+    const T s = Fn<T>::rcp(tr);
     r11 *= s; r12 *= s; r13 *= s; r22 *= s; r23 *= s; r33 *= s;
-    const float third = 0.33333333f;
-    const float b11 = r11 - third, b22 = r22 - third, b33 = r33 - third;
-    const float p2 = (b11 * b11 + b22 * b22 + b33 * b33 + 2.f * (r12 * r12 + r13 * r13 + r23 * r23)) * (1.f / 6.f);
-    float lmin = third, lmid = third, lmax = third;
-    if (p2 > 1e-20f) {
-        const float p = sqrtf(p2);
-        const float detB = b11 * (b22 * b33 - r23 * r23) - r12 * (r12 * b33 - r23 * r13) + r13 * (r12 * r23 - b22 * r13);
-        const float q = fminf(1.f, fmaxf(-1.f, 0.5f * detB * rcp_approx(p2 * p)));
-        const float phi = acosf(q) * third;  // in [0, pi/3]
-        float sn, cs;
-        __sincosf(phi, &sn, &cs);
-        lmax = third + 2.f * p * cs;
-        lmin = third - p * (cs + 1.7320508f * sn);
-        lmid = 1.f - lmax - lmin;
+    const T third = T(1) / T(3);
+    const T b11 = r11 - third, b22 = r22 - third, b33 = r33 - third;
+    const T p2 = (b11 * b11 + b22 * b22 + b33 * b33 + T(2) * (r12 * r12 + r13 * r13 + r23 * r23)) * (T(1) / T(6));
+    T lmin = third, lmid = third, lmax = third;
+    if (p2 > Fn<T>::p2min()) {
+        const T p = Fn<T>::sqrt(p2);
+        const T detB = b11 * (b22 * b33 - r23 * r23) - r12 * (r12 * b33 - r23 * r13) + r13 * (r12 * r23 - b22 * r13);
+        T q = T(0.5) * detB * Fn<T>::rcp(p2 * p);
+        q = q > T(1) ? T(1) : (q < T(-1) ? T(-1) : q);
+        const T phi = Fn<T>::acos(q) * third;  // in [0, pi/3]
+        T sn, cs;
+        Fn<T>::sincos(phi, &sn, &cs);
+        lmax = third + T(2) * p * cs;
+        lmin = third - p * (cs + T(1.7320508075688772) * sn);
+        lmid = T(1) - lmax - lmin;
     }
-    float a0, a1, a2;
-    null_vector(r11, r12, r13, r22, r23, r33, lmin, a0, a1, a2);
-    const float t0 = r11 * a0 + r12 * a1 + r13 * a2;
-    const float t1 = r12 * a0 + r22 * a1 + r23 * a2;
-    const float t2 = r13 * a0 + r23 * a1 + r33 * a2;
-    const float lr = a0 * t0 + a1 * t1 + a2 * t2;
+    T a0, a1, a2;
+    null_vector<T>(r11, r12, r13, r22, r23, r33, lmin, a0, a1, a2);
+    const T t0 = r11 * a0 + r12 * a1 + r13 * a2;
+    const T t1 = r12 * a0 + r22 * a1 + r23 * a2;
+    const T t2 = r13 * a0 + r23 * a1 + r33 * a2;
+    const T lr = a0 * t0 + a1 * t1 + a2 * t2;
     // inverse iteration: w = adj(R - lr I) a
     {
-        const float c11 = (r22 - lr) * (r33 - lr) - r23 * r23, c22 = (r11 - lr) * (r33 - lr) - r13 * r13;
-        const float c33 = (r11 - lr) * (r22 - lr) - r12 * r12;
-        const float c12 = r13 * r23 - r12 * (r33 - lr), c13 = r12 * r23 - r13 * (r22 - lr);
-        const float c23 = r12 * r13 - (r11 - lr) * r23;
-        const float w0 = c11 * a0 + c12 * a1 + c13 * a2;
-        const float w1 = c12 * a0 + c22 * a1 + c23 * a2;
-        const float w2 = c13 * a0 + c23 * a1 + c33 * a2;
-        const float nw = w0 * w0 + w1 * w1 + w2 * w2;
-        if (nw > 1e-36f) {
-            const float q = rsqrt_approx(nw);
+        const T c11 = (r22 - lr) * (r33 - lr) - r23 * r23, c22 = (r11 - lr) * (r33 - lr) - r13 * r13;
+        const T c33 = (r11 - lr) * (r22 - lr) - r12 * r12;
+        const T c12 = r13 * r23 - r12 * (r33 - lr), c13 = r12 * r23 - r13 * (r22 - lr);
+        const T c23 = r12 * r13 - (r11 - lr) * r23;
+        const T w0 = c11 * a0 + c12 * a1 + c13 * a2;
+        const T w1 = c12 * a0 + c22 * a1 + c23 * a2;
+        const T w2 = c13 * a0 + c23 * a1 + c33 * a2;
+        const T nw = w0 * w0 + w1 * w1 + w2 * w2;
+        if (nw > Fn<T>::tiny()) {
+            const T q = Fn<T>::rsqrt(nw);
             a0 = w0 * q; a1 = w1 * q; a2 = w2 * q;
         }
     }
     v0 = a0; v1 = a1; v2 = a2;
-    l0 = fmaxf(lr, 0.f);
-    gap = (lmax > 0.f) ? (lmid - lmin) / lmax : 0.f;
+    l0 = lr > T(0) ? lr : T(0);
+    gap = (lmax > T(0)) ? (lmid - lmin) / lmax : T(0);
 }
 
 // Orientation: d > 0 (the camera centre lies on the positive side); d == 0
 // is broken toward n_z < 0, then toward a negative first nonzero component.
-__device__ __forceinline__ void orient(float& nx, float& ny, float& nz, float& d) {
-    bool flip = d < 0.f;
-    if (d == 0.f) flip = (nz > 0.f) || (nz == 0.f && (nx > 0.f || (nx == 0.f && ny > 0.f)));
+template <typename T>
+__device__ __forceinline__ void orient(T& nx, T& ny, T& nz, T& d) {
+    bool flip = d < T(0);
+    if (d == T(0)) flip = (nz > T(0)) || (nz == T(0) && (nx > T(0) || (nx == T(0) && ny > T(0))));
     if (flip) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
 }
 
@@ -132,54 +159,57 @@ __device__ __forceinline__ void orient(float& nx, float& ny, float& nz, float& d
 //   Y = sum y y^T over y = [j - jhat, i - ihat, (what - w)/what],
 // and every entry of Y follows from the centred integer moments below.
 // The offset is d = -(n . mhat) / what.
-struct DispWindow {
-    float R11, R12, R13, R22, R23, R33;  // Schur complement in ray units (K Y K^T)
-    float mx, my;                        // weighted centroid ray mhat = [mx, my, 1]
-    float what;                          // sum w^2 / sum w, in units of qw
-    float wbar;                          // mean w, in units of qw
+template <typename T>
+struct DispWindowT {
+    T R11, R12, R13, R22, R23, R33;  // Schur complement in ray units (K Y K^T)
+    T mx, my;                        // weighted centroid ray mhat = [mx, my, 1]
+    T what;                          // sum w^2 / sum w, in units of qw
+    T wbar;                          // mean w, in units of qw
 };
+using DispWindow = DispWindowT<float>;
 
-__device__ __forceinline__ DispWindow build_disparity(float nf, float fSj, float fSi, float fSjj, float fSji,
-                                                      float fSii, int64_t Sw, int64_t Swj, int64_t Swi, int64_t Sww,
-                                                      float tx, float ty, float a, float b) {
-    // the mask moments are exact integers held in float32 (all < 2^24)
-    const float inv_n = rcp_approx(nf);
+template <typename T>
+__device__ __forceinline__ DispWindowT<T> build_disparity(T nf, T fSj, T fSi, T fSjj, T fSji, T fSii, int64_t Sw,
+                                                          int64_t Swj, int64_t Swi, int64_t Sww, T tx, T ty, T a,
+                                                          T b) {
+    // the mask moments are exact integers held in T (all < 2^24)
+    const T inv_n = Fn<T>::rcp(nf);
     const int n = (int)nf, Sj = (int)fSj, Si = (int)fSi;
     // exact re-centring on an integer m near the mean disparity (m < 2^31)
-    const int m = __float2int_rn((float)Sw * inv_n);
+    const int m = __float2int_rn((float)((T)Sw * inv_n));
     const int64_t T0 = Sw - (int64_t)n * m;
     const int64_t Tww = Sww - (int64_t)m * (Sw + T0);            // sum (w - m)^2
     const int64_t Twj = Swj - (int64_t)m * Sj;                   // sum (w - m) j
     const int64_t Twi = Swi - (int64_t)m * Si;                   // sum (w - m) i
-    const float fT0 = (float)(int)T0;                            // |T0| < 2^31
-    const float t0 = fT0 * inv_n;
-    const float jb = fSj * inv_n, ib = fSi * inv_n;
-    const float Cjj = fSjj - fSj * jb;
-    const float Cji = fSji - fSj * ib;
-    const float Cii = fSii - fSi * ib;
-    const float Cjw = (float)Twj - fSj * t0;
-    const float Ciw = (float)Twi - fSi * t0;
-    const float Cww = (float)Tww - fT0 * t0;
-    const float wbar = (float)m + t0;  // mean disparity (units of qw)
-    const float inv_nw = rcp_approx(nf * wbar);
-    const float dj = Cjw * inv_nw;     // jhat - jbar
-    const float di = Ciw * inv_nw;     // ihat - ibar
-    const float e = Cww * inv_nw;      // what - wbar
-    const float what = wbar + e;
-    const float Yjj = Cjj + nf * dj * dj;
-    const float Yji = Cji + nf * dj * di;
-    const float Yii = Cii + nf * di * di;
-    const float Yjr = -nf * dj;
-    const float Yir = -nf * di;
-    const float iw = rcp_approx(what);
-    const float Yrr = (Cww + nf * e * e) * iw * iw;
-    DispWindow w;
+    const T fT0 = (T)(int)T0;                                    // |T0| < 2^31
+    const T t0 = fT0 * inv_n;
+    const T jb = fSj * inv_n, ib = fSi * inv_n;
+    const T Cjj = fSjj - fSj * jb;
+    const T Cji = fSji - fSj * ib;
+    const T Cii = fSii - fSi * ib;
+    const T Cjw = (T)Twj - fSj * t0;
+    const T Ciw = (T)Twi - fSi * t0;
+    const T Cww = (T)Tww - fT0 * t0;
+    const T wbar = (T)m + t0;  // mean disparity (units of qw)
+    const T inv_nw = Fn<T>::rcp(nf * wbar);
+    const T dj = Cjw * inv_nw;     // jhat - jbar
+    const T di = Ciw * inv_nw;     // ihat - ibar
+    const T e = Cww * inv_nw;      // what - wbar
+    const T what = wbar + e;
+    const T Yjj = Cjj + nf * dj * dj;
+    const T Yji = Cji + nf * dj * di;
+    const T Yii = Cii + nf * di * di;
+    const T Yjr = -nf * dj;
+    const T Yir = -nf * di;
+    const T iw = Fn<T>::rcp(what);
+    const T Yrr = (Cww + nf * e * e) * iw * iw;
+    DispWindowT<T> w;
     w.mx = tx + a * (jb + dj);
     w.my = ty + b * (ib + di);
-    w.R11 = a * a * Yjj + 2.f * a * w.mx * Yjr + w.mx * w.mx * Yrr;
+    w.R11 = a * a * Yjj + T(2) * a * w.mx * Yjr + w.mx * w.mx * Yrr;
     w.R12 = a * b * Yji + a * w.my * Yjr + b * w.mx * Yir + w.mx * w.my * Yrr;
     w.R13 = a * Yjr + w.mx * Yrr;
-    w.R22 = b * b * Yii + 2.f * b * w.my * Yir + w.my * w.my * Yrr;
+    w.R22 = b * b * Yii + T(2) * b * w.my * Yir + w.my * w.my * Yrr;
     w.R23 = b * Yir + w.my * Yrr;
     w.R33 = Yrr;
     w.what = what;
@@ -187,16 +217,17 @@ __device__ __forceinline__ DispWindow build_disparity(float nf, float fSj, float
     return w;
 }
 
-__device__ __forceinline__ FitOut solve_disparity(float nf, float fSj, float fSi, float fSjj, float fSji, float fSii,
-                                                  int64_t Sw, int64_t Swj, int64_t Swi, int64_t Sww, float qw, float tx,
-                                                  float ty, float a, float b) {
-    const DispWindow w = build_disparity(nf, fSj, fSi, fSjj, fSji, fSii, Sw, Swj, Swi, Sww, tx, ty, a, b);
-    FitOut o;
-    float l0;
-    smallest_eigpair(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, l0, o.gap);
+template <typename T = float>
+__device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj, T fSji, T fSii, int64_t Sw,
+                                                      int64_t Swj, int64_t Swi, int64_t Sww, T qw, T tx, T ty, T a,
+                                                      T b) {
+    const DispWindowT<T> w = build_disparity<T>(nf, fSj, fSi, fSjj, fSji, fSii, Sw, Swj, Swi, Sww, tx, ty, a, b);
+    FitOutT<T> o;
+    T l0;
+    smallest_eigpair<T>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, l0, o.gap);
     o.curv = l0;
-    o.d = -(o.nx * w.mx + o.ny * w.my + o.nz) * rcp_approx(w.what) / qw;
-    orient(o.nx, o.ny, o.nz, o.d);
+    o.d = -(o.nx * w.mx + o.ny * w.my + o.nz) * Fn<T>::rcp(w.what) / qw;
+    orient<T>(o.nx, o.ny, o.nz, o.d);
     return o;
 }
 
@@ -206,39 +237,40 @@ __device__ __forceinline__ FitOut solve_disparity(float nf, float fSj, float fSi
 // P_q = Z_q m_q = T [Z j, Z i, Z] with T = [[a, 0, tx], [0, b, ty], [0, 0, 1]],
 // so the covariance of the points is T C T^T, C the covariance of
 // [z j, z i, z] (re-centred on an integer near the mean depth first).
-__device__ __forceinline__ FitOut solve_standard(float nf, int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
-                                                 int64_t Szzj, int64_t Szzi, int64_t Szzjj, int64_t Szzji,
-                                                 int64_t Szzii, float qz, float tx, float ty, float a, float b) {
-    const float inv_n = rcp_approx(nf);
+template <typename T = float>
+__device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
+                                                     int64_t Szzj, int64_t Szzi, int64_t Szzjj, int64_t Szzji,
+                                                     int64_t Szzii, T qz, T tx, T ty, T a, T b) {
+    const T inv_n = Fn<T>::rcp(nf);
     const int n = (int)nf;
-    const int m = __float2int_rn((float)Sz * inv_n);            // m < 2^31
+    const int m = __float2int_rn((float)((T)Sz * inv_n));       // m < 2^31
     const int64_t T0 = Sz - (int64_t)n * m;
     const int64_t Tzz = Szz - (int64_t)m * (Sz + T0);           // sum (z - m)^2
     const int64_t Tzj = Szzj - (int64_t)m * Szj;                // sum z j (z - m)
     const int64_t Tzi = Szzi - (int64_t)m * Szi;                // sum z i (z - m)
-    const float t0 = (float)(int)T0 * inv_n;                    // zbar - m
-    const float fSzj = (float)Szj, fSzi = (float)Szi;
-    const float Czz = (float)Tzz - (float)(int)T0 * t0;
-    const float Cjz = (float)Tzj - fSzj * t0;
-    const float Ciz = (float)Tzi - fSzi * t0;
-    const float qj = fSzj * inv_n, qi = fSzi * inv_n;           // means of z j, z i
-    const float Cjj = (float)Szzjj - fSzj * qj;
-    const float Cji = (float)Szzji - fSzj * qi;
-    const float Cii = (float)Szzii - fSzi * qi;
-    const float R11 = a * a * Cjj + 2.f * a * tx * Cjz + tx * tx * Czz;
-    const float R12 = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
-    const float R13 = a * Cjz + tx * Czz;
-    const float R22 = b * b * Cii + 2.f * b * ty * Ciz + ty * ty * Czz;
-    const float R23 = b * Ciz + ty * Czz;
-    const float R33 = Czz;
-    FitOut o;
-    float l0;
-    smallest_eigpair(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, l0, o.gap);
+    const T t0 = (T)(int)T0 * inv_n;                            // zbar - m
+    const T fSzj = (T)Szj, fSzi = (T)Szi;
+    const T Czz = (T)Tzz - (T)(int)T0 * t0;
+    const T Cjz = (T)Tzj - fSzj * t0;
+    const T Ciz = (T)Tzi - fSzi * t0;
+    const T qj = fSzj * inv_n, qi = fSzi * inv_n;               // means of z j, z i
+    const T Cjj = (T)Szzjj - fSzj * qj;
+    const T Cji = (T)Szzji - fSzj * qi;
+    const T Cii = (T)Szzii - fSzi * qi;
+    const T R11 = a * a * Cjj + T(2) * a * tx * Cjz + tx * tx * Czz;
+    const T R12 = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
+    const T R13 = a * Cjz + tx * Czz;
+    const T R22 = b * b * Cii + T(2) * b * ty * Ciz + ty * ty * Czz;
+    const T R23 = b * Ciz + ty * Czz;
+    const T R33 = Czz;
+    FitOutT<T> o;
+    T l0;
+    smallest_eigpair<T>(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, l0, o.gap);
     o.curv = l0;
-    const float zb = (float)m + t0;
-    const float px = a * qj + tx * zb, py = b * qi + ty * zb;
+    const T zb = (T)m + t0;
+    const T px = a * qj + tx * zb, py = b * qi + ty * zb;
     o.d = -(o.nx * px + o.ny * py + o.nz * zb) * qz;
-    orient(o.nx, o.ny, o.nz, o.d);
+    orient<T>(o.nx, o.ny, o.nz, o.d);
     return o;
 }
 

@@ -402,7 +402,9 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
                                                           void* __restrict__ planes_base, Calib cal,
                                                           int min_valid, int require_center, int band,
                                                           float* __restrict__ normals, float* __restrict__ offsets,
-                                                          float* __restrict__ curvature, int32_t* __restrict__ counts) {
+                                                          float* __restrict__ curvature, int32_t* __restrict__ counts,
+                                                          float tau, unsigned long long* __restrict__ flags,
+                                                          unsigned* __restrict__ flag_count) {
     const int f = blockIdx.z;
     const int x = blockIdx.x * kVThreads + threadIdx.x;
     if (x >= W) return;
@@ -431,11 +433,66 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
                 fo_ = solve_standard((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
                                      S.Szzii, q, tx, cal.ty[y], cal.a, cal.b);
             nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
+            if (flags && !(fo_.gap >= tau)) {
+                // near-degenerate window: queue it for the FP64 re-solve
+                const unsigned mask = __activemask();
+                const int leader = __ffs(mask) - 1;
+                const int lane = threadIdx.x & 31;
+                unsigned base = 0;
+                if (lane == leader) base = atomicAdd(flag_count, (unsigned)__popc(mask));
+                base = __shfl_sync(mask, base, leader);
+                const unsigned slot = base + __popc(mask & ((1u << lane) - 1u));
+                flags[slot] = ((unsigned long long)f << 48) | ((unsigned long long)y << 24) | (unsigned long long)x;
+            }
         }
         normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
         offsets[oi] = d; curvature[oi] = cu;
         if (counts) counts[oi] = n;
         if (y + 1 < y1) S.slide(pb, Wp, H, y, r);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 re-solve of the queued windows: the exact window moments are
+// recomputed from the scratch planes (the 2r + 1 rows of the pixel's column),
+// then the whole solve runs in double precision and overwrites the outputs.
+// The moments are exact integers, so this removes every float32 rounding of
+// the solve; only the fixed-point quantisation of the depth remains.
+// ---------------------------------------------------------------------------
+template <int DT, int M>
+__global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, float scale,
+                                                      const unsigned* __restrict__ vmax_bits, int bits, int Wp,
+                                                      size_t plane_elems, int nframes, void* __restrict__ planes_base,
+                                                      Calib cal, const double* __restrict__ rays,
+                                                      const unsigned long long* __restrict__ flags,
+                                                      const unsigned* __restrict__ flag_count,
+                                                      float* __restrict__ normals, float* __restrict__ offsets,
+                                                      float* __restrict__ curvature) {
+    const unsigned count = *flag_count;
+    const Planes P(planes_base, nframes, plane_elems);
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
+        const unsigned long long e = flags[idx];
+        const int f = (int)(e >> 48), y = (int)((e >> 24) & 0xffffff), x = (int)(e & 0xffffff);
+        const size_t pb = (size_t)f * plane_elems + x;
+        const double q = (double)quantum<DT, M>(vmax_bits[f], bits, scale);
+        const double tx = rays[x], ty = rays[W + y];  // FP64 ray tangents
+        const double a = rays[W + H], b = rays[W + H + 1];
+        FitOutT<double> o;
+        if constexpr (M == SF_METHOD_DISPARITY) {
+            DispState S(P);
+            S.init(pb, Wp, H, y, r);
+            o = solve_disparity<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj, (double)S.Sji,
+                                        (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty, a, b);
+        } else {
+            StdState S(P);
+            S.init(pb, Wp, H, y, r);
+            o = solve_standard<double>((double)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
+                                       S.Szzii, q, tx, ty, a, b);
+        }
+        const size_t oi = (size_t)f * W * H + (size_t)y * W + x;
+        normals[3 * oi] = (float)o.nx; normals[3 * oi + 1] = (float)o.ny; normals[3 * oi + 2] = (float)o.nz;
+        offsets[oi] = (float)o.d;
+        curvature[oi] = (float)o.curv;
     }
 }
 
@@ -706,6 +763,13 @@ struct sf_ctx {
     size_t d_io_bytes = 0;
     float* adj = nullptr;      // backward: per-window adjoint planes
     size_t adj_bytes = 0;
+    // precision fallback
+    int precision_mode = 0;    // 0 float32 solve, 1 + FP64 re-solve where gap < tau, 2 FP64 everywhere
+    float tau = 1e-2f;
+    unsigned long long* flags = nullptr;
+    size_t flags_cap = 0;      // entries
+    unsigned* flag_count = nullptr;
+    double* rays64 = nullptr;  // [W] tx, [H] ty, 1/fx, 1/fy in FP64
     // profiling: (stage, start event, stop event) per recorded launch
     bool profiling = false;
     struct Rec { int stage; cudaEvent_t a, b; };
@@ -790,10 +854,20 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
         const int band = vertical_band(c, nfr);
         dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
         sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
+        const bool fb = c->precision_mode > 0 && c->flags;
+        if (fb) SF_CUDA(cudaMemsetAsync(c->flag_count, 0, sizeof(unsigned), st));
+        const float tau = c->precision_mode == 2 ? INFINITY : c->tau;
         sf::vpass_kernel<DT, M><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
                                                                bits, raw_z, c->Wp, c->plane_elems, c->planes, cal,
                                                                c->min_valid, c->require_center, band, normals,
-                                                               offsets, curv, counts);
+                                                               offsets, curv, counts, tau, fb ? c->flags : nullptr,
+                                                               c->flag_count);
+        if (fb) {
+            StageTimer t2(c, 3, st);
+            sf::resolve_kernel<DT, M><<<152 * 8, 128, 0, st>>>(c->W, c->H, c->r, c->depth_scale, c->vmax, bits, c->Wp,
+                                                              c->plane_elems, nfr, c->planes, cal, c->rays64,
+                                                              c->flags, c->flag_count, normals, offsets, curv);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -897,6 +971,21 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
     c->max_frames_per_pass = 64;
     e = cudaMalloc(&c->vmax, sizeof(unsigned) * 64);
     if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create vmax"); }
+    e = cudaMalloc(&c->flag_count, sizeof(unsigned));
+    if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create flag counter"); }
+    {
+        // FP64 ray tables for the precision fallback
+        double* h = (double*)malloc(sizeof(double) * (W + H + 2));
+        if (!h) { sf_destroy(c); return fail(SF_ERR_ALLOC, "host table allocation failed"); }
+        for (int x = 0; x < W; ++x) h[x] = (x + K->dx - K->cx) / K->fx;
+        for (int y = 0; y < H; ++y) h[W + y] = (y + K->dy - K->cy) / K->fy;
+        h[W + H] = 1.0 / K->fx;
+        h[W + H + 1] = 1.0 / K->fy;
+        e = cudaMalloc(&c->rays64, sizeof(double) * (W + H + 2));
+        if (e == cudaSuccess) e = cudaMemcpy(c->rays64, h, sizeof(double) * (W + H + 2), cudaMemcpyHostToDevice);
+        free(h);
+        if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create FP64 rays"); }
+    }
     sf_status s = ensure_planes(c, 1);
     if (s != SF_OK) { sf_destroy(c); return s; }
     {
@@ -961,6 +1050,17 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
     int per = std::min(c->max_frames_per_pass, 64);
     sf_status s = ensure_planes(c, std::min(per, n_frames));
     if (s != SF_OK) return s;
+    if (c->precision_mode > 0) {
+        const size_t cap = fe * (size_t)std::min(per, n_frames);  // every pixel may be queued
+        if (c->flags_cap < cap) {
+            if (c->flags) cudaFree(c->flags);
+            c->flags = nullptr;
+            c->flags_cap = 0;
+            cudaError_t e = cudaMalloc(&c->flags, cap * sizeof(unsigned long long));
+            if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "precision-fallback queue of %zu entries failed", cap);
+            c->flags_cap = cap;
+        }
+    }
     for (int f0 = 0; f0 < n_frames; f0 += per) {
         const int nfr = std::min(per, n_frames - f0);
         const void* dp = static_cast<const char*>(depth) + dbytes * fe * f0;
@@ -1024,6 +1124,15 @@ sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals
     memcpy(offsets, ho + 12 * fe * n_frames, 4 * fe * n_frames);
     memcpy(curvature, ho + 16 * fe * n_frames, 4 * fe * n_frames);
     if (counts) memcpy(counts, ho + 20 * fe * n_frames, 4 * fe * n_frames);
+    return SF_OK;
+}
+
+sf_status sf_set_precision(sf_ctx* c, int mode, float tau) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    if (mode < 0 || mode > 2) return fail(SF_ERR_INVALID_ARG, "precision mode %d must be 0, 1 or 2", mode);
+    if (mode == 1 && !(tau > 0.f && tau <= 1.f)) return fail(SF_ERR_INVALID_ARG, "tau must be in (0, 1]");
+    c->precision_mode = mode;
+    if (mode == 1) c->tau = tau;
     return SF_OK;
 }
 
@@ -1109,6 +1218,9 @@ sf_status sf_destroy(sf_ctx* c) {
     if (c->d_io) cudaFree(c->d_io);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->adj) cudaFree(c->adj);
+    if (c->flags) cudaFree(c->flags);
+    if (c->flag_count) cudaFree(c->flag_count);
+    if (c->rays64) cudaFree(c->rays64);
     delete c;
     return SF_OK;
 }
