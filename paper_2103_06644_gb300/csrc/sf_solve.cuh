@@ -30,14 +30,34 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return y;
 }
 
+// arccos on [-1, 1] in the form of Abramowitz & Stegun 4.4.45,
+// acos(x) = sqrt(1 - x) P(x) for x in [0, 1] and pi - acos(-x) below 0, with
+// P a degree-6 polynomial fitted here by iterated weighted least squares
+// (max error 9e-8 in exact arithmetic, ~1.5e-6 evaluated in float32).  The
+// eigenvalue estimate it feeds is refined afterwards, so this accuracy is
+// ample.
+__device__ __forceinline__ float acos_fast(float x) {
+    const float a = fabsf(x);
+    float p = 2.611499099e-03f;
+    p = fmaf(p, a, -1.200276181e-02f);
+    p = fmaf(p, a, 2.776222800e-02f);
+    p = fmaf(p, a, -4.919708793e-02f);
+    p = fmaf(p, a, 8.883580176e-02f);
+    p = fmaf(p, a, -2.145910804e-01f);
+    p = fmaf(p, a, 1.570796239e+00f);
+    const float u = 1.f - a;
+    const float r = (u > 0.f) ? u * rsqrt_approx(u) * p : 0.f;
+    return (x >= 0.f) ? r : 3.14159265f - r;
+}
+
 // Elementary functions for the two solve precisions: fast approximations in
 // float32 (the refinement steps absorb their error), IEEE operations in FP64.
 template <typename T> struct Fn;
 template <> struct Fn<float> {
     static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
     static __device__ __forceinline__ float rsqrt(float x) { return rsqrt_approx(x); }
-    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
-    static __device__ __forceinline__ float acos(float x) { return acosf(x); }
+    static __device__ __forceinline__ float sqrt(float x) { return x > 0.f ? x * rsqrt_approx(x) : 0.f; }
+    static __device__ __forceinline__ float acos(float x) { return acos_fast(x); }
     static __device__ __forceinline__ void sincos(float x, float* s, float* c) { __sincosf(x, s, c); }
     static __device__ __forceinline__ float tiny() { return 1e-36f; }
     static __device__ __forceinline__ float p2min() { return 1e-20f; }
@@ -53,20 +73,20 @@ template <> struct Fn<double> {
 };
 
 // Null vector of the symmetric matrix M = R - l I: the column of the
-// cofactor matrix adj(M) with the largest norm (each column is a cross
-// product of two rows of M, and adj(M) = det(M) M^{-1} is dominated by the
-// eigenvector of the eigenvalue nearest l).
+// cofactor matrix adj(M) with the largest diagonal entry (each column is a
+// cross product of two rows of M; adj(M) = det(M) M^{-1} is dominated by
+// (l1 - l)(l2 - l) v0 v0^T, whose diagonal is largest where |v0_i| is, so
+// that column is v0 scaled by at least 1/sqrt(3) of its largest value).
 template <typename T>
 __device__ __forceinline__ void null_vector(T r11, T r12, T r13, T r22, T r23, T r33, T l, T& v0, T& v1, T& v2) {
     const T a11 = r11 - l, a22 = r22 - l, a33 = r33 - l;
     const T c11 = a22 * a33 - r23 * r23, c22 = a11 * a33 - r13 * r13, c33 = a11 * a22 - r12 * r12;
     const T c12 = r13 * r23 - r12 * a33, c13 = r12 * r23 - r13 * a22, c23 = r12 * r13 - a11 * r23;
-    const T n1 = c11 * c11 + c12 * c12 + c13 * c13;
-    const T n2 = c12 * c12 + c22 * c22 + c23 * c23;
-    const T n3 = c13 * c13 + c23 * c23 + c33 * c33;
-    T b0 = c11, b1 = c12, b2 = c13, nb = n1;
-    if (n2 > nb) { b0 = c12; b1 = c22; b2 = c23; nb = n2; }
-    if (n3 > nb) { b0 = c13; b1 = c23; b2 = c33; nb = n3; }
+    const T d1 = c11 < T(0) ? -c11 : c11, d2 = c22 < T(0) ? -c22 : c22, d3 = c33 < T(0) ? -c33 : c33;
+    T b0 = c11, b1 = c12, b2 = c13, db = d1;
+    if (d2 > db) { b0 = c12; b1 = c22; b2 = c23; db = d2; }
+    if (d3 > db) { b0 = c13; b1 = c23; b2 = c33; }
+    T nb = b0 * b0 + b1 * b1 + b2 * b2;
     if (!(nb > Fn<T>::tiny())) {  // l is (numerically) a double root: any unit vector of the null space
         b0 = T(0); b1 = T(0); b2 = T(0);
         if (a11 <= a22 && a11 <= a33) b0 = T(1); else if (a22 <= a33) b1 = T(1); else b2 = T(1);
