@@ -121,6 +121,34 @@ def cpu_oracle_sample(time_budget_s: float = 15.0):
                       "FP64 direct window sums, OpenMP over rows" % (n, px), "seconds": dt}
 
 
+def mixed_batch_report(dev, timed):
+    """64 frames, resolutions uniform over {320x240, 640x480, 1280x720, 1920x1080}, windows over
+    {5, 7, 11, 21}, intrinsics scaled with the resolution, 0-15 % blob holes: one persistent launch per
+    stage replayed from a CUDA graph, tile shapes from the autotuner."""
+    import torch
+
+    from paper_2103_06644_gb300 import SurfaceFitBatch, autotune
+
+    spec = scenes.mixed_batch_spec(64)
+    frames = []
+    for i, (W, H, k) in enumerate(spec):
+        depth, intr = scenes.mixed_frame(scenes.BASE_SEED + 800 + i, W, H)
+        frames.append(dict(W=W, H=H, window=k, intrinsics=intr.as_tuple(), depth=torch.from_numpy(depth).to(dev)))
+    t0 = time.perf_counter()
+    tuned = autotune.tune(frames)
+    tune_s = time.perf_counter() - t0
+    b = SurfaceFitBatch(tuned, use_graph=True)
+    for _ in range(3):
+        b.run()
+    ms = timed(20, b.run)
+    rep = {"workload": "64 mixed frames (320x240..1920x1080, k in {5,7,11,21}), disparity form, CUDA graph",
+           "pixels": b.pixels, "value": b.pixels / (ms / 1000) / 1e6, "unit": UNIT, "ms_per_step": ms,
+           "launches_per_step": b.launches, "autotune_seconds": tune_s,
+           "tiles": sorted({(f["W"], f["H"], f["window"], f["hseg"], f["vband"]) for f in tuned})}
+    b.close()
+    return rep
+
+
 def precision_report(group, dev):
     """Errors per output against the FP64 oracle on the first 1080p frame, for the float32 solve
     (mode 0), the FP64 re-solve of windows with gamma < 1e-2 (mode 1) and the FP64 solve (mode 2).
@@ -379,6 +407,7 @@ def main():
             diff_step()
         t_fb = timed(20, diff_step)
         t_f = timed(20, lambda: fd.fit(dd))
+        line["mixed_batch"] = mixed_batch_report(dev, timed)
         line["differentiation_k9"] = {"workload": "16x640x480 f32, k=9, loss |n-n*|^2 + 0.1 kappa",
                                       "value": nd * 307200 / (t_fb / 1000) / 1e6, "unit": UNIT,
                                       "ms_per_step_fwd_bwd": t_fb, "ms_forward": t_f}

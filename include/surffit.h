@@ -168,6 +168,52 @@ sf_status sf_fit_host(sf_ctx* ctx, int n_frames, const void* depth, float* norma
 sf_status sf_fit_backward(sf_ctx* ctx, int n_frames, const void* depth, const float* g_normals, const float* g_offsets,
                           const float* g_curvature, float* g_depth, void* stream);
 
+/*
+ * Mixed-resolution batches.  One frame of a batch: its size, window and
+ * intrinsics, its device buffers (layouts as for sf_fit), and optionally its
+ * tile shape (0 = default): hseg in {32, 64, 128} columns per horizontal
+ * tile, vband in [8, 1024] rows per vertical band.
+ */
+typedef struct {
+    int W, H, window;
+    sf_intrinsics K;
+    const void* depth;
+    float* normals;
+    float* offsets;
+    float* curvature;
+    int hseg, vband;
+} sf_batch_frame;
+
+typedef struct sf_batch sf_batch;
+
+/*
+ * sf_batch_create -- prepare the fit of n_frames frames of any sizes and
+ * windows as one pass: a table of per-frame descriptors and of work items
+ * (tiles) is uploaded once, and every pass runs one persistent launch per
+ * stage (quantum, horizontal moments, vertical moments + solve) whose CTAs
+ * claim items with an atomic counter.  With use_graph != 0 the pass is
+ * captured once in a CUDA graph and sf_batch_run replays it.  The device
+ * buffers named in `frames` are bound for the life of the batch: refill them
+ * and run again.  Method, depth type and validity rule are shared by all
+ * frames (disparity or standard implicit fit).  Synchronises once.
+ */
+sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method, int depth_type, float depth_scale,
+                          int min_valid, int require_center_valid, int use_graph, sf_batch** out);
+/* sf_batch_run -- one pass of the batch on `stream` (asynchronous). */
+sf_status sf_batch_run(sf_batch* batch, void* stream);
+/* sf_batch_info -- total pixels (plane fits) per pass and kernel launches per pass. */
+sf_status sf_batch_info(const sf_batch* batch, long long* pixels, int* launches);
+/* sf_batch_destroy -- free the batch (NULL is a no-op). */
+sf_status sf_batch_destroy(sf_batch* batch);
+
+/*
+ * sf_set_tiles -- tile shape of a context: hseg in {32, 64, 128} columns per
+ * horizontal tile, vband rows per vertical band (0 = chosen from the grid
+ * size, else 8..1024).  Results do not depend on the tiles: the window sums
+ * are exact.
+ */
+sf_status sf_set_tiles(sf_ctx* ctx, int hseg, int vband);
+
 /* sf_destroy -- free the context and everything it owns (NULL is a no-op). */
 sf_status sf_destroy(sf_ctx* ctx);
 

@@ -16,7 +16,8 @@ import numpy as np
 from . import _native
 from ._native import SurfFitError
 
-__all__ = ["SurfaceFitter", "SurfFitError", "METHODS", "DEPTH_TYPES", "channel_counts", "version"]
+__all__ = ["SurfaceFitter", "SurfaceFitBatch", "SurfFitError", "METHODS", "DEPTH_TYPES", "channel_counts",
+           "version"]
 
 METHODS = {"disparity": 0, "standard": 1, "explicit_disparity": 2, "explicit_standard": 3}
 DEPTH_TYPES = {"f32": 0, "u16": 1}
@@ -70,6 +71,10 @@ class SurfaceFitter:
         _native.check(_native.lib().sf_set_params(self._h, METHODS[method], DEPTH_TYPES[depth_type],
                                                   float(depth_scale), int(min_valid), int(bool(require_center))))
         self.method, self.depth_type, self.depth_scale = method, depth_type, float(depth_scale)
+
+    def set_tiles(self, hseg: int = 64, vband: int = 0) -> None:
+        """Tile shape: hseg in {32, 64, 128} columns, vband rows per band (0 = automatic)."""
+        _native.check(_native.lib().sf_set_tiles(self._h, int(hseg), int(vband)))
 
     def set_precision(self, mode: int, tau: float = 1e-2) -> None:
         """0: float32 solve; 1: + FP64 re-solve where gamma < tau; 2: FP64 solve everywhere."""
@@ -172,6 +177,61 @@ class SurfaceFitter:
 
     def __exit__(self, *a):
         self.close()
+
+
+class SurfaceFitBatch:
+    """Frames of mixed sizes and windows fitted as one pass (``sf_batch_*``).
+
+    ``frames``: list of dicts with keys W, H, window, intrinsics (4 or 6
+    values), depth (CUDA tensor [H, W]) and optionally hseg, vband (tile
+    shape).  Output tensors are allocated here and stay bound to the batch
+    (``outputs[i] = (normals, offsets, curvature)``); refill the depth tensors
+    in place and call ``run()`` again.
+    """
+
+    def __init__(self, frames, method: str = "disparity", depth_type: str = "f32", depth_scale: float = 1e-3,
+                 min_valid: int = 3, require_center: bool = True, use_graph: bool = True):
+        import torch
+
+        self.frames = frames
+        self.outputs = []
+        arr = (_native.BatchFrame * len(frames))()
+        for i, fr in enumerate(frames):
+            W, H, k = int(fr["W"]), int(fr["H"]), int(fr["window"])
+            it = tuple(float(v) for v in fr["intrinsics"])
+            it = it + (0.0, 0.0) if len(it) == 4 else it
+            d = fr["depth"]
+            if not d.is_cuda or not d.is_contiguous() or tuple(d.shape) != (H, W):
+                raise ValueError("frame %d: depth must be a contiguous CUDA tensor of shape (H, W)" % i)
+            dev = d.device
+            out = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev), torch.empty((H, W), device=dev))
+            self.outputs.append(out)
+            arr[i] = _native.BatchFrame(W, H, k, _native.Intrinsics(*it), d.data_ptr(), out[0].data_ptr(),
+                                        out[1].data_ptr(), out[2].data_ptr(), int(fr.get("hseg", 0)),
+                                        int(fr.get("vband", 0)))
+        h = ctypes.c_void_p()
+        _native.check(_native.lib().sf_batch_create(arr, len(frames), METHODS[method], DEPTH_TYPES[depth_type],
+                                                    float(depth_scale), int(min_valid), int(bool(require_center)),
+                                                    int(bool(use_graph)), ctypes.byref(h)))
+        self._h = h
+        px = ctypes.c_longlong()
+        nl = ctypes.c_int()
+        _native.check(_native.lib().sf_batch_info(self._h, ctypes.byref(px), ctypes.byref(nl)))
+        self.pixels, self.launches = int(px.value), int(nl.value)
+
+    def run(self, stream=None) -> None:
+        _native.check(_native.lib().sf_batch_run(self._h, _stream_handle(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _native.lib().sf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _make_function():

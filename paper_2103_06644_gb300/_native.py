@@ -26,6 +26,12 @@ class Intrinsics(ctypes.Structure):
                 ("cy", ctypes.c_double), ("dx", ctypes.c_double), ("dy", ctypes.c_double)]
 
 
+class BatchFrame(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int), ("H", ctypes.c_int), ("window", ctypes.c_int), ("K", Intrinsics),
+                ("depth", ctypes.c_void_p), ("normals", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("curvature", ctypes.c_void_p), ("hseg", ctypes.c_int), ("vband", ctypes.c_int)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -40,6 +46,11 @@ SIGNATURES = {
     "sf_fit_host": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sf_destroy": (_I, [_VP]),
     "sf_set_precision": (_I, [_VP, _I, _F]),
+    "sf_set_tiles": (_I, [_VP, _I, _I]),
+    "sf_batch_create": (_I, [ctypes.POINTER(BatchFrame), _I, _I, _I, _F, _I, _I, _I, ctypes.POINTER(_VP)]),
+    "sf_batch_run": (_I, [_VP, _VP]),
+    "sf_batch_info": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I)]),
+    "sf_batch_destroy": (_I, [_VP]),
     "sf_fit_backward": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sf_last_error": (ctypes.c_char_p, []),
     "sf_channel_counts": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),

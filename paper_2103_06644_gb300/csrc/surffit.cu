@@ -39,7 +39,7 @@ namespace sf {
 
 constexpr int kMaxR = (SF_MAX_WINDOW - 1) / 2;
 constexpr int kHThreads = 128;   // rows per hpass block
-constexpr int kHSeg = 64;        // output columns per hpass thread
+constexpr int kHSeg = 64;        // default output columns per hpass thread (runtime: 32..128)
 constexpr int kVThreads = 128;   // columns per vpass block
 
 // ---------------------------------------------------------------------------
@@ -152,14 +152,16 @@ __global__ void __launch_bounds__(256) range_kernel(const void* __restrict__ dep
 // Standard planes:
 //   hc int32 count, z0 int64 sum z, z1 int64 sum z j,
 //   b0 int64 sum z^2, b1 int64 sum z^2 j, b2 int64 sum z^2 j^2
+// Frame f of a call occupies elements [pofs_f, pofs_f + Wp_f * H_f) of every
+// plane; `stride` is the number of elements in one plane (all frames).
 struct Planes {
     int32_t* p32;       // the int32 plane
     int64_t* p64;       // first int64 plane; plane c is p64 + c * stride
-    size_t stride;      // n_frames * plane_elems
-    __host__ __device__ Planes(void* base, size_t nf, size_t plane_elems)
+    size_t stride;
+    __host__ __device__ Planes(void* base, size_t stride_)
         : p32(reinterpret_cast<int32_t*>(base)),
-          p64(reinterpret_cast<int64_t*>(reinterpret_cast<int32_t*>(base) + nf * plane_elems)),
-          stride(nf * plane_elems) {}
+          p64(reinterpret_cast<int64_t*>(reinterpret_cast<int32_t*>(base) + stride_)),
+          stride(stride_) {}
     __device__ __forceinline__ int64_t* c64(int c) const { return p64 + (size_t)c * stride; }
 };
 
@@ -196,25 +198,21 @@ __device__ __forceinline__ void slide2(T& S0, T& S1, T out, T in, int r) {
 // 2. hpass: block = 128 rows x 64 output columns, tile of fixed-point values
 //    staged in shared memory with coalesced loads, one thread per row.
 // ---------------------------------------------------------------------------
+// Horizontal moments of one tile: rows [y0, y0 + 128) x output columns
+// [x0, x0 + seg) of one frame.  `depth` points at the frame, `pofs` is the
+// frame's offset in the planes; `tile` is shared memory of
+// kHThreads * ((seg + 2r) | 1) ints.
 template <int DT, int M>
-__global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict__ depth, int W, int H, int r,
-                                                          float scale, const unsigned* __restrict__ vmax_bits,
-                                                          int bits, int raw_z, int Wp, size_t plane_elems,
-                                                          void* planes_base) {
-    extern __shared__ int tile[];
-    const int f = blockIdx.z;
-    const int x0 = blockIdx.x * kHSeg;
-    const int y0 = blockIdx.y * kHThreads;
-    const int IW = kHSeg + 2 * r;
+__device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W, int H, int r, float sc, int Wp,
+                                           const Planes& P, size_t pofs, int x0, int y0, int seg, int* tile) {
+    const int IW = seg + 2 * r;
     const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
-    const float sc = ldexpf(1.f, quant_exponent(vmax_bits[f], bits));  // 2^e, exact
-    const size_t fbase = (size_t)f * W * H;
     const int rows = min(kHThreads, H - y0);
     {
         // warp w loads rows w, w + 4, ...; lanes sweep the row (coalesced)
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int ry = warp; ry < rows; ry += kHThreads / 32) {
-            const size_t rbase = fbase + (size_t)(y0 + ry) * W;
+            const size_t rbase = (size_t)(y0 + ry) * W;
             for (int cx = lane; cx < IW; cx += 32) {
                 const int x = x0 - r + cx;
                 int v = -1;
@@ -224,76 +222,90 @@ __global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict
         }
     }
     __syncthreads();
-    if ((int)threadIdx.x >= rows) return;
-    const int y = y0 + threadIdx.x;
-    const int* row = tile + threadIdx.x * pitch;
-    const int xend = min(x0 + kHSeg, W);
-    const size_t obase = (size_t)f * plane_elems + (size_t)y * Wp;
-
-    // channel state: mask moments (count, sum j, sum j^2) and value moments
-    int h0 = 0, h1 = 0, h2 = 0;
-    int64_t a0 = 0, a1 = 0;          // sum v, sum v j
-    int64_t s0 = 0, s1 = 0, s2 = 0;  // sum v^2, sum v^2 j, sum v^2 j^2 (s1, s2: standard only)
-    for (int j = -r; j <= r; ++j) {
-        const int v = row[j + r];
-        if (v >= 0) {
-            const int64_t vv = (int64_t)v * v;
-            h0 += 1; h1 += j; h2 += j * j;
-            a0 += v; a1 += (int64_t)v * j;
-            s0 += vv;
-            if (M == SF_METHOD_STANDARD) { s1 += vv * j; s2 += vv * (j * j); }
+    if ((int)threadIdx.x < rows) {
+        const int y = y0 + threadIdx.x;
+        const int* row = tile + threadIdx.x * pitch;
+        const int xend = min(x0 + seg, W);
+        const size_t obase = pofs + (size_t)y * Wp;
+        // channel state: mask moments (count, sum j, sum j^2) and value moments
+        int h0 = 0, h1 = 0, h2 = 0;
+        int64_t a0 = 0, a1 = 0;          // sum v, sum v j
+        int64_t s0 = 0, s1 = 0, s2 = 0;  // sum v^2, sum v^2 j, sum v^2 j^2 (s1, s2: standard only)
+        for (int j = -r; j <= r; ++j) {
+            const int v = row[j + r];
+            if (v >= 0) {
+                const int64_t vv = (int64_t)v * v;
+                h0 += 1; h1 += j; h2 += j * j;
+                a0 += v; a1 += (int64_t)v * j;
+                s0 += vv;
+                if (M == SF_METHOD_STANDARD) { s1 += vv * j; s2 += vv * (j * j); }
+            }
         }
-    }
-    const Planes P(planes_base, gridDim.z, plane_elems);
-    for (int xb = x0; xb < xend; xb += 4) {
-        int32_t hmv[4];
-        int64_t c0v[4], c1v[4], c2v[4], c3v[4], c4v[4];
+        for (int xb = x0; xb < xend; xb += 4) {
+            int32_t hmv[4];
+            int64_t c0v[4], c1v[4], c2v[4], c3v[4], c4v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int x = xb + u;
-            if (M == SF_METHOD_DISPARITY) hmv[u] = pack_mask(h0, h1, h2);
-            else hmv[u] = h0;
-            c0v[u] = a0; c1v[u] = a1; c2v[u] = s0; c3v[u] = s1; c4v[u] = s2;
-            if (x + 1 < xend) {
-                const int vo = row[x - x0];              // column x - r leaves
-                const int vi = row[x - x0 + 2 * r + 1];  // column x + r + 1 enters
-                const int mo = vo >= 0, mi = vi >= 0;
-                slide3(h0, h1, h2, mo, mi, r);
-                const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
-                slide2(a0, a1, co, ci, r);
-                const int64_t qo = co * co, qi = ci * ci;
-                if (M == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
-                else s0 = s0 - qo + qi;
+            for (int u = 0; u < 4; ++u) {
+                const int x = xb + u;
+                if (M == SF_METHOD_DISPARITY) hmv[u] = pack_mask(h0, h1, h2);
+                else hmv[u] = h0;
+                c0v[u] = a0; c1v[u] = a1; c2v[u] = s0; c3v[u] = s1; c4v[u] = s2;
+                if (x + 1 < xend) {
+                    const int vo = row[x - x0];              // column x - r leaves
+                    const int vi = row[x - x0 + 2 * r + 1];  // column x + r + 1 enters
+                    const int mo = vo >= 0, mi = vi >= 0;
+                    slide3(h0, h1, h2, mo, mi, r);
+                    const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
+                    slide2(a0, a1, co, ci, r);
+                    const int64_t qo = co * co, qi = ci * ci;
+                    if (M == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
+                    else s0 = s0 - qo + qi;
+                }
             }
-        }
-        const size_t o = obase + xb;
-        if (xb + 4 <= xend) {
-            *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
-            int64_t* c0 = P.c64(0) + o;
-            int64_t* c1 = P.c64(1) + o;
-            int64_t* c2 = P.c64(2) + o;
-            *reinterpret_cast<longlong2*>(c0) = make_longlong2(c0v[0], c0v[1]);
-            *reinterpret_cast<longlong2*>(c0 + 2) = make_longlong2(c0v[2], c0v[3]);
-            *reinterpret_cast<longlong2*>(c1) = make_longlong2(c1v[0], c1v[1]);
-            *reinterpret_cast<longlong2*>(c1 + 2) = make_longlong2(c1v[2], c1v[3]);
-            *reinterpret_cast<longlong2*>(c2) = make_longlong2(c2v[0], c2v[1]);
-            *reinterpret_cast<longlong2*>(c2 + 2) = make_longlong2(c2v[2], c2v[3]);
-            if (M == SF_METHOD_STANDARD) {
-                int64_t* c3 = P.c64(3) + o;
-                int64_t* c4 = P.c64(4) + o;
-                *reinterpret_cast<longlong2*>(c3) = make_longlong2(c3v[0], c3v[1]);
-                *reinterpret_cast<longlong2*>(c3 + 2) = make_longlong2(c3v[2], c3v[3]);
-                *reinterpret_cast<longlong2*>(c4) = make_longlong2(c4v[0], c4v[1]);
-                *reinterpret_cast<longlong2*>(c4 + 2) = make_longlong2(c4v[2], c4v[3]);
-            }
-        } else {
-            for (int u = 0; u < 4 && xb + u < xend; ++u) {
-                P.p32[o + u] = hmv[u];
-                P.c64(0)[o + u] = c0v[u]; P.c64(1)[o + u] = c1v[u]; P.c64(2)[o + u] = c2v[u];
-                if (M == SF_METHOD_STANDARD) { P.c64(3)[o + u] = c3v[u]; P.c64(4)[o + u] = c4v[u]; }
+            const size_t o = obase + xb;
+            if (xb + 4 <= xend) {
+                *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
+                int64_t* c0 = P.c64(0) + o;
+                int64_t* c1 = P.c64(1) + o;
+                int64_t* c2 = P.c64(2) + o;
+                *reinterpret_cast<longlong2*>(c0) = make_longlong2(c0v[0], c0v[1]);
+                *reinterpret_cast<longlong2*>(c0 + 2) = make_longlong2(c0v[2], c0v[3]);
+                *reinterpret_cast<longlong2*>(c1) = make_longlong2(c1v[0], c1v[1]);
+                *reinterpret_cast<longlong2*>(c1 + 2) = make_longlong2(c1v[2], c1v[3]);
+                *reinterpret_cast<longlong2*>(c2) = make_longlong2(c2v[0], c2v[1]);
+                *reinterpret_cast<longlong2*>(c2 + 2) = make_longlong2(c2v[2], c2v[3]);
+                if (M == SF_METHOD_STANDARD) {
+                    int64_t* c3 = P.c64(3) + o;
+                    int64_t* c4 = P.c64(4) + o;
+                    *reinterpret_cast<longlong2*>(c3) = make_longlong2(c3v[0], c3v[1]);
+                    *reinterpret_cast<longlong2*>(c3 + 2) = make_longlong2(c3v[2], c3v[3]);
+                    *reinterpret_cast<longlong2*>(c4) = make_longlong2(c4v[0], c4v[1]);
+                    *reinterpret_cast<longlong2*>(c4 + 2) = make_longlong2(c4v[2], c4v[3]);
+                }
+            } else {
+                for (int u = 0; u < 4 && xb + u < xend; ++u) {
+                    P.p32[o + u] = hmv[u];
+                    P.c64(0)[o + u] = c0v[u]; P.c64(1)[o + u] = c1v[u]; P.c64(2)[o + u] = c2v[u];
+                    if (M == SF_METHOD_STANDARD) { P.c64(3)[o + u] = c3v[u]; P.c64(4)[o + u] = c4v[u]; }
+                }
             }
         }
     }
+}
+
+template <int DT, int M>
+__global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict__ depth, int W, int H, int r,
+                                                          float scale, const unsigned* __restrict__ vmax_bits,
+                                                          int bits, int raw_z, int Wp, size_t plane_elems,
+                                                          void* planes_base, int seg) {
+    extern __shared__ int tile[];
+    const int f = blockIdx.z;
+    const float sc = ldexpf(1.f, quant_exponent(vmax_bits[f], bits));  // 2^e, exact
+    const size_t dbytes = (DT == SF_DEPTH_U16) ? 2 : 4;
+    const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * W * H;
+    const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
+    hpass_tile<DT, M>(dframe, W, H, r, sc, Wp, P, (size_t)f * plane_elems, blockIdx.x * seg,
+                      blockIdx.y * kHThreads, seg, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -395,6 +407,57 @@ struct StdState {
     __device__ __forceinline__ int count() const { return n; }
 };
 
+// Vertical moments + solve for one column x of one frame, output rows
+// [y0, y0 + band).  `depth` and the output pointers point at the frame.
+template <int DT, int M>
+__device__ __forceinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, float scale, float q,
+                                             int Wp, const Planes& P, size_t pofs, int x, int y0, int band,
+                                             const float* __restrict__ txt, const float* __restrict__ tyt, float a,
+                                             float b, int min_valid, int require_center, float* __restrict__ normals,
+                                             float* __restrict__ offsets, float* __restrict__ curvature,
+                                             int32_t* __restrict__ counts, float tau,
+                                             unsigned long long* __restrict__ flags, unsigned* __restrict__ flag_count,
+                                             int frame_tag) {
+    const int y1 = min(y0 + band, H);
+    const size_t pb = pofs + x;
+    const float tx = txt[x];
+    typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
+    S.init(pb, Wp, H, y0, r);
+    for (int y = y0; y < y1; ++y) {
+        const size_t oi = (size_t)y * W + x;
+        const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
+        const int n = S.count();
+        const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
+        float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
+        if (ok) {
+            FitOut fo_;
+            if constexpr (M == SF_METHOD_DISPARITY)
+                fo_ = solve_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, tyt[y],
+                                      a, b);
+            else
+                fo_ = solve_standard((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
+                                     S.Szzii, q, tx, tyt[y], a, b);
+            nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
+            if (flags && !(fo_.gap >= tau)) {
+                // near-degenerate window: queue it for the FP64 re-solve
+                const unsigned mask = __activemask();
+                const int leader = __ffs(mask) - 1;
+                const int lane = threadIdx.x & 31;
+                unsigned base = 0;
+                if (lane == leader) base = atomicAdd(flag_count, (unsigned)__popc(mask));
+                base = __shfl_sync(mask, base, leader);
+                const unsigned slot = base + __popc(mask & ((1u << lane) - 1u));
+                flags[slot] = ((unsigned long long)frame_tag << 48) | ((unsigned long long)y << 24) |
+                              (unsigned long long)x;
+            }
+        }
+        normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
+        offsets[oi] = d; curvature[oi] = cu;
+        if (counts) counts[oi] = n;
+        if (y + 1 < y1) S.slide(pb, Wp, H, y, r);
+    }
+}
+
 template <int DT, int M>
 __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
                                                           float scale, const unsigned* __restrict__ vmax_bits,
@@ -408,47 +471,104 @@ __global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict
     const int f = blockIdx.z;
     const int x = blockIdx.x * kVThreads + threadIdx.x;
     if (x >= W) return;
-    const int y0 = blockIdx.y * band;
-    const int y1 = min(y0 + band, H);
-    const size_t nf = gridDim.z;
-    const size_t pb = (size_t)f * plane_elems + x;
+    const size_t fe = (size_t)W * H;
+    const size_t dbytes = (DT == SF_DEPTH_U16) ? 2 : 4;
+    const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * fe;
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);  // metric value of one fixed-point unit
-    const float tx = cal.tx[x];
-    const size_t fo = (size_t)f * W * H;
-    const Planes P(planes_base, nf, plane_elems);
-    typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
-    S.init(pb, Wp, H, y0, r);
-    for (int y = y0; y < y1; ++y) {
-        const size_t oi = fo + (size_t)y * W + x;
-        const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
-        const int n = S.count();
-        const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
-        float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
-        if (ok) {
-            FitOut fo_;
-            if constexpr (M == SF_METHOD_DISPARITY)
-                fo_ = solve_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx,
-                                      cal.ty[y], cal.a, cal.b);
-            else
-                fo_ = solve_standard((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
-                                     S.Szzii, q, tx, cal.ty[y], cal.a, cal.b);
-            nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
-            if (flags && !(fo_.gap >= tau)) {
-                // near-degenerate window: queue it for the FP64 re-solve
-                const unsigned mask = __activemask();
-                const int leader = __ffs(mask) - 1;
-                const int lane = threadIdx.x & 31;
-                unsigned base = 0;
-                if (lane == leader) base = atomicAdd(flag_count, (unsigned)__popc(mask));
-                base = __shfl_sync(mask, base, leader);
-                const unsigned slot = base + __popc(mask & ((1u << lane) - 1u));
-                flags[slot] = ((unsigned long long)f << 48) | ((unsigned long long)y << 24) | (unsigned long long)x;
-            }
+    const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
+    vpass_column<DT, M>(dframe, W, H, r, scale, q, Wp, P, (size_t)f * plane_elems, x, blockIdx.y * band, band, cal.tx,
+                        cal.ty, cal.a, cal.b, min_valid, require_center, normals + 3 * fe * f, offsets + fe * f,
+                        curvature + fe * f, counts ? counts + fe * f : nullptr, tau, flags, flag_count, f);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-resolution batches: persistent kernels over a table of work items.
+// Each frame has its own size, window, intrinsics and tile shape; every CTA
+// claims the next item with one atomicAdd and never waits on another CTA.
+// ---------------------------------------------------------------------------
+struct FrameDesc {
+    const void* depth;
+    float* normals;
+    float* offsets;
+    float* curvature;
+    const float* tx;   // [W] ray tangents
+    const float* ty;   // [H]
+    float a, b;        // 1/fx, 1/fy
+    int W, H, r, bits, Wp, seg, band;
+    size_t pofs;       // offset of the frame in every moment plane
+};
+
+template <int DT, int M>
+__global__ void __launch_bounds__(256) range_batch_kernel(const FrameDesc* __restrict__ descs,
+                                                          unsigned* __restrict__ vmax_bits) {
+    const int f = blockIdx.y;
+    const FrameDesc& d = descs[f];
+    const size_t fe = (size_t)d.W * d.H;
+    float vmax = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < fe; i += (size_t)gridDim.x * blockDim.x) {
+        const float z = load_raw<DT>(d.depth, i);
+        if (depth_valid(z)) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z));
+    }
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    __shared__ float red[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = vmax;
+    __syncthreads();
+    if (warp == 0) {
+        vmax = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if (lane == 0 && vmax > 0.f) atomicMax(vmax_bits + f, __float_as_uint(vmax));
+    }
+}
+
+// Claim the next work item for the whole CTA (one atomicAdd).
+__device__ __forceinline__ int claim_item(unsigned* counter, int* slot) {
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    return *slot;
+}
+
+template <int DT, int M>
+__global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc* __restrict__ descs,
+                                                                const int3* __restrict__ items, int n_items,
+                                                                unsigned* __restrict__ counter,
+                                                                const unsigned* __restrict__ vmax_bits,
+                                                                void* planes_base, size_t stride, float scale) {
+    extern __shared__ int tile[];
+    __shared__ int slot;
+    const Planes P(planes_base, stride);
+    for (;;) {
+        const int it = claim_item(counter, &slot);
+        if (it >= n_items) break;
+        const int3 w = items[it];
+        const FrameDesc& d = descs[w.x];
+        const float sc = ldexpf(1.f, quant_exponent(vmax_bits[w.x], d.bits));
+        hpass_tile<DT, M>(d.depth, d.W, d.H, d.r, sc, d.Wp, P, d.pofs, w.y, w.z, d.seg, tile);
+    }
+}
+
+template <int DT, int M>
+__global__ void __launch_bounds__(kVThreads) vpass_batch_kernel(const FrameDesc* __restrict__ descs,
+                                                                const int3* __restrict__ items, int n_items,
+                                                                unsigned* __restrict__ counter,
+                                                                const unsigned* __restrict__ vmax_bits,
+                                                                void* planes_base, size_t stride, float scale,
+                                                                int min_valid, int require_center) {
+    __shared__ int slot;
+    const Planes P(planes_base, stride);
+    for (;;) {
+        const int it = claim_item(counter, &slot);
+        if (it >= n_items) break;
+        const int3 w = items[it];
+        const FrameDesc& d = descs[w.x];
+        const int x = w.y + threadIdx.x;
+        if (x < d.W) {
+            const float q = quantum<DT, M>(vmax_bits[w.x], d.bits, scale);
+            vpass_column<DT, M>(d.depth, d.W, d.H, d.r, scale, q, d.Wp, P, d.pofs, x, w.z, d.band, d.tx, d.ty, d.a,
+                                d.b, min_valid, require_center, d.normals, d.offsets, d.curvature, nullptr,
+                                INFINITY, nullptr, nullptr, w.x);
         }
-        normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
-        offsets[oi] = d; curvature[oi] = cu;
-        if (counts) counts[oi] = n;
-        if (y + 1 < y1) S.slide(pb, Wp, H, y, r);
     }
 }
 
@@ -469,7 +589,7 @@ __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, float
                                                       float* __restrict__ normals, float* __restrict__ offsets,
                                                       float* __restrict__ curvature) {
     const unsigned count = *flag_count;
-    const Planes P(planes_base, nframes, plane_elems);
+    const Planes P(planes_base, (size_t)nframes * plane_elems);
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
         const unsigned long long e = flags[idx];
         const int f = (int)(e >> 48), y = (int)((e >> 24) & 0xffffff), x = (int)(e & 0xffffff);
@@ -531,7 +651,7 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);
     const float tx = cal.tx[x];
     const size_t fo = (size_t)f * fe;
-    const Planes P(planes_base, nf, plane_elems);
+    const Planes P(planes_base, nf * plane_elems);
     constexpr int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
     typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
     S.init(pb, Wp, H, y0, r);
@@ -745,6 +865,8 @@ struct sf_ctx {
     size_t plane_elems;
     int method = SF_METHOD_DISPARITY;
     int depth_type = SF_DEPTH_F32;
+    int hseg = 64;        // horizontal tile width (32, 64 or 128)
+    int vband = 0;        // vertical band height (0: chosen from the grid size)
     float depth_scale = 1e-3f;
     int min_valid = 3;
     int require_center = 1;
@@ -822,6 +944,7 @@ static sf_status ensure_planes(sf_ctx* c, int frames) {
 // Band height of the vertical pass: long bands amortise the 2r-row warm-up,
 // short bands give enough threads to fill the GPU (>= 24 warps per SM).
 static int vertical_band(const sf_ctx* c, int nfr) {
+    if (c->vband > 0) return c->vband;
     const size_t cols = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * sf::kVThreads * nfr;
     int band = 256;
     while (band > 16 && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 24 * 32) band /= 2;
@@ -843,11 +966,12 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
     }
     {
         StageTimer t(c, 1, st);
-        dim3 grid((c->W + sf::kHSeg - 1) / sf::kHSeg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
-        const int IW = sf::kHSeg + 2 * c->r;
+        const int seg = c->hseg;
+        dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
+        const int IW = seg + 2 * c->r;
         const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
         sf::hpass_kernel<DT, M><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
-                                                                  bits, raw_z, c->Wp, c->plane_elems, c->planes);
+                                                                  bits, raw_z, c->Wp, c->plane_elems, c->planes, seg);
     }
     {
         StageTimer t(c, 2, st);
@@ -887,11 +1011,12 @@ static sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const fl
         sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, c->depth_scale, c->vmax);
     }
     {
-        dim3 grid((c->W + sf::kHSeg - 1) / sf::kHSeg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
-        const int IW = sf::kHSeg + 2 * c->r;
+        const int seg = c->hseg;
+        dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
+        const int IW = seg + 2 * c->r;
         const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
         sf::hpass_kernel<DT, M><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
-                                                                  bits, raw_z, c->Wp, c->plane_elems, c->planes);
+                                                                  bits, raw_z, c->Wp, c->plane_elems, c->planes, seg);
     }
     sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
     {
@@ -989,7 +1114,7 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
     sf_status s = ensure_planes(c, 1);
     if (s != SF_OK) { sf_destroy(c); return s; }
     {
-        const int IW = sf::kHSeg + 2 * sf::kMaxR;
+        const int IW = 128 + 2 * sf::kMaxR;
         const int smem = (int)(sizeof(int) * sf::kHThreads * (size_t)(IW | 1));
         cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_F32, SF_METHOD_DISPARITY>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1127,6 +1252,15 @@ sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals
     return SF_OK;
 }
 
+sf_status sf_set_tiles(sf_ctx* c, int hseg, int vband) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    if (hseg != 32 && hseg != 64 && hseg != 128) return fail(SF_ERR_INVALID_ARG, "hseg must be 32, 64 or 128");
+    if (vband != 0 && (vband < 8 || vband > 1024)) return fail(SF_ERR_INVALID_ARG, "vband must be 0 or in [8, 1024]");
+    c->hseg = hseg;
+    c->vband = vband;
+    return SF_OK;
+}
+
 sf_status sf_set_precision(sf_ctx* c, int mode, float tau) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (mode < 0 || mode > 2) return fail(SF_ERR_INVALID_ARG, "precision mode %d must be 0, 1 or 2", mode);
@@ -1228,6 +1362,240 @@ sf_status sf_destroy(sf_ctx* c) {
 }  // extern "C"
 
 // ===========================================================================
+// Mixed-resolution batches
+// ===========================================================================
+struct sf_batch {
+    int n = 0;
+    int method = SF_METHOD_DISPARITY, depth_type = SF_DEPTH_F32;
+    float depth_scale = 1e-3f;
+    int min_valid = 3, require_center = 1;
+    sf::FrameDesc* d_desc = nullptr;
+    int3* d_hitems = nullptr;
+    int3* d_vitems = nullptr;
+    int n_h = 0, n_v = 0;
+    unsigned* d_counters = nullptr;  // [2]
+    unsigned* d_vmax = nullptr;      // [n]
+    float* d_rays = nullptr;
+    void* d_planes = nullptr;
+    size_t stride = 0;
+    size_t hsmem = 0;
+    int grid_h = 0, grid_v = 0;
+    long long pixels = 0;
+    bool use_graph = false;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+template <int DT, int M>
+sf_status batch_enqueue_t(sf_batch* b, cudaStream_t st) {
+    SF_CUDA(cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(unsigned), st));
+    SF_CUDA(cudaMemsetAsync(b->d_vmax, 0, sizeof(unsigned) * b->n, st));
+    if (!(DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD))
+        sf::range_batch_kernel<DT, M><<<dim3(16, b->n), 256, 0, st>>>(b->d_desc, b->d_vmax);
+    sf::hpass_batch_kernel<DT, M><<<b->grid_h, sf::kHThreads, b->hsmem, st>>>(
+        b->d_desc, b->d_hitems, b->n_h, b->d_counters, b->d_vmax, b->d_planes, b->stride, b->depth_scale);
+    sf::vpass_batch_kernel<DT, M><<<b->grid_v, sf::kVThreads, 0, st>>>(b->d_desc, b->d_vitems, b->n_v,
+                                                                        b->d_counters + 1, b->d_vmax, b->d_planes,
+                                                                        b->stride, b->depth_scale, b->min_valid,
+                                                                        b->require_center);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+    return SF_OK;
+}
+
+sf_status batch_enqueue(sf_batch* b, cudaStream_t st) {
+    if (b->depth_type == SF_DEPTH_F32)
+        return b->method == SF_METHOD_DISPARITY ? batch_enqueue_t<SF_DEPTH_F32, SF_METHOD_DISPARITY>(b, st)
+                                                : batch_enqueue_t<SF_DEPTH_F32, SF_METHOD_STANDARD>(b, st);
+    return b->method == SF_METHOD_DISPARITY ? batch_enqueue_t<SF_DEPTH_U16, SF_METHOD_DISPARITY>(b, st)
+                                            : batch_enqueue_t<SF_DEPTH_U16, SF_METHOD_STANDARD>(b, st);
+}
+
+template <int DT, int M>
+void batch_grids(sf_batch* b, int sms) {
+    int nb = 0;
+    cudaFuncSetAttribute(sf::hpass_batch_kernel<DT, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->hsmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sf::hpass_batch_kernel<DT, M>, sf::kHThreads, b->hsmem);
+    b->grid_h = std::max(1, nb) * sms;
+    nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sf::vpass_batch_kernel<DT, M>, sf::kVThreads, 0);
+    b->grid_v = std::max(1, nb) * sms;
+}
+
+}  // namespace
+
+extern "C" {
+
+sf_status sf_batch_destroy(sf_batch* b) {
+    if (!b) return SF_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_desc);
+    cudaFree(b->d_hitems);
+    cudaFree(b->d_vitems);
+    cudaFree(b->d_counters);
+    cudaFree(b->d_vmax);
+    cudaFree(b->d_rays);
+    cudaFree(b->d_planes);
+    delete b;
+    return SF_OK;
+}
+
+sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method, int depth_type, float depth_scale,
+                          int min_valid, int require_center_valid, int use_graph, sf_batch** out) {
+    if (!frames || !out || n_frames < 1) return fail(SF_ERR_INVALID_ARG, "need at least one frame and an output");
+    *out = nullptr;
+    if (n_frames > 65535) return fail(SF_ERR_INVALID_ARG, "at most 65535 frames per batch");
+    if (method != SF_METHOD_DISPARITY && method != SF_METHOD_STANDARD)
+        return fail(SF_ERR_UNSUPPORTED, "batches support the disparity and standard implicit fits");
+    if (depth_type != SF_DEPTH_F32 && depth_type != SF_DEPTH_U16)
+        return fail(SF_ERR_INVALID_ARG, "unknown depth type %d", depth_type);
+    if (depth_type == SF_DEPTH_U16 && !(depth_scale > 0.f && std::isfinite(depth_scale)))
+        return fail(SF_ERR_INVALID_ARG, "depth_scale must be positive and finite");
+    if (min_valid < 1) return fail(SF_ERR_INVALID_ARG, "min_valid must be >= 1");
+    std::vector<sf::FrameDesc> desc(n_frames);
+    std::vector<int> order(n_frames);
+    size_t stride = 0, rays = 0;
+    int max_r = 0, max_seg = 32;
+    long long pixels = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        const sf_batch_frame& F = frames[f];
+        if (F.W < 1 || F.H < 1 || (size_t)F.W * F.H > ((size_t)1 << 31))
+            return fail(SF_ERR_INVALID_ARG, "frame %d: bad size %dx%d", f, F.W, F.H);
+        if (F.window < 1 || (F.window & 1) == 0 || F.window > SF_MAX_WINDOW)
+            return fail(SF_ERR_INVALID_ARG, "frame %d: window %d must be odd and in [1, %d]", f, F.window,
+                        SF_MAX_WINDOW);
+        if (!F.depth || !F.normals || !F.offsets || !F.curvature)
+            return fail(SF_ERR_INVALID_ARG, "frame %d: null buffer", f);
+        const sf_intrinsics& K = F.K;
+        if (!(K.fx != 0.0) || !(K.fy != 0.0) || !std::isfinite(K.fx) || !std::isfinite(K.fy) ||
+            !std::isfinite(K.cx) || !std::isfinite(K.cy) || !std::isfinite(K.dx) || !std::isfinite(K.dy))
+            return fail(SF_ERR_INVALID_ARG, "frame %d: intrinsics must be finite with nonzero focal lengths", f);
+        const int seg = F.hseg ? F.hseg : 64;
+        if (seg != 32 && seg != 64 && seg != 128) return fail(SF_ERR_INVALID_ARG, "frame %d: hseg must be 32, 64 or 128", f);
+        const int band = F.vband ? F.vband : 64;
+        if (band < 8 || band > 1024) return fail(SF_ERR_INVALID_ARG, "frame %d: vband must be in [8, 1024]", f);
+        sf::FrameDesc& d = desc[f];
+        d.depth = F.depth; d.normals = F.normals; d.offsets = F.offsets; d.curvature = F.curvature;
+        d.W = F.W; d.H = F.H; d.r = (F.window - 1) / 2; d.bits = quant_bits(method, F.window);
+        d.Wp = (F.W + 63) / 64 * 64; d.seg = seg; d.band = band;
+        d.a = (float)(1.0 / K.fx); d.b = (float)(1.0 / K.fy);
+        d.pofs = stride;
+        stride += (size_t)d.Wp * F.H;
+        rays += (size_t)F.W + F.H;
+        max_r = std::max(max_r, d.r);
+        max_seg = std::max(max_seg, seg);
+        pixels += (long long)F.W * F.H;
+        order[f] = f;
+    }
+    sf_batch* b = new (std::nothrow) sf_batch();
+    if (!b) return fail(SF_ERR_ALLOC, "batch allocation failed");
+    b->n = n_frames; b->method = method; b->depth_type = depth_type; b->depth_scale = depth_scale;
+    b->min_valid = min_valid; b->require_center = require_center_valid ? 1 : 0;
+    b->stride = stride; b->pixels = pixels;
+    // ray tables (Eq. 10) in FP64 -> FP32, all frames in one buffer
+    std::vector<float> hr(rays);
+    size_t ro = 0;
+    std::vector<size_t> rofs(n_frames);
+    for (int f = 0; f < n_frames; ++f) {
+        const sf_batch_frame& F = frames[f];
+        rofs[f] = ro;
+        for (int x = 0; x < F.W; ++x) hr[ro + x] = (float)((x + F.K.dx - F.K.cx) / F.K.fx);
+        for (int y = 0; y < F.H; ++y) hr[ro + F.W + y] = (float)((y + F.K.dy - F.K.cy) / F.K.fy);
+        ro += (size_t)F.W + F.H;
+    }
+    // work items, largest frames first so that the tail holds the small ones
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (long long)desc[a].W * desc[a].H > (long long)desc[c].W * desc[c].H;
+    });
+    std::vector<int3> hitems, vitems;
+    for (int f : order) {
+        const sf::FrameDesc& d = desc[f];
+        for (int y0 = 0; y0 < d.H; y0 += sf::kHThreads)
+            for (int x0 = 0; x0 < d.W; x0 += d.seg) hitems.push_back(make_int3(f, x0, y0));
+        for (int y0 = 0; y0 < d.H; y0 += d.band)
+            for (int x0 = 0; x0 < d.W; x0 += sf::kVThreads) vitems.push_back(make_int3(f, x0, y0));
+    }
+    b->n_h = (int)hitems.size();
+    b->n_v = (int)vitems.size();
+    const int n64 = method == SF_METHOD_STANDARD ? 5 : 3;
+    cudaError_t e = cudaMalloc(&b->d_rays, sizeof(float) * std::max<size_t>(rays, 1));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_rays, hr.data(), sizeof(float) * rays, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        for (int f = 0; f < n_frames; ++f) {
+            desc[f].tx = b->d_rays + rofs[f];
+            desc[f].ty = b->d_rays + rofs[f] + desc[f].W;
+        }
+        e = cudaMalloc(&b->d_desc, sizeof(sf::FrameDesc) * n_frames);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, desc.data(), sizeof(sf::FrameDesc) * n_frames, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_hitems, sizeof(int3) * hitems.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_hitems, hitems.data(), sizeof(int3) * hitems.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_vitems, sizeof(int3) * vitems.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_vitems, vitems.data(), sizeof(int3) * vitems.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_vmax, sizeof(unsigned) * n_frames);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_planes, stride * (4 + 8 * (size_t)n64));
+    if (e != cudaSuccess) { sf_batch_destroy(b); return fail(SF_ERR_ALLOC, "batch buffers: %s", cudaGetErrorString(e)); }
+    b->hsmem = sizeof(int) * sf::kHThreads * (size_t)((max_seg + 2 * max_r) | 1);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (depth_type == SF_DEPTH_F32) {
+        if (method == SF_METHOD_DISPARITY) batch_grids<SF_DEPTH_F32, SF_METHOD_DISPARITY>(b, sms);
+        else batch_grids<SF_DEPTH_F32, SF_METHOD_STANDARD>(b, sms);
+    } else {
+        if (method == SF_METHOD_DISPARITY) batch_grids<SF_DEPTH_U16, SF_METHOD_DISPARITY>(b, sms);
+        else batch_grids<SF_DEPTH_U16, SF_METHOD_STANDARD>(b, sms);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { sf_batch_destroy(b); return cuda_fail(e, "batch kernel attributes"); }
+    if (use_graph) {
+        // capture the whole pass once; sf_batch_run then replays it
+        e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { sf_batch_destroy(b); return cuda_fail(e, "batch graph capture"); }
+        sf_status s = batch_enqueue(b, b->cap);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(b->cap, &g);
+        if (s != SF_OK) { if (g) cudaGraphDestroy(g); sf_batch_destroy(b); return s; }
+        if (e != cudaSuccess) { sf_batch_destroy(b); return cuda_fail(e, "batch graph capture"); }
+        b->graph = g;
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (e != cudaSuccess) { sf_batch_destroy(b); return cuda_fail(e, "batch graph instantiate"); }
+        b->use_graph = true;
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { sf_batch_destroy(b); return cuda_fail(e, "batch setup"); }
+    *out = b;
+    return SF_OK;
+}
+
+sf_status sf_batch_run(sf_batch* b, void* stream) {
+    if (!b) return fail(SF_ERR_INVALID_ARG, "null batch");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (b->use_graph) {
+        cudaError_t e = cudaGraphLaunch(b->exec, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+        return SF_OK;
+    }
+    return batch_enqueue(b, st);
+}
+
+sf_status sf_batch_info(const sf_batch* b, long long* pixels, int* launches) {
+    if (!b || !pixels || !launches) return fail(SF_ERR_INVALID_ARG, "null argument");
+    *pixels = b->pixels;
+    *launches = (b->depth_type == SF_DEPTH_U16 && b->method == SF_METHOD_STANDARD) ? 2 : 3;
+    return SF_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
 // Allocation-free entry point: sf_fit_static
 // ===========================================================================
 // Some callers cannot allocate device memory at the point where they need a
@@ -1273,7 +1641,7 @@ sf_status static_scratch_base(void** out) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, sf::g_static_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "sf_fit_static: cudaGetSymbolAddress");
-        const int IW = sf::kHSeg + 2 * sf::kMaxR;
+        const int IW = 128 + 2 * sf::kMaxR;
         const int smem = (int)(sizeof(int) * sf::kHThreads * (size_t)(IW | 1));
         cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_F32, SF_METHOD_DISPARITY>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
