@@ -31,7 +31,8 @@
  *     0 too make the first nonzero component negative.
  *  6. curvature = lambda0 / (lambda0 + lambda1 + lambda2) of R (0 if the trace is 0).
  *
- * Explicit fits (Section I.D and II.B) are methods 2 and 3:
+ * Explicit fits (Section I.D and II.B) are methods 2 and 3 (a window whose
+ * valid pixels are collinear in the image has no explicit fit: NaN):
  *     explicit disparity (Eq. 15-16): minimise sum (a tx + b ty + c - 1/Z)^2,
  *         alpha = (M^T M)^-1 M^T b with M rows [tx, ty, 1], b = 1/Z.  The plane
  *         a tx + b ty + c - 1/Z = 0 is n.P + d = 0 with n ~ (a,b,c), d ~ -1.
@@ -136,12 +137,13 @@ static inline int valid_depth(double z) { return isfinite(z) && z > 0.0; }
 /* Direct window sums of the method's monomials over V(p).
  * A: 3x3, g: 3, s: scalar; also b2 = sum b^2 (explicit fits only). */
 static int window_sums(const double* Z, int W, int H, const double* intr, int r, int method,
-                       int px, int py, double A[3][3], double g[3], double* s, double* bb) {
+                       int px, int py, double A[3][3], double g[3], double* s, double* bb, int64_t pm[5]) {
     const double fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3], dx = intr[4], dy = intr[5];
     memset(A, 0, 9 * sizeof(double));
     g[0] = g[1] = g[2] = 0.0;
     *s = 0.0; *bb = 0.0;
     int n = 0;
+    if (pm) pm[0] = pm[1] = pm[2] = pm[3] = pm[4] = 0;
     for (int y = py - r; y <= py + r; ++y) {
         if (y < 0 || y >= H) continue;
         const double ty = (y + dy - cy) / fy;
@@ -171,6 +173,10 @@ static int window_sums(const double* Z, int W, int H, const double* intr, int r,
             *s += wgt * wgt;
             *bb += b * b;
             ++n;
+            if (pm) {  /* pixel offsets from the window centre: sum j, i, j^2, j i, i^2 */
+                const int64_t j = x - px, i = y - py;
+                pm[0] += j; pm[1] += i; pm[2] += j * j; pm[3] += j * i; pm[4] += i * i;
+            }
         }
     }
     return n;
@@ -230,7 +236,8 @@ int sfo_fit(const double* Z, int W, int H, const double* intr, int k, int method
         for (int px = 0; px < W; ++px) {
             const size_t o = (size_t)py * W + px;
             double A[3][3], g[3], s, bb;
-            int n = window_sums(Z, W, H, intr, r, method, px, py, A, g, &s, &bb);
+            int64_t pm[5];
+            int n = window_sums(Z, W, H, intr, r, method, px, py, A, g, &s, &bb, pm);
             if (counts) counts[o] = n;
             if (moments) {
                 double* mo = moments + o * 10;
@@ -241,6 +248,15 @@ int sfo_fit(const double* Z, int W, int H, const double* intr, int k, int method
             int ok = n >= min_valid && n > 0;
             if (require_center && !valid_depth(Z[o])) ok = 0;
             if (ok && method <= M_STANDARD && s <= 0.0) ok = 0;
+            if (ok && method >= M_EXPLICIT_DISPARITY) {
+                /* An explicit fit needs a design matrix of full rank: the
+                 * valid pixels must not be collinear in the image, decided
+                 * exactly on integer offsets, n^2 det cov(j, i) != 0. */
+                const int64_t nn = n;
+                const int64_t cjj = nn * pm[2] - pm[0] * pm[0], cii = nn * pm[4] - pm[1] * pm[1];
+                const int64_t cji = nn * pm[3] - pm[0] * pm[1];
+                if (cjj * cii - cji * cji == 0) ok = 0;
+            }
             if (!ok) {
                 normals[3 * o] = normals[3 * o + 1] = normals[3 * o + 2] = NAN;
                 offsets[o] = NAN; curv[o] = NAN;
@@ -335,7 +351,7 @@ int sfo_backward(const double* Z, int W, int H, const double* intr, int k, int m
         for (int px = 0; px < W; ++px) {
             const size_t o = (size_t)py * W + px;
             double A[3][3], g[3], s, bb;
-            int n = window_sums(Z, W, H, intr, r, method, px, py, A, g, &s, &bb);
+            int n = window_sums(Z, W, H, intr, r, method, px, py, A, g, &s, &bb, NULL);
             int ok = n >= min_valid && n > 0 && s > 0.0;
             if (require_center && !valid_depth(Z[o])) ok = 0;
             if (!ok) continue;

@@ -344,3 +344,59 @@ def test_paper_cost_model_counts():
     assert len(dep) == g["implicit_disparity_depth_channels"]
     # Eq. 6 with m=[X,Y,Z,1]: every unique entry except the 1*1 one depends on Z
     assert 10 - 1 == g["implicit_standard_depth_channels"]
+
+
+# ---------------------------------------------------------------------------
+# Explicit fits: rank-deficient (collinear) windows have no fit.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("method", ["explicit_disparity", "explicit_standard"])
+def test_explicit_fit_undefined_on_collinear_windows(method):
+    intr = (525.0, 525.0, 10.0, 0.0, 0.0, 0.0)
+    Z = np.linspace(1.0, 2.0, 20)[None, :].repeat(1, 0)  # a single image row: every window collinear
+    o = oracle.fit(Z, intr, 5, method)
+    assert np.all(np.isnan(o["offsets"]))
+    Z2 = np.full((6, 6), 2.0)
+    Z2[::2, :] = 0.0  # rows 1, 3, 5 valid: 3x3 windows centred on them see one row only
+    o = oracle.fit(Z2, intr, 3, method)
+    assert np.all(np.isnan(o["offsets"][1::2, :]))
+    o = oracle.fit(Z2, intr, 5, method, require_center=False)
+    assert np.isfinite(o["offsets"][2, 2])  # two valid rows: not collinear
+
+
+@pytest.mark.parametrize("method", ["explicit_disparity", "explicit_standard"])
+def test_explicit_fit_is_least_squares(method):
+    """Explicit fits against numpy lstsq on the design matrix of Eq. 9 / Eq. 16 (random noisy window)."""
+    rng = np.random.Generator(np.random.PCG64(4))
+    W, H, k = 9, 9, 7
+    intr = (400.0, 410.0, 4.2, 3.9, 0.1, 0.0)
+    Z = 2.0 + 0.3 * rng.random((H, W))
+    Z[rng.random((H, W)) < 0.15] = 0
+    Z[4, 4] = 2.1
+    o = oracle.fit(Z, intr, k, method)
+    fx, fy, cx, cy, dx, dy = intr
+    y0 = x0 = 4
+    rows, tgt = [], []
+    for y in range(y0 - 3, y0 + 4):
+        for x in range(x0 - 3, x0 + 4):
+            z = Z[y, x]
+            if z <= 0:
+                continue
+            tx, ty = (x + dx - cx) / fx, (y + dy - cy) / fy
+            if method == "explicit_disparity":
+                rows.append([tx, ty, 1.0]); tgt.append(1.0 / z)
+            else:
+                rows.append([z * tx, z * ty, 1.0]); tgt.append(z)
+    M, b = np.array(rows), np.array(tgt)
+    a, *_ = np.linalg.lstsq(M, b, rcond=None)
+    res = np.sum((M @ a - b) ** 2) / len(b)
+    if method == "explicit_disparity":
+        v, d = a.copy(), -1.0
+    else:
+        v, d = np.array([a[0], a[1], -1.0]), a[2]
+    nrm = np.linalg.norm(v)
+    v, d = v / nrm, d / nrm
+    if d < 0:
+        v, d = -v, -d
+    assert np.allclose(o["normals"][y0, x0], v, atol=1e-10)
+    assert abs(o["offsets"][y0, x0] - d) < 1e-10 * abs(d)
+    assert abs(o["curvature"][y0, x0] - res) < 1e-9 * max(res, 1e-12) + 1e-18
