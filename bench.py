@@ -372,6 +372,17 @@ def main():
                                 "ms_per_step": ms_std, "speedup_of_disparity_form": ms_std / ms}
         for f in std:
             f.close()
+        # the explicit fits (Eq. 15-16, Eq. 7-9) on the same batch
+        expl = {}
+        for method in ("explicit_disparity", "explicit_standard"):
+            ef = [SurfaceFitter(intr.as_tuple(), W, H, K, method=method) for (W, H, intr, frames) in groups]
+            for _ in range(3):
+                step(ef)
+            ms_e = timed(max(3, args.steps // 4), lambda: step(ef))
+            expl[method] = {"value": world * total_px / (ms_e / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms_e}
+            for f in ef:
+                f.close()
+        line["explicit_fits"] = expl
         # 640x480, 7x7: the small single-frame case (launch-bound)
         intr = scenes.Intrinsics(525.0, 525.0, 319.5, 239.5)
         vga = torch.from_numpy(scenes.kinect_frame(scenes.BASE_SEED, intr, 640, 480)).to(dev)

@@ -14,8 +14,12 @@
  *   - SF_METHOD_STANDARD: the implicit algebraic fit of Eq. 3-6 with monomials
  *     [X, Y, Z, 1], X and Y from Eq. 1 -- the comparison fit.
  *   - SF_METHOD_EXPLICIT_DISPARITY / SF_METHOD_EXPLICIT_STANDARD: the explicit
- *     fits of Eq. 15-16 and Eq. 7-9; their third output is the mean squared
- *     residual in the fit's own units instead of the curvature.
+ *     fits of Eq. 15-16 (1/Z = a tan(theta_x) + b tan(theta_y) + c) and
+ *     Eq. 7-9 (Z = a X + b Y + c), least squares over the same exact window
+ *     sums; the plane is returned as n.P + d = 0 like the implicit fits.  Their
+ *     third output is the mean squared residual in the fit's own units (1/m^2
+ *     and m^2) instead of the curvature.  A window whose valid pixels are
+ *     collinear in the image has no unique explicit fit and gets NaN.
  *
  * Rays follow Eq. 10: tan(theta_x) = (x + dx - cx)/fx, tan(theta_y) =
  * (y + dy - cy)/fy, with x the column and y the row, both 0-based.
@@ -118,7 +122,8 @@ sf_status sf_set_params(sf_ctx* ctx, int method, int depth_type, float depth_sca
  *   2  FP64 solve for every window (slow: FP64 runs at ~1/64 of the float32
  *      rate on GB300).
  * tau in (0, 1] (mode 1; default 1e-2).  Modes 1 and 2 allocate a queue of
- * 8 bytes per pixel on the next fit.
+ * 8 bytes per pixel on the next fit.  The explicit fits have no eigen-gap:
+ * mode 1 leaves them in float32, mode 2 solves their regression in FP64.
  */
 sf_status sf_set_precision(sf_ctx* ctx, int mode, float tau);
 
@@ -195,7 +200,8 @@ typedef struct sf_batch sf_batch;
  * captured once in a CUDA graph and sf_batch_run replays it.  The device
  * buffers named in `frames` are bound for the life of the batch: refill them
  * and run again.  Method, depth type and validity rule are shared by all
- * frames (disparity or standard implicit fit).  Synchronises once.
+ * frames (disparity or standard implicit fit; SF_ERR_UNSUPPORTED for the
+ * explicit fits).  Synchronises once.
  */
 sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method, int depth_type, float depth_scale,
                           int min_valid, int require_center_valid, int use_graph, sf_batch** out);

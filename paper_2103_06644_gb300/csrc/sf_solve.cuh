@@ -295,6 +295,111 @@ __device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t S
 }
 
 // ---------------------------------------------------------------------------
+// Explicit fits (Section I.D, Section II.B).  Both are linear least squares
+// on the same exact window moments; the regression is done on centred
+// quantities (a 2x2 system for the two slopes, the intercept from the means).
+// A window without a unique fit (collinear pixels) returns ok = false.
+// Third output: mean squared residual in the fit's own units.
+// ---------------------------------------------------------------------------
+
+// Eq. 15-16: 1/Z = ax tx + ay ty + ac.  With w = qw * omega and
+// tx = tx_p + a j, the regression of omega on (j, i) gives the slopes per
+// pixel; the plane ax tx + ay ty + ac - 1/Z = 0 is n.P + d = 0 with
+// n = -(ax, ay, ac)/|.|, d = 1/|(ax, ay, ac)|.
+// Exact rank test of the image coordinates of a window's valid pixels:
+// n^2 det cov(j, i) == 0 iff they are collinear (every moment is an integer).
+template <typename T>
+__device__ __forceinline__ bool pixels_span_plane(T nf, T fSj, T fSi, T fSjj, T fSji, T fSii) {
+    const int n = (int)nf, Sj = (int)fSj, Si = (int)fSi;
+    const int64_t cjj = (int64_t)n * (int)fSjj - (int64_t)Sj * Sj;
+    const int64_t cii = (int64_t)n * (int)fSii - (int64_t)Si * Si;
+    const int64_t cji = (int64_t)n * (int)fSji - (int64_t)Sj * Si;
+    return cjj * cii - cji * cji != 0;
+}
+
+template <typename T = float>
+__device__ __forceinline__ FitOutT<T> solve_explicit_disparity(T nf, T fSj, T fSi, T fSjj, T fSji, T fSii,
+                                                               int64_t Sw, int64_t Swj, int64_t Swi, int64_t Sww,
+                                                               T qw, T tx, T ty, T a, T b, bool& ok) {
+    FitOutT<T> o;
+    const int n = (int)nf, Sj = (int)fSj, Si = (int)fSi;
+    ok = pixels_span_plane<T>(nf, fSj, fSi, fSjj, fSji, fSii);
+    const T inv_n = Fn<T>::rcp(nf);
+    const int m = __float2int_rn((float)((T)Sw * inv_n));
+    const int64_t T0 = Sw - (int64_t)n * m;
+    const int64_t Tww = Sww - (int64_t)m * (Sw + T0);
+    const int64_t Twj = Swj - (int64_t)m * Sj;
+    const int64_t Twi = Swi - (int64_t)m * Si;
+    const T fT0 = (T)(int)T0;
+    const T t0 = fT0 * inv_n;
+    const T jb = fSj * inv_n, ib = fSi * inv_n;
+    const T Cjj = fSjj - fSj * jb, Cji = fSji - fSj * ib, Cii = fSii - fSi * ib;
+    const T Cjw = (T)Twj - fSj * t0, Ciw = (T)Twi - fSi * t0, Cww = (T)Tww - fT0 * t0;
+    const T idet = Fn<T>::rcp(Cjj * Cii - Cji * Cji);
+    const T bj = (Cii * Cjw - Cji * Ciw) * idet;   // d omega / d j
+    const T bi = (Cjj * Ciw - Cji * Cjw) * idet;   // d omega / d i
+    const T bc = ((T)m + t0) - bj * jb - bi * ib;  // omega at the window centre pixel
+    const T ax = qw * bj * Fn<T>::rcp(a), ay = qw * bi * Fn<T>::rcp(b);
+    const T ac = qw * bc - ax * tx - ay * ty;
+    const T s = Fn<T>::rsqrt(ax * ax + ay * ay + ac * ac);
+    o.nx = -ax * s; o.ny = -ay * s; o.nz = -ac * s;
+    o.d = s;
+    orient<T>(o.nx, o.ny, o.nz, o.d);
+    const T res = Cww - bj * Cjw - bi * Ciw;
+    o.curv = (res > T(0) ? res : T(0)) * qw * qw * inv_n;
+    o.gap = T(1);
+    return o;
+}
+
+// Eq. 7-9: Z = ae X + be Y + ce, regression of Z on (X, Y) from the
+// covariance of the window's points (as in solve_standard).  The plane
+// ae X + be Y - Z + ce = 0 is normalised and oriented.  fSj .. fSii are the
+// image moments of the valid pixels (rank test).
+template <typename T = float>
+__device__ __forceinline__ FitOutT<T> solve_explicit_standard(T nf, T fSj, T fSi, T fSjj, T fSji, T fSii,
+                                                              int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
+                                                              int64_t Szzj, int64_t Szzi, int64_t Szzjj,
+                                                              int64_t Szzji, int64_t Szzii, T qz, T tx, T ty, T a,
+                                                              T b, bool& ok) {
+    FitOutT<T> o;
+    const T inv_n = Fn<T>::rcp(nf);
+    const int n = (int)nf;
+    const int m = __float2int_rn((float)((T)Sz * inv_n));
+    const int64_t T0 = Sz - (int64_t)n * m;
+    const int64_t Tzz = Szz - (int64_t)m * (Sz + T0);
+    const int64_t Tzj = Szzj - (int64_t)m * Szj;
+    const int64_t Tzi = Szzi - (int64_t)m * Szi;
+    const T t0 = (T)(int)T0 * inv_n;
+    const T fSzj = (T)Szj, fSzi = (T)Szi;
+    const T Czz = (T)Tzz - (T)(int)T0 * t0;
+    const T Cjz = (T)Tzj - fSzj * t0;
+    const T Ciz = (T)Tzi - fSzi * t0;
+    const T qj = fSzj * inv_n, qi = fSzi * inv_n;
+    const T Cjj = (T)Szzjj - fSzj * qj, Cji = (T)Szzji - fSzj * qi, Cii = (T)Szzii - fSzi * qi;
+    const T Cxx = a * a * Cjj + T(2) * a * tx * Cjz + tx * tx * Czz;
+    const T Cxy = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
+    const T Cxz = a * Cjz + tx * Czz;
+    const T Cyy = b * b * Cii + T(2) * b * ty * Ciz + ty * ty * Czz;
+    const T Cyz = b * Ciz + ty * Czz;
+    const T det = Cxx * Cyy - Cxy * Cxy;
+    ok = pixels_span_plane<T>(nf, fSj, fSi, fSjj, fSji, fSii);
+    const T idet = Fn<T>::rcp(det);
+    const T ae = (Cyy * Cxz - Cxy * Cyz) * idet;
+    const T be = (Cxx * Cyz - Cxy * Cxz) * idet;
+    const T zb = (T)m + t0;
+    const T px = a * qj + tx * zb, py = b * qi + ty * zb;
+    const T ce = (zb - ae * px - be * py) * qz;
+    const T s = Fn<T>::rsqrt(ae * ae + be * be + T(1));
+    o.nx = ae * s; o.ny = be * s; o.nz = -s;
+    o.d = ce * s;
+    orient<T>(o.nx, o.ny, o.nz, o.d);
+    const T res = Czz - ae * Cxz - be * Cyz;
+    o.curv = (res > T(0) ? res : T(0)) * qz * qz * inv_n;
+    o.gap = T(1);
+    return o;
+}
+
+// ---------------------------------------------------------------------------
 // Backward: adjoint of the implicit fit of one window with respect to its
 // Schur complement R (any units), for upstream gradients gn (normal), gk
 // (curvature).  n = sigma v0 with the orientation sign sigma locally constant.

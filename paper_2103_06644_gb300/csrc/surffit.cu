@@ -42,6 +42,12 @@ constexpr int kHThreads = 128;   // rows per hpass block
 constexpr int kHSeg = 64;        // default output columns per hpass thread (runtime: 32..128)
 constexpr int kVThreads = 128;   // columns per vpass block
 
+// The moments an explicit fit needs are those of its implicit counterpart.
+__host__ __device__ constexpr int base_method(int M) {
+    return M == SF_METHOD_EXPLICIT_DISPARITY ? SF_METHOD_DISPARITY
+                                             : (M == SF_METHOD_EXPLICIT_STANDARD ? SF_METHOD_STANDARD : M);
+}
+
 // ---------------------------------------------------------------------------
 // Depth decoding.
 // ---------------------------------------------------------------------------
@@ -65,7 +71,7 @@ __device__ __forceinline__ bool depth_valid(float z) { return z > 0.f && z < INF
 //   folded into the quantum), standard Z (float32) or raw (uint16).
 template <int DT, int M>
 __device__ __forceinline__ float fit_variable_of(float zin) {
-    if (M == SF_METHOD_DISPARITY) return rcp_approx(zin);
+    if (base_method(M) == SF_METHOD_DISPARITY) return rcp_approx(zin);
     return zin;
 }
 
@@ -103,17 +109,17 @@ template <int DT, int M>
 __device__ __forceinline__ int quantize(const void* depth, size_t idx, float sc) {
     const float zin = load_raw<DT>(depth, idx);
     if (!depth_valid(zin)) return -1;
-    if (DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD) return (int)zin;
-    if (M == SF_METHOD_DISPARITY) return quant_recip(zin, sc);
+    if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_STANDARD) return (int)zin;
+    if (base_method(M) == SF_METHOD_DISPARITY) return quant_recip(zin, sc);
     return __float2int_rn(zin * sc);
 }
 
 // Metric size of one fixed-point unit.
 template <int DT, int M>
 __device__ __forceinline__ float quantum(unsigned vmax_bits, int bits, float scale) {
-    if (DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD) return scale;
+    if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_STANDARD) return scale;
     const float q = ldexpf(1.f, -quant_exponent(vmax_bits, bits));
-    if (DT == SF_DEPTH_U16 && M == SF_METHOD_DISPARITY) return q / scale;
+    if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_DISPARITY) return q / scale;
     return q;
 }
 
@@ -238,7 +244,7 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
                 h0 += 1; h1 += j; h2 += j * j;
                 a0 += v; a1 += (int64_t)v * j;
                 s0 += vv;
-                if (M == SF_METHOD_STANDARD) { s1 += vv * j; s2 += vv * (j * j); }
+                if (base_method(M) == SF_METHOD_STANDARD) { s1 += vv * j; s2 += vv * (j * j); }
             }
         }
         for (int xb = x0; xb < xend; xb += 4) {
@@ -247,8 +253,7 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int x = xb + u;
-                if (M == SF_METHOD_DISPARITY) hmv[u] = pack_mask(h0, h1, h2);
-                else hmv[u] = h0;
+                hmv[u] = pack_mask(h0, h1, h2);
                 c0v[u] = a0; c1v[u] = a1; c2v[u] = s0; c3v[u] = s1; c4v[u] = s2;
                 if (x + 1 < xend) {
                     const int vo = row[x - x0];              // column x - r leaves
@@ -258,7 +263,7 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
                     const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
                     slide2(a0, a1, co, ci, r);
                     const int64_t qo = co * co, qi = ci * ci;
-                    if (M == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
+                    if (base_method(M) == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
                     else s0 = s0 - qo + qi;
                 }
             }
@@ -274,7 +279,7 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
                 *reinterpret_cast<longlong2*>(c1 + 2) = make_longlong2(c1v[2], c1v[3]);
                 *reinterpret_cast<longlong2*>(c2) = make_longlong2(c2v[0], c2v[1]);
                 *reinterpret_cast<longlong2*>(c2 + 2) = make_longlong2(c2v[2], c2v[3]);
-                if (M == SF_METHOD_STANDARD) {
+                if (base_method(M) == SF_METHOD_STANDARD) {
                     int64_t* c3 = P.c64(3) + o;
                     int64_t* c4 = P.c64(4) + o;
                     *reinterpret_cast<longlong2*>(c3) = make_longlong2(c3v[0], c3v[1]);
@@ -286,7 +291,7 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
                 for (int u = 0; u < 4 && xb + u < xend; ++u) {
                     P.p32[o + u] = hmv[u];
                     P.c64(0)[o + u] = c0v[u]; P.c64(1)[o + u] = c1v[u]; P.c64(2)[o + u] = c2v[u];
-                    if (M == SF_METHOD_STANDARD) { P.c64(3)[o + u] = c3v[u]; P.c64(4)[o + u] = c4v[u]; }
+                    if (base_method(M) == SF_METHOD_STANDARD) { P.c64(3)[o + u] = c3v[u]; P.c64(4)[o + u] = c4v[u]; }
                 }
             }
         }
@@ -364,40 +369,57 @@ struct DispState {
     __device__ __forceinline__ int count() const { return (int)n; }
 };
 
-// Vertical running sums of the standard form's moments for one column.
-struct StdState {
+// Vertical running sums of the standard form's moments for one column.  With
+// kMask the image moments of the valid pixels (sum j, j^2, i, ji, i^2) are
+// kept too: the explicit standard fit needs them for its rank test.
+template <bool kMask = false>
+struct StdStateT {
     const int32_t* hc; const int64_t* z0; const int64_t* z1; const int64_t* b0; const int64_t* b1; const int64_t* b2;
     int n = 0;
+    float fn = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;  // kMask only
     int64_t Sz = 0, Szi = 0, Szj = 0, Szz = 0, Szzi = 0, Szzii = 0, Szzj = 0, Szzji = 0, Szzjj = 0;
-    __device__ StdState(const Planes& P)
+    __device__ StdStateT(const Planes& P)
         : hc(P.p32), z0(P.c64(0)), z1(P.c64(1)), b0(P.c64(2)), b1(P.c64(3)), b2(P.c64(4)) {}
     __device__ __forceinline__ void init(size_t pb, int Wp, int H, int y0, int r) {
         for (int yy = y0 - r; yy <= y0 + r; ++yy) {
             if (yy < 0 || yy >= H) continue;
             const size_t o = pb + (size_t)yy * Wp;
             const int64_t i = yy - y0;
-            n += __ldg(hc + o);
-            const int64_t c0 = __ldg(z0 + o), q0v = __ldg(b0 + o), q1v = __ldg(b1 + o);
-            Sz += c0; Szi += i * c0; Szj += __ldg(z1 + o);
+            int c0, c1, c2;
+            unpack_mask(__ldg(hc + o), c0, c1, c2);
+            n += c0;
+            if constexpr (kMask) {
+                const float fi = (float)i, f0 = (float)c0, f1 = (float)c1;
+                fn += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
+            }
+            const int64_t c0z = __ldg(z0 + o), q0v = __ldg(b0 + o), q1v = __ldg(b1 + o);
+            Sz += c0z; Szi += i * c0z; Szj += __ldg(z1 + o);
             Szz += q0v; Szzi += i * q0v; Szzii += i * i * q0v;
             Szzj += q1v; Szzji += i * q1v; Szzjj += __ldg(b2 + o);
         }
     }
     __device__ __forceinline__ void slide(size_t pb, int Wp, int H, int y, int r) {
         const int yo = y - r, yi = y + r + 1;
-        int co = 0, ci = 0;
+        int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
         int64_t zo = 0, zjo = 0, qo0 = 0, qo1 = 0, qo2 = 0, zi = 0, zji = 0, qi0 = 0, qi1 = 0, qi2 = 0;
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * Wp;
-            co = __ldg(hc + o); zo = __ldg(z0 + o); zjo = __ldg(z1 + o);
+            unpack_mask(__ldg(hc + o), o0, o1, o2);
+            zo = __ldg(z0 + o); zjo = __ldg(z1 + o);
             qo0 = __ldg(b0 + o); qo1 = __ldg(b1 + o); qo2 = __ldg(b2 + o);
         }
         if (yi < H) {
             const size_t o = pb + (size_t)yi * Wp;
-            ci = __ldg(hc + o); zi = __ldg(z0 + o); zji = __ldg(z1 + o);
+            unpack_mask(__ldg(hc + o), i0, i1, i2);
+            zi = __ldg(z0 + o); zji = __ldg(z1 + o);
             qi0 = __ldg(b0 + o); qi1 = __ldg(b1 + o); qi2 = __ldg(b2 + o);
         }
-        n += ci - co;
+        n += i0 - o0;
+        if constexpr (kMask) {
+            slide3(fn, Si, Sii, (float)o0, (float)i0, r);
+            slide2(Sj, Sji, (float)o1, (float)i1, r);
+            Sjj += (float)(i2 - o2);
+        }
         slide2(Sz, Szi, zo, zi, r);
         Szj += zji - zjo;
         slide3(Szz, Szzi, Szzii, qo0, qi0, r);
@@ -406,6 +428,7 @@ struct StdState {
     }
     __device__ __forceinline__ int count() const { return n; }
 };
+using StdState = StdStateT<false>;
 
 // Vertical moments + solve for one column x of one frame, output rows
 // [y0, y0 + band).  `depth` and the output pointers point at the frame.
@@ -421,22 +444,33 @@ __device__ __forceinline__ void vpass_column(const void* __restrict__ depth, int
     const int y1 = min(y0 + band, H);
     const size_t pb = pofs + x;
     const float tx = txt[x];
-    typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
+    constexpr int B = base_method(M);
+    typename std::conditional<B == SF_METHOD_DISPARITY, DispState,
+                              StdStateT<M == SF_METHOD_EXPLICIT_STANDARD>>::type S(P);
     S.init(pb, Wp, H, y0, r);
     for (int y = y0; y < y1; ++y) {
         const size_t oi = (size_t)y * W + x;
         const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
         const int n = S.count();
-        const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
+        bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
         float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
+        FitOut fo_;
         if (ok) {
-            FitOut fo_;
             if constexpr (M == SF_METHOD_DISPARITY)
                 fo_ = solve_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, tyt[y],
                                       a, b);
-            else
+            else if constexpr (M == SF_METHOD_STANDARD)
                 fo_ = solve_standard((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
                                      S.Szzii, q, tx, tyt[y], a, b);
+            else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY)
+                fo_ = solve_explicit_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q,
+                                               tx, tyt[y], a, b, ok);
+            else
+                fo_ = solve_explicit_standard((float)S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sz, S.Szj, S.Szi,
+                                              S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji, S.Szzii, q, tx, tyt[y], a, b,
+                                              ok);
+        }
+        if (ok) {
             nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
             if (flags && !(fo_.gap >= tau)) {
                 // near-degenerate window: queue it for the FP64 re-solve
@@ -598,17 +632,31 @@ __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, float
         const double tx = rays[x], ty = rays[W + y];  // FP64 ray tangents
         const double a = rays[W + H], b = rays[W + H + 1];
         FitOutT<double> o;
+        bool ok = true;
         if constexpr (M == SF_METHOD_DISPARITY) {
             DispState S(P);
             S.init(pb, Wp, H, y, r);
             o = solve_disparity<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj, (double)S.Sji,
                                         (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty, a, b);
-        } else {
+        } else if constexpr (M == SF_METHOD_STANDARD) {
             StdState S(P);
             S.init(pb, Wp, H, y, r);
             o = solve_standard<double>((double)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
                                        S.Szzii, q, tx, ty, a, b);
+        } else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY) {
+            DispState S(P);
+            S.init(pb, Wp, H, y, r);
+            o = solve_explicit_disparity<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj,
+                                                 (double)S.Sji, (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty,
+                                                 a, b, ok);
+        } else {
+            StdStateT<true> S(P);
+            S.init(pb, Wp, H, y, r);
+            o = solve_explicit_standard<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj,
+                                                (double)S.Sji, (double)S.Sii, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj,
+                                                S.Szzi, S.Szzjj, S.Szzji, S.Szzii, q, tx, ty, a, b, ok);
         }
+        if (!ok) o.nx = o.ny = o.nz = o.d = o.curv = NAN;
         const size_t oi = (size_t)f * W * H + (size_t)y * W + x;
         normals[3 * oi] = (float)o.nx; normals[3 * oi + 1] = (float)o.ny; normals[3 * oi + 2] = (float)o.nz;
         offsets[oi] = (float)o.d;
@@ -838,7 +886,7 @@ sf_status cuda_fail(cudaError_t e, const char* what) {
 
 size_t plane_bytes_per_frame(int method, size_t plane_elems) {
     // disparity: 1 x int32 + 3 x int64 ; standard: 1 x int32 + 5 x int64
-    return plane_elems * (method == SF_METHOD_STANDARD ? (4 + 5 * 8) : (4 + 3 * 8));
+    return plane_elems * (sf::base_method(method) == SF_METHOD_STANDARD ? (4 + 5 * 8) : (4 + 3 * 8));
 }
 
 // Fixed-point bits for a method and window: the most that keeps every exact
@@ -955,14 +1003,15 @@ template <int DT, int M>
 static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,
                              int32_t* counts, cudaStream_t st) {
     const size_t fe = (size_t)c->W * c->H;
-    const int raw_z = (DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD) ? 1 : 0;
+    constexpr int B = sf::base_method(M);  // range and horizontal pass depend on the moments only
+    const int raw_z = (DT == SF_DEPTH_U16 && B == SF_METHOD_STANDARD) ? 1 : 0;
     const int bits = quant_bits(M, c->k);
     SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
     if (!raw_z) {
         StageTimer t(c, 0, st);
         int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
         blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
-        sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, c->depth_scale, c->vmax);
+        sf::range_kernel<DT, B><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, c->depth_scale, c->vmax);
     }
     {
         StageTimer t(c, 1, st);
@@ -970,7 +1019,7 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
         dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
         const int IW = seg + 2 * c->r;
         const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
-        sf::hpass_kernel<DT, M><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
+        sf::hpass_kernel<DT, B><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
                                                                   bits, raw_z, c->Wp, c->plane_elems, c->planes, seg);
     }
     {
@@ -996,6 +1045,21 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return SF_OK;
+}
+
+template <int DT>
+static sf_status launch_pass_for(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,
+                                 int32_t* counts, cudaStream_t st) {
+    switch (c->method) {
+        case SF_METHOD_DISPARITY:
+            return launch_pass<DT, SF_METHOD_DISPARITY>(c, nfr, depth, normals, offsets, curv, counts, st);
+        case SF_METHOD_STANDARD:
+            return launch_pass<DT, SF_METHOD_STANDARD>(c, nfr, depth, normals, offsets, curv, counts, st);
+        case SF_METHOD_EXPLICIT_DISPARITY:
+            return launch_pass<DT, SF_METHOD_EXPLICIT_DISPARITY>(c, nfr, depth, normals, offsets, curv, counts, st);
+        default:
+            return launch_pass<DT, SF_METHOD_EXPLICIT_STANDARD>(c, nfr, depth, normals, offsets, curv, counts, st);
+    }
 }
 
 template <int DT, int M>
@@ -1167,8 +1231,6 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
     if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
     if (n_frames == 0) return SF_OK;
     if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
-    if (c->method == SF_METHOD_EXPLICIT_DISPARITY || c->method == SF_METHOD_EXPLICIT_STANDARD)
-        return fail(SF_ERR_UNSUPPORTED, "explicit fits are not built in this library version");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t fe = (size_t)c->W * c->H;
     const size_t dbytes = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
@@ -1193,15 +1255,8 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
         float* op = offsets + fe * f0;
         float* cp = curvature + fe * f0;
         int32_t* kp = counts ? counts + fe * f0 : nullptr;
-        if (c->depth_type == SF_DEPTH_F32) {
-            s = c->method == SF_METHOD_DISPARITY
-                    ? launch_pass<SF_DEPTH_F32, SF_METHOD_DISPARITY>(c, nfr, dp, np_, op, cp, kp, st)
-                    : launch_pass<SF_DEPTH_F32, SF_METHOD_STANDARD>(c, nfr, dp, np_, op, cp, kp, st);
-        } else {
-            s = c->method == SF_METHOD_DISPARITY
-                    ? launch_pass<SF_DEPTH_U16, SF_METHOD_DISPARITY>(c, nfr, dp, np_, op, cp, kp, st)
-                    : launch_pass<SF_DEPTH_U16, SF_METHOD_STANDARD>(c, nfr, dp, np_, op, cp, kp, st);
-        }
+        s = c->depth_type == SF_DEPTH_F32 ? launch_pass_for<SF_DEPTH_F32>(c, nfr, dp, np_, op, cp, kp, st)
+                                          : launch_pass_for<SF_DEPTH_U16>(c, nfr, dp, np_, op, cp, kp, st);
         if (s != SF_OK) return s;
     }
     return SF_OK;

@@ -87,3 +87,67 @@ def compare(gpu, ref, *, angle_tol=ANGLE_TOL, offset_tol=OFFSET_TOL, gap_min=GAP
         stats["degenerate_max_excess"] = float(excess.max())
         assert excess.max() < 1e-3, "%s: degenerate windows not minimised (%g)" % (label, excess.max())
     return stats
+
+
+# Explicit fits (Section I.D, Section II.B) are linear least squares: their
+# slopes move by about cond(C) * eps under rounding, C the centred 2x2
+# covariance of the regressors ((tx, ty) for Eq. 15-16, (X, Y) for Eq. 7-9),
+# so the tolerances apply where 1/cond(C) >= COND_MIN.  The third output, the
+# mean squared residual, is compared against the variance of the target: it is
+# the difference of that variance and the explained part, so its float32 error
+# is about eps * cond(C) of the variance (up to ~1e-4 at COND_MIN).
+COND_MIN = 1e-3
+RESID_TOL = 1e-4
+
+
+def explicit_design(moments):
+    """(1/cond of the centred regressor covariance, n) from the oracle's moments."""
+    mo = moments
+    n = mo[..., 5]
+    c11 = mo[..., 0] - mo[..., 2] ** 2 / n
+    c12 = mo[..., 1] - mo[..., 2] * mo[..., 4] / n
+    c22 = mo[..., 3] - mo[..., 4] ** 2 / n
+    tr = c11 + c22
+    disc = np.sqrt(np.maximum((c11 - c22) ** 2 + 4 * c12 ** 2, 0.0))
+    lmax, lmin = (tr + disc) / 2, (tr - disc) / 2
+    return np.where(lmax > 0, lmin / np.where(lmax > 0, lmax, 1.0), 0.0), n
+
+
+def compare_explicit(gpu, ref, method, *, angle_tol=ANGLE_TOL, offset_tol=OFFSET_TOL, cond_min=COND_MIN,
+                     resid_tol=RESID_TOL, label=""):
+    """Check an explicit fit (method explicit_disparity / explicit_standard) against the oracle dict."""
+    n, d, c, cnt = [np.asarray(v) for v in gpu]
+    assert np.array_equal(cnt, ref["counts"]), "%s: counts differ at %d pixels" % (label, (cnt != ref["counts"]).sum())
+    ok = np.isfinite(ref["offsets"])
+    assert np.array_equal(np.isfinite(d), ok), "%s: validity mask differs at %d pixels" % (
+        label, (np.isfinite(d) != ok).sum())
+    assert np.array_equal(np.isfinite(n).all(-1), ok) and np.array_equal(np.isfinite(c), ok)
+    stats = {"valid": int(ok.sum()), "pixels": int(ok.size)}
+    if not ok.any():
+        return stats
+    mo = np.where(ok[..., None], ref["moments"], 1.0)
+    rc, cnt_f = explicit_design(mo)
+    good = ok & (rc >= cond_min)
+    # centroid of the window's points: the scale of the offset
+    if method == "explicit_disparity":   # A = sum m m^T (rays), g = sum m / Z
+        mu = np.linalg.norm(np.stack([mo[..., 2], mo[..., 4], cnt_f], -1), axis=-1) / mo[..., 8]
+    else:                                # A = sum [X, Y, 1][X, Y, 1]^T, g = sum Z [X, Y, 1]
+        mu = np.linalg.norm(np.stack([mo[..., 2], mo[..., 4], mo[..., 8]], -1), axis=-1) / cnt_f
+    var_b = np.maximum(mo[..., 9] / cnt_f - (mo[..., 8] / cnt_f) ** 2, 0.0)
+    ang = angle(n[good], ref["normals"][good])
+    rel = np.abs(d[good].astype(np.float64) - ref["offsets"][good]) / mu[good]
+    # a window of equal targets has variance 0 and residual 0; the oracle's
+    # uncentred residual then carries FP64 rounding of the mean square
+    denom = np.maximum(var_b, 1e-9 * mo[..., 9] / cnt_f)
+    cerr = np.abs(c[good].astype(np.float64) - ref["curvature"][good]) / denom[good]
+    stats.update(good=int(good.sum()), max_angle=float(ang.max(initial=0)), max_offset_rel=float(rel.max(initial=0)),
+                 max_resid_rel=float(cerr.max(initial=0)), ill_conditioned=int((ok & ~good).sum()),
+                 rc_at_max_resid=float(rc[good][np.argmax(cerr)]) if cerr.size else 0.0)
+    assert stats["max_angle"] <= angle_tol, "%s: normal angle %g > %g" % (label, stats["max_angle"], angle_tol)
+    assert stats["max_offset_rel"] <= offset_tol, "%s: offset %g > %g" % (label, stats["max_offset_rel"], offset_tol)
+    assert stats["max_resid_rel"] <= resid_tol, "%s: residual %g > %g" % (label, stats["max_resid_rel"], resid_tol)
+    nn = np.linalg.norm(n[ok].astype(np.float64), axis=-1)
+    assert np.max(np.abs(nn - 1)) < 1e-5, "%s: normals not unit" % label
+    assert np.all(d[ok] >= 0), "%s: offsets negative" % label
+    assert np.all(c[ok] >= 0), "%s: residual negative" % label
+    return stats
