@@ -214,8 +214,8 @@ sf_status sf_batch_destroy(sf_batch* batch);
 
 /*
  * sf_set_tiles -- tile shape of a context: hseg in {32, 64, 128} columns per
- * horizontal tile, vband rows per vertical band (0 = chosen from the grid
- * size, else 8..1024).  Results do not depend on the tiles: the window sums
+ * horizontal tile (default 32), vband rows per vertical band (0 = chosen
+ * from the grid size, else 8..1024).  Results do not depend on the tiles: the window sums
  * are exact.
  */
 sf_status sf_set_tiles(sf_ctx* ctx, int hseg, int vband);

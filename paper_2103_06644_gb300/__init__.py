@@ -72,7 +72,7 @@ class SurfaceFitter:
                                                   float(depth_scale), int(min_valid), int(bool(require_center))))
         self.method, self.depth_type, self.depth_scale = method, depth_type, float(depth_scale)
 
-    def set_tiles(self, hseg: int = 64, vband: int = 0) -> None:
+    def set_tiles(self, hseg: int = 32, vband: int = 0) -> None:
         """Tile shape: hseg in {32, 64, 128} columns, vband rows per band (0 = automatic)."""
         _native.check(_native.lib().sf_set_tiles(self._h, int(hseg), int(vband)))
 

@@ -61,6 +61,14 @@ template <> struct Fn<float> {
     static __device__ __forceinline__ void sincos(float x, float* s, float* c) { __sincosf(x, s, c); }
     static __device__ __forceinline__ float tiny() { return 1e-36f; }
     static __device__ __forceinline__ float p2min() { return 1e-20f; }
+    // int64 -> float32 from two signed 32-bit parts, v = hi 2^32 + lo with
+    // lo in [-2^31, 2^31) (within 1 ulp): a direct 64-bit conversion executes
+    // on the FP64 unit, a few per SM and clock.
+    static __device__ __forceinline__ float from_i64(int64_t v) {
+        const int lo = (int)(uint32_t)v;
+        const int hi = (int)((v - (int64_t)lo) >> 32);
+        return fmaf((float)hi, 4294967296.f, (float)lo);
+    }
 };
 template <> struct Fn<double> {
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
@@ -70,6 +78,7 @@ template <> struct Fn<double> {
     static __device__ __forceinline__ void sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
     static __device__ __forceinline__ double tiny() { return 1e-280; }
     static __device__ __forceinline__ double p2min() { return 1e-40; }
+    static __device__ __forceinline__ double from_i64(int64_t v) { return (double)v; }
 };
 
 // Null vector of the symmetric matrix M = R - l I: the column of the
@@ -196,7 +205,7 @@ __device__ __forceinline__ DispWindowT<T> build_disparity(T nf, T fSj, T fSi, T 
     const T inv_n = Fn<T>::rcp(nf);
     const int n = (int)nf, Sj = (int)fSj, Si = (int)fSi;
     // exact re-centring on an integer m near the mean disparity (m < 2^31)
-    const int m = __float2int_rn((float)((T)Sw * inv_n));
+    const int m = __float2int_rn((float)(Fn<T>::from_i64(Sw) * inv_n));
     const int64_t T0 = Sw - (int64_t)n * m;
     const int64_t Tww = Sww - (int64_t)m * (Sw + T0);            // sum (w - m)^2
     const int64_t Twj = Swj - (int64_t)m * Sj;                   // sum (w - m) j
@@ -207,9 +216,9 @@ __device__ __forceinline__ DispWindowT<T> build_disparity(T nf, T fSj, T fSi, T 
     const T Cjj = fSjj - fSj * jb;
     const T Cji = fSji - fSj * ib;
     const T Cii = fSii - fSi * ib;
-    const T Cjw = (T)Twj - fSj * t0;
-    const T Ciw = (T)Twi - fSi * t0;
-    const T Cww = (T)Tww - fT0 * t0;
+    const T Cjw = Fn<T>::from_i64(Twj) - fSj * t0;
+    const T Ciw = Fn<T>::from_i64(Twi) - fSi * t0;
+    const T Cww = Fn<T>::from_i64(Tww) - fT0 * t0;
     const T wbar = (T)m + t0;  // mean disparity (units of qw)
     const T inv_nw = Fn<T>::rcp(nf * wbar);
     const T dj = Cjw * inv_nw;     // jhat - jbar
@@ -263,20 +272,20 @@ __device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t S
                                                      int64_t Szzii, T qz, T tx, T ty, T a, T b) {
     const T inv_n = Fn<T>::rcp(nf);
     const int n = (int)nf;
-    const int m = __float2int_rn((float)((T)Sz * inv_n));       // m < 2^31
+    const int m = __float2int_rn((float)(Fn<T>::from_i64(Sz) * inv_n));       // m < 2^31
     const int64_t T0 = Sz - (int64_t)n * m;
     const int64_t Tzz = Szz - (int64_t)m * (Sz + T0);           // sum (z - m)^2
     const int64_t Tzj = Szzj - (int64_t)m * Szj;                // sum z j (z - m)
     const int64_t Tzi = Szzi - (int64_t)m * Szi;                // sum z i (z - m)
     const T t0 = (T)(int)T0 * inv_n;                            // zbar - m
-    const T fSzj = (T)Szj, fSzi = (T)Szi;
-    const T Czz = (T)Tzz - (T)(int)T0 * t0;
-    const T Cjz = (T)Tzj - fSzj * t0;
-    const T Ciz = (T)Tzi - fSzi * t0;
+    const T fSzj = Fn<T>::from_i64(Szj), fSzi = Fn<T>::from_i64(Szi);
+    const T Czz = Fn<T>::from_i64(Tzz) - (T)(int)T0 * t0;
+    const T Cjz = Fn<T>::from_i64(Tzj) - fSzj * t0;
+    const T Ciz = Fn<T>::from_i64(Tzi) - fSzi * t0;
     const T qj = fSzj * inv_n, qi = fSzi * inv_n;               // means of z j, z i
-    const T Cjj = (T)Szzjj - fSzj * qj;
-    const T Cji = (T)Szzji - fSzj * qi;
-    const T Cii = (T)Szzii - fSzi * qi;
+    const T Cjj = Fn<T>::from_i64(Szzjj) - fSzj * qj;
+    const T Cji = Fn<T>::from_i64(Szzji) - fSzj * qi;
+    const T Cii = Fn<T>::from_i64(Szzii) - fSzi * qi;
     const T R11 = a * a * Cjj + T(2) * a * tx * Cjz + tx * tx * Czz;
     const T R12 = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
     const T R13 = a * Cjz + tx * Czz;
@@ -325,7 +334,7 @@ __device__ __forceinline__ FitOutT<T> solve_explicit_disparity(T nf, T fSj, T fS
     const int n = (int)nf, Sj = (int)fSj, Si = (int)fSi;
     ok = pixels_span_plane<T>(nf, fSj, fSi, fSjj, fSji, fSii);
     const T inv_n = Fn<T>::rcp(nf);
-    const int m = __float2int_rn((float)((T)Sw * inv_n));
+    const int m = __float2int_rn((float)(Fn<T>::from_i64(Sw) * inv_n));
     const int64_t T0 = Sw - (int64_t)n * m;
     const int64_t Tww = Sww - (int64_t)m * (Sw + T0);
     const int64_t Twj = Swj - (int64_t)m * Sj;
@@ -334,7 +343,7 @@ __device__ __forceinline__ FitOutT<T> solve_explicit_disparity(T nf, T fSj, T fS
     const T t0 = fT0 * inv_n;
     const T jb = fSj * inv_n, ib = fSi * inv_n;
     const T Cjj = fSjj - fSj * jb, Cji = fSji - fSj * ib, Cii = fSii - fSi * ib;
-    const T Cjw = (T)Twj - fSj * t0, Ciw = (T)Twi - fSi * t0, Cww = (T)Tww - fT0 * t0;
+    const T Cjw = Fn<T>::from_i64(Twj) - fSj * t0, Ciw = Fn<T>::from_i64(Twi) - fSi * t0, Cww = Fn<T>::from_i64(Tww) - fT0 * t0;
     const T idet = Fn<T>::rcp(Cjj * Cii - Cji * Cji);
     const T bj = (Cii * Cjw - Cji * Ciw) * idet;   // d omega / d j
     const T bi = (Cjj * Ciw - Cji * Cjw) * idet;   // d omega / d i
@@ -364,18 +373,18 @@ __device__ __forceinline__ FitOutT<T> solve_explicit_standard(T nf, T fSj, T fSi
     FitOutT<T> o;
     const T inv_n = Fn<T>::rcp(nf);
     const int n = (int)nf;
-    const int m = __float2int_rn((float)((T)Sz * inv_n));
+    const int m = __float2int_rn((float)(Fn<T>::from_i64(Sz) * inv_n));
     const int64_t T0 = Sz - (int64_t)n * m;
     const int64_t Tzz = Szz - (int64_t)m * (Sz + T0);
     const int64_t Tzj = Szzj - (int64_t)m * Szj;
     const int64_t Tzi = Szzi - (int64_t)m * Szi;
     const T t0 = (T)(int)T0 * inv_n;
-    const T fSzj = (T)Szj, fSzi = (T)Szi;
-    const T Czz = (T)Tzz - (T)(int)T0 * t0;
-    const T Cjz = (T)Tzj - fSzj * t0;
-    const T Ciz = (T)Tzi - fSzi * t0;
+    const T fSzj = Fn<T>::from_i64(Szj), fSzi = Fn<T>::from_i64(Szi);
+    const T Czz = Fn<T>::from_i64(Tzz) - (T)(int)T0 * t0;
+    const T Cjz = Fn<T>::from_i64(Tzj) - fSzj * t0;
+    const T Ciz = Fn<T>::from_i64(Tzi) - fSzi * t0;
     const T qj = fSzj * inv_n, qi = fSzi * inv_n;
-    const T Cjj = (T)Szzjj - fSzj * qj, Cji = (T)Szzji - fSzj * qi, Cii = (T)Szzii - fSzi * qi;
+    const T Cjj = Fn<T>::from_i64(Szzjj) - fSzj * qj, Cji = Fn<T>::from_i64(Szzji) - fSzj * qi, Cii = Fn<T>::from_i64(Szzii) - fSzi * qi;
     const T Cxx = a * a * Cjj + T(2) * a * tx * Cjz + tx * tx * Czz;
     const T Cxy = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
     const T Cxz = a * Cjz + tx * Czz;

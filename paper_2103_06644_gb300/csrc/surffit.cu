@@ -39,14 +39,20 @@ namespace sf {
 
 constexpr int kMaxR = (SF_MAX_WINDOW - 1) / 2;
 constexpr int kHThreads = 128;   // rows per hpass block
-constexpr int kHSeg = 64;        // default output columns per hpass thread (runtime: 32..128)
+constexpr int kHSeg = 32;        // default output columns per hpass thread (runtime: 32..128)
 constexpr int kVThreads = 128;   // columns per vpass block
+
 
 // The moments an explicit fit needs are those of its implicit counterpart.
 __host__ __device__ constexpr int base_method(int M) {
     return M == SF_METHOD_EXPLICIT_DISPARITY ? SF_METHOD_DISPARITY
                                              : (M == SF_METHOD_EXPLICIT_STANDARD ? SF_METHOD_STANDARD : M);
 }
+
+// Register budget of the vertical-pass kernels, as resident blocks per SM:
+// 8 (32 warps, 64 registers) for the disparity form, 6 for the standard form
+// whose state is larger.  Latency hiding of the scratch loads needs the warps.
+__host__ __device__ constexpr int vblocks(int M) { return base_method(M) == SF_METHOD_STANDARD ? 6 : 8; }
 
 // ---------------------------------------------------------------------------
 // Depth decoding.
@@ -104,14 +110,19 @@ __device__ __forceinline__ int quant_exponent(unsigned vmax_bits, int bits) {
     return bits - E;
 }
 
-// Fixed-point value of a valid pixel (>= 0), or -1 for a missing one.
+// Fixed-point value of a valid pixel (>= 0), or -1 for a missing one, from
+// its raw stored value.
 template <int DT, int M>
-__device__ __forceinline__ int quantize(const void* depth, size_t idx, float sc) {
-    const float zin = load_raw<DT>(depth, idx);
+__device__ __forceinline__ int quantize_raw(float zin, float sc) {
     if (!depth_valid(zin)) return -1;
     if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_STANDARD) return (int)zin;
     if (base_method(M) == SF_METHOD_DISPARITY) return quant_recip(zin, sc);
     return __float2int_rn(zin * sc);
+}
+
+template <int DT, int M>
+__device__ __forceinline__ int quantize(const void* depth, size_t idx, float sc) {
+    return quantize_raw<DT, M>(load_raw<DT>(depth, idx), sc);
 }
 
 // Metric size of one fixed-point unit.
@@ -132,10 +143,19 @@ __global__ void __launch_bounds__(256) range_kernel(const void* __restrict__ dep
     const int f = blockIdx.y;
     const size_t base = (size_t)f * frame_elems;
     float vmax = 0.f;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < frame_elems;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const float z = load_raw<DT>(depth, base + i);
-        if (depth_valid(z)) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z));
+    // eight independent loads in flight per thread (issue is in order: a
+    // load consumed right away would expose its whole latency)
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < frame_elems; i0 += 8 * stride) {
+        float z[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const size_t i = i0 + u * stride;
+            z[u] = i < frame_elems ? load_raw<DT>(depth, base + i) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (depth_valid(z[u])) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z[u]));
     }
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     __shared__ float red[8];
@@ -215,15 +235,32 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
     const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
     const int rows = min(kHThreads, H - y0);
     {
-        // warp w loads rows w, w + 4, ...; lanes sweep the row (coalesced)
+        // warp w loads rows w, w + 4, ...; lanes sweep the row (coalesced).
+        // Four rows x up to five 32-column chunks are loaded before any is
+        // used, so 20 loads per thread are in flight at once.
+        constexpr int kRowsPerBatch = 4, kChunks = 5;  // IW <= 128 + 2 * 15 = 158 < 5 * 32
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int ry = warp; ry < rows; ry += kHThreads / 32) {
-            const size_t rbase = (size_t)(y0 + ry) * W;
-            for (int cx = lane; cx < IW; cx += 32) {
-                const int x = x0 - r + cx;
-                int v = -1;
-                if (x >= 0 && x < W) v = quantize<DT, M>(depth, rbase + x, sc);
-                tile[ry * pitch + cx] = v;
+        constexpr int kWarps = kHThreads / 32;
+        for (int rb = warp; rb < rows; rb += kWarps * kRowsPerBatch) {
+            float raw[kRowsPerBatch][kChunks];
+#pragma unroll
+            for (int k = 0; k < kRowsPerBatch; ++k) {
+                const int ry = rb + k * kWarps;
+#pragma unroll
+                for (int c = 0; c < kChunks; ++c) {
+                    const int cx = lane + 32 * c, x = x0 - r + cx;
+                    raw[k][c] = (ry < rows && cx < IW && x >= 0 && x < W)
+                                    ? load_raw<DT>(depth, (size_t)(y0 + ry) * W + x) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kRowsPerBatch; ++k) {
+                const int ry = rb + k * kWarps;
+#pragma unroll
+                for (int c = 0; c < kChunks; ++c) {
+                    const int cx = lane + 32 * c;
+                    if (ry < rows && cx < IW) tile[ry * pitch + cx] = quantize_raw<DT, M>(raw[k][c], sc);
+                }
             }
         }
     }
@@ -343,28 +380,41 @@ struct DispState {
             Sw += w0; Swj += __ldg(g1 + o); Swi += (int64_t)i * w0; Sww += __ldg(q0 + o);
         }
     }
-    // slide from output row y to y + 1
-    __device__ __forceinline__ void slide(size_t pb, int Wp, int H, int y, int r) {
+    // The two horizontal-moment rows of the slide from output row y to y + 1
+    // (leaving row y - r, entering row y + r + 1; zero outside the image).
+    // fetch() only issues the loads, so a caller can overlap them with the
+    // solve of row y and apply() them afterwards.
+    int32_t pm_o = 0, pm_i = 0;
+    int64_t pwo = 0, pwjo = 0, pwwo = 0, pwi = 0, pwji = 0, pwwi = 0;
+    __device__ __forceinline__ void fetch(size_t pb, int Wp, int H, int y, int r) {
         const int yo = y - r, yi = y + r + 1;
-        int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
-        int64_t wo = 0, wjo = 0, wwo = 0, wi = 0, wji = 0, wwi = 0;
+        pm_o = pm_i = 0;
+        pwo = pwjo = pwwo = pwi = pwji = pwwi = 0;
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * Wp;
-            unpack_mask(__ldg(hm + o), o0, o1, o2);
-            wo = __ldg(g0 + o); wjo = __ldg(g1 + o); wwo = __ldg(q0 + o);
+            pm_o = __ldg(hm + o); pwo = __ldg(g0 + o); pwjo = __ldg(g1 + o); pwwo = __ldg(q0 + o);
         }
         if (yi < H) {
             const size_t o = pb + (size_t)yi * Wp;
-            unpack_mask(__ldg(hm + o), i0, i1, i2);
-            wi = __ldg(g0 + o); wji = __ldg(g1 + o); wwi = __ldg(q0 + o);
+            pm_i = __ldg(hm + o); pwi = __ldg(g0 + o); pwji = __ldg(g1 + o); pwwi = __ldg(q0 + o);
         }
+    }
+    __device__ __forceinline__ void apply(int r) {
+        int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
+        if (pm_o) unpack_mask(pm_o, o0, o1, o2);
+        if (pm_i) unpack_mask(pm_i, i0, i1, i2);
         // vertical moments: (n, Si, Sii) from the counts, (Sj, Sji) from sum j, Sjj plain
         slide3(n, Si, Sii, (float)o0, (float)i0, r);
         slide2(Sj, Sji, (float)o1, (float)i1, r);
         Sjj += (float)(i2 - o2);
-        slide2(Sw, Swi, wo, wi, r);
-        Swj += wji - wjo;
-        Sww += wwi - wwo;
+        slide2(Sw, Swi, pwo, pwi, r);
+        Swj += pwji - pwjo;
+        Sww += pwwi - pwwo;
+    }
+    // slide from output row y to y + 1
+    __device__ __forceinline__ void slide(size_t pb, int Wp, int H, int y, int r) {
+        fetch(pb, Wp, H, y, r);
+        apply(r);
     }
     __device__ __forceinline__ int count() const { return (int)n; }
 };
@@ -398,22 +448,33 @@ struct StdStateT {
             Szzj += q1v; Szzji += i * q1v; Szzjj += __ldg(b2 + o);
         }
     }
-    __device__ __forceinline__ void slide(size_t pb, int Wp, int H, int y, int r) {
+    // fetch() / apply(): the slide from output row y to y + 1 split into its
+    // loads and its arithmetic (as for DispState).
+    int32_t pm_o = 0, pm_i = 0;
+    int64_t zo = 0, zjo = 0, qo0 = 0, qo1 = 0, qo2 = 0, zi = 0, zji = 0, qi0 = 0, qi1 = 0, qi2 = 0;
+    __device__ __forceinline__ void fetch(size_t pb, int Wp, int H, int y, int r) {
         const int yo = y - r, yi = y + r + 1;
-        int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
-        int64_t zo = 0, zjo = 0, qo0 = 0, qo1 = 0, qo2 = 0, zi = 0, zji = 0, qi0 = 0, qi1 = 0, qi2 = 0;
+        pm_o = pm_i = 0;
+        zo = zjo = qo0 = qo1 = qo2 = zi = zji = qi0 = qi1 = qi2 = 0;
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * Wp;
-            unpack_mask(__ldg(hc + o), o0, o1, o2);
-            zo = __ldg(z0 + o); zjo = __ldg(z1 + o);
+            pm_o = __ldg(hc + o); zo = __ldg(z0 + o); zjo = __ldg(z1 + o);
             qo0 = __ldg(b0 + o); qo1 = __ldg(b1 + o); qo2 = __ldg(b2 + o);
         }
         if (yi < H) {
             const size_t o = pb + (size_t)yi * Wp;
-            unpack_mask(__ldg(hc + o), i0, i1, i2);
-            zi = __ldg(z0 + o); zji = __ldg(z1 + o);
+            pm_i = __ldg(hc + o); zi = __ldg(z0 + o); zji = __ldg(z1 + o);
             qi0 = __ldg(b0 + o); qi1 = __ldg(b1 + o); qi2 = __ldg(b2 + o);
         }
+    }
+    __device__ __forceinline__ void slide(size_t pb, int Wp, int H, int y, int r) {
+        fetch(pb, Wp, H, y, r);
+        apply(r);
+    }
+    __device__ __forceinline__ void apply(int r) {
+        int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
+        if (pm_o) unpack_mask(pm_o, o0, o1, o2);
+        if (pm_i) unpack_mask(pm_i, i0, i1, i2);
         n += i0 - o0;
         if constexpr (kMask) {
             slide3(fn, Si, Sii, (float)o0, (float)i0, r);
@@ -432,9 +493,12 @@ using StdState = StdStateT<false>;
 
 // Vertical moments + solve for one column x of one frame, output rows
 // [y0, y0 + band).  `depth` and the output pointers point at the frame.
+// Not inlined: the single-context and the batch kernels then run the same
+// machine code, so their results agree bit for bit (inlined copies may be
+// contracted into FMAs differently); one call covers a whole band.
 template <int DT, int M>
-__device__ __forceinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, float scale, float q,
-                                             int Wp, const Planes& P, size_t pofs, int x, int y0, int band,
+__device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, float scale, float q,
+                                             int Wp, const Planes P, size_t pofs, int x, int y0, int band,
                                              const float* __restrict__ txt, const float* __restrict__ tyt, float a,
                                              float b, int min_valid, int require_center, float* __restrict__ normals,
                                              float* __restrict__ offsets, float* __restrict__ curvature,
@@ -448,9 +512,17 @@ __device__ __forceinline__ void vpass_column(const void* __restrict__ depth, int
     typename std::conditional<B == SF_METHOD_DISPARITY, DispState,
                               StdStateT<M == SF_METHOD_EXPLICIT_STANDARD>>::type S(P);
     S.init(pb, Wp, H, y0, r);
+    float zc = load_depth<DT>(depth, (size_t)y0 * W + x, scale);
     for (int y = y0; y < y1; ++y) {
         const size_t oi = (size_t)y * W + x;
-        const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
+        const bool cvalid = depth_valid(zc);
+        // issue the loads of the next slide (and the next centre depth) now:
+        // the solve below hides their latency
+        const bool more = y + 1 < y1;
+        if (more) {
+            S.fetch(pb, Wp, H, y, r);
+            zc = load_depth<DT>(depth, oi + W, scale);
+        }
         const int n = S.count();
         bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
         float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
@@ -488,12 +560,12 @@ __device__ __forceinline__ void vpass_column(const void* __restrict__ depth, int
         normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
         offsets[oi] = d; curvature[oi] = cu;
         if (counts) counts[oi] = n;
-        if (y + 1 < y1) S.slide(pb, Wp, H, y, r);
+        if (more) S.apply(r);
     }
 }
 
 template <int DT, int M>
-__global__ void __launch_bounds__(kVThreads) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
+__global__ void __launch_bounds__(kVThreads, vblocks(M)) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
                                                           float scale, const unsigned* __restrict__ vmax_bits,
                                                           int bits, int raw_z, int Wp, size_t plane_elems,
                                                           void* __restrict__ planes_base, Calib cal,
@@ -583,7 +655,7 @@ __global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc*
 }
 
 template <int DT, int M>
-__global__ void __launch_bounds__(kVThreads) vpass_batch_kernel(const FrameDesc* __restrict__ descs,
+__global__ void __launch_bounds__(kVThreads, vblocks(M)) vpass_batch_kernel(const FrameDesc* __restrict__ descs,
                                                                 const int3* __restrict__ items, int n_items,
                                                                 unsigned* __restrict__ counter,
                                                                 const unsigned* __restrict__ vmax_bits,
@@ -725,21 +797,21 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
             } else {
                 // covariance of the points in metric units (see solve_standard)
                 const float nf = (float)S.n, inv_n = 1.f / nf;
-                const int m = __float2int_rn((float)S.Sz * inv_n);
+                const int m = __float2int_rn(Fn<float>::from_i64(S.Sz) * inv_n);
                 const int64_t T0 = S.Sz - (int64_t)S.n * m;
                 const int64_t Tzz = S.Szz - (int64_t)m * (S.Sz + T0);
                 const int64_t Tzj = S.Szzj - (int64_t)m * S.Szj;
                 const int64_t Tzi = S.Szzi - (int64_t)m * S.Szi;
                 const float t0 = (float)(int)T0 * inv_n;
-                const float fSzj = (float)S.Szj, fSzi = (float)S.Szi;
+                const float fSzj = Fn<float>::from_i64(S.Szj), fSzi = Fn<float>::from_i64(S.Szi);
                 const float q2 = q * q;
-                const float Czz = ((float)Tzz - (float)(int)T0 * t0) * q2;
-                const float Cjz = ((float)Tzj - fSzj * t0) * q2;
-                const float Ciz = ((float)Tzi - fSzi * t0) * q2;
+                const float Czz = (Fn<float>::from_i64(Tzz) - (float)(int)T0 * t0) * q2;
+                const float Cjz = (Fn<float>::from_i64(Tzj) - fSzj * t0) * q2;
+                const float Ciz = (Fn<float>::from_i64(Tzi) - fSzi * t0) * q2;
                 const float qj = fSzj * inv_n, qi = fSzi * inv_n;
-                const float Cjj = ((float)S.Szzjj - fSzj * qj) * q2;
-                const float Cji = ((float)S.Szzji - fSzj * qi) * q2;
-                const float Cii = ((float)S.Szzii - fSzi * qi) * q2;
+                const float Cjj = (Fn<float>::from_i64(S.Szzjj) - fSzj * qj) * q2;
+                const float Cji = (Fn<float>::from_i64(S.Szzji) - fSzj * qi) * q2;
+                const float Cii = (Fn<float>::from_i64(S.Szzii) - fSzi * qi) * q2;
                 const float a = cal.a, b = cal.b, ty = cal.ty[y];
                 R11 = a * a * Cjj + 2.f * a * tx * Cjz + tx * tx * Czz;
                 R12 = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
@@ -913,7 +985,7 @@ struct sf_ctx {
     size_t plane_elems;
     int method = SF_METHOD_DISPARITY;
     int depth_type = SF_DEPTH_F32;
-    int hseg = 64;        // horizontal tile width (32, 64 or 128)
+    int hseg = sf::kHSeg; // horizontal tile width (32, 64 or 128)
     int vband = 0;        // vertical band height (0: chosen from the grid size)
     float depth_scale = 1e-3f;
     int min_valid = 3;
@@ -990,12 +1062,14 @@ static sf_status ensure_planes(sf_ctx* c, int frames) {
 }
 
 // Band height of the vertical pass: long bands amortise the 2r-row warm-up,
-// short bands give enough threads to fill the GPU (>= 24 warps per SM).
+// short bands give enough threads to fill the GPU.
 static int vertical_band(const sf_ctx* c, int nfr) {
     if (c->vband > 0) return c->vband;
     const size_t cols = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * sf::kVThreads * nfr;
+    // at least two waves of 32 resident warps per SM: short bands cost a
+    // 2r-row warm-up each, but the tail of the last wave costs more
     int band = 256;
-    while (band > 16 && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 24 * 32) band /= 2;
+    while (band > 16 && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 64 * 32) band /= 2;
     return band;
 }
 
@@ -1530,7 +1604,7 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
         if (!(K.fx != 0.0) || !(K.fy != 0.0) || !std::isfinite(K.fx) || !std::isfinite(K.fy) ||
             !std::isfinite(K.cx) || !std::isfinite(K.cy) || !std::isfinite(K.dx) || !std::isfinite(K.dy))
             return fail(SF_ERR_INVALID_ARG, "frame %d: intrinsics must be finite with nonzero focal lengths", f);
-        const int seg = F.hseg ? F.hseg : 64;
+        const int seg = F.hseg ? F.hseg : sf::kHSeg;
         if (seg != 32 && seg != 64 && seg != 128) return fail(SF_ERR_INVALID_ARG, "frame %d: hseg must be 32, 64 or 128", f);
         const int band = F.vband ? F.vband : 64;
         if (band < 8 || band > 1024) return fail(SF_ERR_INVALID_ARG, "frame %d: vband must be in [8, 1024]", f);
