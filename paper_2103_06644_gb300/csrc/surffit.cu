@@ -170,7 +170,12 @@ __global__ void __launch_bounds__(256) range_kernel(const void* __restrict__ dep
 }
 
 // ---------------------------------------------------------------------------
-// Scratch layout of the horizontal moments (pitch Wp, a multiple of 64).
+// Scratch layout of the horizontal moments.  Each frame's block of a plane
+// holds Wp x H entries (Wp = W rounded up to 64) interleaved in groups of 8
+// columns: entry (x, y) sits at pofs + (x / 8) * 8H + 8y + x % 8.  The
+// horizontal pass (one thread per row) then writes 32 rows of a group as one
+// contiguous run, and the vertical pass (one thread per column) still reads
+// whole 32-byte sectors: consecutive columns of a row are adjacent.
 // ---------------------------------------------------------------------------
 // Disparity planes, each a block of n_frames * plane_elems entries, in order:
 //   hm int32 packed mask moments: count | (sum j + 512) << 6 | sum j^2 << 16
@@ -180,6 +185,12 @@ __global__ void __launch_bounds__(256) range_kernel(const void* __restrict__ dep
 //   b0 int64 sum z^2, b1 int64 sum z^2 j, b2 int64 sum z^2 j^2
 // Frame f of a call occupies elements [pofs_f, pofs_f + Wp_f * H_f) of every
 // plane; `stride` is the number of elements in one plane (all frames).
+constexpr int kGroup = 8;  // columns per interleaved group; also the row stride inside a group
+
+__device__ __forceinline__ size_t plane_index(size_t pofs, int x, int y, int H) {
+    return pofs + (size_t)(x >> 3) * ((size_t)H << 3) + ((size_t)y << 3) + (size_t)(x & 7);
+}
+
 struct Planes {
     int32_t* p32;       // the int32 plane
     int64_t* p64;       // first int64 plane; plane c is p64 + c * stride
@@ -229,7 +240,7 @@ __device__ __forceinline__ void slide2(T& S0, T& S1, T out, T in, int r) {
 // frame's offset in the planes; `tile` is shared memory of
 // kHThreads * ((seg + 2r) | 1) ints.
 template <int DT, int M>
-__device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W, int H, int r, float sc, int Wp,
+__device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W, int H, int r, float sc,
                                            const Planes& P, size_t pofs, int x0, int y0, int seg, int* tile) {
     const int IW = seg + 2 * r;
     const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
@@ -269,7 +280,7 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
         const int y = y0 + threadIdx.x;
         const int* row = tile + threadIdx.x * pitch;
         const int xend = min(x0 + seg, W);
-        const size_t obase = pofs + (size_t)y * Wp;
+
         // channel state: mask moments (count, sum j, sum j^2) and value moments
         int h0 = 0, h1 = 0, h2 = 0;
         int64_t a0 = 0, a1 = 0;          // sum v, sum v j
@@ -304,7 +315,7 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
                     else s0 = s0 - qo + qi;
                 }
             }
-            const size_t o = obase + xb;
+            const size_t o = plane_index(pofs, xb, y, H);  // xb % 4 == 0: 4 entries in one group
             if (xb + 4 <= xend) {
                 *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
                 int64_t* c0 = P.c64(0) + o;
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict
     const size_t dbytes = (DT == SF_DEPTH_U16) ? 2 : 4;
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * W * H;
     const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
-    hpass_tile<DT, M>(dframe, W, H, r, sc, Wp, P, (size_t)f * plane_elems, blockIdx.x * seg,
+    hpass_tile<DT, M>(dframe, W, H, r, sc, P, (size_t)f * plane_elems, blockIdx.x * seg,
                       blockIdx.y * kHThreads, seg, tile);
 }
 
@@ -367,10 +378,10 @@ struct DispState {
     int64_t Sw = 0, Swj = 0, Swi = 0, Sww = 0;
     __device__ DispState(const Planes& P) : hm(P.p32), g0(P.c64(0)), g1(P.c64(1)), q0(P.c64(2)) {}
     // window of output row y0 from rows y0 - r .. y0 + r
-    __device__ __forceinline__ void init(size_t pb, int Wp, int H, int y0, int r) {
+    __device__ __forceinline__ void init(size_t pb, int rs, int H, int y0, int r) {
         for (int yy = y0 - r; yy <= y0 + r; ++yy) {
             if (yy < 0 || yy >= H) continue;
-            const size_t o = pb + (size_t)yy * Wp;
+            const size_t o = pb + (size_t)yy * rs;
             int c0, c1, c2;
             unpack_mask(__ldg(hm + o), c0, c1, c2);
             const int i = yy - y0;
@@ -386,16 +397,16 @@ struct DispState {
     // solve of row y and apply() them afterwards.
     int32_t pm_o = 0, pm_i = 0;
     int64_t pwo = 0, pwjo = 0, pwwo = 0, pwi = 0, pwji = 0, pwwi = 0;
-    __device__ __forceinline__ void fetch(size_t pb, int Wp, int H, int y, int r) {
+    __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) {
         const int yo = y - r, yi = y + r + 1;
         pm_o = pm_i = 0;
         pwo = pwjo = pwwo = pwi = pwji = pwwi = 0;
         if (yo >= 0) {
-            const size_t o = pb + (size_t)yo * Wp;
+            const size_t o = pb + (size_t)yo * rs;
             pm_o = __ldg(hm + o); pwo = __ldg(g0 + o); pwjo = __ldg(g1 + o); pwwo = __ldg(q0 + o);
         }
         if (yi < H) {
-            const size_t o = pb + (size_t)yi * Wp;
+            const size_t o = pb + (size_t)yi * rs;
             pm_i = __ldg(hm + o); pwi = __ldg(g0 + o); pwji = __ldg(g1 + o); pwwi = __ldg(q0 + o);
         }
     }
@@ -412,8 +423,8 @@ struct DispState {
         Sww += pwwi - pwwo;
     }
     // slide from output row y to y + 1
-    __device__ __forceinline__ void slide(size_t pb, int Wp, int H, int y, int r) {
-        fetch(pb, Wp, H, y, r);
+    __device__ __forceinline__ void slide(size_t pb, int rs, int H, int y, int r) {
+        fetch(pb, rs, H, y, r);
         apply(r);
     }
     __device__ __forceinline__ int count() const { return (int)n; }
@@ -430,10 +441,10 @@ struct StdStateT {
     int64_t Sz = 0, Szi = 0, Szj = 0, Szz = 0, Szzi = 0, Szzii = 0, Szzj = 0, Szzji = 0, Szzjj = 0;
     __device__ StdStateT(const Planes& P)
         : hc(P.p32), z0(P.c64(0)), z1(P.c64(1)), b0(P.c64(2)), b1(P.c64(3)), b2(P.c64(4)) {}
-    __device__ __forceinline__ void init(size_t pb, int Wp, int H, int y0, int r) {
+    __device__ __forceinline__ void init(size_t pb, int rs, int H, int y0, int r) {
         for (int yy = y0 - r; yy <= y0 + r; ++yy) {
             if (yy < 0 || yy >= H) continue;
-            const size_t o = pb + (size_t)yy * Wp;
+            const size_t o = pb + (size_t)yy * rs;
             const int64_t i = yy - y0;
             int c0, c1, c2;
             unpack_mask(__ldg(hc + o), c0, c1, c2);
@@ -452,23 +463,23 @@ struct StdStateT {
     // loads and its arithmetic (as for DispState).
     int32_t pm_o = 0, pm_i = 0;
     int64_t zo = 0, zjo = 0, qo0 = 0, qo1 = 0, qo2 = 0, zi = 0, zji = 0, qi0 = 0, qi1 = 0, qi2 = 0;
-    __device__ __forceinline__ void fetch(size_t pb, int Wp, int H, int y, int r) {
+    __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) {
         const int yo = y - r, yi = y + r + 1;
         pm_o = pm_i = 0;
         zo = zjo = qo0 = qo1 = qo2 = zi = zji = qi0 = qi1 = qi2 = 0;
         if (yo >= 0) {
-            const size_t o = pb + (size_t)yo * Wp;
+            const size_t o = pb + (size_t)yo * rs;
             pm_o = __ldg(hc + o); zo = __ldg(z0 + o); zjo = __ldg(z1 + o);
             qo0 = __ldg(b0 + o); qo1 = __ldg(b1 + o); qo2 = __ldg(b2 + o);
         }
         if (yi < H) {
-            const size_t o = pb + (size_t)yi * Wp;
+            const size_t o = pb + (size_t)yi * rs;
             pm_i = __ldg(hc + o); zi = __ldg(z0 + o); zji = __ldg(z1 + o);
             qi0 = __ldg(b0 + o); qi1 = __ldg(b1 + o); qi2 = __ldg(b2 + o);
         }
     }
-    __device__ __forceinline__ void slide(size_t pb, int Wp, int H, int y, int r) {
-        fetch(pb, Wp, H, y, r);
+    __device__ __forceinline__ void slide(size_t pb, int rs, int H, int y, int r) {
+        fetch(pb, rs, H, y, r);
         apply(r);
     }
     __device__ __forceinline__ void apply(int r) {
@@ -498,7 +509,7 @@ using StdState = StdStateT<false>;
 // contracted into FMAs differently); one call covers a whole band.
 template <int DT, int M>
 __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, float scale, float q,
-                                             int Wp, const Planes P, size_t pofs, int x, int y0, int band,
+                                             const Planes P, size_t pofs, int x, int y0, int band,
                                              const float* __restrict__ txt, const float* __restrict__ tyt, float a,
                                              float b, int min_valid, int require_center, float* __restrict__ normals,
                                              float* __restrict__ offsets, float* __restrict__ curvature,
@@ -506,12 +517,12 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
                                              unsigned long long* __restrict__ flags, unsigned* __restrict__ flag_count,
                                              int frame_tag) {
     const int y1 = min(y0 + band, H);
-    const size_t pb = pofs + x;
+    const size_t pb = plane_index(pofs, x, 0, H);
     const float tx = txt[x];
     constexpr int B = base_method(M);
     typename std::conditional<B == SF_METHOD_DISPARITY, DispState,
                               StdStateT<M == SF_METHOD_EXPLICIT_STANDARD>>::type S(P);
-    S.init(pb, Wp, H, y0, r);
+    S.init(pb, kGroup, H, y0, r);
     float zc = load_depth<DT>(depth, (size_t)y0 * W + x, scale);
     for (int y = y0; y < y1; ++y) {
         const size_t oi = (size_t)y * W + x;
@@ -520,7 +531,7 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
         // the solve below hides their latency
         const bool more = y + 1 < y1;
         if (more) {
-            S.fetch(pb, Wp, H, y, r);
+            S.fetch(pb, kGroup, H, y, r);
             zc = load_depth<DT>(depth, oi + W, scale);
         }
         const int n = S.count();
@@ -582,7 +593,7 @@ __global__ void __launch_bounds__(kVThreads, vblocks(M)) vpass_kernel(const void
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * fe;
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);  // metric value of one fixed-point unit
     const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
-    vpass_column<DT, M>(dframe, W, H, r, scale, q, Wp, P, (size_t)f * plane_elems, x, blockIdx.y * band, band, cal.tx,
+    vpass_column<DT, M>(dframe, W, H, r, scale, q, P, (size_t)f * plane_elems, x, blockIdx.y * band, band, cal.tx,
                         cal.ty, cal.a, cal.b, min_valid, require_center, normals + 3 * fe * f, offsets + fe * f,
                         curvature + fe * f, counts ? counts + fe * f : nullptr, tau, flags, flag_count, f);
 }
@@ -650,7 +661,7 @@ __global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc*
         const int3 w = items[it];
         const FrameDesc& d = descs[w.x];
         const float sc = ldexpf(1.f, quant_exponent(vmax_bits[w.x], d.bits));
-        hpass_tile<DT, M>(d.depth, d.W, d.H, d.r, sc, d.Wp, P, d.pofs, w.y, w.z, d.seg, tile);
+        hpass_tile<DT, M>(d.depth, d.W, d.H, d.r, sc, P, d.pofs, w.y, w.z, d.seg, tile);
     }
 }
 
@@ -671,7 +682,7 @@ __global__ void __launch_bounds__(kVThreads, vblocks(M)) vpass_batch_kernel(cons
         const int x = w.y + threadIdx.x;
         if (x < d.W) {
             const float q = quantum<DT, M>(vmax_bits[w.x], d.bits, scale);
-            vpass_column<DT, M>(d.depth, d.W, d.H, d.r, scale, q, d.Wp, P, d.pofs, x, w.z, d.band, d.tx, d.ty, d.a,
+            vpass_column<DT, M>(d.depth, d.W, d.H, d.r, scale, q, P, d.pofs, x, w.z, d.band, d.tx, d.ty, d.a,
                                 d.b, min_valid, require_center, d.normals, d.offsets, d.curvature, nullptr,
                                 INFINITY, nullptr, nullptr, w.x);
         }
@@ -699,7 +710,7 @@ __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, float
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
         const unsigned long long e = flags[idx];
         const int f = (int)(e >> 48), y = (int)((e >> 24) & 0xffffff), x = (int)(e & 0xffffff);
-        const size_t pb = (size_t)f * plane_elems + x;
+        const size_t pb = plane_index((size_t)f * plane_elems, x, 0, H);
         const double q = (double)quantum<DT, M>(vmax_bits[f], bits, scale);
         const double tx = rays[x], ty = rays[W + y];  // FP64 ray tangents
         const double a = rays[W + H], b = rays[W + H + 1];
@@ -707,23 +718,23 @@ __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, float
         bool ok = true;
         if constexpr (M == SF_METHOD_DISPARITY) {
             DispState S(P);
-            S.init(pb, Wp, H, y, r);
+            S.init(pb, kGroup, H, y, r);
             o = solve_disparity<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj, (double)S.Sji,
                                         (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty, a, b);
         } else if constexpr (M == SF_METHOD_STANDARD) {
             StdState S(P);
-            S.init(pb, Wp, H, y, r);
+            S.init(pb, kGroup, H, y, r);
             o = solve_standard<double>((double)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
                                        S.Szzii, q, tx, ty, a, b);
         } else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY) {
             DispState S(P);
-            S.init(pb, Wp, H, y, r);
+            S.init(pb, kGroup, H, y, r);
             o = solve_explicit_disparity<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj,
                                                  (double)S.Sji, (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty,
                                                  a, b, ok);
         } else {
             StdStateT<true> S(P);
-            S.init(pb, Wp, H, y, r);
+            S.init(pb, kGroup, H, y, r);
             o = solve_explicit_standard<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj,
                                                 (double)S.Sji, (double)S.Sii, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj,
                                                 S.Szzi, S.Szzjj, S.Szzji, S.Szzii, q, tx, ty, a, b, ok);
@@ -767,14 +778,14 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
     const int y1 = min(y0 + band, H);
     const size_t nf = gridDim.z;
     const size_t fe = (size_t)W * H;
-    const size_t pb = (size_t)f * plane_elems + x;
+    const size_t pb = plane_index((size_t)f * plane_elems, x, 0, H);
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);
     const float tx = cal.tx[x];
     const size_t fo = (size_t)f * fe;
     const Planes P(planes_base, nf * plane_elems);
     constexpr int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
     typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
-    S.init(pb, Wp, H, y0, r);
+    S.init(pb, kGroup, H, y0, r);
     for (int y = y0; y < y1; ++y) {
         const size_t oi = fo + (size_t)y * W + x;
         const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
@@ -850,7 +861,7 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) adj[((size_t)c * nf + f) * fe + (size_t)y * W + x] = out[c];
-        if (y + 1 < y1) S.slide(pb, Wp, H, y, r);
+        if (y + 1 < y1) S.slide(pb, kGroup, H, y, r);
     }
 }
 
