@@ -50,9 +50,9 @@ __host__ __device__ constexpr int base_method(int M) {
 }
 
 // Register budget of the vertical-pass kernels, as resident blocks per SM:
-// 8 (32 warps, 64 registers) for the disparity form, 6 for the standard form
-// whose state is larger.  Latency hiding of the scratch loads needs the warps.
-__host__ __device__ constexpr int vblocks(int M) { return base_method(M) == SF_METHOD_STANDARD ? 6 : 8; }
+// 6 blocks (24 warps, 80 registers).  The scratch loads need the warps for
+// latency hiding; at 8 blocks (64 registers) the per-column pass spills.
+constexpr int kVBlocks = 6;
 
 // ---------------------------------------------------------------------------
 // Depth decoding.
@@ -576,7 +576,7 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
 }
 
 template <int DT, int M>
-__global__ void __launch_bounds__(kVThreads, vblocks(M)) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
+__global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
                                                           float scale, const unsigned* __restrict__ vmax_bits,
                                                           int bits, int raw_z, int Wp, size_t plane_elems,
                                                           void* __restrict__ planes_base, Calib cal,
@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc*
 }
 
 template <int DT, int M>
-__global__ void __launch_bounds__(kVThreads, vblocks(M)) vpass_batch_kernel(const FrameDesc* __restrict__ descs,
+__global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_batch_kernel(const FrameDesc* __restrict__ descs,
                                                                 const int3* __restrict__ items, int n_items,
                                                                 unsigned* __restrict__ counter,
                                                                 const unsigned* __restrict__ vmax_bits,
@@ -1077,8 +1077,9 @@ static sf_status ensure_planes(sf_ctx* c, int frames) {
 static int vertical_band(const sf_ctx* c, int nfr) {
     if (c->vband > 0) return c->vband;
     const size_t cols = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * sf::kVThreads * nfr;
-    // at least two waves of 32 resident warps per SM: short bands cost a
-    // 2r-row warm-up each, but the tail of the last wave costs more
+    // at least 152 x 2048 threads (about 2.7 waves of 24 resident warps per
+    // SM): short bands cost a 2r-row warm-up each, but with fewer waves the
+    // tail of the last one costs more
     int band = 256;
     while (band > 16 && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 64 * 32) band /= 2;
     return band;
