@@ -146,9 +146,13 @@ sf_status sf_fit_ex(sf_ctx* ctx, int n_frames, const void* depth, float* normals
                     int32_t* counts, void* stream);
 
 /*
- * sf_fit_host -- sf_fit_ex on HOST buffers: copies the depth in, fits and
- * copies the results out through the context's pinned staging buffers, then
- * synchronises `stream`.  Same layouts as sf_fit_ex; counts may be NULL.
+ * sf_fit_host -- sf_fit_ex on HOST buffers (ordinary pageable memory): the
+ * frames go through in up to four chunks on two context-owned streams, the
+ * copy-out of one chunk overlapping the copy-in and fit of the next, with
+ * copies straight between the caller's buffers and two device staging
+ * buffers owned by the context.  Work already queued on `stream` runs first;
+ * the call returns when every result is in the caller's buffers.  Same
+ * layouts as sf_fit_ex; counts may be NULL.
  */
 sf_status sf_fit_host(sf_ctx* ctx, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
                       int32_t* counts, void* stream);

@@ -132,17 +132,31 @@ class SurfaceFitter:
         return _FitFunction.apply(depth, self)
 
     # -- host API (copies inside the library call) --------------------------------
-    def fit_host(self, depth: np.ndarray, counts: bool = False):
-        """Fit host depth [H, W] or [N, H, W] through ``sf_fit_host``; returns numpy arrays."""
+    def fit_host(self, depth: np.ndarray, counts: bool = False, out=None):
+        """Fit host depth [H, W] or [N, H, W] through ``sf_fit_host``; returns numpy arrays.
+
+        ``out`` = (normals, offsets, curvature[, counts]) reuses caller-owned
+        C-contiguous arrays (float32; int32 counts) instead of allocating.
+        """
         want = np.float32 if self.depth_type == "f32" else np.uint16
         d = np.ascontiguousarray(depth, dtype=want)
         batched = d.ndim == 3
         n = d.shape[0] if batched else 1
         shape = (n, self.H, self.W) if batched else (self.H, self.W)
-        normals = np.empty(shape + (3,), np.float32)
-        offsets = np.empty(shape, np.float32)
-        curv = np.empty(shape, np.float32)
-        cnt = np.empty(shape, np.int32) if counts else None
+        if out is None:
+            normals = np.empty(shape + (3,), np.float32)
+            offsets = np.empty(shape, np.float32)
+            curv = np.empty(shape, np.float32)
+            cnt = np.empty(shape, np.int32) if counts else None
+        else:
+            normals, offsets, curv = out[:3]
+            cnt = out[3] if counts else None
+            want_shapes = [(normals, shape + (3,), np.float32), (offsets, shape, np.float32), (curv, shape, np.float32)]
+            if counts:
+                want_shapes.append((cnt, shape, np.int32))
+            for a, shp, dt in want_shapes:
+                if a.shape != shp or a.dtype != dt or not a.flags.c_contiguous:
+                    raise ValueError("out arrays must be C-contiguous %s of shape %s" % (np.dtype(dt).name, shp))
         _native.check(_native.lib().sf_fit_host(self._h, n, d.ctypes.data, normals.ctypes.data, offsets.ctypes.data,
                                                 curv.ctypes.data, cnt.ctypes.data if cnt is not None else None, None))
         return (normals, offsets, curv, cnt) if counts else (normals, offsets, curv)

@@ -1009,11 +1009,13 @@ struct sf_ctx {
     int planes_frames = 0;     // frames the planes buffer holds
     size_t planes_bytes = 0;
     int max_frames_per_pass = 1;
-    // pinned host staging for sf_fit_host
-    void* h_stage = nullptr;
-    size_t h_stage_bytes = 0;
-    void* d_io = nullptr;
+    // sf_fit_host: two device staging buffers and copy streams (one per
+    // chunk parity) and the event that orders the fits on the shared scratch
+    void* d_io[2] = {nullptr, nullptr};
     size_t d_io_bytes = 0;
+    cudaStream_t io_stream[2] = {nullptr, nullptr};
+    cudaEvent_t io_fit_done[2] = {nullptr, nullptr};
+    cudaEvent_t io_entry = nullptr;
     float* adj = nullptr;      // backward: per-window adjoint planes
     size_t adj_bytes = 0;
     // precision fallback
@@ -1358,38 +1360,78 @@ sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals
     if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
     if (n_frames == 0) return SF_OK;
     if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
     const size_t fe = (size_t)c->W * c->H;
-    const size_t dbytes = (c->depth_type == SF_DEPTH_U16 ? 2 : 4) * fe * n_frames;
-    const size_t obytes = 20 * fe * n_frames + (counts ? 4 * fe * n_frames : 0);
-    const size_t need = dbytes + obytes;
-    if (c->d_io_bytes < need) {
-        if (c->d_io) cudaFree(c->d_io);
-        if (c->h_stage) cudaFreeHost(c->h_stage);
-        c->d_io = nullptr; c->h_stage = nullptr; c->d_io_bytes = c->h_stage_bytes = 0;
-        cudaError_t e = cudaMalloc(&c->d_io, need);
-        if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "device staging of %zu bytes failed", need);
-        e = cudaMallocHost(&c->h_stage, need);
-        if (e != cudaSuccess) { cudaFree(c->d_io); c->d_io = nullptr; return fail(SF_ERR_ALLOC, "pinned staging failed"); }
-        c->d_io_bytes = c->h_stage_bytes = need;
+    const size_t dpx = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
+    // Frames go through in chunks on two streams: the copy-out of chunk i-1
+    // overlaps the copy-in and fit of chunk i.  Copies read and write the
+    // caller's (pageable) buffers directly; the fits share the context's
+    // scratch, so each waits for the previous one.
+    const int nchunks = std::min(n_frames, 4);
+    const int per = (n_frames + nchunks - 1) / nchunks;
+    const size_t dbytes = dpx * fe * per;
+    const size_t need = dbytes + (20 + (counts ? 4 : 0)) * fe * per;
+    if (!c->io_stream[0]) {
+        for (int i = 0; i < 2; ++i) {
+            SF_CUDA(cudaStreamCreateWithFlags(&c->io_stream[i], cudaStreamNonBlocking));
+            SF_CUDA(cudaEventCreateWithFlags(&c->io_fit_done[i], cudaEventDisableTiming));
+        }
+        SF_CUDA(cudaEventCreateWithFlags(&c->io_entry, cudaEventDisableTiming));
     }
-    char* hs = static_cast<char*>(c->h_stage);
-    char* ds = static_cast<char*>(c->d_io);
-    memcpy(hs, depth, dbytes);
-    SF_CUDA(cudaMemcpyAsync(ds, hs, dbytes, cudaMemcpyHostToDevice, st));
-    float* dn = reinterpret_cast<float*>(ds + dbytes);
-    float* dof = dn + 3 * fe * n_frames;
-    float* dc = dof + fe * n_frames;
-    int32_t* dk = counts ? reinterpret_cast<int32_t*>(dc + fe * n_frames) : nullptr;
-    sf_status s = sf_fit_ex(c, n_frames, ds, dn, dof, dc, dk, stream);
+    if (c->d_io_bytes < need) {
+        for (int i = 0; i < 2; ++i) {
+            if (c->d_io[i]) cudaFree(c->d_io[i]);
+            c->d_io[i] = nullptr;
+        }
+        c->d_io_bytes = 0;
+        for (int i = 0; i < 2; ++i) {
+            cudaError_t e = cudaMalloc(&c->d_io[i], need);
+            if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "device staging of 2 x %zu bytes failed", need);
+        }
+        c->d_io_bytes = need;
+    }
+    // work already queued on the caller's stream (e.g. a fit using the same
+    // scratch) comes first
+    SF_CUDA(cudaEventRecord(c->io_entry, user));
+    for (int i = 0; i < 2; ++i) SF_CUDA(cudaStreamWaitEvent(c->io_stream[i], c->io_entry, 0));
+    auto copy_out = [&](int ci) -> sf_status {
+        const int f0 = ci * per, nf = std::min(per, n_frames - f0);
+        cudaStream_t st = c->io_stream[ci & 1];
+        const char* ds = static_cast<const char*>(c->d_io[ci & 1]);
+        const float* dn = reinterpret_cast<const float*>(ds + dbytes);
+        const float* dof = dn + 3 * fe * per;
+        const float* dc = dof + fe * per;
+        const int32_t* dk = reinterpret_cast<const int32_t*>(dc + fe * per);
+        SF_CUDA(cudaMemcpyAsync(normals + 3 * fe * f0, dn, 12 * fe * nf, cudaMemcpyDeviceToHost, st));
+        SF_CUDA(cudaMemcpyAsync(offsets + fe * f0, dof, 4 * fe * nf, cudaMemcpyDeviceToHost, st));
+        SF_CUDA(cudaMemcpyAsync(curvature + fe * f0, dc, 4 * fe * nf, cudaMemcpyDeviceToHost, st));
+        if (counts) SF_CUDA(cudaMemcpyAsync(counts + fe * f0, dk, 4 * fe * nf, cudaMemcpyDeviceToHost, st));
+        return SF_OK;
+    };
+    for (int ci = 0; ci < nchunks; ++ci) {
+        const int f0 = ci * per, nf = std::min(per, n_frames - f0);
+        if (nf <= 0) break;
+        cudaStream_t st = c->io_stream[ci & 1];
+        char* ds = static_cast<char*>(c->d_io[ci & 1]);
+        SF_CUDA(cudaMemcpyAsync(ds, static_cast<const char*>(depth) + dpx * fe * f0, dpx * fe * nf,
+                                cudaMemcpyHostToDevice, st));
+        if (ci > 0) SF_CUDA(cudaStreamWaitEvent(st, c->io_fit_done[(ci - 1) & 1], 0));
+        float* dn = reinterpret_cast<float*>(ds + dbytes);
+        float* dof = dn + 3 * fe * per;
+        float* dc = dof + fe * per;
+        int32_t* dk = counts ? reinterpret_cast<int32_t*>(dc + fe * per) : nullptr;
+        // each output plane of the staging buffer has room for [per] frames
+        sf_status s = sf_fit_ex(c, nf, ds, dn, dof, dc, dk, st);
+        if (s != SF_OK) return s;
+        SF_CUDA(cudaEventRecord(c->io_fit_done[ci & 1], st));
+        if (ci > 0) {
+            s = copy_out(ci - 1);
+            if (s != SF_OK) return s;
+        }
+    }
+    sf_status s = copy_out((n_frames - 1) / per);
     if (s != SF_OK) return s;
-    SF_CUDA(cudaMemcpyAsync(hs + dbytes, ds + dbytes, obytes, cudaMemcpyDeviceToHost, st));
-    SF_CUDA(cudaStreamSynchronize(st));
-    const char* ho = hs + dbytes;
-    memcpy(normals, ho, 12 * fe * n_frames);
-    memcpy(offsets, ho + 12 * fe * n_frames, 4 * fe * n_frames);
-    memcpy(curvature, ho + 16 * fe * n_frames, 4 * fe * n_frames);
-    if (counts) memcpy(counts, ho + 20 * fe * n_frames, 4 * fe * n_frames);
+    for (int i = 0; i < 2; ++i) SF_CUDA(cudaStreamSynchronize(c->io_stream[i]));
     return SF_OK;
 }
 
@@ -1490,8 +1532,12 @@ sf_status sf_destroy(sf_ctx* c) {
     if (c->ty) cudaFree(c->ty);
     if (c->vmax) cudaFree(c->vmax);
     if (c->planes) cudaFree(c->planes);
-    if (c->d_io) cudaFree(c->d_io);
-    if (c->h_stage) cudaFreeHost(c->h_stage);
+    for (int i = 0; i < 2; ++i) {
+        if (c->d_io[i]) cudaFree(c->d_io[i]);
+        if (c->io_stream[i]) cudaStreamDestroy(c->io_stream[i]);
+        if (c->io_fit_done[i]) cudaEventDestroy(c->io_fit_done[i]);
+    }
+    if (c->io_entry) cudaEventDestroy(c->io_entry);
     if (c->adj) cudaFree(c->adj);
     if (c->flags) cudaFree(c->flags);
     if (c->flag_count) cudaFree(c->flag_count);

@@ -119,14 +119,32 @@ def test_batched_frames_match_single():
     f.close()
 
 
-def test_host_api_matches_device():
+@pytest.mark.parametrize("nfr", [1, 3, 5, 8])
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_host_api_matches_device(nfr, method):
+    """sf_fit_host (chunked over two streams, pageable buffers) == sf_fit_ex, bit for bit."""
     W, H, k = 128, 96, 7
     intr = scenes.Intrinsics.scaled(W, H)
-    frames = np.stack([scenes.kinect_frame(80 + i, intr, W, H) for i in range(3)])
-    f = SurfaceFitter(intr.as_tuple(), W, H, k)
-    nh, dh, ch, kh = f.fit_host(frames, counts=True)
-    nd, dd, cd, kd = f.fit(torch.from_numpy(frames).cuda(), counts=True)
+    frames = np.stack([scenes.kinect_frame(80 + i, intr, W, H) for i in range(nfr)])
+    f = SurfaceFitter(intr.as_tuple(), W, H, k, method=method)
+    for counts in (True, False):
+        host = f.fit_host(frames, counts=counts)
+        dev = f.fit(torch.from_numpy(frames).cuda(), counts=counts)
+        torch.cuda.synchronize()
+        for h, d in zip(host, dev):
+            assert np.array_equal(np.nan_to_num(h, nan=7.0), np.nan_to_num(d.cpu().numpy(), nan=7.0))
+    # caller-owned result arrays
+    outs = (np.empty(frames.shape + (3,), np.float32), np.empty(frames.shape, np.float32),
+            np.empty(frames.shape, np.float32))
+    r = f.fit_host(frames, out=outs)
+    assert r[0] is outs[0] and np.array_equal(np.nan_to_num(outs[1], nan=7.0), np.nan_to_num(host[1], nan=7.0))
+    with pytest.raises(ValueError):
+        f.fit_host(frames, out=(outs[0][..., :2], outs[1], outs[2]))
+    # a host call between device calls on the same context (shared scratch)
+    d0 = f.fit(torch.from_numpy(frames).cuda())
+    h1 = f.fit_host(frames[::-1].copy())
+    d2 = f.fit(torch.from_numpy(frames).cuda())
     torch.cuda.synchronize()
-    assert np.array_equal(np.nan_to_num(nh, nan=7.0), np.nan_to_num(nd.cpu().numpy(), nan=7.0))
-    assert np.array_equal(kh, kd.cpu().numpy())
+    assert torch.equal(torch.nan_to_num(d0[1], 7.0), torch.nan_to_num(d2[1], 7.0))
+    assert np.array_equal(np.nan_to_num(h1[1][::-1], nan=7.0), np.nan_to_num(d2[1].cpu().numpy(), nan=7.0))
     f.close()
