@@ -121,7 +121,7 @@ def cpu_oracle_sample(time_budget_s: float = 15.0):
                       "FP64 direct window sums, OpenMP over rows" % (n, px), "seconds": dt}
 
 
-def mixed_batch_report(dev, timed):
+def mixed_batch_report(dev, timed, world=1):
     """64 frames, resolutions uniform over {320x240, 640x480, 1280x720, 1920x1080}, windows over
     {5, 7, 11, 21}, intrinsics scaled with the resolution, 0-15 % blob holes: one persistent launch per
     stage replayed from a CUDA graph, tile shapes from the autotuner."""
@@ -142,7 +142,7 @@ def mixed_batch_report(dev, timed):
         b.run()
     ms = timed(20, b.run)
     rep = {"workload": "64 mixed frames (320x240..1920x1080, k in {5,7,11,21}), disparity form, CUDA graph",
-           "pixels": b.pixels, "value": b.pixels / (ms / 1000) / 1e6, "unit": UNIT, "ms_per_step": ms,
+           "pixels": b.pixels, "value": whole_job_rate(world, b.pixels, ms), "unit": UNIT, "ms_per_step": ms,
            "launches_per_step": b.launches, "autotune_seconds": tune_s,
            "tiles": sorted({(f["W"], f["H"], f["window"], f["hseg"], f["vband"]) for f in tuned})}
     b.close()
@@ -195,6 +195,23 @@ def precision_report(group, dev):
         rep["mode%d" % mode] = ent
         f.close()
     return rep
+
+
+def rank_max(x: float, world: int, device) -> float:
+    """Max of a per-rank scalar over all ranks (the job's slowest rank sets the time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, px_per_rank: int, ms: float) -> float:
+    """Mpix/s of the whole job: every rank fits px_per_rank pixels per step in ms (max over ranks)."""
+    return world * px_per_rank / (ms / 1000.0) / 1e6
 
 
 def run_single_case(args):
@@ -313,12 +330,7 @@ def main():
             fn()
         e1.record()
         barrier()
-        ms = e0.elapsed_time(e1) / nsteps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return rank_max(e0.elapsed_time(e1) / nsteps, world, dev)
 
     for _ in range(args.warmup):
         step()
@@ -338,7 +350,7 @@ def main():
         f.profile(False)
     # pixels processed per launch of each stage (every launch covers a whole group)
     px_per_launch = {}
-    value = world * total_px / (ms / 1000.0) / 1e6
+    value = whole_job_rate(world, total_px, ms)
     peak, peak_kind = load_peaks()
     dom = max(prof, key=lambda s: prof[s][0])
     dom_ms, dom_n = prof[dom][0], prof[dom][1]
@@ -368,7 +380,7 @@ def main():
         for _ in range(3):
             step(std)
         ms_std = timed(max(3, args.steps // 2), lambda: step(std))
-        line["standard_fit"] = {"value": world * total_px / (ms_std / 1000.0) / 1e6, "unit": UNIT,
+        line["standard_fit"] = {"value": whole_job_rate(world, total_px, ms_std), "unit": UNIT,
                                 "ms_per_step": ms_std, "speedup_of_disparity_form": ms_std / ms}
         for f in std:
             f.close()
@@ -379,7 +391,7 @@ def main():
             for _ in range(3):
                 step(ef)
             ms_e = timed(max(3, args.steps // 4), lambda: step(ef))
-            expl[method] = {"value": world * total_px / (ms_e / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": ms_e}
+            expl[method] = {"value": whole_job_rate(world, total_px, ms_e), "unit": UNIT, "ms_per_step": ms_e}
             for f in ef:
                 f.close()
         line["explicit_fits"] = expl
@@ -394,7 +406,7 @@ def main():
             for _ in range(5):
                 fv.fit(vga, out=ov)
             t = timed(50, lambda: fv.fit(vga, out=ov))
-            vres[method] = {"us_per_frame": 1000 * t, "value": 307200 / (t / 1000) / 1e6, "unit": UNIT}
+            vres[method] = {"us_per_frame": 1000 * t, "value": whole_job_rate(world, 307200, t), "unit": UNIT}
             fv.close()
         line["vga_k7"] = vres
         # differentiation: 16 x 640x480 f32, k=9, loss = sum |n - n*|^2 + 0.1 kappa over valid pixels;
@@ -418,9 +430,9 @@ def main():
             diff_step()
         t_fb = timed(20, diff_step)
         t_f = timed(20, lambda: fd.fit(dd))
-        line["mixed_batch"] = mixed_batch_report(dev, timed)
+        line["mixed_batch"] = mixed_batch_report(dev, timed, world)
         line["differentiation_k9"] = {"workload": "16x640x480 f32, k=9, loss |n-n*|^2 + 0.1 kappa",
-                                      "value": nd * 307200 / (t_fb / 1000) / 1e6, "unit": UNIT,
+                                      "value": whole_job_rate(world, nd * 307200, t_fb), "unit": UNIT,
                                       "ms_per_step_fwd_bwd": t_fb, "ms_forward": t_f}
         fd.close()
     if not args.no_e2e and not args.profile_only:
@@ -436,12 +448,8 @@ def main():
         for _ in range(ne):
             for f, h, o in zip(fitters, host, hout):
                 f.fit_host(h, out=o)
-        dt = (time.perf_counter() - t0) / ne
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        line["e2e"] = {"value": world * total_px / dt / 1e6, "unit": UNIT,
+        dt = rank_max((time.perf_counter() - t0) / ne, world, dev)
+        line["e2e"] = {"value": whole_job_rate(world, total_px, 1000 * dt), "unit": UNIT,
                        "h2d_bytes_per_step": int(sum(h.nbytes for h in host)),
                        "d2h_bytes_per_step": int(20 * total_px), "ms_per_step": 1000 * dt,
                        "api": "sf_fit_host (pageable host buffers, copies inside the call, result arrays reused)"}
