@@ -13,8 +13,10 @@ on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import shutil
 import signal
 import statistics
@@ -197,6 +199,36 @@ def precision_report(group, dev):
     return rep
 
 
+PROFILE_LAUNCHES = os.path.join(ROOT, "profiles", "batch_1080p_4k_k31_launches.md")
+STAGE_KERNEL = {"range": "range", "hpass": "hpass", "vpass_solve": "vpass", "fp64_resolve": "resolve"}
+
+
+def kernel_source_hash() -> str:
+    """Hash of the device sources (kernels + solve); host-side changes do not alter it."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2103_06644_gb300", "csrc")
+    for f in ("sf_kernels.cuh", "sf_solve.cuh"):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(stage: str):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu launch summary, or None
+    when that capture was taken on other kernel sources (or is missing)."""
+    kern = STAGE_KERNEL.get(stage)
+    try:
+        with open(PROFILE_LAUNCHES) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_record: kernel=%s sources=([0-9a-f]+) bytes_per_launch=(\d+)" % kern, text)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    return int(m.group(2))
+
+
 def rank_max(x: float, world: int, device) -> float:
     """Max of a per-rank scalar over all ranks (the job's slowest rank sets the time)."""
     if world <= 1:
@@ -365,7 +397,7 @@ def main():
         "config": {"workload": WORKLOAD, "frames": 10, "pixels_per_step_per_gpu": total_px, "window": K,
                    "l2": "inputs (167 MB) and outputs (834 MB) larger than L2; no flush"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(dom),
                      "algorithmic_bytes_per_pixel": BYTES_PER_PIXEL,
                      "stage_ms_per_step": {s: v[0] / args.steps for s, v in prof.items()}},
         "path_hbm_frac": BYTES_PER_PIXEL * total_px / (ms / 1000.0) / 1e9 / peak,

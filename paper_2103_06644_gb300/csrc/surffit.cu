@@ -1,23 +1,5 @@
-// surffit.cu -- GB300 (sm_103a) kernels and C ABI for dense RGBD plane fitting.
-//
-// Pipeline for one frame (all device work, no host synchronisation):
-//   1. range     max of the fixed-point variable over the frame's valid pixels
-//                (1/Z for the disparity form, Z for the standard form), giving
-//                a power-of-two quantum so that every value fits in `bits`
-//                bits (26-28 for the disparity form, 23-28 for the standard
-//                form: the most that keeps every exact sum inside int64).
-//   2. hpass     one thread per image row slides a k-wide window along the row
-//                and writes exact integer horizontal window moments
-//                (sums of v, v*j, v*j^2 for the mask, w and w^2 ...) to scratch.
-//   3. vpass     one thread per image column slides the window down the
-//                column over those moments (plus the i-weighted sums), which
-//                yields the exact 2D window moments of every pixel, and solves
-//                the plane fit in registers (sf_solve.cuh).
-//
-// The integral-image idea of Section II.C appears here as running sums: every
-// window sum costs O(1) per pixel regardless of k.  All sums are integers, so
-// they are exact and the result does not depend on the image size or on the
-// order of summation (no floating-point summed-area table is ever formed).
+// surffit.cu -- C ABI of the dense RGBD plane-fitting library (host side:
+// contexts, launches, batches, staging) over the kernels of sf_kernels.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,911 +16,8 @@
 
 #include "surffit.h"
 #include "sf_solve.cuh"
+#include "sf_kernels.cuh"
 
-namespace sf {
-
-constexpr int kMaxR = (SF_MAX_WINDOW - 1) / 2;
-constexpr int kHThreads = 128;   // rows per hpass block
-constexpr int kHSeg = 32;        // default output columns per hpass thread (runtime: 32..128)
-constexpr int kVThreads = 128;   // columns per vpass block
-
-
-// The moments an explicit fit needs are those of its implicit counterpart.
-__host__ __device__ constexpr int base_method(int M) {
-    return M == SF_METHOD_EXPLICIT_DISPARITY ? SF_METHOD_DISPARITY
-                                             : (M == SF_METHOD_EXPLICIT_STANDARD ? SF_METHOD_STANDARD : M);
-}
-
-// Register budget of the vertical-pass kernels, as resident blocks per SM:
-// 6 blocks (24 warps, 80 registers).  The scratch loads need the warps for
-// latency hiding; at 8 blocks (64 registers) the per-column pass spills.
-constexpr int kVBlocks = 6;
-
-// ---------------------------------------------------------------------------
-// Depth decoding.
-// ---------------------------------------------------------------------------
-template <int DT>
-__device__ __forceinline__ float load_depth(const void* base, size_t idx, float scale);
-
-template <>
-__device__ __forceinline__ float load_depth<SF_DEPTH_F32>(const void* base, size_t idx, float) {
-    return __ldg(reinterpret_cast<const float*>(base) + idx);
-}
-template <>
-__device__ __forceinline__ float load_depth<SF_DEPTH_U16>(const void* base, size_t idx, float scale) {
-    const unsigned short raw = __ldg(reinterpret_cast<const unsigned short*>(base) + idx);
-    return raw ? (float)raw * scale : 0.f;
-}
-
-__device__ __forceinline__ bool depth_valid(float z) { return z > 0.f && z < INFINITY; }
-
-// The variable summed by each method, before fixed-point scaling:
-//   disparity 1/Z (float32 depth) or 1/raw (uint16 depth; the metric scale is
-//   folded into the quantum), standard Z (float32) or raw (uint16).
-template <int DT, int M>
-__device__ __forceinline__ float fit_variable_of(float zin) {
-    if (base_method(M) == SF_METHOD_DISPARITY) return rcp_approx(zin);
-    return zin;
-}
-
-// Raw stored value: metres for float32, raw units for uint16 (0 = missing).
-template <int DT>
-__device__ __forceinline__ float load_raw(const void* base, size_t idx) {
-    if (DT == SF_DEPTH_F32) return __ldg(reinterpret_cast<const float*>(base) + idx);
-    return (float)__ldg(reinterpret_cast<const unsigned short*>(base) + idx);
-}
-
-// round(sc / z) to the nearest integer for sc = 2^e, without the 24-bit limit
-// of a float32 reciprocal: y = rcp(z) is refined by the exact FMA residual
-// e = 1 - z*y (exact in float32 for |e| <= 2^-22), so 1/z = y + y*e to about
-// 2^-44; the integer is assembled from the two parts without re-rounding.
-__device__ __forceinline__ int quant_recip(float z, float sc) {
-    const float y = rcp_approx(z);
-    const float e = fmaf(-z, y, 1.f);
-    const float hi = y * sc;           // exact: power-of-two scaling
-    const float lo = (y * e) * sc;
-    const float hr = rintf(hi);
-    return (int)hr + (int)rintf((hi - hr) + lo);
-}
-
-// Exponent e such that v * 2^e <= 2^bits for all v <= vmax.
-__device__ __forceinline__ int quant_exponent(unsigned vmax_bits, int bits) {
-    const float vmax = __uint_as_float(vmax_bits);
-    if (!(vmax > 0.f)) return 0;
-    int E;
-    frexpf(vmax, &E);
-    return bits - E;
-}
-
-// Fixed-point value of a valid pixel (>= 0), or -1 for a missing one, from
-// its raw stored value.
-template <int DT, int M>
-__device__ __forceinline__ int quantize_raw(float zin, float sc) {
-    if (!depth_valid(zin)) return -1;
-    if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_STANDARD) return (int)zin;
-    if (base_method(M) == SF_METHOD_DISPARITY) return quant_recip(zin, sc);
-    return __float2int_rn(zin * sc);
-}
-
-template <int DT, int M>
-__device__ __forceinline__ int quantize(const void* depth, size_t idx, float sc) {
-    return quantize_raw<DT, M>(load_raw<DT>(depth, idx), sc);
-}
-
-// Metric size of one fixed-point unit.
-template <int DT, int M>
-__device__ __forceinline__ float quantum(unsigned vmax_bits, int bits, float scale) {
-    if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_STANDARD) return scale;
-    const float q = ldexpf(1.f, -quant_exponent(vmax_bits, bits));
-    if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_DISPARITY) return q / scale;
-    return q;
-}
-
-// ---------------------------------------------------------------------------
-// 1. range
-// ---------------------------------------------------------------------------
-template <int DT, int M>
-__global__ void __launch_bounds__(256) range_kernel(const void* __restrict__ depth, size_t frame_elems, float scale,
-                                                    unsigned* __restrict__ vmax_bits) {
-    const int f = blockIdx.y;
-    const size_t base = (size_t)f * frame_elems;
-    float vmax = 0.f;
-    // eight independent loads in flight per thread (issue is in order: a
-    // load consumed right away would expose its whole latency)
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < frame_elems; i0 += 8 * stride) {
-        float z[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const size_t i = i0 + u * stride;
-            z[u] = i < frame_elems ? load_raw<DT>(depth, base + i) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (depth_valid(z[u])) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z[u]));
-    }
-    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    __shared__ float red[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = vmax;
-    __syncthreads();
-    if (warp == 0) {
-        vmax = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
-        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        if (lane == 0 && vmax > 0.f) atomicMax(vmax_bits + f, __float_as_uint(vmax));
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Scratch layout of the horizontal moments.  Each frame's block of a plane
-// holds Wp x H entries (Wp = W rounded up to 64) interleaved in groups of 8
-// columns: entry (x, y) sits at pofs + (x / 8) * 8H + 8y + x % 8.  The
-// horizontal pass (one thread per row) then writes 32 rows of a group as one
-// contiguous run, and the vertical pass (one thread per column) still reads
-// whole 32-byte sectors: consecutive columns of a row are adjacent.
-// ---------------------------------------------------------------------------
-// Disparity planes, each a block of n_frames * plane_elems entries, in order:
-//   hm int32 packed mask moments: count | (sum j + 512) << 6 | sum j^2 << 16
-//   g0 int64 sum w,  g1 int64 sum w j,  q0 int64 sum w^2
-// Standard planes:
-//   hc int32 count, z0 int64 sum z, z1 int64 sum z j,
-//   b0 int64 sum z^2, b1 int64 sum z^2 j, b2 int64 sum z^2 j^2
-// Frame f of a call occupies elements [pofs_f, pofs_f + Wp_f * H_f) of every
-// plane; `stride` is the number of elements in one plane (all frames).
-constexpr int kGroup = 8;  // columns per interleaved group; also the row stride inside a group
-
-__device__ __forceinline__ size_t plane_index(size_t pofs, int x, int y, int H) {
-    return pofs + (size_t)(x >> 3) * ((size_t)H << 3) + ((size_t)y << 3) + (size_t)(x & 7);
-}
-
-struct Planes {
-    int32_t* p32;       // the int32 plane
-    int64_t* p64;       // first int64 plane; plane c is p64 + c * stride
-    size_t stride;
-    __host__ __device__ Planes(void* base, size_t stride_)
-        : p32(reinterpret_cast<int32_t*>(base)),
-          p64(reinterpret_cast<int64_t*>(reinterpret_cast<int32_t*>(base) + stride_)),
-          stride(stride_) {}
-    __device__ __forceinline__ int64_t* c64(int c) const { return p64 + (size_t)c * stride; }
-};
-
-__device__ __forceinline__ int32_t pack_mask(int h0, int h1, int h2) {
-    return h0 | ((h1 + 512) << 6) | (h2 << 16);
-}
-__device__ __forceinline__ void unpack_mask(int32_t v, int& h0, int& h1, int& h2) {
-    h0 = v & 63;
-    h1 = ((v >> 6) & 1023) - 512;
-    h2 = (int)((uint32_t)v >> 16);
-}
-
-// Running sums of c, c*j, c*j^2 over j in [-r, r] slide by one column with
-//   S0' = S0 - out + in
-//   S1' = S1 + r*out + (r+1)*in - S0'
-//   S2' = S2 - r(r+2)*out + (r+1)(r-1)*in - 2*S1 + S0'
-// (out leaves at j = -r, in enters at j = r + 1; S1 on the right is the old one).
-template <typename T>
-__device__ __forceinline__ void slide3(T& S0, T& S1, T& S2, T out, T in, int r) {
-    // exact for integers, and for float32 while every value stays below 2^24
-    const T n0 = S0 - out + in;
-    const T n1 = S1 + (T)r * out + (T)(r + 1) * in - n0;
-    const T n2 = S2 - (T)(r * (r + 2)) * out + (T)((r + 1) * (r - 1)) * in - 2 * S1 + n0;
-    S0 = n0; S1 = n1; S2 = n2;
-}
-template <typename T>
-__device__ __forceinline__ void slide2(T& S0, T& S1, T out, T in, int r) {
-    const T n0 = S0 - out + in;
-    S1 = S1 + (T)r * out + (T)(r + 1) * in - n0;
-    S0 = n0;
-}
-
-// ---------------------------------------------------------------------------
-// 2. hpass: block = 128 rows x 64 output columns, tile of fixed-point values
-//    staged in shared memory with coalesced loads, one thread per row.
-// ---------------------------------------------------------------------------
-// Horizontal moments of one tile: rows [y0, y0 + 128) x output columns
-// [x0, x0 + seg) of one frame.  `depth` points at the frame, `pofs` is the
-// frame's offset in the planes; `tile` is shared memory of
-// kHThreads * ((seg + 2r) | 1) ints.
-template <int DT, int M>
-__device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W, int H, int r, float sc,
-                                           const Planes& P, size_t pofs, int x0, int y0, int seg, int* tile) {
-    const int IW = seg + 2 * r;
-    const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
-    const int rows = min(kHThreads, H - y0);
-    {
-        // warp w loads rows w, w + 4, ...; lanes sweep the row (coalesced).
-        // Four rows x up to five 32-column chunks are loaded before any is
-        // used, so 20 loads per thread are in flight at once.
-        constexpr int kRowsPerBatch = 4, kChunks = 5;  // IW <= 128 + 2 * 15 = 158 < 5 * 32
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        constexpr int kWarps = kHThreads / 32;
-        for (int rb = warp; rb < rows; rb += kWarps * kRowsPerBatch) {
-            float raw[kRowsPerBatch][kChunks];
-#pragma unroll
-            for (int k = 0; k < kRowsPerBatch; ++k) {
-                const int ry = rb + k * kWarps;
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c) {
-                    const int cx = lane + 32 * c, x = x0 - r + cx;
-                    raw[k][c] = (ry < rows && cx < IW && x >= 0 && x < W)
-                                    ? load_raw<DT>(depth, (size_t)(y0 + ry) * W + x) : 0.f;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kRowsPerBatch; ++k) {
-                const int ry = rb + k * kWarps;
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c) {
-                    const int cx = lane + 32 * c;
-                    if (ry < rows && cx < IW) tile[ry * pitch + cx] = quantize_raw<DT, M>(raw[k][c], sc);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < rows) {
-        const int y = y0 + threadIdx.x;
-        const int* row = tile + threadIdx.x * pitch;
-        const int xend = min(x0 + seg, W);
-
-        // channel state: mask moments (count, sum j, sum j^2) and value moments
-        int h0 = 0, h1 = 0, h2 = 0;
-        int64_t a0 = 0, a1 = 0;          // sum v, sum v j
-        int64_t s0 = 0, s1 = 0, s2 = 0;  // sum v^2, sum v^2 j, sum v^2 j^2 (s1, s2: standard only)
-        for (int j = -r; j <= r; ++j) {
-            const int v = row[j + r];
-            if (v >= 0) {
-                const int64_t vv = (int64_t)v * v;
-                h0 += 1; h1 += j; h2 += j * j;
-                a0 += v; a1 += (int64_t)v * j;
-                s0 += vv;
-                if (base_method(M) == SF_METHOD_STANDARD) { s1 += vv * j; s2 += vv * (j * j); }
-            }
-        }
-        for (int xb = x0; xb < xend; xb += 4) {
-            int32_t hmv[4];
-            int64_t c0v[4], c1v[4], c2v[4], c3v[4], c4v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int x = xb + u;
-                hmv[u] = pack_mask(h0, h1, h2);
-                c0v[u] = a0; c1v[u] = a1; c2v[u] = s0; c3v[u] = s1; c4v[u] = s2;
-                if (x + 1 < xend) {
-                    const int vo = row[x - x0];              // column x - r leaves
-                    const int vi = row[x - x0 + 2 * r + 1];  // column x + r + 1 enters
-                    const int mo = vo >= 0, mi = vi >= 0;
-                    slide3(h0, h1, h2, mo, mi, r);
-                    const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
-                    slide2(a0, a1, co, ci, r);
-                    const int64_t qo = co * co, qi = ci * ci;
-                    if (base_method(M) == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
-                    else s0 = s0 - qo + qi;
-                }
-            }
-            const size_t o = plane_index(pofs, xb, y, H);  // xb % 4 == 0: 4 entries in one group
-            if (xb + 4 <= xend) {
-                *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
-                int64_t* c0 = P.c64(0) + o;
-                int64_t* c1 = P.c64(1) + o;
-                int64_t* c2 = P.c64(2) + o;
-                *reinterpret_cast<longlong2*>(c0) = make_longlong2(c0v[0], c0v[1]);
-                *reinterpret_cast<longlong2*>(c0 + 2) = make_longlong2(c0v[2], c0v[3]);
-                *reinterpret_cast<longlong2*>(c1) = make_longlong2(c1v[0], c1v[1]);
-                *reinterpret_cast<longlong2*>(c1 + 2) = make_longlong2(c1v[2], c1v[3]);
-                *reinterpret_cast<longlong2*>(c2) = make_longlong2(c2v[0], c2v[1]);
-                *reinterpret_cast<longlong2*>(c2 + 2) = make_longlong2(c2v[2], c2v[3]);
-                if (base_method(M) == SF_METHOD_STANDARD) {
-                    int64_t* c3 = P.c64(3) + o;
-                    int64_t* c4 = P.c64(4) + o;
-                    *reinterpret_cast<longlong2*>(c3) = make_longlong2(c3v[0], c3v[1]);
-                    *reinterpret_cast<longlong2*>(c3 + 2) = make_longlong2(c3v[2], c3v[3]);
-                    *reinterpret_cast<longlong2*>(c4) = make_longlong2(c4v[0], c4v[1]);
-                    *reinterpret_cast<longlong2*>(c4 + 2) = make_longlong2(c4v[2], c4v[3]);
-                }
-            } else {
-                for (int u = 0; u < 4 && xb + u < xend; ++u) {
-                    P.p32[o + u] = hmv[u];
-                    P.c64(0)[o + u] = c0v[u]; P.c64(1)[o + u] = c1v[u]; P.c64(2)[o + u] = c2v[u];
-                    if (base_method(M) == SF_METHOD_STANDARD) { P.c64(3)[o + u] = c3v[u]; P.c64(4)[o + u] = c4v[u]; }
-                }
-            }
-        }
-    }
-}
-
-template <int DT, int M>
-__global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict__ depth, int W, int H, int r,
-                                                          float scale, const unsigned* __restrict__ vmax_bits,
-                                                          int bits, int raw_z, int Wp, size_t plane_elems,
-                                                          void* planes_base, int seg) {
-    extern __shared__ int tile[];
-    const int f = blockIdx.z;
-    const float sc = ldexpf(1.f, quant_exponent(vmax_bits[f], bits));  // 2^e, exact
-    const size_t dbytes = (DT == SF_DEPTH_U16) ? 2 : 4;
-    const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * W * H;
-    const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
-    hpass_tile<DT, M>(dframe, W, H, r, sc, P, (size_t)f * plane_elems, blockIdx.x * seg,
-                      blockIdx.y * kHThreads, seg, tile);
-}
-
-// ---------------------------------------------------------------------------
-// 3. vpass + solve: one thread per column, band of `band` output rows.
-// ---------------------------------------------------------------------------
-struct Calib {
-    const float* tx;  // [W] ray tangent per column
-    const float* ty;  // [H] ray tangent per row
-    float a, b;       // 1/fx, 1/fy
-};
-
-// Vertical running sums of the disparity form's moments for one column.
-struct DispState {
-    const int32_t* hm; const int64_t* g0; const int64_t* g1; const int64_t* q0;
-    // mask moments: exact small integers, kept in float32 (all < 2^24)
-    float n = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;
-    int64_t Sw = 0, Swj = 0, Swi = 0, Sww = 0;
-    __device__ DispState(const Planes& P) : hm(P.p32), g0(P.c64(0)), g1(P.c64(1)), q0(P.c64(2)) {}
-    // window of output row y0 from rows y0 - r .. y0 + r
-    __device__ __forceinline__ void init(size_t pb, int rs, int H, int y0, int r) {
-        for (int yy = y0 - r; yy <= y0 + r; ++yy) {
-            if (yy < 0 || yy >= H) continue;
-            const size_t o = pb + (size_t)yy * rs;
-            int c0, c1, c2;
-            unpack_mask(__ldg(hm + o), c0, c1, c2);
-            const int i = yy - y0;
-            const float f0 = (float)c0, f1 = (float)c1, fi = (float)i;
-            n += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
-            const int64_t w0 = __ldg(g0 + o);
-            Sw += w0; Swj += __ldg(g1 + o); Swi += (int64_t)i * w0; Sww += __ldg(q0 + o);
-        }
-    }
-    // The two horizontal-moment rows of the slide from output row y to y + 1
-    // (leaving row y - r, entering row y + r + 1; zero outside the image).
-    // fetch() only issues the loads, so a caller can overlap them with the
-    // solve of row y and apply() them afterwards.
-    int32_t pm_o = 0, pm_i = 0;
-    int64_t pwo = 0, pwjo = 0, pwwo = 0, pwi = 0, pwji = 0, pwwi = 0;
-    __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) {
-        const int yo = y - r, yi = y + r + 1;
-        pm_o = pm_i = 0;
-        pwo = pwjo = pwwo = pwi = pwji = pwwi = 0;
-        if (yo >= 0) {
-            const size_t o = pb + (size_t)yo * rs;
-            pm_o = __ldg(hm + o); pwo = __ldg(g0 + o); pwjo = __ldg(g1 + o); pwwo = __ldg(q0 + o);
-        }
-        if (yi < H) {
-            const size_t o = pb + (size_t)yi * rs;
-            pm_i = __ldg(hm + o); pwi = __ldg(g0 + o); pwji = __ldg(g1 + o); pwwi = __ldg(q0 + o);
-        }
-    }
-    __device__ __forceinline__ void apply(int r) {
-        int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
-        if (pm_o) unpack_mask(pm_o, o0, o1, o2);
-        if (pm_i) unpack_mask(pm_i, i0, i1, i2);
-        // vertical moments: (n, Si, Sii) from the counts, (Sj, Sji) from sum j, Sjj plain
-        slide3(n, Si, Sii, (float)o0, (float)i0, r);
-        slide2(Sj, Sji, (float)o1, (float)i1, r);
-        Sjj += (float)(i2 - o2);
-        slide2(Sw, Swi, pwo, pwi, r);
-        Swj += pwji - pwjo;
-        Sww += pwwi - pwwo;
-    }
-    // slide from output row y to y + 1
-    __device__ __forceinline__ void slide(size_t pb, int rs, int H, int y, int r) {
-        fetch(pb, rs, H, y, r);
-        apply(r);
-    }
-    __device__ __forceinline__ int count() const { return (int)n; }
-};
-
-// Vertical running sums of the standard form's moments for one column.  With
-// kMask the image moments of the valid pixels (sum j, j^2, i, ji, i^2) are
-// kept too: the explicit standard fit needs them for its rank test.
-template <bool kMask = false>
-struct StdStateT {
-    const int32_t* hc; const int64_t* z0; const int64_t* z1; const int64_t* b0; const int64_t* b1; const int64_t* b2;
-    int n = 0;
-    float fn = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;  // kMask only
-    int64_t Sz = 0, Szi = 0, Szj = 0, Szz = 0, Szzi = 0, Szzii = 0, Szzj = 0, Szzji = 0, Szzjj = 0;
-    __device__ StdStateT(const Planes& P)
-        : hc(P.p32), z0(P.c64(0)), z1(P.c64(1)), b0(P.c64(2)), b1(P.c64(3)), b2(P.c64(4)) {}
-    __device__ __forceinline__ void init(size_t pb, int rs, int H, int y0, int r) {
-        for (int yy = y0 - r; yy <= y0 + r; ++yy) {
-            if (yy < 0 || yy >= H) continue;
-            const size_t o = pb + (size_t)yy * rs;
-            const int64_t i = yy - y0;
-            int c0, c1, c2;
-            unpack_mask(__ldg(hc + o), c0, c1, c2);
-            n += c0;
-            if constexpr (kMask) {
-                const float fi = (float)i, f0 = (float)c0, f1 = (float)c1;
-                fn += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
-            }
-            const int64_t c0z = __ldg(z0 + o), q0v = __ldg(b0 + o), q1v = __ldg(b1 + o);
-            Sz += c0z; Szi += i * c0z; Szj += __ldg(z1 + o);
-            Szz += q0v; Szzi += i * q0v; Szzii += i * i * q0v;
-            Szzj += q1v; Szzji += i * q1v; Szzjj += __ldg(b2 + o);
-        }
-    }
-    // fetch() / apply(): the slide from output row y to y + 1 split into its
-    // loads and its arithmetic (as for DispState).
-    int32_t pm_o = 0, pm_i = 0;
-    int64_t zo = 0, zjo = 0, qo0 = 0, qo1 = 0, qo2 = 0, zi = 0, zji = 0, qi0 = 0, qi1 = 0, qi2 = 0;
-    __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) {
-        const int yo = y - r, yi = y + r + 1;
-        pm_o = pm_i = 0;
-        zo = zjo = qo0 = qo1 = qo2 = zi = zji = qi0 = qi1 = qi2 = 0;
-        if (yo >= 0) {
-            const size_t o = pb + (size_t)yo * rs;
-            pm_o = __ldg(hc + o); zo = __ldg(z0 + o); zjo = __ldg(z1 + o);
-            qo0 = __ldg(b0 + o); qo1 = __ldg(b1 + o); qo2 = __ldg(b2 + o);
-        }
-        if (yi < H) {
-            const size_t o = pb + (size_t)yi * rs;
-            pm_i = __ldg(hc + o); zi = __ldg(z0 + o); zji = __ldg(z1 + o);
-            qi0 = __ldg(b0 + o); qi1 = __ldg(b1 + o); qi2 = __ldg(b2 + o);
-        }
-    }
-    __device__ __forceinline__ void slide(size_t pb, int rs, int H, int y, int r) {
-        fetch(pb, rs, H, y, r);
-        apply(r);
-    }
-    __device__ __forceinline__ void apply(int r) {
-        int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
-        if (pm_o) unpack_mask(pm_o, o0, o1, o2);
-        if (pm_i) unpack_mask(pm_i, i0, i1, i2);
-        n += i0 - o0;
-        if constexpr (kMask) {
-            slide3(fn, Si, Sii, (float)o0, (float)i0, r);
-            slide2(Sj, Sji, (float)o1, (float)i1, r);
-            Sjj += (float)(i2 - o2);
-        }
-        slide2(Sz, Szi, zo, zi, r);
-        Szj += zji - zjo;
-        slide3(Szz, Szzi, Szzii, qo0, qi0, r);
-        slide2(Szzj, Szzji, qo1, qi1, r);
-        Szzjj += qi2 - qo2;
-    }
-    __device__ __forceinline__ int count() const { return n; }
-};
-using StdState = StdStateT<false>;
-
-// Vertical moments + solve for one column x of one frame, output rows
-// [y0, y0 + band).  `depth` and the output pointers point at the frame.
-// Not inlined: the single-context and the batch kernels then run the same
-// machine code, so their results agree bit for bit (inlined copies may be
-// contracted into FMAs differently); one call covers a whole band.
-template <int DT, int M>
-__device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, float scale, float q,
-                                             const Planes P, size_t pofs, int x, int y0, int band,
-                                             const float* __restrict__ txt, const float* __restrict__ tyt, float a,
-                                             float b, int min_valid, int require_center, float* __restrict__ normals,
-                                             float* __restrict__ offsets, float* __restrict__ curvature,
-                                             int32_t* __restrict__ counts, float tau,
-                                             unsigned long long* __restrict__ flags, unsigned* __restrict__ flag_count,
-                                             int frame_tag) {
-    const int y1 = min(y0 + band, H);
-    const size_t pb = plane_index(pofs, x, 0, H);
-    const float tx = txt[x];
-    constexpr int B = base_method(M);
-    typename std::conditional<B == SF_METHOD_DISPARITY, DispState,
-                              StdStateT<M == SF_METHOD_EXPLICIT_STANDARD>>::type S(P);
-    S.init(pb, kGroup, H, y0, r);
-    float zc = load_depth<DT>(depth, (size_t)y0 * W + x, scale);
-    for (int y = y0; y < y1; ++y) {
-        const size_t oi = (size_t)y * W + x;
-        const bool cvalid = depth_valid(zc);
-        // issue the loads of the next slide (and the next centre depth) now:
-        // the solve below hides their latency
-        const bool more = y + 1 < y1;
-        if (more) {
-            S.fetch(pb, kGroup, H, y, r);
-            zc = load_depth<DT>(depth, oi + W, scale);
-        }
-        const int n = S.count();
-        bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
-        float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
-        FitOut fo_;
-        if (ok) {
-            if constexpr (M == SF_METHOD_DISPARITY)
-                fo_ = solve_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, tyt[y],
-                                      a, b);
-            else if constexpr (M == SF_METHOD_STANDARD)
-                fo_ = solve_standard((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
-                                     S.Szzii, q, tx, tyt[y], a, b);
-            else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY)
-                fo_ = solve_explicit_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q,
-                                               tx, tyt[y], a, b, ok);
-            else
-                fo_ = solve_explicit_standard((float)S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sz, S.Szj, S.Szi,
-                                              S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji, S.Szzii, q, tx, tyt[y], a, b,
-                                              ok);
-        }
-        if (ok) {
-            nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
-            if (flags && !(fo_.gap >= tau)) {
-                // near-degenerate window: queue it for the FP64 re-solve
-                const unsigned mask = __activemask();
-                const int leader = __ffs(mask) - 1;
-                const int lane = threadIdx.x & 31;
-                unsigned base = 0;
-                if (lane == leader) base = atomicAdd(flag_count, (unsigned)__popc(mask));
-                base = __shfl_sync(mask, base, leader);
-                const unsigned slot = base + __popc(mask & ((1u << lane) - 1u));
-                flags[slot] = ((unsigned long long)frame_tag << 48) | ((unsigned long long)y << 24) |
-                              (unsigned long long)x;
-            }
-        }
-        normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
-        offsets[oi] = d; curvature[oi] = cu;
-        if (counts) counts[oi] = n;
-        if (more) S.apply(r);
-    }
-}
-
-template <int DT, int M>
-__global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
-                                                          float scale, const unsigned* __restrict__ vmax_bits,
-                                                          int bits, int raw_z, int Wp, size_t plane_elems,
-                                                          void* __restrict__ planes_base, Calib cal,
-                                                          int min_valid, int require_center, int band,
-                                                          float* __restrict__ normals, float* __restrict__ offsets,
-                                                          float* __restrict__ curvature, int32_t* __restrict__ counts,
-                                                          float tau, unsigned long long* __restrict__ flags,
-                                                          unsigned* __restrict__ flag_count) {
-    const int f = blockIdx.z;
-    const int x = blockIdx.x * kVThreads + threadIdx.x;
-    if (x >= W) return;
-    const size_t fe = (size_t)W * H;
-    const size_t dbytes = (DT == SF_DEPTH_U16) ? 2 : 4;
-    const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * fe;
-    const float q = quantum<DT, M>(vmax_bits[f], bits, scale);  // metric value of one fixed-point unit
-    const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
-    vpass_column<DT, M>(dframe, W, H, r, scale, q, P, (size_t)f * plane_elems, x, blockIdx.y * band, band, cal.tx,
-                        cal.ty, cal.a, cal.b, min_valid, require_center, normals + 3 * fe * f, offsets + fe * f,
-                        curvature + fe * f, counts ? counts + fe * f : nullptr, tau, flags, flag_count, f);
-}
-
-// ---------------------------------------------------------------------------
-// Mixed-resolution batches: persistent kernels over a table of work items.
-// Each frame has its own size, window, intrinsics and tile shape; every CTA
-// claims the next item with one atomicAdd and never waits on another CTA.
-// ---------------------------------------------------------------------------
-struct FrameDesc {
-    const void* depth;
-    float* normals;
-    float* offsets;
-    float* curvature;
-    const float* tx;   // [W] ray tangents
-    const float* ty;   // [H]
-    float a, b;        // 1/fx, 1/fy
-    int W, H, r, bits, Wp, seg, band;
-    size_t pofs;       // offset of the frame in every moment plane
-};
-
-template <int DT, int M>
-__global__ void __launch_bounds__(256) range_batch_kernel(const FrameDesc* __restrict__ descs,
-                                                          unsigned* __restrict__ vmax_bits) {
-    const int f = blockIdx.y;
-    const FrameDesc& d = descs[f];
-    const size_t fe = (size_t)d.W * d.H;
-    float vmax = 0.f;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < fe; i += (size_t)gridDim.x * blockDim.x) {
-        const float z = load_raw<DT>(d.depth, i);
-        if (depth_valid(z)) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z));
-    }
-    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    __shared__ float red[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = vmax;
-    __syncthreads();
-    if (warp == 0) {
-        vmax = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
-        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        if (lane == 0 && vmax > 0.f) atomicMax(vmax_bits + f, __float_as_uint(vmax));
-    }
-}
-
-// Claim the next work item for the whole CTA (one atomicAdd).
-__device__ __forceinline__ int claim_item(unsigned* counter, int* slot) {
-    __syncthreads();
-    if (threadIdx.x == 0) *slot = (int)atomicAdd(counter, 1u);
-    __syncthreads();
-    return *slot;
-}
-
-template <int DT, int M>
-__global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc* __restrict__ descs,
-                                                                const int3* __restrict__ items, int n_items,
-                                                                unsigned* __restrict__ counter,
-                                                                const unsigned* __restrict__ vmax_bits,
-                                                                void* planes_base, size_t stride, float scale) {
-    extern __shared__ int tile[];
-    __shared__ int slot;
-    const Planes P(planes_base, stride);
-    for (;;) {
-        const int it = claim_item(counter, &slot);
-        if (it >= n_items) break;
-        const int3 w = items[it];
-        const FrameDesc& d = descs[w.x];
-        const float sc = ldexpf(1.f, quant_exponent(vmax_bits[w.x], d.bits));
-        hpass_tile<DT, M>(d.depth, d.W, d.H, d.r, sc, P, d.pofs, w.y, w.z, d.seg, tile);
-    }
-}
-
-template <int DT, int M>
-__global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_batch_kernel(const FrameDesc* __restrict__ descs,
-                                                                const int3* __restrict__ items, int n_items,
-                                                                unsigned* __restrict__ counter,
-                                                                const unsigned* __restrict__ vmax_bits,
-                                                                void* planes_base, size_t stride, float scale,
-                                                                int min_valid, int require_center) {
-    __shared__ int slot;
-    const Planes P(planes_base, stride);
-    for (;;) {
-        const int it = claim_item(counter, &slot);
-        if (it >= n_items) break;
-        const int3 w = items[it];
-        const FrameDesc& d = descs[w.x];
-        const int x = w.y + threadIdx.x;
-        if (x < d.W) {
-            const float q = quantum<DT, M>(vmax_bits[w.x], d.bits, scale);
-            vpass_column<DT, M>(d.depth, d.W, d.H, d.r, scale, q, P, d.pofs, x, w.z, d.band, d.tx, d.ty, d.a,
-                                d.b, min_valid, require_center, d.normals, d.offsets, d.curvature, nullptr,
-                                INFINITY, nullptr, nullptr, w.x);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// FP64 re-solve of the queued windows: the exact window moments are
-// recomputed from the scratch planes (the 2r + 1 rows of the pixel's column),
-// then the whole solve runs in double precision and overwrites the outputs.
-// The moments are exact integers, so this removes every float32 rounding of
-// the solve; only the fixed-point quantisation of the depth remains.
-// ---------------------------------------------------------------------------
-template <int DT, int M>
-__global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, float scale,
-                                                      const unsigned* __restrict__ vmax_bits, int bits, int Wp,
-                                                      size_t plane_elems, int nframes, void* __restrict__ planes_base,
-                                                      Calib cal, const double* __restrict__ rays,
-                                                      const unsigned long long* __restrict__ flags,
-                                                      const unsigned* __restrict__ flag_count,
-                                                      float* __restrict__ normals, float* __restrict__ offsets,
-                                                      float* __restrict__ curvature) {
-    const unsigned count = *flag_count;
-    const Planes P(planes_base, (size_t)nframes * plane_elems);
-    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
-        const unsigned long long e = flags[idx];
-        const int f = (int)(e >> 48), y = (int)((e >> 24) & 0xffffff), x = (int)(e & 0xffffff);
-        const size_t pb = plane_index((size_t)f * plane_elems, x, 0, H);
-        const double q = (double)quantum<DT, M>(vmax_bits[f], bits, scale);
-        const double tx = rays[x], ty = rays[W + y];  // FP64 ray tangents
-        const double a = rays[W + H], b = rays[W + H + 1];
-        FitOutT<double> o;
-        bool ok = true;
-        if constexpr (M == SF_METHOD_DISPARITY) {
-            DispState S(P);
-            S.init(pb, kGroup, H, y, r);
-            o = solve_disparity<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj, (double)S.Sji,
-                                        (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty, a, b);
-        } else if constexpr (M == SF_METHOD_STANDARD) {
-            StdState S(P);
-            S.init(pb, kGroup, H, y, r);
-            o = solve_standard<double>((double)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
-                                       S.Szzii, q, tx, ty, a, b);
-        } else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY) {
-            DispState S(P);
-            S.init(pb, kGroup, H, y, r);
-            o = solve_explicit_disparity<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj,
-                                                 (double)S.Sji, (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty,
-                                                 a, b, ok);
-        } else {
-            StdStateT<true> S(P);
-            S.init(pb, kGroup, H, y, r);
-            o = solve_explicit_standard<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj,
-                                                (double)S.Sji, (double)S.Sii, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj,
-                                                S.Szzi, S.Szzjj, S.Szzji, S.Szzii, q, tx, ty, a, b, ok);
-        }
-        if (!ok) o.nx = o.ny = o.nz = o.d = o.curv = NAN;
-        const size_t oi = (size_t)f * W * H + (size_t)y * W + x;
-        normals[3 * oi] = (float)o.nx; normals[3 * oi + 1] = (float)o.ny; normals[3 * oi + 2] = (float)o.nz;
-        offsets[oi] = (float)o.d;
-        curvature[oi] = (float)o.curv;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Backward, step 1: per-window adjoint.  For every valid window p, from the
-// same exact moments as the forward pass and the upstream gradients
-// (gn, gd, gk) of (normal, offset, curvature), write the quantities that
-// carry the window's contribution to each of its pixels q:
-//   disparity: dL_p/dw_q = w_q [(P_q - mu_p) . gbar_p - c_p]   (7 floats: gbar, mu, c)
-//   standard:  dL_p/dP_q = 2 Rbar_p (P_q - mu_p) - e_p         (12 floats: 2Rbar, mu, e)
-// with mu_p the window's (weighted) centroid.  The disparity form follows
-// from R = A - g g^T / s, g = sum w m, s = sum w^2: gbar = -2 Rbar mu - gd n/s,
-// sbar = g^T Rbar g / s^2 + gd n.g / s^2, and mu.gbar + 2 sbar = -gd d / s,
-// so the contribution gbar.m_q + 2 w_q sbar is centred on the window and
-// never subtracts two large numbers.  Invalid windows write zeros.
-// Adjoint planes: channel c of frame f at adj + (c * nf + f) * fe.
-// ---------------------------------------------------------------------------
-template <int DT, int M>
-__global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restrict__ depth, int W, int H, int r,
-                                                             float scale, const unsigned* __restrict__ vmax_bits,
-                                                             int bits, int Wp, size_t plane_elems,
-                                                             void* __restrict__ planes_base, Calib cal, int min_valid,
-                                                             int require_center, int band,
-                                                             const float* __restrict__ g_normals,
-                                                             const float* __restrict__ g_offsets,
-                                                             const float* __restrict__ g_curv,
-                                                             float* __restrict__ adj) {
-    const int f = blockIdx.z;
-    const int x = blockIdx.x * kVThreads + threadIdx.x;
-    if (x >= W) return;
-    const int y0 = blockIdx.y * band;
-    const int y1 = min(y0 + band, H);
-    const size_t nf = gridDim.z;
-    const size_t fe = (size_t)W * H;
-    const size_t pb = plane_index((size_t)f * plane_elems, x, 0, H);
-    const float q = quantum<DT, M>(vmax_bits[f], bits, scale);
-    const float tx = cal.tx[x];
-    const size_t fo = (size_t)f * fe;
-    const Planes P(planes_base, nf * plane_elems);
-    constexpr int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
-    typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
-    S.init(pb, kGroup, H, y0, r);
-    for (int y = y0; y < y1; ++y) {
-        const size_t oi = fo + (size_t)y * W + x;
-        const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
-        const int n = S.count();
-        const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
-        float out[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) out[c] = 0.f;
-        if (ok) {
-            const float gnx = g_normals[3 * oi], gny = g_normals[3 * oi + 1], gnz = g_normals[3 * oi + 2];
-            const float gd = g_offsets[oi], gk = g_curv[oi];
-            float R11, R12, R13, R22, R23, R33, mux, muy, muz, s_or_n;
-            if constexpr (M == SF_METHOD_DISPARITY) {
-                const DispWindow w = build_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi,
-                                                     S.Sww, tx, cal.ty[y], cal.a, cal.b);
-                R11 = w.R11; R12 = w.R12; R13 = w.R13; R22 = w.R22; R23 = w.R23; R33 = w.R33;
-                const float iwm = 1.f / (w.what * q);  // 1 / what_metric
-                mux = w.mx * iwm; muy = w.my * iwm; muz = iwm;
-                s_or_n = S.n * (w.wbar * q) * (w.what * q);  // sum w^2 = n wbar what
-            } else {
-                // covariance of the points in metric units (see solve_standard)
-                const float nf = (float)S.n, inv_n = 1.f / nf;
-                const int m = __float2int_rn(Fn<float>::from_i64(S.Sz) * inv_n);
-                const int64_t T0 = S.Sz - (int64_t)S.n * m;
-                const int64_t Tzz = S.Szz - (int64_t)m * (S.Sz + T0);
-                const int64_t Tzj = S.Szzj - (int64_t)m * S.Szj;
-                const int64_t Tzi = S.Szzi - (int64_t)m * S.Szi;
-                const float t0 = (float)(int)T0 * inv_n;
-                const float fSzj = Fn<float>::from_i64(S.Szj), fSzi = Fn<float>::from_i64(S.Szi);
-                const float q2 = q * q;
-                const float Czz = (Fn<float>::from_i64(Tzz) - (float)(int)T0 * t0) * q2;
-                const float Cjz = (Fn<float>::from_i64(Tzj) - fSzj * t0) * q2;
-                const float Ciz = (Fn<float>::from_i64(Tzi) - fSzi * t0) * q2;
-                const float qj = fSzj * inv_n, qi = fSzi * inv_n;
-                const float Cjj = (Fn<float>::from_i64(S.Szzjj) - fSzj * qj) * q2;
-                const float Cji = (Fn<float>::from_i64(S.Szzji) - fSzj * qi) * q2;
-                const float Cii = (Fn<float>::from_i64(S.Szzii) - fSzi * qi) * q2;
-                const float a = cal.a, b = cal.b, ty = cal.ty[y];
-                R11 = a * a * Cjj + 2.f * a * tx * Cjz + tx * tx * Czz;
-                R12 = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
-                R13 = a * Cjz + tx * Czz;
-                R22 = b * b * Cii + 2.f * b * ty * Ciz + ty * ty * Czz;
-                R23 = b * Ciz + ty * Czz;
-                R33 = Czz;
-                const float zb = ((float)m + t0) * q;
-                mux = a * qj * q + tx * zb; muy = b * qi * q + ty * zb; muz = zb;
-                s_or_n = nf;
-            }
-            float v0, v1, v2, l0n, gap;
-            smallest_eigpair(R11, R12, R13, R22, R23, R33, v0, v1, v2, l0n, gap);
-            const float tr = R11 + R22 + R33;
-            const float d0 = -(v0 * mux + v1 * muy + v2 * muz);
-            float nx = v0, ny = v1, nz = v2, d = d0;
-            orient(nx, ny, nz, d);
-            const float sg = (nx * v0 + ny * v1 + nz * v2) >= 0.f ? 1.f : -1.f;
-            // d = -n . mu: gradient wrt the oriented normal, then wrt v0
-            const float bx = sg * (gnx - gd * mux), by = sg * (gny - gd * muy), bz = sg * (gnz - gd * muz);
-            const Sym3 Rb = eig_adjoint(R11, R12, R13, R22, R23, R33, v0, v1, v2, l0n * tr, tr, bx, by, bz, gk);
-            if constexpr (M == SF_METHOD_DISPARITY) {
-                const float is = 1.f / s_or_n;
-                out[0] = -2.f * (Rb.a11 * mux + Rb.a12 * muy + Rb.a13 * muz) - gd * nx * is;
-                out[1] = -2.f * (Rb.a12 * mux + Rb.a22 * muy + Rb.a23 * muz) - gd * ny * is;
-                out[2] = -2.f * (Rb.a13 * mux + Rb.a23 * muy + Rb.a33 * muz) - gd * nz * is;
-                out[3] = mux; out[4] = muy; out[5] = muz;
-                out[6] = gd * d * is;
-            } else {
-                const float in = 1.f / s_or_n;
-                out[0] = 2.f * Rb.a11; out[1] = 2.f * Rb.a12; out[2] = 2.f * Rb.a13;
-                out[3] = 2.f * Rb.a22; out[4] = 2.f * Rb.a23; out[5] = 2.f * Rb.a33;
-                out[6] = mux; out[7] = muy; out[8] = muz;
-                out[9] = gd * nx * in; out[10] = gd * ny * in; out[11] = gd * nz * in;
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) adj[((size_t)c * nf + f) * fe + (size_t)y * W + x] = out[c];
-        if (y + 1 < y1) S.slide(pb, kGroup, H, y, r);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Backward, step 2: every pixel q gathers the contributions of the windows
-// p that contain it (p in the k x k window around q, by symmetry) from a
-// shared-memory tile of the adjoint planes, and applies the chain rule
-//   disparity: dL/dZ_q = -w_q^3 sum_p [(P_q - mu_p) . gbar_p - c_p]
-//   standard:  dL/dZ_q = m_q . sum_p [2 Rbar_p (P_q - mu_p) - e_p]
-// Missing pixels get 0.  Block: 32 x 8 threads, 32 x 32 output tile.
-// ---------------------------------------------------------------------------
-constexpr int kGTile = 32;
-
-template <int DT, int M>
-__global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ depth, int W, int H, int r, float scale,
-                                                     Calib cal, const float* __restrict__ adj,
-                                                     float* __restrict__ g_depth) {
-    extern __shared__ float sadj[];
-    constexpr int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
-    const int f = blockIdx.z;
-    const size_t nf = gridDim.z;
-    const size_t fe = (size_t)W * H;
-    const int x0 = blockIdx.x * kGTile, y0 = blockIdx.y * kGTile;
-    const int T = kGTile + 2 * r;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int c = 0; c < NC; ++c) {
-        const float* src = adj + ((size_t)c * nf + f) * fe;
-        for (int idx = tid; idx < T * T; idx += 256) {
-            const int ty_ = idx / T, tx_ = idx - ty_ * T;
-            const int xx = x0 - r + tx_, yy = y0 - r + ty_;
-            float v = 0.f;
-            if (xx >= 0 && xx < W && yy >= 0 && yy < H) v = src[(size_t)yy * W + xx];
-            sadj[(c * T + ty_) * T + tx_] = v;
-        }
-    }
-    __syncthreads();
-    const int x = x0 + threadIdx.x;
-    if (x >= W) return;
-    const float tx = cal.tx[x];
-    for (int yr = threadIdx.y; yr < kGTile; yr += 8) {
-        const int y = y0 + yr;
-        if (y >= H) break;
-        const size_t oi = (size_t)f * fe + (size_t)y * W + x;
-        const float z = load_depth<DT>(depth, oi, scale);
-        float g = 0.f;
-        if (depth_valid(z)) {
-            const float px = z * tx, py = z * cal.ty[y], pz = z;
-            float acc = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-            for (int dy = 0; dy <= 2 * r; ++dy) {
-                const int row = yr + dy;
-                for (int dx = 0; dx <= 2 * r; ++dx) {
-                    const int col = threadIdx.x + dx;
-                    const float* sp = sadj + row * T + col;
-                    const size_t cs = (size_t)T * T;
-                    if constexpr (M == SF_METHOD_DISPARITY) {
-                        acc += (px - sp[3 * cs]) * sp[0] + (py - sp[4 * cs]) * sp[cs] + (pz - sp[5 * cs]) * sp[2 * cs] -
-                               sp[6 * cs];
-                    } else {
-                        const float ux = px - sp[6 * cs], uy = py - sp[7 * cs], uz = pz - sp[8 * cs];
-                        ax += sp[0] * ux + sp[cs] * uy + sp[2 * cs] * uz - sp[9 * cs];
-                        ay += sp[cs] * ux + sp[3 * cs] * uy + sp[4 * cs] * uz - sp[10 * cs];
-                        az += sp[2 * cs] * ux + sp[4 * cs] * uy + sp[5 * cs] * uz - sp[11 * cs];
-                    }
-                }
-            }
-            if constexpr (M == SF_METHOD_DISPARITY) {
-                const float w = 1.f / z;
-                g = -w * w * w * acc;
-            } else {
-                g = tx * ax + cal.ty[y] * ay + az;
-            }
-        }
-        g_depth[oi] = g;
-    }
-}
-
-}  // namespace sf
 
 // ===========================================================================
 // C ABI
