@@ -58,6 +58,9 @@ def _load():
         lib.sfo_eig_sym.restype = ctypes.c_int
         lib.sfo_num_threads.argtypes = []
         lib.sfo_num_threads.restype = ctypes.c_int
+        lib.sfo_fit_rect.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ip]
+        lib.sfo_fit_rect.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -142,3 +145,75 @@ def eig_sym(m: np.ndarray):
 
 def num_threads() -> int:
     return int(_load().sfo_num_threads())
+
+
+def fit_rect(Z: np.ndarray, intr: Sequence[float], x0: int, y0: int, w: int, h: int, method: str = "disparity",
+             min_valid: int = 3) -> Dict[str, object]:
+    """The fit of the pixels [x0, x0 + w) x [y0, y0 + h) of an FP64 depth image (metres).
+
+    Returns ``ok``, ``count``, ``normal``, ``offset``, ``curvature`` (mean squared residual for the
+    explicit fits), ``lam`` (eigenvalues of R) and ``residual`` (the minimised residual sum: lambda0
+    of R for the implicit fits, the residual sum of squares for the explicit ones).
+    """
+    lib = _load()
+    H, W = Z.shape
+    it = np.ascontiguousarray(np.asarray(intr, dtype=np.float64))
+    out = np.empty(9)
+    cnt = np.zeros(1, np.int32)
+    rc = lib.sfo_fit_rect(_dp(Z), W, H, _dp(it), int(x0), int(y0), int(w), int(h), METHODS[method],
+                          int(min_valid), _dp(out), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc < 0:
+        raise ValueError("oracle rejected the rectangle")
+    return {"ok": rc == 1, "count": int(cnt[0]), "normal": out[0:3].copy(), "offset": float(out[3]),
+            "curvature": float(out[4]), "lam": out[5:8].copy(), "residual": float(out[8])}
+
+
+# Node status of the planar segmentation (Section III): a plane that fits, a
+# tile split into four, a tile whose fit error stays above the threshold at
+# the deepest level, and a tile with too few valid pixels.
+QUAD_FIT, QUAD_SPLIT, QUAD_HIGH_ERROR, QUAD_INVALID = 0, 1, 2, 3
+
+
+def quadtree(depth: np.ndarray, intr: Sequence[float], method: str = "disparity", *, tile: int = 64,
+             max_level: int = 3, tau: float = 1e-3, min_valid_permille: int = 500, min_valid: int = 3,
+             depth_scale: float = 1e-3) -> list:
+    """Planar segmentation by tile subdivision (Section III, planar segmentation application).
+
+    The image is cut into tile x tile squares from the top-left corner (clipped at the right and
+    bottom borders).  A node with fewer than max(min_valid, ceil(permille * area / 1000)) valid
+    pixels is INVALID.  Otherwise its plane is fitted over all its valid pixels, and its error is the
+    root mean square of the residual the method minimises, e = sqrt(residual / n) (for the implicit
+    fits lambda0 of R: the algebraic distance over depth for the disparity form, the point-to-plane
+    distance in metres for the standard form).  If e > tau the node splits into four children of
+    half its width and height (left/top halves floor(w/2), floor(h/2)) while level < max_level and
+    w, h >= 2; otherwise it is a FIT leaf (e <= tau) or a HIGH_ERROR leaf.
+
+    Returns every evaluated node in breadth-first order as dicts with x0, y0, w, h, level, status,
+    count, normal, offset, curvature, rms.
+    """
+    Z = np.ascontiguousarray(depth_to_f64(depth, depth_scale))
+    H, W = Z.shape
+    level_nodes = [(x0, y0, min(tile, W - x0), min(tile, H - y0)) for y0 in range(0, H, tile)
+                   for x0 in range(0, W, tile)]
+    out = []
+    for level in range(max_level + 1):
+        nxt = []
+        for (x0, y0, w, h) in level_nodes:
+            need = max(min_valid, (min_valid_permille * w * h + 999) // 1000)
+            r = fit_rect(Z, intr, x0, y0, w, h, method, min_valid=need)
+            node = {"x0": x0, "y0": y0, "w": w, "h": h, "level": level, "count": r["count"],
+                    "normal": r["normal"], "offset": r["offset"], "curvature": r["curvature"], "rms": np.nan}
+            if not r["ok"]:
+                node["status"] = QUAD_INVALID
+            else:
+                node["rms"] = float(np.sqrt(max(r["residual"], 0.0) / r["count"]))
+                if node["rms"] > tau and level < max_level and w >= 2 and h >= 2:
+                    node["status"] = QUAD_SPLIT
+                    w1, h1 = w // 2, h // 2
+                    nxt += [(x0, y0, w1, h1), (x0 + w1, y0, w - w1, h1), (x0, y0 + h1, w1, h - h1),
+                            (x0 + w1, y0 + h1, w - w1, h - h1)]
+                else:
+                    node["status"] = QUAD_FIT if node["rms"] <= tau else QUAD_HIGH_ERROR
+            out.append(node)
+        level_nodes = nxt
+    return out

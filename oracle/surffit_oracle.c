@@ -134,20 +134,22 @@ static void orient(double nrm[3], double* d) {
 
 static inline int valid_depth(double z) { return isfinite(z) && z > 0.0; }
 
-/* Direct window sums of the method's monomials over V(p).
- * A: 3x3, g: 3, s: scalar; also b2 = sum b^2 (explicit fits only). */
-static int window_sums(const double* Z, int W, int H, const double* intr, int r, int method,
-                       int px, int py, double A[3][3], double g[3], double* s, double* bb, int64_t pm[5]) {
+/* Direct sums of the method's monomials over the valid pixels of the box
+ * [xa, xb] x [ya, yb] (inclusive, clipped to the image).
+ * A: 3x3, g: 3, s: scalar; also bb = sum b^2 (explicit fits only); pm: the
+ * pixel offsets from the reference pixel (px, py), NULL allowed. */
+static int box_sums(const double* Z, int W, int H, const double* intr, int method, int xa, int xb, int ya,
+                    int yb, int px, int py, double A[3][3], double g[3], double* s, double* bb, int64_t pm[5]) {
     const double fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3], dx = intr[4], dy = intr[5];
     memset(A, 0, 9 * sizeof(double));
     g[0] = g[1] = g[2] = 0.0;
     *s = 0.0; *bb = 0.0;
     int n = 0;
     if (pm) pm[0] = pm[1] = pm[2] = pm[3] = pm[4] = 0;
-    for (int y = py - r; y <= py + r; ++y) {
+    for (int y = ya; y <= yb; ++y) {
         if (y < 0 || y >= H) continue;
         const double ty = (y + dy - cy) / fy;
-        for (int x = px - r; x <= px + r; ++x) {
+        for (int x = xa; x <= xb; ++x) {
             if (x < 0 || x >= W) continue;
             const double z = Z[(size_t)y * W + x];
             if (!valid_depth(z)) continue;
@@ -173,13 +175,19 @@ static int window_sums(const double* Z, int W, int H, const double* intr, int r,
             *s += wgt * wgt;
             *bb += b * b;
             ++n;
-            if (pm) {  /* pixel offsets from the window centre: sum j, i, j^2, j i, i^2 */
+            if (pm) {  /* pixel offsets from the reference pixel: sum j, i, j^2, j i, i^2 */
                 const int64_t j = x - px, i = y - py;
                 pm[0] += j; pm[1] += i; pm[2] += j * j; pm[3] += j * i; pm[4] += i * i;
             }
         }
     }
     return n;
+}
+
+/* Direct window sums over V(p): the k x k box centred on p. */
+static int window_sums(const double* Z, int W, int H, const double* intr, int r, int method,
+                       int px, int py, double A[3][3], double g[3], double* s, double* bb, int64_t pm[5]) {
+    return box_sums(Z, W, H, intr, method, px - r, px + r, py - r, py + r, px, py, A, g, s, bb, pm);
 }
 
 /* Solve the 3x3 symmetric system A x = g in FP64 by Gaussian elimination with
@@ -207,6 +215,76 @@ static int solve3(const double A[3][3], const double g[3], double x[3]) {
         for (int j = i + 1; j < 3; ++j) acc -= m[i][j] * x[j];
         x[i] = acc / m[i][i];
     }
+    return 1;
+}
+
+/*
+ * The fit of one set of sums (steps 2-6 of the header), shared by the
+ * per-pixel windows and the rectangles of the quadtree.
+ *   n, pm    valid count and pixel-offset moments (explicit rank rule)
+ *   outputs  nrm[3], d, third (curvature, or the mean squared residual of an
+ *            explicit fit), l[3] eigenvalues of R ascending (NaN for explicit
+ *            fits), lam0 (the minimised residual: lambda0 of R, or the
+ *            residual sum of an explicit fit)
+ * Returns 1 when the fit is defined, 0 when it is not (then nothing is set).
+ */
+static int fit_sums(int method, int unit4, double A[3][3], const double g[3], double s, double bb, int n,
+                    const int64_t pm[5], double nrm[3], double* d_out, double* third_out, double l_out[3],
+                    double* lam0_out) {
+    if (method <= M_STANDARD && s <= 0.0) return 0;
+    if (method >= M_EXPLICIT_DISPARITY) {
+        /* An explicit fit needs a design matrix of full rank: the valid
+         * pixels must not be collinear in the image, decided exactly on
+         * integer offsets, n^2 det cov(j, i) != 0. */
+        const int64_t nn = n;
+        const int64_t cjj = nn * pm[2] - pm[0] * pm[0], cii = nn * pm[4] - pm[1] * pm[1];
+        const int64_t cji = nn * pm[3] - pm[0] * pm[1];
+        if (cjj * cii - cji * cji == 0) return 0;
+    }
+    double d, third;
+    if (method <= M_STANDARD) {
+        double R[4][4] = {{0}}, l[4], vec[4][4];
+        if (!unit4) {
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) R[i][j] = A[i][j] - g[i] * g[j] / s;
+            eig_sorted(3, R, l, vec);
+            for (int i = 0; i < 3; ++i) nrm[i] = vec[0][i];
+            d = -(nrm[0] * g[0] + nrm[1] * g[1] + nrm[2] * g[2]) / s;
+            double tr = l[0] + l[1] + l[2];
+            third = tr != 0.0 ? l[0] / tr : 0.0;
+        } else {
+            for (int i = 0; i < 3; ++i) {
+                for (int j = 0; j < 3; ++j) R[i][j] = A[i][j];
+                R[i][3] = R[3][i] = g[i];
+            }
+            R[3][3] = s;
+            eig_sorted(4, R, l, vec);
+            double nn = sqrt(vec[0][0] * vec[0][0] + vec[0][1] * vec[0][1] + vec[0][2] * vec[0][2]);
+            for (int i = 0; i < 3; ++i) nrm[i] = vec[0][i] / nn;
+            d = vec[0][3] / nn;
+            double tr = l[0] + l[1] + l[2] + l[3];
+            third = tr != 0.0 ? l[0] / tr : 0.0;
+        }
+        l_out[0] = l[0]; l_out[1] = l[1]; l_out[2] = l[2];
+        *lam0_out = l[0];
+    } else {
+        double x[3];
+        if (!solve3(A, g, x)) return 0;
+        /* residual sum b^T b - alpha^T M^T b (normal equations) */
+        double res = bb - (x[0] * g[0] + x[1] * g[1] + x[2] * g[2]);
+        third = res / n;
+        double v[3];
+        if (method == M_EXPLICIT_DISPARITY) { v[0] = x[0]; v[1] = x[1]; v[2] = x[2]; d = -1.0; }
+        else { v[0] = x[0]; v[1] = x[1]; v[2] = -1.0; d = x[2]; }
+        double nn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int i = 0; i < 3; ++i) nrm[i] = v[i] / nn;
+        d /= nn;
+        l_out[0] = l_out[1] = l_out[2] = NAN;
+        *lam0_out = res;
+    }
+    orient(nrm, &d);
+    *d_out = d;
+    *third_out = third;
     return 1;
 }
 
@@ -247,74 +325,52 @@ int sfo_fit(const double* Z, int W, int H, const double* intr, int k, int method
             }
             int ok = n >= min_valid && n > 0;
             if (require_center && !valid_depth(Z[o])) ok = 0;
-            if (ok && method <= M_STANDARD && s <= 0.0) ok = 0;
-            if (ok && method >= M_EXPLICIT_DISPARITY) {
-                /* An explicit fit needs a design matrix of full rank: the
-                 * valid pixels must not be collinear in the image, decided
-                 * exactly on integer offsets, n^2 det cov(j, i) != 0. */
-                const int64_t nn = n;
-                const int64_t cjj = nn * pm[2] - pm[0] * pm[0], cii = nn * pm[4] - pm[1] * pm[1];
-                const int64_t cji = nn * pm[3] - pm[0] * pm[1];
-                if (cjj * cii - cji * cji == 0) ok = 0;
-            }
+            double nrm[3], d, third, l[3], lam0;
+            if (ok) ok = fit_sums(method, unit4, A, g, s, bb, n, pm, nrm, &d, &third, l, &lam0);
             if (!ok) {
                 normals[3 * o] = normals[3 * o + 1] = normals[3 * o + 2] = NAN;
                 offsets[o] = NAN; curv[o] = NAN;
                 if (lam) lam[3 * o] = lam[3 * o + 1] = lam[3 * o + 2] = NAN;
                 continue;
             }
-            double nrm[3], d, third;
-            if (method <= M_STANDARD) {
-                double R[4][4] = {{0}}, l[4], vec[4][4];
-                if (!unit4) {
-                    for (int i = 0; i < 3; ++i)
-                        for (int j = 0; j < 3; ++j) R[i][j] = A[i][j] - g[i] * g[j] / s;
-                    eig_sorted(3, R, l, vec);
-                    for (int i = 0; i < 3; ++i) nrm[i] = vec[0][i];
-                    d = -(nrm[0] * g[0] + nrm[1] * g[1] + nrm[2] * g[2]) / s;
-                    double tr = l[0] + l[1] + l[2];
-                    third = tr != 0.0 ? l[0] / tr : 0.0;
-                    if (lam) { lam[3 * o] = l[0]; lam[3 * o + 1] = l[1]; lam[3 * o + 2] = l[2]; }
-                } else {
-                    for (int i = 0; i < 3; ++i) {
-                        for (int j = 0; j < 3; ++j) R[i][j] = A[i][j];
-                        R[i][3] = R[3][i] = g[i];
-                    }
-                    R[3][3] = s;
-                    eig_sorted(4, R, l, vec);
-                    double nn = sqrt(vec[0][0] * vec[0][0] + vec[0][1] * vec[0][1] + vec[0][2] * vec[0][2]);
-                    for (int i = 0; i < 3; ++i) nrm[i] = vec[0][i] / nn;
-                    d = vec[0][3] / nn;
-                    double tr = l[0] + l[1] + l[2] + l[3];
-                    third = tr != 0.0 ? l[0] / tr : 0.0;
-                    if (lam) { lam[3 * o] = l[0]; lam[3 * o + 1] = l[1]; lam[3 * o + 2] = l[2]; }
-                }
-            } else {
-                double x[3];
-                if (!solve3(A, g, x)) {
-                    normals[3 * o] = normals[3 * o + 1] = normals[3 * o + 2] = NAN;
-                    offsets[o] = NAN; curv[o] = NAN;
-                    if (lam) lam[3 * o] = lam[3 * o + 1] = lam[3 * o + 2] = NAN;
-                    continue;
-                }
-                /* residual sum b^T b - alpha^T M^T b (normal equations) */
-                double res = bb - (x[0] * g[0] + x[1] * g[1] + x[2] * g[2]);
-                third = res / n;
-                double v[3];
-                if (method == M_EXPLICIT_DISPARITY) { v[0] = x[0]; v[1] = x[1]; v[2] = x[2]; d = -1.0; }
-                else { v[0] = x[0]; v[1] = x[1]; v[2] = -1.0; d = x[2]; }
-                double nn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                for (int i = 0; i < 3; ++i) nrm[i] = v[i] / nn;
-                d /= nn;
-                if (lam) lam[3 * o] = lam[3 * o + 1] = lam[3 * o + 2] = NAN;
-            }
-            orient(nrm, &d);
             normals[3 * o] = nrm[0]; normals[3 * o + 1] = nrm[1]; normals[3 * o + 2] = nrm[2];
             offsets[o] = d;
             curv[o] = third;
+            if (lam) { lam[3 * o] = l[0]; lam[3 * o + 1] = l[1]; lam[3 * o + 2] = l[2]; }
         }
     }
     return 0;
+}
+
+/*
+ * sfo_fit_rect: the fit of one rectangle of pixels, [x0, x0 + w) x [y0, y0 + h)
+ * clipped to the image (the grid tiles of the planar segmentation, Section
+ * III), with the same sums and solve as the per-pixel windows.  The pixel
+ * offsets of the explicit rank rule are taken from (x0, y0).
+ *   out[0..2] normal, out[3] offset, out[4] curvature (or mean squared
+ *   residual), out[5..7] eigenvalues of R, out[8] the minimised residual
+ *   (lambda0, or the explicit residual sum); *count = valid pixels.
+ * Returns 1 when the fit is defined, 0 when it is not (n < min_valid, no
+ * data, or a rank-deficient explicit fit; out is then NaN), -1 on bad
+ * arguments.
+ */
+int sfo_fit_rect(const double* Z, int W, int H, const double* intr, int x0, int y0, int w, int h, int method,
+                 int min_valid, double* out, int32_t* count) {
+    if (!Z || W <= 0 || H <= 0 || !intr || w <= 0 || h <= 0 || method < 0 || method > 3 || !out || !count)
+        return -1;
+    double A[3][3], g[3], s, bb;
+    int64_t pm[5];
+    int n = box_sums(Z, W, H, intr, method, x0, x0 + w - 1, y0, y0 + h - 1, x0, y0, A, g, &s, &bb, pm);
+    *count = n;
+    for (int i = 0; i < 9; ++i) out[i] = NAN;
+    if (n < min_valid || n <= 0) return 0;
+    double nrm[3], d, third, l[3], lam0;
+    if (!fit_sums(method, 0, A, g, s, bb, n, pm, nrm, &d, &third, l, &lam0)) return 0;
+    out[0] = nrm[0]; out[1] = nrm[1]; out[2] = nrm[2];
+    out[3] = d; out[4] = third;
+    out[5] = l[0]; out[6] = l[1]; out[7] = l[2];
+    out[8] = lam0;
+    return 1;
 }
 
 /*

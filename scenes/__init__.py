@@ -293,3 +293,32 @@ def target_normals(seed: int, H: int, W: int) -> np.ndarray:
     v = rng.standard_normal((H, W, 3))
     v[..., 2] = -np.abs(v[..., 2]) - 0.5
     return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+# Time-of-flight camera of the paper's segmentation experiment (Section III):
+# 512 x 424 depth frames; intrinsics of that sensor class.
+SEG_W, SEG_H = 512, 424
+SEG_INTRINSICS = Intrinsics(365.0, 365.0, 255.5, 211.5)
+
+
+def segmentation_frame(seed: int, intr: Intrinsics = SEG_INTRINSICS, W: int = SEG_W, H: int = SEG_H,
+                       planes_lo: int = 6, planes_hi: int = 10, z_lo: float = 0.5, z_hi: float = 4.5,
+                       noise_coef: float = KINECT_SIGMA_COEF, miss_lo: float = 0.02,
+                       miss_hi: float = 0.08) -> np.ndarray:
+    """A room-like piecewise-planar frame for the planar segmentation: 6-10 Voronoi planes at
+    0.5-4.5 m, noise 1.425e-3 Z^2 (Eq. 2), 2-8 % blob holes; float32 metres (0 = missing)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = int(rng.integers(planes_lo, planes_hi + 1))
+    Z, _, _ = voronoi_planes(rng, intr, W, H, k, z_lo, z_hi)
+    Z = add_depth_noise(rng, Z, noise_coef)
+    Z = drop_blobs(rng, Z, rng.uniform(miss_lo, miss_hi))
+    return to_f32_metres(Z)
+
+
+def two_plane_frame(intr: Intrinsics, W: int, H: int, split_x: int, n_left, d_left, n_right,
+                    d_right) -> np.ndarray:
+    """Noise-free depth of two planes n.P + d = 0 meeting at column split_x (FP64 metres)."""
+    left = plane_depth(Plane(np.asarray(n_left, float), float(d_left)), intr, W, H)
+    right = plane_depth(Plane(np.asarray(n_right, float), float(d_right)), intr, W, H)
+    Z = np.where(np.arange(W)[None, :] < split_x, left, right)
+    return Z
