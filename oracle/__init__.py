@@ -181,7 +181,7 @@ def quadtree(depth: np.ndarray, intr: Sequence[float], method: str = "disparity"
 
     The image is cut into tile x tile squares from the top-left corner (clipped at the right and
     bottom borders).  A node with fewer than max(min_valid, ceil(permille * area / 1000)) valid
-    pixels is INVALID.  Otherwise its plane is fitted over all its valid pixels, and its error is the
+    pixels, or whose valid pixels are collinear in the image, is INVALID.  Otherwise its plane is fitted over all its valid pixels, and its error is the
     root mean square of the residual the method minimises, e = sqrt(residual / n) (for the implicit
     fits lambda0 of R: the algebraic distance over depth for the disparity form, the point-to-plane
     distance in metres for the standard form).  If e > tau the node splits into four children of
@@ -189,7 +189,7 @@ def quadtree(depth: np.ndarray, intr: Sequence[float], method: str = "disparity"
     w, h >= 2; otherwise it is a FIT leaf (e <= tau) or a HIGH_ERROR leaf.
 
     Returns every evaluated node in breadth-first order as dicts with x0, y0, w, h, level, status,
-    count, normal, offset, curvature, rms.
+    count, normal, offset, curvature, rms, lam (eigenvalues of R, NaN for explicit fits).
     """
     Z = np.ascontiguousarray(depth_to_f64(depth, depth_scale))
     H, W = Z.shape
@@ -202,7 +202,8 @@ def quadtree(depth: np.ndarray, intr: Sequence[float], method: str = "disparity"
             need = max(min_valid, (min_valid_permille * w * h + 999) // 1000)
             r = fit_rect(Z, intr, x0, y0, w, h, method, min_valid=need)
             node = {"x0": x0, "y0": y0, "w": w, "h": h, "level": level, "count": r["count"],
-                    "normal": r["normal"], "offset": r["offset"], "curvature": r["curvature"], "rms": np.nan}
+                    "normal": r["normal"], "offset": r["offset"], "curvature": r["curvature"], "rms": np.nan,
+                    "lam": r["lam"]}
             if not r["ok"]:
                 node["status"] = QUAD_INVALID
             else:

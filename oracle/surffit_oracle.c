@@ -350,9 +350,12 @@ int sfo_fit(const double* Z, int W, int H, const double* intr, int k, int method
  *   out[0..2] normal, out[3] offset, out[4] curvature (or mean squared
  *   residual), out[5..7] eigenvalues of R, out[8] the minimised residual
  *   (lambda0, or the explicit residual sum); *count = valid pixels.
+ * A rectangle whose valid pixels are collinear in the image has no surface
+ * fit with any method: its implicit fit would be the plane through the camera
+ * centre that contains their rays (d = 0), for every depth (exact integer
+ * test on the pixel offsets, as for the explicit fits).
  * Returns 1 when the fit is defined, 0 when it is not (n < min_valid, no
- * data, or a rank-deficient explicit fit; out is then NaN), -1 on bad
- * arguments.
+ * data, collinear pixels; out is then NaN), -1 on bad arguments.
  */
 int sfo_fit_rect(const double* Z, int W, int H, const double* intr, int x0, int y0, int w, int h, int method,
                  int min_valid, double* out, int32_t* count) {
@@ -364,6 +367,12 @@ int sfo_fit_rect(const double* Z, int W, int H, const double* intr, int x0, int 
     *count = n;
     for (int i = 0; i < 9; ++i) out[i] = NAN;
     if (n < min_valid || n <= 0) return 0;
+    {
+        const int64_t nn = n;
+        const int64_t cjj = nn * pm[2] - pm[0] * pm[0], cii = nn * pm[4] - pm[1] * pm[1];
+        const int64_t cji = nn * pm[3] - pm[0] * pm[1];
+        if (cjj * cii - cji * cji == 0) return 0;
+    }
     double nrm[3], d, third, l[3], lam0;
     if (!fit_sums(method, 0, A, g, s, bb, n, pm, nrm, &d, &third, l, &lam0)) return 0;
     out[0] = nrm[0]; out[1] = nrm[1]; out[2] = nrm[2];

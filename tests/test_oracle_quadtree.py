@@ -116,6 +116,19 @@ def test_rect_fit_equals_window_fit(method):
         assert r["offset"] == pytest.approx(ref["offsets"][py, px], rel=1e-12)
 
 
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_collinear_node_is_invalid(method):
+    """One row of pixels: every depth lies in the plane of its camera rays, so there is no surface."""
+    Z, _ = scenes.single_plane_frame(13, INTR, 16, 16)
+    r = oracle.fit_rect(Z, INTR.as_tuple(), 0, 5, 16, 1, method)
+    assert not r["ok"] and r["count"] == 16
+    Zd = Z.copy()
+    Zd[6:, :] = 0.0
+    Zd[:5, :] = 0.0
+    nodes = oracle.quadtree(Zd, INTR.as_tuple(), method, tile=16, max_level=1, tau=1.0, min_valid_permille=0)
+    assert nodes[0]["status"] == oracle.QUAD_INVALID
+
+
 def test_valid_count_rule_is_integer():
     Z, _ = scenes.single_plane_frame(12, INTR, 16, 16)
     area = 16 * 16
