@@ -151,6 +151,33 @@ def mixed_batch_report(dev, timed, world=1):
     return rep
 
 
+def segmentation_report(dev, timed, world=1):
+    """Planar segmentation (Section III): 30 frames of 512x424, root tiles 64 px, up to 3 splits,
+    every form; one step = the whole segmentation of the 30 frames (nodes stay on the device)."""
+    import torch
+
+    from paper_2103_06644_gb300 import SurfaceFitter
+
+    frames = torch.from_numpy(np.stack([scenes.segmentation_frame(scenes.BASE_SEED + 1000 + i)
+                                        for i in range(30)])).to(dev)
+    intr = scenes.SEG_INTRINSICS.as_tuple()
+    taus = {"disparity": 1e-2, "standard": 2e-2, "explicit_disparity": 5e-3, "explicit_standard": 2.6e-2}
+    rep = {"workload": "30 x 512x424 f32, 6-10 planes, 0.5-4.5 m, sigma 1.425e-3 Z^2, 2-8 % holes; "
+                       "root tile 64, max 3 splits, min 50 % valid", "tau": taus}
+    for method, tau in taus.items():
+        f = SurfaceFitter(intr, scenes.SEG_W, scenes.SEG_H, 5, method=method)
+        bufs = f.quadtree(frames, tile=64, max_level=3, tau=tau, to_host=False)
+        for _ in range(3):
+            f.quadtree(frames, tile=64, max_level=3, tau=tau, out=bufs, to_host=False)
+        ms = timed(20, lambda: f.quadtree(frames, tile=64, max_level=3, tau=tau, out=bufs, to_host=False))
+        nodes = int(bufs[1].item())
+        rep[method] = {"ms_per_30_frames": ms, "frames_per_s": world * 30 / (ms / 1000), "nodes": nodes,
+                       "Mnodes_per_s": world * nodes / (ms / 1000) / 1e6,
+                       "value": whole_job_rate(world, 30 * scenes.SEG_W * scenes.SEG_H, ms), "unit": UNIT}
+        f.close()
+    return rep
+
+
 def precision_report(group, dev):
     """Errors per output against the FP64 oracle on the first 1080p frame, for the float32 solve
     (mode 0), the FP64 re-solve of windows with gamma < 1e-2 (mode 1) and the FP64 solve (mode 2).
@@ -463,6 +490,7 @@ def main():
         t_fb = timed(20, diff_step)
         t_f = timed(20, lambda: fd.fit(dd))
         line["mixed_batch"] = mixed_batch_report(dev, timed, world)
+        line["segmentation_512x424"] = segmentation_report(dev, timed, world)
         line["differentiation_k9"] = {"workload": "16x640x480 f32, k=9, loss |n-n*|^2 + 0.1 kappa",
                                       "value": whole_job_rate(world, nd * 307200, t_fb), "unit": UNIT,
                                       "ms_per_step_fwd_bwd": t_fb, "ms_forward": t_f}

@@ -283,6 +283,59 @@ sf_status sf_fit_static(const sf_intrinsics* K, int W, int H, int window, int me
                         float depth_scale, int min_valid, int require_center_valid, const void* depth,
                         float* normals, float* offsets, float* curvature, void* stream);
 
+/*
+ * Planar segmentation by tile subdivision (Section III, planar segmentation
+ * application): the image is cut into square root tiles from the top-left
+ * corner (clipped at the right and bottom borders); each tile's plane is fitted
+ * over all its valid pixels with the context's method; a tile whose fit error
+ * is above the threshold is split into four children of half its width and
+ * height (left/top halves floor(w/2), floor(h/2)), down to max_level
+ * subdivisions.  The fit error is the root mean square of the residual the
+ * method minimises, sqrt(residual / n): for the implicit fits lambda0 of the
+ * Schur complement (the disparity form's residual is the point-to-plane
+ * distance divided by the depth, unitless; the standard form's is the
+ * point-to-plane distance in metres); for the explicit fits the residual of
+ * their regression.  Every node is solved in FP64 from exact integer sums.
+ * Clustering the plane coefficients (the paper's K-means step) is not part of
+ * the library.
+ */
+typedef struct {
+    int tile;               /* root tile side in pixels, 2..64 */
+    int max_level;          /* subdivisions below the roots, 0..6 */
+    float tau;              /* split threshold on the rms fit error (> 0, method units) */
+    int min_valid_permille; /* a node needs >= max(min_valid, ceil(permille * area / 1000))
+                               valid pixels, else it is SF_QUAD_INVALID; 0..1000 */
+} sf_quad_params;
+
+typedef enum {
+    SF_QUAD_FIT = 0,        /* leaf: rms <= tau */
+    SF_QUAD_SPLIT = 1,      /* inner node: rms > tau, its four children follow at level + 1 */
+    SF_QUAD_HIGH_ERROR = 2, /* leaf: rms > tau at max_level (or a side of 1 pixel) */
+    SF_QUAD_INVALID = 3     /* leaf: too few valid pixels, or valid pixels collinear in the image
+                               (no surface fit with any method); fit fields NaN */
+} sf_quad_status;
+
+typedef struct {
+    int32_t frame, x0, y0, w, h, level, status, count; /* rectangle [x0, x0+w) x [y0, y0+h) of frame */
+    float normal[3], offset, curvature, rms;            /* fit (curvature: as for sf_fit) */
+} sf_quad_node;
+
+/*
+ * sf_quadtree -- the segmentation of n_frames frames of the context's size.
+ *   depth     device, as for sf_fit_ex ([n_frames][H][W])
+ *   params    host pointer, read during the call
+ *   nodes     device array of `capacity` sf_quad_node, out: every evaluated
+ *             node (inner nodes included), in no particular order
+ *   n_nodes   device int32, out: the number of nodes evaluated; when it
+ *             exceeds `capacity` only `capacity` were stored
+ * The context's method, depth type and min_valid apply (its window and
+ * require_center_valid do not).  Asynchronous on `stream`; scratch (node
+ * queues, sized for the deepest level) is owned by the context.
+ * Errors: SF_ERR_INVALID_ARG for parameters out of range or null pointers.
+ */
+sf_status sf_quadtree(sf_ctx* ctx, int n_frames, const void* depth, const sf_quad_params* params, sf_quad_node* nodes,
+                      int capacity, int32_t* n_nodes, void* stream);
+
 /* Library version as a static string. */
 const char* sf_version(void);
 

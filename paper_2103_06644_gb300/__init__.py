@@ -131,6 +131,43 @@ class SurfaceFitter:
         """(normals, offsets, curvature) with a backward to the float32 depth (torch.autograd)."""
         return _FitFunction.apply(depth, self)
 
+    # -- planar segmentation (Section III) -------------------------------------------
+    QUAD_FIT, QUAD_SPLIT, QUAD_HIGH_ERROR, QUAD_INVALID = 0, 1, 2, 3
+
+    def quadtree(self, depth, tile: int = 64, max_level: int = 3, tau: float = 1e-2, min_frac: float = 0.5,
+                 capacity: int = 0, out=None, to_host: bool = True, stream=None):
+        """Tile-subdivision plane segmentation of [H, W] or [N, H, W] depth (``sf_quadtree``).
+
+        Returns every evaluated node as a numpy record array (fields of ``sf_quad_node``) sorted by
+        frame, level, y0, x0.  ``min_frac`` is the minimum valid fraction of a node (rounded to
+        per mille); ``capacity`` 0 sizes the node buffer for the largest possible tree.  With
+        ``to_host=False`` nothing is copied or synchronised: the device buffers (nodes as bytes,
+        count) are returned, and ``out`` may pass them back in for reuse.
+        """
+        import torch
+
+        self._check_depth(depth)
+        n = depth.shape[0] if depth.dim() == 3 else 1
+        tiles = -(-self.W // tile) * -(-self.H // tile)
+        if capacity <= 0:
+            capacity = min(tiles * n * sum(4 ** l for l in range(max_level + 1)), 4 * self.W * self.H * n)
+        if out is None:
+            buf = torch.empty(capacity * 56, dtype=torch.uint8, device=depth.device)
+            cnt = torch.zeros(1, dtype=torch.int32, device=depth.device)
+        else:
+            buf, cnt = out
+            capacity = buf.numel() // 56
+        prm = _native.QuadParams(int(tile), int(max_level), float(tau), int(round(1000 * float(min_frac))))
+        _native.check(_native.lib().sf_quadtree(self._h, n, depth.data_ptr(), ctypes.byref(prm), buf.data_ptr(),
+                                                int(capacity), cnt.data_ptr(), _stream_handle(stream)))
+        if not to_host:
+            return buf, cnt
+        total = int(cnt.item())
+        if total > capacity:
+            raise SurfFitError("quadtree produced %d nodes, capacity %d" % (total, capacity))
+        rec = buf[:total * 56].cpu().numpy().view(np.dtype(_native.QUAD_NODE_DTYPE))
+        return np.sort(rec, order=["frame", "level", "y0", "x0"])
+
     # -- host API (copies inside the library call) --------------------------------
     def fit_host(self, depth: np.ndarray, counts: bool = False, out=None):
         """Fit host depth [H, W] or [N, H, W] through ``sf_fit_host``; returns numpy arrays.

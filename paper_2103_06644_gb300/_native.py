@@ -38,6 +38,16 @@ _lib = None
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
 _F = ctypes.c_float
+class QuadParams(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("max_level", ctypes.c_int), ("tau", ctypes.c_float),
+                ("min_valid_permille", ctypes.c_int)]
+
+
+# sf_quad_node as a numpy record (56 bytes)
+QUAD_NODE_DTYPE = [("frame", "<i4"), ("x0", "<i4"), ("y0", "<i4"), ("w", "<i4"), ("h", "<i4"), ("level", "<i4"),
+                   ("status", "<i4"), ("count", "<i4"), ("normal", "<f4", (3,)), ("offset", "<f4"),
+                   ("curvature", "<f4"), ("rms", "<f4")]
+
 SIGNATURES = {
     "sf_create": (_I, [ctypes.POINTER(Intrinsics), _I, _I, _I, ctypes.POINTER(_VP)]),
     "sf_set_params": (_I, [_VP, _I, _I, _F, _I, _I]),
@@ -58,6 +68,7 @@ SIGNATURES = {
     "sf_profile_enable": (_I, [_VP, _I]),
     "sf_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)]),
     "sf_fit_static": (_I, [ctypes.POINTER(Intrinsics), _I, _I, _I, _I, _I, _F, _I, _I, _VP, _VP, _VP, _VP, _VP]),
+    "sf_quadtree": (_I, [_VP, _I, _VP, ctypes.POINTER(QuadParams), _VP, _I, _VP, _VP]),
 }
 
 

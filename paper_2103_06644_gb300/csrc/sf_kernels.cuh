@@ -227,6 +227,42 @@ __device__ __forceinline__ void slide2(T& S0, T& S1, T out, T in, int r) {
 // 2. hpass: block = 128 rows x 64 output columns, tile of fixed-point values
 //    staged in shared memory with coalesced loads, one thread per row.
 // ---------------------------------------------------------------------------
+// Load and quantise the raw depth of a horizontal tile into shared memory:
+// rows [y0, y0 + rows), columns [x0 - r, x0 - r + IW), at row pitch `pitch`.
+// Warp w takes rows w, w + 4, ...; lanes sweep a row (coalesced).  Four rows x
+// CHUNKS 32-column chunks are loaded before any is used, so 4 * CHUNKS loads
+// per thread are in flight at once (issue is in order: a load consumed right
+// away would expose its whole latency).
+template <int DT, int M, int CHUNKS>
+__device__ __forceinline__ void load_tile(const void* __restrict__ depth, int W, int r, float sc, int x0, int y0,
+                                          int rows, int IW, int pitch, int* tile) {
+    constexpr int kRowsPerBatch = 4;
+    constexpr int kWarps = kHThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int rb = warp; rb < rows; rb += kWarps * kRowsPerBatch) {
+        float raw[kRowsPerBatch][CHUNKS];
+#pragma unroll
+        for (int k = 0; k < kRowsPerBatch; ++k) {
+            const int ry = rb + k * kWarps;
+#pragma unroll
+            for (int c = 0; c < CHUNKS; ++c) {
+                const int cx = lane + 32 * c, x = x0 - r + cx;
+                raw[k][c] = (ry < rows && cx < IW && x >= 0 && x < W)
+                                ? load_raw<DT>(depth, (size_t)(y0 + ry) * W + x) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kRowsPerBatch; ++k) {
+            const int ry = rb + k * kWarps;
+#pragma unroll
+            for (int c = 0; c < CHUNKS; ++c) {
+                const int cx = lane + 32 * c;
+                if (ry < rows && cx < IW) tile[ry * pitch + cx] = quantize_raw<DT, M>(raw[k][c], sc);
+            }
+        }
+    }
+}
+
 // Horizontal moments of one tile: rows [y0, y0 + 128) x output columns
 // [x0, x0 + seg) of one frame.  `depth` points at the frame, `pofs` is the
 // frame's offset in the planes; `tile` is shared memory of
@@ -237,36 +273,11 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
     const int IW = seg + 2 * r;
     const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
     const int rows = min(kHThreads, H - y0);
-    {
-        // warp w loads rows w, w + 4, ...; lanes sweep the row (coalesced).
-        // Four rows x up to five 32-column chunks are loaded before any is
-        // used, so 20 loads per thread are in flight at once.
-        constexpr int kRowsPerBatch = 4, kChunks = 5;  // IW <= 128 + 2 * 15 = 158 < 5 * 32
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        constexpr int kWarps = kHThreads / 32;
-        for (int rb = warp; rb < rows; rb += kWarps * kRowsPerBatch) {
-            float raw[kRowsPerBatch][kChunks];
-#pragma unroll
-            for (int k = 0; k < kRowsPerBatch; ++k) {
-                const int ry = rb + k * kWarps;
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c) {
-                    const int cx = lane + 32 * c, x = x0 - r + cx;
-                    raw[k][c] = (ry < rows && cx < IW && x >= 0 && x < W)
-                                    ? load_raw<DT>(depth, (size_t)(y0 + ry) * W + x) : 0.f;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kRowsPerBatch; ++k) {
-                const int ry = rb + k * kWarps;
-#pragma unroll
-                for (int c = 0; c < kChunks; ++c) {
-                    const int cx = lane + 32 * c;
-                    if (ry < rows && cx < IW) tile[ry * pitch + cx] = quantize_raw<DT, M>(raw[k][c], sc);
-                }
-            }
-        }
-    }
+    // the tile's raw depth, quantised; ceil(IW / 32) column chunks per row
+    // (IW <= seg + 30): 2 for seg 32, 3 for 64, 5 for 128
+    if (seg <= 32) load_tile<DT, M, 2>(depth, W, r, sc, x0, y0, rows, IW, pitch, tile);
+    else if (seg <= 64) load_tile<DT, M, 3>(depth, W, r, sc, x0, y0, rows, IW, pitch, tile);
+    else load_tile<DT, M, 5>(depth, W, r, sc, x0, y0, rows, IW, pitch, tile);
     __syncthreads();
     if ((int)threadIdx.x < rows) {
         const int y = y0 + threadIdx.x;
@@ -928,6 +939,129 @@ __global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ de
         }
         g_depth[oi] = g;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Planar segmentation by tile subdivision (Section III): one warp per node.
+// The lanes sum the node's exact integer moments over its rectangle (offsets
+// j, i from the rectangle's centre pixel (x0 + w/2, y0 + h/2), |j|, |i| <= 32),
+// reduce them across the warp, and
+// lane 0 solves the fit in FP64, decides the node's status and, for a split,
+// appends its four children to the next level's queue.
+// ---------------------------------------------------------------------------
+struct QuadRect {
+    int frame, x0, y0, w, h;
+};
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int DT, int M>
+__global__ void __launch_bounds__(256) quad_level_kernel(const void* __restrict__ depth, int W, int H, float scale,
+                                                         const unsigned* __restrict__ vmax_bits, int bits,
+                                                         const double* __restrict__ rays, const QuadRect* __restrict__ in,
+                                                         const int* __restrict__ in_count, int level, int max_level,
+                                                         double tau, int min_valid, int permille,
+                                                         QuadRect* __restrict__ next, int* __restrict__ next_count,
+                                                         int next_cap, sf_quad_node* __restrict__ nodes,
+                                                         int* __restrict__ node_count, int node_cap,
+                                                         int frame_base) {
+    constexpr int B = base_method(M);
+    const int lane = threadIdx.x & 31;
+    const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (idx >= *in_count) return;
+    const QuadRect q = in[idx];
+    const size_t fe = (size_t)W * H;
+    const size_t dbytes = (DT == SF_DEPTH_U16) ? 2 : 4;
+    const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)q.frame * fe;
+    const float sc = ldexpf(1.f, quant_exponent(vmax_bits[q.frame], bits));
+    // exact sums: mask moments in int32 (< 2^31 for sides <= 64), values in int64
+    int n = 0, Sj = 0, Si = 0, Sjj = 0, Sji = 0, Sii = 0;
+    int64_t c0 = 0, cj = 0, ci = 0, c2 = 0, c2j = 0, c2i = 0, c2jj = 0, c2ji = 0, c2ii = 0;
+    const int area = q.w * q.h;
+    const int xc = q.x0 + (q.w >> 1), yc = q.y0 + (q.h >> 1);
+    for (int p = lane; p < area; p += 32) {
+        const int ri = p / q.w, rj = p - ri * q.w;
+        const int i = q.y0 + ri - yc, j = q.x0 + rj - xc;
+        const int v = quantize_raw<DT, M>(load_raw<DT>(dframe, (size_t)(q.y0 + ri) * W + q.x0 + rj), sc);
+        if (v < 0) continue;
+        n += 1; Sj += j; Si += i; Sjj += j * j; Sji += j * i; Sii += i * i;
+        const int64_t vv = (int64_t)v * v;
+        c0 += v; cj += (int64_t)v * j; ci += (int64_t)v * i; c2 += vv;
+        if (B == SF_METHOD_STANDARD) { c2j += vv * j; c2i += vv * i; c2jj += vv * (j * j); c2ji += vv * (j * i); c2ii += vv * (i * i); }
+    }
+    n = warp_sum(n); Sj = warp_sum(Sj); Si = warp_sum(Si); Sjj = warp_sum(Sjj); Sji = warp_sum(Sji); Sii = warp_sum(Sii);
+    c0 = warp_sum(c0); cj = warp_sum(cj); ci = warp_sum(ci); c2 = warp_sum(c2);
+    if (B == SF_METHOD_STANDARD) {
+        c2j = warp_sum(c2j); c2i = warp_sum(c2i); c2jj = warp_sum(c2jj); c2ji = warp_sum(c2ji); c2ii = warp_sum(c2ii);
+    }
+    if (lane != 0) return;
+    sf_quad_node o;
+    o.frame = frame_base + q.frame; o.x0 = q.x0; o.y0 = q.y0; o.w = q.w; o.h = q.h; o.level = level; o.count = n;
+    o.normal[0] = o.normal[1] = o.normal[2] = NAN;
+    o.offset = o.curvature = o.rms = NAN;
+    const int need = max(min_valid, (int)(((int64_t)permille * area + 999) / 1000));
+    // collinear pixels have no surface fit with any method (the implicit one
+    // would be the plane of their camera rays, d = 0): exact integer test
+    bool ok = n >= need && n > 0 && pixels_span_plane<double>(n, Sj, Si, Sjj, Sji, Sii);
+    double rms = 0.0;
+    if (ok) {
+        const double qv = (double)quantum<DT, M>(vmax_bits[q.frame], bits, scale);
+        const double tx = rays[xc], ty = rays[W + yc], a = rays[W + H], b = rays[W + H + 1];
+        const double nf = (double)n;
+        FitOutT<double> f;
+        if constexpr (M == SF_METHOD_DISPARITY)
+            f = solve_disparity<double>(nf, (double)Sj, (double)Si, (double)Sjj, (double)Sji, (double)Sii, c0, cj,
+                                        ci, c2, qv, tx, ty, a, b);
+        else if constexpr (M == SF_METHOD_STANDARD)
+            f = solve_standard<double>(nf, c0, cj, ci, c2, c2j, c2i, c2jj, c2ji, c2ii, qv, tx, ty, a, b);
+        else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY)
+            f = solve_explicit_disparity<double>(nf, (double)Sj, (double)Si, (double)Sjj, (double)Sji, (double)Sii,
+                                                 c0, cj, ci, c2, qv, tx, ty, a, b, ok);
+        else
+            f = solve_explicit_standard<double>(nf, (double)Sj, (double)Si, (double)Sjj, (double)Sji, (double)Sii,
+                                                c0, cj, ci, c2, c2j, c2i, c2jj, c2ji, c2ii, qv, tx, ty, a, b, ok);
+        if (ok) {
+            // mean squared residual: lambda0 / n (implicit), the regression's own (explicit)
+            const double ms = (M == SF_METHOD_DISPARITY || M == SF_METHOD_STANDARD) ? f.curv * f.tr / nf : f.curv;
+            rms = sqrt(ms > 0.0 ? ms : 0.0);
+            o.normal[0] = (float)f.nx; o.normal[1] = (float)f.ny; o.normal[2] = (float)f.nz;
+            o.offset = (float)f.d; o.curvature = (float)f.curv; o.rms = (float)rms;
+        }
+    }
+    if (!ok) {
+        o.status = SF_QUAD_INVALID;
+    } else if (rms > tau && level < max_level && q.w >= 2 && q.h >= 2) {
+        o.status = SF_QUAD_SPLIT;
+        const int base = atomicAdd(next_count, 4);
+        if (base + 4 <= next_cap) {
+            const int w1 = q.w >> 1, h1 = q.h >> 1;
+            next[base + 0] = QuadRect{q.frame, q.x0, q.y0, w1, h1};
+            next[base + 1] = QuadRect{q.frame, q.x0 + w1, q.y0, q.w - w1, h1};
+            next[base + 2] = QuadRect{q.frame, q.x0, q.y0 + h1, w1, q.h - h1};
+            next[base + 3] = QuadRect{q.frame, q.x0 + w1, q.y0 + h1, q.w - w1, q.h - h1};
+        }
+    } else {
+        o.status = rms <= tau ? SF_QUAD_FIT : SF_QUAD_HIGH_ERROR;
+    }
+    const int slot = atomicAdd(node_count, 1);
+    if (slot < node_cap) nodes[slot] = o;
+}
+
+// The root tiles of every frame, in frame-major, row-major order.
+__global__ void quad_roots_kernel(int W, int H, int tile, int nfr, QuadRect* __restrict__ out, int* __restrict__ count) {
+    const int tw = (W + tile - 1) / tile, th = (H + tile - 1) / tile;
+    const int total = tw * th * nfr;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int f = t / (tw * th), rem = t - f * tw * th, ty = rem / tw, tx = rem - ty * tw;
+        const int x0 = tx * tile, y0 = ty * tile;
+        out[t] = QuadRect{f, x0, y0, min(tile, W - x0), min(tile, H - y0)};
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = total;
 }
 
 }  // namespace sf

@@ -15,6 +15,7 @@ template <typename T>
 struct FitOutT {
     T nx, ny, nz, d, curv;
     T gap;  // (lambda1 - lambda0) / lambda2 of the normalised 3x3 matrix
+    T tr;   // trace of R in metric units (implicit fits): lambda0 = curv * tr
 };
 using FitOut = FitOutT<float>;
 
@@ -255,6 +256,7 @@ __device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj
     T l0;
     smallest_eigpair<T>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, l0, o.gap);
     o.curv = l0;
+    o.tr = w.R11 + w.R22 + w.R33;  // R = K Y K^T is the Schur complement itself (no unit)
     o.d = -(o.nx * w.mx + o.ny * w.my + o.nz) * Fn<T>::rcp(w.what) / qw;
     orient<T>(o.nx, o.ny, o.nz, o.d);
     return o;
@@ -296,6 +298,7 @@ __device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t S
     T l0;
     smallest_eigpair<T>(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, l0, o.gap);
     o.curv = l0;
+    o.tr = (R11 + R22 + R33) * qz * qz;  // R is in units of the fixed-point depth squared
     const T zb = (T)m + t0;
     const T px = a * qj + tx * zb, py = b * qi + ty * zb;
     o.d = -(o.nx * px + o.ny * py + o.nz * zb) * qz;
@@ -357,6 +360,7 @@ __device__ __forceinline__ FitOutT<T> solve_explicit_disparity(T nf, T fSj, T fS
     const T res = Cww - bj * Cjw - bi * Ciw;
     o.curv = (res > T(0) ? res : T(0)) * qw * qw * inv_n;
     o.gap = T(1);
+    o.tr = T(0);
     return o;
 }
 
@@ -405,6 +409,7 @@ __device__ __forceinline__ FitOutT<T> solve_explicit_standard(T nf, T fSj, T fSi
     const T res = Czz - ae * Cxz - be * Cyz;
     o.curv = (res > T(0) ? res : T(0)) * qz * qz * inv_n;
     o.gap = T(1);
+    o.tr = T(0);
     return o;
 }
 

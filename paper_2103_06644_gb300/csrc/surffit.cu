@@ -104,6 +104,10 @@ struct sf_ctx {
     size_t flags_cap = 0;      // entries
     unsigned* flag_count = nullptr;
     double* rays64 = nullptr;  // [W] tx, [H] ty, 1/fx, 1/fy in FP64
+    // sf_quadtree: two node queues (ping-pong between levels) and the per-level counters
+    sf::QuadRect* quad_q[2] = {nullptr, nullptr};
+    size_t quad_cap = 0;       // entries per queue
+    int* quad_cnt = nullptr;   // [8]
     // profiling: (stage, start event, stop event) per recorded launch
     bool profiling = false;
     struct Rec { int stage; cudaEvent_t a, b; };
@@ -212,6 +216,62 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return SF_OK;
+}
+
+// Fixed-point bits of the quadtree's node sums: nodes of up to 64 x 64 pixels
+// with offsets |j|, |i| <= 32 from the node's centre keep sum v^2 (disparity)
+// and sum v^2 j^2 (standard: 2^12 * 2^10 * 2^40 = 2^62) inside int64.
+static int quad_bits(int method) { return sf::base_method(method) == SF_METHOD_STANDARD ? 20 : 24; }
+
+template <int DT, int M>
+static sf_status launch_quadtree(sf_ctx* c, int nfr, int frame_base, const void* depth, const sf_quad_params* p,
+                                 sf_quad_node* nodes, int capacity, int32_t* n_nodes, size_t roots, cudaStream_t st) {
+    constexpr int B = sf::base_method(M);
+    const size_t fe = (size_t)c->W * c->H;
+    const int raw_z = (DT == SF_DEPTH_U16 && B == SF_METHOD_STANDARD) ? 1 : 0;
+    const int bits = quad_bits(M);
+    SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
+    if (!raw_z) {
+        int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
+        blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
+        sf::range_kernel<DT, B><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, c->depth_scale, c->vmax);
+    }
+    SF_CUDA(cudaMemsetAsync(c->quad_cnt, 0, sizeof(int) * 8, st));
+    sf::quad_roots_kernel<<<(int)std::min<size_t>((roots + 255) / 256, 1024), 256, 0, st>>>(c->W, c->H, p->tile, nfr,
+                                                                                            c->quad_q[0], c->quad_cnt);
+    size_t level_max = roots;
+    for (int l = 0; l <= p->max_level; ++l) {
+        const size_t n = std::min(level_max, c->quad_cap);
+        const int blocks = (int)((n + 7) / 8);
+        sf::quad_level_kernel<DT, M><<<blocks, 256, 0, st>>>(
+            depth, c->W, c->H, c->depth_scale, c->vmax, bits, c->rays64, c->quad_q[l & 1], c->quad_cnt + l, l,
+            p->max_level, (double)p->tau, c->min_valid, p->min_valid_permille, c->quad_q[(l + 1) & 1],
+            c->quad_cnt + l + 1, (int)c->quad_cap, nodes, n_nodes, capacity, frame_base);
+        level_max *= 4;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "quadtree launch");
+    return SF_OK;
+}
+
+template <int DT>
+static sf_status launch_quadtree_for(sf_ctx* c, int nfr, int frame_base, const void* depth, const sf_quad_params* p,
+                                     sf_quad_node* nodes, int capacity, int32_t* n_nodes, size_t roots,
+                                     cudaStream_t st) {
+    switch (c->method) {
+        case SF_METHOD_DISPARITY:
+            return launch_quadtree<DT, SF_METHOD_DISPARITY>(c, nfr, frame_base, depth, p, nodes, capacity, n_nodes,
+                                                            roots, st);
+        case SF_METHOD_STANDARD:
+            return launch_quadtree<DT, SF_METHOD_STANDARD>(c, nfr, frame_base, depth, p, nodes, capacity, n_nodes,
+                                                           roots, st);
+        case SF_METHOD_EXPLICIT_DISPARITY:
+            return launch_quadtree<DT, SF_METHOD_EXPLICIT_DISPARITY>(c, nfr, frame_base, depth, p, nodes, capacity,
+                                                                     n_nodes, roots, st);
+        default:
+            return launch_quadtree<DT, SF_METHOD_EXPLICIT_STANDARD>(c, nfr, frame_base, depth, p, nodes, capacity,
+                                                                    n_nodes, roots, st);
+    }
 }
 
 template <int DT>
@@ -514,6 +574,60 @@ sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals
     return SF_OK;
 }
 
+sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_params* p, sf_quad_node* nodes,
+                      int capacity, int32_t* n_nodes, void* stream) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    if (!p || !n_nodes) return fail(SF_ERR_INVALID_ARG, "null params or n_nodes");
+    if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
+    if (capacity < 0 || (capacity > 0 && !nodes)) return fail(SF_ERR_INVALID_ARG, "bad node buffer");
+    if (p->tile < 2 || p->tile > 64) return fail(SF_ERR_INVALID_ARG, "tile must be in [2, 64]");
+    if (p->max_level < 0 || p->max_level > 6) return fail(SF_ERR_INVALID_ARG, "max_level must be in [0, 6]");
+    if (!(p->tau > 0.f) || !std::isfinite(p->tau)) return fail(SF_ERR_INVALID_ARG, "tau must be finite and > 0");
+    if (p->min_valid_permille < 0 || p->min_valid_permille > 1000)
+        return fail(SF_ERR_INVALID_ARG, "min_valid_permille must be in [0, 1000]");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    SF_CUDA(cudaMemsetAsync(n_nodes, 0, sizeof(int32_t), st));
+    if (n_frames == 0) return SF_OK;
+    if (!depth) return fail(SF_ERR_INVALID_ARG, "null depth");
+    // frames go through in groups of at most 64 (the per-frame quantum slots)
+    const int per = std::min(n_frames, 64);
+    const size_t tiles = (size_t)((c->W + p->tile - 1) / p->tile) * ((c->H + p->tile - 1) / p->tile);
+    const size_t roots = tiles * per;
+    size_t cap = roots;
+    for (int l = 0; l < p->max_level; ++l) cap *= 4;
+    cap = std::min(cap, (size_t)c->W * c->H * per);  // a node holds at least one pixel
+    if (cap > ((size_t)1 << 28)) return fail(SF_ERR_INVALID_ARG, "quadtree too large: %zu nodes per level", cap);
+    if (c->quad_cap < cap) {
+        for (int i = 0; i < 2; ++i) {
+            if (c->quad_q[i]) cudaFree(c->quad_q[i]);
+            c->quad_q[i] = nullptr;
+        }
+        c->quad_cap = 0;
+        for (int i = 0; i < 2; ++i) {
+            cudaError_t e = cudaMalloc(&c->quad_q[i], sizeof(sf::QuadRect) * cap);
+            if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "quadtree queue of %zu nodes failed", cap);
+        }
+        c->quad_cap = cap;
+    }
+    if (!c->quad_cnt) {
+        cudaError_t e = cudaMalloc(&c->quad_cnt, sizeof(int) * 8);
+        if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "quadtree counters failed");
+    }
+    const size_t fe = (size_t)c->W * c->H;
+    const size_t dbytes = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
+    for (int f0 = 0; f0 < n_frames; f0 += per) {
+        const int nfr = std::min(per, n_frames - f0);
+        const void* dp = static_cast<const char*>(depth) + dbytes * fe * f0;
+        sf_status s = c->depth_type == SF_DEPTH_F32
+                          ? launch_quadtree_for<SF_DEPTH_F32>(c, nfr, f0, dp, p, nodes, capacity, n_nodes,
+                                                              tiles * nfr, st)
+                          : launch_quadtree_for<SF_DEPTH_U16>(c, nfr, f0, dp, p, nodes, capacity, n_nodes,
+                                                              tiles * nfr, st);
+        if (s != SF_OK) return s;
+    }
+    return SF_OK;
+}
+
 sf_status sf_set_tiles(sf_ctx* c, int hseg, int vband) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (hseg != 32 && hseg != 64 && hseg != 128) return fail(SF_ERR_INVALID_ARG, "hseg must be 32, 64 or 128");
@@ -621,6 +735,9 @@ sf_status sf_destroy(sf_ctx* c) {
     if (c->flags) cudaFree(c->flags);
     if (c->flag_count) cudaFree(c->flag_count);
     if (c->rays64) cudaFree(c->rays64);
+    for (int i = 0; i < 2; ++i)
+        if (c->quad_q[i]) cudaFree(c->quad_q[i]);
+    if (c->quad_cnt) cudaFree(c->quad_cnt);
     delete c;
     return SF_OK;
 }
