@@ -113,6 +113,26 @@ sf_status sf_set_params(sf_ctx* ctx, int method, int depth_type, float depth_sca
                         int require_center_valid);
 
 /*
+ * Normalisation of the implicit fits (Eq. 4).  Section I.C's Euclidean
+ * invariance holds for |(a, b, c)| = 1, the default: the offset is eliminated
+ * and the normal is the smallest eigenvector of the 3x3 Schur complement.  The
+ * literal constraint of Eq. 4, |(a, b, c, d)| = 1, takes the smallest
+ * eigenvector alpha of the whole 4x4 scatter matrix in metric units (metres,
+ * 1/metres): n = alpha[0:3] / |alpha[0:3]|, d = alpha[3] / |alpha[0:3]|,
+ * curvature = lambda0 / trace of the 4x4.  Its result depends on the units.
+ */
+typedef enum { SF_CONSTRAINT_UNIT3 = 0, SF_CONSTRAINT_UNIT4 = 1 } sf_constraint;
+
+/*
+ * sf_set_constraint -- choose the normalisation for the implicit fits of this
+ * context (SF_CONSTRAINT_UNIT3 default).  With SF_CONSTRAINT_UNIT4, sf_fit,
+ * sf_fit_ex and sf_fit_host solve the 4x4 problem (explicit methods:
+ * SF_ERR_UNSUPPORTED at fit time); sf_fit_backward and sf_quadtree return
+ * SF_ERR_UNSUPPORTED.  sf_set_precision applies to both constraints.
+ */
+sf_status sf_set_constraint(sf_ctx* ctx, int constraint);
+
+/*
  * sf_set_precision -- precision of the per-pixel solve.  The window sums are
  * exact integers in every mode; the modes differ in the solve:
  *   0  float32 solve (default).  Normal error ~ 4e-7 / gamma rad against an

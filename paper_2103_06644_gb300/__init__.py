@@ -76,6 +76,10 @@ class SurfaceFitter:
         """Tile shape: hseg in {32, 64, 128} columns, vband rows per band (0 = automatic)."""
         _native.check(_native.lib().sf_set_tiles(self._h, int(hseg), int(vband)))
 
+    def set_constraint(self, unit4: bool) -> None:
+        """|(a,b,c)| = 1 (default, False) or the literal |(a,b,c,d)| = 1 of Eq. 4 (True) for the implicit fits."""
+        _native.check(_native.lib().sf_set_constraint(self._h, 1 if unit4 else 0))
+
     def set_precision(self, mode: int, tau: float = 1e-2) -> None:
         """0: float32 solve; 1: + FP64 re-solve where gamma < tau; 2: FP64 solve everywhere."""
         _native.check(_native.lib().sf_set_precision(self._h, int(mode), float(tau)))

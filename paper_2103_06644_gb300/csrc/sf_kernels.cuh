@@ -510,7 +510,7 @@ using StdState = StdStateT<false>;
 // Not inlined: the single-context and the batch kernels then run the same
 // machine code, so their results agree bit for bit (inlined copies may be
 // contracted into FMAs differently); one call covers a whole band.
-template <int DT, int M>
+template <int DT, int M, bool U4 = false>
 __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, float scale, float q,
                                              const Planes P, size_t pofs, int x, int y0, int band,
                                              const float* __restrict__ txt, const float* __restrict__ tyt, float a,
@@ -543,10 +543,10 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
         FitOut fo_;
         if (ok) {
             if constexpr (M == SF_METHOD_DISPARITY)
-                fo_ = solve_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, tyt[y],
+                fo_ = solve_disparity<float, U4>(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, tyt[y],
                                       a, b);
             else if constexpr (M == SF_METHOD_STANDARD)
-                fo_ = solve_standard((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
+                fo_ = solve_standard<float, U4>((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
                                      S.Szzii, q, tx, tyt[y], a, b);
             else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY)
                 fo_ = solve_explicit_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q,
@@ -578,7 +578,7 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
     }
 }
 
-template <int DT, int M>
+template <int DT, int M, bool U4 = false>
 __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
                                                           float scale, const unsigned* __restrict__ vmax_bits,
                                                           int bits, int raw_z, int Wp, size_t plane_elems,
@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* 
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * fe;
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);  // metric value of one fixed-point unit
     const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
-    vpass_column<DT, M>(dframe, W, H, r, scale, q, P, (size_t)f * plane_elems, x, blockIdx.y * band, band, cal.tx,
+    vpass_column<DT, M, U4>(dframe, W, H, r, scale, q, P, (size_t)f * plane_elems, x, blockIdx.y * band, band, cal.tx,
                         cal.ty, cal.a, cal.b, min_valid, require_center, normals + 3 * fe * f, offsets + fe * f,
                         curvature + fe * f, counts ? counts + fe * f : nullptr, tau, flags, flag_count, f);
 }
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_batch_kernel(const 
 // The moments are exact integers, so this removes every float32 rounding of
 // the solve; only the fixed-point quantisation of the depth remains.
 // ---------------------------------------------------------------------------
-template <int DT, int M>
+template <int DT, int M, bool U4 = false>
 __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, float scale,
                                                       const unsigned* __restrict__ vmax_bits, int bits, int Wp,
                                                       size_t plane_elems, int nframes, void* __restrict__ planes_base,
@@ -722,12 +722,12 @@ __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, float
         if constexpr (M == SF_METHOD_DISPARITY) {
             DispState S(P);
             S.init(pb, kGroup, H, y, r);
-            o = solve_disparity<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj, (double)S.Sji,
+            o = solve_disparity<double, U4>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj, (double)S.Sji,
                                         (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty, a, b);
         } else if constexpr (M == SF_METHOD_STANDARD) {
             StdState S(P);
             S.init(pb, kGroup, H, y, r);
-            o = solve_standard<double>((double)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
+            o = solve_standard<double, U4>((double)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
                                        S.Szzii, q, tx, ty, a, b);
         } else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY) {
             DispState S(P);

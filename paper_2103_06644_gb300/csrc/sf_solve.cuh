@@ -172,6 +172,63 @@ __device__ __forceinline__ void orient(T& nx, T& ny, T& nz, T& d) {
     if (flip) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
 }
 
+// The literal constraint of Eq. 4, |(a, b, c, d)| = 1: the smallest eigenpair
+// of the 4x4 scatter M = [[A, g], [g^T, s]] (metric units).  With
+// alpha = (u, t), the eigen-equations give t = g.u / (lambda - s) and
+// (A - g g^T / (s - lambda)) u = lambda u, i.e. u is an eigenvector of
+// R_lambda = R - lambda / (s (s - lambda)) g g^T (R the Schur complement) for
+// the eigenvalue lambda itself.  Iteration: u = smallest eigenvector of
+// R_lambda (a 3x3 solve on the centred R), then lambda = the Rayleigh
+// quotient of M at (u, t(u)),
+//   rho = [u^T R u + (g.u)^2 lambda^2 / (s (s - lambda)^2)] / [1 + (g.u)^2 / (s - lambda)^2],
+// a sum of non-negative terms (no cancellation, where lambda0(R) - c (g.u)^2
+// would lose a factor ~d^2 for distant planes).  Rayleigh quotients stay
+// >= lambda_min(M) and converge quadratically: 4-5 steps to 1e-6 typically,
+// at most kU4Steps.  Outputs: n = u, d = t (|u| = 1), curvature
+// lambda / trace(M).  Working on R rather than on M keeps the raw second
+// moments of M, whose smallest eigenvalue is ~1e-6 of its largest, out of
+// the floating-point arithmetic.
+constexpr int kU4Steps = 10;
+
+template <typename T>
+__device__ __forceinline__ FitOutT<T> solve_unit4(T R11, T R12, T R13, T R22, T R23, T R33, T g0, T g1, T g2, T s) {
+    FitOutT<T> o;
+    const T g2sum = g0 * g0 + g1 * g1 + g2 * g2;
+    T lam = T(0), u0 = T(0), u1 = T(0), u2 = T(1), l0n = T(0), gap = T(0), l0R = T(0), gu = T(0);
+#pragma unroll 1
+    for (int it = 0;; ++it) {
+        const T c = lam * Fn<T>::rcp(s * (s - lam));
+        const T a11 = R11 - c * g0 * g0, a12 = R12 - c * g0 * g1, a13 = R13 - c * g0 * g2;
+        const T a22 = R22 - c * g1 * g1, a23 = R23 - c * g1 * g2, a33 = R33 - c * g2 * g2;
+        // R_lambda may be indefinite: its eigenvalues are >= lambda0(R) - c|g|^2, so a shift by
+        // the excess keeps it semi-definite with the same eigenvectors (0 near the root)
+        const T ex = c * g2sum - l0R;
+        const T sh = ex > T(0) ? ex : T(0);
+        smallest_eigpair<T>(a11 + sh, a12, a13, a22 + sh, a23, a33 + sh, u0, u1, u2, l0n, gap);
+        const T uRu = u0 * (R11 * u0 + R12 * u1 + R13 * u2) + u1 * (R12 * u0 + R22 * u1 + R23 * u2) +
+                      u2 * (R13 * u0 + R23 * u1 + R33 * u2);
+        if (it == 0) l0R = uRu > T(0) ? uRu : T(0);
+        gu = g0 * u0 + g1 * u1 + g2 * u2;
+        const T sl = s - lam;
+        const T isl2 = Fn<T>::rcp(sl * sl);
+        T rho = (uRu + gu * gu * lam * lam * Fn<T>::rcp(s) * isl2) * Fn<T>::rcp(T(1) + gu * gu * isl2);
+        const T top = s * T(0.999999);
+        rho = rho < T(0) ? T(0) : (rho > top ? top : rho);
+        const T step = rho > lam ? rho - lam : lam - rho;
+        const bool done = step <= T(1e-6) * rho || it == kU4Steps;
+        lam = rho;
+        if (done) break;
+    }
+    o.nx = u0; o.ny = u1; o.nz = u2;
+    o.d = gu * Fn<T>::rcp(lam - s);
+    orient<T>(o.nx, o.ny, o.nz, o.d);
+    const T trM = R11 + R22 + R33 + g2sum * Fn<T>::rcp(s) + s;
+    o.curv = lam * Fn<T>::rcp(trM);
+    o.gap = gap;
+    o.tr = trM;
+    return o;
+}
+
 // Disparity (RGBD-space) implicit fit of one window, Eq. 12 / Eq. 14.
 //
 // Inputs are exact window sums over the valid pixels q of the window:
@@ -247,11 +304,17 @@ __device__ __forceinline__ DispWindowT<T> build_disparity(T nf, T fSj, T fSi, T 
     return w;
 }
 
-template <typename T = float>
+template <typename T = float, bool U4 = false>
 __device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj, T fSji, T fSii, int64_t Sw,
                                                       int64_t Swj, int64_t Swi, int64_t Sww, T qw, T tx, T ty, T a,
                                                       T b) {
     const DispWindowT<T> w = build_disparity<T>(nf, fSj, fSi, fSjj, fSji, fSii, Sw, Swj, Swi, Sww, tx, ty, a, b);
+    if constexpr (U4) {
+        // g = sum w m = (sum w) mhat, s = sum w^2 = n wbar what (metric)
+        const T sw = qw * nf * w.wbar;
+        return solve_unit4<T>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, sw * w.mx, sw * w.my, sw,
+                              sw * qw * w.what);
+    }
     FitOutT<T> o;
     T l0;
     smallest_eigpair<T>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, l0, o.gap);
@@ -268,7 +331,7 @@ __device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj
 // P_q = Z_q m_q = T [Z j, Z i, Z] with T = [[a, 0, tx], [0, b, ty], [0, 0, 1]],
 // so the covariance of the points is T C T^T, C the covariance of
 // [z j, z i, z] (re-centred on an integer near the mean depth first).
-template <typename T = float>
+template <typename T = float, bool U4 = false>
 __device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
                                                      int64_t Szzj, int64_t Szzi, int64_t Szzjj, int64_t Szzji,
                                                      int64_t Szzii, T qz, T tx, T ty, T a, T b) {
@@ -294,13 +357,19 @@ __device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t S
     const T R22 = b * b * Cii + T(2) * b * ty * Ciz + ty * ty * Czz;
     const T R23 = b * Ciz + ty * Czz;
     const T R33 = Czz;
+    const T zb = (T)m + t0;
+    const T px = a * qj + tx * zb, py = b * qi + ty * zb;
+    if constexpr (U4) {
+        // metric: R qz^2, g = sum P = n qz (px, py, zb), s = n
+        const T q2 = qz * qz, gn = nf * qz;
+        return solve_unit4<T>(R11 * q2, R12 * q2, R13 * q2, R22 * q2, R23 * q2, R33 * q2, gn * px, gn * py,
+                              gn * zb, nf);
+    }
     FitOutT<T> o;
     T l0;
     smallest_eigpair<T>(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, l0, o.gap);
     o.curv = l0;
     o.tr = (R11 + R22 + R33) * qz * qz;  // R is in units of the fixed-point depth squared
-    const T zb = (T)m + t0;
-    const T px = a * qj + tx * zb, py = b * qi + ty * zb;
     o.d = -(o.nx * px + o.ny * py + o.nz * zb) * qz;
     orient<T>(o.nx, o.ny, o.nz, o.d);
     return o;

@@ -99,6 +99,7 @@ struct sf_ctx {
     size_t adj_bytes = 0;
     // precision fallback
     int precision_mode = 0;    // 0 float32 solve, 1 + FP64 re-solve where gap < tau, 2 FP64 everywhere
+    int constraint = SF_CONSTRAINT_UNIT3;  // normalisation of the implicit fits (Eq. 4)
     float tau = 1e-2f;
     unsigned long long* flags = nullptr;
     size_t flags_cap = 0;      // entries
@@ -170,7 +171,7 @@ static int vertical_band(const sf_ctx* c, int nfr) {
     return band;
 }
 
-template <int DT, int M>
+template <int DT, int M, bool U4 = false>
 static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,
                              int32_t* counts, cudaStream_t st) {
     const size_t fe = (size_t)c->W * c->H;
@@ -201,14 +202,14 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
         const bool fb = c->precision_mode > 0 && c->flags;
         if (fb) SF_CUDA(cudaMemsetAsync(c->flag_count, 0, sizeof(unsigned), st));
         const float tau = c->precision_mode == 2 ? INFINITY : c->tau;
-        sf::vpass_kernel<DT, M><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
+        sf::vpass_kernel<DT, M, U4><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
                                                                bits, raw_z, c->Wp, c->plane_elems, c->planes, cal,
                                                                c->min_valid, c->require_center, band, normals,
                                                                offsets, curv, counts, tau, fb ? c->flags : nullptr,
                                                                c->flag_count);
         if (fb) {
             StageTimer t2(c, 3, st);
-            sf::resolve_kernel<DT, M><<<152 * 8, 128, 0, st>>>(c->W, c->H, c->r, c->depth_scale, c->vmax, bits, c->Wp,
+            sf::resolve_kernel<DT, M, U4><<<152 * 8, 128, 0, st>>>(c->W, c->H, c->r, c->depth_scale, c->vmax, bits, c->Wp,
                                                               c->plane_elems, nfr, c->planes, cal, c->rays64,
                                                               c->flags, c->flag_count, normals, offsets, curv);
         }
@@ -279,9 +280,13 @@ static sf_status launch_pass_for(sf_ctx* c, int nfr, const void* depth, float* n
                                  int32_t* counts, cudaStream_t st) {
     switch (c->method) {
         case SF_METHOD_DISPARITY:
-            return launch_pass<DT, SF_METHOD_DISPARITY>(c, nfr, depth, normals, offsets, curv, counts, st);
+            return c->constraint == SF_CONSTRAINT_UNIT4
+                       ? launch_pass<DT, SF_METHOD_DISPARITY, true>(c, nfr, depth, normals, offsets, curv, counts, st)
+                       : launch_pass<DT, SF_METHOD_DISPARITY>(c, nfr, depth, normals, offsets, curv, counts, st);
         case SF_METHOD_STANDARD:
-            return launch_pass<DT, SF_METHOD_STANDARD>(c, nfr, depth, normals, offsets, curv, counts, st);
+            return c->constraint == SF_CONSTRAINT_UNIT4
+                       ? launch_pass<DT, SF_METHOD_STANDARD, true>(c, nfr, depth, normals, offsets, curv, counts, st)
+                       : launch_pass<DT, SF_METHOD_STANDARD>(c, nfr, depth, normals, offsets, curv, counts, st);
         case SF_METHOD_EXPLICIT_DISPARITY:
             return launch_pass<DT, SF_METHOD_EXPLICIT_DISPARITY>(c, nfr, depth, normals, offsets, curv, counts, st);
         default:
@@ -458,6 +463,8 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
     if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
     if (n_frames == 0) return SF_OK;
     if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
+    if (c->constraint == SF_CONSTRAINT_UNIT4 && c->method != SF_METHOD_DISPARITY && c->method != SF_METHOD_STANDARD)
+        return fail(SF_ERR_UNSUPPORTED, "the |(a,b,c,d)| = 1 constraint applies to the implicit fits");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t fe = (size_t)c->W * c->H;
     const size_t dbytes = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
@@ -578,6 +585,8 @@ sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_
                       int capacity, int32_t* n_nodes, void* stream) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (!p || !n_nodes) return fail(SF_ERR_INVALID_ARG, "null params or n_nodes");
+    if (c->constraint != SF_CONSTRAINT_UNIT3)
+        return fail(SF_ERR_UNSUPPORTED, "the segmentation uses the |(a,b,c)| = 1 constraint only");
     if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
     if (capacity < 0 || (capacity > 0 && !nodes)) return fail(SF_ERR_INVALID_ARG, "bad node buffer");
     if (p->tile < 2 || p->tile > 64) return fail(SF_ERR_INVALID_ARG, "tile must be in [2, 64]");
@@ -646,6 +655,14 @@ sf_status sf_set_precision(sf_ctx* c, int mode, float tau) {
     return SF_OK;
 }
 
+sf_status sf_set_constraint(sf_ctx* c, int constraint) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    if (constraint != SF_CONSTRAINT_UNIT3 && constraint != SF_CONSTRAINT_UNIT4)
+        return fail(SF_ERR_INVALID_ARG, "constraint %d must be SF_CONSTRAINT_UNIT3 or SF_CONSTRAINT_UNIT4", constraint);
+    c->constraint = constraint;
+    return SF_OK;
+}
+
 sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const float* g_normals, const float* g_offsets,
                           const float* g_curvature, float* g_depth, void* stream) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
@@ -655,6 +672,8 @@ sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const floa
         return fail(SF_ERR_INVALID_ARG, "null buffer");
     if (c->method != SF_METHOD_DISPARITY && c->method != SF_METHOD_STANDARD)
         return fail(SF_ERR_UNSUPPORTED, "the backward covers the implicit fits only");
+    if (c->constraint != SF_CONSTRAINT_UNIT3)
+        return fail(SF_ERR_UNSUPPORTED, "the backward covers the |(a,b,c)| = 1 constraint only");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t fe = (size_t)c->W * c->H;
     const size_t dbytes = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
