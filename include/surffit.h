@@ -66,7 +66,11 @@ typedef enum {
     SF_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up                 */
 } sf_status;
 
-typedef enum { SF_DEPTH_F32 = 0, SF_DEPTH_U16 = 1 } sf_depth_type;
+/* SF_DEPTH_DISPARITY_U16: raw sensor disparity D (uint16, 0 = missing) with
+ * 1/Z = alpha D + beta (sf_set_disparity_model); the disparity form then
+ * fits the measured disparity directly, without any Z -> 1/Z conversion
+ * (the future work of the paper's conclusion). */
+typedef enum { SF_DEPTH_F32 = 0, SF_DEPTH_U16 = 1, SF_DEPTH_DISPARITY_U16 = 2 } sf_depth_type;
 
 typedef enum {
     SF_METHOD_DISPARITY = 0,
@@ -104,13 +108,27 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
 /*
  * sf_set_params -- choose the fit and the depth encoding.
  *   method        an sf_method value
- *   depth_type    SF_DEPTH_F32 (metres) or SF_DEPTH_U16 (raw units, 0 = missing)
+ *   depth_type    SF_DEPTH_F32 (metres), SF_DEPTH_U16 (raw units, 0 = missing) or
+ *                 SF_DEPTH_DISPARITY_U16 (raw disparity, model from sf_set_disparity_model)
  *   depth_scale   metres per raw unit for SF_DEPTH_U16 (ignored for f32), > 0
  *   min_valid     minimum number of valid window pixels, >= 1
  *   require_center_valid  nonzero: the centre pixel must be valid
  */
 sf_status sf_set_params(sf_ctx* ctx, int method, int depth_type, float depth_scale, int min_valid,
                         int require_center_valid);
+
+/*
+ * sf_set_disparity_model -- the sensor model of SF_DEPTH_DISPARITY_U16 input,
+ * 1/Z = alpha D + beta (1/metres; e.g. alpha = 1/(f b s) for a stereo pair of
+ * baseline b and focal length f reporting disparity in 1/s pixel, beta = 0).
+ * The library represents the model exactly in integers as
+ * 1/Z = (|alpha| / 128) (sign(alpha) 128 D + round(128 beta / |alpha|)): beta
+ * is kept to 1/128 of a disparity unit, alpha exactly.  A pixel is missing
+ * when D == 0 or its 1/Z <= 0.
+ * Errors: SF_ERR_INVALID_ARG unless alpha is finite and nonzero and
+ * |128 beta / alpha| <= 2^23.  Default: alpha = 1, beta = 0.
+ */
+sf_status sf_set_disparity_model(sf_ctx* ctx, double alpha, double beta);
 
 /*
  * Normalisation of the implicit fits (Eq. 4).  Section I.C's Euclidean

@@ -20,7 +20,7 @@ __all__ = ["SurfaceFitter", "SurfaceFitBatch", "SurfFitError", "METHODS", "DEPTH
            "version"]
 
 METHODS = {"disparity": 0, "standard": 1, "explicit_disparity": 2, "explicit_standard": 3}
-DEPTH_TYPES = {"f32": 0, "u16": 1}
+DEPTH_TYPES = {"f32": 0, "u16": 1, "disparity_u16": 2}
 
 
 def version() -> str:
@@ -76,6 +76,10 @@ class SurfaceFitter:
         """Tile shape: hseg in {32, 64, 128} columns, vband rows per band (0 = automatic)."""
         _native.check(_native.lib().sf_set_tiles(self._h, int(hseg), int(vband)))
 
+    def set_disparity_model(self, alpha: float, beta: float = 0.0) -> None:
+        """Sensor model of ``disparity_u16`` input: 1/Z = alpha * D + beta (1/metres)."""
+        _native.check(_native.lib().sf_set_disparity_model(self._h, float(alpha), float(beta)))
+
     def set_constraint(self, unit4: bool) -> None:
         """|(a,b,c)| = 1 (default, False) or the literal |(a,b,c,d)| = 1 of Eq. 4 (True) for the implicit fits."""
         _native.check(_native.lib().sf_set_constraint(self._h, 1 if unit4 else 0))
@@ -88,7 +92,7 @@ class SurfaceFitter:
     def _check_depth(self, depth):
         import torch
 
-        want = torch.float32 if self.depth_type == "f32" else torch.uint16
+        want = torch.float32 if self.depth_type == "f32" else torch.uint16  # u16 and disparity_u16
         if depth.dtype != want and not (want == torch.uint16 and depth.dtype == torch.int16):
             raise TypeError("depth must be %s for depth_type %s" % (want, self.depth_type))
         if not depth.is_cuda or not depth.is_contiguous():

@@ -47,37 +47,58 @@ __host__ __device__ constexpr int base_method(int M) {
 constexpr int kVBlocks = 6;
 
 // ---------------------------------------------------------------------------
-// Depth decoding.
+// Depth decoding.  Codec: how a stored value becomes depth.
+//   SF_DEPTH_F32             metres (scale unused)
+//   SF_DEPTH_U16             raw * scale metres, raw == 0 missing
+//   SF_DEPTH_DISPARITY_U16   raw disparity D: 1/Z = scale * (dmul * D + dadd)
+//                            (dmul = +-128, dadd an integer: the sensor model
+//                            1/Z = alpha D + beta with beta to 1/128 of a
+//                            disparity unit); D == 0 or 1/Z <= 0 missing
 // ---------------------------------------------------------------------------
-template <int DT>
-__device__ __forceinline__ float load_depth(const void* base, size_t idx, float scale);
-
-template <>
-__device__ __forceinline__ float load_depth<SF_DEPTH_F32>(const void* base, size_t idx, float) {
-    return __ldg(reinterpret_cast<const float*>(base) + idx);
-}
-template <>
-__device__ __forceinline__ float load_depth<SF_DEPTH_U16>(const void* base, size_t idx, float scale) {
-    const unsigned short raw = __ldg(reinterpret_cast<const unsigned short*>(base) + idx);
-    return raw ? (float)raw * scale : 0.f;
-}
-
-__device__ __forceinline__ bool depth_valid(float z) { return z > 0.f && z < INFINITY; }
-
-// The variable summed by each method, before fixed-point scaling:
-//   disparity 1/Z (float32 depth) or 1/raw (uint16 depth; the metric scale is
-//   folded into the quantum), standard Z (float32) or raw (uint16).
-template <int DT, int M>
-__device__ __forceinline__ float fit_variable_of(float zin) {
-    if (base_method(M) == SF_METHOD_DISPARITY) return rcp_approx(zin);
-    return zin;
-}
+struct Codec {
+    float scale;
+    int dmul, dadd;
+};
 
 // Raw stored value: metres for float32, raw units for uint16 (0 = missing).
 template <int DT>
 __device__ __forceinline__ float load_raw(const void* base, size_t idx) {
     if (DT == SF_DEPTH_F32) return __ldg(reinterpret_cast<const float*>(base) + idx);
     return (float)__ldg(reinterpret_cast<const unsigned short*>(base) + idx);
+}
+
+// Disparity input: the integer w = dmul * D + dadd (units of scale), or -1.
+__device__ __forceinline__ int disparity_units(float d_raw, const Codec& cd) {
+    const int D = (int)d_raw;
+    const int w = cd.dmul * D + cd.dadd;
+    return (D != 0 && w > 0) ? w : -1;
+}
+
+// Depth in metres (0 when missing).
+template <int DT>
+__device__ __forceinline__ float load_depth(const void* base, size_t idx, const Codec& cd) {
+    const float raw = load_raw<DT>(base, idx);
+    if (DT == SF_DEPTH_F32) return raw;
+    if (DT == SF_DEPTH_U16) return raw != 0.f ? raw * cd.scale : 0.f;
+    const int w = disparity_units(raw, cd);
+    return w > 0 ? 1.f / (cd.scale * (float)w) : 0.f;
+}
+
+__device__ __forceinline__ bool depth_valid(float z) { return z > 0.f && z < INFINITY; }
+
+// The variable summed by each method, before fixed-point scaling:
+//   disparity 1/Z (float32 depth), 1/raw (uint16 depth; the metric scale is
+//   folded into the quantum) or w (disparity input); standard Z (float32 or
+//   disparity input) or raw (uint16).
+template <int DT, int M>
+__device__ __forceinline__ float fit_variable_of(float zin, const Codec& cd = Codec{1.f, 0, 0}) {
+    if (DT == SF_DEPTH_DISPARITY_U16) {
+        const int w = disparity_units(zin, cd);
+        if (base_method(M) == SF_METHOD_DISPARITY) return (float)w;
+        return w > 0 ? 1.f / (cd.scale * (float)w) : 0.f;
+    }
+    if (base_method(M) == SF_METHOD_DISPARITY) return rcp_approx(zin);
+    return zin;
 }
 
 // round(sc / z) to the nearest integer for sc = 2^e, without the 24-bit limit
@@ -93,6 +114,19 @@ __device__ __forceinline__ int quant_recip(float z, float sc) {
     return (int)hr + (int)rintf((hi - hr) + lo);
 }
 
+// round(K / w) for an integer 0 < w < 2^24 and any K > 0 with K / w < 2^30:
+// y = rcp(w) refined by its exact FMA residual e = 1 - w y, and K y split
+// exactly into p + pe (FMA), so K / w = p + pe + p e to about 2^-44 relative.
+__device__ __forceinline__ int quant_div(float K, int w) {
+    const float wf = (float)w;
+    const float y = rcp_approx(wf);
+    const float e = fmaf(-wf, y, 1.f);
+    const float p = K * y;
+    const float pe = fmaf(K, y, -p);
+    const float hr = rintf(p);
+    return (int)hr + (int)rintf((p - hr) + fmaf(p, e, pe));
+}
+
 // Exponent e such that v * 2^e <= 2^bits for all v <= vmax.
 __device__ __forceinline__ int quant_exponent(unsigned vmax_bits, int bits) {
     const float vmax = __uint_as_float(vmax_bits);
@@ -103,9 +137,17 @@ __device__ __forceinline__ int quant_exponent(unsigned vmax_bits, int bits) {
 }
 
 // Fixed-point value of a valid pixel (>= 0), or -1 for a missing one, from
-// its raw stored value.
+// its raw stored value.  Disparity input needs no reciprocal for the
+// disparity form: its integer w is the fixed-point value itself.
 template <int DT, int M>
-__device__ __forceinline__ int quantize_raw(float zin, float sc) {
+__device__ __forceinline__ int quantize_raw(float zin, float sc, const Codec& cd) {
+    if (DT == SF_DEPTH_DISPARITY_U16) {
+        const int w = disparity_units(zin, cd);
+        if (base_method(M) == SF_METHOD_DISPARITY || w < 0) return w;
+        // Z / quantum = (sc / scale) / w, correctly rounded for the frame's one
+        // K = sc / scale (its own rounding scales every depth alike)
+        return quant_div(sc / cd.scale, w);
+    }
     if (!depth_valid(zin)) return -1;
     if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_STANDARD) return (int)zin;
     if (base_method(M) == SF_METHOD_DISPARITY) return quant_recip(zin, sc);
@@ -113,16 +155,25 @@ __device__ __forceinline__ int quantize_raw(float zin, float sc) {
 }
 
 template <int DT, int M>
-__device__ __forceinline__ int quantize(const void* depth, size_t idx, float sc) {
-    return quantize_raw<DT, M>(load_raw<DT>(depth, idx), sc);
+__device__ __forceinline__ int quantize(const void* depth, size_t idx, float sc, const Codec& cd) {
+    return quantize_raw<DT, M>(load_raw<DT>(depth, idx), sc, cd);
+}
+
+// The quantum is fixed by the input (no range pass) for uint16 depth in the
+// standard form and for disparity input in the disparity form.
+template <int DT, int M>
+__host__ __device__ constexpr bool fixed_quantum() {
+    return (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_STANDARD) ||
+           (DT == SF_DEPTH_DISPARITY_U16 && base_method(M) == SF_METHOD_DISPARITY);
 }
 
 // Metric size of one fixed-point unit.
 template <int DT, int M>
-__device__ __forceinline__ float quantum(unsigned vmax_bits, int bits, float scale) {
-    if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_STANDARD) return scale;
+__device__ __forceinline__ float quantum(unsigned vmax_bits, int bits, const Codec& cd) {
+    if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_STANDARD) return cd.scale;
+    if (DT == SF_DEPTH_DISPARITY_U16 && base_method(M) == SF_METHOD_DISPARITY) return cd.scale;
     const float q = ldexpf(1.f, -quant_exponent(vmax_bits, bits));
-    if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_DISPARITY) return q / scale;
+    if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_DISPARITY) return q / cd.scale;
     return q;
 }
 
@@ -130,7 +181,7 @@ __device__ __forceinline__ float quantum(unsigned vmax_bits, int bits, float sca
 // 1. range
 // ---------------------------------------------------------------------------
 template <int DT, int M>
-__global__ void __launch_bounds__(256) range_kernel(const void* __restrict__ depth, size_t frame_elems, float scale,
+__global__ void __launch_bounds__(256) range_kernel(const void* __restrict__ depth, size_t frame_elems, Codec scale,
                                                     unsigned* __restrict__ vmax_bits) {
     const int f = blockIdx.y;
     const size_t base = (size_t)f * frame_elems;
@@ -147,7 +198,7 @@ __global__ void __launch_bounds__(256) range_kernel(const void* __restrict__ dep
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            if (depth_valid(z[u])) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z[u]));
+            if (depth_valid(z[u])) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z[u], scale));
     }
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     __shared__ float red[8];
@@ -234,8 +285,8 @@ __device__ __forceinline__ void slide2(T& S0, T& S1, T out, T in, int r) {
 // per thread are in flight at once (issue is in order: a load consumed right
 // away would expose its whole latency).
 template <int DT, int M, int CHUNKS>
-__device__ __forceinline__ void load_tile(const void* __restrict__ depth, int W, int r, float sc, int x0, int y0,
-                                          int rows, int IW, int pitch, int* tile) {
+__device__ __forceinline__ void load_tile(const void* __restrict__ depth, int W, int r, float sc, const Codec& cd,
+                                          int x0, int y0, int rows, int IW, int pitch, int* tile) {
     constexpr int kRowsPerBatch = 4;
     constexpr int kWarps = kHThreads / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -257,7 +308,7 @@ __device__ __forceinline__ void load_tile(const void* __restrict__ depth, int W,
 #pragma unroll
             for (int c = 0; c < CHUNKS; ++c) {
                 const int cx = lane + 32 * c;
-                if (ry < rows && cx < IW) tile[ry * pitch + cx] = quantize_raw<DT, M>(raw[k][c], sc);
+                if (ry < rows && cx < IW) tile[ry * pitch + cx] = quantize_raw<DT, M>(raw[k][c], sc, cd);
             }
         }
     }
@@ -269,15 +320,16 @@ __device__ __forceinline__ void load_tile(const void* __restrict__ depth, int W,
 // kHThreads * ((seg + 2r) | 1) ints.
 template <int DT, int M>
 __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W, int H, int r, float sc,
-                                           const Planes& P, size_t pofs, int x0, int y0, int seg, int* tile) {
+                                           const Codec& cd, const Planes& P, size_t pofs, int x0, int y0, int seg,
+                                           int* tile) {
     const int IW = seg + 2 * r;
     const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
     const int rows = min(kHThreads, H - y0);
     // the tile's raw depth, quantised; ceil(IW / 32) column chunks per row
     // (IW <= seg + 30): 2 for seg 32, 3 for 64, 5 for 128
-    if (seg <= 32) load_tile<DT, M, 2>(depth, W, r, sc, x0, y0, rows, IW, pitch, tile);
-    else if (seg <= 64) load_tile<DT, M, 3>(depth, W, r, sc, x0, y0, rows, IW, pitch, tile);
-    else load_tile<DT, M, 5>(depth, W, r, sc, x0, y0, rows, IW, pitch, tile);
+    if (seg <= 32) load_tile<DT, M, 2>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
+    else if (seg <= 64) load_tile<DT, M, 3>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
+    else load_tile<DT, M, 5>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
     __syncthreads();
     if ((int)threadIdx.x < rows) {
         const int y = y0 + threadIdx.x;
@@ -351,16 +403,16 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
 
 template <int DT, int M>
 __global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict__ depth, int W, int H, int r,
-                                                          float scale, const unsigned* __restrict__ vmax_bits,
+                                                          Codec scale, const unsigned* __restrict__ vmax_bits,
                                                           int bits, int raw_z, int Wp, size_t plane_elems,
                                                           void* planes_base, int seg) {
     extern __shared__ int tile[];
     const int f = blockIdx.z;
     const float sc = ldexpf(1.f, quant_exponent(vmax_bits[f], bits));  // 2^e, exact
-    const size_t dbytes = (DT == SF_DEPTH_U16) ? 2 : 4;
+    const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * W * H;
     const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
-    hpass_tile<DT, M>(dframe, W, H, r, sc, P, (size_t)f * plane_elems, blockIdx.x * seg,
+    hpass_tile<DT, M>(dframe, W, H, r, sc, scale, P, (size_t)f * plane_elems, blockIdx.x * seg,
                       blockIdx.y * kHThreads, seg, tile);
 }
 
@@ -511,7 +563,7 @@ using StdState = StdStateT<false>;
 // machine code, so their results agree bit for bit (inlined copies may be
 // contracted into FMAs differently); one call covers a whole band.
 template <int DT, int M, bool U4 = false>
-__device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, float scale, float q,
+__device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, Codec scale, float q,
                                              const Planes P, size_t pofs, int x, int y0, int band,
                                              const float* __restrict__ txt, const float* __restrict__ tyt, float a,
                                              float b, int min_valid, int require_center, float* __restrict__ normals,
@@ -580,7 +632,7 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
 
 template <int DT, int M, bool U4 = false>
 __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
-                                                          float scale, const unsigned* __restrict__ vmax_bits,
+                                                          Codec scale, const unsigned* __restrict__ vmax_bits,
                                                           int bits, int raw_z, int Wp, size_t plane_elems,
                                                           void* __restrict__ planes_base, Calib cal,
                                                           int min_valid, int require_center, int band,
@@ -592,7 +644,7 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* 
     const int x = blockIdx.x * kVThreads + threadIdx.x;
     if (x >= W) return;
     const size_t fe = (size_t)W * H;
-    const size_t dbytes = (DT == SF_DEPTH_U16) ? 2 : 4;
+    const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * fe;
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);  // metric value of one fixed-point unit
     const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
@@ -654,7 +706,7 @@ __global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc*
                                                                 const int3* __restrict__ items, int n_items,
                                                                 unsigned* __restrict__ counter,
                                                                 const unsigned* __restrict__ vmax_bits,
-                                                                void* planes_base, size_t stride, float scale) {
+                                                                void* planes_base, size_t stride, Codec scale) {
     extern __shared__ int tile[];
     __shared__ int slot;
     const Planes P(planes_base, stride);
@@ -664,7 +716,7 @@ __global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc*
         const int3 w = items[it];
         const FrameDesc& d = descs[w.x];
         const float sc = ldexpf(1.f, quant_exponent(vmax_bits[w.x], d.bits));
-        hpass_tile<DT, M>(d.depth, d.W, d.H, d.r, sc, P, d.pofs, w.y, w.z, d.seg, tile);
+        hpass_tile<DT, M>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, d.seg, tile);
     }
 }
 
@@ -673,7 +725,7 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_batch_kernel(const 
                                                                 const int3* __restrict__ items, int n_items,
                                                                 unsigned* __restrict__ counter,
                                                                 const unsigned* __restrict__ vmax_bits,
-                                                                void* planes_base, size_t stride, float scale,
+                                                                void* planes_base, size_t stride, Codec scale,
                                                                 int min_valid, int require_center) {
     __shared__ int slot;
     const Planes P(planes_base, stride);
@@ -700,7 +752,7 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_batch_kernel(const 
 // the solve; only the fixed-point quantisation of the depth remains.
 // ---------------------------------------------------------------------------
 template <int DT, int M, bool U4 = false>
-__global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, float scale,
+__global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, Codec scale,
                                                       const unsigned* __restrict__ vmax_bits, int bits, int Wp,
                                                       size_t plane_elems, int nframes, void* __restrict__ planes_base,
                                                       Calib cal, const double* __restrict__ rays,
@@ -766,7 +818,7 @@ __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, float
 // ---------------------------------------------------------------------------
 template <int DT, int M>
 __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restrict__ depth, int W, int H, int r,
-                                                             float scale, const unsigned* __restrict__ vmax_bits,
+                                                             Codec scale, const unsigned* __restrict__ vmax_bits,
                                                              int bits, int Wp, size_t plane_elems,
                                                              void* __restrict__ planes_base, Calib cal, int min_valid,
                                                              int require_center, int band,
@@ -879,7 +931,7 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
 constexpr int kGTile = 32;
 
 template <int DT, int M>
-__global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ depth, int W, int H, int r, float scale,
+__global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ depth, int W, int H, int r, Codec scale,
                                                      Calib cal, const float* __restrict__ adj,
                                                      float* __restrict__ g_depth) {
     extern __shared__ float sadj[];
@@ -961,7 +1013,7 @@ __device__ __forceinline__ V warp_sum(V v) {
 }
 
 template <int DT, int M>
-__global__ void __launch_bounds__(256) quad_level_kernel(const void* __restrict__ depth, int W, int H, float scale,
+__global__ void __launch_bounds__(256) quad_level_kernel(const void* __restrict__ depth, int W, int H, Codec scale,
                                                          const unsigned* __restrict__ vmax_bits, int bits,
                                                          const double* __restrict__ rays, const QuadRect* __restrict__ in,
                                                          const int* __restrict__ in_count, int level, int max_level,
@@ -976,7 +1028,7 @@ __global__ void __launch_bounds__(256) quad_level_kernel(const void* __restrict_
     if (idx >= *in_count) return;
     const QuadRect q = in[idx];
     const size_t fe = (size_t)W * H;
-    const size_t dbytes = (DT == SF_DEPTH_U16) ? 2 : 4;
+    const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)q.frame * fe;
     const float sc = ldexpf(1.f, quant_exponent(vmax_bits[q.frame], bits));
     // exact sums: mask moments in int32 (< 2^31 for sides <= 64), values in int64
@@ -987,7 +1039,7 @@ __global__ void __launch_bounds__(256) quad_level_kernel(const void* __restrict_
     for (int p = lane; p < area; p += 32) {
         const int ri = p / q.w, rj = p - ri * q.w;
         const int i = q.y0 + ri - yc, j = q.x0 + rj - xc;
-        const int v = quantize_raw<DT, M>(load_raw<DT>(dframe, (size_t)(q.y0 + ri) * W + q.x0 + rj), sc);
+        const int v = quantize_raw<DT, M>(load_raw<DT>(dframe, (size_t)(q.y0 + ri) * W + q.x0 + rj), sc, scale);
         if (v < 0) continue;
         n += 1; Sj += j; Si += i; Sjj += j * j; Sji += j * i; Sii += i * i;
         const int64_t vv = (int64_t)v * v;

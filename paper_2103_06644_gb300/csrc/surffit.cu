@@ -78,6 +78,9 @@ struct sf_ctx {
     int hseg = sf::kHSeg; // horizontal tile width (32, 64 or 128)
     int vband = 0;        // vertical band height (0: chosen from the grid size)
     float depth_scale = 1e-3f;
+    // SF_DEPTH_DISPARITY_U16: 1/Z = disp_q * (disp_mul * D + disp_add)
+    float disp_q = 1.f / 128.f;
+    int disp_mul = 128, disp_add = 0;
     int min_valid = 3;
     int require_center = 1;
     int device = 0;
@@ -117,6 +120,13 @@ struct sf_ctx {
 };
 
 namespace {
+sf::Codec codec_of(const sf_ctx* c) {
+    if (c->depth_type == SF_DEPTH_DISPARITY_U16) return sf::Codec{c->disp_q, c->disp_mul, c->disp_add};
+    return sf::Codec{c->depth_scale, 0, 0};
+}
+
+size_t depth_bytes(int depth_type) { return depth_type == SF_DEPTH_F32 ? 4 : 2; }
+
 cudaEvent_t take_event(sf_ctx* c) {
     if (!c->event_pool.empty()) {
         cudaEvent_t e = c->event_pool.back();
@@ -176,14 +186,14 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
                              int32_t* counts, cudaStream_t st) {
     const size_t fe = (size_t)c->W * c->H;
     constexpr int B = sf::base_method(M);  // range and horizontal pass depend on the moments only
-    const int raw_z = (DT == SF_DEPTH_U16 && B == SF_METHOD_STANDARD) ? 1 : 0;
+    const int raw_z = sf::fixed_quantum<DT, B>() ? 1 : 0;
     const int bits = quant_bits(M, c->k);
     SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
     if (!raw_z) {
         StageTimer t(c, 0, st);
         int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
         blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
-        sf::range_kernel<DT, B><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, c->depth_scale, c->vmax);
+        sf::range_kernel<DT, B><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
     }
     {
         StageTimer t(c, 1, st);
@@ -191,7 +201,7 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
         dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
         const int IW = seg + 2 * c->r;
         const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
-        sf::hpass_kernel<DT, B><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
+        sf::hpass_kernel<DT, B><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
                                                                   bits, raw_z, c->Wp, c->plane_elems, c->planes, seg);
     }
     {
@@ -202,14 +212,14 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
         const bool fb = c->precision_mode > 0 && c->flags;
         if (fb) SF_CUDA(cudaMemsetAsync(c->flag_count, 0, sizeof(unsigned), st));
         const float tau = c->precision_mode == 2 ? INFINITY : c->tau;
-        sf::vpass_kernel<DT, M, U4><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
+        sf::vpass_kernel<DT, M, U4><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
                                                                bits, raw_z, c->Wp, c->plane_elems, c->planes, cal,
                                                                c->min_valid, c->require_center, band, normals,
                                                                offsets, curv, counts, tau, fb ? c->flags : nullptr,
                                                                c->flag_count);
         if (fb) {
             StageTimer t2(c, 3, st);
-            sf::resolve_kernel<DT, M, U4><<<152 * 8, 128, 0, st>>>(c->W, c->H, c->r, c->depth_scale, c->vmax, bits, c->Wp,
+            sf::resolve_kernel<DT, M, U4><<<152 * 8, 128, 0, st>>>(c->W, c->H, c->r, codec_of(c), c->vmax, bits, c->Wp,
                                                               c->plane_elems, nfr, c->planes, cal, c->rays64,
                                                               c->flags, c->flag_count, normals, offsets, curv);
         }
@@ -229,13 +239,13 @@ static sf_status launch_quadtree(sf_ctx* c, int nfr, int frame_base, const void*
                                  sf_quad_node* nodes, int capacity, int32_t* n_nodes, size_t roots, cudaStream_t st) {
     constexpr int B = sf::base_method(M);
     const size_t fe = (size_t)c->W * c->H;
-    const int raw_z = (DT == SF_DEPTH_U16 && B == SF_METHOD_STANDARD) ? 1 : 0;
+    const int raw_z = sf::fixed_quantum<DT, B>() ? 1 : 0;
     const int bits = quad_bits(M);
     SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
     if (!raw_z) {
         int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
         blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
-        sf::range_kernel<DT, B><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, c->depth_scale, c->vmax);
+        sf::range_kernel<DT, B><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
     }
     SF_CUDA(cudaMemsetAsync(c->quad_cnt, 0, sizeof(int) * 8, st));
     sf::quad_roots_kernel<<<(int)std::min<size_t>((roots + 255) / 256, 1024), 256, 0, st>>>(c->W, c->H, p->tile, nfr,
@@ -245,7 +255,7 @@ static sf_status launch_quadtree(sf_ctx* c, int nfr, int frame_base, const void*
         const size_t n = std::min(level_max, c->quad_cap);
         const int blocks = (int)((n + 7) / 8);
         sf::quad_level_kernel<DT, M><<<blocks, 256, 0, st>>>(
-            depth, c->W, c->H, c->depth_scale, c->vmax, bits, c->rays64, c->quad_q[l & 1], c->quad_cnt + l, l,
+            depth, c->W, c->H, codec_of(c), c->vmax, bits, c->rays64, c->quad_q[l & 1], c->quad_cnt + l, l,
             p->max_level, (double)p->tau, c->min_valid, p->min_valid_permille, c->quad_q[(l + 1) & 1],
             c->quad_cnt + l + 1, (int)c->quad_cap, nodes, n_nodes, capacity, frame_base);
         level_max *= 4;
@@ -298,27 +308,27 @@ template <int DT, int M>
 static sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const float* gn, const float* gd,
                                  const float* gk, float* g_depth, cudaStream_t st) {
     const size_t fe = (size_t)c->W * c->H;
-    const int raw_z = (DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD) ? 1 : 0;
+    const int raw_z = sf::fixed_quantum<DT, M>() ? 1 : 0;
     const int bits = quant_bits(M, c->k);
     SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
     if (!raw_z) {
         int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
         blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
-        sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, c->depth_scale, c->vmax);
+        sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
     }
     {
         const int seg = c->hseg;
         dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
         const int IW = seg + 2 * c->r;
         const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
-        sf::hpass_kernel<DT, M><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
+        sf::hpass_kernel<DT, M><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
                                                                   bits, raw_z, c->Wp, c->plane_elems, c->planes, seg);
     }
     sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
     {
         const int band = vertical_band(c, nfr);
         dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
-        sf::vadjoint_kernel<DT, M><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, c->depth_scale, c->vmax,
+        sf::vadjoint_kernel<DT, M><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
                                                                   bits, c->Wp, c->plane_elems, c->planes, cal,
                                                                   c->min_valid, c->require_center, band, gn, gd, gk,
                                                                   c->adj);
@@ -328,7 +338,7 @@ static sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const fl
         const int T = sf::kGTile + 2 * c->r;
         const size_t smem = sizeof(float) * NC * (size_t)T * T;
         dim3 grid((c->W + sf::kGTile - 1) / sf::kGTile, (c->H + sf::kGTile - 1) / sf::kGTile, nfr);
-        sf::gather_kernel<DT, M><<<grid, dim3(32, 8), smem, st>>>(depth, c->W, c->H, c->r, c->depth_scale, cal,
+        sf::gather_kernel<DT, M><<<grid, dim3(32, 8), smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), cal,
                                                                    c->adj, g_depth);
     }
     cudaError_t e = cudaGetLastError();
@@ -444,7 +454,7 @@ sf_status sf_set_params(sf_ctx* c, int method, int depth_type, float depth_scale
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (method < SF_METHOD_DISPARITY || method > SF_METHOD_EXPLICIT_STANDARD)
         return fail(SF_ERR_INVALID_ARG, "unknown method %d", method);
-    if (depth_type != SF_DEPTH_F32 && depth_type != SF_DEPTH_U16)
+    if (depth_type != SF_DEPTH_F32 && depth_type != SF_DEPTH_U16 && depth_type != SF_DEPTH_DISPARITY_U16)
         return fail(SF_ERR_INVALID_ARG, "unknown depth type %d", depth_type);
     if (depth_type == SF_DEPTH_U16 && !(depth_scale > 0.f && std::isfinite(depth_scale)))
         return fail(SF_ERR_INVALID_ARG, "depth_scale must be positive and finite");
@@ -467,7 +477,7 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
         return fail(SF_ERR_UNSUPPORTED, "the |(a,b,c,d)| = 1 constraint applies to the implicit fits");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t fe = (size_t)c->W * c->H;
-    const size_t dbytes = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
+    const size_t dbytes = depth_bytes(c->depth_type);
     int per = std::min(c->max_frames_per_pass, 64);
     sf_status s = ensure_planes(c, std::min(per, n_frames));
     if (s != SF_OK) return s;
@@ -489,8 +499,9 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
         float* op = offsets + fe * f0;
         float* cp = curvature + fe * f0;
         int32_t* kp = counts ? counts + fe * f0 : nullptr;
-        s = c->depth_type == SF_DEPTH_F32 ? launch_pass_for<SF_DEPTH_F32>(c, nfr, dp, np_, op, cp, kp, st)
-                                          : launch_pass_for<SF_DEPTH_U16>(c, nfr, dp, np_, op, cp, kp, st);
+        s = c->depth_type == SF_DEPTH_F32   ? launch_pass_for<SF_DEPTH_F32>(c, nfr, dp, np_, op, cp, kp, st)
+            : c->depth_type == SF_DEPTH_U16 ? launch_pass_for<SF_DEPTH_U16>(c, nfr, dp, np_, op, cp, kp, st)
+                                            : launch_pass_for<SF_DEPTH_DISPARITY_U16>(c, nfr, dp, np_, op, cp, kp, st);
         if (s != SF_OK) return s;
     }
     return SF_OK;
@@ -508,7 +519,7 @@ sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals
     if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
     cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
     const size_t fe = (size_t)c->W * c->H;
-    const size_t dpx = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
+    const size_t dpx = depth_bytes(c->depth_type);
     // Frames go through in chunks on two streams: the copy-out of chunk i-1
     // overlaps the copy-in and fit of chunk i.  Copies read and write the
     // caller's (pageable) buffers directly; the fits share the context's
@@ -623,14 +634,16 @@ sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_
         if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "quadtree counters failed");
     }
     const size_t fe = (size_t)c->W * c->H;
-    const size_t dbytes = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
+    const size_t dbytes = depth_bytes(c->depth_type);
     for (int f0 = 0; f0 < n_frames; f0 += per) {
         const int nfr = std::min(per, n_frames - f0);
         const void* dp = static_cast<const char*>(depth) + dbytes * fe * f0;
-        sf_status s = c->depth_type == SF_DEPTH_F32
-                          ? launch_quadtree_for<SF_DEPTH_F32>(c, nfr, f0, dp, p, nodes, capacity, n_nodes,
-                                                              tiles * nfr, st)
-                          : launch_quadtree_for<SF_DEPTH_U16>(c, nfr, f0, dp, p, nodes, capacity, n_nodes,
+        sf_status s =
+            c->depth_type == SF_DEPTH_F32
+                ? launch_quadtree_for<SF_DEPTH_F32>(c, nfr, f0, dp, p, nodes, capacity, n_nodes, tiles * nfr, st)
+            : c->depth_type == SF_DEPTH_U16
+                ? launch_quadtree_for<SF_DEPTH_U16>(c, nfr, f0, dp, p, nodes, capacity, n_nodes, tiles * nfr, st)
+                : launch_quadtree_for<SF_DEPTH_DISPARITY_U16>(c, nfr, f0, dp, p, nodes, capacity, n_nodes,
                                                               tiles * nfr, st);
         if (s != SF_OK) return s;
     }
@@ -663,6 +676,18 @@ sf_status sf_set_constraint(sf_ctx* c, int constraint) {
     return SF_OK;
 }
 
+sf_status sf_set_disparity_model(sf_ctx* c, double alpha, double beta) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    if (!(alpha != 0.0) || !std::isfinite(alpha) || !std::isfinite(beta))
+        return fail(SF_ERR_INVALID_ARG, "alpha must be finite and nonzero, beta finite");
+    const double k = 128.0 * beta / std::fabs(alpha);
+    if (!(std::fabs(k) <= 8388608.0)) return fail(SF_ERR_INVALID_ARG, "|128 beta / alpha| must be <= 2^23");
+    c->disp_q = (float)(std::fabs(alpha) / 128.0);
+    c->disp_mul = alpha > 0.0 ? 128 : -128;
+    c->disp_add = (int)std::lround(k);
+    return SF_OK;
+}
+
 sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const float* g_normals, const float* g_offsets,
                           const float* g_curvature, float* g_depth, void* stream) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
@@ -674,9 +699,11 @@ sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const floa
         return fail(SF_ERR_UNSUPPORTED, "the backward covers the implicit fits only");
     if (c->constraint != SF_CONSTRAINT_UNIT3)
         return fail(SF_ERR_UNSUPPORTED, "the backward covers the |(a,b,c)| = 1 constraint only");
+    if (c->depth_type == SF_DEPTH_DISPARITY_U16)
+        return fail(SF_ERR_UNSUPPORTED, "the backward takes depth input (f32 or u16)");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t fe = (size_t)c->W * c->H;
-    const size_t dbytes = c->depth_type == SF_DEPTH_U16 ? 2 : 4;
+    const size_t dbytes = depth_bytes(c->depth_type);
     const int per = std::min(c->max_frames_per_pass, 64);
     const int first = std::min(per, n_frames);
     sf_status s = ensure_planes(c, first);
@@ -798,10 +825,10 @@ sf_status batch_enqueue_t(sf_batch* b, cudaStream_t st) {
     if (!(DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD))
         sf::range_batch_kernel<DT, M><<<dim3(16, b->n), 256, 0, st>>>(b->d_desc, b->d_vmax);
     sf::hpass_batch_kernel<DT, M><<<b->grid_h, sf::kHThreads, b->hsmem, st>>>(
-        b->d_desc, b->d_hitems, b->n_h, b->d_counters, b->d_vmax, b->d_planes, b->stride, b->depth_scale);
+        b->d_desc, b->d_hitems, b->n_h, b->d_counters, b->d_vmax, b->d_planes, b->stride, sf::Codec{b->depth_scale, 0, 0});
     sf::vpass_batch_kernel<DT, M><<<b->grid_v, sf::kVThreads, 0, st>>>(b->d_desc, b->d_vitems, b->n_v,
                                                                         b->d_counters + 1, b->d_vmax, b->d_planes,
-                                                                        b->stride, b->depth_scale, b->min_valid,
+                                                                        b->stride, sf::Codec{b->depth_scale, 0, 0}, b->min_valid,
                                                                         b->require_center);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
@@ -854,6 +881,8 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
     if (n_frames > 65535) return fail(SF_ERR_INVALID_ARG, "at most 65535 frames per batch");
     if (method != SF_METHOD_DISPARITY && method != SF_METHOD_STANDARD)
         return fail(SF_ERR_UNSUPPORTED, "batches support the disparity and standard implicit fits");
+    if (depth_type == SF_DEPTH_DISPARITY_U16)
+        return fail(SF_ERR_UNSUPPORTED, "disparity input goes through a context (sf_fit_ex, sf_quadtree)");
     if (depth_type != SF_DEPTH_F32 && depth_type != SF_DEPTH_U16)
         return fail(SF_ERR_INVALID_ARG, "unknown depth type %d", depth_type);
     if (depth_type == SF_DEPTH_U16 && !(depth_scale > 0.f && std::isfinite(depth_scale)))
@@ -1076,6 +1105,8 @@ extern "C" sf_status sf_fit_static(const sf_intrinsics* K, int W, int H, int win
         return fail(SF_ERR_INVALID_ARG, "intrinsics must be finite with nonzero focal lengths");
     if (method != SF_METHOD_DISPARITY && method != SF_METHOD_STANDARD)
         return fail(SF_ERR_UNSUPPORTED, "sf_fit_static supports the disparity and standard implicit fits");
+    if (depth_type == SF_DEPTH_DISPARITY_U16)
+        return fail(SF_ERR_UNSUPPORTED, "disparity input goes through a context (sf_fit_ex, sf_quadtree)");
     if (depth_type != SF_DEPTH_F32 && depth_type != SF_DEPTH_U16)
         return fail(SF_ERR_INVALID_ARG, "unknown depth type %d", depth_type);
     if (depth_type == SF_DEPTH_U16 && !(depth_scale > 0.f && std::isfinite(depth_scale)))

@@ -322,3 +322,27 @@ def two_plane_frame(intr: Intrinsics, W: int, H: int, split_x: int, n_left, d_le
     right = plane_depth(Plane(np.asarray(n_right, float), float(d_right)), intr, W, H)
     Z = np.where(np.arange(W)[None, :] < split_x, left, right)
     return Z
+
+
+# Raw disparity sensors (1/Z = alpha D + beta).  Stereo: D in 1/8 px of a pair
+# of baseline 0.075 m, alpha = 1 / (8 f B), beta = 0.  A structured-light
+# sensor of the Kinect class reports an 11-bit code with a negative alpha.
+KINECT_RAW_ALPHA, KINECT_RAW_BETA = -0.0030711, 3.3309
+
+
+def disparity_frame(seed: int, intr: Intrinsics, W: int, H: int, alpha: float, beta: float,
+                    planes_lo: int = 4, planes_hi: int = 8, z_lo: float = 0.5, z_hi: float = 6.0,
+                    noise_coef: float = KINECT_SIGMA_COEF, miss_lo: float = 0.02,
+                    miss_hi: float = 0.08, d_max: int = 65535) -> np.ndarray:
+    """Voronoi planes + Eq. 2 noise + blob holes as a raw disparity image: D = round((1/Z - beta) / alpha),
+    uint16, 0 where missing or outside [1, d_max]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = int(rng.integers(planes_lo, planes_hi + 1))
+    Z, _, _ = voronoi_planes(rng, intr, W, H, k, z_lo, z_hi)
+    Z = add_depth_noise(rng, Z, noise_coef)
+    Z = drop_blobs(rng, Z, rng.uniform(miss_lo, miss_hi))
+    ok = np.isfinite(Z) & (Z > 0)
+    D = np.zeros(Z.shape)
+    D[ok] = np.round((1.0 / Z[ok] - beta) / alpha)
+    D[(D < 1) | (D > d_max)] = 0
+    return D.astype(np.uint16)

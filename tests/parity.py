@@ -3,10 +3,14 @@ import numpy as np
 
 # Tolerances for the floating-point outputs: normal angle 1e-3 rad; offset
 # 1e-4 relative, measured against the distance |mu| of the window's (weighted)
-# centroid from the camera.  Since d = -n . mu, |d| <= |mu| and an error dn in
+# centroid from the camera, beyond the part |dn| |mu| that the normal's own
+# error dn carries into d = -n . mu.  Since d = -n . mu, |d| <= |mu| and an error dn in
 # the normal moves d by up to |dn| |mu|: for windows seen edge-on (d -> 0) a
 # relative error in d itself is unbounded for any finite-precision normal,
 # while |dd| / |mu| stays well-defined; for head-on windows the two coincide.
+# Where the fitted plane passes the camera centre closer than the offset
+# tolerance (|d| <= 1e-4 |mu|) the orientation rule (d >= 0) has nothing to
+# decide at that tolerance, so normals and offsets are compared up to sign.
 # They apply to windows that are not near-degenerate: the eigenvector of a
 # 3x3 problem moves by |dR| / (lambda1 - lambda0) under a perturbation dR, so
 # where the eigen-gap gamma = (lambda1 - lambda0) / lambda2 is tiny the normal
@@ -59,10 +63,19 @@ def compare(gpu, ref, *, angle_tol=ANGLE_TOL, offset_tol=OFFSET_TOL, gap_min=GAP
     # lambda1 at FP64 rounding level: rank <= 1 (collinear points), degenerate
     gap = np.where(np.abs(lam[..., 1]) <= 1e-9 * np.abs(l2), 0.0, gap)
     good = ok & (gap >= gap_min)
-    ang = angle(n[good], ref["normals"][good])
     mo = ref["moments"]
-    mu = np.linalg.norm(mo[..., 6:9] / mo[..., 9:10], axis=-1)
-    rel = np.abs(d[good].astype(np.float64) - ref["offsets"][good]) / mu[good]
+    mu = np.linalg.norm(mo[..., 6:9] / np.where(ok[..., None], mo[..., 9:10], 1.0), axis=-1)
+    # a plane through the camera centre to within the offset tolerance has no
+    # orientation at that tolerance (d ~ 0 decides it): compare up to sign
+    sign_free = np.abs(np.where(ok, ref["offsets"], 1.0)) <= offset_tol * np.where(ok, mu, 1.0)
+    ang = angle(n[good], ref["normals"][good])
+    flipped = angle(-n[good], ref["normals"][good])
+    ang = np.where(sign_free[good], np.minimum(ang, flipped), ang)
+    err_d = np.abs(np.where(sign_free[good], np.abs(d[good]), d[good]).astype(np.float64) -
+                   np.where(sign_free[good], np.abs(ref["offsets"][good]), ref["offsets"][good])) / mu[good]
+    # d = -n . mu: a normal off by ang moves d by up to ang |mu|; the offset test
+    # checks the rest (the offset's own error), bounded by offset_tol
+    rel = np.maximum(err_d - ang, 0.0)
     cerr = np.abs(c[good].astype(np.float64) - ref["curvature"][good])
     stats.update(good=int(good.sum()), max_angle=float(ang.max(initial=0)), max_offset_rel=float(rel.max(initial=0)),
                  max_curv=float(cerr.max(initial=0)), degenerate=int((ok & ~good).sum()))
