@@ -126,7 +126,10 @@ sf_status sf_set_params(sf_ctx* ctx, int method, int depth_type, float depth_sca
  * is kept to 1/128 of a disparity unit, alpha exactly.  A pixel is missing
  * when D == 0 or its 1/Z <= 0.
  * Errors: SF_ERR_INVALID_ARG unless alpha is finite and nonzero and
- * |128 beta / alpha| <= 2^23.  Default: alpha = 1, beta = 0.
+ * |128 beta / alpha| <= 2^23; a later disparity-form fit rejects a model
+ * whose largest value 128 * 65535 + |round(128 beta / alpha)| times
+ * max(k, r (r + 1)) (k the window, r = (k - 1)/2) reaches 2^31.
+ * Default: alpha = 1, beta = 0.
  */
 sf_status sf_set_disparity_model(sf_ctx* ctx, double alpha, double beta);
 
@@ -304,7 +307,7 @@ sf_status sf_profile_read(sf_ctx* ctx, int n_stages, double* ms, int* launches);
  *   method                   SF_METHOD_DISPARITY or SF_METHOD_STANDARD
  *   depth_type, depth_scale, min_valid, require_center_valid   as for sf_set_params
  *   depth, normals, offsets, curvature, stream                 as for sf_fit
- * Limits and errors: the frame's scratch (about 28 B per pixel for the
+ * Limits and errors: the frame's scratch (about 20 B per pixel for the
  * disparity form, 44 B for the standard form, plus the ray tables) must fit
  * in SF_STATIC_SCRATCH_BYTES, e.g. 1280x720 disparity or 640x480 standard;
  * larger frames are rejected with SF_ERR_INVALID_ARG and a message, before

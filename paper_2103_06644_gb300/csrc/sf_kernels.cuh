@@ -234,14 +234,21 @@ __device__ __forceinline__ size_t plane_index(size_t pofs, int x, int y, int H) 
     return pofs + (size_t)(x >> 3) * ((size_t)H << 3) + ((size_t)y << 3) + (size_t)(x & 7);
 }
 
+// n32 int32 planes (the disparity form: mask, sum w, sum w j -- every row sum
+// of these fits 31 bits by the choice of fixed-point bits) then the int64
+// planes (the disparity form: sum w^2; the standard form: 1 int32 + 5 int64).
+template <int M>
+__host__ __device__ constexpr int planes32() { return base_method(M) == SF_METHOD_DISPARITY ? 3 : 1; }
+
 struct Planes {
-    int32_t* p32;       // the int32 plane
+    int32_t* p32;       // first int32 plane (the packed mask); plane c is p32 + c * stride
     int64_t* p64;       // first int64 plane; plane c is p64 + c * stride
     size_t stride;
-    __host__ __device__ Planes(void* base, size_t stride_)
+    __host__ __device__ Planes(void* base, size_t stride_, int n32)
         : p32(reinterpret_cast<int32_t*>(base)),
-          p64(reinterpret_cast<int64_t*>(reinterpret_cast<int32_t*>(base) + stride_)),
+          p64(reinterpret_cast<int64_t*>(reinterpret_cast<int32_t*>(base) + (size_t)n32 * stride_)),
           stride(stride_) {}
+    __device__ __forceinline__ int32_t* c32(int c) const { return p32 + (size_t)c * stride; }
     __device__ __forceinline__ int64_t* c64(int c) const { return p64 + (size_t)c * stride; }
 };
 
@@ -371,30 +378,46 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
                 }
             }
             const size_t o = plane_index(pofs, xb, y, H);  // xb % 4 == 0: 4 entries in one group
-            if (xb + 4 <= xend) {
+            if (base_method(M) == SF_METHOD_DISPARITY) {
+                // row sums of w and w j fit 31 bits (the fixed-point bits are chosen so): int32
+                if (xb + 4 <= xend) {
+                    *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
+                    *reinterpret_cast<int4*>(P.c32(1) + o) =
+                        make_int4((int)c0v[0], (int)c0v[1], (int)c0v[2], (int)c0v[3]);
+                    *reinterpret_cast<int4*>(P.c32(2) + o) =
+                        make_int4((int)c1v[0], (int)c1v[1], (int)c1v[2], (int)c1v[3]);
+                    int64_t* q0 = P.c64(0) + o;
+                    *reinterpret_cast<longlong2*>(q0) = make_longlong2(c2v[0], c2v[1]);
+                    *reinterpret_cast<longlong2*>(q0 + 2) = make_longlong2(c2v[2], c2v[3]);
+                } else {
+                    for (int u = 0; u < 4 && xb + u < xend; ++u) {
+                        P.p32[o + u] = hmv[u];
+                        P.c32(1)[o + u] = (int)c0v[u]; P.c32(2)[o + u] = (int)c1v[u];
+                        P.c64(0)[o + u] = c2v[u];
+                    }
+                }
+            } else if (xb + 4 <= xend) {
                 *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
                 int64_t* c0 = P.c64(0) + o;
                 int64_t* c1 = P.c64(1) + o;
                 int64_t* c2 = P.c64(2) + o;
+                int64_t* c3 = P.c64(3) + o;
+                int64_t* c4 = P.c64(4) + o;
                 *reinterpret_cast<longlong2*>(c0) = make_longlong2(c0v[0], c0v[1]);
                 *reinterpret_cast<longlong2*>(c0 + 2) = make_longlong2(c0v[2], c0v[3]);
                 *reinterpret_cast<longlong2*>(c1) = make_longlong2(c1v[0], c1v[1]);
                 *reinterpret_cast<longlong2*>(c1 + 2) = make_longlong2(c1v[2], c1v[3]);
                 *reinterpret_cast<longlong2*>(c2) = make_longlong2(c2v[0], c2v[1]);
                 *reinterpret_cast<longlong2*>(c2 + 2) = make_longlong2(c2v[2], c2v[3]);
-                if (base_method(M) == SF_METHOD_STANDARD) {
-                    int64_t* c3 = P.c64(3) + o;
-                    int64_t* c4 = P.c64(4) + o;
-                    *reinterpret_cast<longlong2*>(c3) = make_longlong2(c3v[0], c3v[1]);
-                    *reinterpret_cast<longlong2*>(c3 + 2) = make_longlong2(c3v[2], c3v[3]);
-                    *reinterpret_cast<longlong2*>(c4) = make_longlong2(c4v[0], c4v[1]);
-                    *reinterpret_cast<longlong2*>(c4 + 2) = make_longlong2(c4v[2], c4v[3]);
-                }
+                *reinterpret_cast<longlong2*>(c3) = make_longlong2(c3v[0], c3v[1]);
+                *reinterpret_cast<longlong2*>(c3 + 2) = make_longlong2(c3v[2], c3v[3]);
+                *reinterpret_cast<longlong2*>(c4) = make_longlong2(c4v[0], c4v[1]);
+                *reinterpret_cast<longlong2*>(c4 + 2) = make_longlong2(c4v[2], c4v[3]);
             } else {
                 for (int u = 0; u < 4 && xb + u < xend; ++u) {
                     P.p32[o + u] = hmv[u];
                     P.c64(0)[o + u] = c0v[u]; P.c64(1)[o + u] = c1v[u]; P.c64(2)[o + u] = c2v[u];
-                    if (base_method(M) == SF_METHOD_STANDARD) { P.c64(3)[o + u] = c3v[u]; P.c64(4)[o + u] = c4v[u]; }
+                    P.c64(3)[o + u] = c3v[u]; P.c64(4)[o + u] = c4v[u];
                 }
             }
         }
@@ -411,7 +434,7 @@ __global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict
     const float sc = ldexpf(1.f, quant_exponent(vmax_bits[f], bits));  // 2^e, exact
     const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * W * H;
-    const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
+    const Planes P(planes_base, (size_t)gridDim.z * plane_elems, planes32<M>());
     hpass_tile<DT, M>(dframe, W, H, r, sc, scale, P, (size_t)f * plane_elems, blockIdx.x * seg,
                       blockIdx.y * kHThreads, seg, tile);
 }
@@ -427,11 +450,11 @@ struct Calib {
 
 // Vertical running sums of the disparity form's moments for one column.
 struct DispState {
-    const int32_t* hm; const int64_t* g0; const int64_t* g1; const int64_t* q0;
+    const int32_t* hm; const int32_t* g0; const int32_t* g1; const int64_t* q0;
     // mask moments: exact small integers, kept in float32 (all < 2^24)
     float n = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;
     int64_t Sw = 0, Swj = 0, Swi = 0, Sww = 0;
-    __device__ DispState(const Planes& P) : hm(P.p32), g0(P.c64(0)), g1(P.c64(1)), q0(P.c64(2)) {}
+    __device__ DispState(const Planes& P) : hm(P.p32), g0(P.c32(1)), g1(P.c32(2)), q0(P.c64(0)) {}
     // window of output row y0 from rows y0 - r .. y0 + r
     __device__ __forceinline__ void init(size_t pb, int rs, int H, int y0, int r) {
         for (int yy = y0 - r; yy <= y0 + r; ++yy) {
@@ -450,12 +473,13 @@ struct DispState {
     // (leaving row y - r, entering row y + r + 1; zero outside the image).
     // fetch() only issues the loads, so a caller can overlap them with the
     // solve of row y and apply() them afterwards.
-    int32_t pm_o = 0, pm_i = 0;
-    int64_t pwo = 0, pwjo = 0, pwwo = 0, pwi = 0, pwji = 0, pwwi = 0;
+    int32_t pm_o = 0, pm_i = 0, pwo = 0, pwjo = 0, pwi = 0, pwji = 0;
+    int64_t pwwo = 0, pwwi = 0;
     __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) {
         const int yo = y - r, yi = y + r + 1;
         pm_o = pm_i = 0;
-        pwo = pwjo = pwwo = pwi = pwji = pwwi = 0;
+        pwo = pwjo = pwi = pwji = 0;
+        pwwo = pwwi = 0;
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * rs;
             pm_o = __ldg(hm + o); pwo = __ldg(g0 + o); pwjo = __ldg(g1 + o); pwwo = __ldg(q0 + o);
@@ -473,8 +497,8 @@ struct DispState {
         slide3(n, Si, Sii, (float)o0, (float)i0, r);
         slide2(Sj, Sji, (float)o1, (float)i1, r);
         Sjj += (float)(i2 - o2);
-        slide2(Sw, Swi, pwo, pwi, r);
-        Swj += pwji - pwjo;
+        slide2(Sw, Swi, (int64_t)pwo, (int64_t)pwi, r);
+        Swj += (int64_t)pwji - pwjo;
         Sww += pwwi - pwwo;
     }
     // slide from output row y to y + 1
@@ -647,7 +671,7 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* 
     const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * fe;
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);  // metric value of one fixed-point unit
-    const Planes P(planes_base, (size_t)gridDim.z * plane_elems);
+    const Planes P(planes_base, (size_t)gridDim.z * plane_elems, planes32<M>());
     vpass_column<DT, M, U4>(dframe, W, H, r, scale, q, P, (size_t)f * plane_elems, x, blockIdx.y * band, band, cal.tx,
                         cal.ty, cal.a, cal.b, min_valid, require_center, normals + 3 * fe * f, offsets + fe * f,
                         curvature + fe * f, counts ? counts + fe * f : nullptr, tau, flags, flag_count, f);
@@ -709,7 +733,7 @@ __global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc*
                                                                 void* planes_base, size_t stride, Codec scale) {
     extern __shared__ int tile[];
     __shared__ int slot;
-    const Planes P(planes_base, stride);
+    const Planes P(planes_base, stride, planes32<M>());
     for (;;) {
         const int it = claim_item(counter, &slot);
         if (it >= n_items) break;
@@ -728,7 +752,7 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_batch_kernel(const 
                                                                 void* planes_base, size_t stride, Codec scale,
                                                                 int min_valid, int require_center) {
     __shared__ int slot;
-    const Planes P(planes_base, stride);
+    const Planes P(planes_base, stride, planes32<M>());
     for (;;) {
         const int it = claim_item(counter, &slot);
         if (it >= n_items) break;
@@ -761,7 +785,7 @@ __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, Codec
                                                       float* __restrict__ normals, float* __restrict__ offsets,
                                                       float* __restrict__ curvature) {
     const unsigned count = *flag_count;
-    const Planes P(planes_base, (size_t)nframes * plane_elems);
+    const Planes P(planes_base, (size_t)nframes * plane_elems, planes32<M>());
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
         const unsigned long long e = flags[idx];
         const int f = (int)(e >> 48), y = (int)((e >> 24) & 0xffffff), x = (int)(e & 0xffffff);
@@ -837,7 +861,7 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);
     const float tx = cal.tx[x];
     const size_t fo = (size_t)f * fe;
-    const Planes P(planes_base, nf * plane_elems);
+    const Planes P(planes_base, nf * plane_elems, planes32<M>());
     constexpr int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
     typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
     S.init(pb, kGroup, H, y0, r);

@@ -47,8 +47,8 @@ sf_status cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 size_t plane_bytes_per_frame(int method, size_t plane_elems) {
-    // disparity: 1 x int32 + 3 x int64 ; standard: 1 x int32 + 5 x int64
-    return plane_elems * (sf::base_method(method) == SF_METHOD_STANDARD ? (4 + 5 * 8) : (4 + 3 * 8));
+    // disparity: 3 x int32 + 1 x int64 ; standard: 1 x int32 + 5 x int64
+    return plane_elems * (sf::base_method(method) == SF_METHOD_STANDARD ? (4 + 5 * 8) : (3 * 4 + 8));
 }
 
 // Fixed-point bits for a method and window: the most that keeps every exact
@@ -63,6 +63,11 @@ int quant_bits(int method, int k) {
         weight = std::max(weight, wjj);
     }
     int b = (int)std::floor((63.0 - std::log2(weight)) / 2.0 - 1e-9);
+    if (sf::base_method(method) == SF_METHOD_DISPARITY) {
+        // the row sums of v and v j are stored as int32: k 2^b and r (r + 1) 2^b < 2^31
+        b = std::min(b, (int)std::floor(31.0 - std::log2((double)k) - 1e-9));
+        b = std::min(b, (int)std::floor(31.0 - std::log2((double)std::max(1, r * (r + 1))) - 1e-9));
+    }
     return std::min(28, std::max(16, b));
 }
 
@@ -475,6 +480,12 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
     if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
     if (c->constraint == SF_CONSTRAINT_UNIT4 && c->method != SF_METHOD_DISPARITY && c->method != SF_METHOD_STANDARD)
         return fail(SF_ERR_UNSUPPORTED, "the |(a,b,c,d)| = 1 constraint applies to the implicit fits");
+    if (c->depth_type == SF_DEPTH_DISPARITY_U16 && sf::base_method(c->method) == SF_METHOD_DISPARITY) {
+        // the disparity integers go into the int32 row sums unscaled: k w and r (r + 1) w < 2^31
+        const double wmax = 128.0 * 65535.0 + std::fabs((double)c->disp_add);
+        if (wmax * std::max(c->k, std::max(1, c->r * (c->r + 1))) >= 2147483648.0)
+            return fail(SF_ERR_INVALID_ARG, "disparity model offset too large for a %d x %d window", c->k, c->k);
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t fe = (size_t)c->W * c->H;
     const size_t dbytes = depth_bytes(c->depth_type);
