@@ -343,23 +343,28 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
         const int* row = tile + threadIdx.x * pitch;
         const int xend = min(x0 + seg, W);
 
-        // channel state: mask moments (count, sum j, sum j^2) and value moments
+        // channel state: mask moments (count, sum j, sum j^2) and value moments.
+        // The disparity form's row sums of v and v j fit 31 bits (the fixed-point
+        // bits are chosen so): they slide in 32-bit unsigned arithmetic, exact
+        // modulo 2^32, which the stored int32 values are.
+        using Acc = typename std::conditional<base_method(M) == SF_METHOD_DISPARITY, uint32_t, int64_t>::type;
         int h0 = 0, h1 = 0, h2 = 0;
-        int64_t a0 = 0, a1 = 0;          // sum v, sum v j
+        Acc a0 = 0, a1 = 0;              // sum v, sum v j
         int64_t s0 = 0, s1 = 0, s2 = 0;  // sum v^2, sum v^2 j, sum v^2 j^2 (s1, s2: standard only)
         for (int j = -r; j <= r; ++j) {
             const int v = row[j + r];
             if (v >= 0) {
                 const int64_t vv = (int64_t)v * v;
                 h0 += 1; h1 += j; h2 += j * j;
-                a0 += v; a1 += (int64_t)v * j;
+                a0 += (Acc)v; a1 += (Acc)((int64_t)v * j);
                 s0 += vv;
                 if (base_method(M) == SF_METHOD_STANDARD) { s1 += vv * j; s2 += vv * (j * j); }
             }
         }
         for (int xb = x0; xb < xend; xb += 4) {
             int32_t hmv[4];
-            int64_t c0v[4], c1v[4], c2v[4], c3v[4], c4v[4];
+            Acc c0v[4], c1v[4];
+            int64_t c2v[4], c3v[4], c4v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int x = xb + u;
@@ -371,7 +376,7 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
                     const int mo = vo >= 0, mi = vi >= 0;
                     slide3(h0, h1, h2, mo, mi, r);
                     const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
-                    slide2(a0, a1, co, ci, r);
+                    slide2(a0, a1, (Acc)co, (Acc)ci, r);
                     const int64_t qo = co * co, qi = ci * ci;
                     if (base_method(M) == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
                     else s0 = s0 - qo + qi;
