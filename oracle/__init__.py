@@ -61,6 +61,9 @@ def _load():
         lib.sfo_fit_rect.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ip]
         lib.sfo_fit_rect.restype = ctypes.c_int
+        lib.sfo_fit_at.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, ip, dp, dp, ctypes.c_int]
+        lib.sfo_fit_at.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -124,6 +127,29 @@ def fit(depth: np.ndarray, intr: Sequence[float], k: int, method: str = "dispari
     if mom is not None:
         out["moments"] = mom
     return out
+
+
+def fit_at(depth: np.ndarray, intr: Sequence[float], k: int, xy: np.ndarray, method: str = "disparity", *,
+           unit4: bool = False, min_valid: int = 3, require_center: bool = True, depth_scale: float = 1e-3,
+           threads: int = 0) -> Dict[str, np.ndarray]:
+    """``fit`` evaluated at the pixels xy [N, 2] (x, y) only: the same dict with a leading N axis
+    (lam and moments always included)."""
+    lib = _load()
+    Z = np.ascontiguousarray(depth_to_f64(depth, depth_scale))
+    H, W = Z.shape
+    it = np.ascontiguousarray(np.asarray(intr, dtype=np.float64))
+    pts = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
+    n = pts.shape[0]
+    normals, offsets, curv = np.empty((n, 3)), np.empty(n), np.empty(n)
+    counts = np.empty(n, dtype=np.int32)
+    lam, mom = np.empty((n, 3)), np.empty((n, 10))
+    ip = ctypes.POINTER(ctypes.c_int32)
+    rc = lib.sfo_fit_at(_dp(Z), W, H, _dp(it), int(k), METHODS[method], int(unit4), int(min_valid),
+                        int(require_center), n, pts.ctypes.data_as(ip), _dp(normals), _dp(offsets), _dp(curv),
+                        counts.ctypes.data_as(ip), _dp(lam), _dp(mom), int(threads))
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments (rc=%d)" % rc)
+    return {"normals": normals, "offsets": offsets, "curvature": curv, "counts": counts, "lam": lam, "moments": mom}
 
 
 def backward(depth: np.ndarray, intr: Sequence[float], k: int, g_normals: np.ndarray, g_offsets: np.ndarray,

@@ -288,6 +288,36 @@ static int fit_sums(int method, int unit4, double A[3][3], const double g[3], do
     return 1;
 }
 
+/* Steps 1-6 of the header for the window of pixel (px, py); results go to output slot o. */
+static void fit_pixel(const double* Z, int W, int H, const double* intr, int r, int method, int unit4, int min_valid,
+                      int require_center, int px, int py, size_t o, double* normals, double* offsets, double* curv,
+                      int32_t* counts, double* lam, double* moments) {
+    double A[3][3], g[3], s, bb;
+    int64_t pm[5];
+    int n = window_sums(Z, W, H, intr, r, method, px, py, A, g, &s, &bb, pm);
+    if (counts) counts[o] = n;
+    if (moments) {
+        double* mo = moments + o * 10;
+        mo[0] = A[0][0]; mo[1] = A[0][1]; mo[2] = A[0][2];
+        mo[3] = A[1][1]; mo[4] = A[1][2]; mo[5] = A[2][2];
+        mo[6] = g[0]; mo[7] = g[1]; mo[8] = g[2]; mo[9] = s;
+    }
+    int ok = n >= min_valid && n > 0;
+    if (require_center && !valid_depth(Z[(size_t)py * W + px])) ok = 0;
+    double nrm[3], d, third, l[3], lam0;
+    if (ok) ok = fit_sums(method, unit4, A, g, s, bb, n, pm, nrm, &d, &third, l, &lam0);
+    if (!ok) {
+        normals[3 * o] = normals[3 * o + 1] = normals[3 * o + 2] = NAN;
+        offsets[o] = NAN; curv[o] = NAN;
+        if (lam) lam[3 * o] = lam[3 * o + 1] = lam[3 * o + 2] = NAN;
+        return;
+    }
+    normals[3 * o] = nrm[0]; normals[3 * o + 1] = nrm[1]; normals[3 * o + 2] = nrm[2];
+    offsets[o] = d;
+    curv[o] = third;
+    if (lam) { lam[3 * o] = l[0]; lam[3 * o + 1] = l[1]; lam[3 * o + 2] = l[2]; }
+}
+
 /*
  * sfo_fit: the whole forward oracle.
  *   Z        [H*W] depth (metres), non-finite or <= 0 means missing
@@ -310,35 +340,32 @@ int sfo_fit(const double* Z, int W, int H, const double* intr, int k, int method
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 2)
 #endif
-    for (int py = 0; py < H; ++py) {
-        for (int px = 0; px < W; ++px) {
-            const size_t o = (size_t)py * W + px;
-            double A[3][3], g[3], s, bb;
-            int64_t pm[5];
-            int n = window_sums(Z, W, H, intr, r, method, px, py, A, g, &s, &bb, pm);
-            if (counts) counts[o] = n;
-            if (moments) {
-                double* mo = moments + o * 10;
-                mo[0] = A[0][0]; mo[1] = A[0][1]; mo[2] = A[0][2];
-                mo[3] = A[1][1]; mo[4] = A[1][2]; mo[5] = A[2][2];
-                mo[6] = g[0]; mo[7] = g[1]; mo[8] = g[2]; mo[9] = s;
-            }
-            int ok = n >= min_valid && n > 0;
-            if (require_center && !valid_depth(Z[o])) ok = 0;
-            double nrm[3], d, third, l[3], lam0;
-            if (ok) ok = fit_sums(method, unit4, A, g, s, bb, n, pm, nrm, &d, &third, l, &lam0);
-            if (!ok) {
-                normals[3 * o] = normals[3 * o + 1] = normals[3 * o + 2] = NAN;
-                offsets[o] = NAN; curv[o] = NAN;
-                if (lam) lam[3 * o] = lam[3 * o + 1] = lam[3 * o + 2] = NAN;
-                continue;
-            }
-            normals[3 * o] = nrm[0]; normals[3 * o + 1] = nrm[1]; normals[3 * o + 2] = nrm[2];
-            offsets[o] = d;
-            curv[o] = third;
-            if (lam) { lam[3 * o] = l[0]; lam[3 * o + 1] = l[1]; lam[3 * o + 2] = l[2]; }
-        }
-    }
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px)
+            fit_pixel(Z, W, H, intr, r, method, unit4, min_valid, require_center, px, py, (size_t)py * W + px,
+                      normals, offsets, curv, counts, lam, moments);
+    return 0;
+}
+
+/*
+ * sfo_fit_at: sfo_fit evaluated at npix pixels only, xy = [x0, y0, x1, y1, ...];
+ * output slot i holds pixel i (same layouts as sfo_fit with H*W -> npix).
+ */
+int sfo_fit_at(const double* Z, int W, int H, const double* intr, int k, int method, int unit4, int min_valid,
+               int require_center, int npix, const int32_t* xy, double* normals, double* offsets, double* curv,
+               int32_t* counts, double* lam, double* moments, int nthreads) {
+    if (!Z || W <= 0 || H <= 0 || !intr || k < 1 || (k & 1) == 0 || method < 0 || method > 3 || npix < 0 || !xy)
+        return -1;
+    for (int i = 0; i < npix; ++i)
+        if (xy[2 * i] < 0 || xy[2 * i] >= W || xy[2 * i + 1] < 0 || xy[2 * i + 1] >= H) return -1;
+    const int r = (k - 1) / 2;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int i = 0; i < npix; ++i)
+        fit_pixel(Z, W, H, intr, r, method, unit4, min_valid, require_center, xy[2 * i], xy[2 * i + 1], (size_t)i,
+                  normals, offsets, curv, counts, lam, moments);
     return 0;
 }
 

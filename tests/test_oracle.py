@@ -400,3 +400,21 @@ def test_explicit_fit_is_least_squares(method):
     assert np.allclose(o["normals"][y0, x0], v, atol=1e-10)
     assert abs(o["offsets"][y0, x0] - d) < 1e-10 * abs(d)
     assert abs(o["curvature"][y0, x0] - res) < 1e-9 * max(res, 1e-12) + 1e-18
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard", "explicit_disparity", "explicit_standard"])
+def test_fit_at_equals_fit_at_those_pixels(method):
+    """The sampled form used at full workload sizes returns what the whole-frame fit returns there."""
+    W, H, k = 97, 61, 9
+    intr = scenes.Intrinsics.scaled(W, H)
+    depth = scenes.kinect_frame(scenes.BASE_SEED + 77, intr, W, H)
+    full = oracle.fit(depth, intr.as_tuple(), k, method, want_lambda=True, want_moments=True)
+    rng = np.random.Generator(np.random.PCG64(5))
+    xy = np.concatenate([[[0, 0], [W - 1, H - 1], [W - 1, 0], [0, H - 1]],
+                         np.stack([rng.integers(0, W, 200), rng.integers(0, H, 200)], -1)])
+    pts = oracle.fit_at(depth, intr.as_tuple(), k, xy, method)
+    for key in ("normals", "offsets", "curvature", "counts", "lam", "moments"):
+        a = np.nan_to_num(full[key][xy[:, 1], xy[:, 0]], nan=7.0)
+        assert np.array_equal(a, np.nan_to_num(pts[key], nan=7.0)), key
+    with pytest.raises(ValueError):
+        oracle.fit_at(depth, intr.as_tuple(), k, [[W, 0]], method)
