@@ -255,6 +255,8 @@ struct Planes {
 __device__ __forceinline__ int32_t pack_mask(int h0, int h1, int h2) {
     return h0 | ((h1 + 512) << 6) | (h2 << 16);
 }
+// the packed mask moments of a row without valid pixels (every field zero)
+constexpr int32_t kEmptyMask = 512 << 6;
 __device__ __forceinline__ void unpack_mask(int32_t v, int& h0, int& h1, int& h2) {
     h0 = v & 63;
     h1 = ((v >> 6) & 1023) - 512;
@@ -460,18 +462,32 @@ struct DispState {
     float n = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;
     int64_t Sw = 0, Swj = 0, Swi = 0, Sww = 0;
     __device__ DispState(const Planes& P) : hm(P.p32), g0(P.c32(1)), g1(P.c32(2)), q0(P.c64(0)) {}
-    // window of output row y0 from rows y0 - r .. y0 + r
+    // window of output row y0 from rows y0 - r .. y0 + r (clipped to the
+    // image), in batches of kInitRows rows whose loads are all issued before
+    // any is used; rows past the end of a batch read as empty
+    static constexpr int kInitRows = 8;
     __device__ __forceinline__ void init(size_t pb, int rs, int H, int y0, int r) {
-        for (int yy = y0 - r; yy <= y0 + r; ++yy) {
-            if (yy < 0 || yy >= H) continue;
-            const size_t o = pb + (size_t)yy * rs;
-            int c0, c1, c2;
-            unpack_mask(__ldg(hm + o), c0, c1, c2);
-            const int i = yy - y0;
-            const float f0 = (float)c0, f1 = (float)c1, fi = (float)i;
-            n += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
-            const int64_t w0 = __ldg(g0 + o);
-            Sw += w0; Swj += __ldg(g1 + o); Swi += (int64_t)i * w0; Sww += __ldg(q0 + o);
+        const int ylo = max(y0 - r, 0), yhi = min(y0 + r, H - 1);
+        for (int yb = ylo; yb <= yhi; yb += kInitRows) {
+            int32_t hv[kInitRows], av[kInitRows], bv[kInitRows];
+            int64_t qv[kInitRows];
+#pragma unroll
+            for (int u = 0; u < kInitRows; ++u) {
+                hv[u] = kEmptyMask; av[u] = 0; bv[u] = 0; qv[u] = 0;
+                if (yb + u <= yhi) {
+                    const size_t o = pb + (size_t)(yb + u) * rs;
+                    hv[u] = __ldg(hm + o); av[u] = __ldg(g0 + o); bv[u] = __ldg(g1 + o); qv[u] = __ldg(q0 + o);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kInitRows; ++u) {
+                const int i = yb + u - y0;
+                int c0, c1, c2;
+                unpack_mask(hv[u], c0, c1, c2);
+                const float f0 = (float)c0, f1 = (float)c1, fi = (float)i;
+                n += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
+                Sw += av[u]; Swj += bv[u]; Swi += (int64_t)i * av[u]; Sww += qv[u];
+            }
         }
     }
     // The two horizontal-moment rows of the slide from output row y to y + 1
@@ -525,22 +541,36 @@ struct StdStateT {
     int64_t Sz = 0, Szi = 0, Szj = 0, Szz = 0, Szzi = 0, Szzii = 0, Szzj = 0, Szzji = 0, Szzjj = 0;
     __device__ StdStateT(const Planes& P)
         : hc(P.p32), z0(P.c64(0)), z1(P.c64(1)), b0(P.c64(2)), b1(P.c64(3)), b2(P.c64(4)) {}
+    // as DispState::init, in batches of kInitRows rows
+    static constexpr int kInitRows = 4;
     __device__ __forceinline__ void init(size_t pb, int rs, int H, int y0, int r) {
-        for (int yy = y0 - r; yy <= y0 + r; ++yy) {
-            if (yy < 0 || yy >= H) continue;
-            const size_t o = pb + (size_t)yy * rs;
-            const int64_t i = yy - y0;
-            int c0, c1, c2;
-            unpack_mask(__ldg(hc + o), c0, c1, c2);
-            n += c0;
-            if constexpr (kMask) {
-                const float fi = (float)i, f0 = (float)c0, f1 = (float)c1;
-                fn += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
+        const int ylo = max(y0 - r, 0), yhi = min(y0 + r, H - 1);
+        for (int yb = ylo; yb <= yhi; yb += kInitRows) {
+            int32_t hv[kInitRows];
+            int64_t zv[kInitRows], zjv[kInitRows], q0v[kInitRows], q1v[kInitRows], q2v[kInitRows];
+#pragma unroll
+            for (int u = 0; u < kInitRows; ++u) {
+                hv[u] = kEmptyMask; zv[u] = zjv[u] = q0v[u] = q1v[u] = q2v[u] = 0;
+                if (yb + u <= yhi) {
+                    const size_t o = pb + (size_t)(yb + u) * rs;
+                    hv[u] = __ldg(hc + o); zv[u] = __ldg(z0 + o); zjv[u] = __ldg(z1 + o);
+                    q0v[u] = __ldg(b0 + o); q1v[u] = __ldg(b1 + o); q2v[u] = __ldg(b2 + o);
+                }
             }
-            const int64_t c0z = __ldg(z0 + o), q0v = __ldg(b0 + o), q1v = __ldg(b1 + o);
-            Sz += c0z; Szi += i * c0z; Szj += __ldg(z1 + o);
-            Szz += q0v; Szzi += i * q0v; Szzii += i * i * q0v;
-            Szzj += q1v; Szzji += i * q1v; Szzjj += __ldg(b2 + o);
+#pragma unroll
+            for (int u = 0; u < kInitRows; ++u) {
+                const int64_t i = yb + u - y0;
+                int c0, c1, c2;
+                unpack_mask(hv[u], c0, c1, c2);
+                n += c0;
+                if constexpr (kMask) {
+                    const float fi = (float)i, f0 = (float)c0, f1 = (float)c1;
+                    fn += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
+                }
+                Sz += zv[u]; Szi += i * zv[u]; Szj += zjv[u];
+                Szz += q0v[u]; Szzi += i * q0v[u]; Szzii += i * i * q0v[u];
+                Szzj += q1v[u]; Szzji += i * q1v[u]; Szzjj += q2v[u];
+            }
         }
     }
     // fetch() / apply(): the slide from output row y to y + 1 split into its
@@ -607,16 +637,22 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
     typename std::conditional<B == SF_METHOD_DISPARITY, DispState,
                               StdStateT<M == SF_METHOD_EXPLICIT_STANDARD>>::type S(P);
     S.init(pb, kGroup, H, y0, r);
-    float zc = load_depth<DT>(depth, (size_t)y0 * W + x, scale);
+    // row pointers, advanced by one image row per output row
+    size_t oi = (size_t)y0 * W + x;
+    float* pn = normals + 3 * oi;
+    float* po = offsets + oi;
+    float* pc = curvature + oi;
+    int32_t* pk = counts ? counts + oi : nullptr;
+    float zc = load_depth<DT>(depth, oi, scale);
     for (int y = y0; y < y1; ++y) {
-        const size_t oi = (size_t)y * W + x;
         const bool cvalid = depth_valid(zc);
         // issue the loads of the next slide (and the next centre depth) now:
         // the solve below hides their latency
         const bool more = y + 1 < y1;
+        oi += W;
         if (more) {
             S.fetch(pb, kGroup, H, y, r);
-            zc = load_depth<DT>(depth, oi + W, scale);
+            zc = load_depth<DT>(depth, oi, scale);
         }
         const int n = S.count();
         bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
@@ -652,9 +688,10 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
                               (unsigned long long)x;
             }
         }
-        normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
-        offsets[oi] = d; curvature[oi] = cu;
-        if (counts) counts[oi] = n;
+        pn[0] = nx; pn[1] = ny; pn[2] = nz;
+        *po = d; *pc = cu;
+        if (pk) { *pk = n; pk += W; }
+        pn += 3 * (size_t)W; po += W; pc += W;
         if (more) S.apply(r);
     }
 }

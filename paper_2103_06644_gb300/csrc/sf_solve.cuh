@@ -96,14 +96,15 @@ __device__ __forceinline__ void null_vector(T r11, T r12, T r13, T r22, T r23, T
     T b0 = c11, b1 = c12, b2 = c13, db = d1;
     if (d2 > db) { b0 = c12; b1 = c22; b2 = c23; db = d2; }
     if (d3 > db) { b0 = c13; b1 = c23; b2 = c33; }
-    T nb = b0 * b0 + b1 * b1 + b2 * b2;
-    if (!(nb > Fn<T>::tiny())) {  // l is (numerically) a double root: any unit vector of the null space
-        b0 = T(0); b1 = T(0); b2 = T(0);
-        if (a11 <= a22 && a11 <= a33) b0 = T(1); else if (a22 <= a33) b1 = T(1); else b2 = T(1);
-        nb = T(1);
-    }
-    const T s = Fn<T>::rsqrt(nb);
-    v0 = b0 * s; v1 = b1 * s; v2 = b2 * s;
+    const T nb = b0 * b0 + b1 * b1 + b2 * b2;
+    // l is (numerically) a double root where every cofactor vanishes: any unit
+    // vector of the null space (selects rather than a branch)
+    const bool deg = !(nb > Fn<T>::tiny());
+    const bool e0 = a11 <= a22 && a11 <= a33, e1 = !e0 && a22 <= a33;
+    const T s = Fn<T>::rsqrt(deg ? T(1) : nb);
+    v0 = deg ? (e0 ? T(1) : T(0)) : b0 * s;
+    v1 = deg ? (e1 ? T(1) : T(0)) : b1 * s;
+    v2 = deg ? (e0 || e1 ? T(0) : T(1)) : b2 * s;
 }
 
 // Smallest eigenpair of a symmetric positive semi-definite 3x3 matrix R
@@ -124,19 +125,19 @@ __device__ __forceinline__ void smallest_eigpair(T r11, T r12, T r13, T r22, T r
     const T third = T(1) / T(3);
     const T b11 = r11 - third, b22 = r22 - third, b33 = r33 - third;
     const T p2 = (b11 * b11 + b22 * b22 + b33 * b33 + T(2) * (r12 * r12 + r13 * r13 + r23 * r23)) * (T(1) / T(6));
-    T lmin = third, lmid = third, lmax = third;
-    if (p2 > Fn<T>::p2min()) {
-        const T p = Fn<T>::sqrt(p2);
-        const T detB = b11 * (b22 * b33 - r23 * r23) - r12 * (r12 * b33 - r23 * r13) + r13 * (r12 * r23 - b22 * r13);
-        T q = T(0.5) * detB * Fn<T>::rcp(p2 * p);
-        q = q > T(1) ? T(1) : (q < T(-1) ? T(-1) : q);
-        const T phi = Fn<T>::acos(q) * third;  // in [0, pi/3]
-        T sn, cs;
-        Fn<T>::sincos(phi, &sn, &cs);
-        lmax = third + T(2) * p * cs;
-        lmin = third - p * (cs + T(1.7320508075688772) * sn);
-        lmid = T(1) - lmax - lmin;
-    }
+    // p2 <= p2min: three equal eigenvalues (computed with a stand-in p2, then discarded)
+    const bool spread = p2 > Fn<T>::p2min();
+    const T p2s = spread ? p2 : T(1);
+    const T p = Fn<T>::sqrt(p2s);
+    const T detB = b11 * (b22 * b33 - r23 * r23) - r12 * (r12 * b33 - r23 * r13) + r13 * (r12 * r23 - b22 * r13);
+    T q = T(0.5) * detB * Fn<T>::rcp(p2s * p);
+    q = q > T(1) ? T(1) : (q < T(-1) ? T(-1) : q);
+    const T phi = Fn<T>::acos(q) * third;  // in [0, pi/3]
+    T sn, cs;
+    Fn<T>::sincos(phi, &sn, &cs);
+    const T lmax = spread ? third + T(2) * p * cs : third;
+    const T lmin = spread ? third - p * (cs + T(1.7320508075688772) * sn) : third;
+    const T lmid = spread ? T(1) - lmax - lmin : third;
     T a0, a1, a2;
     null_vector<T>(r11, r12, r13, r22, r23, r33, lmin, a0, a1, a2);
     const T t0 = r11 * a0 + r12 * a1 + r13 * a2;
@@ -153,23 +154,22 @@ __device__ __forceinline__ void smallest_eigpair(T r11, T r12, T r13, T r22, T r
         const T w1 = c12 * a0 + c22 * a1 + c23 * a2;
         const T w2 = c13 * a0 + c23 * a1 + c33 * a2;
         const T nw = w0 * w0 + w1 * w1 + w2 * w2;
-        if (nw > Fn<T>::tiny()) {
-            const T q = Fn<T>::rsqrt(nw);
-            a0 = w0 * q; a1 = w1 * q; a2 = w2 * q;
-        }
+        const bool okw = nw > Fn<T>::tiny();  // else keep a (an exact eigenvector already)
+        const T q = Fn<T>::rsqrt(okw ? nw : T(1));
+        a0 = okw ? w0 * q : a0; a1 = okw ? w1 * q : a1; a2 = okw ? w2 * q : a2;
     }
     v0 = a0; v1 = a1; v2 = a2;
     l0 = lr > T(0) ? lr : T(0);
-    gap = (lmax > T(0)) ? (lmid - lmin) / lmax : T(0);
+    gap = (lmax > T(0)) ? (lmid - lmin) * Fn<T>::rcp(lmax > T(0) ? lmax : T(1)) : T(0);
 }
 
 // Orientation: d > 0 (the camera centre lies on the positive side); d == 0
 // is broken toward n_z < 0, then toward a negative first nonzero component.
 template <typename T>
 __device__ __forceinline__ void orient(T& nx, T& ny, T& nz, T& d) {
-    bool flip = d < T(0);
-    if (d == T(0)) flip = (nz > T(0)) || (nz == T(0) && (nx > T(0) || (nx == T(0) && ny > T(0))));
-    if (flip) { nx = -nx; ny = -ny; nz = -nz; d = -d; }
+    const bool tie = (nz > T(0)) || (nz == T(0) && (nx > T(0) || (nx == T(0) && ny > T(0))));
+    const bool flip = d < T(0) || (d == T(0) && tie);
+    nx = flip ? -nx : nx; ny = flip ? -ny : ny; nz = flip ? -nz : nz; d = flip ? -d : d;
 }
 
 // The literal constraint of Eq. 4, |(a, b, c, d)| = 1: the smallest eigenpair
@@ -320,7 +320,7 @@ __device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj
     smallest_eigpair<T>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, l0, o.gap);
     o.curv = l0;
     o.tr = w.R11 + w.R22 + w.R33;  // R = K Y K^T is the Schur complement itself (no unit)
-    o.d = -(o.nx * w.mx + o.ny * w.my + o.nz) * Fn<T>::rcp(w.what) / qw;
+    o.d = -(o.nx * w.mx + o.ny * w.my + o.nz) * Fn<T>::rcp(w.what * qw);
     orient<T>(o.nx, o.ny, o.nz, o.d);
     return o;
 }
