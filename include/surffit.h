@@ -174,7 +174,8 @@ sf_status sf_set_precision(sf_ctx* ctx, int mode, float tau);
  *   normals    device [H][W][3] float32, out
  *   offsets    device [H][W] float32, out
  *   curvature  device [H][W] float32, out (mean squared residual for explicit fits)
- * Asynchronous on `stream`.
+ * Every buffer must be aligned to its element size (SF_ERR_INVALID_ARG
+ * otherwise; CUDA allocations always are).  Asynchronous on `stream`.
  */
 sf_status sf_fit(sf_ctx* ctx, const void* depth, float* normals, float* offsets, float* curvature, void* stream);
 

@@ -180,25 +180,54 @@ __device__ __forceinline__ float quantum(unsigned vmax_bits, int bits, const Cod
 // ---------------------------------------------------------------------------
 // 1. range
 // ---------------------------------------------------------------------------
+// Raw stored values of one 16-byte vector: 4 float32 or 8 uint16 values.
+template <int DT>
+struct RawVec {
+    static constexpr int kN = DT == SF_DEPTH_F32 ? 4 : 8;
+    __device__ static __forceinline__ float get(const uint4& v, int e) {
+        const unsigned w = e < kN / 4 ? v.x : e < kN / 2 ? v.y : e < 3 * kN / 4 ? v.z : v.w;
+        if (DT == SF_DEPTH_F32) return __uint_as_float(w);
+        return (float)((e & 1) ? (w >> 16) : (w & 0xffffu));
+    }
+};
+
 template <int DT, int M>
-__global__ void __launch_bounds__(256) range_kernel(const void* __restrict__ depth, size_t frame_elems, Codec scale,
+__device__ __forceinline__ float range_update(float vmax, float z, const Codec& cd) {
+    return depth_valid(z) ? fmaxf(vmax, fit_variable_of<DT, M>(z, cd)) : vmax;
+}
+
+// Largest fit variable of each frame (blockIdx.y).  The frame is read as
+// 16-byte vectors, two in flight per thread (8 resident 256-thread blocks
+// per SM fit in 32 registers) (issue is in order: a load
+// consumed right away would expose its whole latency); the elements before
+// the first 16-byte boundary and after the last whole vector are read singly.
+template <int DT, int M>
+__global__ void __launch_bounds__(256, 8) range_kernel(const void* __restrict__ depth, size_t frame_elems, Codec scale,
                                                     unsigned* __restrict__ vmax_bits) {
+    constexpr size_t kES = DT == SF_DEPTH_F32 ? 4 : 2;
+    constexpr int kN = RawVec<DT>::kN;
     const int f = blockIdx.y;
-    const size_t base = (size_t)f * frame_elems;
-    float vmax = 0.f;
-    // eight independent loads in flight per thread (issue is in order: a
-    // load consumed right away would expose its whole latency)
+    const char* fb = static_cast<const char*>(depth) + kES * (size_t)f * frame_elems;
+    const size_t head = min(frame_elems, (size_t)((16u - ((uintptr_t)fb & 15u)) & 15u) / kES);
+    const size_t nvec = (frame_elems - head) / kN;
+    const size_t tail = head + nvec * kN;
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < frame_elems; i0 += 8 * stride) {
-        float z[8];
+    float vmax = 0.f;
+    if (tid < head) vmax = range_update<DT, M>(vmax, load_raw<DT>(fb, tid), scale);
+    if (tid < frame_elems - tail) vmax = range_update<DT, M>(vmax, load_raw<DT>(fb, tail + tid), scale);
+    const uint4* vb = reinterpret_cast<const uint4*>(fb + kES * head);
+    for (size_t i0 = tid; i0 < nvec; i0 += 2 * stride) {
+        uint4 v[2];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 2; ++u) {
             const size_t i = i0 + u * stride;
-            z[u] = i < frame_elems ? load_raw<DT>(depth, base + i) : 0.f;
+            v[u] = i < nvec ? __ldg(vb + i) : make_uint4(0u, 0u, 0u, 0u);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (depth_valid(z[u])) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z[u], scale));
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int e = 0; e < kN; ++e) vmax = range_update<DT, M>(vmax, RawVec<DT>::get(v[u], e), scale);
     }
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     __shared__ float red[8];
@@ -323,38 +352,21 @@ __device__ __forceinline__ void load_tile(const void* __restrict__ depth, int W,
     }
 }
 
-// Horizontal moments of one tile: rows [y0, y0 + 128) x output columns
-// [x0, x0 + seg) of one frame.  `depth` points at the frame, `pofs` is the
-// frame's offset in the planes; `tile` is shared memory of
-// kHThreads * ((seg + 2r) | 1) ints.
-template <int DT, int M>
-__device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W, int H, int r, float sc,
-                                           const Codec& cd, const Planes& P, size_t pofs, int x0, int y0, int seg,
-                                           int* tile) {
-    const int IW = seg + 2 * r;
-    const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
-    const int rows = min(kHThreads, H - y0);
-    // the tile's raw depth, quantised; ceil(IW / 32) column chunks per row
-    // (IW <= seg + 30): 2 for seg 32, 3 for 64, 5 for 128
-    if (seg <= 32) load_tile<DT, M, 2>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
-    else if (seg <= 64) load_tile<DT, M, 3>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
-    else load_tile<DT, M, 5>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
-    __syncthreads();
-    if ((int)threadIdx.x < rows) {
-        const int y = y0 + threadIdx.x;
-        const int* row = tile + threadIdx.x * pitch;
-        const int xend = min(x0 + seg, W);
-
-        // channel state: mask moments (count, sum j, sum j^2) and value moments.
-        // The disparity form's row sums of v and v j fit 31 bits (the fixed-point
-        // bits are chosen so): they slide in 32-bit unsigned arithmetic, exact
-        // modulo 2^32, which the stored int32 values are.
-        using Acc = typename std::conditional<base_method(M) == SF_METHOD_DISPARITY, uint32_t, int64_t>::type;
-        int h0 = 0, h1 = 0, h2 = 0;
-        Acc a0 = 0, a1 = 0;              // sum v, sum v j
-        int64_t s0 = 0, s1 = 0, s2 = 0;  // sum v^2, sum v^2 j, sum v^2 j^2 (s1, s2: standard only)
+// Running horizontal sums of one row over one 32-column output segment:
+// mask moments (count, sum j, sum j^2) and value moments.  The disparity
+// form's row sums of v and v j fit 31 bits (the fixed-point bits are chosen
+// so): they slide in 32-bit unsigned arithmetic, exact modulo 2^32, which the
+// stored int32 values are.
+template <int M>
+struct HRowState {
+    using Acc = typename std::conditional<base_method(M) == SF_METHOD_DISPARITY, uint32_t, int64_t>::type;
+    int h0 = 0, h1 = 0, h2 = 0;
+    Acc a0 = 0, a1 = 0;              // sum v, sum v j
+    int64_t s0 = 0, s1 = 0, s2 = 0;  // sum v^2, sum v^2 j, sum v^2 j^2 (s1, s2: standard only)
+    // window of output column x0: tile columns x0 - xt .. x0 - xt + 2r
+    __device__ __forceinline__ void init(const int* row, int c0, int r) {
         for (int j = -r; j <= r; ++j) {
-            const int v = row[j + r];
+            const int v = row[c0 + j + r];
             if (v >= 0) {
                 const int64_t vv = (int64_t)v * v;
                 h0 += 1; h1 += j; h2 += j * j;
@@ -363,31 +375,51 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
                 if (base_method(M) == SF_METHOD_STANDARD) { s1 += vv * j; s2 += vv * (j * j); }
             }
         }
-        for (int xb = x0; xb < xend; xb += 4) {
+    }
+    // slide from output column c to c + 1 (tile-relative c)
+    __device__ __forceinline__ void step(const int* row, int c, int r) {
+        const int vo = row[c];              // column x - r leaves
+        const int vi = row[c + 2 * r + 1];  // column x + r + 1 enters
+        const int mo = vo >= 0, mi = vi >= 0;
+        slide3(h0, h1, h2, mo, mi, r);
+        const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
+        slide2(a0, a1, (Acc)co, (Acc)ci, r);
+        const int64_t qo = co * co, qi = ci * ci;
+        if (base_method(M) == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
+        else s0 = s0 - qo + qi;
+    }
+};
+
+// One row of a tile: L independent 32-column output segments [x0 + 32 l,
+// x0 + 32 (l + 1)) clipped to xend, slid in lock step (L independent
+// dependency chains per thread), four columns per store.
+template <int M, int L>
+__device__ __forceinline__ void hpass_row(const int* row, int x0, int xend, int y, int H, int r, const Planes& P,
+                                          size_t pofs) {
+    constexpr int kSub = 32;
+    HRowState<M> st[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l)
+        if (x0 + l * kSub < xend) st[l].init(row, l * kSub, r);
+    for (int xb = 0; xb < kSub; xb += 4) {
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const int xs = x0 + l * kSub + xb;  // first of the four columns
+            const int xe = min(x0 + (l + 1) * kSub, xend);
+            if (xs >= xe) continue;
             int32_t hmv[4];
-            Acc c0v[4], c1v[4];
+            typename HRowState<M>::Acc c0v[4], c1v[4];
             int64_t c2v[4], c3v[4], c4v[4];
+            HRowState<M>& S = st[l];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int x = xb + u;
-                hmv[u] = pack_mask(h0, h1, h2);
-                c0v[u] = a0; c1v[u] = a1; c2v[u] = s0; c3v[u] = s1; c4v[u] = s2;
-                if (x + 1 < xend) {
-                    const int vo = row[x - x0];              // column x - r leaves
-                    const int vi = row[x - x0 + 2 * r + 1];  // column x + r + 1 enters
-                    const int mo = vo >= 0, mi = vi >= 0;
-                    slide3(h0, h1, h2, mo, mi, r);
-                    const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
-                    slide2(a0, a1, (Acc)co, (Acc)ci, r);
-                    const int64_t qo = co * co, qi = ci * ci;
-                    if (base_method(M) == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
-                    else s0 = s0 - qo + qi;
-                }
+                hmv[u] = pack_mask(S.h0, S.h1, S.h2);
+                c0v[u] = S.a0; c1v[u] = S.a1; c2v[u] = S.s0; c3v[u] = S.s1; c4v[u] = S.s2;
+                if (xs + u + 1 < xe) S.step(row, xs + u - x0, r);
             }
-            const size_t o = plane_index(pofs, xb, y, H);  // xb % 4 == 0: 4 entries in one group
+            const size_t o = plane_index(pofs, xs, y, H);  // xs % 4 == 0: 4 entries in one group
             if (base_method(M) == SF_METHOD_DISPARITY) {
-                // row sums of w and w j fit 31 bits (the fixed-point bits are chosen so): int32
-                if (xb + 4 <= xend) {
+                if (xs + 4 <= xe) {
                     *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
                     *reinterpret_cast<int4*>(P.c32(1) + o) =
                         make_int4((int)c0v[0], (int)c0v[1], (int)c0v[2], (int)c0v[3]);
@@ -397,13 +429,13 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
                     *reinterpret_cast<longlong2*>(q0) = make_longlong2(c2v[0], c2v[1]);
                     *reinterpret_cast<longlong2*>(q0 + 2) = make_longlong2(c2v[2], c2v[3]);
                 } else {
-                    for (int u = 0; u < 4 && xb + u < xend; ++u) {
+                    for (int u = 0; u < 4 && xs + u < xe; ++u) {
                         P.p32[o + u] = hmv[u];
                         P.c32(1)[o + u] = (int)c0v[u]; P.c32(2)[o + u] = (int)c1v[u];
                         P.c64(0)[o + u] = c2v[u];
                     }
                 }
-            } else if (xb + 4 <= xend) {
+            } else if (xs + 4 <= xe) {
                 *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
                 int64_t* c0 = P.c64(0) + o;
                 int64_t* c1 = P.c64(1) + o;
@@ -421,7 +453,7 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
                 *reinterpret_cast<longlong2*>(c4) = make_longlong2(c4v[0], c4v[1]);
                 *reinterpret_cast<longlong2*>(c4 + 2) = make_longlong2(c4v[2], c4v[3]);
             } else {
-                for (int u = 0; u < 4 && xb + u < xend; ++u) {
+                for (int u = 0; u < 4 && xs + u < xe; ++u) {
                     P.p32[o + u] = hmv[u];
                     P.c64(0)[o + u] = c0v[u]; P.c64(1)[o + u] = c1v[u]; P.c64(2)[o + u] = c2v[u];
                     P.c64(3)[o + u] = c3v[u]; P.c64(4)[o + u] = c4v[u];
@@ -431,19 +463,46 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
     }
 }
 
-template <int DT, int M>
-__global__ void __launch_bounds__(kHThreads) hpass_kernel(const void* __restrict__ depth, int W, int H, int r,
-                                                          Codec scale, const unsigned* __restrict__ vmax_bits,
-                                                          int bits, int raw_z, int Wp, size_t plane_elems,
-                                                          void* planes_base, int seg) {
+// Horizontal moments of one tile: rows [y0, y0 + 128) x output columns
+// [x0, x0 + 32 L) of one frame.  `depth` points at the frame, `pofs` is the
+// frame's offset in the planes; `tile` is shared memory of
+// kHThreads * ((32 L + 2r) | 1) ints.
+template <int DT, int M, int L>
+__device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W, int H, int r, float sc,
+                                           const Codec& cd, const Planes& P, size_t pofs, int x0, int y0,
+                                           int* tile) {
+    constexpr int seg = 32 * L;
+    const int IW = seg + 2 * r;
+    const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
+    const int rows = min(kHThreads, H - y0);
+    // the tile's raw depth, quantised; ceil(IW / 32) column chunks per row
+    // (IW <= seg + 30): 2 for seg 32, 3 for 64, 5 for 128
+    load_tile<DT, M, L + 1 + (L == 4)>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
+    __syncthreads();
+    if ((int)threadIdx.x < rows)
+        hpass_row<M, L>(tile + threadIdx.x * pitch, x0, min(x0 + seg, W), y0 + threadIdx.x, H, r, P, pofs);
+}
+
+// Resident blocks per SM of the horizontal pass for 32 L-column tiles (shared
+// memory: 32 KB, 48 KB, 80 KB per block at r = 15), which caps the registers
+// (6 for the standard form's 32-column tiles: its int64 sums need more).
+template <int M, int L>
+__host__ __device__ constexpr int hpass_blocks() {
+    return L == 1 ? (base_method(M) == SF_METHOD_STANDARD ? 6 : 7) : (L == 2 ? 4 : 2);
+}
+
+template <int DT, int M, int L>
+__global__ void __launch_bounds__(kHThreads, hpass_blocks<M, L>()) hpass_kernel(
+    const void* __restrict__ depth, int W, int H, int r, Codec scale, const unsigned* __restrict__ vmax_bits, int bits,
+    int raw_z, int Wp, size_t plane_elems, void* planes_base) {
     extern __shared__ int tile[];
     const int f = blockIdx.z;
     const float sc = ldexpf(1.f, quant_exponent(vmax_bits[f], bits));  // 2^e, exact
     const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * W * H;
     const Planes P(planes_base, (size_t)gridDim.z * plane_elems, planes32<M>());
-    hpass_tile<DT, M>(dframe, W, H, r, sc, scale, P, (size_t)f * plane_elems, blockIdx.x * seg,
-                      blockIdx.y * kHThreads, seg, tile);
+    hpass_tile<DT, M, L>(dframe, W, H, r, sc, scale, P, (size_t)f * plane_elems, blockIdx.x * 32 * L,
+                         blockIdx.y * kHThreads, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -782,7 +841,9 @@ __global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc*
         const int3 w = items[it];
         const FrameDesc& d = descs[w.x];
         const float sc = ldexpf(1.f, quant_exponent(vmax_bits[w.x], d.bits));
-        hpass_tile<DT, M>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, d.seg, tile);
+        if (d.seg <= 32) hpass_tile<DT, M, 1>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, tile);
+        else if (d.seg <= 64) hpass_tile<DT, M, 2>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, tile);
+        else hpass_tile<DT, M, 4>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, tile);
     }
 }
 

@@ -89,6 +89,7 @@ struct sf_ctx {
     int min_valid = 3;
     int require_center = 1;
     int device = 0;
+    int sms = 152;        // streaming multiprocessors of the device (grid sizing)
     float* tx = nullptr;  // [W]
     float* ty = nullptr;  // [H]
     unsigned* vmax = nullptr;  // [max_frames]
@@ -173,6 +174,48 @@ static sf_status ensure_planes(sf_ctx* c, int frames) {
     return SF_OK;
 }
 
+static bool misaligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) != 0; }
+
+// The horizontal pass for tiles of seg = 32, 64 or 128 columns (one kernel
+// each: their register budgets differ).
+template <int DT, int M>
+static void launch_hpass(dim3 grid, size_t smem, cudaStream_t st, const void* depth, const sf_ctx* c, int bits,
+                         int raw_z, int seg) {
+    if (seg <= 32)
+        sf::hpass_kernel<DT, M, 1><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
+                                                                     bits, raw_z, c->Wp, c->plane_elems, c->planes);
+    else if (seg <= 64)
+        sf::hpass_kernel<DT, M, 2><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
+                                                                     bits, raw_z, c->Wp, c->plane_elems, c->planes);
+    else
+        sf::hpass_kernel<DT, M, 4><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
+                                                                     bits, raw_z, c->Wp, c->plane_elems, c->planes);
+}
+
+template <int DT, int M>
+static void set_hpass_smem_one(int smem) {
+    cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+// Opt every horizontal-pass kernel in to `smem` bytes of dynamic shared memory.
+static void set_hpass_smem(int smem) {
+    set_hpass_smem_one<SF_DEPTH_F32, SF_METHOD_DISPARITY>(smem);
+    set_hpass_smem_one<SF_DEPTH_F32, SF_METHOD_STANDARD>(smem);
+    set_hpass_smem_one<SF_DEPTH_U16, SF_METHOD_DISPARITY>(smem);
+    set_hpass_smem_one<SF_DEPTH_U16, SF_METHOD_STANDARD>(smem);
+    set_hpass_smem_one<SF_DEPTH_DISPARITY_U16, SF_METHOD_DISPARITY>(smem);
+    set_hpass_smem_one<SF_DEPTH_DISPARITY_U16, SF_METHOD_STANDARD>(smem);
+}
+
+// Blocks per frame of the range pass: one wave of 256-thread blocks (8 per
+// SM) over all frames, at most one block per 16 x 256 elements.
+static int range_blocks(const sf_ctx* c, size_t fe, int nfr) {
+    const size_t per_frame = (size_t)c->sms * 8 / (size_t)std::max(1, nfr);
+    return (int)std::max<size_t>(1, std::min((fe + 4095) / 4096, per_frame));
+}
+
 // Band height of the vertical pass: long bands amortise the 2r-row warm-up,
 // short bands give enough threads to fill the GPU.
 static int vertical_band(const sf_ctx* c, int nfr) {
@@ -196,8 +239,7 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
     SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
     if (!raw_z) {
         StageTimer t(c, 0, st);
-        int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
-        blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
+        const int blocks = range_blocks(c, fe, nfr);
         sf::range_kernel<DT, B><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
     }
     {
@@ -206,8 +248,7 @@ static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* norma
         dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
         const int IW = seg + 2 * c->r;
         const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
-        sf::hpass_kernel<DT, B><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
-                                                                  bits, raw_z, c->Wp, c->plane_elems, c->planes, seg);
+        launch_hpass<DT, B>(grid, smem, st, depth, c, bits, raw_z, seg);
     }
     {
         StageTimer t(c, 2, st);
@@ -248,8 +289,7 @@ static sf_status launch_quadtree(sf_ctx* c, int nfr, int frame_base, const void*
     const int bits = quad_bits(M);
     SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
     if (!raw_z) {
-        int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
-        blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
+        const int blocks = range_blocks(c, fe, nfr);
         sf::range_kernel<DT, B><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
     }
     SF_CUDA(cudaMemsetAsync(c->quad_cnt, 0, sizeof(int) * 8, st));
@@ -317,8 +357,7 @@ static sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const fl
     const int bits = quant_bits(M, c->k);
     SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
     if (!raw_z) {
-        int blocks = (int)std::min<size_t>(1024, (fe + 255) / 256);
-        blocks = std::max(1, std::min(blocks, 2 * 152 * 8 / std::max(1, nfr)));
+        const int blocks = range_blocks(c, fe, nfr);
         sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
     }
     {
@@ -326,8 +365,7 @@ static sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const fl
         dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
         const int IW = seg + 2 * c->r;
         const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
-        sf::hpass_kernel<DT, M><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
-                                                                  bits, raw_z, c->Wp, c->plane_elems, c->planes, seg);
+        launch_hpass<DT, M>(grid, smem, st, depth, c, bits, raw_z, seg);
     }
     sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
     {
@@ -390,6 +428,8 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
     c->Wp = (W + 63) / 64 * 64;
     c->plane_elems = (size_t)c->Wp * H;
     cudaGetDevice(&c->device);
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->sms < 1)
+        c->sms = 152;
     // Calibration tables (Eq. 10), computed in FP64 on the host, stored as FP32.
     float* htx = (float*)malloc(sizeof(float) * W);
     float* hty = (float*)malloc(sizeof(float) * H);
@@ -427,14 +467,7 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
     {
         const int IW = 128 + 2 * sf::kMaxR;
         const int smem = (int)(sizeof(int) * sf::kHThreads * (size_t)(IW | 1));
-        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_F32, SF_METHOD_DISPARITY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_F32, SF_METHOD_STANDARD>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_U16, SF_METHOD_DISPARITY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_U16, SF_METHOD_STANDARD>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        set_hpass_smem(smem);
         const int T = sf::kGTile + 2 * sf::kMaxR;
         const int gs7 = (int)(sizeof(float) * 7 * T * T), gs12 = (int)(sizeof(float) * 12 * T * T);
         cudaFuncSetAttribute(sf::gather_kernel<SF_DEPTH_F32, SF_METHOD_DISPARITY>,
@@ -478,6 +511,9 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
     if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
     if (n_frames == 0) return SF_OK;
     if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
+    if (misaligned(depth, depth_bytes(c->depth_type)) || misaligned(normals, 4) || misaligned(offsets, 4) ||
+        misaligned(curvature, 4) || misaligned(counts, 4))
+        return fail(SF_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     if (c->constraint == SF_CONSTRAINT_UNIT4 && c->method != SF_METHOD_DISPARITY && c->method != SF_METHOD_STANDARD)
         return fail(SF_ERR_UNSUPPORTED, "the |(a,b,c,d)| = 1 constraint applies to the implicit fits");
     if (c->depth_type == SF_DEPTH_DISPARITY_U16 && sf::base_method(c->method) == SF_METHOD_DISPARITY) {
@@ -620,6 +656,7 @@ sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_
     SF_CUDA(cudaMemsetAsync(n_nodes, 0, sizeof(int32_t), st));
     if (n_frames == 0) return SF_OK;
     if (!depth) return fail(SF_ERR_INVALID_ARG, "null depth");
+    if (misaligned(depth, depth_bytes(c->depth_type))) return fail(SF_ERR_INVALID_ARG, "depth must be aligned to its element size");
     // frames go through in groups of at most 64 (the per-frame quantum slots)
     const int per = std::min(n_frames, 64);
     const size_t tiles = (size_t)((c->W + p->tile - 1) / p->tile) * ((c->H + p->tile - 1) / p->tile);
@@ -706,6 +743,9 @@ sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const floa
     if (n_frames == 0) return SF_OK;
     if (!depth || !g_normals || !g_offsets || !g_curvature || !g_depth)
         return fail(SF_ERR_INVALID_ARG, "null buffer");
+    if (misaligned(depth, depth_bytes(c->depth_type)) || misaligned(g_normals, 4) || misaligned(g_offsets, 4) ||
+        misaligned(g_curvature, 4) || misaligned(g_depth, 4))
+        return fail(SF_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     if (c->method != SF_METHOD_DISPARITY && c->method != SF_METHOD_STANDARD)
         return fail(SF_ERR_UNSUPPORTED, "the backward covers the implicit fits only");
     if (c->constraint != SF_CONSTRAINT_UNIT3)
@@ -1085,14 +1125,7 @@ sf_status static_scratch_base(void** out) {
         if (e != cudaSuccess) return cuda_fail(e, "sf_fit_static: cudaGetSymbolAddress");
         const int IW = 128 + 2 * sf::kMaxR;
         const int smem = (int)(sizeof(int) * sf::kHThreads * (size_t)(IW | 1));
-        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_F32, SF_METHOD_DISPARITY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_F32, SF_METHOD_STANDARD>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_U16, SF_METHOD_DISPARITY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(sf::hpass_kernel<SF_DEPTH_U16, SF_METHOD_STANDARD>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        set_hpass_smem(smem);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "sf_fit_static: kernel attributes");
         g_static_base[dev] = p;
@@ -1108,6 +1141,9 @@ extern "C" sf_status sf_fit_static(const sf_intrinsics* K, int W, int H, int win
                                    float* normals, float* offsets, float* curvature, void* stream) {
     if (!K) return fail(SF_ERR_INVALID_ARG, "null intrinsics");
     if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
+    if (misaligned(depth, depth_type == SF_DEPTH_F32 ? 4 : 2) || misaligned(normals, 4) || misaligned(offsets, 4) ||
+        misaligned(curvature, 4))
+        return fail(SF_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     if (W < 1 || H < 1) return fail(SF_ERR_INVALID_ARG, "image size %dx%d must be positive", W, H);
     if (window < 1 || (window & 1) == 0 || window > SF_MAX_WINDOW)
         return fail(SF_ERR_INVALID_ARG, "window %d must be odd and in [1, %d]", window, SF_MAX_WINDOW);

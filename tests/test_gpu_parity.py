@@ -148,3 +148,36 @@ def test_host_api_matches_device(nfr, method):
     assert torch.equal(torch.nan_to_num(d0[1], 7.0), torch.nan_to_num(d2[1], 7.0))
     assert np.array_equal(np.nan_to_num(h1[1][::-1], nan=7.0), np.nan_to_num(d2[1].cpu().numpy(), nan=7.0))
     f.close()
+
+
+@pytest.mark.parametrize("depth_type", ["f32", "u16"])
+def test_unaligned_frame_bases(depth_type):
+    """Frames whose base is not 16-byte aligned (odd pixel counts, sliced batches) are read correctly,
+    and a buffer not aligned to its element size is rejected before any work."""
+    from paper_2103_06644_gb300 import SurfFitError, _native
+
+    W, H, k = 37, 23, 7  # 851 px: every frame of a stacked batch starts at a different 16-byte phase
+    intr = scenes.Intrinsics.scaled(W, H)
+    frames = []
+    for i in range(5):
+        z = scenes.kinect_frame(scenes.BASE_SEED + 60 + i, intr, W, H)
+        frames.append(np.where(z > 0, np.round(z * 1000.0), 0).astype(np.uint16) if depth_type == "u16" else z)
+    stack = np.stack(frames)
+    t = torch.from_numpy(stack.view(np.int16) if depth_type == "u16" else stack).cuda()
+    if depth_type == "u16":
+        t = t.view(torch.uint16)
+    f = SurfaceFitter(intr.as_tuple(), W, H, k, depth_type=depth_type)
+    out = f.fit(t[1:], counts=True)  # the slice starts 851 elements in
+    torch.cuda.synchronize()
+    for i in range(4):
+        ref = oracle.fit(frames[i + 1], intr.as_tuple(), k, "disparity", want_lambda=True, want_moments=True)
+        compare(tuple(o[i].cpu().numpy() for o in out), ref, label="frame %d of a sliced batch" % (i + 1))
+    n, d, c = (torch.empty((H, W, 3), device="cuda"), torch.empty((H, W), device="cuda"),
+               torch.empty((H, W), device="cuda"))
+    with pytest.raises(SurfFitError):
+        _native.check(_native.lib().sf_fit_ex(f._h, 1, t.data_ptr() + 1, n.data_ptr(), n.data_ptr(), n.data_ptr(),
+                                              None, None))
+    with pytest.raises(SurfFitError):
+        _native.check(_native.lib().sf_fit_ex(f._h, 1, t.data_ptr(), n.data_ptr() + 2, d.data_ptr(), c.data_ptr(),
+                                              None, None))
+    f.close()
