@@ -703,15 +703,18 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
     float* pc = curvature + oi;
     int32_t* pk = counts ? counts + oi : nullptr;
     float zc = load_depth<DT>(depth, oi, scale);
+    float tyn = tyt[y0];
     for (int y = y0; y < y1; ++y) {
         const bool cvalid = depth_valid(zc);
-        // issue the loads of the next slide (and the next centre depth) now:
-        // the solve below hides their latency
+        const float ty = tyn;
+        // issue the loads of the next slide (and the next centre depth and
+        // ray) now: the solve below hides their latency
         const bool more = y + 1 < y1;
         oi += W;
         if (more) {
             S.fetch(pb, kGroup, H, y, r);
             zc = load_depth<DT>(depth, oi, scale);
+            tyn = tyt[y + 1];
         }
         const int n = S.count();
         bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
@@ -719,17 +722,17 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
         FitOut fo_;
         if (ok) {
             if constexpr (M == SF_METHOD_DISPARITY)
-                fo_ = solve_disparity<float, U4>(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, tyt[y],
+                fo_ = solve_disparity<float, U4>(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty,
                                       a, b);
             else if constexpr (M == SF_METHOD_STANDARD)
                 fo_ = solve_standard<float, U4>((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
-                                     S.Szzii, q, tx, tyt[y], a, b);
+                                     S.Szzii, q, tx, ty, a, b);
             else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY)
                 fo_ = solve_explicit_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q,
-                                               tx, tyt[y], a, b, ok);
+                                               tx, ty, a, b, ok);
             else
                 fo_ = solve_explicit_standard((float)S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sz, S.Szj, S.Szi,
-                                              S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji, S.Szzii, q, tx, tyt[y], a, b,
+                                              S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji, S.Szzii, q, tx, ty, a, b,
                                               ok);
         }
         if (ok) {
