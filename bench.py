@@ -13,6 +13,7 @@ on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -60,9 +61,10 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons; `summary` keeps the samples
+    taken inside a host-time window (the timed region), else the two nearest ones."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -74,12 +76,17 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen([smi, "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # wait (up to 3 s) for the first sample, so that sampling covers what follows
+            t_end = time.time() + 3.0
+            while time.time() < t_end and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
 
-    def stop(self):
+    def stop(self, window=None):
         if self.proc is None:
             return None
+        time.sleep(0.1)  # one more sample after the region
         self.proc.send_signal(signal.SIGTERM)
         try:
             self.proc.wait(timeout=5)
@@ -89,17 +96,29 @@ class ClockSampler:
         with open(self.path) as f:
             for line in f:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) >= 10:
+                    try:
+                        t = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    except ValueError:
+                        continue
+                    rows.append((t, parts[1:]))
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        inside = rows
+        if window is not None:
+            inside = [r for r in rows if window[0] <= r[0] <= window[1]]
+            if not inside:
+                mid = 0.5 * (window[0] + window[1])
+                inside = sorted(rows, key=lambda r: abs(r[0] - mid))[:2]
+        sel = [r[1] for r in inside]
+        sm = [float(r[1]) for r in sel if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in sel if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in sel for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(sel),
+                "samples_in_timed_region": len([r for r in rows if window and window[0] <= r[0] <= window[1]])}
 
 
 def cpu_oracle_sample(time_budget_s: float = 15.0):
@@ -202,7 +221,8 @@ def precision_report(group, dev):
         n, o, c = [t.cpu().numpy().astype(np.float64) for t in f.fit(d)]
         torch.cuda.synchronize()
         ent = {}
-        for name, gmin in (("gamma>=1e-3", 1e-3), ("gamma>=1e-5", 1e-5)):
+        for name, gmin in (("gamma>=1e-2", 1e-2), ("gamma>=1e-3", 1e-3), ("gamma>=1e-4", 1e-4),
+                           ("gamma>=1e-5", 1e-5)):
             sel = ok & (gap >= gmin)
             a, b = n[sel], ref["normals"][sel]
             ang = np.arctan2(np.linalg.norm(np.cross(a, b), axis=-1), np.sum(a * b, -1))
@@ -327,7 +347,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -398,8 +418,10 @@ def main():
     for f in fitters:
         f.profile(True)
     sampler = ClockSampler(local)
+    t_region = [time.time(), 0.0]
     ms = timed(args.steps, step)
-    clocks = sampler.stop()
+    t_region[1] = time.time()
+    clocks = sampler.stop(t_region)
     prof = {}
     for f in fitters:
         for stage, (t, n) in f.profile_read().items():

@@ -127,8 +127,8 @@ sf_status sf_set_params(sf_ctx* ctx, int method, int depth_type, float depth_sca
  * when D == 0 or its 1/Z <= 0.
  * Errors: SF_ERR_INVALID_ARG unless alpha is finite and nonzero and
  * |128 beta / alpha| <= 2^23; a later disparity-form fit rejects a model
- * whose largest value 128 * 65535 + |round(128 beta / alpha)| times
- * max(k, r (r + 1)) (k the window, r = (k - 1)/2) reaches 2^31.
+ * whose largest value 128 * 65535 + |round(128 beta / alpha)| times the
+ * window size k reaches 2^31.
  * Default: alpha = 1, beta = 0.
  */
 sf_status sf_set_disparity_model(sf_ctx* ctx, double alpha, double beta);

@@ -251,7 +251,8 @@ __global__ void __launch_bounds__(256, 8) range_kernel(const void* __restrict__ 
 // ---------------------------------------------------------------------------
 // Disparity planes, each a block of n_frames * plane_elems entries, in order:
 //   hm int32 packed mask moments: count | (sum j + 512) << 6 | sum j^2 << 16
-//   g0 int64 sum w,  g1 int64 sum w j,  q0 int64 sum w^2
+//   g0 int32 sum w,  g1 int32 low 32 bits of sum w j (high part in hm),
+//   q0 int64 sum w^2
 // Standard planes:
 //   hc int32 count, z0 int64 sum z, z1 int64 sum z j,
 //   b0 int64 sum z^2, b1 int64 sum z^2 j, b2 int64 sum z^2 j^2
@@ -281,15 +282,27 @@ struct Planes {
     __device__ __forceinline__ int64_t* c64(int c) const { return p64 + (size_t)c * stride; }
 };
 
-__device__ __forceinline__ int32_t pack_mask(int h0, int h1, int h2) {
-    return h0 | ((h1 + 512) << 6) | (h2 << 16);
+// Packed per-row word: count (bits 0-4, <= 31), sum j + 512 (bits 5-14), sum
+// j^2 (bits 15-26, <= 2480 for r <= 15) and, for the disparity form, the high
+// part hi (bits 27-31, signed) of the row sum of w j, whose low 32 bits are
+// stored in their own plane: sum w j = hi 2^32 + (uint32) lo (|sum w j| <
+// 2^34 by the choice of fixed-point bits).  A row without valid pixels has
+// the word kEmptyMask, never 0 (0 marks a row outside the image).
+__device__ __forceinline__ int32_t pack_mask(int h0, int h1, int h2, int hi = 0) {
+    return (int32_t)((uint32_t)h0 | ((uint32_t)(h1 + 512) << 5) | ((uint32_t)h2 << 15) | ((uint32_t)hi << 27));
 }
 // the packed mask moments of a row without valid pixels (every field zero)
-constexpr int32_t kEmptyMask = 512 << 6;
+constexpr int32_t kEmptyMask = 512 << 5;
 __device__ __forceinline__ void unpack_mask(int32_t v, int& h0, int& h1, int& h2) {
-    h0 = v & 63;
-    h1 = ((v >> 6) & 1023) - 512;
-    h2 = (int)((uint32_t)v >> 16);
+    h0 = v & 31;
+    h1 = ((v >> 5) & 1023) - 512;
+    h2 = (v >> 15) & 4095;
+}
+__device__ __forceinline__ int mask_hi(int32_t v) { return v >> 27; }
+__device__ __forceinline__ int32_t lo32(int64_t v) { return (int32_t)(uint32_t)((uint64_t)v & 0xffffffffull); }
+// the row sum of w j from its high part (in the packed word) and low 32 bits
+__device__ __forceinline__ int64_t join_wj(int32_t word, int32_t lo) {
+    return ((int64_t)mask_hi(word) << 32) + (int64_t)(uint32_t)lo;
 }
 
 // Running sums of c, c*j, c*j^2 over j in [-r, r] slide by one column with
@@ -354,14 +367,16 @@ __device__ __forceinline__ void load_tile(const void* __restrict__ depth, int W,
 
 // Running horizontal sums of one row over one 32-column output segment:
 // mask moments (count, sum j, sum j^2) and value moments.  The disparity
-// form's row sums of v and v j fit 31 bits (the fixed-point bits are chosen
-// so): they slide in 32-bit unsigned arithmetic, exact modulo 2^32, which the
-// stored int32 values are.
+// form's row sum of v fits 31 bits (the fixed-point bits are chosen so): it
+// slides in 32-bit unsigned arithmetic, exact modulo 2^32, which the stored
+// int32 value is; its row sum of v j is exact in 64 bits and stored split
+// (low 32 bits in a plane, the high part in the packed mask word).
 template <int M>
 struct HRowState {
     using Acc = typename std::conditional<base_method(M) == SF_METHOD_DISPARITY, uint32_t, int64_t>::type;
     int h0 = 0, h1 = 0, h2 = 0;
-    Acc a0 = 0, a1 = 0;              // sum v, sum v j
+    Acc a0 = 0;                      // sum v
+    int64_t a1 = 0;                  // sum v j
     int64_t s0 = 0, s1 = 0, s2 = 0;  // sum v^2, sum v^2 j, sum v^2 j^2 (s1, s2: standard only)
     // window of output column x0: tile columns x0 - xt .. x0 - xt + 2r
     __device__ __forceinline__ void init(const int* row, int c0, int r) {
@@ -370,7 +385,7 @@ struct HRowState {
             if (v >= 0) {
                 const int64_t vv = (int64_t)v * v;
                 h0 += 1; h1 += j; h2 += j * j;
-                a0 += (Acc)v; a1 += (Acc)((int64_t)v * j);
+                a0 += (Acc)v; a1 += (int64_t)v * j;
                 s0 += vv;
                 if (base_method(M) == SF_METHOD_STANDARD) { s1 += vv * j; s2 += vv * (j * j); }
             }
@@ -383,7 +398,8 @@ struct HRowState {
         const int mo = vo >= 0, mi = vi >= 0;
         slide3(h0, h1, h2, mo, mi, r);
         const int64_t co = mo ? vo : 0, ci = mi ? vi : 0;
-        slide2(a0, a1, (Acc)co, (Acc)ci, r);
+        a0 = a0 - (Acc)co + (Acc)ci;
+        a1 = a1 + (int64_t)r * co + (int64_t)(r + 1) * ci - (int64_t)a0;
         const int64_t qo = co * co, qi = ci * ci;
         if (base_method(M) == SF_METHOD_STANDARD) slide3(s0, s1, s2, qo, qi, r);
         else s0 = s0 - qo + qi;
@@ -408,12 +424,13 @@ __device__ __forceinline__ void hpass_row(const int* row, int x0, int xend, int 
             const int xe = min(x0 + (l + 1) * kSub, xend);
             if (xs >= xe) continue;
             int32_t hmv[4];
-            typename HRowState<M>::Acc c0v[4], c1v[4];
-            int64_t c2v[4], c3v[4], c4v[4];
+            typename HRowState<M>::Acc c0v[4];
+            int64_t c1v[4], c2v[4], c3v[4], c4v[4];
             HRowState<M>& S = st[l];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                hmv[u] = pack_mask(S.h0, S.h1, S.h2);
+                hmv[u] = pack_mask(S.h0, S.h1, S.h2,
+                                   base_method(M) == SF_METHOD_DISPARITY ? (int)(S.a1 >> 32) : 0);
                 c0v[u] = S.a0; c1v[u] = S.a1; c2v[u] = S.s0; c3v[u] = S.s1; c4v[u] = S.s2;
                 if (xs + u + 1 < xe) S.step(row, xs + u - x0, r);
             }
@@ -423,15 +440,15 @@ __device__ __forceinline__ void hpass_row(const int* row, int x0, int xend, int 
                     *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
                     *reinterpret_cast<int4*>(P.c32(1) + o) =
                         make_int4((int)c0v[0], (int)c0v[1], (int)c0v[2], (int)c0v[3]);
-                    *reinterpret_cast<int4*>(P.c32(2) + o) =
-                        make_int4((int)c1v[0], (int)c1v[1], (int)c1v[2], (int)c1v[3]);
+                    *reinterpret_cast<int4*>(P.c32(2) + o) = make_int4(lo32(c1v[0]), lo32(c1v[1]), lo32(c1v[2]),
+                                                                       lo32(c1v[3]));
                     int64_t* q0 = P.c64(0) + o;
                     *reinterpret_cast<longlong2*>(q0) = make_longlong2(c2v[0], c2v[1]);
                     *reinterpret_cast<longlong2*>(q0 + 2) = make_longlong2(c2v[2], c2v[3]);
                 } else {
                     for (int u = 0; u < 4 && xs + u < xe; ++u) {
                         P.p32[o + u] = hmv[u];
-                        P.c32(1)[o + u] = (int)c0v[u]; P.c32(2)[o + u] = (int)c1v[u];
+                        P.c32(1)[o + u] = (int)c0v[u]; P.c32(2)[o + u] = lo32(c1v[u]);
                         P.c64(0)[o + u] = c2v[u];
                     }
                 }
@@ -545,7 +562,7 @@ struct DispState {
                 unpack_mask(hv[u], c0, c1, c2);
                 const float f0 = (float)c0, f1 = (float)c1, fi = (float)i;
                 n += f0; Sj += f1; Sjj += (float)c2; Si += fi * f0; Sji += fi * f1; Sii += fi * fi * f0;
-                Sw += av[u]; Swj += bv[u]; Swi += (int64_t)i * av[u]; Sww += qv[u];
+                Sw += av[u]; Swj += join_wj(hv[u], bv[u]); Swi += (int64_t)i * av[u]; Sww += qv[u];
             }
         }
     }
@@ -553,7 +570,7 @@ struct DispState {
     // (leaving row y - r, entering row y + r + 1; zero outside the image).
     // fetch() only issues the loads, so a caller can overlap them with the
     // solve of row y and apply() them afterwards.
-    int32_t pm_o = 0, pm_i = 0, pwo = 0, pwjo = 0, pwi = 0, pwji = 0;
+    int32_t pm_o = 0, pm_i = 0, pwo = 0, pwi = 0, pwjo = 0, pwji = 0;
     int64_t pwwo = 0, pwwi = 0;
     __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) {
         const int yo = y - r, yi = y + r + 1;
@@ -578,7 +595,7 @@ struct DispState {
         slide2(Sj, Sji, (float)o1, (float)i1, r);
         Sjj += (float)(i2 - o2);
         slide2(Sw, Swi, (int64_t)pwo, (int64_t)pwi, r);
-        Swj += (int64_t)pwji - pwjo;
+        Swj += join_wj(pm_i, pwji) - join_wj(pm_o, pwjo);
         Sww += pwwi - pwwo;
     }
     // slide from output row y to y + 1
@@ -850,8 +867,10 @@ __global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc*
     }
 }
 
+// One block fewer per SM than vpass_kernel: the claim loop's state stays live
+// across the column calls, and at 80 registers the calls would spill.
 template <int DT, int M>
-__global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_batch_kernel(const FrameDesc* __restrict__ descs,
+__global__ void __launch_bounds__(kVThreads, kVBlocks - 1) vpass_batch_kernel(const FrameDesc* __restrict__ descs,
                                                                 const int3* __restrict__ items, int n_items,
                                                                 unsigned* __restrict__ counter,
                                                                 const unsigned* __restrict__ vmax_bits,

@@ -64,9 +64,10 @@ int quant_bits(int method, int k) {
     }
     int b = (int)std::floor((63.0 - std::log2(weight)) / 2.0 - 1e-9);
     if (sf::base_method(method) == SF_METHOD_DISPARITY) {
-        // the row sums of v and v j are stored as int32: k 2^b and r (r + 1) 2^b < 2^31
+        // the row sums of v are stored as int32: k 2^b < 2^31; those of v j
+        // as 32 + 5 bits: r (r + 1) 2^b < 2^36
         b = std::min(b, (int)std::floor(31.0 - std::log2((double)k) - 1e-9));
-        b = std::min(b, (int)std::floor(31.0 - std::log2((double)std::max(1, r * (r + 1))) - 1e-9));
+        b = std::min(b, (int)std::floor(36.0 - std::log2((double)std::max(1, r * (r + 1))) - 1e-9));
     }
     return std::min(28, std::max(16, b));
 }
@@ -517,9 +518,9 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
     if (c->constraint == SF_CONSTRAINT_UNIT4 && c->method != SF_METHOD_DISPARITY && c->method != SF_METHOD_STANDARD)
         return fail(SF_ERR_UNSUPPORTED, "the |(a,b,c,d)| = 1 constraint applies to the implicit fits");
     if (c->depth_type == SF_DEPTH_DISPARITY_U16 && sf::base_method(c->method) == SF_METHOD_DISPARITY) {
-        // the disparity integers go into the int32 row sums unscaled: k w and r (r + 1) w < 2^31
+        // the disparity integers go into the int32 row sums unscaled: k w < 2^31
         const double wmax = 128.0 * 65535.0 + std::fabs((double)c->disp_add);
-        if (wmax * std::max(c->k, std::max(1, c->r * (c->r + 1))) >= 2147483648.0)
+        if (wmax * c->k >= 2147483648.0)
             return fail(SF_ERR_INVALID_ARG, "disparity model offset too large for a %d x %d window", c->k, c->k);
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1004,7 +1005,6 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
     }
     b->n_h = (int)hitems.size();
     b->n_v = (int)vitems.size();
-    const int n64 = method == SF_METHOD_STANDARD ? 5 : 3;
     cudaError_t e = cudaMalloc(&b->d_rays, sizeof(float) * std::max<size_t>(rays, 1));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_rays, hr.data(), sizeof(float) * rays, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
@@ -1021,7 +1021,7 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
     if (e == cudaSuccess) e = cudaMemcpy(b->d_vitems, vitems.data(), sizeof(int3) * vitems.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_vmax, sizeof(unsigned) * n_frames);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_planes, stride * (4 + 8 * (size_t)n64));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_planes, plane_bytes_per_frame(method, stride));
     if (e != cudaSuccess) { sf_batch_destroy(b); return fail(SF_ERR_ALLOC, "batch buffers: %s", cudaGetErrorString(e)); }
     b->hsmem = sizeof(int) * sf::kHThreads * (size_t)((max_seg + 2 * max_r) | 1);
     int dev = 0, sms = 152;
