@@ -331,14 +331,14 @@ __device__ __forceinline__ void slide2(T& S0, T& S1, T out, T in, int r) {
 // ---------------------------------------------------------------------------
 // Load and quantise the raw depth of a horizontal tile into shared memory:
 // rows [y0, y0 + rows), columns [x0 - r, x0 - r + IW), at row pitch `pitch`.
-// Warp w takes rows w, w + 4, ...; lanes sweep a row (coalesced).  Four rows x
-// CHUNKS 32-column chunks are loaded before any is used, so 4 * CHUNKS loads
+// Warp w takes rows w, w + 4, ...; lanes sweep a row (coalesced).  Eight rows x
+// CHUNKS 32-column chunks are loaded before any is used, so 8 * CHUNKS loads
 // per thread are in flight at once (issue is in order: a load consumed right
 // away would expose its whole latency).
 template <int DT, int M, int CHUNKS>
 __device__ __forceinline__ void load_tile(const void* __restrict__ depth, int W, int r, float sc, const Codec& cd,
                                           int x0, int y0, int rows, int IW, int pitch, int* tile) {
-    constexpr int kRowsPerBatch = 4;
+    constexpr int kRowsPerBatch = 8;
     constexpr int kWarps = kHThreads / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int rb = warp; rb < rows; rb += kWarps * kRowsPerBatch) {

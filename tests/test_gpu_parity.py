@@ -181,3 +181,32 @@ def test_unaligned_frame_bases(depth_type):
         _native.check(_native.lib().sf_fit_ex(f._h, 1, t.data_ptr(), n.data_ptr() + 2, d.data_ptr(), c.data_ptr(),
                                               None, None))
     f.close()
+
+
+@pytest.mark.parametrize("method", ["disparity", "explicit_disparity"])
+def test_row_sums_beyond_32_bits(method):
+    """A near surface (0.3 m) beside missing pixels: the row sums of w j reach ~2^33 at k = 31, so their
+    high part (packed with the mask moments) is nonzero; results must still match the oracle."""
+    W, H, k = 160, 96, 31
+    intr = scenes.Intrinsics.scaled(W, H)
+    rng = np.random.Generator(np.random.PCG64(scenes.BASE_SEED + 71))
+    x = np.arange(W)[None, :]
+    y = np.arange(H)[:, None]
+    depth = (0.3 + 0.0004 * x + 0.0003 * y + rng.normal(0.0, 2e-5, (H, W))).astype(np.float32)
+    depth[:, W // 2:] = 0.0                       # missing right half
+    depth[H // 3: H // 3 + 4, :] = 9.5            # a far strip sets the quantum's dynamic range
+    depth[H // 3: H // 3 + 4, W // 2:] = 0.0
+    ref = oracle.fit(depth, intr.as_tuple(), k, method, want_lambda=True, want_moments=True)
+    # the largest |row sum of w j| in fixed-point units (26 bits at k = 31): beyond int32
+    wq = np.where(depth > 0, 1.0 / np.where(depth > 0, depth, 1.0), 0.0)
+    wq = wq / wq.max() * 2.0 ** 26
+    r = k // 2
+    j = np.arange(-r, r + 1)
+    rows = np.array([[np.dot(wq[yy, xx - r: xx + r + 1], j) for xx in range(r, W - r)] for yy in range(0, H, 8)])
+    assert np.abs(rows).max() > 2.0 ** 32
+    gpu = run_gpu(depth, intr.as_tuple(), k, method)
+    if method == "disparity":
+        compare(gpu, ref, label="near surface beside missing pixels")
+    else:
+        from parity import compare_explicit
+        compare_explicit(gpu, ref, method, label="near surface beside missing pixels (explicit)")
