@@ -261,19 +261,45 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(stage: str):
-    """DRAM bytes per launch of a stage's kernel from the committed ncu launch summary, or None
-    when that capture was taken on other kernel sources (or is missing)."""
+def _profile_record(name: str, stage: str, field: str):
+    """A per-launch figure of a stage's kernel from the committed ncu launch summary
+    (`<name>: kernel=K sources=HASH <field>=N`), or None when that capture was taken on other kernel
+    sources (or is missing)."""
     kern = STAGE_KERNEL.get(stage)
     try:
         with open(PROFILE_LAUNCHES) as fh:
             text = fh.read()
     except OSError:
         return None
-    m = re.search(r"traffic_record: kernel=%s sources=([0-9a-f]+) bytes_per_launch=(\d+)" % kern, text)
+    m = re.search(r"%s: kernel=%s sources=([0-9a-f]+) %s=(\d+)" % (name, kern, field), text)
     if not m or m.group(1) != kernel_source_hash():
         return None
     return int(m.group(2))
+
+
+def recorded_traffic(stage: str):
+    """DRAM bytes (read + write) per launch of a stage's kernel, from ncu."""
+    return _profile_record("traffic_record", stage, "bytes_per_launch")
+
+
+def recorded_instructions(stage: str):
+    """Thread instructions executed per launch of a stage's kernel, from ncu."""
+    return _profile_record("instr_record", stage, "thread_inst_per_launch")
+
+
+def issue_roofline(stage: str, launch_ms: float, clocks, sms: int):
+    """The stage's kernel against instruction issue: executed thread instructions (ncu count per
+    launch) / CUDA-event launch time, against SMs x 4 schedulers x 32 lanes x SM clock (one warp
+    instruction per scheduler per cycle).  None without a matching ncu record."""
+    inst = recorded_instructions(stage)
+    if inst is None or launch_ms <= 0:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = sms * 128 * mhz * 1e6 / 1e12
+    achieved = inst / (launch_ms / 1000.0) / 1e12
+    return {"bound": "alu", "kernel": stage, "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+            "frac": achieved / peak, "thread_inst_per_launch": inst, "sm_mhz": mhz, "sms": sms,
+            "peak_source": "SMs x 128 lanes x sampled SM clock"}
 
 
 def rank_max(x: float, world: int, device) -> float:
@@ -449,6 +475,8 @@ def main():
                      "frac": achieved / peak, "peak_source": peak_kind, "traffic": recorded_traffic(dom),
                      "algorithmic_bytes_per_pixel": BYTES_PER_PIXEL,
                      "stage_ms_per_step": {s: v[0] / args.steps for s, v in prof.items()}},
+        "issue_roofline": issue_roofline(dom, dom_avg_ms, clocks,
+                                         torch.cuda.get_device_properties(dev).multi_processor_count),
         "path_hbm_frac": BYTES_PER_PIXEL * total_px / (ms / 1000.0) / 1e9 / peak,
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clocks,
