@@ -63,15 +63,22 @@ def test_clock_sampler_window_without_samples_falls_back_to_the_nearest(fake_smi
     assert out["samples_in_timed_region"] == 0 and out["samples"] == 2
 
 
-def test_profile_records_follow_the_kernel_sources(monkeypatch):
-    # the committed launch summary matches the committed kernel sources
-    assert bench.recorded_traffic("vpass_solve") is not None
-    assert bench.recorded_instructions("vpass_solve") is not None
+def test_profile_records_follow_the_kernel_sources(monkeypatch, tmp_path):
+    h = bench.kernel_source_hash()
+    rec = tmp_path / "launches.md"
+    rec.write_text("text\n\ntraffic_record: kernel=vpass sources=%s bytes_per_launch=1341341952\n"
+                   "instr_record: kernel=vpass sources=%s thread_inst_per_launch=9715365121\n" % (h, h))
+    monkeypatch.setattr(bench, "PROFILE_LAUNCHES", str(rec))
+    assert bench.recorded_traffic("vpass_solve") == 1341341952
+    assert bench.recorded_instructions("vpass_solve") == 9715365121
+    assert bench.recorded_traffic("hpass") is None  # no record for that kernel
     # any other source hash (a kernel changed since the capture) voids them
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
     assert bench.recorded_traffic("vpass_solve") is None
     assert bench.recorded_instructions("vpass_solve") is None
     assert bench.issue_roofline("vpass_solve", 0.35, {"sm_mhz": 2070.0}, 152) is None
+    monkeypatch.setattr(bench, "PROFILE_LAUNCHES", str(tmp_path / "missing.md"))
+    assert bench.recorded_traffic("vpass_solve") is None
 
 
 def test_issue_roofline_arithmetic(monkeypatch):
