@@ -188,7 +188,8 @@ sf_status sf_fit_ex(sf_ctx* ctx, int n_frames, const void* depth, float* normals
                     int32_t* counts, void* stream);
 
 /*
- * sf_fit_host -- sf_fit_ex on HOST buffers (ordinary pageable memory): the
+ * sf_fit_host -- sf_fit_ex on HOST buffers (pageable or page-locked memory;
+ * page-locked buffers let the copies run as DMA in both directions): the
  * frames go through in up to four chunks on two context-owned streams, the
  * copy-out of one chunk overlapping the copy-in and fit of the next, with
  * copies straight between the caller's buffers and two device staging
