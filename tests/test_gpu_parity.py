@@ -210,3 +210,30 @@ def test_row_sums_beyond_32_bits(method):
     else:
         from parity import compare_explicit
         compare_explicit(gpu, ref, method, label="near surface beside missing pixels (explicit)")
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard", "explicit_disparity", "explicit_standard"])
+def test_tile_shapes_do_not_change_results(method):
+    """Every horizontal tile width (32, 64, 128 columns: one kernel each) and vertical band height gives
+    bit-identical results: the window sums are exact integers whatever the tiling."""
+    W, H, k = 300, 170, 15
+    intr = scenes.Intrinsics.scaled(W, H)
+    depth = scenes.kinect_frame(scenes.BASE_SEED + 91, intr, W, H)
+    t = torch.from_numpy(np.stack([depth, depth[::-1].copy()])).cuda()
+    f = SurfaceFitter(intr.as_tuple(), W, H, k, method=method)
+    base = [x.clone() for x in f.fit(t, counts=True)]
+    for hseg, vband in [(64, 0), (128, 0), (32, 8), (64, 48), (128, 1024)]:
+        f.set_tiles(hseg, vband)
+        out = f.fit(t, counts=True)
+        torch.cuda.synchronize()
+        for a, b in zip(base, out):
+            assert torch.equal(torch.nan_to_num(a.float(), nan=7.0), torch.nan_to_num(b.float(), nan=7.0)), \
+                (method, hseg, vband)
+    f.close()
+    ref = oracle.fit(depth, intr.as_tuple(), k, method, want_lambda=True, want_moments=True)
+    gpu = tuple(x[0].cpu().numpy() for x in base)
+    if method.startswith("explicit"):
+        from parity import compare_explicit
+        compare_explicit(gpu, ref, method, label="tiles " + method)
+    else:
+        compare(gpu, ref, label="tiles " + method)
