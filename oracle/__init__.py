@@ -51,6 +51,9 @@ def _load():
         lib.sfo_fit.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_int, dp, dp, dp, ip, dp, dp, ctypes.c_int]
         lib.sfo_fit.restype = ctypes.c_int
+        lib.sfo_fit_delta.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, ip, dp, dp, ctypes.c_int]
+        lib.sfo_fit_delta.restype = ctypes.c_int
         lib.sfo_backward.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, dp, dp, dp, dp, ctypes.c_int]
         lib.sfo_backward.restype = ctypes.c_int
@@ -96,13 +99,15 @@ def depth_from_disparity(D: np.ndarray, alpha: float, beta: float) -> np.ndarray
 
 def fit(depth: np.ndarray, intr: Sequence[float], k: int, method: str = "disparity", *, unit4: bool = False,
         min_valid: int = 3, require_center: bool = True, depth_scale: float = 1e-3, want_lambda: bool = False,
-        want_moments: bool = False, threads: int = 0) -> Dict[str, np.ndarray]:
+        want_moments: bool = False, threads: int = 0, delta=None) -> Dict[str, np.ndarray]:
     """Run the FP64 oracle on one [H, W] depth image.
 
     Returns a dict with ``normals`` [H,W,3], ``offsets`` [H,W], ``curvature``
     [H,W] (FP64, NaN where the validity rule fails), ``counts`` [H,W] int32
     and optionally ``lam`` [H,W,3] (eigenvalues of R, ascending) and
     ``moments`` [H,W,10] (A11 A12 A13 A22 A23 A33 g1 g2 g3 s).
+    ``delta`` = (ddx, ddy), per-pixel adjustments [H, W] in pixels added to
+    the intrinsics' (dx, dy) in the rays of Eq. 1 / Eq. 10, or None.
     """
     lib = _load()
     Z = np.ascontiguousarray(depth_to_f64(depth, depth_scale))
@@ -115,10 +120,18 @@ def fit(depth: np.ndarray, intr: Sequence[float], k: int, method: str = "dispari
     counts = np.empty((H, W), dtype=np.int32)
     lam = np.empty((H, W, 3)) if want_lambda else None
     mom = np.empty((H, W, 10)) if want_moments else None
-    rc = lib.sfo_fit(_dp(Z), W, H, _dp(it), int(k), METHODS[method], int(unit4), int(min_valid),
-                     int(require_center), _dp(normals), _dp(offsets), _dp(curv),
-                     counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                     _dp(lam) if lam is not None else None, _dp(mom) if mom is not None else None, int(threads))
+    if delta is None:
+        ddx = ddy = None
+    else:
+        ddx, ddy = (np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in delta)
+        if ddx.shape != (H, W) or ddy.shape != (H, W):
+            raise ValueError("delta tables must be [H, W]")
+    rc = lib.sfo_fit_delta(_dp(Z), W, H, _dp(it), _dp(ddx) if ddx is not None else None,
+                           _dp(ddy) if ddy is not None else None, int(k), METHODS[method], int(unit4),
+                           int(min_valid), int(require_center), _dp(normals), _dp(offsets), _dp(curv),
+                           counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                           _dp(lam) if lam is not None else None, _dp(mom) if mom is not None else None,
+                           int(threads))
     if rc != 0:
         raise ValueError("oracle rejected its arguments (rc=%d)" % rc)
     out = {"normals": normals, "offsets": offsets, "curvature": curv, "counts": counts}

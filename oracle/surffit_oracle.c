@@ -137,9 +137,12 @@ static inline int valid_depth(double z) { return isfinite(z) && z > 0.0; }
 /* Direct sums of the method's monomials over the valid pixels of the box
  * [xa, xb] x [ya, yb] (inclusive, clipped to the image).
  * A: 3x3, g: 3, s: scalar; also bb = sum b^2 (explicit fits only); pm: the
- * pixel offsets from the reference pixel (px, py), NULL allowed. */
-static int box_sums(const double* Z, int W, int H, const double* intr, int method, int xa, int xb, int ya,
-                    int yb, int px, int py, double A[3][3], double g[3], double* s, double* bb, int64_t pm[5]) {
+ * pixel offsets from the reference pixel (px, py), NULL allowed.
+ * ddx, ddy: per-pixel adjustments [H][W] added to (dx, dy) in the rays of
+ * Eq. 1 / Eq. 10, or NULL (constant dx, dy only). */
+static int box_sums(const double* Z, int W, int H, const double* intr, const double* ddx, const double* ddy,
+                    int method, int xa, int xb, int ya, int yb, int px, int py, double A[3][3], double g[3],
+                    double* s, double* bb, int64_t pm[5]) {
     const double fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3], dx = intr[4], dy = intr[5];
     memset(A, 0, 9 * sizeof(double));
     g[0] = g[1] = g[2] = 0.0;
@@ -148,12 +151,14 @@ static int box_sums(const double* Z, int W, int H, const double* intr, int metho
     if (pm) pm[0] = pm[1] = pm[2] = pm[3] = pm[4] = 0;
     for (int y = ya; y <= yb; ++y) {
         if (y < 0 || y >= H) continue;
-        const double ty = (y + dy - cy) / fy;
+        const double ty0 = (y + dy - cy) / fy;
         for (int x = xa; x <= xb; ++x) {
             if (x < 0 || x >= W) continue;
-            const double z = Z[(size_t)y * W + x];
+            const size_t q = (size_t)y * W + x;
+            const double z = Z[q];
             if (!valid_depth(z)) continue;
-            const double tx = (x + dx - cx) / fx;
+            const double tx = ddx ? (x + dx + ddx[q] - cx) / fx : (x + dx - cx) / fx;
+            const double ty = ddy ? (y + dy + ddy[q] - cy) / fy : ty0;
             double u[3];
             double wgt, b;
             if (method == M_DISPARITY || method == M_EXPLICIT_DISPARITY) {
@@ -185,9 +190,10 @@ static int box_sums(const double* Z, int W, int H, const double* intr, int metho
 }
 
 /* Direct window sums over V(p): the k x k box centred on p. */
-static int window_sums(const double* Z, int W, int H, const double* intr, int r, int method,
-                       int px, int py, double A[3][3], double g[3], double* s, double* bb, int64_t pm[5]) {
-    return box_sums(Z, W, H, intr, method, px - r, px + r, py - r, py + r, px, py, A, g, s, bb, pm);
+static int window_sums(const double* Z, int W, int H, const double* intr, const double* ddx, const double* ddy,
+                       int r, int method, int px, int py, double A[3][3], double g[3], double* s, double* bb,
+                       int64_t pm[5]) {
+    return box_sums(Z, W, H, intr, ddx, ddy, method, px - r, px + r, py - r, py + r, px, py, A, g, s, bb, pm);
 }
 
 /* Solve the 3x3 symmetric system A x = g in FP64 by Gaussian elimination with
@@ -289,12 +295,13 @@ static int fit_sums(int method, int unit4, double A[3][3], const double g[3], do
 }
 
 /* Steps 1-6 of the header for the window of pixel (px, py); results go to output slot o. */
-static void fit_pixel(const double* Z, int W, int H, const double* intr, int r, int method, int unit4, int min_valid,
-                      int require_center, int px, int py, size_t o, double* normals, double* offsets, double* curv,
-                      int32_t* counts, double* lam, double* moments) {
+static void fit_pixel(const double* Z, int W, int H, const double* intr, const double* ddx, const double* ddy, int r,
+                      int method, int unit4, int min_valid, int require_center, int px, int py, size_t o,
+                      double* normals, double* offsets, double* curv, int32_t* counts, double* lam,
+                      double* moments) {
     double A[3][3], g[3], s, bb;
     int64_t pm[5];
-    int n = window_sums(Z, W, H, intr, r, method, px, py, A, g, &s, &bb, pm);
+    int n = window_sums(Z, W, H, intr, ddx, ddy, r, method, px, py, A, g, &s, &bb, pm);
     if (counts) counts[o] = n;
     if (moments) {
         double* mo = moments + o * 10;
@@ -330,10 +337,23 @@ static void fit_pixel(const double* Z, int W, int H, const double* intr, int r, 
  *   moments  optional [H*W*10]: A11 A12 A13 A22 A23 A33 g1 g2 g3 s
  * Returns 0 on success, -1 on bad arguments.
  */
+int sfo_fit_delta(const double* Z, int W, int H, const double* intr, const double* ddx, const double* ddy, int k,
+                  int method, int unit4, int min_valid, int require_center, double* normals, double* offsets,
+                  double* curv, int32_t* counts, double* lam, double* moments, int nthreads);
+
 int sfo_fit(const double* Z, int W, int H, const double* intr, int k, int method, int unit4,
             int min_valid, int require_center, double* normals, double* offsets, double* curv,
             int32_t* counts, double* lam, double* moments, int nthreads) {
-    if (!Z || W <= 0 || H <= 0 || !intr || k < 1 || (k & 1) == 0 || method < 0 || method > 3)
+    return sfo_fit_delta(Z, W, H, intr, NULL, NULL, k, method, unit4, min_valid, require_center, normals, offsets,
+                         curv, counts, lam, moments, nthreads);
+}
+
+/* sfo_fit with per-pixel ray adjustments ddx, ddy [H*W] (pixels, added to
+ * intr's dx, dy in Eq. 1 / Eq. 10), or NULL for none. */
+int sfo_fit_delta(const double* Z, int W, int H, const double* intr, const double* ddx, const double* ddy, int k,
+                  int method, int unit4, int min_valid, int require_center, double* normals, double* offsets,
+                  double* curv, int32_t* counts, double* lam, double* moments, int nthreads) {
+    if (!Z || W <= 0 || H <= 0 || !intr || k < 1 || (k & 1) == 0 || method < 0 || method > 3 || (!ddx != !ddy))
         return -1;
     const int r = (k - 1) / 2;
 #ifdef _OPENMP
@@ -342,8 +362,8 @@ int sfo_fit(const double* Z, int W, int H, const double* intr, int k, int method
 #endif
     for (int py = 0; py < H; ++py)
         for (int px = 0; px < W; ++px)
-            fit_pixel(Z, W, H, intr, r, method, unit4, min_valid, require_center, px, py, (size_t)py * W + px,
-                      normals, offsets, curv, counts, lam, moments);
+            fit_pixel(Z, W, H, intr, ddx, ddy, r, method, unit4, min_valid, require_center, px, py,
+                      (size_t)py * W + px, normals, offsets, curv, counts, lam, moments);
     return 0;
 }
 
@@ -364,7 +384,7 @@ int sfo_fit_at(const double* Z, int W, int H, const double* intr, int k, int met
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
     for (int i = 0; i < npix; ++i)
-        fit_pixel(Z, W, H, intr, r, method, unit4, min_valid, require_center, xy[2 * i], xy[2 * i + 1], (size_t)i,
+        fit_pixel(Z, W, H, intr, NULL, NULL, r, method, unit4, min_valid, require_center, xy[2 * i], xy[2 * i + 1], (size_t)i,
                   normals, offsets, curv, counts, lam, moments);
     return 0;
 }
@@ -390,7 +410,7 @@ int sfo_fit_rect(const double* Z, int W, int H, const double* intr, int x0, int 
         return -1;
     double A[3][3], g[3], s, bb;
     int64_t pm[5];
-    int n = box_sums(Z, W, H, intr, method, x0, x0 + w - 1, y0, y0 + h - 1, x0, y0, A, g, &s, &bb, pm);
+    int n = box_sums(Z, W, H, intr, NULL, NULL, method, x0, x0 + w - 1, y0, y0 + h - 1, x0, y0, A, g, &s, &bb, pm);
     *count = n;
     for (int i = 0; i < 9; ++i) out[i] = NAN;
     if (n < min_valid || n <= 0) return 0;
@@ -443,7 +463,7 @@ int sfo_backward(const double* Z, int W, int H, const double* intr, int k, int m
         for (int px = 0; px < W; ++px) {
             const size_t o = (size_t)py * W + px;
             double A[3][3], g[3], s, bb;
-            int n = window_sums(Z, W, H, intr, r, method, px, py, A, g, &s, &bb, NULL);
+            int n = window_sums(Z, W, H, intr, NULL, NULL, r, method, px, py, A, g, &s, &bb, NULL);
             int ok = n >= min_valid && n > 0 && s > 0.0;
             if (require_center && !valid_depth(Z[o])) ok = 0;
             if (!ok) continue;

@@ -67,6 +67,35 @@ def rays(intr: Intrinsics, W: int, H: int) -> Tuple[np.ndarray, np.ndarray]:
     return tx, ty
 
 
+def delta_table(seed: int, intr: Intrinsics, W: int, H: int, amp: float = 1.5) -> Tuple[np.ndarray, np.ndarray]:
+    """Per-pixel ray adjustments (ddx, ddy) [H, W] in pixels: a radial field (a stand-in for lens
+    distortion, up to `amp` px at the corners) plus a seeded ripple, in multiples of 1/256 px."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = (np.arange(W, dtype=np.float64) - intr.cx)[None, :]
+    y = (np.arange(H, dtype=np.float64) - intr.cy)[:, None]
+    rho2 = (x / max(W / 2.0, 1.0)) ** 2 + (y / max(H / 2.0, 1.0)) ** 2
+    k1 = amp * 0.5 * rng.uniform(0.5, 1.0)
+    ddx = k1 * rho2 * x / max(W / 2.0, 1.0)
+    ddy = k1 * rho2 * y / max(H / 2.0, 1.0)
+    ph = rng.uniform(0, 2 * np.pi, 2)
+    ddx = ddx + 0.2 * amp * np.sin(0.05 * y + 0.03 * x + ph[0])
+    ddy = ddy + 0.2 * amp * np.cos(0.04 * x - 0.02 * y + ph[1])
+    q = lambda a: np.clip(np.round(a * 256.0), -(16 * 256 - 1), 16 * 256 - 1) / 256.0
+    return q(ddx), q(ddy)
+
+
+def plane_depth_delta(plane: "Plane", intr: Intrinsics, ddx: np.ndarray, ddy: np.ndarray) -> np.ndarray:
+    """plane_depth with per-pixel rays (x + dx + ddx - cx)/fx, (y + dy + ddy - cy)/fy."""
+    H, W = ddx.shape
+    tx = (np.arange(W, dtype=np.float64)[None, :] + intr.dx + ddx - intr.cx) / intr.fx
+    ty = (np.arange(H, dtype=np.float64)[:, None] + intr.dy + ddy - intr.cy) / intr.fy
+    denom = plane.n[0] * tx + plane.n[1] * ty + plane.n[2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Z = -plane.d / denom
+    Z[~(denom < 0)] = np.inf
+    return Z
+
+
 def _random_normal_toward_camera(rng: np.random.Generator, max_tilt_deg: float) -> np.ndarray:
     """Unit normal tilted from -Z by U[0, max_tilt] at a uniform azimuth."""
     tilt = math.radians(rng.uniform(0.0, max_tilt_deg))

@@ -418,3 +418,38 @@ def test_fit_at_equals_fit_at_those_pixels(method):
         assert np.array_equal(a, np.nan_to_num(pts[key], nan=7.0)), key
     with pytest.raises(ValueError):
         oracle.fit_at(depth, intr.as_tuple(), k, [[W, 0]], method)
+
+
+def test_constant_delta_table_equals_constant_delta():
+    """A per-pixel table holding one value c everywhere is the constant adjustment dx = c, dy = c
+    of Eq. 1 (bit for bit: the same rays)."""
+    W, H, k = 40, 30, 7
+    base = scenes.Intrinsics(300.0, 310.0, 19.2, 14.7)
+    depth = scenes.kinect_frame(scenes.BASE_SEED + 33, base, W, H)
+    c = (0.375, -0.625)
+    shifted = scenes.Intrinsics(base.fx, base.fy, base.cx, base.cy, c[0], c[1])
+    for method in ("disparity", "standard", "explicit_disparity"):
+        a = oracle.fit(depth, shifted.as_tuple(), k, method, want_lambda=True)
+        b = oracle.fit(depth, base.as_tuple(), k, method, want_lambda=True,
+                       delta=(np.full((H, W), c[0]), np.full((H, W), c[1])))
+        for key in ("normals", "offsets", "curvature", "counts"):
+            assert np.array_equal(np.nan_to_num(a[key], nan=7.0), np.nan_to_num(b[key], nan=7.0)), (method, key)
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_noise_free_plane_with_per_pixel_rays(method):
+    """Depth rendered through per-pixel rays (a radial field + ripple of up to ~2 px) is fitted exactly
+    when the fit uses the same rays, and visibly wrongly when it ignores them (closed form, Eq. 12)."""
+    W, H, k = 48, 36, 7
+    intr = scenes.Intrinsics(200.0, 205.0, 23.5, 17.5)
+    ddx, ddy = scenes.delta_table(5, intr, W, H, amp=2.0)
+    assert np.abs(ddx).max() > 0.5 and np.abs(ddy).max() > 0.5
+    pl = scenes.plane_through(np.array([0.1, -0.05, 1.7]), np.array([0.3, -0.2, -1.0]))
+    Z = scenes.plane_depth_delta(pl, intr, ddx, ddy)
+    assert np.isfinite(Z).all()
+    o = oracle.fit(Z, intr.as_tuple(), k, method, delta=(ddx, ddy))
+    assert np.isfinite(o["offsets"]).all()
+    assert np.nanmax(_angle(o["normals"], pl.n[None, None, :])) < 1e-8
+    assert np.max(np.abs(o["offsets"] - pl.d)) < 1e-8 * pl.d
+    plain = oracle.fit(Z, intr.as_tuple(), k, method)
+    assert np.nanmax(_angle(plain["normals"], pl.n[None, None, :])) > 1e-3
