@@ -264,6 +264,22 @@ sf_status sf_batch_info(const sf_batch* batch, long long* pixels, int* launches)
 sf_status sf_batch_destroy(sf_batch* batch);
 
 /*
+ * sf_set_delta_table -- per-pixel ray adjustments (Eq. 1 and Eq. 10 add an
+ * adjustment (dx, dy) to a pixel's coordinates before its ray is formed; this
+ * gives every pixel its own, added to the intrinsics' dx, dy):
+ *   ddx, ddy   host float [H][W] in pixels, |value| < 16, finite; read during
+ *              the call and stored on the device rounded to 1/256 pixel
+ *              (both NULL: remove the table)
+ * With a table, sf_fit / sf_fit_ex / sf_fit_host of SF_METHOD_DISPARITY (either
+ * constraint, precision mode 0) use the per-pixel rays; every other method,
+ * precision modes 1 and 2, sf_fit_backward and sf_quadtree return
+ * SF_ERR_UNSUPPORTED while a table is set.  The table's scratch is 64 B per
+ * pixel instead of 20.  Synchronous.  Errors: SF_ERR_INVALID_ARG (one table
+ * NULL, entry out of range), SF_ERR_ALLOC, SF_ERR_CUDA.
+ */
+sf_status sf_set_delta_table(sf_ctx* ctx, const float* ddx, const float* ddy);
+
+/*
  * sf_set_tiles -- tile shape of a context: hseg in {32, 64, 128} columns per
  * horizontal tile (default 32), vband rows per vertical band (0 = chosen
  * from the grid size, else 8..1024).  Results do not depend on the tiles: the window sums

@@ -76,6 +76,17 @@ class SurfaceFitter:
         """Tile shape: hseg in {32, 64, 128} columns, vband rows per band (0 = automatic)."""
         _native.check(_native.lib().sf_set_tiles(self._h, int(hseg), int(vband)))
 
+    def set_delta_table(self, ddx=None, ddy=None) -> None:
+        """Per-pixel ray adjustments [H, W] in pixels (``sf_set_delta_table``); None, None removes them."""
+        if ddx is None and ddy is None:
+            _native.check(_native.lib().sf_set_delta_table(self._h, None, None))
+            return
+        a = np.ascontiguousarray(ddx, dtype=np.float32)
+        b = np.ascontiguousarray(ddy, dtype=np.float32)
+        if a.shape != (self.H, self.W) or b.shape != (self.H, self.W):
+            raise ValueError("delta tables must be [H, W] = [%d, %d]" % (self.H, self.W))
+        _native.check(_native.lib().sf_set_delta_table(self._h, a.ctypes.data, b.ctypes.data))
+
     def set_disparity_model(self, alpha: float, beta: float = 0.0) -> None:
         """Sensor model of ``disparity_u16`` input: 1/Z = alpha * D + beta (1/metres)."""
         _native.check(_native.lib().sf_set_disparity_model(self._h, float(alpha), float(beta)))

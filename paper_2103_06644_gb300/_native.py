@@ -59,6 +59,7 @@ SIGNATURES = {
     "sf_set_constraint": (_I, [_VP, _I]),
     "sf_set_disparity_model": (_I, [_VP, ctypes.c_double, ctypes.c_double]),
     "sf_set_tiles": (_I, [_VP, _I, _I]),
+    "sf_set_delta_table": (_I, [_VP, _VP, _VP]),
     "sf_batch_create": (_I, [ctypes.POINTER(BatchFrame), _I, _I, _I, _F, _I, _I, _I, ctypes.POINTER(_VP)]),
     "sf_batch_run": (_I, [_VP, _VP]),
     "sf_batch_info": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I)]),

@@ -17,6 +17,7 @@
 #include "surffit.h"
 #include "sf_solve.cuh"
 #include "sf_kernels.cuh"
+#include "sf_delta.cuh"
 
 
 // ===========================================================================
@@ -107,6 +108,7 @@ struct sf_ctx {
     cudaEvent_t io_entry = nullptr;
     float* adj = nullptr;      // backward: per-window adjoint planes
     size_t adj_bytes = 0;
+    int* dtab = nullptr;       // per-pixel ray adjustments [H][W], packed (D, E) in 1/256 pixel, or none
     // precision fallback
     int precision_mode = 0;    // 0 float32 solve, 1 + FP64 re-solve where gap < tau, 2 FP64 everywhere
     int constraint = SF_CONSTRAINT_UNIT3;  // normalisation of the implicit fits (Eq. 4)
@@ -161,7 +163,9 @@ struct StageTimer {
 }  // namespace
 
 static sf_status ensure_planes(sf_ctx* c, int frames) {
-    const size_t need = plane_bytes_per_frame(SF_METHOD_STANDARD, c->plane_elems) * (size_t)frames;
+    const size_t delta_bytes = (sf::kDeltaPlanes32 * 4 + sf::kDeltaPlanes64 * 8) * c->plane_elems;
+    const size_t need = std::max(plane_bytes_per_frame(SF_METHOD_STANDARD, c->plane_elems),
+                                 c->dtab ? delta_bytes : (size_t)0) * (size_t)frames;
     if (c->planes && c->planes_bytes >= need && c->planes_frames >= frames) return SF_OK;
     if (c->planes) cudaFree(c->planes);
     c->planes = nullptr;
@@ -350,6 +354,50 @@ static sf_status launch_pass_for(sf_ctx* c, int nfr, const void* depth, float* n
     }
 }
 
+// The disparity-form pass with a per-pixel table of ray adjustments
+// (sf_set_delta_table): range as usual, then the table's row and column passes.
+template <int DT, bool U4>
+static sf_status launch_pass_delta(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,
+                                   int32_t* counts, cudaStream_t st) {
+    constexpr int M = SF_METHOD_DISPARITY;
+    const size_t fe = (size_t)c->W * c->H;
+    const int raw_z = sf::fixed_quantum<DT, M>() ? 1 : 0;
+    const int bits = quant_bits(M, c->k);
+    SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
+    if (!raw_z) {
+        StageTimer t(c, 0, st);
+        const int blocks = range_blocks(c, fe, nfr);
+        sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
+    }
+    {
+        StageTimer t(c, 1, st);
+        dim3 grid((c->W + 31) / 32, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
+        const size_t smem = 2 * sizeof(int) * sf::kHThreads * (size_t)((32 + 2 * c->r) | 1);
+        sf::hpass_delta_kernel<DT><<<grid, sf::kHThreads, smem, st>>>(depth, c->dtab, c->W, c->H, c->r, codec_of(c),
+                                                                     c->vmax, bits, c->plane_elems, c->planes);
+    }
+    {
+        StageTimer t(c, 2, st);
+        const int band = vertical_band(c, nfr);
+        dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
+        sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
+        sf::vpass_delta_kernel<DT, U4><<<grid, sf::kVThreads, 0, st>>>(
+            depth, c->W, c->H, c->r, codec_of(c), c->vmax, bits, c->plane_elems, c->planes, cal, c->min_valid,
+            c->require_center, band, normals, offsets, curv, counts);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return SF_OK;
+}
+
+template <int DT>
+static sf_status launch_pass_delta_for(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets,
+                                       float* curv, int32_t* counts, cudaStream_t st) {
+    return c->constraint == SF_CONSTRAINT_UNIT4
+               ? launch_pass_delta<DT, true>(c, nfr, depth, normals, offsets, curv, counts, st)
+               : launch_pass_delta<DT, false>(c, nfr, depth, normals, offsets, curv, counts, st);
+}
+
 template <int DT, int M>
 static sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const float* gn, const float* gd,
                                  const float* gk, float* g_depth, cudaStream_t st) {
@@ -517,6 +565,8 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
         return fail(SF_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     if (c->constraint == SF_CONSTRAINT_UNIT4 && c->method != SF_METHOD_DISPARITY && c->method != SF_METHOD_STANDARD)
         return fail(SF_ERR_UNSUPPORTED, "the |(a,b,c,d)| = 1 constraint applies to the implicit fits");
+    if (c->dtab && (c->method != SF_METHOD_DISPARITY || c->precision_mode != 0))
+        return fail(SF_ERR_UNSUPPORTED, "a per-pixel delta table applies to the disparity-form fit in precision mode 0");
     if (c->depth_type == SF_DEPTH_DISPARITY_U16 && sf::base_method(c->method) == SF_METHOD_DISPARITY) {
         // the disparity integers go into the int32 row sums unscaled: k w < 2^31
         const double wmax = 128.0 * 65535.0 + std::fabs((double)c->disp_add);
@@ -547,9 +597,16 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
         float* op = offsets + fe * f0;
         float* cp = curvature + fe * f0;
         int32_t* kp = counts ? counts + fe * f0 : nullptr;
-        s = c->depth_type == SF_DEPTH_F32   ? launch_pass_for<SF_DEPTH_F32>(c, nfr, dp, np_, op, cp, kp, st)
-            : c->depth_type == SF_DEPTH_U16 ? launch_pass_for<SF_DEPTH_U16>(c, nfr, dp, np_, op, cp, kp, st)
-                                            : launch_pass_for<SF_DEPTH_DISPARITY_U16>(c, nfr, dp, np_, op, cp, kp, st);
+        if (c->dtab)
+            s = c->depth_type == SF_DEPTH_F32 ? launch_pass_delta_for<SF_DEPTH_F32>(c, nfr, dp, np_, op, cp, kp, st)
+                : c->depth_type == SF_DEPTH_U16
+                    ? launch_pass_delta_for<SF_DEPTH_U16>(c, nfr, dp, np_, op, cp, kp, st)
+                    : launch_pass_delta_for<SF_DEPTH_DISPARITY_U16>(c, nfr, dp, np_, op, cp, kp, st);
+        else
+            s = c->depth_type == SF_DEPTH_F32 ? launch_pass_for<SF_DEPTH_F32>(c, nfr, dp, np_, op, cp, kp, st)
+                : c->depth_type == SF_DEPTH_U16
+                    ? launch_pass_for<SF_DEPTH_U16>(c, nfr, dp, np_, op, cp, kp, st)
+                    : launch_pass_for<SF_DEPTH_DISPARITY_U16>(c, nfr, dp, np_, op, cp, kp, st);
         if (s != SF_OK) return s;
     }
     return SF_OK;
@@ -644,6 +701,7 @@ sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_
                       int capacity, int32_t* n_nodes, void* stream) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (!p || !n_nodes) return fail(SF_ERR_INVALID_ARG, "null params or n_nodes");
+    if (c->dtab) return fail(SF_ERR_UNSUPPORTED, "the segmentation does not take a per-pixel delta table");
     if (c->constraint != SF_CONSTRAINT_UNIT3)
         return fail(SF_ERR_UNSUPPORTED, "the segmentation uses the |(a,b,c)| = 1 constraint only");
     if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
@@ -699,6 +757,40 @@ sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_
     return SF_OK;
 }
 
+sf_status sf_set_delta_table(sf_ctx* c, const float* ddx, const float* ddy) {
+    if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    if (!ddx != !ddy) return fail(SF_ERR_INVALID_ARG, "give both tables or neither");
+    if (!ddx) {
+        if (c->dtab) cudaFree(c->dtab);
+        c->dtab = nullptr;
+        return SF_OK;
+    }
+    const size_t n = (size_t)c->W * c->H;
+    std::vector<int> packed(n);
+    for (size_t i = 0; i < n; ++i) {
+        const float a = ddx[i], b = ddy[i];
+        if (!std::isfinite(a) || !std::isfinite(b) || std::fabs(a) * sf::kDeltaScale > sf::kDeltaMax ||
+            std::fabs(b) * sf::kDeltaScale > sf::kDeltaMax)
+            return fail(SF_ERR_INVALID_ARG, "delta table entry %zu (%g, %g) must be finite and below 16 pixels", i,
+                        (double)a, (double)b);
+        const int D = (int)std::lrint((double)a * sf::kDeltaScale), E = (int)std::lrint((double)b * sf::kDeltaScale);
+        packed[i] = (int)((uint32_t)(uint16_t)(int16_t)D | ((uint32_t)(uint16_t)(int16_t)E << 16));
+    }
+    if (!c->dtab) {
+        cudaError_t e = cudaMalloc(&c->dtab, n * sizeof(int));
+        if (e != cudaSuccess) { c->dtab = nullptr; return fail(SF_ERR_ALLOC, "delta table of %zu bytes", n * 4); }
+    }
+    SF_CUDA(cudaMemcpy(c->dtab, packed.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    // the table's row pass holds two tiles in shared memory
+    const int smem = (int)(2 * sizeof(int) * sf::kHThreads * (size_t)((32 + 2 * sf::kMaxR) | 1));
+    cudaFuncSetAttribute(sf::hpass_delta_kernel<SF_DEPTH_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(sf::hpass_delta_kernel<SF_DEPTH_U16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(sf::hpass_delta_kernel<SF_DEPTH_DISPARITY_U16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    SF_CUDA(cudaGetLastError());
+    return SF_OK;
+}
+
 sf_status sf_set_tiles(sf_ctx* c, int hseg, int vband) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (hseg != 32 && hseg != 64 && hseg != 128) return fail(SF_ERR_INVALID_ARG, "hseg must be 32, 64 or 128");
@@ -749,6 +841,7 @@ sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const floa
         return fail(SF_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     if (c->method != SF_METHOD_DISPARITY && c->method != SF_METHOD_STANDARD)
         return fail(SF_ERR_UNSUPPORTED, "the backward covers the implicit fits only");
+    if (c->dtab) return fail(SF_ERR_UNSUPPORTED, "the backward does not take a per-pixel delta table");
     if (c->constraint != SF_CONSTRAINT_UNIT3)
         return fail(SF_ERR_UNSUPPORTED, "the backward covers the |(a,b,c)| = 1 constraint only");
     if (c->depth_type == SF_DEPTH_DISPARITY_U16)
@@ -830,6 +923,7 @@ sf_status sf_destroy(sf_ctx* c) {
     }
     if (c->io_entry) cudaEventDestroy(c->io_entry);
     if (c->adj) cudaFree(c->adj);
+    if (c->dtab) cudaFree(c->dtab);
     if (c->flags) cudaFree(c->flags);
     if (c->flag_count) cudaFree(c->flag_count);
     if (c->rays64) cudaFree(c->rays64);
