@@ -504,6 +504,51 @@ def main():
             for f in ef:
                 f.close()
         line["explicit_fits"] = expl
+        # the disparity form on the same batch under the literal |(a,b,c,d)| = 1 constraint (row N4) and
+        # with a per-pixel ray table (row N3)
+        nxt = {}
+        for name in ("unit4", "delta_table"):
+            fs2 = []
+            for (W, H, intr, frames) in groups:
+                f2 = SurfaceFitter(intr.as_tuple(), W, H, K)
+                if name == "unit4":
+                    f2.set_constraint(True)
+                else:
+                    f2.set_delta_table(*scenes.delta_table(scenes.BASE_SEED + 600, intr, W, H))
+                fs2.append(f2)
+            for _ in range(3):
+                step(fs2)
+            ms2 = timed(max(3, args.steps // 4), lambda: step(fs2))
+            nxt[name] = {"value": whole_job_rate(world, total_px, ms2), "unit": UNIT, "ms_per_step": ms2}
+            for f2 in fs2:
+                f2.close()
+        # raw disparity input (row N3): the batch's depth as 1/8-pixel stereo disparity of a 7.5 cm baseline
+        fs3, ins3 = [], []
+        for (W, H, intr, frames) in groups:
+            alpha = 1.0 / (8.0 * intr.fx * 0.075)
+            z = np.stack(frames).astype(np.float64)
+            disp = np.zeros(z.shape)
+            ok = np.isfinite(z) & (z > 0)
+            disp[ok] = np.round(1.0 / z[ok] / alpha)
+            disp[(disp < 1) | (disp > 65535)] = 0
+            f3 = SurfaceFitter(intr.as_tuple(), W, H, K, depth_type="disparity_u16")
+            f3.set_disparity_model(alpha, 0.0)
+            fs3.append(f3)
+            ins3.append(torch.from_numpy(disp.astype(np.uint16).view(np.int16)).to(dev).view(torch.uint16))
+
+        def step3():
+            for f3, d3, o in zip(fs3, ins3, outputs):
+                f3.fit(d3, out=o)
+
+        for _ in range(3):
+            step3()
+        ms3 = timed(max(3, args.steps // 4), step3)
+        nxt["disparity_input"] = {"value": whole_job_rate(world, total_px, ms3), "unit": UNIT, "ms_per_step": ms3,
+                                  "input": "uint16 disparity, 1/Z = D / (8 fx 0.075 m)"}
+        for f3 in fs3:
+            f3.close()
+        del ins3
+        line["next_rows"] = nxt
         # 640x480, 7x7: the small single-frame case (launch-bound)
         intr = scenes.Intrinsics(525.0, 525.0, 319.5, 239.5)
         vga = torch.from_numpy(scenes.kinect_frame(scenes.BASE_SEED, intr, 640, 480)).to(dev)

@@ -263,9 +263,16 @@ __global__ void __launch_bounds__(kVThreads) vpass_delta_kernel(const void* __re
     const float tx = cal.tx[x];
     DispDeltaState S(P);
     S.init(pb, kGroup, H, y0, r);
+    float zc = load_depth<DT>(dframe, (size_t)y0 * W + x, scale);
     for (int y = y0; y < y1; ++y) {
         const size_t oi = (size_t)f * fe + (size_t)y * W + x;
-        const bool cvalid = depth_valid(load_depth<DT>(dframe, (size_t)y * W + x, scale));
+        const bool cvalid = depth_valid(zc);
+        // the next slide's rows (and the next centre depth) load while this row solves
+        const bool more = y + 1 < y1;
+        if (more) {
+            S.fetch(pb, kGroup, H, y, r);
+            zc = load_depth<DT>(dframe, (size_t)(y + 1) * W + x, scale);
+        }
         const int n = S.count();
         const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
         float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
@@ -288,10 +295,7 @@ __global__ void __launch_bounds__(kVThreads) vpass_delta_kernel(const void* __re
         normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
         offsets[oi] = d; curvature[oi] = cu;
         if (counts) counts[oi] = n;
-        if (y + 1 < y1) {
-            S.fetch(pb, kGroup, H, y, r);
-            S.apply(r);
-        }
+        if (more) S.apply(r);
     }
 }
 
