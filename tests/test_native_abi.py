@@ -55,6 +55,7 @@ def test_host_argument_checks(lib):
     assert lib.sf_destroy(None) == 0
     assert lib.sf_fit(None, None, None, None, None, None) == 1
     assert lib.sf_set_params(None, 0, 0, 1e-3, 3, 1) == 1
+    assert lib.sf_set_delta_table(None, None, None) == 1
 
 
 def test_channel_counts_follow_the_paper(lib):
