@@ -108,3 +108,37 @@ def test_autograd_function_matches_direct_backward():
     torch.cuda.synchronize()
     assert torch.allclose(d.grad, direct, rtol=1e-5, atol=1e-6 * direct.abs().max().item())
     f.close()
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_backward_uint16_frame_batch(method):
+    """uint16 millimetre frames fitted and differentiated as one batch of 3: each frame's dL/dZ (metres)
+    matches the oracle's adjoint of that frame alone."""
+    W, H, k = 160, 120, 7
+    intr = scenes.Intrinsics(115.0, 115.0, 79.5, 59.5)
+    frames = [scenes.structured_light_frame(scenes.BASE_SEED + 170 + i, intr, W, H) for i in range(3)]
+    rng = np.random.Generator(np.random.PCG64(17))
+    gns, gds, gks, refs, goods = [], [], [], [], []
+    for u in frames:
+        fwd = oracle.fit(u, intr.as_tuple(), k, method, want_lambda=True)
+        ok = np.isfinite(fwd["offsets"])
+        gn = np.where(ok[..., None], rng.standard_normal((H, W, 3)), 0.0)
+        gd = np.where(ok, rng.standard_normal((H, W)), 0.0)
+        gk = np.where(ok, rng.standard_normal((H, W)) * 10, 0.0)
+        refs.append(oracle.backward(u, intr.as_tuple(), k, gn, gd, gk, method))
+        lam = fwd["lam"]
+        gap = np.where(ok, (lam[..., 1] - lam[..., 0]) / np.where(ok, lam[..., 2], 1.0), np.inf)
+        goods.append((_box_min(gap, k // 2) >= GAP_MIN) & (u > 0))
+        gns.append(gn); gds.append(gd); gks.append(gk)
+    f = SurfaceFitter(intr.as_tuple(), W, H, k, method=method, depth_type="u16")
+    t = torch.from_numpy(np.stack(frames).view(np.int16)).cuda().view(torch.uint16)
+    as_t = lambda a: torch.from_numpy(np.stack(a).astype(np.float32)).cuda()
+    g = f.backward(t, as_t(gns), as_t(gds), as_t(gks))
+    torch.cuda.synchronize()
+    g = g.cpu().numpy().astype(np.float64)
+    f.close()
+    for i, (ref, sel) in enumerate(zip(refs, goods)):
+        assert np.all(g[i][frames[i] == 0] == 0.0)
+        assert sel.mean() > 0.4
+        err = np.abs(g[i][sel] - ref[sel]).max() / np.abs(ref[sel]).max()
+        assert err < REL_TOL, (i, err)
