@@ -453,3 +453,50 @@ def test_noise_free_plane_with_per_pixel_rays(method):
     assert np.max(np.abs(o["offsets"] - pl.d)) < 1e-8 * pl.d
     plain = oracle.fit(Z, intr.as_tuple(), k, method)
     assert np.nanmax(_angle(plain["normals"], pl.n[None, None, :])) > 1e-3
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_unit4_and_curvature_match_lapack_on_noisy_windows(method):
+    """On noisy data, the literal |(a,b,c,d)| = 1 fit is the smallest eigenvector of the 4x4 scatter of
+    the window's monomials (Eq. 4-6 / Eq. 14), and the default fit's curvature is lambda0 / trace of the
+    Schur complement: both recomputed here by brute force over the window and LAPACK (numpy eigh)."""
+    W, H, k = 30, 24, 7
+    intr = scenes.Intrinsics(90.0, 92.0, 14.7, 11.2, 0.1, -0.2)
+    depth = scenes.kinect_frame(scenes.BASE_SEED + 177, intr, W, H, noise_coef=0.004)
+    Z = oracle.depth_to_f64(depth, 1e-3)
+    o4 = oracle.fit(depth, intr.as_tuple(), k, method, unit4=True, want_lambda=True)
+    o3 = oracle.fit(depth, intr.as_tuple(), k, method, want_lambda=True)
+    r = k // 2
+    rng = np.random.Generator(np.random.PCG64(3))
+    checked = 0
+    for _ in range(60):
+        px, py = int(rng.integers(0, W)), int(rng.integers(0, H))
+        us = []
+        for y in range(py - r, py + r + 1):
+            for x in range(px - r, px + r + 1):
+                if 0 <= x < W and 0 <= y < H and np.isfinite(Z[y, x]) and Z[y, x] > 0:
+                    tx = (x + intr.dx - intr.cx) / intr.fx
+                    ty = (y + intr.dy - intr.cy) / intr.fy
+                    z = Z[y, x]
+                    us.append([tx, ty, 1.0, 1.0 / z] if method == "disparity" else [z * tx, z * ty, z, 1.0])
+        if not np.isfinite(o4["offsets"][py, px]):
+            continue
+        U = np.array(us)
+        M = U.T @ U
+        lam, vec = np.linalg.eigh(M)
+        if (lam[1] - lam[0]) < 1e-6 * lam[3]:
+            continue  # the 4x4 eigenvector is ill-posed here
+        a = vec[:, 0]
+        nn = np.linalg.norm(a[:3])
+        n, d = a[:3] / nn, a[3] / nn
+        if d < 0:
+            n, d = -n, -d
+        assert _angle(o4["normals"][py, px], n) < 1e-8
+        assert abs(o4["offsets"][py, px] - d) < 1e-8 * max(abs(d), 1e-3)
+        assert abs(o4["curvature"][py, px] - lam[0] / lam.sum()) < 1e-9
+        # default constraint: curvature = lambda0 / trace of the Schur complement
+        A, g, s = M[:3, :3], M[:3, 3], M[3, 3]
+        l3 = np.linalg.eigvalsh(A - np.outer(g, g) / s)
+        assert abs(o3["curvature"][py, px] - l3[0] / l3.sum()) < 1e-9
+        checked += 1
+    assert checked > 30
