@@ -5,7 +5,6 @@ dropped term, a wrong sign, a transposed operand or a wrong index in
 ``oracle/surffit_oracle.c`` fails at least one of them.
 """
 import json
-import math
 import os
 
 import numpy as np
