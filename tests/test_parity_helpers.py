@@ -80,3 +80,34 @@ def test_mistakes_below_the_tolerances_pass(frame):
     d[y, x] += 5e-5 * mu
     c[y, x] += 5e-6
     compare((n, d, c, cnt), ref, label="within tolerance")
+
+
+@pytest.mark.parametrize("method", ["explicit_disparity", "explicit_standard"])
+@pytest.mark.parametrize("what", [None, "normal 2e-3 rad", "residual x 1.01", "count - 1", "lost fit"])
+def test_explicit_comparator(method, what):
+    from parity import compare_explicit, explicit_design
+
+    W, H, k = 48, 40, 7
+    intr = scenes.Intrinsics.scaled(W, H)
+    depth = scenes.kinect_frame(scenes.BASE_SEED + 211, intr, W, H)
+    ref = oracle.fit(depth, intr.as_tuple(), k, method, want_lambda=True, want_moments=True)
+    n, d, c, cnt = (ref["normals"].astype(np.float32), ref["offsets"].astype(np.float32),
+                    ref["curvature"].astype(np.float32), ref["counts"].copy())
+    ok = np.isfinite(ref["offsets"])
+    rc, _ = explicit_design(np.where(ok[..., None], ref["moments"], 1.0))
+    y, x = np.argwhere(ok & (rc > 0.1) & (ref["curvature"] > 0))[0]
+    if what == "normal 2e-3 rad":
+        n[y, x] = _rotate(ref["normals"][y, x], 2e-3)
+    elif what == "residual x 1.01":
+        c[y, x] *= 1.01
+    elif what == "count - 1":
+        cnt[y, x] -= 1
+    elif what == "lost fit":
+        n[y, x] = np.nan
+        d[y, x] = np.nan
+        c[y, x] = np.nan
+    if what is None:
+        compare_explicit((n, d, c, cnt), ref, method, label="copy")
+    else:
+        with pytest.raises(AssertionError):
+            compare_explicit((n, d, c, cnt), ref, method, label=what)
