@@ -67,6 +67,10 @@ def _load():
         lib.sfo_fit_at.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, ip, dp, dp, ctypes.c_int]
         lib.sfo_fit_at.restype = ctypes.c_int
+        lib.sfo_fit_at_delta.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, ip,
+                                         dp, dp, ctypes.c_int]
+        lib.sfo_fit_at_delta.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -144,9 +148,9 @@ def fit(depth: np.ndarray, intr: Sequence[float], k: int, method: str = "dispari
 
 def fit_at(depth: np.ndarray, intr: Sequence[float], k: int, xy: np.ndarray, method: str = "disparity", *,
            unit4: bool = False, min_valid: int = 3, require_center: bool = True, depth_scale: float = 1e-3,
-           threads: int = 0) -> Dict[str, np.ndarray]:
+           threads: int = 0, delta=None) -> Dict[str, np.ndarray]:
     """``fit`` evaluated at the pixels xy [N, 2] (x, y) only: the same dict with a leading N axis
-    (lam and moments always included)."""
+    (lam and moments always included); ``delta`` as for ``fit``."""
     lib = _load()
     Z = np.ascontiguousarray(depth_to_f64(depth, depth_scale))
     H, W = Z.shape
@@ -157,9 +161,16 @@ def fit_at(depth: np.ndarray, intr: Sequence[float], k: int, xy: np.ndarray, met
     counts = np.empty(n, dtype=np.int32)
     lam, mom = np.empty((n, 3)), np.empty((n, 10))
     ip = ctypes.POINTER(ctypes.c_int32)
-    rc = lib.sfo_fit_at(_dp(Z), W, H, _dp(it), int(k), METHODS[method], int(unit4), int(min_valid),
-                        int(require_center), n, pts.ctypes.data_as(ip), _dp(normals), _dp(offsets), _dp(curv),
-                        counts.ctypes.data_as(ip), _dp(lam), _dp(mom), int(threads))
+    if delta is None:
+        ddx = ddy = None
+    else:
+        ddx, ddy = (np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in delta)
+        if ddx.shape != (H, W) or ddy.shape != (H, W):
+            raise ValueError("delta tables must be [H, W]")
+    rc = lib.sfo_fit_at_delta(_dp(Z), W, H, _dp(it), _dp(ddx) if ddx is not None else None,
+                              _dp(ddy) if ddy is not None else None, int(k), METHODS[method], int(unit4),
+                              int(min_valid), int(require_center), n, pts.ctypes.data_as(ip), _dp(normals),
+                              _dp(offsets), _dp(curv), counts.ctypes.data_as(ip), _dp(lam), _dp(mom), int(threads))
     if rc != 0:
         raise ValueError("oracle rejected its arguments (rc=%d)" % rc)
     return {"normals": normals, "offsets": offsets, "curvature": curv, "counts": counts, "lam": lam, "moments": mom}

@@ -370,11 +370,14 @@ int sfo_fit_delta(const double* Z, int W, int H, const double* intr, const doubl
 /*
  * sfo_fit_at: sfo_fit evaluated at npix pixels only, xy = [x0, y0, x1, y1, ...];
  * output slot i holds pixel i (same layouts as sfo_fit with H*W -> npix).
+ * sfo_fit_at_delta: the same with per-pixel ray adjustments (as sfo_fit_delta).
  */
-int sfo_fit_at(const double* Z, int W, int H, const double* intr, int k, int method, int unit4, int min_valid,
-               int require_center, int npix, const int32_t* xy, double* normals, double* offsets, double* curv,
-               int32_t* counts, double* lam, double* moments, int nthreads) {
-    if (!Z || W <= 0 || H <= 0 || !intr || k < 1 || (k & 1) == 0 || method < 0 || method > 3 || npix < 0 || !xy)
+int sfo_fit_at_delta(const double* Z, int W, int H, const double* intr, const double* ddx, const double* ddy, int k,
+                     int method, int unit4, int min_valid, int require_center, int npix, const int32_t* xy,
+                     double* normals, double* offsets, double* curv, int32_t* counts, double* lam, double* moments,
+                     int nthreads) {
+    if (!Z || W <= 0 || H <= 0 || !intr || k < 1 || (k & 1) == 0 || method < 0 || method > 3 || npix < 0 || !xy ||
+        (!ddx != !ddy))
         return -1;
     for (int i = 0; i < npix; ++i)
         if (xy[2 * i] < 0 || xy[2 * i] >= W || xy[2 * i + 1] < 0 || xy[2 * i + 1] >= H) return -1;
@@ -384,9 +387,16 @@ int sfo_fit_at(const double* Z, int W, int H, const double* intr, int k, int met
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
     for (int i = 0; i < npix; ++i)
-        fit_pixel(Z, W, H, intr, NULL, NULL, r, method, unit4, min_valid, require_center, xy[2 * i], xy[2 * i + 1], (size_t)i,
-                  normals, offsets, curv, counts, lam, moments);
+        fit_pixel(Z, W, H, intr, ddx, ddy, r, method, unit4, min_valid, require_center, xy[2 * i], xy[2 * i + 1],
+                  (size_t)i, normals, offsets, curv, counts, lam, moments);
     return 0;
+}
+
+int sfo_fit_at(const double* Z, int W, int H, const double* intr, int k, int method, int unit4, int min_valid,
+               int require_center, int npix, const int32_t* xy, double* normals, double* offsets, double* curv,
+               int32_t* counts, double* lam, double* moments, int nthreads) {
+    return sfo_fit_at_delta(Z, W, H, intr, NULL, NULL, k, method, unit4, min_valid, require_center, npix, xy, normals,
+                            offsets, curv, counts, lam, moments, nthreads);
 }
 
 /*

@@ -12,7 +12,8 @@ Workloads (synthetic, seeded as in the benchmark):
   resolution fitted as one stacked batch (both forms);
 - 30 x 1280x720 uint16 structured-light frames, k in {5, 9, 15} (both forms);
 - the 64-frame mixed batch (320x240 .. 1920x1080, k in {5, 7, 11, 21}) with
-  autotuned tiles, replayed from a CUDA graph.
+  autotuned tiles, replayed from a CUDA graph;
+- a per-pixel ray table on 1080p and 4K frames of the benchmark, k = 31.
 """
 import numpy as np
 import pytest
@@ -123,3 +124,24 @@ def test_mixed_batch_64_frames_graph():
         check_frame(out, cnt, depth, intr.as_tuple(), k, "disparity", xy, "mixed frame %d %dx%d k=%d" % (i, W, H, k))
         f.close()
     b.close()
+
+
+def test_delta_table_1080p_and_4k_k31():
+    """The per-pixel ray table at the benchmark's sizes: 2 x 1920x1080 and 1 x 4096x3072, k = 31,
+    disparity form, each resolution fitted as one stacked batch."""
+    K = 31
+    for (W, H, n, seed0) in [(1920, 1080, 2, scenes.BASE_SEED + 300), (4096, 3072, 1, scenes.BASE_SEED + 400)]:
+        intr = scenes.Intrinsics.scaled(W, H)
+        frames = [scenes.wide_range_frame(seed0 + i, intr, W, H) for i in range(n)]
+        table = scenes.delta_table(scenes.BASE_SEED + 600, intr, W, H)
+        f = SurfaceFitter(intr.as_tuple(), W, H, K)
+        f.set_delta_table(*table)
+        nrm, off, cur, cnt = f.fit(torch.from_numpy(np.stack(frames)).cuda(), counts=True)
+        torch.cuda.synchronize()
+        for i in range(n):
+            xy = sample_xy(seed0 + 70 + i, W, H, K, n_interior=800, n_edge=24)
+            ref = oracle.fit_at(frames[i], intr.as_tuple(), K, xy, "disparity", delta=table)
+            gpu = (at(nrm[i], xy), at(off[i], xy), at(cur[i], xy), at(cnt[i], xy))
+            s = compare(gpu, ref, label="delta table %dx%d frame %d" % (W, H, i))
+            assert s["good"] > 0.8 * s["valid"], s
+        f.close()

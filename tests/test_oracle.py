@@ -417,6 +417,12 @@ def test_fit_at_equals_fit_at_those_pixels(method):
         assert np.array_equal(a, np.nan_to_num(pts[key], nan=7.0)), key
     with pytest.raises(ValueError):
         oracle.fit_at(depth, intr.as_tuple(), k, [[W, 0]], method)
+    table = scenes.delta_table(4, intr, W, H)
+    full = oracle.fit(depth, intr.as_tuple(), k, method, want_lambda=True, want_moments=True, delta=table)
+    pts = oracle.fit_at(depth, intr.as_tuple(), k, xy, method, delta=table)
+    for key in ("normals", "offsets", "curvature", "counts", "lam", "moments"):
+        a = np.nan_to_num(full[key][xy[:, 1], xy[:, 0]], nan=7.0)
+        assert np.array_equal(a, np.nan_to_num(pts[key], nan=7.0)), key
 
 
 def test_constant_delta_table_equals_constant_delta():
