@@ -274,7 +274,8 @@ sf_status sf_batch_destroy(sf_batch* batch);
  * constraint, precision mode 0) use the per-pixel rays; every other method,
  * precision modes 1 and 2, sf_fit_backward and sf_quadtree return
  * SF_ERR_UNSUPPORTED while a table is set.  The table's scratch is 64 B per
- * pixel instead of 20.  Synchronous.  Errors: SF_ERR_INVALID_ARG (one table
+ * pixel instead of 20.  Synchronous: waits for the device to finish queued
+ * work before replacing a table.  Errors: SF_ERR_INVALID_ARG (one table
  * NULL, entry out of range), SF_ERR_ALLOC, SF_ERR_CUDA.
  */
 sf_status sf_set_delta_table(sf_ctx* ctx, const float* ddx, const float* ddy);

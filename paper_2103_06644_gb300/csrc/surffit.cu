@@ -760,6 +760,8 @@ sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_
 sf_status sf_set_delta_table(sf_ctx* c, const float* ddx, const float* ddy) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (!ddx != !ddy) return fail(SF_ERR_INVALID_ARG, "give both tables or neither");
+    // fits already queued may still read the old table
+    SF_CUDA(cudaDeviceSynchronize());
     if (!ddx) {
         if (c->dtab) cudaFree(c->dtab);
         c->dtab = nullptr;
