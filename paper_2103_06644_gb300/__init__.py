@@ -5,6 +5,24 @@ Thin PyTorch binding over the C ABI of ``libsurffit.so`` (``include/surffit.h``)
 PyTorch supplies device memory and streams; every step of the fit runs in the
 library's CUDA kernels.  There is no CPU fallback: on a machine without the
 built library or without a GPU, the calls raise.
+
+Example::
+
+    import torch
+    from paper_2103_06644_gb300 import SurfaceFitter
+
+    fit = SurfaceFitter((fx, fy, cx, cy), W, H, 7)           # 7 x 7 windows, disparity form
+    depth = torch.as_tensor(z_metres, device="cuda")         # [H, W] or [N, H, W] float32, 0 = missing
+    normals, offsets, curvature = fit.fit(depth)             # NaN where a window has no fit
+    counts = fit.fit(depth, counts=True)[3]                  # valid pixels per window
+    n_host, d_host, k_host = fit.fit_host(z_numpy)           # the same from host memory
+    n, d, k = fit.fit_differentiable(depth.requires_grad_()) # backward to the depth (implicit fits)
+
+``SurfaceFitter(..., method="standard" | "explicit_disparity" | "explicit_standard",
+depth_type="u16" | "disparity_u16")`` selects the fit and the depth encoding;
+``set_precision``, ``set_constraint``, ``set_delta_table``, ``set_disparity_model`` and
+``set_tiles`` adjust a context; ``quadtree`` segments frames into planes;
+``SurfaceFitBatch`` fits frames of mixed sizes and windows in one persistent pass.
 """
 from __future__ import annotations
 
