@@ -154,23 +154,46 @@ typedef enum { SF_CONSTRAINT_UNIT3 = 0, SF_CONSTRAINT_UNIT4 = 1 } sf_constraint;
 sf_status sf_set_constraint(sf_ctx* ctx, int constraint);
 
 /*
- * sf_set_precision -- precision of the per-pixel solve.  The window sums are
- * exact integers in every mode; the modes differ in the solve:
- *   0  float32 solve (default).  Normal error ~ 4e-7 / gamma rad against an
- *      FP64 fit of the same data, gamma = (lambda1 - lambda0) / lambda2.
- *   1  float32 solve, then every window with gamma < tau is queued and solved
- *      again in FP64 from the same exact moments (overwriting its outputs).
- *   2  FP64 solve for every window (slow: FP64 runs at ~1/64 of the float32
- *      rate on GB300).
- * In every mode the sums hold the depth (or disparity) in fixed point with
- * 26-28 bits per frame (26 at k = 31), which bounds the agreement with a fit
- * of the unquantised depth (about 3e-5 rad at gamma >= 1e-3, 3e-4 rad at
- * gamma >= 1e-5 on 1080p frames at k = 31 in modes 1 and 2).
- * tau in (0, 1] (mode 1; default 1e-2).  Modes 1 and 2 allocate a queue of
- * 8 bytes per pixel on the next fit.  The explicit fits have no eigen-gap:
- * mode 1 leaves them in float32, mode 2 solves their regression in FP64.
+ * sf_set_precision -- precision of the per-pixel solve (Eq. 4-5: the normal is
+ * the eigenvector of the smallest eigenvalue of R, whose error under a
+ * perturbation dR is about |dR| / (lambda1 - lambda0)).  The window sums are
+ * exact integers of the depth (or disparity) in fixed point, 26-28 bits per
+ * frame; the modes differ in the solve and in how the fixed-point rounding of
+ * the depth is treated:
+ *   0  float32 solve (default).  Normal error ~ 3e-8 / gamma rad against an
+ *      FP64 fit of the same data, gamma = (lambda1 - lambda0) / lambda2, plus
+ *      the effect of the rounding.
+ *   1  float32 solve, then every window with gamma < tau, or whose rounding
+ *      could move its normal by more than 3e-5 rad (an estimate from the
+ *      float32 eigenvalues), is queued: its normal is refined in double-float
+ *      (pairs of float32) from the same exact moments, and where the
+ *      refined estimate of the rounding's effect (5.5 standard deviations)
+ *      still exceeds 3e-5 rad the window's depth is re-summed without the
+ *      rounding before refining again; the queued windows' outputs are
+ *      overwritten.  The estimate treats the pixels' rounding errors as
+ *      independent, which holds unless many depths of a window repeat exactly
+ *      (depths quantised coarsely at the source).  Measured on 1080p frames at
+ *      k = 31: within 3e-5 rad of the FP64 fit of the unrounded depth on
+ *      every window with gamma >= 1e-6.
+ *   2  the refinement and the re-summing for every window (slow: every
+ *      window reads its k x k depth again): agreement with the FP64 fit to
+ *      ~1e-7 rad, whatever the data.
+ * tau in (0, 1] (mode 1; default 1e-3).  Modes 1 and 2 allocate on the next fit
+ * a queue of 8 bytes per pixel plus the queued windows' moments (80 bytes for
+ * a quarter of the pixels in mode 1, for every pixel in mode 2).  The explicit
+ * fits and the |(a,b,c,d)| = 1 constraint are re-solved in FP64 from the exact
+ * moments instead (mode 1 leaves the explicit fits in float32).
  */
 sf_status sf_set_precision(sf_ctx* ctx, int mode, float tau);
+
+/*
+ * sf_precision_stats -- for the context's most recent fit pass (the last group
+ * of up to 64 frames of its last sf_fit / sf_fit_ex / sf_fit_host call) in
+ * precision mode 1 or 2: the number of windows queued for refinement and the
+ * number among them re-summed from the depth (both 0 in mode 0).  Waits for
+ * the context's device to finish its queued work.
+ */
+sf_status sf_precision_stats(sf_ctx* ctx, unsigned long long* queued, unsigned long long* resummed);
 
 /*
  * sf_fit -- fit every pixel of one frame.

@@ -113,9 +113,15 @@ class SurfaceFitter:
         """|(a,b,c)| = 1 (default, False) or the literal |(a,b,c,d)| = 1 of Eq. 4 (True) for the implicit fits."""
         _native.check(_native.lib().sf_set_constraint(self._h, 1 if unit4 else 0))
 
-    def set_precision(self, mode: int, tau: float = 1e-2) -> None:
-        """0: float32 solve; 1: + FP64 re-solve where gamma < tau; 2: FP64 solve everywhere."""
+    def set_precision(self, mode: int, tau: float = 1e-3) -> None:
+        """0: float32 solve; 1: + double-float refinement where gamma < tau; 2: refinement everywhere."""
         _native.check(_native.lib().sf_set_precision(self._h, int(mode), float(tau)))
+
+    def precision_stats(self) -> Tuple[int, int]:
+        """(windows queued for refinement, windows re-summed from the depth) in the last fit pass."""
+        q, r = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+        _native.check(_native.lib().sf_precision_stats(self._h, ctypes.byref(q), ctypes.byref(r)))
+        return int(q.value), int(r.value)
 
     # -- device API -------------------------------------------------------------
     def _check_depth(self, depth):

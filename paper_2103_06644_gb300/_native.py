@@ -56,6 +56,7 @@ SIGNATURES = {
     "sf_fit_host": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sf_destroy": (_I, [_VP]),
     "sf_set_precision": (_I, [_VP, _I, _F]),
+    "sf_precision_stats": (_I, [_VP, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)]),
     "sf_set_constraint": (_I, [_VP, _I]),
     "sf_set_disparity_model": (_I, [_VP, ctypes.c_double, ctypes.c_double]),
     "sf_set_tiles": (_I, [_VP, _I, _I]),

@@ -46,6 +46,10 @@ __host__ __device__ constexpr int base_method(int M) {
 // latency hiding; at 8 blocks (64 registers) the per-column pass spills.
 constexpr int kVBlocks = 6;
 
+// Normal error (rad) above which a window's fixed-point rounding sends it to
+// the refinement of precision modes 1 and 2 (the tier-C threshold there).
+constexpr float kRefineRounding = 3e-5f;
+
 // ---------------------------------------------------------------------------
 // Depth decoding.  Codec: how a stored value becomes depth.
 //   SF_DEPTH_F32             metres (scale unused)
@@ -697,7 +701,7 @@ using StdState = StdStateT<false>;
 // Not inlined: the single-context and the batch kernels then run the same
 // machine code, so their results agree bit for bit (inlined copies may be
 // contracted into FMAs differently); one call covers a whole band.
-template <int DT, int M, bool U4 = false>
+template <int DT, int M, bool U4 = false, bool kGuard = false>
 __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, Codec scale, float q,
                                              const Planes P, size_t pofs, int x, int y0, int band,
                                              const float* __restrict__ txt, const float* __restrict__ tyt, float a,
@@ -705,7 +709,7 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
                                              float* __restrict__ offsets, float* __restrict__ curvature,
                                              int32_t* __restrict__ counts, float tau,
                                              unsigned long long* __restrict__ flags, unsigned* __restrict__ flag_count,
-                                             int frame_tag) {
+                                             int frame_tag, void* __restrict__ mq, unsigned mcap) {
     const int y1 = min(y0 + band, H);
     const size_t pb = plane_index(pofs, x, 0, H);
     const float tx = txt[x];
@@ -739,11 +743,11 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
         FitOut fo_;
         if (ok) {
             if constexpr (M == SF_METHOD_DISPARITY)
-                fo_ = solve_disparity<float, U4>(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty,
-                                      a, b);
+                fo_ = solve_disparity<float, U4, kGuard>(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi,
+                                                         S.Sww, q, tx, ty, a, b);
             else if constexpr (M == SF_METHOD_STANDARD)
-                fo_ = solve_standard<float, U4>((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji,
-                                     S.Szzii, q, tx, ty, a, b);
+                fo_ = solve_standard<float, U4, kGuard>((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj,
+                                                        S.Szzji, S.Szzii, q, tx, ty, a, b);
             else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY)
                 fo_ = solve_explicit_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q,
                                                tx, ty, a, b, ok);
@@ -754,7 +758,11 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
         }
         if (ok) {
             nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
-            if (flags && !(fo_.gap >= tau)) {
+            // queue a near-degenerate window, and (kGuard) one whose fixed-point
+            // rounding could move its normal by more than the refinement's threshold
+            bool queue = flags && !(fo_.gap >= tau);
+            if constexpr (kGuard) queue = queue || (flags && fo_.qerr2 > kRefineRounding * kRefineRounding);
+            if (queue) {
                 // near-degenerate window: queue it for the FP64 re-solve
                 const unsigned mask = __activemask();
                 const int leader = __ffs(mask) - 1;
@@ -765,6 +773,23 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
                 const unsigned slot = base + __popc(mask & ((1u << lane) - 1u));
                 flags[slot] = ((unsigned long long)frame_tag << 48) | ((unsigned long long)y << 24) |
                               (unsigned long long)x;
+                if (slot < mcap) {
+                    // the window's exact moments travel with it (80 B, five 16-byte stores)
+                    longlong2* e = reinterpret_cast<longlong2*>(static_cast<char*>(mq) + (size_t)slot * 80);
+                    if constexpr (B == SF_METHOD_DISPARITY) {
+                        e[0] = make_longlong2((long long)S.n, (long long)S.Sj);
+                        e[1] = make_longlong2((long long)S.Si, (long long)S.Sjj);
+                        e[2] = make_longlong2((long long)S.Sji, (long long)S.Sii);
+                        e[3] = make_longlong2(S.Sw, S.Swj);
+                        e[4] = make_longlong2(S.Swi, S.Sww);
+                    } else {
+                        e[0] = make_longlong2((long long)S.n, S.Sz);
+                        e[1] = make_longlong2(S.Szj, S.Szi);
+                        e[2] = make_longlong2(S.Szz, S.Szzj);
+                        e[3] = make_longlong2(S.Szzi, S.Szzjj);
+                        e[4] = make_longlong2(S.Szzji, S.Szzii);
+                    }
+                }
             }
         }
         pn[0] = nx; pn[1] = ny; pn[2] = nz;
@@ -775,7 +800,9 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
     }
 }
 
-template <int DT, int M, bool U4 = false>
+// kGuard: the instantiation of precision modes 1 and 2 (implicit |(a,b,c)| = 1
+// fits), which also queues windows by their estimated rounding error.
+template <int DT, int M, bool U4 = false, bool kGuard = false>
 __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
                                                           Codec scale, const unsigned* __restrict__ vmax_bits,
                                                           int bits, int raw_z, int Wp, size_t plane_elems,
@@ -784,7 +811,8 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* 
                                                           float* __restrict__ normals, float* __restrict__ offsets,
                                                           float* __restrict__ curvature, int32_t* __restrict__ counts,
                                                           float tau, unsigned long long* __restrict__ flags,
-                                                          unsigned* __restrict__ flag_count) {
+                                                          unsigned* __restrict__ flag_count, void* __restrict__ mq,
+                                                          unsigned mcap) {
     const int f = blockIdx.z;
     const int x = blockIdx.x * kVThreads + threadIdx.x;
     if (x >= W) return;
@@ -793,9 +821,10 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* 
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * fe;
     const float q = quantum<DT, M>(vmax_bits[f], bits, scale);  // metric value of one fixed-point unit
     const Planes P(planes_base, (size_t)gridDim.z * plane_elems, planes32<M>());
-    vpass_column<DT, M, U4>(dframe, W, H, r, scale, q, P, (size_t)f * plane_elems, x, blockIdx.y * band, band, cal.tx,
+    vpass_column<DT, M, U4, kGuard>(dframe, W, H, r, scale, q, P, (size_t)f * plane_elems, x, blockIdx.y * band, band, cal.tx,
                         cal.ty, cal.a, cal.b, min_valid, require_center, normals + 3 * fe * f, offsets + fe * f,
-                        curvature + fe * f, counts ? counts + fe * f : nullptr, tau, flags, flag_count, f);
+                        curvature + fe * f, counts ? counts + fe * f : nullptr, tau, flags, flag_count, f, mq,
+                        mcap);
 }
 
 // ---------------------------------------------------------------------------
@@ -888,7 +917,7 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks - 1) vpass_batch_kernel(co
             const float q = quantum<DT, M>(vmax_bits[w.x], d.bits, scale);
             vpass_column<DT, M>(d.depth, d.W, d.H, d.r, scale, q, P, d.pofs, x, w.z, d.band, d.tx, d.ty, d.a,
                                 d.b, min_valid, require_center, d.normals, d.offsets, d.curvature, nullptr,
-                                INFINITY, nullptr, nullptr, w.x);
+                                INFINITY, nullptr, nullptr, w.x, nullptr, 0u);
         }
     }
 }
@@ -1254,7 +1283,7 @@ __global__ void __launch_bounds__(256) quad_level_kernel(const void* __restrict_
 }
 
 // The root tiles of every frame, in frame-major, row-major order.
-__global__ void quad_roots_kernel(int W, int H, int tile, int nfr, QuadRect* __restrict__ out, int* __restrict__ count) {
+static __global__ void quad_roots_kernel(int W, int H, int tile, int nfr, QuadRect* __restrict__ out, int* __restrict__ count) {
     const int tw = (W + tile - 1) / tile, th = (H + tile - 1) / tile;
     const int total = tw * th * nfr;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {

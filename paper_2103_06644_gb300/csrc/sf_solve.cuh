@@ -16,7 +16,11 @@ struct FitOutT {
     T nx, ny, nz, d, curv;
     T gap;  // (lambda1 - lambda0) / lambda2 of the normalised 3x3 matrix
     T tr;   // trace of R in metric units (implicit fits): lambda0 = curv * tr
+    // squared estimate of the normal's error due to the fixed-point rounding
+    // of the depth (rounding_error2; computed by the solves only on request)
+    T qerr2;
 };
+
 using FitOut = FitOutT<float>;
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -82,6 +86,37 @@ template <> struct Fn<double> {
     static __device__ __forceinline__ double from_i64(int64_t v) { return (double)v; }
 };
 
+// Squared estimate, 5.5 standard deviations, of the normal's error (rad) due to
+// rounding every pixel's fixed-point value by up to half a unit, for a window
+// whose R (upper triangle r..) has eigenvalues l0 <= l1 <= l2, n the unit
+// eigenvector of l0 and c the centroid in units where the rounding is half a
+// unit (d = -n . c).  A rounding error e_q of pixel q moves n1^T R n0 by
+// e_q (d f_q - (n1 . c) r_q) to first order (r_q, f_q the pixel's residuals
+// along n0 and n1), so its standard deviation is
+// sqrt((d^2 l1 + (n1 . c)^2 l0) / 12) and the normal moves by that over
+// l1 - l0.  n1 is not formed: with cp = c + d n = (n1 . c) n1 + (n2 . c) n2,
+// (n1 . c)^2 = (l2 |cp|^2 - cp^T R cp) / (l2 - l1), padded by the rounding of
+// that difference and bounded by |cp|^2.  The estimate assumes the rounding
+// errors of the pixels independent, as they are for depths that do not repeat.
+template <typename T>
+__device__ __forceinline__ T rounding_error2(T r11, T r12, T r13, T r22, T r23, T r33, T nx, T ny, T nz, T cx, T cy,
+                                             T cz, T l0, T l1, T l2) {
+    const T d = -(nx * cx + ny * cy + nz * cz);
+    const T px = cx + d * nx, py = cy + d * ny, pz = cz + d * nz;
+    const T p2 = px * px + py * py + pz * pz;
+    const T pRp = px * (r11 * px + r12 * py + r13 * pz) + py * (r12 * px + r22 * py + r23 * pz) +
+                  pz * (r13 * px + r23 * py + r33 * pz);
+    const T dl = l1 - l0, d21 = l2 - l1;
+    T n1c2 = p2;
+    if (d21 > T(0)) {
+        const T t = (l2 * p2 - pRp + T(5e-7) * l2 * p2) * Fn<T>::rcp(d21);
+        n1c2 = t < p2 ? (t > T(0) ? t : T(0)) : p2;
+    }
+    if (!(dl > T(0))) return T(INFINITY);
+    const T num = d * d * (l1 > T(0) ? l1 : T(0)) + n1c2 * (l0 > T(0) ? l0 : T(0));
+    return T(2.5208333) * num * Fn<T>::rcp(dl * dl);
+}
+
 // Null vector of the symmetric matrix M = R - l I: the column of the
 // cofactor matrix adj(M) with the largest diagonal entry (each column is a
 // cross product of two rows of M; adj(M) = det(M) M^{-1} is dominated by
@@ -118,7 +153,7 @@ __device__ __forceinline__ void null_vector(T r11, T r12, T r13, T r22, T r23, T
 // The eigenvector error left is ~|dR| / (lambda1 - lambda0).
 template <typename T>
 __device__ __forceinline__ void smallest_eigpair(T r11, T r12, T r13, T r22, T r23, T r33, T& v0, T& v1, T& v2, T& l0,
-                                                 T& gap) {
+                                                 T& gap, T* l2 = nullptr) {
     const T tr = r11 + r22 + r33;
     const T s = Fn<T>::rcp(tr);
     r11 *= s; r12 *= s; r13 *= s; r22 *= s; r23 *= s; r33 *= s;
@@ -161,6 +196,7 @@ __device__ __forceinline__ void smallest_eigpair(T r11, T r12, T r13, T r22, T r
     v0 = a0; v1 = a1; v2 = a2;
     l0 = lr > T(0) ? lr : T(0);
     gap = (lmax > T(0)) ? (lmid - lmin) * Fn<T>::rcp(lmax > T(0) ? lmax : T(1)) : T(0);
+    if (l2) *l2 = lmax;
 }
 
 // Orientation: d > 0 (the camera centre lies on the positive side); d == 0
@@ -304,7 +340,7 @@ __device__ __forceinline__ DispWindowT<T> build_disparity(T nf, T fSj, T fSi, T 
     return w;
 }
 
-template <typename T = float, bool U4 = false>
+template <typename T = float, bool U4 = false, bool kEst = false>
 __device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj, T fSji, T fSii, int64_t Sw,
                                                       int64_t Swj, int64_t Swi, int64_t Sww, T qw, T tx, T ty, T a,
                                                       T b) {
@@ -316,10 +352,17 @@ __device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj
                               sw * qw * w.what);
     }
     FitOutT<T> o;
-    T l0;
-    smallest_eigpair<T>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, l0, o.gap);
+    T l0, l2n;
+    smallest_eigpair<T>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, l0, o.gap, &l2n);
     o.curv = l0;
     o.tr = w.R11 + w.R22 + w.R33;  // R = K Y K^T is the Schur complement itself (no unit)
+    o.qerr2 = T(0);
+    if constexpr (kEst) {
+        // the weighted centroid mhat / (what qw) in units of 1 / qw
+        const T iw = Fn<T>::rcp(w.what);
+        o.qerr2 = rounding_error2<T>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, w.mx * iw,
+                                     w.my * iw, iw, l0 * o.tr, (l0 + o.gap * l2n) * o.tr, l2n * o.tr);
+    }
     o.d = -(o.nx * w.mx + o.ny * w.my + o.nz) * Fn<T>::rcp(w.what * qw);
     orient<T>(o.nx, o.ny, o.nz, o.d);
     return o;
@@ -331,7 +374,7 @@ __device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj
 // P_q = Z_q m_q = T [Z j, Z i, Z] with T = [[a, 0, tx], [0, b, ty], [0, 0, 1]],
 // so the covariance of the points is T C T^T, C the covariance of
 // [z j, z i, z] (re-centred on an integer near the mean depth first).
-template <typename T = float, bool U4 = false>
+template <typename T = float, bool U4 = false, bool kEst = false>
 __device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
                                                      int64_t Szzj, int64_t Szzi, int64_t Szzjj, int64_t Szzji,
                                                      int64_t Szzii, T qz, T tx, T ty, T a, T b) {
@@ -366,10 +409,19 @@ __device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t S
                               gn * zb, nf);
     }
     FitOutT<T> o;
-    T l0;
-    smallest_eigpair<T>(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, l0, o.gap);
+    T l0, l2n;
+    smallest_eigpair<T>(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, l0, o.gap, &l2n);
     o.curv = l0;
-    o.tr = (R11 + R22 + R33) * qz * qz;  // R is in units of the fixed-point depth squared
+    const T trR = R11 + R22 + R33;
+    o.tr = trR * qz * qz;  // R is in units of the fixed-point depth squared
+    o.qerr2 = T(0);
+    if constexpr (kEst) {
+        // the centroid (px, py, zb) qz over its depth zb qz: a rounding of half a
+        // unit of z perturbs P by m / 2, m = P / Z the pixel's ray
+        const T iz = Fn<T>::rcp(zb);
+        o.qerr2 = rounding_error2<T>(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, px * iz, py * iz, T(1),
+                                     l0 * trR, (l0 + o.gap * l2n) * trR, l2n * trR);
+    }
     o.d = -(o.nx * px + o.ny * py + o.nz * zb) * qz;
     orient<T>(o.nx, o.ny, o.nz, o.d);
     return o;

@@ -1,5 +1,7 @@
 // surffit.cu -- C ABI of the dense RGBD plane-fitting library (host side:
-// contexts, launches, batches, staging) over the kernels of sf_kernels.cuh.
+// contexts, argument checks, batches, staging, the allocation-free entry
+// point).  Kernel launches live in fit_f32.cu, fit_u16.cu and fit_disp.cu, one
+// per depth encoding (sf_launch.cuh).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -9,23 +11,23 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <string>
 #include <mutex>
-#include <type_traits>
+#include <string>
 #include <vector>
 
 #include "surffit.h"
-#include "sf_solve.cuh"
+#include "sf_host.h"
 #include "sf_kernels.cuh"
 #include "sf_delta.cuh"
 
+using sfh::cuda_fail;
+using sfh::fail;
 
-// ===========================================================================
-// C ABI
-// ===========================================================================
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+namespace sfh {
 
 sf_status fail(sf_status s, const char* fmt, ...) {
     char buf[512];
@@ -40,12 +42,6 @@ sf_status fail(sf_status s, const char* fmt, ...) {
 sf_status cuda_fail(cudaError_t e, const char* what) {
     return fail(SF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
-
-#define SF_CUDA(call)                                        \
-    do {                                                     \
-        cudaError_t _e = (call);                             \
-        if (_e != cudaSuccess) return cuda_fail(_e, #call);  \
-    } while (0)
 
 size_t plane_bytes_per_frame(int method, size_t plane_elems) {
     // disparity: 3 x int32 + 1 x int64 ; standard: 1 x int32 + 5 x int64
@@ -73,98 +69,40 @@ int quant_bits(int method, int k) {
     return std::min(28, std::max(16, b));
 }
 
-}  // namespace
-
-struct sf_ctx {
-    sf_intrinsics K;
-    int W, H, k, r;
-    int Wp;
-    size_t plane_elems;
-    int method = SF_METHOD_DISPARITY;
-    int depth_type = SF_DEPTH_F32;
-    int hseg = sf::kHSeg; // horizontal tile width (32, 64 or 128)
-    int vband = 0;        // vertical band height (0: chosen from the grid size)
-    float depth_scale = 1e-3f;
-    // SF_DEPTH_DISPARITY_U16: 1/Z = disp_q * (disp_mul * D + disp_add)
-    float disp_q = 1.f / 128.f;
-    int disp_mul = 128, disp_add = 0;
-    int min_valid = 3;
-    int require_center = 1;
-    int device = 0;
-    int sms = 152;        // streaming multiprocessors of the device (grid sizing)
-    float* tx = nullptr;  // [W]
-    float* ty = nullptr;  // [H]
-    unsigned* vmax = nullptr;  // [max_frames]
-    void* planes = nullptr;
-    int planes_frames = 0;     // frames the planes buffer holds
-    size_t planes_bytes = 0;
-    int max_frames_per_pass = 1;
-    // sf_fit_host: two device staging buffers and copy streams (one per
-    // chunk parity) and the event that orders the fits on the shared scratch
-    void* d_io[2] = {nullptr, nullptr};
-    size_t d_io_bytes = 0;
-    cudaStream_t io_stream[2] = {nullptr, nullptr};
-    cudaEvent_t io_fit_done[2] = {nullptr, nullptr};
-    cudaEvent_t io_entry = nullptr;
-    float* adj = nullptr;      // backward: per-window adjoint planes
-    size_t adj_bytes = 0;
-    int* dtab = nullptr;       // per-pixel ray adjustments [H][W], packed (D, E) in 1/256 pixel, or none
-    // precision fallback
-    int precision_mode = 0;    // 0 float32 solve, 1 + FP64 re-solve where gap < tau, 2 FP64 everywhere
-    int constraint = SF_CONSTRAINT_UNIT3;  // normalisation of the implicit fits (Eq. 4)
-    float tau = 1e-2f;
-    unsigned long long* flags = nullptr;
-    size_t flags_cap = 0;      // entries
-    unsigned* flag_count = nullptr;
-    double* rays64 = nullptr;  // [W] tx, [H] ty, 1/fx, 1/fy in FP64
-    // sf_quadtree: two node queues (ping-pong between levels) and the per-level counters
-    sf::QuadRect* quad_q[2] = {nullptr, nullptr};
-    size_t quad_cap = 0;       // entries per queue
-    int* quad_cnt = nullptr;   // [8]
-    // profiling: (stage, start event, stop event) per recorded launch
-    bool profiling = false;
-    struct Rec { int stage; cudaEvent_t a, b; };
-    std::vector<Rec> recs;
-    std::vector<cudaEvent_t> event_pool;
-};
+}  // namespace sfh
 
 namespace {
-sf::Codec codec_of(const sf_ctx* c) {
-    if (c->depth_type == SF_DEPTH_DISPARITY_U16) return sf::Codec{c->disp_q, c->disp_mul, c->disp_add};
-    return sf::Codec{c->depth_scale, 0, 0};
-}
 
 size_t depth_bytes(int depth_type) { return depth_type == SF_DEPTH_F32 ? 4 : 2; }
 
-cudaEvent_t take_event(sf_ctx* c) {
-    if (!c->event_pool.empty()) {
-        cudaEvent_t e = c->event_pool.back();
-        c->event_pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
+// Kernel attributes (large dynamic shared memory) of every launcher.
+void set_kernel_attributes() {
+    sfh::set_kernel_smem_f32();
+    sfh::set_kernel_smem_u16();
+    sfh::set_kernel_smem_disp();
 }
-// Bracket one launch with events when profiling is on.
-struct StageTimer {
-    sf_ctx* c; int stage; cudaStream_t st; cudaEvent_t a = nullptr;
-    StageTimer(sf_ctx* c_, int s_, cudaStream_t st_) : c(c_), stage(s_), st(st_) {
-        if (c->profiling) { a = take_event(c); cudaEventRecord(a, st); }
-    }
-    ~StageTimer() {
-        if (a) {
-            cudaEvent_t b = take_event(c);
-            cudaEventRecord(b, st);
-            c->recs.push_back({stage, a, b});
+
+sf_status fit_pass(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,
+                   int32_t* counts, cudaStream_t st) {
+    if (c->dtab) {
+        switch (c->depth_type) {
+            case SF_DEPTH_F32: return sfh::delta_pass_f32(c, nfr, depth, normals, offsets, curv, counts, st);
+            case SF_DEPTH_U16: return sfh::delta_pass_u16(c, nfr, depth, normals, offsets, curv, counts, st);
+            default: return sfh::delta_pass_disp(c, nfr, depth, normals, offsets, curv, counts, st);
         }
     }
-};
+    switch (c->depth_type) {
+        case SF_DEPTH_F32: return sfh::fit_pass_f32(c, nfr, depth, normals, offsets, curv, counts, st);
+        case SF_DEPTH_U16: return sfh::fit_pass_u16(c, nfr, depth, normals, offsets, curv, counts, st);
+        default: return sfh::fit_pass_disp(c, nfr, depth, normals, offsets, curv, counts, st);
+    }
+}
+
 }  // namespace
 
 static sf_status ensure_planes(sf_ctx* c, int frames) {
     const size_t delta_bytes = (sf::kDeltaPlanes32 * 4 + sf::kDeltaPlanes64 * 8) * c->plane_elems;
-    const size_t need = std::max(plane_bytes_per_frame(SF_METHOD_STANDARD, c->plane_elems),
+    const size_t need = std::max(sfh::plane_bytes_per_frame(SF_METHOD_STANDARD, c->plane_elems),
                                  c->dtab ? delta_bytes : (size_t)0) * (size_t)frames;
     if (c->planes && c->planes_bytes >= need && c->planes_frames >= frames) return SF_OK;
     if (c->planes) cudaFree(c->planes);
@@ -180,263 +118,6 @@ static sf_status ensure_planes(sf_ctx* c, int frames) {
 }
 
 static bool misaligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) != 0; }
-
-// The horizontal pass for tiles of seg = 32, 64 or 128 columns (one kernel
-// each: their register budgets differ).
-template <int DT, int M>
-static void launch_hpass(dim3 grid, size_t smem, cudaStream_t st, const void* depth, const sf_ctx* c, int bits,
-                         int raw_z, int seg) {
-    if (seg <= 32)
-        sf::hpass_kernel<DT, M, 1><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
-                                                                     bits, raw_z, c->Wp, c->plane_elems, c->planes);
-    else if (seg <= 64)
-        sf::hpass_kernel<DT, M, 2><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
-                                                                     bits, raw_z, c->Wp, c->plane_elems, c->planes);
-    else
-        sf::hpass_kernel<DT, M, 4><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
-                                                                     bits, raw_z, c->Wp, c->plane_elems, c->planes);
-}
-
-template <int DT, int M>
-static void set_hpass_smem_one(int smem) {
-    cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-}
-
-// Opt every horizontal-pass kernel in to `smem` bytes of dynamic shared memory.
-static void set_hpass_smem(int smem) {
-    set_hpass_smem_one<SF_DEPTH_F32, SF_METHOD_DISPARITY>(smem);
-    set_hpass_smem_one<SF_DEPTH_F32, SF_METHOD_STANDARD>(smem);
-    set_hpass_smem_one<SF_DEPTH_U16, SF_METHOD_DISPARITY>(smem);
-    set_hpass_smem_one<SF_DEPTH_U16, SF_METHOD_STANDARD>(smem);
-    set_hpass_smem_one<SF_DEPTH_DISPARITY_U16, SF_METHOD_DISPARITY>(smem);
-    set_hpass_smem_one<SF_DEPTH_DISPARITY_U16, SF_METHOD_STANDARD>(smem);
-}
-
-// Blocks per frame of the range pass: one wave of 256-thread blocks (8 per
-// SM) over all frames, at most one block per 16 x 256 elements.
-static int range_blocks(const sf_ctx* c, size_t fe, int nfr) {
-    const size_t per_frame = (size_t)c->sms * 8 / (size_t)std::max(1, nfr);
-    return (int)std::max<size_t>(1, std::min((fe + 4095) / 4096, per_frame));
-}
-
-// Band height of the vertical pass: long bands amortise the 2r-row warm-up,
-// short bands give enough threads to fill the GPU.
-static int vertical_band(const sf_ctx* c, int nfr) {
-    if (c->vband > 0) return c->vband;
-    const size_t cols = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * sf::kVThreads * nfr;
-    // at least 152 x 2048 threads (about 2.7 waves of 24 resident warps per
-    // SM): short bands cost a 2r-row warm-up each, but with fewer waves the
-    // tail of the last one costs more
-    int band = 256;
-    while (band > 16 && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 64 * 32) band /= 2;
-    return band;
-}
-
-template <int DT, int M, bool U4 = false>
-static sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,
-                             int32_t* counts, cudaStream_t st) {
-    const size_t fe = (size_t)c->W * c->H;
-    constexpr int B = sf::base_method(M);  // range and horizontal pass depend on the moments only
-    const int raw_z = sf::fixed_quantum<DT, B>() ? 1 : 0;
-    const int bits = quant_bits(M, c->k);
-    SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
-    if (!raw_z) {
-        StageTimer t(c, 0, st);
-        const int blocks = range_blocks(c, fe, nfr);
-        sf::range_kernel<DT, B><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
-    }
-    {
-        StageTimer t(c, 1, st);
-        const int seg = c->hseg;
-        dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
-        const int IW = seg + 2 * c->r;
-        const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
-        launch_hpass<DT, B>(grid, smem, st, depth, c, bits, raw_z, seg);
-    }
-    {
-        StageTimer t(c, 2, st);
-        const int band = vertical_band(c, nfr);
-        dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
-        sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
-        const bool fb = c->precision_mode > 0 && c->flags;
-        if (fb) SF_CUDA(cudaMemsetAsync(c->flag_count, 0, sizeof(unsigned), st));
-        const float tau = c->precision_mode == 2 ? INFINITY : c->tau;
-        sf::vpass_kernel<DT, M, U4><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
-                                                               bits, raw_z, c->Wp, c->plane_elems, c->planes, cal,
-                                                               c->min_valid, c->require_center, band, normals,
-                                                               offsets, curv, counts, tau, fb ? c->flags : nullptr,
-                                                               c->flag_count);
-        if (fb) {
-            StageTimer t2(c, 3, st);
-            sf::resolve_kernel<DT, M, U4><<<152 * 8, 128, 0, st>>>(c->W, c->H, c->r, codec_of(c), c->vmax, bits, c->Wp,
-                                                              c->plane_elems, nfr, c->planes, cal, c->rays64,
-                                                              c->flags, c->flag_count, normals, offsets, curv);
-        }
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-    return SF_OK;
-}
-
-// Fixed-point bits of the quadtree's node sums: nodes of up to 64 x 64 pixels
-// with offsets |j|, |i| <= 32 from the node's centre keep sum v^2 (disparity)
-// and sum v^2 j^2 (standard: 2^12 * 2^10 * 2^40 = 2^62) inside int64.
-static int quad_bits(int method) { return sf::base_method(method) == SF_METHOD_STANDARD ? 20 : 24; }
-
-template <int DT, int M>
-static sf_status launch_quadtree(sf_ctx* c, int nfr, int frame_base, const void* depth, const sf_quad_params* p,
-                                 sf_quad_node* nodes, int capacity, int32_t* n_nodes, size_t roots, cudaStream_t st) {
-    constexpr int B = sf::base_method(M);
-    const size_t fe = (size_t)c->W * c->H;
-    const int raw_z = sf::fixed_quantum<DT, B>() ? 1 : 0;
-    const int bits = quad_bits(M);
-    SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
-    if (!raw_z) {
-        const int blocks = range_blocks(c, fe, nfr);
-        sf::range_kernel<DT, B><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
-    }
-    SF_CUDA(cudaMemsetAsync(c->quad_cnt, 0, sizeof(int) * 8, st));
-    sf::quad_roots_kernel<<<(int)std::min<size_t>((roots + 255) / 256, 1024), 256, 0, st>>>(c->W, c->H, p->tile, nfr,
-                                                                                            c->quad_q[0], c->quad_cnt);
-    size_t level_max = roots;
-    for (int l = 0; l <= p->max_level; ++l) {
-        const size_t n = std::min(level_max, c->quad_cap);
-        const int blocks = (int)((n + 7) / 8);
-        sf::quad_level_kernel<DT, M><<<blocks, 256, 0, st>>>(
-            depth, c->W, c->H, codec_of(c), c->vmax, bits, c->rays64, c->quad_q[l & 1], c->quad_cnt + l, l,
-            p->max_level, (double)p->tau, c->min_valid, p->min_valid_permille, c->quad_q[(l + 1) & 1],
-            c->quad_cnt + l + 1, (int)c->quad_cap, nodes, n_nodes, capacity, frame_base);
-        level_max *= 4;
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "quadtree launch");
-    return SF_OK;
-}
-
-template <int DT>
-static sf_status launch_quadtree_for(sf_ctx* c, int nfr, int frame_base, const void* depth, const sf_quad_params* p,
-                                     sf_quad_node* nodes, int capacity, int32_t* n_nodes, size_t roots,
-                                     cudaStream_t st) {
-    switch (c->method) {
-        case SF_METHOD_DISPARITY:
-            return launch_quadtree<DT, SF_METHOD_DISPARITY>(c, nfr, frame_base, depth, p, nodes, capacity, n_nodes,
-                                                            roots, st);
-        case SF_METHOD_STANDARD:
-            return launch_quadtree<DT, SF_METHOD_STANDARD>(c, nfr, frame_base, depth, p, nodes, capacity, n_nodes,
-                                                           roots, st);
-        case SF_METHOD_EXPLICIT_DISPARITY:
-            return launch_quadtree<DT, SF_METHOD_EXPLICIT_DISPARITY>(c, nfr, frame_base, depth, p, nodes, capacity,
-                                                                     n_nodes, roots, st);
-        default:
-            return launch_quadtree<DT, SF_METHOD_EXPLICIT_STANDARD>(c, nfr, frame_base, depth, p, nodes, capacity,
-                                                                    n_nodes, roots, st);
-    }
-}
-
-template <int DT>
-static sf_status launch_pass_for(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,
-                                 int32_t* counts, cudaStream_t st) {
-    switch (c->method) {
-        case SF_METHOD_DISPARITY:
-            return c->constraint == SF_CONSTRAINT_UNIT4
-                       ? launch_pass<DT, SF_METHOD_DISPARITY, true>(c, nfr, depth, normals, offsets, curv, counts, st)
-                       : launch_pass<DT, SF_METHOD_DISPARITY>(c, nfr, depth, normals, offsets, curv, counts, st);
-        case SF_METHOD_STANDARD:
-            return c->constraint == SF_CONSTRAINT_UNIT4
-                       ? launch_pass<DT, SF_METHOD_STANDARD, true>(c, nfr, depth, normals, offsets, curv, counts, st)
-                       : launch_pass<DT, SF_METHOD_STANDARD>(c, nfr, depth, normals, offsets, curv, counts, st);
-        case SF_METHOD_EXPLICIT_DISPARITY:
-            return launch_pass<DT, SF_METHOD_EXPLICIT_DISPARITY>(c, nfr, depth, normals, offsets, curv, counts, st);
-        default:
-            return launch_pass<DT, SF_METHOD_EXPLICIT_STANDARD>(c, nfr, depth, normals, offsets, curv, counts, st);
-    }
-}
-
-// The disparity-form pass with a per-pixel table of ray adjustments
-// (sf_set_delta_table): range as usual, then the table's row and column passes.
-template <int DT, bool U4>
-static sf_status launch_pass_delta(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,
-                                   int32_t* counts, cudaStream_t st) {
-    constexpr int M = SF_METHOD_DISPARITY;
-    const size_t fe = (size_t)c->W * c->H;
-    const int raw_z = sf::fixed_quantum<DT, M>() ? 1 : 0;
-    const int bits = quant_bits(M, c->k);
-    SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
-    if (!raw_z) {
-        StageTimer t(c, 0, st);
-        const int blocks = range_blocks(c, fe, nfr);
-        sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
-    }
-    {
-        StageTimer t(c, 1, st);
-        dim3 grid((c->W + 31) / 32, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
-        const size_t smem = 2 * sizeof(int) * sf::kHThreads * (size_t)((32 + 2 * c->r) | 1);
-        sf::hpass_delta_kernel<DT><<<grid, sf::kHThreads, smem, st>>>(depth, c->dtab, c->W, c->H, c->r, codec_of(c),
-                                                                     c->vmax, bits, c->plane_elems, c->planes);
-    }
-    {
-        StageTimer t(c, 2, st);
-        const int band = vertical_band(c, nfr);
-        dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
-        sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
-        sf::vpass_delta_kernel<DT, U4><<<grid, sf::kVThreads, 0, st>>>(
-            depth, c->W, c->H, c->r, codec_of(c), c->vmax, bits, c->plane_elems, c->planes, cal, c->min_valid,
-            c->require_center, band, normals, offsets, curv, counts);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-    return SF_OK;
-}
-
-template <int DT>
-static sf_status launch_pass_delta_for(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets,
-                                       float* curv, int32_t* counts, cudaStream_t st) {
-    return c->constraint == SF_CONSTRAINT_UNIT4
-               ? launch_pass_delta<DT, true>(c, nfr, depth, normals, offsets, curv, counts, st)
-               : launch_pass_delta<DT, false>(c, nfr, depth, normals, offsets, curv, counts, st);
-}
-
-template <int DT, int M>
-static sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const float* gn, const float* gd,
-                                 const float* gk, float* g_depth, cudaStream_t st) {
-    const size_t fe = (size_t)c->W * c->H;
-    const int raw_z = sf::fixed_quantum<DT, M>() ? 1 : 0;
-    const int bits = quant_bits(M, c->k);
-    SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
-    if (!raw_z) {
-        const int blocks = range_blocks(c, fe, nfr);
-        sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
-    }
-    {
-        const int seg = c->hseg;
-        dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
-        const int IW = seg + 2 * c->r;
-        const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
-        launch_hpass<DT, M>(grid, smem, st, depth, c, bits, raw_z, seg);
-    }
-    sf::Calib cal{c->tx, c->ty, (float)(1.0 / c->K.fx), (float)(1.0 / c->K.fy)};
-    {
-        const int band = vertical_band(c, nfr);
-        dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
-        sf::vadjoint_kernel<DT, M><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
-                                                                  bits, c->Wp, c->plane_elems, c->planes, cal,
-                                                                  c->min_valid, c->require_center, band, gn, gd, gk,
-                                                                  c->adj);
-    }
-    {
-        const int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
-        const int T = sf::kGTile + 2 * c->r;
-        const size_t smem = sizeof(float) * NC * (size_t)T * T;
-        dim3 grid((c->W + sf::kGTile - 1) / sf::kGTile, (c->H + sf::kGTile - 1) / sf::kGTile, nfr);
-        sf::gather_kernel<DT, M><<<grid, dim3(32, 8), smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), cal,
-                                                                   c->adj, g_depth);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "backward kernel launch");
-    return SF_OK;
-}
 
 extern "C" {
 
@@ -496,7 +177,8 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
     c->max_frames_per_pass = 64;
     e = cudaMalloc(&c->vmax, sizeof(unsigned) * 64);
     if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create vmax"); }
-    e = cudaMalloc(&c->flag_count, sizeof(unsigned));
+    e = cudaMalloc(&c->flag_count, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->flag_count, 0, 2 * sizeof(unsigned));
     if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create flag counter"); }
     {
         // FP64 ray tables for the precision fallback
@@ -514,19 +196,7 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
     sf_status s = ensure_planes(c, 1);
     if (s != SF_OK) { sf_destroy(c); return s; }
     {
-        const int IW = 128 + 2 * sf::kMaxR;
-        const int smem = (int)(sizeof(int) * sf::kHThreads * (size_t)(IW | 1));
-        set_hpass_smem(smem);
-        const int T = sf::kGTile + 2 * sf::kMaxR;
-        const int gs7 = (int)(sizeof(float) * 7 * T * T), gs12 = (int)(sizeof(float) * 12 * T * T);
-        cudaFuncSetAttribute(sf::gather_kernel<SF_DEPTH_F32, SF_METHOD_DISPARITY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, gs7);
-        cudaFuncSetAttribute(sf::gather_kernel<SF_DEPTH_U16, SF_METHOD_DISPARITY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, gs7);
-        cudaFuncSetAttribute(sf::gather_kernel<SF_DEPTH_F32, SF_METHOD_STANDARD>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, gs12);
-        cudaFuncSetAttribute(sf::gather_kernel<SF_DEPTH_U16, SF_METHOD_STANDARD>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, gs12);
+        set_kernel_attributes();
         e = cudaGetLastError();
         if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create kernel attributes"); }
     }
@@ -585,9 +255,25 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
             if (c->flags) cudaFree(c->flags);
             c->flags = nullptr;
             c->flags_cap = 0;
+            if (c->queue_c) cudaFree(c->queue_c);
+            c->queue_c = nullptr;
             cudaError_t e = cudaMalloc(&c->flags, cap * sizeof(unsigned long long));
+            if (e == cudaSuccess) e = cudaMalloc(&c->queue_c, cap * sizeof(unsigned));
             if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "precision-fallback queue of %zu entries failed", cap);
             c->flags_cap = cap;
+        }
+        // the exact moments of queued windows: every window in mode 2, a quarter of
+        // them in mode 1 (windows queued beyond that re-read their moments from
+        // the scratch planes)
+        const size_t mcap = c->precision_mode == 2 ? cap : (cap + 3) / 4;
+        if (c->moments_cap < mcap) {
+            if (c->moments_q) cudaFree(c->moments_q);
+            c->moments_q = nullptr;
+            c->moments_cap = 0;
+            cudaError_t e = cudaMalloc(&c->moments_q, mcap * sfh::kMomentEntryBytes);
+            if (e != cudaSuccess)
+                return fail(SF_ERR_ALLOC, "precision-fallback moments of %zu entries failed", mcap);
+            c->moments_cap = mcap;
         }
     }
     for (int f0 = 0; f0 < n_frames; f0 += per) {
@@ -597,16 +283,7 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
         float* op = offsets + fe * f0;
         float* cp = curvature + fe * f0;
         int32_t* kp = counts ? counts + fe * f0 : nullptr;
-        if (c->dtab)
-            s = c->depth_type == SF_DEPTH_F32 ? launch_pass_delta_for<SF_DEPTH_F32>(c, nfr, dp, np_, op, cp, kp, st)
-                : c->depth_type == SF_DEPTH_U16
-                    ? launch_pass_delta_for<SF_DEPTH_U16>(c, nfr, dp, np_, op, cp, kp, st)
-                    : launch_pass_delta_for<SF_DEPTH_DISPARITY_U16>(c, nfr, dp, np_, op, cp, kp, st);
-        else
-            s = c->depth_type == SF_DEPTH_F32 ? launch_pass_for<SF_DEPTH_F32>(c, nfr, dp, np_, op, cp, kp, st)
-                : c->depth_type == SF_DEPTH_U16
-                    ? launch_pass_for<SF_DEPTH_U16>(c, nfr, dp, np_, op, cp, kp, st)
-                    : launch_pass_for<SF_DEPTH_DISPARITY_U16>(c, nfr, dp, np_, op, cp, kp, st);
+        s = fit_pass(c, nfr, dp, np_, op, cp, kp, st);
         if (s != SF_OK) return s;
     }
     return SF_OK;
@@ -745,13 +422,12 @@ sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_
     for (int f0 = 0; f0 < n_frames; f0 += per) {
         const int nfr = std::min(per, n_frames - f0);
         const void* dp = static_cast<const char*>(depth) + dbytes * fe * f0;
+        const size_t roots_n = tiles * nfr;
         sf_status s =
-            c->depth_type == SF_DEPTH_F32
-                ? launch_quadtree_for<SF_DEPTH_F32>(c, nfr, f0, dp, p, nodes, capacity, n_nodes, tiles * nfr, st)
+            c->depth_type == SF_DEPTH_F32 ? sfh::quadtree_f32(c, nfr, f0, dp, p, nodes, capacity, n_nodes, roots_n, st)
             : c->depth_type == SF_DEPTH_U16
-                ? launch_quadtree_for<SF_DEPTH_U16>(c, nfr, f0, dp, p, nodes, capacity, n_nodes, tiles * nfr, st)
-                : launch_quadtree_for<SF_DEPTH_DISPARITY_U16>(c, nfr, f0, dp, p, nodes, capacity, n_nodes,
-                                                              tiles * nfr, st);
+                ? sfh::quadtree_u16(c, nfr, f0, dp, p, nodes, capacity, n_nodes, roots_n, st)
+                : sfh::quadtree_disp(c, nfr, f0, dp, p, nodes, capacity, n_nodes, roots_n, st);
         if (s != SF_OK) return s;
     }
     return SF_OK;
@@ -783,12 +459,6 @@ sf_status sf_set_delta_table(sf_ctx* c, const float* ddx, const float* ddy) {
         if (e != cudaSuccess) { c->dtab = nullptr; return fail(SF_ERR_ALLOC, "delta table of %zu bytes", n * 4); }
     }
     SF_CUDA(cudaMemcpy(c->dtab, packed.data(), n * sizeof(int), cudaMemcpyHostToDevice));
-    // the table's row pass holds two tiles in shared memory
-    const int smem = (int)(2 * sizeof(int) * sf::kHThreads * (size_t)((32 + 2 * sf::kMaxR) | 1));
-    cudaFuncSetAttribute(sf::hpass_delta_kernel<SF_DEPTH_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(sf::hpass_delta_kernel<SF_DEPTH_U16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(sf::hpass_delta_kernel<SF_DEPTH_DISPARITY_U16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem);
     SF_CUDA(cudaGetLastError());
     return SF_OK;
 }
@@ -871,17 +541,27 @@ sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const floa
         const float* gd = g_offsets + fe * f0;
         const float* gk = g_curvature + fe * f0;
         float* gz = g_depth + fe * f0;
-        if (c->depth_type == SF_DEPTH_F32) {
-            s = c->method == SF_METHOD_DISPARITY
-                    ? launch_backward<SF_DEPTH_F32, SF_METHOD_DISPARITY>(c, nfr, dp, gn, gd, gk, gz, st)
-                    : launch_backward<SF_DEPTH_F32, SF_METHOD_STANDARD>(c, nfr, dp, gn, gd, gk, gz, st);
-        } else {
-            s = c->method == SF_METHOD_DISPARITY
-                    ? launch_backward<SF_DEPTH_U16, SF_METHOD_DISPARITY>(c, nfr, dp, gn, gd, gk, gz, st)
-                    : launch_backward<SF_DEPTH_U16, SF_METHOD_STANDARD>(c, nfr, dp, gn, gd, gk, gz, st);
-        }
+        s = c->depth_type == SF_DEPTH_F32 ? sfh::backward_f32(c, nfr, dp, gn, gd, gk, gz, st)
+                                           : sfh::backward_u16(c, nfr, dp, gn, gd, gk, gz, st);
         if (s != SF_OK) return s;
     }
+    return SF_OK;
+}
+
+sf_status sf_precision_stats(sf_ctx* c, unsigned long long* queued, unsigned long long* resummed) {
+    if (!c || !queued || !resummed) return fail(SF_ERR_INVALID_ARG, "null argument");
+    unsigned h[2] = {0u, 0u};
+    if (c->precision_mode > 0) {
+        int prev = 0;
+        SF_CUDA(cudaGetDevice(&prev));
+        if (prev != c->device) SF_CUDA(cudaSetDevice(c->device));
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(h, c->flag_count, sizeof(h), cudaMemcpyDeviceToHost);
+        if (prev != c->device) cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(e, "sf_precision_stats");
+    }
+    *queued = h[0];
+    *resummed = c->precision_mode == 2 ? h[0] : h[1];  // mode 2 re-sums every queued window
     return SF_OK;
 }
 
@@ -927,6 +607,8 @@ sf_status sf_destroy(sf_ctx* c) {
     if (c->adj) cudaFree(c->adj);
     if (c->dtab) cudaFree(c->dtab);
     if (c->flags) cudaFree(c->flags);
+    if (c->moments_q) cudaFree(c->moments_q);
+    if (c->queue_c) cudaFree(c->queue_c);
     if (c->flag_count) cudaFree(c->flag_count);
     if (c->rays64) cudaFree(c->rays64);
     for (int i = 0; i < 2; ++i)
@@ -941,65 +623,10 @@ sf_status sf_destroy(sf_ctx* c) {
 // ===========================================================================
 // Mixed-resolution batches
 // ===========================================================================
-struct sf_batch {
-    int n = 0;
-    int method = SF_METHOD_DISPARITY, depth_type = SF_DEPTH_F32;
-    float depth_scale = 1e-3f;
-    int min_valid = 3, require_center = 1;
-    sf::FrameDesc* d_desc = nullptr;
-    int3* d_hitems = nullptr;
-    int3* d_vitems = nullptr;
-    int n_h = 0, n_v = 0;
-    unsigned* d_counters = nullptr;  // [2]
-    unsigned* d_vmax = nullptr;      // [n]
-    float* d_rays = nullptr;
-    void* d_planes = nullptr;
-    size_t stride = 0;
-    size_t hsmem = 0;
-    int grid_h = 0, grid_v = 0;
-    long long pixels = 0;
-    bool use_graph = false;
-    cudaStream_t cap = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
-
 namespace {
 
-template <int DT, int M>
-sf_status batch_enqueue_t(sf_batch* b, cudaStream_t st) {
-    SF_CUDA(cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(unsigned), st));
-    SF_CUDA(cudaMemsetAsync(b->d_vmax, 0, sizeof(unsigned) * b->n, st));
-    if (!(DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD))
-        sf::range_batch_kernel<DT, M><<<dim3(16, b->n), 256, 0, st>>>(b->d_desc, b->d_vmax);
-    sf::hpass_batch_kernel<DT, M><<<b->grid_h, sf::kHThreads, b->hsmem, st>>>(
-        b->d_desc, b->d_hitems, b->n_h, b->d_counters, b->d_vmax, b->d_planes, b->stride, sf::Codec{b->depth_scale, 0, 0});
-    sf::vpass_batch_kernel<DT, M><<<b->grid_v, sf::kVThreads, 0, st>>>(b->d_desc, b->d_vitems, b->n_v,
-                                                                        b->d_counters + 1, b->d_vmax, b->d_planes,
-                                                                        b->stride, sf::Codec{b->depth_scale, 0, 0}, b->min_valid,
-                                                                        b->require_center);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
-    return SF_OK;
-}
-
 sf_status batch_enqueue(sf_batch* b, cudaStream_t st) {
-    if (b->depth_type == SF_DEPTH_F32)
-        return b->method == SF_METHOD_DISPARITY ? batch_enqueue_t<SF_DEPTH_F32, SF_METHOD_DISPARITY>(b, st)
-                                                : batch_enqueue_t<SF_DEPTH_F32, SF_METHOD_STANDARD>(b, st);
-    return b->method == SF_METHOD_DISPARITY ? batch_enqueue_t<SF_DEPTH_U16, SF_METHOD_DISPARITY>(b, st)
-                                            : batch_enqueue_t<SF_DEPTH_U16, SF_METHOD_STANDARD>(b, st);
-}
-
-template <int DT, int M>
-void batch_grids(sf_batch* b, int sms) {
-    int nb = 0;
-    cudaFuncSetAttribute(sf::hpass_batch_kernel<DT, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->hsmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sf::hpass_batch_kernel<DT, M>, sf::kHThreads, b->hsmem);
-    b->grid_h = std::max(1, nb) * sms;
-    nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sf::vpass_batch_kernel<DT, M>, sf::kVThreads, 0);
-    b->grid_v = std::max(1, nb) * sms;
+    return b->depth_type == SF_DEPTH_F32 ? sfh::batch_enqueue_f32(b, st) : sfh::batch_enqueue_u16(b, st);
 }
 
 }  // namespace
@@ -1060,7 +687,7 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
         if (band < 8 || band > 1024) return fail(SF_ERR_INVALID_ARG, "frame %d: vband must be in [8, 1024]", f);
         sf::FrameDesc& d = desc[f];
         d.depth = F.depth; d.normals = F.normals; d.offsets = F.offsets; d.curvature = F.curvature;
-        d.W = F.W; d.H = F.H; d.r = (F.window - 1) / 2; d.bits = quant_bits(method, F.window);
+        d.W = F.W; d.H = F.H; d.r = (F.window - 1) / 2; d.bits = sfh::quant_bits(method, F.window);
         d.Wp = (F.W + 63) / 64 * 64; d.seg = seg; d.band = band;
         d.a = (float)(1.0 / K.fx); d.b = (float)(1.0 / K.fy);
         d.pofs = stride;
@@ -1117,19 +744,14 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
     if (e == cudaSuccess) e = cudaMemcpy(b->d_vitems, vitems.data(), sizeof(int3) * vitems.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_vmax, sizeof(unsigned) * n_frames);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_planes, plane_bytes_per_frame(method, stride));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_planes, sfh::plane_bytes_per_frame(method, stride));
     if (e != cudaSuccess) { sf_batch_destroy(b); return fail(SF_ERR_ALLOC, "batch buffers: %s", cudaGetErrorString(e)); }
     b->hsmem = sizeof(int) * sf::kHThreads * (size_t)((max_seg + 2 * max_r) | 1);
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (depth_type == SF_DEPTH_F32) {
-        if (method == SF_METHOD_DISPARITY) batch_grids<SF_DEPTH_F32, SF_METHOD_DISPARITY>(b, sms);
-        else batch_grids<SF_DEPTH_F32, SF_METHOD_STANDARD>(b, sms);
-    } else {
-        if (method == SF_METHOD_DISPARITY) batch_grids<SF_DEPTH_U16, SF_METHOD_DISPARITY>(b, sms);
-        else batch_grids<SF_DEPTH_U16, SF_METHOD_STANDARD>(b, sms);
-    }
+    if (depth_type == SF_DEPTH_F32) sfh::batch_grids_f32(b, sms);
+    else sfh::batch_grids_u16(b, sms);
     e = cudaGetLastError();
     if (e != cudaSuccess) { sf_batch_destroy(b); return cuda_fail(e, "batch kernel attributes"); }
     if (use_graph) {
@@ -1219,9 +841,7 @@ sf_status static_scratch_base(void** out) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, sf::g_static_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "sf_fit_static: cudaGetSymbolAddress");
-        const int IW = 128 + 2 * sf::kMaxR;
-        const int smem = (int)(sizeof(int) * sf::kHThreads * (size_t)(IW | 1));
-        set_hpass_smem(smem);
+        set_kernel_attributes();
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "sf_fit_static: kernel attributes");
         g_static_base[dev] = p;
@@ -1261,7 +881,7 @@ extern "C" sf_status sf_fit_static(const sf_intrinsics* K, int W, int H, int win
     const size_t off_tx = 256;
     const size_t off_ty = off_tx + align256(sizeof(float) * W);
     const size_t off_planes = off_ty + align256(sizeof(float) * H);
-    const size_t need = off_planes + plane_bytes_per_frame(method, plane_elems);
+    const size_t need = off_planes + sfh::plane_bytes_per_frame(method, plane_elems);
     if (need > sf::kStaticScratchBytes)
         return fail(SF_ERR_INVALID_ARG,
                     "sf_fit_static: a %dx%d frame needs %zu bytes of scratch, more than the %zu-byte static array "
@@ -1291,16 +911,9 @@ extern "C" sf_status sf_fit_static(const sf_intrinsics* K, int W, int H, int win
         sf::ray_table_kernel<<<(n + 255) / 256, 256, 0, st>>>(K->fx, K->fy, K->cx, K->cy, K->dx, K->dy, W, H, c.tx,
                                                             c.ty);
     }
-    // launch_pass clears the quantum word itself (cudaMemsetAsync) before use.
-    if (depth_type == SF_DEPTH_F32) {
-        s = method == SF_METHOD_DISPARITY
-                ? launch_pass<SF_DEPTH_F32, SF_METHOD_DISPARITY>(&c, 1, depth, normals, offsets, curvature, nullptr, st)
-                : launch_pass<SF_DEPTH_F32, SF_METHOD_STANDARD>(&c, 1, depth, normals, offsets, curvature, nullptr, st);
-    } else {
-        s = method == SF_METHOD_DISPARITY
-                ? launch_pass<SF_DEPTH_U16, SF_METHOD_DISPARITY>(&c, 1, depth, normals, offsets, curvature, nullptr, st)
-                : launch_pass<SF_DEPTH_U16, SF_METHOD_STANDARD>(&c, 1, depth, normals, offsets, curvature, nullptr, st);
-    }
+    // the pass clears the quantum word itself (cudaMemsetAsync) before use
+    s = depth_type == SF_DEPTH_F32 ? sfh::fit_pass_f32(&c, 1, depth, normals, offsets, curvature, nullptr, st)
+                                   : sfh::fit_pass_u16(&c, 1, depth, normals, offsets, curvature, nullptr, st);
     // c points into the static array: nothing to free
     c.tx = nullptr; c.ty = nullptr; c.vmax = nullptr; c.planes = nullptr;
     return s;

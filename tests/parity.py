@@ -3,11 +3,12 @@ import numpy as np
 
 # Tolerances for the floating-point outputs: normal angle 1e-3 rad; offset
 # 1e-4 relative, measured against the distance |mu| of the window's (weighted)
-# centroid from the camera, beyond the part |dn| |mu| that the normal's own
-# error dn carries into d = -n . mu.  Since d = -n . mu, |d| <= |mu| and an error dn in
-# the normal moves d by up to |dn| |mu|: for windows seen edge-on (d -> 0) a
-# relative error in d itself is unbounded for any finite-precision normal,
-# while |dd| / |mu| stays well-defined; for head-on windows the two coincide.
+# centroid from the camera: |d - d_ref| <= 1e-4 |mu|, and for head-on windows
+# (|d_ref| >= 0.1 |mu|) also |d - d_ref| <= 1e-4 |d_ref|.  Since d = -n . mu,
+# |d| <= |mu| and an error dn in the normal moves d by up to |dn| |mu|: for
+# windows seen edge-on (d -> 0) a relative error in d itself is unbounded for
+# any finite-precision normal, while |dd| / |mu| stays well-defined; for
+# head-on windows the two coincide.
 # Where the fitted plane passes the camera centre closer than the offset
 # tolerance (|d| <= 1e-4 |mu|) the orientation rule (d >= 0) has nothing to
 # decide at that tolerance, so normals and offsets are compared up to sign.
@@ -73,9 +74,7 @@ def compare(gpu, ref, *, angle_tol=ANGLE_TOL, offset_tol=OFFSET_TOL, gap_min=GAP
     ang = np.where(sign_free[good], np.minimum(ang, flipped), ang)
     err_d = np.abs(np.where(sign_free[good], np.abs(d[good]), d[good]).astype(np.float64) -
                    np.where(sign_free[good], np.abs(ref["offsets"][good]), ref["offsets"][good])) / mu[good]
-    # d = -n . mu: a normal off by ang moves d by up to ang |mu|; the offset test
-    # checks the rest (the offset's own error), bounded by offset_tol
-    rel = np.maximum(err_d - ang, 0.0)
+    rel = err_d
     cerr = np.abs(c[good].astype(np.float64) - ref["curvature"][good])
     stats.update(good=int(good.sum()), max_angle=float(ang.max(initial=0)), max_offset_rel=float(rel.max(initial=0)),
                  max_curv=float(cerr.max(initial=0)), degenerate=int((ok & ~good).sum()))
@@ -91,6 +90,8 @@ def compare(gpu, ref, *, angle_tol=ANGLE_TOL, offset_tol=OFFSET_TOL, gap_min=GAP
     headon = good & (np.abs(np.where(ok, ref["offsets"], 0)) >= 0.1 * mu)
     stats["max_offset_rel_headon"] = float((np.abs(d[headon].astype(np.float64) - ref["offsets"][headon]) /
                                             np.abs(ref["offsets"][headon])).max(initial=0))
+    assert stats["max_offset_rel_headon"] <= offset_tol, "%s: head-on offset %g > %g" % (
+        label, stats["max_offset_rel_headon"], offset_tol)
     if check_degenerate and (ok & ~good).any():
         bad = ok & ~good
         R = schur(ref["moments"][bad])

@@ -23,6 +23,18 @@ from paper_2103_06644_gb300 import SurfaceFitter  # noqa: E402
 
 GAP_MIN = 1e-2
 REL_TOL = 2e-3  # of the largest gradient magnitude in the frame
+# and per pixel: |g - g_ref| <= PIX_REL |g_ref| + PIX_FLOOR max |g_ref|
+PIX_REL = 1e-3
+PIX_FLOOR = 1e-5
+
+
+def _check_per_pixel(g, ref, sel, label=""):
+    scale = np.abs(ref[sel]).max()
+    bound = PIX_REL * np.abs(ref[sel]) + PIX_FLOOR * scale
+    excess = np.abs(g[sel] - ref[sel]) / bound
+    assert excess.max() <= 1.0, "%s: per-pixel gradient error %g of its bound (%d pixels over)" % (
+        label, excess.max(), int((excess > 1).sum()))
+    return float(excess.max())
 
 
 def _box_min(a, r):
@@ -62,6 +74,7 @@ def _compare(depth, intr, k, method, gn, gd, gk):
     err = np.abs(g[sel] - ref[sel]).max() / scale
     assert sel.mean() > 0.5
     assert err < REL_TOL, err
+    _check_per_pixel(g, ref, sel, "%s k=%d" % (method, k))
     return err, sel.mean()
 
 
@@ -142,3 +155,4 @@ def test_backward_uint16_frame_batch(method):
         assert sel.mean() > 0.4
         err = np.abs(g[i][sel] - ref[sel]).max() / np.abs(ref[sel]).max()
         assert err < REL_TOL, (i, err)
+        _check_per_pixel(g[i], ref, sel, "frame %d" % i)

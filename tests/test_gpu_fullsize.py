@@ -9,7 +9,8 @@ tests/parity.py.
 
 Workloads (synthetic, seeded as in the benchmark):
 - 8 x 1920x1080 + 2 x 4096x3072 float32 frames, 0.3-10 m, k = 31, each
-  resolution fitted as one stacked batch (both forms);
+  resolution fitted as one stacked batch (both forms) in precision mode 1
+  (tau = 1e-3), judged on every sampled window with gamma >= 1e-6;
 - 30 x 1280x720 uint16 structured-light frames, k in {5, 9, 15} (both forms);
 - the 64-frame mixed batch (320x240 .. 1920x1080, k in {5, 7, 11, 21}) with
   autotuned tiles, replayed from a CUDA graph;
@@ -55,21 +56,23 @@ def at(t, xy):
     return a[xy[:, 1], xy[:, 0]]
 
 
-def check_frame(outs, counts, depth, intr, k, method, xy, label):
+def check_frame(outs, counts, depth, intr, k, method, xy, label, **kw):
     ref = oracle.fit_at(depth, intr, k, xy, method)
     gpu = tuple(at(t, xy) for t in outs) + (at(counts, xy),)
-    return compare(gpu, ref, label=label)
+    return compare(gpu, ref, label=label, **kw)
 
 
 @pytest.mark.parametrize("method", ["disparity", "standard"])
 def test_wide_range_1080p_and_4k_k31(method):
-    """The benchmark's batch: 8 x 1920x1080 and 2 x 4096x3072, k = 31, fitted per resolution."""
+    """The benchmark's batch: 8 x 1920x1080 and 2 x 4096x3072, k = 31, fitted per resolution in the
+    benchmark's precision mode (1, tau = 1e-3)."""
     K = 31
     for (W, H, n, seed0) in [(1920, 1080, 8, scenes.BASE_SEED + 300), (4096, 3072, 2, scenes.BASE_SEED + 400)]:
         intr = scenes.Intrinsics.scaled(W, H)
         frames = [scenes.wide_range_frame(seed0 + i, intr, W, H) for i in range(n)]
         d = torch.from_numpy(np.stack(frames)).cuda()
         f = SurfaceFitter(intr.as_tuple(), W, H, K, method=method)
+        f.set_precision(1, 1e-3)
         out = (torch.empty((n, H, W, 3), device="cuda"), torch.empty((n, H, W), device="cuda"),
                torch.empty((n, H, W), device="cuda"))
         f.fit(d, out=out)
@@ -80,7 +83,7 @@ def test_wide_range_1080p_and_4k_k31(method):
         for i in range(n):
             xy = sample_xy(seed0 + 50 + i, W, H, K)
             s = check_frame(tuple(t[i] for t in out), withc[3][i], frames[i], intr.as_tuple(), K, method, xy,
-                            "%dx%d frame %d %s" % (W, H, i, method))
+                            "%dx%d frame %d %s" % (W, H, i, method), gap_min=1e-6)
             assert s["good"] > 0.8 * s["valid"], s
         f.close()
         del d, out, withc

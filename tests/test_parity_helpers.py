@@ -45,7 +45,9 @@ def _rotate(n, ang):
 
 
 @pytest.mark.parametrize("what", ["normal 2e-3 rad", "offset 3e-4 |mu|", "flipped orientation", "count + 1",
-                                  "lost fit", "extra fit", "curvature + 3e-5"])
+                                  "lost fit", "extra fit", "curvature + 3e-5",
+                                  "offset 1.5e-4 |mu| beside a normal off by 1e-4 rad",
+                                  "head-on offset 1.2e-4 relative"])
 def test_planted_mistake_is_caught(frame, what):
     ref, gpu, (y, x), mu = frame
     n, d, c, cnt = _copy(gpu)
@@ -56,6 +58,12 @@ def test_planted_mistake_is_caught(frame, what):
     elif what == "flipped orientation":
         n[y, x] = -n[y, x]
         d[y, x] = -d[y, x]
+    elif what == "offset 1.5e-4 |mu| beside a normal off by 1e-4 rad":
+        # the offset's own error may not hide behind the normal's
+        n[y, x] = _rotate(ref["normals"][y, x], 1e-4)
+        d[y, x] += 1.5e-4 * mu
+    elif what == "head-on offset 1.2e-4 relative":
+        d[y, x] *= 1.0 + 1.2e-4
     elif what == "count + 1":
         cnt[y, x] += 1
     elif what == "lost fit":
