@@ -121,14 +121,16 @@ sf_status sf_set_params(sf_ctx* ctx, int method, int depth_type, float depth_sca
  * sf_set_disparity_model -- the sensor model of SF_DEPTH_DISPARITY_U16 input,
  * 1/Z = alpha D + beta (1/metres; e.g. alpha = 1/(f b s) for a stereo pair of
  * baseline b and focal length f reporting disparity in 1/s pixel, beta = 0).
- * The library represents the model exactly in integers as
- * 1/Z = (|alpha| / 128) (sign(alpha) 128 D + round(128 beta / |alpha|)): beta
- * is kept to 1/128 of a disparity unit, alpha exactly.  A pixel is missing
- * when D == 0 or its 1/Z <= 0.
+ * The library holds the model as 1/Z = (|alpha| / 128) (sign(alpha) 128 D + B + f)
+ * with B + f = 128 beta / |alpha| (B an integer, f in [0, 1) stored as a
+ * float32): the exact window sums hold the integers sign(alpha) 128 D + B,
+ * and the fraction f, common to every pixel, enters the solve through the
+ * mean disparity.  The model is therefore reproduced to float32 rounding of
+ * |alpha| / 128 (a common scale, which moves no normal) and of f.  A pixel is
+ * missing when D == 0 or its 1/Z <= 0.
  * Errors: SF_ERR_INVALID_ARG unless alpha is finite and nonzero and
  * |128 beta / alpha| <= 2^23; a later disparity-form fit rejects a model
- * whose largest value 128 * 65535 + |round(128 beta / alpha)| times the
- * window size k reaches 2^31.
+ * whose largest value 128 * 65535 + |B| + 1 times the window size k reaches 2^31.
  * Default: alpha = 1, beta = 0.
  */
 sf_status sf_set_disparity_model(sf_ctx* ctx, double alpha, double beta);
@@ -291,15 +293,17 @@ sf_status sf_batch_destroy(sf_batch* batch);
  * adjustment (dx, dy) to a pixel's coordinates before its ray is formed; this
  * gives every pixel its own, added to the intrinsics' dx, dy):
  *   ddx, ddy   host float [H][W] in pixels, |value| < 16, finite; read during
- *              the call and stored on the device rounded to 1/256 pixel
+ *              the call and stored on the device rounded to 1/2^18 pixel
  *              (both NULL: remove the table)
  * With a table, sf_fit / sf_fit_ex / sf_fit_host of SF_METHOD_DISPARITY (either
  * constraint, precision mode 0) use the per-pixel rays; every other method,
  * precision modes 1 and 2, sf_fit_backward and sf_quadtree return
- * SF_ERR_UNSUPPORTED while a table is set.  The table's scratch is 64 B per
- * pixel instead of 20.  Synchronous: waits for the device to finish queued
- * work before replacing a table.  Errors: SF_ERR_INVALID_ARG (one table
- * NULL, entry out of range), SF_ERR_ALLOC, SF_ERR_CUDA.
+ * SF_ERR_UNSUPPORTED while a table is set.  The table takes 8 B per pixel and
+ * its scratch 84 B per pixel instead of 20.  Synchronous: waits for the
+ * context's device to finish its queued work before replacing a table; do not
+ * call it while a stream capture is in progress on that device.
+ * Errors: SF_ERR_INVALID_ARG (one table NULL, entry out of range),
+ * SF_ERR_ALLOC, SF_ERR_CUDA.
  */
 sf_status sf_set_delta_table(sf_ctx* ctx, const float* ddx, const float* ddy);
 

@@ -89,15 +89,13 @@ def depth_to_f64(depth: np.ndarray, depth_scale: float = 1e-3) -> np.ndarray:
 
 
 def depth_from_disparity(D: np.ndarray, alpha: float, beta: float) -> np.ndarray:
-    """FP64 depth (metres, 0 = missing) of raw disparity D under the sensor model 1/Z = alpha D + beta,
-    as the disparity input is defined: 1/Z = (|alpha| / 128) (sign(alpha) 128 D + round(128 beta / |alpha|)),
-    i.e. beta kept to 1/128 of a disparity unit; D == 0 or 1/Z <= 0 is missing."""
-    D = np.asarray(D).astype(np.int64)
-    q = abs(alpha) / 128.0
-    w = (128 if alpha > 0 else -128) * D + int(np.round(128.0 * beta / abs(alpha)))
+    """FP64 depth (metres, 0 = missing) of raw disparity D under the sensor model 1/Z = alpha D + beta
+    (the disparity input of the paper's conclusion); D == 0 or 1/Z <= 0 is missing."""
+    D = np.asarray(D).astype(np.float64)
+    w = alpha * D + beta
     ok = (D != 0) & (w > 0)
     Z = np.zeros(D.shape)
-    Z[ok] = 1.0 / (q * w[ok].astype(np.float64))
+    Z[ok] = 1.0 / w[ok]
     return Z
 
 

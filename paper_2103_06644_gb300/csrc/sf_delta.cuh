@@ -1,65 +1,68 @@
 // sf_delta.cuh -- per-pixel ray adjustments (a delta table) for the disparity
-// form (device code, included by surffit.cu after sf_kernels.cuh).
+// form (device code, included after sf_kernels.cuh).
 //
 // Eq. 1 and Eq. 10 add an adjustment (dx, dy) to a pixel's coordinates before
 // its ray is formed.  With one adjustment per pixel the ray of pixel q in the
 // window of p is
-//   tx_q = tx_p + a (j + D_q / 256),   ty_q = ty_p + b (i + E_q / 256)
+//   tx_q = tx_p + a (j + D_q / S),   ty_q = ty_p + b (i + E_q / S)
 // (a = 1/fx, b = 1/fy, tx_p, ty_p the rays without the table, D, E the table
-// in 1/256 pixel), so every sum over the window's pixel offsets j, i becomes a
-// sum over the shifted offsets jh = j + D/256, ih = i + E/256.  With integer
-// D, E these sums stay exact integers, in units of 1/256 (first moments) and
-// 1/65536 (second moments): the row pass adds the sums of D, D j, E, E j, D^2,
-// E^2, D E, v D and v E (valid pixels) to its usual ones, the column pass
-// slides them (with i weights where a moment needs them), and the build forms
-// the shifted moments exactly before the usual centring and solve.
+// in units of 1/S pixel, S = 2^18), so every sum over the window's pixel
+// offsets j, i becomes a sum over the shifted offsets jh = j + D/S,
+// ih = i + E/S.  With integer D, E these sums stay exact integers, in units of
+// 1/S (first moments) and 1/S^2 (second moments): the row pass adds the sums
+// of D, D j, E, E j, D^2, E^2, D E, v D and v E (valid pixels) to its usual
+// ones, the column pass slides them (with i weights where a moment needs
+// them), and the build forms the shifted moments exactly (128-bit products)
+// before the usual centring and solve.
+//
+// The resolution: the table's rounding to 1/S pixel moves each pixel's ray
+// like a pixel-position error of up to 1/(2S); at S = 2^18 that keeps the
+// normal within ~1e-5 rad of the unrounded rays on 5 x 5 windows (the error
+// scales with 1/S and falls with the window size).
 #pragma once
 
 namespace sf {
 
-constexpr int kDeltaScale = 256;  // table units per pixel
+constexpr int kDeltaScale = 1 << 18;  // table units per pixel
 constexpr int kDeltaMax = 16 * kDeltaScale - 1;
 // scratch planes of the table path: int32 mask, sum v, sum v j (low word),
-// sum D, sum D j, sum E, sum E j, sum D^2, sum E^2, sum D E; int64 sum v^2,
-// sum v D, sum v E (20 + 44 = 64 B per pixel)
-constexpr int kDeltaPlanes32 = 10;
-constexpr int kDeltaPlanes64 = 3;
-
-// a table entry packs D (low 16 bits) and E (high 16 bits), both signed
-__device__ __forceinline__ int delta_x(int p) { return (int)(int16_t)(p & 0xffff); }
-__device__ __forceinline__ int delta_y(int p) { return p >> 16; }
+// sum D, sum E; int64 sum v^2, sum D j, sum E j, sum D^2, sum E^2, sum D E,
+// sum v D, sum v E (20 + 64 = 84 B per pixel)
+constexpr int kDeltaPlanes32 = 5;
+constexpr int kDeltaPlanes64 = 8;
 
 // Row sums of one row over one 32-column output segment, with the table's sums.
-__device__ __forceinline__ void hpass_row_delta(const int* row, const int* drow, int x0, int xend, int y, int H,
-                                                int r, const Planes& P, size_t pofs) {
+// drow / erow: the row's table entries D and E (tile-relative like row).
+__device__ __forceinline__ void hpass_row_delta(const int* row, const int* drow, const int* erow, int x0, int xend,
+                                                int y, int H, int r, const Planes& P, size_t pofs) {
     HRowState<SF_METHOD_DISPARITY> S;
-    int d0 = 0, d1 = 0, e0 = 0, e1 = 0, dd = 0, ee = 0, de = 0;
-    int64_t vd = 0, ve = 0;
+    int64_t d0 = 0, d1 = 0, e0 = 0, e1 = 0, dd = 0, ee = 0, de = 0, vd = 0, ve = 0;
     S.init(row, 0, r);
     for (int j = -r; j <= r; ++j) {
         const int v = row[j + r];
         if (v >= 0) {
-            const int p = drow[j + r], D = delta_x(p), E = delta_y(p);
+            const int64_t D = drow[j + r], E = erow[j + r];
             d0 += D; d1 += D * j; e0 += E; e1 += E * j;
             dd += D * D; ee += E * E; de += D * E;
             vd += (int64_t)v * D; ve += (int64_t)v * E;
         }
     }
     for (int xb = x0; xb < xend; xb += 4) {
-        int32_t hmv[4], c0v[4], c1v[4], t[7][4];
-        int64_t c2v[4], vdv[4], vev[4];
+        int32_t hmv[4], c0v[4], c1v[4], t32[2][4];
+        int64_t t64[8][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int x = xb + u;
             hmv[u] = pack_mask(S.h0, S.h1, S.h2, (int)(S.a1 >> 32));
-            c0v[u] = (int)S.a0; c1v[u] = lo32(S.a1); c2v[u] = S.s0;
-            t[0][u] = d0; t[1][u] = d1; t[2][u] = e0; t[3][u] = e1; t[4][u] = dd; t[5][u] = ee; t[6][u] = de;
-            vdv[u] = vd; vev[u] = ve;
+            c0v[u] = (int)S.a0; c1v[u] = lo32(S.a1);
+            t32[0][u] = (int32_t)d0; t32[1][u] = (int32_t)e0;
+            t64[0][u] = S.s0; t64[1][u] = d1; t64[2][u] = e1; t64[3][u] = dd; t64[4][u] = ee; t64[5][u] = de;
+            t64[6][u] = vd; t64[7][u] = ve;
             if (x + 1 < xend) {
                 const int c = x - x0;
                 const int vo = row[c], vi = row[c + 2 * r + 1];
-                const int po = vo >= 0 ? drow[c] : 0, pi = vi >= 0 ? drow[c + 2 * r + 1] : 0;
-                const int Do = delta_x(po), Eo = delta_y(po), Di = delta_x(pi), Ei = delta_y(pi);
+                const int64_t Do = vo >= 0 ? drow[c] : 0, Eo = vo >= 0 ? erow[c] : 0;
+                const int64_t Di = vi >= 0 ? drow[c + 2 * r + 1] : 0, Ei = vi >= 0 ? erow[c + 2 * r + 1] : 0;
                 slide2(d0, d1, Do, Di, r);
                 slide2(e0, e1, Eo, Ei, r);
                 dd += Di * Di - Do * Do; ee += Ei * Ei - Eo * Eo; de += Di * Ei - Do * Eo;
@@ -74,29 +77,27 @@ __device__ __forceinline__ void hpass_row_delta(const int* row, const int* drow,
             *reinterpret_cast<int4*>(P.c32(1) + o) = make_int4(c0v[0], c0v[1], c0v[2], c0v[3]);
             *reinterpret_cast<int4*>(P.c32(2) + o) = make_int4(c1v[0], c1v[1], c1v[2], c1v[3]);
 #pragma unroll
-            for (int q = 0; q < 7; ++q)
-                *reinterpret_cast<int4*>(P.c32(3 + q) + o) = make_int4(t[q][0], t[q][1], t[q][2], t[q][3]);
-            int64_t* a = P.c64(0) + o;
-            int64_t* b = P.c64(1) + o;
-            int64_t* c = P.c64(2) + o;
-            *reinterpret_cast<longlong2*>(a) = make_longlong2(c2v[0], c2v[1]);
-            *reinterpret_cast<longlong2*>(a + 2) = make_longlong2(c2v[2], c2v[3]);
-            *reinterpret_cast<longlong2*>(b) = make_longlong2(vdv[0], vdv[1]);
-            *reinterpret_cast<longlong2*>(b + 2) = make_longlong2(vdv[2], vdv[3]);
-            *reinterpret_cast<longlong2*>(c) = make_longlong2(vev[0], vev[1]);
-            *reinterpret_cast<longlong2*>(c + 2) = make_longlong2(vev[2], vev[3]);
+            for (int q = 0; q < 2; ++q)
+                *reinterpret_cast<int4*>(P.c32(3 + q) + o) = make_int4(t32[q][0], t32[q][1], t32[q][2], t32[q][3]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                int64_t* a = P.c64(q) + o;
+                *reinterpret_cast<longlong2*>(a) = make_longlong2(t64[q][0], t64[q][1]);
+                *reinterpret_cast<longlong2*>(a + 2) = make_longlong2(t64[q][2], t64[q][3]);
+            }
         } else {
             for (int u = 0; u < 4 && xb + u < xend; ++u) {
                 P.p32[o + u] = hmv[u]; P.c32(1)[o + u] = c0v[u]; P.c32(2)[o + u] = c1v[u];
-                for (int q = 0; q < 7; ++q) P.c32(3 + q)[o + u] = t[q][u];
-                P.c64(0)[o + u] = c2v[u]; P.c64(1)[o + u] = vdv[u]; P.c64(2)[o + u] = vev[u];
+                for (int q = 0; q < 2; ++q) P.c32(3 + q)[o + u] = t32[q][u];
+                for (int q = 0; q < 8; ++q) P.c64(q)[o + u] = t64[q][u];
             }
         }
     }
 }
 
 // Row pass with the table: tiles of 128 rows x 32 columns; shared memory holds
-// the quantised depth tile and the table's tile, each kHThreads x ((32 + 2r) | 1).
+// the quantised depth tile and the table's two tiles, each kHThreads x
+// ((32 + 2r) | 1).  dtab holds the table's D plane then its E plane ([H][W] each).
 template <int DT>
 __global__ void __launch_bounds__(kHThreads) hpass_delta_kernel(const void* __restrict__ depth,
                                                                 const int* __restrict__ dtab, int W, int H, int r,
@@ -112,15 +113,20 @@ __global__ void __launch_bounds__(kHThreads) hpass_delta_kernel(const void* __re
     const int x0 = blockIdx.x * seg, y0 = blockIdx.y * kHThreads;
     const int IW = seg + 2 * r, pitch = IW | 1, rows = min(kHThreads, H - y0);
     int* dt = tile + kHThreads * pitch;
+    int* et = dt + kHThreads * pitch;
+    const size_t fe = (size_t)W * H;
     load_tile<DT, SF_METHOD_DISPARITY, 2>(dframe, W, r, sc, scale, x0, y0, rows, IW, pitch, tile);
     for (int idx = threadIdx.x; idx < rows * IW; idx += kHThreads) {
         const int ry = idx / IW, cx = idx - ry * IW, x = x0 - r + cx;
-        dt[ry * pitch + cx] = (x >= 0 && x < W) ? __ldg(dtab + (size_t)(y0 + ry) * W + x) : 0;
+        const bool in = x >= 0 && x < W;
+        const size_t g = (size_t)(y0 + ry) * W + x;
+        dt[ry * pitch + cx] = in ? __ldg(dtab + g) : 0;
+        et[ry * pitch + cx] = in ? __ldg(dtab + fe + g) : 0;
     }
     __syncthreads();
     if ((int)threadIdx.x < rows)
-        hpass_row_delta(tile + threadIdx.x * pitch, dt + threadIdx.x * pitch, x0, min(x0 + seg, W), y0 + threadIdx.x,
-                        H, r, P, (size_t)f * plane_elems);
+        hpass_row_delta(tile + threadIdx.x * pitch, dt + threadIdx.x * pitch, et + threadIdx.x * pitch, x0,
+                        min(x0 + seg, W), y0 + threadIdx.x, H, r, P, (size_t)f * plane_elems);
 }
 
 // Column sums of the table path: the usual disparity sums (DispState on the
@@ -129,74 +135,85 @@ __global__ void __launch_bounds__(kHThreads) hpass_delta_kernel(const void* __re
 // v D, v E are plain sums of the row sums.
 struct DispDeltaState {
     DispState B;
-    const int32_t* pd[7];  // sum D, sum D j, sum E, sum E j, sum D^2, sum E^2, sum D E
-    const int64_t* pv[2];  // sum v D, sum v E
-    int TD = 0, TDi = 0, TDj = 0, TE = 0, TEi = 0, TEj = 0;
-    int64_t TDD = 0, TEE = 0, TDE = 0, TwD = 0, TwE = 0;
-    int32_t qo[7] = {0, 0, 0, 0, 0, 0, 0}, qi[7] = {0, 0, 0, 0, 0, 0, 0};
-    int64_t wo[2] = {0, 0}, wi[2] = {0, 0};
+    const int32_t* pd[2];  // row sum D, row sum E
+    const int64_t* pq[7];  // row sums D j, E j, D^2, E^2, D E, v D, v E
+    int64_t TD = 0, TDi = 0, TE = 0, TEi = 0;
+    int64_t T[7] = {0, 0, 0, 0, 0, 0, 0};  // window sums D j, E j, D^2, E^2, D E, v D, v E
+    int32_t qo[2] = {0, 0}, qi[2] = {0, 0};
+    int64_t wo[7] = {0, 0, 0, 0, 0, 0, 0}, wi[7] = {0, 0, 0, 0, 0, 0, 0};
     __device__ DispDeltaState(const Planes& P) : B(P) {
-        for (int q = 0; q < 7; ++q) pd[q] = P.c32(3 + q);
-        pv[0] = P.c64(1); pv[1] = P.c64(2);
+        pd[0] = P.c32(3); pd[1] = P.c32(4);
+        for (int q = 0; q < 7; ++q) pq[q] = P.c64(1 + q);
     }
     __device__ __forceinline__ void init(size_t pb, int rs, int H, int y0, int r) {
         B.init(pb, rs, H, y0, r);
         const int ylo = max(y0 - r, 0), yhi = min(y0 + r, H - 1);
         for (int yy = ylo; yy <= yhi; ++yy) {
             const size_t o = pb + (size_t)yy * rs;
-            const int i = yy - y0;
-            const int d0 = __ldg(pd[0] + o), e0 = __ldg(pd[2] + o);
-            TD += d0; TDi += i * d0; TDj += __ldg(pd[1] + o);
-            TE += e0; TEi += i * e0; TEj += __ldg(pd[3] + o);
-            TDD += __ldg(pd[4] + o); TEE += __ldg(pd[5] + o); TDE += __ldg(pd[6] + o);
-            TwD += __ldg(pv[0] + o); TwE += __ldg(pv[1] + o);
+            const int64_t i = yy - y0;
+            const int64_t d0 = __ldg(pd[0] + o), e0 = __ldg(pd[1] + o);
+            TD += d0; TDi += i * d0;
+            TE += e0; TEi += i * e0;
+            for (int q = 0; q < 7; ++q) T[q] += __ldg(pq[q] + o);
         }
     }
     __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) {
         B.fetch(pb, rs, H, y, r);
         const int yo = y - r, yi = y + r + 1;
-        for (int q = 0; q < 7; ++q) { qo[q] = 0; qi[q] = 0; }
-        wo[0] = wo[1] = wi[0] = wi[1] = 0;
+        qo[0] = qo[1] = qi[0] = qi[1] = 0;
+        for (int q = 0; q < 7; ++q) { wo[q] = 0; wi[q] = 0; }
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * rs;
-            for (int q = 0; q < 7; ++q) qo[q] = __ldg(pd[q] + o);
-            wo[0] = __ldg(pv[0] + o); wo[1] = __ldg(pv[1] + o);
+            qo[0] = __ldg(pd[0] + o); qo[1] = __ldg(pd[1] + o);
+            for (int q = 0; q < 7; ++q) wo[q] = __ldg(pq[q] + o);
         }
         if (yi < H) {
             const size_t o = pb + (size_t)yi * rs;
-            for (int q = 0; q < 7; ++q) qi[q] = __ldg(pd[q] + o);
-            wi[0] = __ldg(pv[0] + o); wi[1] = __ldg(pv[1] + o);
+            qi[0] = __ldg(pd[0] + o); qi[1] = __ldg(pd[1] + o);
+            for (int q = 0; q < 7; ++q) wi[q] = __ldg(pq[q] + o);
         }
     }
     __device__ __forceinline__ void apply(int r) {
         B.apply(r);
-        slide2(TD, TDi, qo[0], qi[0], r);
-        TDj += qi[1] - qo[1];
-        slide2(TE, TEi, qo[2], qi[2], r);
-        TEj += qi[3] - qo[3];
-        TDD += (int64_t)qi[4] - qo[4]; TEE += (int64_t)qi[5] - qo[5]; TDE += (int64_t)qi[6] - qo[6];
-        TwD += wi[0] - wo[0]; TwE += wi[1] - wo[1];
+        slide2(TD, TDi, (int64_t)qo[0], (int64_t)qi[0], r);
+        slide2(TE, TEi, (int64_t)qo[1], (int64_t)qi[1], r);
+        for (int q = 0; q < 7; ++q) T[q] += wi[q] - wo[q];
     }
     __device__ __forceinline__ int count() const { return B.count(); }
 };
 
+// float32 value of a 128-bit integer (to float32 rounding): the magnitude's
+// 32-bit words scaled and summed from the top, then the sign
+__device__ __forceinline__ float from_i128(__int128 v) {
+    const bool neg = v < 0;
+    const unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const uint64_t hi = (uint64_t)(a >> 64), lo = (uint64_t)a;
+    float f = __uint2float_rn((uint32_t)(hi >> 32)) * 4294967296.f + __uint2float_rn((uint32_t)hi);
+    f = f * 4294967296.f + __uint2float_rn((uint32_t)(lo >> 32));
+    f = f * 4294967296.f + __uint2float_rn((uint32_t)lo);
+    return neg ? -f : f;
+}
+
 // The disparity window (as build_disparity) from the shifted offsets
-// jh = j + D/256, ih = i + E/256.  With S = 256, every shifted moment is an
-// exact integer: J = S sum jh, JJ = S^2 sum jh^2, JI = S^2 sum jh ih,
-// WJ = S sum w jh (w in units of qw), and the centred moments
-// n JJ - J^2 etc. are formed in int64 before the conversion to float.
+// jh = j + D/S, ih = i + E/S.  Every shifted moment is an exact integer:
+// J = S sum jh, JJ = S^2 sum jh^2, JI = S^2 sum jh ih, WJ = S sum w jh (w in
+// units of qw), and the centred moments n JJ - J^2 etc. are formed in
+// 128-bit integers before the conversion to float.  wfrac: the fractional
+// offset of disparity input (added to the mean disparity).
 __device__ __forceinline__ DispWindowT<float> build_disparity_delta(const DispDeltaState& st, float tx, float ty,
-                                                                    float a, float b) {
+                                                                    float a, float b, float wfrac) {
     using T = float;
     const DispState& s = st.B;
     const int64_t S = kDeltaScale;
     const int n = (int)s.n;
     const int64_t Sj = (int)s.Sj, Si = (int)s.Si, Sjj = (int)s.Sjj, Sji = (int)s.Sji, Sii = (int)s.Sii;
+    const int64_t TDj = st.T[0], TEj = st.T[1], TDD = st.T[2], TEE = st.T[3], TDE = st.T[4], TwD = st.T[5],
+                  TwE = st.T[6];
     const int64_t J = S * Sj + st.TD, I = S * Si + st.TE;
-    const int64_t JJ = S * S * Sjj + 2 * S * st.TDj + st.TDD;
-    const int64_t JI = S * S * Sji + S * (int64_t)st.TEj + S * (int64_t)st.TDi + st.TDE;
-    const int64_t II = S * S * Sii + 2 * S * st.TEi + st.TEE;
-    const int64_t WJ = S * s.Swj + st.TwD, WI = S * s.Swi + st.TwE;
+    const int64_t JJ = S * S * Sjj + 2 * S * TDj + TDD;
+    const int64_t JI = S * S * Sji + S * TEj + S * st.TDi + TDE;
+    const int64_t II = S * S * Sii + 2 * S * st.TEi + TEE;
+    const int64_t WJ = S * s.Swj + TwD, WI = S * s.Swi + TwE;
     const T nf = (T)n;
     const T inv_n = Fn<T>::rcp(nf);
     // exact re-centring of w on an integer m near its mean (as build_disparity)
@@ -211,13 +228,13 @@ __device__ __forceinline__ DispWindowT<float> build_disparity_delta(const DispDe
     const T fJ = Fn<T>::from_i64(J), fI = Fn<T>::from_i64(I);
     const T jb = fJ * iS * inv_n, ib = fI * iS * inv_n;
     const T inS2 = iS * iS * inv_n;
-    const T Cjj = Fn<T>::from_i64((int64_t)n * JJ - J * J) * inS2;
-    const T Cji = Fn<T>::from_i64((int64_t)n * JI - J * I) * inS2;
-    const T Cii = Fn<T>::from_i64((int64_t)n * II - I * I) * inS2;
+    const T Cjj = from_i128((__int128)n * JJ - (__int128)J * J) * inS2;
+    const T Cji = from_i128((__int128)n * JI - (__int128)J * I) * inS2;
+    const T Cii = from_i128((__int128)n * II - (__int128)I * I) * inS2;
     const T Cjw = (Fn<T>::from_i64(TWJ) - fJ * t0) * iS;
     const T Ciw = (Fn<T>::from_i64(TWI) - fI * t0) * iS;
     const T Cww = Fn<T>::from_i64(Tww) - fT0 * t0;
-    const T wbar = (T)m + t0;
+    const T wbar = (T)m + t0 + wfrac;
     const T inv_nw = Fn<T>::rcp(nf * wbar);
     const T dj = Cjw * inv_nw, di = Ciw * inv_nw, e = Cww * inv_nw;
     const T what = wbar + e;
@@ -257,6 +274,7 @@ __global__ void __launch_bounds__(kVThreads) vpass_delta_kernel(const void* __re
     const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * fe;
     const float q = quantum<DT, SF_METHOD_DISPARITY>(vmax_bits[f], bits, scale);
+    const float wfrac = DT == SF_DEPTH_DISPARITY_U16 ? scale.frac : 0.f;
     const Planes P(planes_base, (size_t)gridDim.z * plane_elems, kDeltaPlanes32);
     const size_t pb = plane_index((size_t)f * plane_elems, x, 0, H);
     const int y0 = blockIdx.y * band, y1 = min(y0 + band, H);
@@ -277,7 +295,7 @@ __global__ void __launch_bounds__(kVThreads) vpass_delta_kernel(const void* __re
         const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
         float nx = NAN, ny = NAN, nz = NAN, d = NAN, cu = NAN;
         if (ok) {
-            const DispWindowT<float> w = build_disparity_delta(S, tx, cal.ty[y], cal.a, cal.b);
+            const DispWindowT<float> w = build_disparity_delta(S, tx, cal.ty[y], cal.a, cal.b, wfrac);
             FitOut fo;
             if constexpr (U4) {
                 const float sw = q * (float)n * w.wbar;

@@ -27,9 +27,10 @@ struct sf_ctx {
     int hseg = 32;        // horizontal tile width (32, 64 or 128)
     int vband = 0;        // vertical band height (0: chosen from the grid size)
     float depth_scale = 1e-3f;
-    // SF_DEPTH_DISPARITY_U16: 1/Z = disp_q * (disp_mul * D + disp_add)
+    // SF_DEPTH_DISPARITY_U16: 1/Z = disp_q * (disp_mul * D + disp_add + disp_frac)
     float disp_q = 1.f / 128.f;
     int disp_mul = 128, disp_add = 0;
+    float disp_frac = 0.f;    // in [0, 1)
     int min_valid = 3;
     int require_center = 1;
     int device = 0;
@@ -50,7 +51,7 @@ struct sf_ctx {
     cudaEvent_t io_entry = nullptr;
     float* adj = nullptr;      // backward: per-window adjoint planes
     size_t adj_bytes = 0;
-    int* dtab = nullptr;       // per-pixel ray adjustments [H][W], packed (D, E) in 1/256 pixel, or none
+    int* dtab = nullptr;       // per-pixel ray adjustments: D plane then E plane [H][W], 1/2^18 pixel, or none
     // precision fallback
     int precision_mode = 0;    // 0 float32 solve, 1 + refinement where gap < tau, 2 refinement everywhere
     int constraint = SF_CONSTRAINT_UNIT3;  // normalisation of the implicit fits (Eq. 4)

@@ -54,14 +54,20 @@ constexpr float kRefineRounding = 3e-5f;
 // Depth decoding.  Codec: how a stored value becomes depth.
 //   SF_DEPTH_F32             metres (scale unused)
 //   SF_DEPTH_U16             raw * scale metres, raw == 0 missing
-//   SF_DEPTH_DISPARITY_U16   raw disparity D: 1/Z = scale * (dmul * D + dadd)
-//                            (dmul = +-128, dadd an integer: the sensor model
-//                            1/Z = alpha D + beta with beta to 1/128 of a
-//                            disparity unit); D == 0 or 1/Z <= 0 missing
+//   SF_DEPTH_DISPARITY_U16   raw disparity D: 1/Z = scale * (dmul * D + dadd + frac)
+//                            (dmul = +-128, dadd an integer and frac in [0, 1):
+//                            the sensor model 1/Z = alpha D + beta with
+//                            scale = |alpha| / 128 and dadd + frac =
+//                            128 beta / |alpha|); D == 0 or 1/Z <= 0 missing.
+//                            The integer part w = dmul D + dadd is what the
+//                            exact sums hold; frac shifts every value of a
+//                            window alike, so it enters the solve only through
+//                            the mean disparity.
 // ---------------------------------------------------------------------------
 struct Codec {
     float scale;
     int dmul, dadd;
+    float frac;
 };
 
 // Raw stored value: metres for float32, raw units for uint16 (0 = missing).
@@ -71,11 +77,12 @@ __device__ __forceinline__ float load_raw(const void* base, size_t idx) {
     return (float)__ldg(reinterpret_cast<const unsigned short*>(base) + idx);
 }
 
-// Disparity input: the integer w = dmul * D + dadd (units of scale), or -1.
+// Disparity input: the integer part w = dmul * D + dadd (units of scale) of a
+// valid pixel (w + frac > 0), or -1.
 __device__ __forceinline__ int disparity_units(float d_raw, const Codec& cd) {
     const int D = (int)d_raw;
     const int w = cd.dmul * D + cd.dadd;
-    return (D != 0 && w > 0) ? w : -1;
+    return (D != 0 && (cd.frac > 0.f ? w >= 0 : w > 0)) ? w : -1;
 }
 
 // Depth in metres (0 when missing).
@@ -85,7 +92,7 @@ __device__ __forceinline__ float load_depth(const void* base, size_t idx, const 
     if (DT == SF_DEPTH_F32) return raw;
     if (DT == SF_DEPTH_U16) return raw != 0.f ? raw * cd.scale : 0.f;
     const int w = disparity_units(raw, cd);
-    return w > 0 ? 1.f / (cd.scale * (float)w) : 0.f;
+    return w >= 0 ? 1.f / (cd.scale * ((float)w + cd.frac)) : 0.f;
 }
 
 __device__ __forceinline__ bool depth_valid(float z) { return z > 0.f && z < INFINITY; }
@@ -99,7 +106,7 @@ __device__ __forceinline__ float fit_variable_of(float zin, const Codec& cd = Co
     if (DT == SF_DEPTH_DISPARITY_U16) {
         const int w = disparity_units(zin, cd);
         if (base_method(M) == SF_METHOD_DISPARITY) return (float)w;
-        return w > 0 ? 1.f / (cd.scale * (float)w) : 0.f;
+        return w >= 0 ? 1.f / (cd.scale * ((float)w + cd.frac)) : 0.f;
     }
     if (base_method(M) == SF_METHOD_DISPARITY) return rcp_approx(zin);
     return zin;
@@ -118,13 +125,15 @@ __device__ __forceinline__ int quant_recip(float z, float sc) {
     return (int)hr + (int)rintf((hi - hr) + lo);
 }
 
-// round(K / w) for an integer 0 < w < 2^24 and any K > 0 with K / w < 2^30:
-// y = rcp(w) refined by its exact FMA residual e = 1 - w y, and K y split
-// exactly into p + pe (FMA), so K / w = p + pe + p e to about 2^-44 relative.
-__device__ __forceinline__ int quant_div(float K, int w) {
+// round(K / (w + f)) for an integer 0 <= w < 2^24, f in [0, 1), w + f > 0 and
+// any K > 0 with K / (w + f) < 2^30: y = rcp(w + f) refined by its residual
+// e = 1 - (w + f) y (exact FMA for w, f y to float32 of a quantity below
+// 2^-23 relative), and K y split exactly into p + pe (FMA), so
+// K / (w + f) = p + pe + p e to about 2^-44 relative.
+__device__ __forceinline__ int quant_div(float K, int w, float f = 0.f) {
     const float wf = (float)w;
-    const float y = rcp_approx(wf);
-    const float e = fmaf(-wf, y, 1.f);
+    const float y = rcp_approx(wf + f);
+    const float e = fmaf(-wf, y, 1.f) - f * y;
     const float p = K * y;
     const float pe = fmaf(K, y, -p);
     const float hr = rintf(p);
@@ -148,9 +157,9 @@ __device__ __forceinline__ int quantize_raw(float zin, float sc, const Codec& cd
     if (DT == SF_DEPTH_DISPARITY_U16) {
         const int w = disparity_units(zin, cd);
         if (base_method(M) == SF_METHOD_DISPARITY || w < 0) return w;
-        // Z / quantum = (sc / scale) / w, correctly rounded for the frame's one
-        // K = sc / scale (its own rounding scales every depth alike)
-        return quant_div(sc / cd.scale, w);
+        // Z / quantum = (sc / scale) / (w + frac), correctly rounded for the
+        // frame's one K = sc / scale (its own rounding scales every depth alike)
+        return quant_div(sc / cd.scale, w, cd.frac);
     }
     if (!depth_valid(zin)) return -1;
     if (DT == SF_DEPTH_U16 && base_method(M) == SF_METHOD_STANDARD) return (int)zin;
@@ -714,6 +723,7 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
     const size_t pb = plane_index(pofs, x, 0, H);
     const float tx = txt[x];
     constexpr int B = base_method(M);
+    const float wfrac = DT == SF_DEPTH_DISPARITY_U16 ? scale.frac : 0.f;  // disparity input offset
     typename std::conditional<B == SF_METHOD_DISPARITY, DispState,
                               StdStateT<M == SF_METHOD_EXPLICIT_STANDARD>>::type S(P);
     S.init(pb, kGroup, H, y0, r);
@@ -744,13 +754,13 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
         if (ok) {
             if constexpr (M == SF_METHOD_DISPARITY)
                 fo_ = solve_disparity<float, U4, kGuard>(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi,
-                                                         S.Sww, q, tx, ty, a, b);
+                                                         S.Sww, q, tx, ty, a, b, wfrac);
             else if constexpr (M == SF_METHOD_STANDARD)
                 fo_ = solve_standard<float, U4, kGuard>((float)S.n, S.Sz, S.Szj, S.Szi, S.Szz, S.Szzj, S.Szzi, S.Szzjj,
                                                         S.Szzji, S.Szzii, q, tx, ty, a, b);
             else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY)
                 fo_ = solve_explicit_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q,
-                                               tx, ty, a, b, ok);
+                                               tx, ty, a, b, ok, wfrac);
             else
                 fo_ = solve_explicit_standard((float)S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sz, S.Szj, S.Szi,
                                               S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji, S.Szzii, q, tx, ty, a, b,
@@ -947,13 +957,14 @@ __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, Codec
         const double q = (double)quantum<DT, M>(vmax_bits[f], bits, scale);
         const double tx = rays[x], ty = rays[W + y];  // FP64 ray tangents
         const double a = rays[W + H], b = rays[W + H + 1];
+        const double wfrac = DT == SF_DEPTH_DISPARITY_U16 ? (double)scale.frac : 0.0;
         FitOutT<double> o;
         bool ok = true;
         if constexpr (M == SF_METHOD_DISPARITY) {
             DispState S(P);
             S.init(pb, kGroup, H, y, r);
             o = solve_disparity<double, U4>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj, (double)S.Sji,
-                                        (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty, a, b);
+                                        (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty, a, b, wfrac);
         } else if constexpr (M == SF_METHOD_STANDARD) {
             StdState S(P);
             S.init(pb, kGroup, H, y, r);
@@ -964,7 +975,7 @@ __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, Codec
             S.init(pb, kGroup, H, y, r);
             o = solve_explicit_disparity<double>((double)S.n, (double)S.Sj, (double)S.Si, (double)S.Sjj,
                                                  (double)S.Sji, (double)S.Sii, S.Sw, S.Swj, S.Swi, S.Sww, q, tx, ty,
-                                                 a, b, ok);
+                                                 a, b, ok, wfrac);
         } else {
             StdStateT<true> S(P);
             S.init(pb, kGroup, H, y, r);
@@ -1243,15 +1254,16 @@ __global__ void __launch_bounds__(256) quad_level_kernel(const void* __restrict_
         const double qv = (double)quantum<DT, M>(vmax_bits[q.frame], bits, scale);
         const double tx = rays[xc], ty = rays[W + yc], a = rays[W + H], b = rays[W + H + 1];
         const double nf = (double)n;
+        const double wfrac = DT == SF_DEPTH_DISPARITY_U16 ? (double)scale.frac : 0.0;
         FitOutT<double> f;
         if constexpr (M == SF_METHOD_DISPARITY)
             f = solve_disparity<double>(nf, (double)Sj, (double)Si, (double)Sjj, (double)Sji, (double)Sii, c0, cj,
-                                        ci, c2, qv, tx, ty, a, b);
+                                        ci, c2, qv, tx, ty, a, b, wfrac);
         else if constexpr (M == SF_METHOD_STANDARD)
             f = solve_standard<double>(nf, c0, cj, ci, c2, c2j, c2i, c2jj, c2ji, c2ii, qv, tx, ty, a, b);
         else if constexpr (M == SF_METHOD_EXPLICIT_DISPARITY)
             f = solve_explicit_disparity<double>(nf, (double)Sj, (double)Si, (double)Sjj, (double)Sji, (double)Sii,
-                                                 c0, cj, ci, c2, qv, tx, ty, a, b, ok);
+                                                 c0, cj, ci, c2, qv, tx, ty, a, b, ok, wfrac);
         else
             f = solve_explicit_standard<double>(nf, (double)Sj, (double)Si, (double)Sjj, (double)Sji, (double)Sii,
                                                 c0, cj, ci, c2, c2j, c2i, c2jj, c2ji, c2ii, qv, tx, ty, a, b, ok);

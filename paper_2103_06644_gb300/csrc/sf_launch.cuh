@@ -17,8 +17,8 @@ namespace sfh {
 namespace {
 
 sf::Codec codec_of(const sf_ctx* c) {
-    if (c->depth_type == SF_DEPTH_DISPARITY_U16) return sf::Codec{c->disp_q, c->disp_mul, c->disp_add};
-    return sf::Codec{c->depth_scale, 0, 0};
+    if (c->depth_type == SF_DEPTH_DISPARITY_U16) return sf::Codec{c->disp_q, c->disp_mul, c->disp_add, c->disp_frac};
+    return sf::Codec{c->depth_scale, 0, 0, 0.f};
 }
 
 cudaEvent_t take_event(sf_ctx* c) {
@@ -272,7 +272,7 @@ sf_status launch_pass_delta(sf_ctx* c, int nfr, const void* depth, float* normal
     {
         StageTimer t(c, 1, st);
         dim3 grid((c->W + 31) / 32, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
-        const size_t smem = 2 * sizeof(int) * sf::kHThreads * (size_t)((32 + 2 * c->r) | 1);
+        const size_t smem = 3 * sizeof(int) * sf::kHThreads * (size_t)((32 + 2 * c->r) | 1);
         sf::hpass_delta_kernel<DT><<<grid, sf::kHThreads, smem, st>>>(depth, c->dtab, c->W, c->H, c->r, codec_of(c),
                                                                      c->vmax, bits, c->plane_elems, c->planes);
     }
@@ -366,7 +366,7 @@ void set_kernel_smem_t() {
     const int smem = (int)(sizeof(int) * sf::kHThreads * (size_t)(IW | 1));
     set_hpass_smem_one<DT, SF_METHOD_DISPARITY>(smem);
     set_hpass_smem_one<DT, SF_METHOD_STANDARD>(smem);
-    const int dsmem = (int)(2 * sizeof(int) * sf::kHThreads * (size_t)((32 + 2 * sf::kMaxR) | 1));
+    const int dsmem = (int)(3 * sizeof(int) * sf::kHThreads * (size_t)((32 + 2 * sf::kMaxR) | 1));
     cudaFuncSetAttribute(sf::hpass_delta_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
     if constexpr (DT != SF_DEPTH_DISPARITY_U16) {
         const int T = sf::kGTile + 2 * sf::kMaxR;

@@ -147,6 +147,7 @@ struct WinGeo {
 struct DispCentred {
     int n, Sj, Si, Sjj, Sji, Sii, m;
     df T0, Twj, Twi, Tww;
+    float frac;  // fractional offset of disparity input, added to every value
 };
 
 __device__ __forceinline__ DispCentred centre_disparity(const int64_t* v) {
@@ -160,6 +161,7 @@ __device__ __forceinline__ DispCentred centre_disparity(const int64_t* v) {
     c.Twj = df_i64(Swj - (int64_t)c.m * c.Sj);
     c.Twi = df_i64(Swi - (int64_t)c.m * c.Si);
     c.Tww = df_i64(Sww - (int64_t)c.m * (Sw + T0));
+    c.frac = 0.f;
     return c;
 }
 
@@ -175,7 +177,8 @@ __device__ __forceinline__ Sym3df build_disparity_df(const DispCentred& w, df tx
     const df Cjw = (w.Twj * nf - w.T0 * (float)w.Sj) * inv_n;
     const df Ciw = (w.Twi * nf - w.T0 * (float)w.Si) * inv_n;
     const df Cww = (w.Tww * nf - w.T0 * w.T0) * inv_n;
-    const df Sw = w.T0 + df_i64((int64_t)w.n * w.m);  // n wbar
+    // n wbar (the fractional offset moves the mean only: the centred sums are shift-invariant)
+    const df Sw = w.T0 + df_i64((int64_t)w.n * w.m) + two_prod(nf, w.frac);
     const df inv_nw = dfv(1.f) / Sw;
     const df dj = Cjw * inv_nw, di = Ciw * inv_nw, e = Cww * inv_nw;
     const df wbar = Sw * inv_n;
@@ -491,8 +494,8 @@ __device__ __forceinline__ void residual_of(float zin, float sc, const Codec& cd
         if (B == SF_METHOD_DISPARITY) { V = w; return; }
         const float K = sc / cd.scale;
         const float wf = (float)w;
-        const float y = rcp_approx(wf);
-        const float e = fmaf(-wf, y, 1.f);
+        const float y = rcp_approx(wf + cd.frac);
+        const float e = fmaf(-wf, y, 1.f) - cd.frac * y;
         const float p = K * y;
         const float pe = fmaf(K, y, -p);
         const float hr = rintf(p);
@@ -690,6 +693,7 @@ __global__ void __launch_bounds__(128) refine_kernel(const void* __restrict__ de
             tx = df_d(rays[x]); ty = df_d(rays[W + y]);
             if constexpr (B == SF_METHOD_DISPARITY) {
                 wc = centre_disparity(mo);
+                if (DT == SF_DEPTH_DISPARITY_U16) wc.frac = cd.frac;
                 R = build_disparity_df(wc, tx, ty, a, b, q, geo);
             } else {
                 wc = centre_standard(mo);
@@ -749,8 +753,12 @@ __global__ void __launch_bounds__(128) resum_kernel(const void* __restrict__ dep
         }
         typename std::conditional<B == SF_METHOD_DISPARITY, DispCentred, StdCentred>::type wc{};
         if (active) {
-            if constexpr (B == SF_METHOD_DISPARITY) wc = centre_disparity(mo);
-            else wc = centre_standard(mo);
+            if constexpr (B == SF_METHOD_DISPARITY) {
+                wc = centre_disparity(mo);
+                if (DT == SF_DEPTH_DISPARITY_U16) wc.frac = cd.frac;
+            } else {
+                wc = centre_standard(mo);
+            }
         }
         const unsigned vb = active ? vmax_bits[f] : 0u;
         float mine[kResidSums];

@@ -294,7 +294,7 @@ using DispWindow = DispWindowT<float>;
 template <typename T>
 __device__ __forceinline__ DispWindowT<T> build_disparity(T nf, T fSj, T fSi, T fSjj, T fSji, T fSii, int64_t Sw,
                                                           int64_t Swj, int64_t Swi, int64_t Sww, T tx, T ty, T a,
-                                                          T b) {
+                                                          T b, T wfrac = T(0)) {
     // the mask moments are exact integers held in T (all < 2^24)
     const T inv_n = Fn<T>::rcp(nf);
     const int n = (int)nf, Sj = (int)fSj, Si = (int)fSi;
@@ -313,7 +313,9 @@ __device__ __forceinline__ DispWindowT<T> build_disparity(T nf, T fSj, T fSi, T 
     const T Cjw = Fn<T>::from_i64(Twj) - fSj * t0;
     const T Ciw = Fn<T>::from_i64(Twi) - fSi * t0;
     const T Cww = Fn<T>::from_i64(Tww) - fT0 * t0;
-    const T wbar = (T)m + t0;  // mean disparity (units of qw)
+    // mean disparity (units of qw); wfrac shifts every value alike (disparity
+    // input with a fractional offset) and so leaves the covariances unchanged
+    const T wbar = (T)m + t0 + wfrac;
     const T inv_nw = Fn<T>::rcp(nf * wbar);
     const T dj = Cjw * inv_nw;     // jhat - jbar
     const T di = Ciw * inv_nw;     // ihat - ibar
@@ -343,8 +345,9 @@ __device__ __forceinline__ DispWindowT<T> build_disparity(T nf, T fSj, T fSi, T 
 template <typename T = float, bool U4 = false, bool kEst = false>
 __device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj, T fSji, T fSii, int64_t Sw,
                                                       int64_t Swj, int64_t Swi, int64_t Sww, T qw, T tx, T ty, T a,
-                                                      T b) {
-    const DispWindowT<T> w = build_disparity<T>(nf, fSj, fSi, fSjj, fSji, fSii, Sw, Swj, Swi, Sww, tx, ty, a, b);
+                                                      T b, T wfrac = T(0)) {
+    const DispWindowT<T> w = build_disparity<T>(nf, fSj, fSi, fSjj, fSji, fSii, Sw, Swj, Swi, Sww, tx, ty, a, b,
+                                                wfrac);
     if constexpr (U4) {
         // g = sum w m = (sum w) mhat, s = sum w^2 = n wbar what (metric)
         const T sw = qw * nf * w.wbar;
@@ -453,7 +456,8 @@ __device__ __forceinline__ bool pixels_span_plane(T nf, T fSj, T fSi, T fSjj, T 
 template <typename T = float>
 __device__ __forceinline__ FitOutT<T> solve_explicit_disparity(T nf, T fSj, T fSi, T fSjj, T fSji, T fSii,
                                                                int64_t Sw, int64_t Swj, int64_t Swi, int64_t Sww,
-                                                               T qw, T tx, T ty, T a, T b, bool& ok) {
+                                                               T qw, T tx, T ty, T a, T b, bool& ok,
+                                                               T wfrac = T(0)) {
     FitOutT<T> o;
     const int n = (int)nf, Sj = (int)fSj, Si = (int)fSi;
     ok = pixels_span_plane<T>(nf, fSj, fSi, fSjj, fSji, fSii);
@@ -471,7 +475,7 @@ __device__ __forceinline__ FitOutT<T> solve_explicit_disparity(T nf, T fSj, T fS
     const T idet = Fn<T>::rcp(Cjj * Cii - Cji * Cji);
     const T bj = (Cii * Cjw - Cji * Ciw) * idet;   // d omega / d j
     const T bi = (Cjj * Ciw - Cji * Cjw) * idet;   // d omega / d i
-    const T bc = ((T)m + t0) - bj * jb - bi * ib;  // omega at the window centre pixel
+    const T bc = ((T)m + t0 + wfrac) - bj * jb - bi * ib;  // omega at the window centre pixel
     const T ax = qw * bj * Fn<T>::rcp(a), ay = qw * bi * Fn<T>::rcp(b);
     const T ac = qw * bc - ax * tx - ay * ty;
     const T s = Fn<T>::rsqrt(ax * ax + ay * ay + ac * ac);

@@ -239,7 +239,7 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
         return fail(SF_ERR_UNSUPPORTED, "a per-pixel delta table applies to the disparity-form fit in precision mode 0");
     if (c->depth_type == SF_DEPTH_DISPARITY_U16 && sf::base_method(c->method) == SF_METHOD_DISPARITY) {
         // the disparity integers go into the int32 row sums unscaled: k w < 2^31
-        const double wmax = 128.0 * 65535.0 + std::fabs((double)c->disp_add);
+        const double wmax = 128.0 * 65535.0 + std::fabs((double)c->disp_add) + 1.0;
         if (wmax * c->k >= 2147483648.0)
             return fail(SF_ERR_INVALID_ARG, "disparity model offset too large for a %d x %d window", c->k, c->k);
     }
@@ -436,29 +436,37 @@ sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_
 sf_status sf_set_delta_table(sf_ctx* c, const float* ddx, const float* ddy) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (!ddx != !ddy) return fail(SF_ERR_INVALID_ARG, "give both tables or neither");
-    // fits already queued may still read the old table
-    SF_CUDA(cudaDeviceSynchronize());
+    // fits already queued on the context's device may still read the old table
+    {
+        int prev = 0;
+        SF_CUDA(cudaGetDevice(&prev));
+        if (prev != c->device) SF_CUDA(cudaSetDevice(c->device));
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (prev != c->device) cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(e, "sf_set_delta_table: synchronise");
+    }
     if (!ddx) {
         if (c->dtab) cudaFree(c->dtab);
         c->dtab = nullptr;
         return SF_OK;
     }
     const size_t n = (size_t)c->W * c->H;
-    std::vector<int> packed(n);
+    // the D plane then the E plane, in 1/kDeltaScale pixel
+    std::vector<int> planes(2 * n);
     for (size_t i = 0; i < n; ++i) {
         const float a = ddx[i], b = ddy[i];
-        if (!std::isfinite(a) || !std::isfinite(b) || std::fabs(a) * sf::kDeltaScale > sf::kDeltaMax ||
-            std::fabs(b) * sf::kDeltaScale > sf::kDeltaMax)
+        if (!std::isfinite(a) || !std::isfinite(b) || std::fabs((double)a) * sf::kDeltaScale > sf::kDeltaMax ||
+            std::fabs((double)b) * sf::kDeltaScale > sf::kDeltaMax)
             return fail(SF_ERR_INVALID_ARG, "delta table entry %zu (%g, %g) must be finite and below 16 pixels", i,
                         (double)a, (double)b);
-        const int D = (int)std::lrint((double)a * sf::kDeltaScale), E = (int)std::lrint((double)b * sf::kDeltaScale);
-        packed[i] = (int)((uint32_t)(uint16_t)(int16_t)D | ((uint32_t)(uint16_t)(int16_t)E << 16));
+        planes[i] = (int)std::lrint((double)a * sf::kDeltaScale);
+        planes[n + i] = (int)std::lrint((double)b * sf::kDeltaScale);
     }
     if (!c->dtab) {
-        cudaError_t e = cudaMalloc(&c->dtab, n * sizeof(int));
-        if (e != cudaSuccess) { c->dtab = nullptr; return fail(SF_ERR_ALLOC, "delta table of %zu bytes", n * 4); }
+        cudaError_t e = cudaMalloc(&c->dtab, 2 * n * sizeof(int));
+        if (e != cudaSuccess) { c->dtab = nullptr; return fail(SF_ERR_ALLOC, "delta table of %zu bytes", n * 8); }
     }
-    SF_CUDA(cudaMemcpy(c->dtab, packed.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    SF_CUDA(cudaMemcpy(c->dtab, planes.data(), 2 * n * sizeof(int), cudaMemcpyHostToDevice));
     SF_CUDA(cudaGetLastError());
     return SF_OK;
 }
@@ -497,7 +505,11 @@ sf_status sf_set_disparity_model(sf_ctx* c, double alpha, double beta) {
     if (!(std::fabs(k) <= 8388608.0)) return fail(SF_ERR_INVALID_ARG, "|128 beta / alpha| must be <= 2^23");
     c->disp_q = (float)(std::fabs(alpha) / 128.0);
     c->disp_mul = alpha > 0.0 ? 128 : -128;
-    c->disp_add = (int)std::lround(k);
+    // 128 beta / |alpha| = integer part + fraction in [0, 1)
+    const double fl = std::floor(k);
+    c->disp_add = (int)fl;
+    c->disp_frac = (float)(k - fl);
+    if (c->disp_frac >= 1.f) { c->disp_add += 1; c->disp_frac = 0.f; }
     return SF_OK;
 }
 

@@ -68,8 +68,8 @@ def rays(intr: Intrinsics, W: int, H: int) -> Tuple[np.ndarray, np.ndarray]:
 
 
 def delta_table(seed: int, intr: Intrinsics, W: int, H: int, amp: float = 1.5) -> Tuple[np.ndarray, np.ndarray]:
-    """Per-pixel ray adjustments (ddx, ddy) [H, W] in pixels: a radial field (a stand-in for lens
-    distortion, up to `amp` px at the corners) plus a seeded ripple, in multiples of 1/256 px."""
+    """Per-pixel ray adjustments (ddx, ddy) [H, W] in pixels, float32: a radial field (a stand-in for
+    lens distortion, up to `amp` px at the corners) plus a seeded ripple, inside +-16 px."""
     rng = np.random.Generator(np.random.PCG64(seed))
     x = (np.arange(W, dtype=np.float64) - intr.cx)[None, :]
     y = (np.arange(H, dtype=np.float64) - intr.cy)[:, None]
@@ -80,8 +80,8 @@ def delta_table(seed: int, intr: Intrinsics, W: int, H: int, amp: float = 1.5) -
     ph = rng.uniform(0, 2 * np.pi, 2)
     ddx = ddx + 0.2 * amp * np.sin(0.05 * y + 0.03 * x + ph[0])
     ddy = ddy + 0.2 * amp * np.cos(0.04 * x - 0.02 * y + ph[1])
-    q = lambda a: np.clip(np.round(a * 256.0), -(16 * 256 - 1), 16 * 256 - 1) / 256.0
-    return q(ddx), q(ddy)
+    c = lambda a: np.clip(a, -15.99, 15.99).astype(np.float32)
+    return c(ddx), c(ddy)
 
 
 def plane_depth_delta(plane: "Plane", intr: Intrinsics, ddx: np.ndarray, ddy: np.ndarray) -> np.ndarray:

@@ -1,8 +1,9 @@
 """GPU fits with a per-pixel table of ray adjustments (sf_set_delta_table) against the oracle's
 per-pixel rays (Eq. 1 / Eq. 10 with one adjustment per pixel).
 
-The tables hold multiples of 1/256 pixel, the library's resolution, so both sides use the same rays;
-counts and masks bit-exact, floats within the tolerances of tests/parity.py.
+The tables are continuous float32 fields; the library stores them to 1/2^18 pixel and the oracle uses
+them as given, so the library's rounding of the rays is part of what is judged: counts and masks
+bit-exact, floats within the tolerances of tests/parity.py.
 """
 import numpy as np
 import pytest

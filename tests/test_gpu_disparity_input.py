@@ -1,11 +1,11 @@
 """Raw disparity input (SF_DEPTH_DISPARITY_U16, sf_set_disparity_model) against
 the oracle fed the depth that the input's sensor model defines.
 
-The model 1/Z = alpha D + beta is represented as
-1/Z = (|alpha|/128)(sign(alpha) 128 D + round(128 beta/|alpha|)); the oracle
-applies the same definition (oracle.depth_from_disparity) in FP64.  For the
-disparity form the GPU sums the integers 128 D + round(...) directly: no
-reciprocal, no range pass.
+The oracle takes the model 1/Z = alpha D + beta exactly (oracle.depth_from_disparity,
+FP64).  The library sums the integers sign(alpha) 128 D + B with
+B + f = 128 beta / |alpha| and adds the fraction f to the mean disparity, so its
+own representation of the model is judged: no reciprocal, no range pass for the
+disparity form.
 """
 import numpy as np
 import pytest
@@ -25,6 +25,8 @@ from paper_2103_06644_gb300 import SurfaceFitter, SurfFitError  # noqa: E402
 
 INTR = scenes.Intrinsics(580.0, 580.0, 319.5, 239.5)
 STEREO = (1.0 / (8 * 580.0 * 0.075), 0.0)
+# a stereo pair with a calibrated disparity offset: beta not a multiple of |alpha| / 128
+STEREO_OFFSET = (1.0 / (8 * 580.0 * 0.075), 0.0123)
 KINECT = (scenes.KINECT_RAW_ALPHA, scenes.KINECT_RAW_BETA)
 
 
@@ -52,7 +54,7 @@ def _gpu(D, model, k, method):
 
 @pytest.mark.parametrize("method", ["disparity", "standard", "explicit_disparity"])
 @pytest.mark.parametrize("k", [5, 9])
-@pytest.mark.parametrize("model", [STEREO, KINECT], ids=["stereo", "kinect"])
+@pytest.mark.parametrize("model", [STEREO, STEREO_OFFSET, KINECT], ids=["stereo", "stereo_offset", "kinect"])
 def test_disparity_input_matches_oracle(model, k, method):
     D = _frame(model, 4000 + k)
     Z = oracle.depth_from_disparity(D, *model)

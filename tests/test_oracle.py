@@ -508,24 +508,24 @@ def test_unit4_and_curvature_match_lapack_on_noisy_windows(method):
 
 
 def test_depth_from_disparity_model():
-    """The raw-disparity model 1/Z = alpha D + beta, with beta kept to 1/128 of a disparity unit:
-    exact for beta = 0 and for beta a multiple of alpha/128 (either sign of alpha), within alpha/256
-    of the real-valued model otherwise; D == 0 or 1/Z <= 0 is missing."""
+    """The raw-disparity model 1/Z = alpha D + beta, either sign of alpha, any beta: D == 0 or
+    1/Z <= 0 is missing."""
     D = np.array([[0, 1, 7, 300], [1000, 65535, 2, 5]], dtype=np.uint16)
     a = 1.0 / (8.0 * 575.0 * 0.075)
     Z = oracle.depth_from_disparity(D, a, 0.0)
     ok = D > 0
     assert np.all(Z[~ok] == 0.0)
     assert np.allclose(Z[ok], 1.0 / (a * D[ok].astype(np.float64)), rtol=1e-15, atol=0)
-    b = 37.0 * a / 128.0
+    b = 0.3717 * a  # not a multiple of any power-of-two fraction of alpha
     Zb = oracle.depth_from_disparity(D, a, b)
-    assert np.allclose(1.0 / Zb[ok], a * D[ok] + b, rtol=1e-13, atol=0)
-    # a structured-light style model with negative alpha: nearer for larger raw values is reversed
+    assert np.allclose(1.0 / Zb[ok], a * D[ok] + b, rtol=1e-14, atol=0)
+    # a structured-light style model with negative alpha: larger raw values are farther
     ka, kb = scenes.KINECT_RAW_ALPHA, scenes.KINECT_RAW_BETA
     Dk = np.array([[0, 400, 800, 1084, 1085, 2047]], dtype=np.uint16)
     Zk = oracle.depth_from_disparity(Dk, ka, kb)
     w = ka * Dk.astype(np.float64) + kb
-    valid = (Dk > 0) & (w > abs(ka) / 256.0)
+    valid = (Dk > 0) & (w > 0)
     assert np.all(Zk[Dk == 0] == 0.0)
-    assert np.all(np.abs(1.0 / Zk[valid] - w[valid]) <= abs(ka) / 256.0 + 1e-12)
-    assert np.all(Zk[(Dk > 0) & (w < -abs(ka))] == 0.0)  # behind the camera: missing
+    assert np.allclose(1.0 / Zk[valid], w[valid], rtol=1e-14, atol=0)
+    assert np.all(np.diff(Zk[valid]) > 0)  # farther with the raw code
+    assert np.all(Zk[(Dk > 0) & (w <= 0)] == 0.0)  # behind the camera: missing
