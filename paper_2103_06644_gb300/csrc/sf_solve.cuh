@@ -208,6 +208,87 @@ __device__ __forceinline__ void orient(T& nx, T& ny, T& nz, T& d) {
     nx = flip ? -nx : nx; ny = flip ? -ny : ny; nz = flip ? -nz : nz; d = flip ? -d : d;
 }
 
+// Smallest eigenpair as smallest_eigpair, robust to a cluster of the two
+// smallest eigenvalues: the trigonometric estimate cannot separate a pair of
+// eigenvalues much closer than sqrt(eps) of the trace (its cos argument q is
+// within rounding of +-1 there), so the eigenvector of the isolated eigenvalue
+// (lambda2 when q >= 0, lambda0 otherwise) is found first (cofactor column and
+// one inverse-iteration step), and the other two from the closed-form 2x2
+// problem of R on its orthogonal complement, whose eigenvalue difference
+// 2 sqrt(h^2 + b^2) involves no cancellation.  l0 and gap as smallest_eigpair.
+template <typename T>
+__device__ __forceinline__ void smallest_eigpair_iso(T r11, T r12, T r13, T r22, T r23, T r33, T& v0, T& v1, T& v2,
+                                                     T& l0, T& gap) {
+    const T tr = r11 + r22 + r33;
+    const T s = tr > T(0) ? T(1) / tr : T(1);
+    r11 *= s; r12 *= s; r13 *= s; r22 *= s; r23 *= s; r33 *= s;
+    const T third = T(1) / T(3);
+    const T b11 = r11 - third, b22 = r22 - third, b33 = r33 - third;
+    const T p2 = (b11 * b11 + b22 * b22 + b33 * b33 + T(2) * (r12 * r12 + r13 * r13 + r23 * r23)) / T(6);
+    const T p = Fn<T>::sqrt(p2 > Fn<T>::p2min() ? p2 : Fn<T>::p2min());
+    const T detB = b11 * (b22 * b33 - r23 * r23) - r12 * (r12 * b33 - r23 * r13) + r13 * (r12 * r23 - b22 * r13);
+    T q = T(0.5) * detB / (p * p * p);
+    q = q > T(1) ? T(1) : (q < T(-1) ? T(-1) : q);
+    const T phi = Fn<T>::acos(q) * third;
+    T sn, cs;
+    Fn<T>::sincos(phi, &sn, &cs);
+    const bool top = q >= T(0);  // lambda2 is the isolated eigenvalue
+    const T liso = top ? third + T(2) * p * cs : third - p * (cs + T(1.7320508075688772) * sn);
+    T e0, e1, e2;
+    null_vector<T>(r11, r12, r13, r22, r23, r33, liso, e0, e1, e2);
+    T le = e0 * (r11 * e0 + r12 * e1 + r13 * e2) + e1 * (r12 * e0 + r22 * e1 + r23 * e2) +
+           e2 * (r13 * e0 + r23 * e1 + r33 * e2);
+    {
+        // one inverse-iteration step, shift = the Rayleigh quotient
+        const T a11 = r11 - le, a22 = r22 - le, a33 = r33 - le;
+        const T c11 = a22 * a33 - r23 * r23, c22 = a11 * a33 - r13 * r13, c33 = a11 * a22 - r12 * r12;
+        const T c12 = r13 * r23 - r12 * a33, c13 = r12 * r23 - r13 * a22, c23 = r12 * r13 - a11 * r23;
+        const T w0 = c11 * e0 + c12 * e1 + c13 * e2, w1 = c12 * e0 + c22 * e1 + c23 * e2;
+        const T w2 = c13 * e0 + c23 * e1 + c33 * e2;
+        const T nw = w0 * w0 + w1 * w1 + w2 * w2;
+        if (nw > Fn<T>::tiny()) {
+            const T iw = Fn<T>::rsqrt(nw);
+            e0 = w0 * iw; e1 = w1 * iw; e2 = w2 * iw;
+            le = e0 * (r11 * e0 + r12 * e1 + r13 * e2) + e1 * (r12 * e0 + r22 * e1 + r23 * e2) +
+                 e2 * (r13 * e0 + r23 * e1 + r33 * e2);
+        }
+    }
+    // orthonormal basis (pa, pb) of e's complement, from the axis least aligned with e
+    const T x0 = e0 < T(0) ? -e0 : e0, x1 = e1 < T(0) ? -e1 : e1, x2 = e2 < T(0) ? -e2 : e2;
+    const int ax = (x0 <= x1 && x0 <= x2) ? 0 : (x1 <= x2 ? 1 : 2);
+    T pa0 = ax == 0 ? T(0) : (ax == 1 ? -e2 : e1);
+    T pa1 = ax == 0 ? e2 : (ax == 1 ? T(0) : -e0);
+    T pa2 = ax == 0 ? -e1 : (ax == 1 ? e0 : T(0));
+    const T ia = Fn<T>::rsqrt(pa0 * pa0 + pa1 * pa1 + pa2 * pa2);
+    pa0 *= ia; pa1 *= ia; pa2 *= ia;
+    const T pb0 = e1 * pa2 - e2 * pa1, pb1 = e2 * pa0 - e0 * pa2, pb2 = e0 * pa1 - e1 * pa0;
+    // R on the complement: [[c11, c12], [c12, c22]]
+    const T ra0 = r11 * pa0 + r12 * pa1 + r13 * pa2, ra1 = r12 * pa0 + r22 * pa1 + r23 * pa2;
+    const T ra2 = r13 * pa0 + r23 * pa1 + r33 * pa2;
+    const T c11 = pa0 * ra0 + pa1 * ra1 + pa2 * ra2, c12 = pb0 * ra0 + pb1 * ra1 + pb2 * ra2;
+    const T c22 = pb0 * (r11 * pb0 + r12 * pb1 + r13 * pb2) + pb1 * (r12 * pb0 + r22 * pb1 + r23 * pb2) +
+                  pb2 * (r13 * pb0 + r23 * pb1 + r33 * pb2);
+    const T h = T(0.5) * (c11 - c22), m = T(0.5) * (c11 + c22);
+    const T rt = Fn<T>::sqrt(h * h + c12 * c12);
+    // eigenvector of the smaller eigenvalue of the 2x2, from its better-conditioned row
+    T sx = h >= T(0) ? c12 : rt - h, sy = h >= T(0) ? -(h + rt) : -c12;
+    const T ns = sx * sx + sy * sy;
+    if (!(ns > Fn<T>::tiny())) { sx = T(1); sy = T(0); }
+    const T is = Fn<T>::rsqrt(sx * sx + sy * sy);
+    sx *= is; sy *= is;
+    const T lsm = m - rt, lbg = m + rt;
+    if (top) {
+        v0 = sx * pa0 + sy * pb0; v1 = sx * pa1 + sy * pb1; v2 = sx * pa2 + sy * pb2;
+        l0 = lsm;
+        gap = le > T(0) ? (lbg - lsm) / le : T(0);
+    } else {
+        v0 = e0; v1 = e1; v2 = e2;
+        l0 = le;
+        gap = lbg > T(0) ? (lsm - le) / lbg : T(0);
+    }
+    l0 = l0 > T(0) ? l0 : T(0);
+}
+
 // The literal constraint of Eq. 4, |(a, b, c, d)| = 1: the smallest eigenpair
 // of the 4x4 scatter M = [[A, g], [g^T, s]] (metric units).  With
 // alpha = (u, t), the eigen-equations give t = g.u / (lambda - s) and
@@ -221,7 +302,9 @@ __device__ __forceinline__ void orient(T& nx, T& ny, T& nz, T& d) {
 // would lose a factor ~d^2 for distant planes).  Rayleigh quotients stay
 // >= lambda_min(M) and converge quadratically: 4-5 steps to 1e-6 typically,
 // at most kU4Steps.  Outputs: n = u, d = t (|u| = 1), curvature
-// lambda / trace(M).  Working on R rather than on M keeps the raw second
+// lambda / trace(M).  R_lambda can be line-like (two small eigenvalues close
+// together), so its 3x3 solves take the isolated eigenvalue first
+// (smallest_eigpair_iso), and the iteration divides exactly (IEEE).  Working on R rather than on M keeps the raw second
 // moments of M, whose smallest eigenvalue is ~1e-6 of its largest, out of
 // the floating-point arithmetic.
 constexpr int kU4Steps = 10;
@@ -233,21 +316,21 @@ __device__ __forceinline__ FitOutT<T> solve_unit4(T R11, T R12, T R13, T R22, T 
     T lam = T(0), u0 = T(0), u1 = T(0), u2 = T(1), l0n = T(0), gap = T(0), l0R = T(0), gu = T(0);
 #pragma unroll 1
     for (int it = 0;; ++it) {
-        const T c = lam * Fn<T>::rcp(s * (s - lam));
+        const T c = lam / (s * (s - lam));
         const T a11 = R11 - c * g0 * g0, a12 = R12 - c * g0 * g1, a13 = R13 - c * g0 * g2;
         const T a22 = R22 - c * g1 * g1, a23 = R23 - c * g1 * g2, a33 = R33 - c * g2 * g2;
         // R_lambda may be indefinite: its eigenvalues are >= lambda0(R) - c|g|^2, so a shift by
         // the excess keeps it semi-definite with the same eigenvectors (0 near the root)
         const T ex = c * g2sum - l0R;
         const T sh = ex > T(0) ? ex : T(0);
-        smallest_eigpair<T>(a11 + sh, a12, a13, a22 + sh, a23, a33 + sh, u0, u1, u2, l0n, gap);
+        smallest_eigpair_iso<T>(a11 + sh, a12, a13, a22 + sh, a23, a33 + sh, u0, u1, u2, l0n, gap);
         const T uRu = u0 * (R11 * u0 + R12 * u1 + R13 * u2) + u1 * (R12 * u0 + R22 * u1 + R23 * u2) +
                       u2 * (R13 * u0 + R23 * u1 + R33 * u2);
         if (it == 0) l0R = uRu > T(0) ? uRu : T(0);
         gu = g0 * u0 + g1 * u1 + g2 * u2;
         const T sl = s - lam;
-        const T isl2 = Fn<T>::rcp(sl * sl);
-        T rho = (uRu + gu * gu * lam * lam * Fn<T>::rcp(s) * isl2) * Fn<T>::rcp(T(1) + gu * gu * isl2);
+        const T isl2 = T(1) / (sl * sl);
+        T rho = (uRu + gu * gu * lam * lam / s * isl2) / (T(1) + gu * gu * isl2);
         const T top = s * T(0.999999);
         rho = rho < T(0) ? T(0) : (rho > top ? top : rho);
         const T step = rho > lam ? rho - lam : lam - rho;
@@ -256,7 +339,7 @@ __device__ __forceinline__ FitOutT<T> solve_unit4(T R11, T R12, T R13, T R22, T 
         if (done) break;
     }
     o.nx = u0; o.ny = u1; o.nz = u2;
-    o.d = gu * Fn<T>::rcp(lam - s);
+    o.d = gu / (lam - s);
     orient<T>(o.nx, o.ny, o.nz, o.d);
     const T trM = R11 + R22 + R33 + g2sum * Fn<T>::rcp(s) + s;
     o.curv = lam * Fn<T>::rcp(trM);

@@ -3,12 +3,11 @@
 
 Counts and masks bit-exact; the normal within 1e-3 rad and the offset within
 1e-4 |mu| where the 4x4 problem is well posed.  The float32 solve reaches
-lambda by an iteration of 3x3 solves on R_lambda, whose own eigen-gap can be
-far below the 4x4 eigen-gap gamma = (lambda1 - lambda0) / lambda2: its normal
-error was measured at ~2e-5 / gamma (1.6e-3 rad at gamma = 1.15e-2 on the
-wide-range k=31 frame, up to 0.02 rad below 1e-2), so the float32 mode is
-judged at gamma >= 2e-2, the FP64 modes at 1e-3 and (mode 1, whose re-solve
-covers every window below tau = 1e-2) at 1e-5.
+lambda by an iteration of 3x3 solves on R_lambda, whose two smallest
+eigenvalues can cluster (a line-like R_lambda); its 3x3 solves take the
+isolated eigenvalue first.  The float32 mode is judged at 4x4 eigen-gaps
+gamma = (lambda1 - lambda0) / lambda2 >= 1e-2, the FP64 modes at 1e-3 and
+mode 1 (whose FP64 re-solve covers every window below tau) at 1e-5.
 """
 import numpy as np
 import pytest
@@ -44,7 +43,7 @@ def test_unit4_640x480_k7(method):
     intr = scenes.Intrinsics(525.0, 525.0, 319.5, 239.5)
     depth = scenes.kinect_frame(scenes.BASE_SEED, intr, 640, 480)
     ref = oracle.fit(depth, intr.as_tuple(), 7, method, unit4=True, want_lambda=True, want_moments=True)
-    s = compare(_gpu(depth, intr.as_tuple(), 7, method), ref, gap_min=2e-2, check_degenerate=False,
+    s = compare(_gpu(depth, intr.as_tuple(), 7, method), ref, gap_min=1e-2, check_degenerate=False,
                 label="unit4 " + method)
     assert s["good"] > 0.85 * s["valid"]
     print(method, s)
@@ -59,7 +58,7 @@ def test_unit4_wide_range_k31_fp64(method):
     intr = scenes.Intrinsics.scaled(W, H, f640=525.0)
     depth = scenes.wide_range_frame(scenes.BASE_SEED + 2, intr, W, H)
     ref = oracle.fit(depth, intr.as_tuple(), 31, method, unit4=True, want_lambda=True, want_moments=True)
-    for precision, gmin in ((0, 2e-2), (2, 1e-3)):
+    for precision, gmin in ((0, 1e-2), (2, 1e-3)):
         compare(_gpu(depth, intr.as_tuple(), 31, method, precision), ref, gap_min=gmin, check_degenerate=False,
                 label="unit4 k31 %s mode %d" % (method, precision))
 
