@@ -296,9 +296,13 @@ sf_status sf_batch_destroy(sf_batch* batch);
  *              the call and stored on the device rounded to 1/2^18 pixel
  *              (both NULL: remove the table)
  * With a table, sf_fit / sf_fit_ex / sf_fit_host of SF_METHOD_DISPARITY (either
- * constraint, precision mode 0) use the per-pixel rays; every other method,
- * precision modes 1 and 2, sf_fit_backward and sf_quadtree return
- * SF_ERR_UNSUPPORTED while a table is set.  The table takes 8 B per pixel and
+ * constraint, every precision mode) use the per-pixel rays; every other
+ * method, sf_fit_backward and sf_quadtree return SF_ERR_UNSUPPORTED while a
+ * table is set.  In precision modes 1 and 2 the windows that the float32
+ * solve queues (mode 1: gap below tau or a rounding estimate above 3e-5 rad;
+ * mode 2: every window) are solved again in FP64 from the unrounded depth and
+ * the stored rays, one warp per window: exact to FP64 rounding, at the cost
+ * of one k x k re-read per queued window.  The table takes 8 B per pixel and
  * its scratch 84 B per pixel instead of 20.  Synchronous: waits for the
  * context's device to finish its queued work before replacing a table; do not
  * call it while a stream capture is in progress on that device.

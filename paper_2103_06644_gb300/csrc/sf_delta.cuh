@@ -258,6 +258,9 @@ __device__ __forceinline__ DispWindowT<float> build_disparity_delta(const DispDe
 
 // Column pass + solve with the table (disparity form; U4 the literal
 // |(a,b,c,d)| = 1 constraint), one thread per column over a band of rows.
+// With flags (precision modes 1 and 2) windows whose float32 eigen-gap is
+// below tau, or whose fixed-point rounding could move the normal by more than
+// kRefineRounding, are queued for direct_delta_kernel.
 template <int DT, bool U4>
 __global__ void __launch_bounds__(kVThreads) vpass_delta_kernel(const void* __restrict__ depth, int W, int H, int r,
                                                                 Codec scale, const unsigned* __restrict__ vmax_bits,
@@ -266,7 +269,9 @@ __global__ void __launch_bounds__(kVThreads) vpass_delta_kernel(const void* __re
                                                                 int band, float* __restrict__ normals,
                                                                 float* __restrict__ offsets,
                                                                 float* __restrict__ curvature,
-                                                                int32_t* __restrict__ counts) {
+                                                                int32_t* __restrict__ counts, float tau,
+                                                                unsigned long long* __restrict__ flags,
+                                                                unsigned* __restrict__ flag_count) {
     const int f = blockIdx.z;
     const int x = blockIdx.x * kVThreads + threadIdx.x;
     if (x >= W) return;
@@ -275,6 +280,7 @@ __global__ void __launch_bounds__(kVThreads) vpass_delta_kernel(const void* __re
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * fe;
     const float q = quantum<DT, SF_METHOD_DISPARITY>(vmax_bits[f], bits, scale);
     const float wfrac = DT == SF_DEPTH_DISPARITY_U16 ? scale.frac : 0.f;
+    const int lane = threadIdx.x & 31;
     const Planes P(planes_base, (size_t)gridDim.z * plane_elems, kDeltaPlanes32);
     const size_t pb = plane_index((size_t)f * plane_elems, x, 0, H);
     const int y0 = blockIdx.y * band, y1 = min(y0 + band, H);
@@ -297,23 +303,207 @@ __global__ void __launch_bounds__(kVThreads) vpass_delta_kernel(const void* __re
         if (ok) {
             const DispWindowT<float> w = build_disparity_delta(S, tx, cal.ty[y], cal.a, cal.b, wfrac);
             FitOut fo;
+            bool queue = false;
             if constexpr (U4) {
                 const float sw = q * (float)n * w.wbar;
                 fo = solve_unit4<float>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, sw * w.mx, sw * w.my, sw,
                                         sw * q * w.what);
+                queue = flags && !(fo.gap >= tau);
             } else {
-                float l0;
-                smallest_eigpair<float>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, fo.nx, fo.ny, fo.nz, l0, fo.gap);
+                float l0, l2n;
+                smallest_eigpair<float>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, fo.nx, fo.ny, fo.nz, l0, fo.gap,
+                                        &l2n);
                 fo.curv = l0;
+                if (flags) {
+                    queue = !(fo.gap >= tau);
+                    if (!queue && !fixed_quantum<DT, SF_METHOD_DISPARITY>()) {
+                        const float tr = w.R11 + w.R22 + w.R33, iw = 1.f / w.what;
+                        queue = rounding_error2<float>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, fo.nx, fo.ny, fo.nz,
+                                                       w.mx * iw, w.my * iw, iw, l0 * tr, (l0 + fo.gap * l2n) * tr,
+                                                       l2n * tr) > kRefineRounding * kRefineRounding;
+                    }
+                }
                 fo.d = -(fo.nx * w.mx + fo.ny * w.my + fo.nz) * Fn<float>::rcp(w.what * q);
                 orient<float>(fo.nx, fo.ny, fo.nz, fo.d);
             }
             nx = fo.nx; ny = fo.ny; nz = fo.nz; d = fo.d; cu = fo.curv;
+            if (queue) {
+                const unsigned mask = __activemask();
+                const int leader = __ffs(mask) - 1;
+                unsigned base = 0;
+                if (lane == leader) base = atomicAdd(flag_count, (unsigned)__popc(mask));
+                base = __shfl_sync(mask, base, leader);
+                flags[base + __popc(mask & ((1u << lane) - 1u))] =
+                    ((unsigned long long)f << 48) | ((unsigned long long)y << 24) | (unsigned long long)x;
+            }
         }
         normals[3 * oi] = nx; normals[3 * oi + 1] = ny; normals[3 * oi + 2] = nz;
         offsets[oi] = d; curvature[oi] = cu;
         if (counts) counts[oi] = n;
         if (more) S.apply(r);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Precision modes with a table: the queued windows solved again in FP64 from
+// sums of the unrounded depth and the table's rays, as the paper defines the
+// fit (Eq. 14 with the rays of Eq. 1 / Eq. 10), with no fixed point.  Each
+// warp takes 32 windows; for each in turn its lanes sum the window's columns
+// (lane l: column offset j = l - r), first the count and the disparity to
+// centre on, then the moments of the shifted offsets jh = j + D/S,
+// ih = i + E/S and of w' = w - wc; every lane then solves its own window.
+// ---------------------------------------------------------------------------
+// Disparity (1/m) of a stored value in FP64, or -1 for a missing pixel,
+// under the same validity rule as the fixed-point path.
+template <int DT>
+__device__ __forceinline__ double disparity_f64(float zin, const Codec& cd) {
+    if (DT == SF_DEPTH_DISPARITY_U16) {
+        const int w = disparity_units(zin, cd);
+        return w < 0 ? -1.0 : (double)cd.scale * ((double)w + (double)cd.frac);
+    }
+    if (DT == SF_DEPTH_U16) return zin != 0.f ? 1.0 / ((double)zin * (double)cd.scale) : -1.0;
+    return depth_valid(zin) ? 1.0 / (double)zin : -1.0;
+}
+
+constexpr int kDirectSums = 10;  // n, sum jh, ih, jh^2, jh ih, ih^2, w', w' jh, w' ih, w'^2
+
+template <int DT>
+__device__ __forceinline__ void direct_sums(const void* __restrict__ dframe, const int* __restrict__ dtab, int W,
+                                            int H, int r, const Codec& cd, int px, int py, double* out) {
+    const int lane = threadIdx.x & 31;
+    const int j = lane - r;
+    const int x = px + j;
+    const bool col = lane <= 2 * r && x >= 0 && x < W;
+    const size_t fe = (size_t)W * H;
+    // pass 1: the mean disparity, to centre the second moments on
+    double n = 0.0, sw = 0.0;
+#pragma unroll 1
+    for (int i = -r; i <= r; ++i) {
+        const int y = py + i;
+        if (!(col && y >= 0 && y < H)) continue;
+        const double w = disparity_f64<DT>(load_raw<DT>(dframe, (size_t)y * W + x), cd);
+        if (w < 0.0) continue;
+        n += 1.0; sw += w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+        sw += __shfl_xor_sync(0xffffffffu, sw, o);
+    }
+    const double wc = n > 0.0 ? sw / n : 0.0;
+    double v[kDirectSums];
+#pragma unroll
+    for (int c = 0; c < kDirectSums; ++c) v[c] = 0.0;
+    const double iS = 1.0 / (double)kDeltaScale;
+#pragma unroll 1
+    for (int i = -r; i <= r; ++i) {
+        const int y = py + i;
+        if (!(col && y >= 0 && y < H)) continue;
+        const size_t g = (size_t)y * W + x;
+        double w = disparity_f64<DT>(load_raw<DT>(dframe, g), cd);
+        if (w < 0.0) continue;
+        w -= wc;
+        const double jh = (double)j + (double)__ldg(dtab + g) * iS;
+        const double ih = (double)i + (double)__ldg(dtab + fe + g) * iS;
+        v[0] += 1.0; v[1] += jh; v[2] += ih; v[3] += jh * jh; v[4] += jh * ih; v[5] += ih * ih;
+        v[6] += w; v[7] += w * jh; v[8] += w * ih; v[9] += w * w;
+    }
+#pragma unroll
+    for (int c = 0; c < kDirectSums; ++c) {
+        double a = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        out[c] = a;
+    }
+    out[kDirectSums] = wc;
+}
+
+// The disparity window (as build_disparity: R = K Y K^T) from FP64 sums of the
+// shifted offsets and of w' = w - wc (w in 1/m).
+__device__ __forceinline__ DispWindowT<double> disparity_window_f64(const double* m, double tx, double ty, double a,
+                                                                    double b) {
+    using T = double;
+    const T n = m[0], wc = m[kDirectSums];
+    const T jb = m[1] / n, ib = m[2] / n;
+    const T Cjj = m[3] - m[1] * jb, Cji = m[4] - m[1] * ib, Cii = m[5] - m[2] * ib;
+    const T t0 = m[6] / n;
+    const T Cjw = m[7] - m[1] * t0, Ciw = m[8] - m[2] * t0, Cww = m[9] - m[6] * t0;
+    const T wbar = wc + t0;
+    const T inv_nw = T(1) / (n * wbar);
+    const T dj = Cjw * inv_nw, di = Ciw * inv_nw, e = Cww * inv_nw;
+    const T what = wbar + e;
+    const T Yjj = Cjj + n * dj * dj, Yji = Cji + n * dj * di, Yii = Cii + n * di * di;
+    const T Yjr = -n * dj, Yir = -n * di;
+    const T iw = T(1) / what;
+    const T Yrr = (Cww + n * e * e) * iw * iw;
+    DispWindowT<T> w;
+    w.mx = tx + a * (jb + dj);
+    w.my = ty + b * (ib + di);
+    w.R11 = a * a * Yjj + T(2) * a * w.mx * Yjr + w.mx * w.mx * Yrr;
+    w.R12 = a * b * Yji + a * w.my * Yjr + b * w.mx * Yir + w.mx * w.my * Yrr;
+    w.R13 = a * Yjr + w.mx * Yrr;
+    w.R22 = b * b * Yii + T(2) * b * w.my * Yir + w.my * w.my * Yrr;
+    w.R23 = b * Yir + w.my * Yrr;
+    w.R33 = Yrr;
+    w.what = what;
+    w.wbar = wbar;
+    return w;
+}
+
+template <int DT, bool U4>
+__global__ void __launch_bounds__(128) direct_delta_kernel(const void* __restrict__ depth,
+                                                           const int* __restrict__ dtab, int W, int H, int r,
+                                                           Codec cd, const double* __restrict__ rays,
+                                                           const unsigned long long* __restrict__ flags,
+                                                           const unsigned* __restrict__ flag_count,
+                                                           float* __restrict__ normals, float* __restrict__ offsets,
+                                                           float* __restrict__ curvature) {
+    const unsigned count = *flag_count;
+    const int lane = threadIdx.x & 31;
+    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    const size_t fe = (size_t)W * H;
+    const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
+    for (unsigned base = warp * 32u; base < count; base += nwarps * 32u) {
+        const bool active = base + lane < count;
+        int f = 0, x = 0, y = 0;
+        if (active) {
+            const unsigned long long e = flags[base + lane];
+            f = (int)(e >> 48); y = (int)((e >> 24) & 0xffffff); x = (int)(e & 0xffffff);
+        }
+        double mine[kDirectSums + 1];
+        unsigned todo = __ballot_sync(0xffffffffu, active);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const int sf_ = __shfl_sync(0xffffffffu, f, src);
+            const int sx = __shfl_sync(0xffffffffu, x, src);
+            const int sy = __shfl_sync(0xffffffffu, y, src);
+            const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)sf_ * fe;
+            double sums[kDirectSums + 1];
+            direct_sums<DT>(dframe, dtab, W, H, r, cd, sx, sy, sums);
+            if (lane == src) {
+#pragma unroll
+                for (int c = 0; c <= kDirectSums; ++c) mine[c] = sums[c];
+            }
+        }
+        if (!active) continue;
+        const DispWindowT<double> w = disparity_window_f64(mine, rays[x], rays[W + y], rays[W + H], rays[W + H + 1]);
+        FitOutT<double> o;
+        if constexpr (U4) {
+            const double sw = mine[0] * w.wbar;  // sum w (1/m); sum w^2 = sw what
+            o = solve_unit4<double>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, sw * w.mx, sw * w.my, sw, sw * w.what);
+        } else {
+            double l0;
+            smallest_eigpair_iso<double>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, l0, o.gap);
+            o.curv = l0;
+            o.d = -(o.nx * w.mx + o.ny * w.my + o.nz) / w.what;
+            orient<double>(o.nx, o.ny, o.nz, o.d);
+        }
+        const size_t oi = (size_t)f * fe + (size_t)y * W + x;
+        normals[3 * oi] = (float)o.nx; normals[3 * oi + 1] = (float)o.ny; normals[3 * oi + 2] = (float)o.nz;
+        offsets[oi] = (float)o.d;
+        curvature[oi] = (float)o.curv;
     }
 }
 

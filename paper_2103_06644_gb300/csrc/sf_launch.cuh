@@ -276,13 +276,27 @@ sf_status launch_pass_delta(sf_ctx* c, int nfr, const void* depth, float* normal
         sf::hpass_delta_kernel<DT><<<grid, sf::kHThreads, smem, st>>>(depth, c->dtab, c->W, c->H, c->r, codec_of(c),
                                                                      c->vmax, bits, c->plane_elems, c->planes);
     }
+    // precision modes: the column pass queues the windows it cannot vouch for
+    // (mode 1) or every window (mode 2), and the direct kernel solves them again
+    // in FP64 from the unrounded depth
+    const bool fb = c->precision_mode > 0 && c->flags;
+    if (fb) SF_CUDA(cudaMemsetAsync(c->flag_count, 0, 2 * sizeof(unsigned), st));
     {
         StageTimer t(c, 2, st);
         const int band = vertical_band(c, nfr);
         dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
+        const float tau = c->precision_mode == 2 ? INFINITY : c->tau;
         sf::vpass_delta_kernel<DT, U4><<<grid, sf::kVThreads, 0, st>>>(
             depth, c->W, c->H, c->r, codec_of(c), c->vmax, bits, c->plane_elems, c->planes, calib_of(c),
-            c->min_valid, c->require_center, band, normals, offsets, curv, counts);
+            c->min_valid, c->require_center, band, normals, offsets, curv, counts, tau, fb ? c->flags : nullptr,
+            c->flag_count);
+    }
+    if (fb) {
+        StageTimer t(c, 3, st);
+        static const int nb = resident_blocks(c, sf::direct_delta_kernel<DT, U4>, 128);
+        sf::direct_delta_kernel<DT, U4><<<nb, 128, 0, st>>>(depth, c->dtab, c->W, c->H, c->r, codec_of(c),
+                                                             c->rays64, c->flags, c->flag_count, normals, offsets,
+                                                             curv);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");

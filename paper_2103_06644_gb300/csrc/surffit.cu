@@ -235,8 +235,8 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
         return fail(SF_ERR_INVALID_ARG, "buffers must be aligned to their element size");
     if (c->constraint == SF_CONSTRAINT_UNIT4 && c->method != SF_METHOD_DISPARITY && c->method != SF_METHOD_STANDARD)
         return fail(SF_ERR_UNSUPPORTED, "the |(a,b,c,d)| = 1 constraint applies to the implicit fits");
-    if (c->dtab && (c->method != SF_METHOD_DISPARITY || c->precision_mode != 0))
-        return fail(SF_ERR_UNSUPPORTED, "a per-pixel delta table applies to the disparity-form fit in precision mode 0");
+    if (c->dtab && c->method != SF_METHOD_DISPARITY)
+        return fail(SF_ERR_UNSUPPORTED, "a per-pixel delta table applies to the disparity-form fit");
     if (c->depth_type == SF_DEPTH_DISPARITY_U16 && sf::base_method(c->method) == SF_METHOD_DISPARITY) {
         // the disparity integers go into the int32 row sums unscaled: k w < 2^31
         const double wmax = 128.0 * 65535.0 + std::fabs((double)c->disp_add) + 1.0;
@@ -265,7 +265,8 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
         // the exact moments of queued windows: every window in mode 2, a quarter of
         // them in mode 1 (windows queued beyond that re-read their moments from
         // the scratch planes)
-        const size_t mcap = c->precision_mode == 2 ? cap : (cap + 3) / 4;
+        // (the delta-table path solves from the depth and keeps no moments)
+        const size_t mcap = c->dtab ? 0 : c->precision_mode == 2 ? cap : (cap + 3) / 4;
         if (c->moments_cap < mcap) {
             if (c->moments_q) cudaFree(c->moments_q);
             c->moments_q = nullptr;
