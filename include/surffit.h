@@ -434,6 +434,18 @@ sf_status sf_quadtree(sf_ctx* ctx, int n_frames, const void* depth, const sf_qua
 /* Library version as a static string. */
 const char* sf_version(void);
 
+/*
+ * sf_eval_acos -- diagnostics: the float32 arccos that the per-pixel solve's
+ * trigonometric eigenvalue estimate uses (the closed-form roots of the 3x3
+ * characteristic polynomial behind Eq. 4-5), evaluated on the device for n
+ * values:
+ *   x   device float [n], each in [-1, 1]
+ *   y   device float [n], out
+ * Errors: SF_ERR_INVALID_ARG (null pointer, n < 0, misaligned buffer).
+ * Asynchronous on `stream`.
+ */
+sf_status sf_eval_acos(const float* x, float* y, int n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,7 @@ SIGNATURES = {
     "sf_last_error": (ctypes.c_char_p, []),
     "sf_channel_counts": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "sf_version": (ctypes.c_char_p, []),
+    "sf_eval_acos": (_I, [_VP, _VP, _I, _VP]),
     "sf_profile_enable": (_I, [_VP, _I]),
     "sf_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)]),
     "sf_fit_static": (_I, [ctypes.POINTER(Intrinsics), _I, _I, _I, _I, _I, _F, _I, _I, _VP, _VP, _VP, _VP, _VP]),

@@ -123,6 +123,23 @@ extern "C" {
 
 const char* sf_last_error(void) { return g_last_error.c_str(); }
 
+namespace {
+__global__ void acos_eval_kernel(const float* __restrict__ x, float* __restrict__ y, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = sf::acos_fast(x[i]);
+}
+}  // namespace
+
+sf_status sf_eval_acos(const float* x, float* y, int n, void* stream) {
+    if (n < 0) return fail(SF_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return SF_OK;
+    if (!x || !y) return fail(SF_ERR_INVALID_ARG, "null buffer");
+    if (misaligned(x, 4) || misaligned(y, 4)) return fail(SF_ERR_INVALID_ARG, "buffers must be 4-byte aligned");
+    acos_eval_kernel<<<(n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, y, n);
+    SF_CUDA(cudaGetLastError());
+    return SF_OK;
+}
+
 const char* sf_version(void) { return "surffit-gb300 0.1 (sm_103a)"; }
 
 sf_status sf_channel_counts(int method, int* depth_channels, int* mask_channels) {
