@@ -694,11 +694,20 @@ def main():
             diff_step()
         t_fb = timed(20, diff_step)
         t_f = timed(20, lambda: fd.fit(dd))
+        fd.close()
+        # the same step with 31 x 31 windows (the box sums of the backward are O(1) per pixel)
+        fd = SurfaceFitter(intr.as_tuple(), 640, 480, 31, method="disparity")
+        for _ in range(3):
+            diff_step()
+        t_fb31 = timed(10, diff_step)
+        t_f31 = timed(10, lambda: fd.fit(dd))
         line["mixed_batch"] = mixed_batch_report(dev, timed, world)
         line["segmentation_512x424"] = segmentation_report(dev, timed, world)
         line["differentiation_k9"] = {"workload": "16x640x480 f32, k=9, loss |n-n*|^2 + 0.1 kappa",
                                       "value": whole_job_rate(world, nd * 307200, t_fb), "unit": UNIT,
-                                      "ms_per_step_fwd_bwd": t_fb, "ms_forward": t_f}
+                                      "ms_per_step_fwd_bwd": t_fb, "ms_forward": t_f,
+                                      "k31": {"value": whole_job_rate(world, nd * 307200, t_fb31), "unit": UNIT,
+                                              "ms_per_step_fwd_bwd": t_fb31, "ms_forward": t_f31}}
         fd.close()
     if not args.no_e2e and not args.profile_only:
         # inputs and caller-owned result arrays in pinned (page-locked) host memory, reused every step

@@ -50,6 +50,7 @@ struct sf_ctx {
     cudaEvent_t io_fit_done[2] = {nullptr, nullptr};
     cudaEvent_t io_entry = nullptr;
     float* adj = nullptr;      // backward: per-window adjoint planes
+    float* adj_max = nullptr;  // backward: per-frame bounds of the adjoint terms [64][3] (inside adj)
     size_t adj_bytes = 0;
     int* dtab = nullptr;       // per-pixel ray adjustments: D plane then E plane [H][W], 1/2^18 pixel, or none
     // precision fallback

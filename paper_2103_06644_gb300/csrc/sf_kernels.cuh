@@ -582,35 +582,39 @@ struct DispState {
     // The two horizontal-moment rows of the slide from output row y to y + 1
     // (leaving row y - r, entering row y + r + 1; zero outside the image).
     // fetch() only issues the loads, so a caller can overlap them with the
-    // solve of row y and apply() them afterwards.
-    int32_t pm_o = 0, pm_i = 0, pwo = 0, pwi = 0, pwjo = 0, pwji = 0;
-    int64_t pwwo = 0, pwwi = 0;
-    __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) {
+    // solve of row y and apply() them afterwards; fetch_rows / apply_rows do
+    // the same with a caller-held buffer (several slides in flight).
+    struct Rows {
+        int32_t m_o = 0, m_i = 0, w_o = 0, w_i = 0, wj_o = 0, wj_i = 0;
+        int64_t ww_o = 0, ww_i = 0;
+    };
+    Rows pend;
+    __device__ __forceinline__ void fetch_rows(Rows& R, size_t pb, int rs, int H, int y, int r) const {
         const int yo = y - r, yi = y + r + 1;
-        pm_o = pm_i = 0;
-        pwo = pwjo = pwi = pwji = 0;
-        pwwo = pwwi = 0;
+        R = Rows();
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * rs;
-            pm_o = __ldg(hm + o); pwo = __ldg(g0 + o); pwjo = __ldg(g1 + o); pwwo = __ldg(q0 + o);
+            R.m_o = __ldg(hm + o); R.w_o = __ldg(g0 + o); R.wj_o = __ldg(g1 + o); R.ww_o = __ldg(q0 + o);
         }
         if (yi < H) {
             const size_t o = pb + (size_t)yi * rs;
-            pm_i = __ldg(hm + o); pwi = __ldg(g0 + o); pwji = __ldg(g1 + o); pwwi = __ldg(q0 + o);
+            R.m_i = __ldg(hm + o); R.w_i = __ldg(g0 + o); R.wj_i = __ldg(g1 + o); R.ww_i = __ldg(q0 + o);
         }
     }
-    __device__ __forceinline__ void apply(int r) {
+    __device__ __forceinline__ void apply_rows(const Rows& R, int r) {
         int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
-        if (pm_o) unpack_mask(pm_o, o0, o1, o2);
-        if (pm_i) unpack_mask(pm_i, i0, i1, i2);
+        if (R.m_o) unpack_mask(R.m_o, o0, o1, o2);
+        if (R.m_i) unpack_mask(R.m_i, i0, i1, i2);
         // vertical moments: (n, Si, Sii) from the counts, (Sj, Sji) from sum j, Sjj plain
         slide3(n, Si, Sii, (float)o0, (float)i0, r);
         slide2(Sj, Sji, (float)o1, (float)i1, r);
         Sjj += (float)(i2 - o2);
-        slide2(Sw, Swi, (int64_t)pwo, (int64_t)pwi, r);
-        Swj += join_wj(pm_i, pwji) - join_wj(pm_o, pwjo);
-        Sww += pwwi - pwwo;
+        slide2(Sw, Swi, (int64_t)R.w_o, (int64_t)R.w_i, r);
+        Swj += join_wj(R.m_i, R.wj_i) - join_wj(R.m_o, R.wj_o);
+        Sww += R.ww_i - R.ww_o;
     }
+    __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) { fetch_rows(pend, pb, rs, H, y, r); }
+    __device__ __forceinline__ void apply(int r) { apply_rows(pend, r); }
     // slide from output row y to y + 1
     __device__ __forceinline__ void slide(size_t pb, int rs, int H, int y, int r) {
         fetch(pb, rs, H, y, r);
@@ -663,43 +667,48 @@ struct StdStateT {
         }
     }
     // fetch() / apply(): the slide from output row y to y + 1 split into its
-    // loads and its arithmetic (as for DispState).
-    int32_t pm_o = 0, pm_i = 0;
-    int64_t zo = 0, zjo = 0, qo0 = 0, qo1 = 0, qo2 = 0, zi = 0, zji = 0, qi0 = 0, qi1 = 0, qi2 = 0;
-    __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) {
+    // loads and its arithmetic (as for DispState); fetch_rows / apply_rows
+    // with a caller-held buffer.
+    struct Rows {
+        int32_t m_o = 0, m_i = 0;
+        int64_t zo = 0, zjo = 0, qo0 = 0, qo1 = 0, qo2 = 0, zi = 0, zji = 0, qi0 = 0, qi1 = 0, qi2 = 0;
+    };
+    Rows pend;
+    __device__ __forceinline__ void fetch_rows(Rows& R, size_t pb, int rs, int H, int y, int r) const {
         const int yo = y - r, yi = y + r + 1;
-        pm_o = pm_i = 0;
-        zo = zjo = qo0 = qo1 = qo2 = zi = zji = qi0 = qi1 = qi2 = 0;
+        R = Rows();
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * rs;
-            pm_o = __ldg(hc + o); zo = __ldg(z0 + o); zjo = __ldg(z1 + o);
-            qo0 = __ldg(b0 + o); qo1 = __ldg(b1 + o); qo2 = __ldg(b2 + o);
+            R.m_o = __ldg(hc + o); R.zo = __ldg(z0 + o); R.zjo = __ldg(z1 + o);
+            R.qo0 = __ldg(b0 + o); R.qo1 = __ldg(b1 + o); R.qo2 = __ldg(b2 + o);
         }
         if (yi < H) {
             const size_t o = pb + (size_t)yi * rs;
-            pm_i = __ldg(hc + o); zi = __ldg(z0 + o); zji = __ldg(z1 + o);
-            qi0 = __ldg(b0 + o); qi1 = __ldg(b1 + o); qi2 = __ldg(b2 + o);
+            R.m_i = __ldg(hc + o); R.zi = __ldg(z0 + o); R.zji = __ldg(z1 + o);
+            R.qi0 = __ldg(b0 + o); R.qi1 = __ldg(b1 + o); R.qi2 = __ldg(b2 + o);
         }
     }
-    __device__ __forceinline__ void slide(size_t pb, int rs, int H, int y, int r) {
-        fetch(pb, rs, H, y, r);
-        apply(r);
-    }
-    __device__ __forceinline__ void apply(int r) {
+    __device__ __forceinline__ void apply_rows(const Rows& R, int r) {
         int o0 = 0, o1 = 0, o2 = 0, i0 = 0, i1 = 0, i2 = 0;
-        if (pm_o) unpack_mask(pm_o, o0, o1, o2);
-        if (pm_i) unpack_mask(pm_i, i0, i1, i2);
+        if (R.m_o) unpack_mask(R.m_o, o0, o1, o2);
+        if (R.m_i) unpack_mask(R.m_i, i0, i1, i2);
         n += i0 - o0;
         if constexpr (kMask) {
             slide3(fn, Si, Sii, (float)o0, (float)i0, r);
             slide2(Sj, Sji, (float)o1, (float)i1, r);
             Sjj += (float)(i2 - o2);
         }
-        slide2(Sz, Szi, zo, zi, r);
-        Szj += zji - zjo;
-        slide3(Szz, Szzi, Szzii, qo0, qi0, r);
-        slide2(Szzj, Szzji, qo1, qi1, r);
-        Szzjj += qi2 - qo2;
+        slide2(Sz, Szi, R.zo, R.zi, r);
+        Szj += R.zji - R.zjo;
+        slide3(Szz, Szzi, Szzii, R.qo0, R.qi0, r);
+        slide2(Szzj, Szzji, R.qo1, R.qi1, r);
+        Szzjj += R.qi2 - R.qo2;
+    }
+    __device__ __forceinline__ void fetch(size_t pb, int rs, int H, int y, int r) { fetch_rows(pend, pb, rs, H, y, r); }
+    __device__ __forceinline__ void apply(int r) { apply_rows(pend, r); }
+    __device__ __forceinline__ void slide(size_t pb, int rs, int H, int y, int r) {
+        fetch(pb, rs, H, y, r);
+        apply(r);
     }
     __device__ __forceinline__ int count() const { return n; }
 };
@@ -1014,7 +1023,7 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
                                                              const float* __restrict__ g_normals,
                                                              const float* __restrict__ g_offsets,
                                                              const float* __restrict__ g_curv,
-                                                             float* __restrict__ adj) {
+                                                             float* __restrict__ adj, float* __restrict__ adj_max) {
     const int f = blockIdx.z;
     const int x = blockIdx.x * kVThreads + threadIdx.x;
     if (x >= W) return;
@@ -1030,6 +1039,7 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
     constexpr int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
     typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
     S.init(pb, kGroup, H, y0, r);
+    float tmax[3] = {0.f, 0.f, 0.f};
     for (int y = y0; y < y1; ++y) {
         const size_t oi = fo + (size_t)y * W + x;
         const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
@@ -1104,78 +1114,229 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
             }
         }
 #pragma unroll
-        for (int c = 0; c < NC; ++c) adj[((size_t)c * nf + f) * fe + (size_t)y * W + x] = out[c];
+        for (int c = 0; c < NC; ++c) {
+            adj[((size_t)c * nf + f) * fe + (size_t)y * W + x] = out[c];
+            // the frame's bounds of the box-summed terms (gather_kernel's fixed-point scales)
+            const int grp = M == SF_METHOD_DISPARITY ? (c < 3 ? 0 : (c < 6 ? 1 : 2)) : (c < 6 ? 0 : (c < 9 ? 1 : 2));
+            tmax[grp] = fmaxf(tmax[grp], fabsf(out[c]));
+        }
         if (y + 1 < y1) S.slide(pb, kGroup, H, y, r);
+    }
+    // non-negative floats order as their bit patterns
+    const unsigned mask = __activemask();
+    const bool leader = (threadIdx.x & 31) == __ffs(mask) - 1;
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+        const unsigned m = __reduce_max_sync(mask, __float_as_uint(tmax[g]));
+        if (leader && m) atomicMax(reinterpret_cast<unsigned*>(adj_max) + 3 * f + g, m);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Backward, step 2: every pixel q gathers the contributions of the windows
-// p that contain it (p in the k x k window around q, by symmetry) from a
-// shared-memory tile of the adjoint planes, and applies the chain rule
+// Backward, step 2: every pixel q sums the contributions of the windows p that
+// contain it (p in the k x k window around q, by symmetry) and applies the
+// chain rule
 //   disparity: dL/dZ_q = -w_q^3 sum_p [(P_q - mu_p) . gbar_p - c_p]
 //   standard:  dL/dZ_q = m_q . sum_p [2 Rbar_p (P_q - mu_p) - e_p]
-// Missing pixels get 0.  Block: 32 x 8 threads, 32 x 32 output tile.
+// With a reference point P0 the sums factor into k x k box sums of per-window
+// quantities, O(1) per pixel like the forward's window sums (Section II.C):
+//   disparity: (P_q - P0) . G_q - E_q,      G = box(gbar), E = box((mu - P0) . gbar + c)
+//   standard:  A_q (P_q - P0) - V_q,        A = box(2 Rbar), V = box(2 Rbar (mu - P0) + e)
+// P0 is the centroid of the output tile's centre window.  The two terms
+// cancel by the ratio of |P_q - P0| to the window's extent (large where a
+// tile straddles a depth edge), so the box sums are exact: the per-window
+// terms are quantised to int64 fixed point with a power of two per channel
+// group that puts the frame's bound on them (from the maxima the adjoint
+// kernel records) below 2^39, so that sums of up to 961 terms stay below
+// 2^49, and the final difference is formed in float-float arithmetic.
+// Block: 32 x 8 threads, one 32 x 32 output tile.  Each warp takes whole rows
+// of the tile and its r-pixel halo (two staged columns per lane, every
+// channel loaded at once), quantises them and forms the horizontal window
+// sums with a warp scan; the 32 sums of each row go to shared memory, where
+// the columns are box-summed in place (running sums).  Missing pixels get 0.
 // ---------------------------------------------------------------------------
 constexpr int kGTile = 32;
+template <int M>
+__host__ __device__ constexpr int gather_channels_box() { return M == SF_METHOD_DISPARITY ? 4 : 9; }
+// boxed channels in the first group (gbar; 2 Rbar), the rest in the second
+template <int M>
+__host__ __device__ constexpr int gather_group0() { return M == SF_METHOD_DISPARITY ? 3 : 6; }
+__host__ __device__ constexpr size_t gather_smem_bytes(int nb, int r) {
+    return sizeof(long long) * (size_t)nb * (size_t)(kGTile + 2 * r) * kGTile;
+}
+
+// round(t) for |t| < 2^41 as int64 without a 64-bit conversion instruction:
+// |t| < 2^31 rounds through int32; larger t are integers already (24-bit
+// significand) and split exactly into 2^32 hi + lo with lo in [0, 2^32).
+__device__ __forceinline__ long long round_i64(float t) {
+    if (fabsf(t) < 2147483648.f) return (long long)__float2int_rn(t);
+    const float hi = floorf(t * 2.3283064365386963e-10f);  // t / 2^32
+    const float lo = fmaf(hi, -4294967296.f, t);            // exact
+    return ((long long)(int)hi << 32) + (long long)__float2uint_rn(lo);
+}
+
+// The boxed terms of one window (adjoint channels at element o of the frame).
+template <int M>
+__device__ __forceinline__ void gather_terms(const float* __restrict__ src, size_t cstride, size_t o, float p0x,
+                                             float p0y, float p0z, float* v) {
+    if constexpr (M == SF_METHOD_DISPARITY) {
+        const float g0 = src[o], g1 = src[cstride + o], g2 = src[2 * cstride + o];
+        const float ux = src[3 * cstride + o] - p0x, uy = src[4 * cstride + o] - p0y, uz = src[5 * cstride + o] - p0z;
+        v[0] = g0; v[1] = g1; v[2] = g2;
+        v[3] = fmaf(ux, g0, fmaf(uy, g1, fmaf(uz, g2, src[6 * cstride + o])));
+    } else {
+        float a[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a[c] = src[c * cstride + o];
+        const float ux = src[6 * cstride + o] - p0x, uy = src[7 * cstride + o] - p0y, uz = src[8 * cstride + o] - p0z;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] = a[c];
+        v[6] = fmaf(a[0], ux, fmaf(a[1], uy, fmaf(a[2], uz, src[9 * cstride + o])));
+        v[7] = fmaf(a[1], ux, fmaf(a[3], uy, fmaf(a[4], uz, src[10 * cstride + o])));
+        v[8] = fmaf(a[2], ux, fmaf(a[4], uy, fmaf(a[5], uz, src[11 * cstride + o])));
+    }
+}
+
+// Float-float arithmetic for the final difference (FP64 runs at a small
+// fraction of the float32 rate): x = hi + lo with |lo| <= ulp(hi) / 2.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return FF{s, (a - (s - bb)) + (b - bb)};
+}
+// an exact integer sum (|v| < 2^49) times a power of two, to float-float:
+// v = h 2^32 + m 2^16 + l with h < 2^17 and m, l < 2^16 (each exact in
+// float32); the two error-free sums leave only the low word's rounding
+// (2^-48 relative)
+__device__ __forceinline__ FF ff_from_i64(long long v, float sc) {
+    const float h = (float)(int)(v >> 32) * 4294967296.f * sc;
+    const float m = (float)(int)((v >> 16) & 0xffff) * 65536.f * sc;
+    const float l = (float)(int)(v & 0xffff) * sc;
+    const FF a = ff_two_sum(h, m);
+    const FF b = ff_two_sum(a.hi, l);
+    return FF{b.hi, b.lo + a.lo};
+}
+// acc += u * x (u float), error-free up to the low-order products
+__device__ __forceinline__ void ff_fma(FF& acc, float u, FF x) {
+    const float p = u * x.hi, pe = fmaf(u, x.hi, -p);
+    const FF s = ff_two_sum(acc.hi, p);
+    acc.hi = s.hi;
+    acc.lo += s.lo + pe + u * x.lo;
+}
+__device__ __forceinline__ void ff_sub(FF& acc, FF x) {
+    const FF s = ff_two_sum(acc.hi, -x.hi);
+    acc.hi = s.hi;
+    acc.lo += s.lo - x.lo;
+}
+
+// Power-of-two scale putting values up to `bound` below 2^39 (0 for a zero or
+// non-finite bound: the channel group contributes nothing).
+__device__ __forceinline__ float gather_scale(float bound) {
+    if (!(bound > 0.f && bound < INFINITY)) return 0.f;
+    int e = 0;
+    frexpf(bound, &e);
+    return ldexpf(1.f, 39 - e);
+}
 
 template <int DT, int M>
 __global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ depth, int W, int H, int r, Codec scale,
                                                      Calib cal, const float* __restrict__ adj,
-                                                     float* __restrict__ g_depth) {
-    extern __shared__ float sadj[];
-    constexpr int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
+                                                     const float* __restrict__ adj_max, float* __restrict__ g_depth) {
+    extern __shared__ long long hs[];  // [channel][staged row][output column]
+    constexpr int NB = gather_channels_box<M>(), NG = gather_group0<M>();
+    constexpr int MU = (M == SF_METHOD_DISPARITY) ? 3 : 6;  // first centroid channel
     const int f = blockIdx.z;
-    const size_t nf = gridDim.z;
     const size_t fe = (size_t)W * H;
+    const size_t cstride = (size_t)gridDim.z * fe;
+    const float* src = adj + (size_t)f * fe;
     const int x0 = blockIdx.x * kGTile, y0 = blockIdx.y * kGTile;
-    const int T = kGTile + 2 * r;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int c = 0; c < NC; ++c) {
-        const float* src = adj + ((size_t)c * nf + f) * fe;
-        for (int idx = tid; idx < T * T; idx += 256) {
-            const int ty_ = idx / T, tx_ = idx - ty_ * T;
-            const int xx = x0 - r + tx_, yy = y0 - r + ty_;
-            float v = 0.f;
-            if (xx >= 0 && xx < W && yy >= 0 && yy < H) v = src[(size_t)yy * W + xx];
-            sadj[(c * T + ty_) * T + tx_] = v;
+    const int K = 2 * r + 1, T = kGTile + 2 * r;
+    const int lane = threadIdx.x, warp = threadIdx.y, tid = warp * 32 + lane;
+    // reference point: the centroid of the window at the tile centre (0 where that window is invalid)
+    const size_t oc = (size_t)min(y0 + kGTile / 2, H - 1) * W + min(x0 + kGTile / 2, W - 1);
+    const float p0x = src[MU * cstride + oc], p0y = src[(MU + 1) * cstride + oc], p0z = src[(MU + 2) * cstride + oc];
+    // |group 0| <= gm; |group 1| <= |mu - P0|_max |gbar|_1 + |c| <= 2 mm 3 gm + cm (likewise 2 Rbar, e)
+    const float gm = adj_max[3 * f], mm = adj_max[3 * f + 1], cm = adj_max[3 * f + 2];
+    const float s0 = gather_scale(gm), s1 = gather_scale(6.f * mm * gm + cm);
+    for (int ty_ = warp; ty_ < T; ty_ += 8) {
+        const int yy = y0 - r + ty_;
+        float v[2][NB];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xx = x0 - r + lane + 32 * h;
+#pragma unroll
+            for (int c = 0; c < NB; ++c) v[h][c] = 0.f;
+            if (lane + 32 * h < T && xx >= 0 && xx < W && yy >= 0 && yy < H)
+                gather_terms<M>(src, cstride, (size_t)yy * W + xx, p0x, p0y, p0z, v[h]);
+        }
+        const int hi = lane + 2 * r;  // last staged column of output column `lane`'s window (< 64)
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+            const float sc = c < NG ? s0 : s1;
+            long long a = round_i64(v[0][c] * sc), b = round_i64(v[1][c] * sc);
+            // inclusive prefix sums over staged columns 0..31 (a) and 32..63 (b)
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long ta = __shfl_up_sync(0xffffffffu, a, o), tb = __shfl_up_sync(0xffffffffu, b, o);
+                if (lane >= o) { a += ta; b += tb; }
+            }
+            b += __shfl_sync(0xffffffffu, a, 31);
+            const long long pa = __shfl_sync(0xffffffffu, a, hi & 31), pb = __shfl_sync(0xffffffffu, b, hi & 31);
+            const long long pl = __shfl_sync(0xffffffffu, a, (lane + 31) & 31);
+            hs[((size_t)c * T + ty_) * kGTile + lane] = (hi < 32 ? pa : pb) - (lane > 0 ? pl : 0ll);
         }
     }
     __syncthreads();
-    const int x = x0 + threadIdx.x;
+    // vertical box sums of every output column, in place
+    for (int item = tid; item < NB * kGTile; item += 256) {
+        long long* a = hs + (size_t)(item / kGTile) * T * kGTile + (item % kGTile);
+        long long S = 0;
+        for (int i = 0; i < K; ++i) S += a[(size_t)i * kGTile];
+        for (int i = 0; i < kGTile; ++i) {
+            const long long out = S;
+            if (i + 1 < kGTile) S += a[(size_t)(i + K) * kGTile] - a[(size_t)i * kGTile];
+            a[(size_t)i * kGTile] = out;
+        }
+    }
+    __syncthreads();
+    // 1 / scale: powers of two, so scaling is exact
+    const float i0 = s0 > 0.f ? 1.f / s0 : 0.f, i1 = s1 > 0.f ? 1.f / s1 : 0.f;
+    const size_t cs = (size_t)T * kGTile;
+    const int x = x0 + lane;
     if (x >= W) return;
     const float tx = cal.tx[x];
-    for (int yr = threadIdx.y; yr < kGTile; yr += 8) {
+    for (int yr = warp; yr < kGTile; yr += 8) {
         const int y = y0 + yr;
         if (y >= H) break;
         const size_t oi = (size_t)f * fe + (size_t)y * W + x;
         const float z = load_depth<DT>(depth, oi, scale);
         float g = 0.f;
         if (depth_valid(z)) {
-            const float px = z * tx, py = z * cal.ty[y], pz = z;
-            float acc = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-            for (int dy = 0; dy <= 2 * r; ++dy) {
-                const int row = yr + dy;
-                for (int dx = 0; dx <= 2 * r; ++dx) {
-                    const int col = threadIdx.x + dx;
-                    const float* sp = sadj + row * T + col;
-                    const size_t cs = (size_t)T * T;
-                    if constexpr (M == SF_METHOD_DISPARITY) {
-                        acc += (px - sp[3 * cs]) * sp[0] + (py - sp[4 * cs]) * sp[cs] + (pz - sp[5 * cs]) * sp[2 * cs] -
-                               sp[6 * cs];
-                    } else {
-                        const float ux = px - sp[6 * cs], uy = py - sp[7 * cs], uz = pz - sp[8 * cs];
-                        ax += sp[0] * ux + sp[cs] * uy + sp[2 * cs] * uz - sp[9 * cs];
-                        ay += sp[cs] * ux + sp[3 * cs] * uy + sp[4 * cs] * uz - sp[10 * cs];
-                        az += sp[2 * cs] * ux + sp[4 * cs] * uy + sp[5 * cs] * uz - sp[11 * cs];
-                    }
-                }
-            }
+            const float ty = cal.ty[y];
+            const float ux = z * tx - p0x, uy = z * ty - p0y, uz = z - p0z;
+            const size_t p = (size_t)yr * kGTile + lane;
             if constexpr (M == SF_METHOD_DISPARITY) {
+                FF acc{0.f, 0.f};
+                ff_fma(acc, ux, ff_from_i64(hs[p], i0));
+                ff_fma(acc, uy, ff_from_i64(hs[cs + p], i0));
+                ff_fma(acc, uz, ff_from_i64(hs[2 * cs + p], i0));
+                ff_sub(acc, ff_from_i64(hs[3 * cs + p], i1));
                 const float w = 1.f / z;
-                g = -w * w * w * acc;
+                g = -w * w * w * (acc.hi + acc.lo);
             } else {
-                g = tx * ax + cal.ty[y] * ay + az;
+                const FF a11 = ff_from_i64(hs[p], i0), a12 = ff_from_i64(hs[cs + p], i0);
+                const FF a13 = ff_from_i64(hs[2 * cs + p], i0), a22 = ff_from_i64(hs[3 * cs + p], i0);
+                const FF a23 = ff_from_i64(hs[4 * cs + p], i0), a33 = ff_from_i64(hs[5 * cs + p], i0);
+                FF ax{0.f, 0.f}, ay{0.f, 0.f}, az{0.f, 0.f};
+                ff_fma(ax, ux, a11); ff_fma(ax, uy, a12); ff_fma(ax, uz, a13);
+                ff_fma(ay, ux, a12); ff_fma(ay, uy, a22); ff_fma(ay, uz, a23);
+                ff_fma(az, ux, a13); ff_fma(az, uy, a23); ff_fma(az, uz, a33);
+                ff_sub(ax, ff_from_i64(hs[6 * cs + p], i1));
+                ff_sub(ay, ff_from_i64(hs[7 * cs + p], i1));
+                ff_sub(az, ff_from_i64(hs[8 * cs + p], i1));
+                g = tx * (ax.hi + ax.lo) + ty * (ay.hi + ay.lo) + (az.hi + az.lo);
             }
         }
         g_depth[oi] = g;

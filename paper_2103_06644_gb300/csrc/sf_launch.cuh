@@ -325,18 +325,17 @@ sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const float* gn
     {
         const int band = vertical_band(c, nfr);
         dim3 grid((c->W + sf::kVThreads - 1) / sf::kVThreads, (c->H + band - 1) / band, nfr);
+        SF_CUDA(cudaMemsetAsync(c->adj_max, 0, sizeof(float) * 3 * nfr, st));
         sf::vadjoint_kernel<DT, M><<<grid, sf::kVThreads, 0, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
                                                                   bits, c->Wp, c->plane_elems, c->planes, cal,
                                                                   c->min_valid, c->require_center, band, gn, gd, gk,
-                                                                  c->adj);
+                                                                  c->adj, c->adj_max);
     }
     {
-        const int NC = (M == SF_METHOD_DISPARITY) ? 7 : 12;
-        const int T = sf::kGTile + 2 * c->r;
-        const size_t smem = sizeof(float) * NC * (size_t)T * T;
+        const size_t smem = sf::gather_smem_bytes(sf::gather_channels_box<M>(), c->r);
         dim3 grid((c->W + sf::kGTile - 1) / sf::kGTile, (c->H + sf::kGTile - 1) / sf::kGTile, nfr);
-        sf::gather_kernel<DT, M><<<grid, dim3(32, 8), smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), cal,
-                                                                   c->adj, g_depth);
+        sf::gather_kernel<DT, M><<<grid, dim3(32, 8), smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), cal, c->adj,
+                                                                   c->adj_max, g_depth);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "backward kernel launch");
@@ -383,12 +382,10 @@ void set_kernel_smem_t() {
     const int dsmem = (int)(3 * sizeof(int) * sf::kHThreads * (size_t)((32 + 2 * sf::kMaxR) | 1));
     cudaFuncSetAttribute(sf::hpass_delta_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem);
     if constexpr (DT != SF_DEPTH_DISPARITY_U16) {
-        const int T = sf::kGTile + 2 * sf::kMaxR;
-        const int gs7 = (int)(sizeof(float) * 7 * T * T), gs12 = (int)(sizeof(float) * 12 * T * T);
         cudaFuncSetAttribute(sf::gather_kernel<DT, SF_METHOD_DISPARITY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             gs7);
+                             (int)sf::gather_smem_bytes(4, sf::kMaxR));
         cudaFuncSetAttribute(sf::gather_kernel<DT, SF_METHOD_STANDARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             gs12);
+                             (int)sf::gather_smem_bytes(9, sf::kMaxR));
     }
 }
 

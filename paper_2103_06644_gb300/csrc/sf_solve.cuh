@@ -460,10 +460,16 @@ __device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj
 // P_q = Z_q m_q = T [Z j, Z i, Z] with T = [[a, 0, tx], [0, b, ty], [0, 0, 1]],
 // so the covariance of the points is T C T^T, C the covariance of
 // [z j, z i, z] (re-centred on an integer near the mean depth first).
-template <typename T = float, bool U4 = false, bool kEst = false>
-__device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
-                                                     int64_t Szzj, int64_t Szzi, int64_t Szzjj, int64_t Szzji,
-                                                     int64_t Szzii, T qz, T tx, T ty, T a, T b) {
+template <typename T>
+struct StdWindowT {
+    T R11, R12, R13, R22, R23, R33;  // covariance of the window's points (units of qz^2)
+    T px, py, zb;                    // their centroid (units of qz)
+};
+
+template <typename T = float>
+__device__ __forceinline__ StdWindowT<T> build_standard(T nf, int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
+                                                        int64_t Szzj, int64_t Szzi, int64_t Szzjj, int64_t Szzji,
+                                                        int64_t Szzii, T tx, T ty, T a, T b) {
     const T inv_n = Fn<T>::rcp(nf);
     const int n = (int)nf;
     const int m = __float2int_rn((float)(Fn<T>::from_i64(Sz) * inv_n));       // m < 2^31
@@ -480,14 +486,26 @@ __device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t S
     const T Cjj = Fn<T>::from_i64(Szzjj) - fSzj * qj;
     const T Cji = Fn<T>::from_i64(Szzji) - fSzj * qi;
     const T Cii = Fn<T>::from_i64(Szzii) - fSzi * qi;
-    const T R11 = a * a * Cjj + T(2) * a * tx * Cjz + tx * tx * Czz;
-    const T R12 = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
-    const T R13 = a * Cjz + tx * Czz;
-    const T R22 = b * b * Cii + T(2) * b * ty * Ciz + ty * ty * Czz;
-    const T R23 = b * Ciz + ty * Czz;
-    const T R33 = Czz;
-    const T zb = (T)m + t0;
-    const T px = a * qj + tx * zb, py = b * qi + ty * zb;
+    StdWindowT<T> w;
+    w.R11 = a * a * Cjj + T(2) * a * tx * Cjz + tx * tx * Czz;
+    w.R12 = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
+    w.R13 = a * Cjz + tx * Czz;
+    w.R22 = b * b * Cii + T(2) * b * ty * Ciz + ty * ty * Czz;
+    w.R23 = b * Ciz + ty * Czz;
+    w.R33 = Czz;
+    w.zb = (T)m + t0;
+    w.px = a * qj + tx * w.zb;
+    w.py = b * qi + ty * w.zb;
+    return w;
+}
+
+template <typename T = float, bool U4 = false, bool kEst = false>
+__device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t Szj, int64_t Szi, int64_t Szz,
+                                                     int64_t Szzj, int64_t Szzi, int64_t Szzjj, int64_t Szzji,
+                                                     int64_t Szzii, T qz, T tx, T ty, T a, T b) {
+    const StdWindowT<T> w = build_standard<T>(nf, Sz, Szj, Szi, Szz, Szzj, Szzi, Szzjj, Szzji, Szzii, tx, ty, a, b);
+    const T R11 = w.R11, R12 = w.R12, R13 = w.R13, R22 = w.R22, R23 = w.R23, R33 = w.R33;
+    const T px = w.px, py = w.py, zb = w.zb;
     if constexpr (U4) {
         // metric: R qz^2, g = sum P = n qz (px, py, zb), s = n
         const T q2 = qz * qz, gn = nf * qz;

@@ -555,15 +555,19 @@ sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const floa
     const int first = std::min(per, n_frames);
     sf_status s = ensure_planes(c, first);
     if (s != SF_OK) return s;
-    const size_t need = sizeof(float) * 12 * fe * (size_t)first;
+    // 12 adjoint planes per frame, then the per-frame bounds of their terms
+    const size_t planes_bytes = sizeof(float) * 12 * fe * (size_t)first;
+    const size_t need = planes_bytes + sizeof(float) * 3 * 64;
     if (c->adj_bytes < need) {
         if (c->adj) cudaFree(c->adj);
         c->adj = nullptr;
+        c->adj_max = nullptr;
         c->adj_bytes = 0;
         cudaError_t e = cudaMalloc(&c->adj, need);
         if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "adjoint scratch of %zu bytes failed", need);
         c->adj_bytes = need;
     }
+    c->adj_max = reinterpret_cast<float*>(reinterpret_cast<char*>(c->adj) + c->adj_bytes - sizeof(float) * 3 * 64);
     for (int f0 = 0; f0 < n_frames; f0 += per) {
         const int nfr = std::min(per, n_frames - f0);
         const void* dp = static_cast<const char*>(depth) + dbytes * fe * f0;
