@@ -269,10 +269,15 @@ typedef struct sf_batch sf_batch;
 
 /*
  * sf_batch_create -- prepare the fit of n_frames frames of any sizes and
- * windows as one pass: a table of per-frame descriptors and of work items
- * (tiles) is uploaded once, and every pass runs one persistent launch per
- * stage (quantum, horizontal moments, vertical moments + solve) whose CTAs
- * claim items with an atomic counter.  With use_graph != 0 the pass is
+ * windows as one pass (the per-frame fit of Eq. 12-14 / Eq. 3-6 with the
+ * window sums of Section II.C): a table of per-frame descriptors and of work
+ * items is uploaded once, and every pass is ONE persistent kernel launch
+ * whose CTAs claim items with an atomic counter, in this order: the quantum
+ * chunks of every frame, its horizontal tiles, its column bands.  A tile
+ * waits for its frame's quantum, a band for its frame's tiles; each wait
+ * polls a counter at most a set number of times (sf_batch_set_wait_limit),
+ * and one that gives up records it for sf_batch_check and skips its item.
+ * With use_graph != 0 the pass (two counter resets and the launch) is
  * captured once in a CUDA graph and sf_batch_run replays it.  The device
  * buffers named in `frames` are bound for the life of the batch: refill them
  * and run again.  Method, depth type and validity rule are shared by all
@@ -283,7 +288,19 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
                           int min_valid, int require_center_valid, int use_graph, sf_batch** out);
 /* sf_batch_run -- one pass of the batch on `stream` (asynchronous). */
 sf_status sf_batch_run(sf_batch* batch, void* stream);
-/* sf_batch_info -- total pixels (plane fits) per pass and kernel launches per pass. */
+/*
+ * sf_batch_check -- waits for the last pass to finish and returns
+ * SF_ERR_TIMEOUT if one of its waits gave up (that pass's outputs are then
+ * incomplete; the batch stays usable), else SF_OK.
+ */
+sf_status sf_batch_check(sf_batch* batch);
+/*
+ * sf_batch_set_wait_limit -- polls per wait of the following passes (default
+ * 2^22, about a second; 0: every wait that has something to wait for gives
+ * up at once).  Waits for the last pass to finish first.
+ */
+sf_status sf_batch_set_wait_limit(sf_batch* batch, unsigned polls);
+/* sf_batch_info -- total pixels (plane fits) per pass and kernel launches per pass (1). */
 sf_status sf_batch_info(const sf_batch* batch, long long* pixels, int* launches);
 /* sf_batch_destroy -- free the batch (NULL is a no-op). */
 sf_status sf_batch_destroy(sf_batch* batch);

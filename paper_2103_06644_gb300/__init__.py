@@ -316,6 +316,14 @@ class SurfaceFitBatch:
     def run(self, stream=None) -> None:
         _native.check(_native.lib().sf_batch_run(self._h, _stream_handle(stream)))
 
+    def check(self) -> None:
+        """Wait for the last pass; raise SurfFitError (SF_ERR_TIMEOUT) if one of its waits gave up."""
+        _native.check(_native.lib().sf_batch_check(self._h))
+
+    def set_wait_limit(self, polls: int) -> None:
+        """Polls per wait of the following passes (0: every wait that has something to wait for gives up)."""
+        _native.check(_native.lib().sf_batch_set_wait_limit(self._h, int(polls)))
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             _native.lib().sf_batch_destroy(self._h)

@@ -70,6 +70,8 @@ SIGNATURES = {
     "sf_channel_counts": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "sf_version": (ctypes.c_char_p, []),
     "sf_eval_acos": (_I, [_VP, _VP, _I, _VP]),
+    "sf_batch_check": (_I, [_VP]),
+    "sf_batch_set_wait_limit": (_I, [_VP, ctypes.c_uint]),
     "sf_profile_enable": (_I, [_VP, _I]),
     "sf_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)]),
     "sf_fit_static": (_I, [ctypes.POINTER(Intrinsics), _I, _I, _I, _I, _I, _F, _I, _I, _VP, _VP, _VP, _VP, _VP]),

@@ -81,16 +81,15 @@ struct sf_batch {
     float depth_scale = 1e-3f;
     int min_valid = 3, require_center = 1;
     sf::FrameDesc* d_desc = nullptr;
-    int3* d_hitems = nullptr;
-    int3* d_vitems = nullptr;
-    int n_h = 0, n_v = 0;
-    unsigned* d_counters = nullptr;  // [2]
-    unsigned* d_vmax = nullptr;      // [n]
+    int3* d_items = nullptr;         // quantum chunks, horizontal tiles, column bands
+    int n_r = 0, n_h = 0, n_v = 0;
+    unsigned* d_sync = nullptr;      // claim, error word, poll limit, then per frame [3][n]
     float* d_rays = nullptr;
     void* d_planes = nullptr;
     size_t stride = 0;
     size_t hsmem = 0;
-    int grid_h = 0, grid_v = 0;
+    int grid = 0;
+    cudaEvent_t done = nullptr;      // recorded after each run
     long long pixels = 0;
     bool use_graph = false;
     cudaStream_t cap = nullptr;

@@ -544,13 +544,23 @@ struct Calib {
     float a, b;       // 1/fx, 1/fy
 };
 
+// Load of a horizontal-moment plane entry: through the read-only cache, or
+// (kCoh) coherently from L2, for a kernel that also writes the planes (the
+// merged batch kernel, whose column items read what its tile items wrote).
+template <bool kCoh, typename T>
+__device__ __forceinline__ T load_plane(const T* p) {
+    if constexpr (kCoh) return __ldcg(p);
+    else return __ldg(p);
+}
+
 // Vertical running sums of the disparity form's moments for one column.
-struct DispState {
+template <bool kCoh = false>
+struct DispStateT {
     const int32_t* hm; const int32_t* g0; const int32_t* g1; const int64_t* q0;
     // mask moments: exact small integers, kept in float32 (all < 2^24)
     float n = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;
     int64_t Sw = 0, Swj = 0, Swi = 0, Sww = 0;
-    __device__ DispState(const Planes& P) : hm(P.p32), g0(P.c32(1)), g1(P.c32(2)), q0(P.c64(0)) {}
+    __device__ DispStateT(const Planes& P) : hm(P.p32), g0(P.c32(1)), g1(P.c32(2)), q0(P.c64(0)) {}
     // window of output row y0 from rows y0 - r .. y0 + r (clipped to the
     // image), in batches of kInitRows rows whose loads are all issued before
     // any is used; rows past the end of a batch read as empty
@@ -565,7 +575,8 @@ struct DispState {
                 hv[u] = kEmptyMask; av[u] = 0; bv[u] = 0; qv[u] = 0;
                 if (yb + u <= yhi) {
                     const size_t o = pb + (size_t)(yb + u) * rs;
-                    hv[u] = __ldg(hm + o); av[u] = __ldg(g0 + o); bv[u] = __ldg(g1 + o); qv[u] = __ldg(q0 + o);
+                    hv[u] = load_plane<kCoh>(hm + o); av[u] = load_plane<kCoh>(g0 + o);
+                    bv[u] = load_plane<kCoh>(g1 + o); qv[u] = load_plane<kCoh>(q0 + o);
                 }
             }
 #pragma unroll
@@ -594,11 +605,13 @@ struct DispState {
         R = Rows();
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * rs;
-            R.m_o = __ldg(hm + o); R.w_o = __ldg(g0 + o); R.wj_o = __ldg(g1 + o); R.ww_o = __ldg(q0 + o);
+            R.m_o = load_plane<kCoh>(hm + o); R.w_o = load_plane<kCoh>(g0 + o);
+            R.wj_o = load_plane<kCoh>(g1 + o); R.ww_o = load_plane<kCoh>(q0 + o);
         }
         if (yi < H) {
             const size_t o = pb + (size_t)yi * rs;
-            R.m_i = __ldg(hm + o); R.w_i = __ldg(g0 + o); R.wj_i = __ldg(g1 + o); R.ww_i = __ldg(q0 + o);
+            R.m_i = load_plane<kCoh>(hm + o); R.w_i = load_plane<kCoh>(g0 + o);
+            R.wj_i = load_plane<kCoh>(g1 + o); R.ww_i = load_plane<kCoh>(q0 + o);
         }
     }
     __device__ __forceinline__ void apply_rows(const Rows& R, int r) {
@@ -622,11 +635,12 @@ struct DispState {
     }
     __device__ __forceinline__ int count() const { return (int)n; }
 };
+using DispState = DispStateT<false>;
 
 // Vertical running sums of the standard form's moments for one column.  With
 // kMask the image moments of the valid pixels (sum j, j^2, i, ji, i^2) are
 // kept too: the explicit standard fit needs them for its rank test.
-template <bool kMask = false>
+template <bool kMask = false, bool kCoh = false>
 struct StdStateT {
     const int32_t* hc; const int64_t* z0; const int64_t* z1; const int64_t* b0; const int64_t* b1; const int64_t* b2;
     int n = 0;
@@ -646,8 +660,8 @@ struct StdStateT {
                 hv[u] = kEmptyMask; zv[u] = zjv[u] = q0v[u] = q1v[u] = q2v[u] = 0;
                 if (yb + u <= yhi) {
                     const size_t o = pb + (size_t)(yb + u) * rs;
-                    hv[u] = __ldg(hc + o); zv[u] = __ldg(z0 + o); zjv[u] = __ldg(z1 + o);
-                    q0v[u] = __ldg(b0 + o); q1v[u] = __ldg(b1 + o); q2v[u] = __ldg(b2 + o);
+                    hv[u] = load_plane<kCoh>(hc + o); zv[u] = load_plane<kCoh>(z0 + o); zjv[u] = load_plane<kCoh>(z1 + o);
+                    q0v[u] = load_plane<kCoh>(b0 + o); q1v[u] = load_plane<kCoh>(b1 + o); q2v[u] = load_plane<kCoh>(b2 + o);
                 }
             }
 #pragma unroll
@@ -679,13 +693,13 @@ struct StdStateT {
         R = Rows();
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * rs;
-            R.m_o = __ldg(hc + o); R.zo = __ldg(z0 + o); R.zjo = __ldg(z1 + o);
-            R.qo0 = __ldg(b0 + o); R.qo1 = __ldg(b1 + o); R.qo2 = __ldg(b2 + o);
+            R.m_o = load_plane<kCoh>(hc + o); R.zo = load_plane<kCoh>(z0 + o); R.zjo = load_plane<kCoh>(z1 + o);
+            R.qo0 = load_plane<kCoh>(b0 + o); R.qo1 = load_plane<kCoh>(b1 + o); R.qo2 = load_plane<kCoh>(b2 + o);
         }
         if (yi < H) {
             const size_t o = pb + (size_t)yi * rs;
-            R.m_i = __ldg(hc + o); R.zi = __ldg(z0 + o); R.zji = __ldg(z1 + o);
-            R.qi0 = __ldg(b0 + o); R.qi1 = __ldg(b1 + o); R.qi2 = __ldg(b2 + o);
+            R.m_i = load_plane<kCoh>(hc + o); R.zi = load_plane<kCoh>(z0 + o); R.zji = load_plane<kCoh>(z1 + o);
+            R.qi0 = load_plane<kCoh>(b0 + o); R.qi1 = load_plane<kCoh>(b1 + o); R.qi2 = load_plane<kCoh>(b2 + o);
         }
     }
     __device__ __forceinline__ void apply_rows(const Rows& R, int r) {
@@ -719,7 +733,7 @@ using StdState = StdStateT<false>;
 // Not inlined: the single-context and the batch kernels then run the same
 // machine code, so their results agree bit for bit (inlined copies may be
 // contracted into FMAs differently); one call covers a whole band.
-template <int DT, int M, bool U4 = false, bool kGuard = false>
+template <int DT, int M, bool U4 = false, bool kGuard = false, bool kCoh = false>
 __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, Codec scale, float q,
                                              const Planes P, size_t pofs, int x, int y0, int band,
                                              const float* __restrict__ txt, const float* __restrict__ tyt, float a,
@@ -733,8 +747,8 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
     const float tx = txt[x];
     constexpr int B = base_method(M);
     const float wfrac = DT == SF_DEPTH_DISPARITY_U16 ? scale.frac : 0.f;  // disparity input offset
-    typename std::conditional<B == SF_METHOD_DISPARITY, DispState,
-                              StdStateT<M == SF_METHOD_EXPLICIT_STANDARD>>::type S(P);
+    typename std::conditional<B == SF_METHOD_DISPARITY, DispStateT<kCoh>,
+                              StdStateT<M == SF_METHOD_EXPLICIT_STANDARD, kCoh>>::type S(P);
     S.init(pb, kGroup, H, y0, r);
     // row pointers, advanced by one image row per output row
     size_t oi = (size_t)y0 * W + x;
@@ -847,9 +861,16 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* 
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-resolution batches: persistent kernels over a table of work items.
-// Each frame has its own size, window, intrinsics and tile shape; every CTA
-// claims the next item with one atomicAdd and never waits on another CTA.
+// Mixed-resolution batches: one persistent kernel over a table of work items.
+// Each frame has its own size, window, intrinsics and tile shape.  The items
+// are, in claim order, the quantum chunks of every frame, then its horizontal
+// tiles, then its column bands; a CTA claims the next item with one atomicAdd.
+// A tile waits until every quantum chunk of its frame is done, a band until
+// every tile of its frame is: each wait is for items claimed earlier, which
+// CTAs that are running hold, so the kernel cannot deadlock.  Every wait is
+// bounded (a number of polls read from device memory); one that gives up sets
+// the batch's error word and skips its item, so that the kernel still ends
+// and the host reports SF_ERR_TIMEOUT.
 // ---------------------------------------------------------------------------
 struct FrameDesc {
     const void* depth;
@@ -860,30 +881,32 @@ struct FrameDesc {
     const float* ty;   // [H]
     float a, b;        // 1/fx, 1/fy
     int W, H, r, bits, Wp, seg, band;
+    int nr, nh;        // quantum chunks and horizontal tiles of the frame
     size_t pofs;       // offset of the frame in every moment plane
 };
 
-template <int DT, int M>
-__global__ void __launch_bounds__(256) range_batch_kernel(const FrameDesc* __restrict__ descs,
-                                                          unsigned* __restrict__ vmax_bits) {
-    const int f = blockIdx.y;
-    const FrameDesc& d = descs[f];
-    const size_t fe = (size_t)d.W * d.H;
-    float vmax = 0.f;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < fe; i += (size_t)gridDim.x * blockDim.x) {
-        const float z = load_raw<DT>(d.depth, i);
-        if (depth_valid(z)) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z));
-    }
-    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    __shared__ float red[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = vmax;
-    __syncthreads();
-    if (warp == 0) {
-        vmax = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.f;
-        for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        if (lane == 0 && vmax > 0.f) atomicMax(vmax_bits + f, __float_as_uint(vmax));
-    }
+// Elements of a frame per quantum chunk.
+constexpr int kRangeChunk = 16384;
+
+// The batch's synchronisation words: [0] claim counter, [1] error word (bit 0:
+// a tile gave up waiting for its frame's quantum, bit 1: a band gave up
+// waiting for its frame's tiles), [2] polls per wait, then per frame the
+// quantum bits, the finished quantum chunks and the finished tiles.
+struct BatchSync {
+    unsigned* w;
+    int n;
+    __device__ __forceinline__ unsigned* claim() const { return w; }
+    __device__ __forceinline__ unsigned* error() const { return w + 1; }
+    __device__ __forceinline__ unsigned limit() const { return __ldcg(w + 2); }
+    __device__ __forceinline__ unsigned* vmax(int f) const { return w + 3 + f; }
+    __device__ __forceinline__ unsigned* done_range(int f) const { return w + 3 + n + f; }
+    __device__ __forceinline__ unsigned* done_tiles(int f) const { return w + 3 + 2 * n + f; }
+};
+
+__device__ __forceinline__ unsigned load_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
 // Claim the next work item for the whole CTA (one atomicAdd).
@@ -894,49 +917,101 @@ __device__ __forceinline__ int claim_item(unsigned* counter, int* slot) {
     return *slot;
 }
 
+// CTA-wide wait until *ctr >= target, polled by thread 0 at most `limit`
+// times (none needed for target 0; a limit of 0 gives up at once otherwise);
+// false when it gave up.  Acquire: what the counted items wrote is visible
+// to the whole CTA afterwards.
+__device__ __forceinline__ bool cta_wait(const unsigned* ctr, unsigned target, unsigned limit, int* flag) {
+    if (threadIdx.x == 0) {
+        bool ok = target == 0;
+        for (unsigned i = 0; !ok && i < limit; ++i) {
+            ok = load_acquire(ctr) >= target;
+            if (!ok) __nanosleep(256);
+        }
+        *flag = ok;
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+// Count a finished item (release: the CTA's writes become visible first).
+__device__ __forceinline__ void cta_signal(unsigned* ctr) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+    }
+}
+
 template <int DT, int M>
-__global__ void __launch_bounds__(kHThreads) hpass_batch_kernel(const FrameDesc* __restrict__ descs,
-                                                                const int3* __restrict__ items, int n_items,
-                                                                unsigned* __restrict__ counter,
-                                                                const unsigned* __restrict__ vmax_bits,
-                                                                void* planes_base, size_t stride, Codec scale) {
-    extern __shared__ int tile[];
-    __shared__ int slot;
-    const Planes P(planes_base, stride, planes32<M>());
-    for (;;) {
-        const int it = claim_item(counter, &slot);
-        if (it >= n_items) break;
-        const int3 w = items[it];
-        const FrameDesc& d = descs[w.x];
-        const float sc = ldexpf(1.f, quant_exponent(vmax_bits[w.x], d.bits));
-        if (d.seg <= 32) hpass_tile<DT, M, 1>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, tile);
-        else if (d.seg <= 64) hpass_tile<DT, M, 2>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, tile);
-        else hpass_tile<DT, M, 4>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, tile);
+__device__ __forceinline__ void range_chunk(const FrameDesc& d, int chunk, unsigned* vmax_bits, float* red) {
+    const size_t fe = (size_t)d.W * d.H;
+    const size_t i0 = (size_t)chunk * kRangeChunk, i1 = min(fe, i0 + kRangeChunk);
+    float vmax = 0.f;
+    for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const float z = load_raw<DT>(d.depth, i);
+        if (depth_valid(z)) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z));
+    }
+    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = vmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) vmax = fmaxf(vmax, red[k]);
+        if (vmax > 0.f) atomicMax(vmax_bits, __float_as_uint(vmax));
     }
 }
 
 // One block fewer per SM than vpass_kernel: the claim loop's state stays live
 // across the column calls, and at 80 registers the calls would spill.
 template <int DT, int M>
-__global__ void __launch_bounds__(kVThreads, kVBlocks - 1) vpass_batch_kernel(const FrameDesc* __restrict__ descs,
-                                                                const int3* __restrict__ items, int n_items,
-                                                                unsigned* __restrict__ counter,
-                                                                const unsigned* __restrict__ vmax_bits,
-                                                                void* planes_base, size_t stride, Codec scale,
-                                                                int min_valid, int require_center) {
-    __shared__ int slot;
+__global__ void __launch_bounds__(kVThreads, kVBlocks - 1) batch_kernel(const FrameDesc* __restrict__ descs,
+                                                                        const int3* __restrict__ items, int n_r,
+                                                                        int n_h, int n_v, BatchSync sync,
+                                                                        void* planes_base, size_t stride,
+                                                                        Codec scale, int min_valid,
+                                                                        int require_center) {
+    static_assert(kHThreads == kVThreads, "one block shape for every item");
+    extern __shared__ int tile[];
+    __shared__ int slot, ok;
+    __shared__ float red[kVThreads / 32];
     const Planes P(planes_base, stride, planes32<M>());
+    const unsigned limit = sync.limit();
     for (;;) {
-        const int it = claim_item(counter, &slot);
-        if (it >= n_items) break;
+        const int it = claim_item(sync.claim(), &slot);
+        if (it >= n_r + n_h + n_v) break;
         const int3 w = items[it];
         const FrameDesc& d = descs[w.x];
-        const int x = w.y + threadIdx.x;
-        if (x < d.W) {
-            const float q = quantum<DT, M>(vmax_bits[w.x], d.bits, scale);
-            vpass_column<DT, M>(d.depth, d.W, d.H, d.r, scale, q, P, d.pofs, x, w.z, d.band, d.tx, d.ty, d.a,
-                                d.b, min_valid, require_center, d.normals, d.offsets, d.curvature, nullptr,
-                                INFINITY, nullptr, nullptr, w.x, nullptr, 0u);
+        if (it < n_r) {
+            range_chunk<DT, M>(d, w.y, sync.vmax(w.x), red);
+            cta_signal(sync.done_range(w.x));
+        } else if (it < n_r + n_h) {
+            if (!cta_wait(sync.done_range(w.x), (unsigned)d.nr, limit, &ok)) {
+                if (threadIdx.x == 0) atomicOr(sync.error(), 1u);
+                continue;
+            }
+            const float sc = ldexpf(1.f, quant_exponent(__ldcg(sync.vmax(w.x)), d.bits));
+            // the standard form's wider tiles (several int64 running states per
+            // thread) would spill under this kernel's register budget: its frames
+            // are tiled 32 columns wide (tiling never changes the exact sums)
+            if (base_method(M) == SF_METHOD_STANDARD || d.seg <= 32)
+                hpass_tile<DT, M, 1>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, tile);
+            else if (d.seg <= 64) hpass_tile<DT, M, 2>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, tile);
+            else hpass_tile<DT, M, 4>(d.depth, d.W, d.H, d.r, sc, scale, P, d.pofs, w.y, w.z, tile);
+            cta_signal(sync.done_tiles(w.x));
+        } else {
+            if (!cta_wait(sync.done_tiles(w.x), (unsigned)d.nh, limit, &ok)) {
+                if (threadIdx.x == 0) atomicOr(sync.error(), 2u);
+                continue;
+            }
+            const int x = w.y + threadIdx.x;
+            if (x < d.W) {
+                const float q = quantum<DT, M>(__ldcg(sync.vmax(w.x)), d.bits, scale);
+                vpass_column<DT, M, false, false, true>(d.depth, d.W, d.H, d.r, scale, q, P, d.pofs, x, w.z, d.band,
+                                                        d.tx, d.ty, d.a, d.b, min_valid, require_center, d.normals,
+                                                        d.offsets, d.curvature, nullptr, INFINITY, nullptr, nullptr,
+                                                        w.x, nullptr, 0u);
+            }
         }
     }
 }

@@ -344,18 +344,14 @@ sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const float* gn
 
 template <int DT, int M>
 sf_status batch_enqueue_t(sf_batch* b, cudaStream_t st) {
-    SF_CUDA(cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(unsigned), st));
-    SF_CUDA(cudaMemsetAsync(b->d_vmax, 0, sizeof(unsigned) * b->n, st));
-    if (!(DT == SF_DEPTH_U16 && M == SF_METHOD_STANDARD))
-        sf::range_batch_kernel<DT, M><<<dim3(16, b->n), 256, 0, st>>>(b->d_desc, b->d_vmax);
+    // claim counter and error word, then the per-frame quantum bits and counters
+    // (the poll limit in between is kept)
+    SF_CUDA(cudaMemsetAsync(b->d_sync, 0, 2 * sizeof(unsigned), st));
+    SF_CUDA(cudaMemsetAsync(b->d_sync + 3, 0, 3 * sizeof(unsigned) * b->n, st));
     const sf::Codec cd{b->depth_scale, 0, 0};
-    sf::hpass_batch_kernel<DT, M><<<b->grid_h, sf::kHThreads, b->hsmem, st>>>(b->d_desc, b->d_hitems, b->n_h,
-                                                                              b->d_counters, b->d_vmax, b->d_planes,
-                                                                              b->stride, cd);
-    sf::vpass_batch_kernel<DT, M><<<b->grid_v, sf::kVThreads, 0, st>>>(b->d_desc, b->d_vitems, b->n_v,
-                                                                        b->d_counters + 1, b->d_vmax, b->d_planes,
-                                                                        b->stride, cd, b->min_valid,
-                                                                        b->require_center);
+    sf::batch_kernel<DT, M><<<b->grid, sf::kVThreads, b->hsmem, st>>>(
+        b->d_desc, b->d_items, b->n_r, b->n_h, b->n_v, sf::BatchSync{b->d_sync, b->n}, b->d_planes, b->stride, cd,
+        b->min_valid, b->require_center);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
     return SF_OK;
@@ -364,12 +360,9 @@ sf_status batch_enqueue_t(sf_batch* b, cudaStream_t st) {
 template <int DT, int M>
 void batch_grids_t(sf_batch* b, int sms) {
     int nb = 0;
-    cudaFuncSetAttribute(sf::hpass_batch_kernel<DT, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->hsmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sf::hpass_batch_kernel<DT, M>, sf::kHThreads, b->hsmem);
-    b->grid_h = std::max(1, nb) * sms;
-    nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sf::vpass_batch_kernel<DT, M>, sf::kVThreads, 0);
-    b->grid_v = std::max(1, nb) * sms;
+    cudaFuncSetAttribute(sf::batch_kernel<DT, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->hsmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sf::batch_kernel<DT, M>, sf::kVThreads, b->hsmem);
+    b->grid = std::max(1, nb) * sms;
 }
 
 // Opt the kernels that take large dynamic shared memory in to their maximum.

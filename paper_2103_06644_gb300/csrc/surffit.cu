@@ -117,6 +117,9 @@ static sf_status ensure_planes(sf_ctx* c, int frames) {
     return SF_OK;
 }
 
+// Polls per wait of the merged batch kernel (about a second at its sleep between polls).
+static constexpr unsigned kBatchWaitPolls = 1u << 22;
+
 static bool misaligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) != 0; }
 
 extern "C" {
@@ -673,10 +676,9 @@ sf_status sf_batch_destroy(sf_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
     cudaFree(b->d_desc);
-    cudaFree(b->d_hitems);
-    cudaFree(b->d_vitems);
-    cudaFree(b->d_counters);
-    cudaFree(b->d_vmax);
+    cudaFree(b->d_items);
+    cudaFree(b->d_sync);
+    if (b->done) cudaEventDestroy(b->done);
     cudaFree(b->d_rays);
     cudaFree(b->d_planes);
     delete b;
@@ -715,8 +717,9 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
         if (!(K.fx != 0.0) || !(K.fy != 0.0) || !std::isfinite(K.fx) || !std::isfinite(K.fy) ||
             !std::isfinite(K.cx) || !std::isfinite(K.cy) || !std::isfinite(K.dx) || !std::isfinite(K.dy))
             return fail(SF_ERR_INVALID_ARG, "frame %d: intrinsics must be finite with nonzero focal lengths", f);
-        const int seg = F.hseg ? F.hseg : sf::kHSeg;
+        int seg = F.hseg ? F.hseg : sf::kHSeg;
         if (seg != 32 && seg != 64 && seg != 128) return fail(SF_ERR_INVALID_ARG, "frame %d: hseg must be 32, 64 or 128", f);
+        if (method == SF_METHOD_STANDARD) seg = 32;  // the batch kernel's tiles of the standard form
         const int band = F.vband ? F.vband : 64;
         if (band < 8 || band > 1024) return fail(SF_ERR_INVALID_ARG, "frame %d: vband must be in [8, 1024]", f);
         sf::FrameDesc& d = desc[f];
@@ -752,16 +755,26 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         return (long long)desc[a].W * desc[a].H > (long long)desc[c].W * desc[c].H;
     });
-    std::vector<int3> hitems, vitems;
+    // in claim order: every frame's quantum chunks, then its tiles, then its bands
+    const bool fixed_q = depth_type == SF_DEPTH_U16 && method == SF_METHOD_STANDARD;  // raw depth, no quantum
+    std::vector<int3> ritems, hitems, vitems;
     for (int f : order) {
-        const sf::FrameDesc& d = desc[f];
+        sf::FrameDesc& d = desc[f];
+        const size_t fe = (size_t)d.W * d.H;
+        d.nr = fixed_q ? 0 : (int)((fe + sf::kRangeChunk - 1) / sf::kRangeChunk);
+        for (int c = 0; c < d.nr; ++c) ritems.push_back(make_int3(f, c, 0));
+        d.nh = 0;
         for (int y0 = 0; y0 < d.H; y0 += sf::kHThreads)
-            for (int x0 = 0; x0 < d.W; x0 += d.seg) hitems.push_back(make_int3(f, x0, y0));
+            for (int x0 = 0; x0 < d.W; x0 += d.seg) { hitems.push_back(make_int3(f, x0, y0)); ++d.nh; }
         for (int y0 = 0; y0 < d.H; y0 += d.band)
             for (int x0 = 0; x0 < d.W; x0 += sf::kVThreads) vitems.push_back(make_int3(f, x0, y0));
     }
+    b->n_r = (int)ritems.size();
     b->n_h = (int)hitems.size();
     b->n_v = (int)vitems.size();
+    std::vector<int3> items(ritems);
+    items.insert(items.end(), hitems.begin(), hitems.end());
+    items.insert(items.end(), vitems.begin(), vitems.end());
     cudaError_t e = cudaMalloc(&b->d_rays, sizeof(float) * std::max<size_t>(rays, 1));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_rays, hr.data(), sizeof(float) * rays, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
@@ -772,12 +785,15 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
         e = cudaMalloc(&b->d_desc, sizeof(sf::FrameDesc) * n_frames);
     }
     if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, desc.data(), sizeof(sf::FrameDesc) * n_frames, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_hitems, sizeof(int3) * hitems.size());
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_hitems, hitems.data(), sizeof(int3) * hitems.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_vitems, sizeof(int3) * vitems.size());
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_vitems, vitems.data(), sizeof(int3) * vitems.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_vmax, sizeof(unsigned) * n_frames);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int3) * items.size());
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(int3) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sync, sizeof(unsigned) * (3 + 3 * (size_t)n_frames));
+    if (e == cudaSuccess) e = cudaMemset(b->d_sync, 0, sizeof(unsigned) * (3 + 3 * (size_t)n_frames));
+    if (e == cudaSuccess) {
+        const unsigned limit = kBatchWaitPolls;
+        e = cudaMemcpy(b->d_sync + 2, &limit, sizeof(unsigned), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_planes, sfh::plane_bytes_per_frame(method, stride));
     if (e != cudaSuccess) { sf_batch_destroy(b); return fail(SF_ERR_ALLOC, "batch buffers: %s", cudaGetErrorString(e)); }
     b->hsmem = sizeof(int) * sf::kHThreads * (size_t)((max_seg + 2 * max_r) | 1);
@@ -815,15 +831,36 @@ sf_status sf_batch_run(sf_batch* b, void* stream) {
     if (b->use_graph) {
         cudaError_t e = cudaGraphLaunch(b->exec, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
-        return SF_OK;
+    } else {
+        sf_status s = batch_enqueue(b, st);
+        if (s != SF_OK) return s;
     }
-    return batch_enqueue(b, st);
+    SF_CUDA(cudaEventRecord(b->done, st));
+    return SF_OK;
+}
+
+sf_status sf_batch_check(sf_batch* b) {
+    if (!b) return fail(SF_ERR_INVALID_ARG, "null batch");
+    SF_CUDA(cudaEventSynchronize(b->done));
+    unsigned err = 0;
+    SF_CUDA(cudaMemcpy(&err, b->d_sync + 1, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err)
+        return fail(SF_ERR_TIMEOUT, "batch: a %s gave up waiting (error word 0x%x); its outputs are not written",
+                    (err & 2) ? "column band" : "horizontal tile", err);
+    return SF_OK;
+}
+
+sf_status sf_batch_set_wait_limit(sf_batch* b, unsigned polls) {
+    if (!b) return fail(SF_ERR_INVALID_ARG, "null batch");
+    SF_CUDA(cudaEventSynchronize(b->done));
+    SF_CUDA(cudaMemcpy(b->d_sync + 2, &polls, sizeof(unsigned), cudaMemcpyHostToDevice));
+    return SF_OK;
 }
 
 sf_status sf_batch_info(const sf_batch* b, long long* pixels, int* launches) {
     if (!b || !pixels || !launches) return fail(SF_ERR_INVALID_ARG, "null argument");
     *pixels = b->pixels;
-    *launches = (b->depth_type == SF_DEPTH_U16 && b->method == SF_METHOD_STANDARD) ? 2 : 3;
+    *launches = 1;
     return SF_OK;
 }
 

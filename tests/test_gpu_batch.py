@@ -1,5 +1,6 @@
-"""Mixed-resolution batches (sf_batch_*): one persistent launch per stage over
-a tile table, replayed from a CUDA graph.
+"""Mixed-resolution batches (sf_batch_*): one persistent launch per pass over a
+table of work items (quantum chunks, horizontal tiles, column bands), replayed
+from a CUDA graph.
 
 The window sums are exact integers, so a frame's results cannot depend on the
 batch it runs in, on its tile shape or on the order in which CTAs claim work:
@@ -21,7 +22,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
-from paper_2103_06644_gb300 import SurfaceFitBatch, SurfaceFitter  # noqa: E402
+from paper_2103_06644_gb300 import SurfaceFitBatch, SurfaceFitter, SurfFitError  # noqa: E402
 
 SPEC = [(200, 150, 5), (97, 61, 21), (320, 240, 7), (640, 480, 11), (320, 240, 21), (160, 120, 5), (640, 480, 5),
         (131, 257, 7)]
@@ -114,3 +115,33 @@ def test_autotuner_returns_valid_shapes(tmp_path):
     assert os.path.exists(str(tmp_path / "tiles.json"))
     again = autotune.tune(frames)  # from the cache
     assert [(t["hseg"], t["vband"]) for t in again] == [(t["hseg"], t["vband"]) for t in tuned]
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_one_launch_and_bounded_waits(use_graph):
+    """One kernel launch per pass.  With a poll limit of 0 every tile and band that has something to wait
+    for gives up at once: the pass ends, sf_batch_check reports SF_ERR_TIMEOUT, and with the limit restored
+    the same batch runs again and matches the single-frame fits bit for bit."""
+    frames = [{k: v for k, v in f.items() if k not in ("np_depth", "intr")} for f in _frames(980)]
+    b = SurfaceFitBatch(frames, use_graph=use_graph)
+    assert b.launches == 1
+    b.run()
+    b.check()
+    b.set_wait_limit(0)
+    for o in b.outputs:
+        o[1].fill_(123.0)
+    b.run()
+    with pytest.raises(SurfFitError) as exc:
+        b.check()
+    assert exc.value.status == 5  # SF_ERR_TIMEOUT
+    assert any(bool((o[1] == 123.0).any()) for o in b.outputs)  # skipped bands left their outputs unwritten
+    b.set_wait_limit(1 << 22)
+    b.run()
+    b.check()
+    torch.cuda.synchronize()
+    for f, out in zip(frames, b.outputs):
+        s = SurfaceFitter(f["intrinsics"], f["W"], f["H"], f["window"])
+        for x, y in zip(out, s.fit(f["depth"])):
+            assert _same(x, y)
+        s.close()
+    b.close()
