@@ -331,8 +331,8 @@ sf_status sf_set_delta_table(sf_ctx* ctx, const float* ddx, const float* ddy);
 /*
  * sf_set_tiles -- tile shape of a context: hseg in {32, 64, 128} columns per
  * horizontal tile (default 32), vband rows per vertical band (0 = chosen
- * from the grid size, else 8..1024).  Results do not depend on the tiles: the window sums
- * are exact.
+ * from the grid size, else 2..1024).  Results do not depend on the tiles:
+ * the window sums are exact.
  */
 sf_status sf_set_tiles(sf_ctx* ctx, int hseg, int vband);
 

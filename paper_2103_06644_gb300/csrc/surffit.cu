@@ -114,6 +114,7 @@ static sf_status ensure_planes(sf_ctx* c, int frames) {
                                       cudaGetErrorString(e));
     c->planes_bytes = need;
     c->planes_frames = frames;
+    ++c->gen;
     return SF_OK;
 }
 
@@ -229,6 +230,7 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
 sf_status sf_set_params(sf_ctx* c, int method, int depth_type, float depth_scale, int min_valid,
                         int require_center_valid) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    ++c->gen;  // a captured fit graph no longer applies
     if (method < SF_METHOD_DISPARITY || method > SF_METHOD_EXPLICIT_STANDARD)
         return fail(SF_ERR_INVALID_ARG, "unknown method %d", method);
     if (depth_type != SF_DEPTH_F32 && depth_type != SF_DEPTH_U16 && depth_type != SF_DEPTH_DISPARITY_U16)
@@ -243,6 +245,42 @@ sf_status sf_set_params(sf_ctx* c, int method, int depth_type, float depth_scale
     c->require_center = require_center_valid ? 1 : 0;
     return SF_OK;
 }
+
+}  // extern "C"
+
+// Capture one single-pass fit into the context's graph (updated in place when
+// one exists and has the same shape).  On failure the direct path runs.
+static sf_status capture_fit(sf_ctx* c, const sf_ctx::FitKey& key, int n, const void* depth, float* normals,
+                             float* offsets, float* curvature, int32_t* counts) {
+    if (!c->graph_stream) SF_CUDA(cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+    SF_CUDA(cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeThreadLocal));
+    const sf_status s = fit_pass(c, n, depth, normals, offsets, curvature, counts, c->graph_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->graph_stream, &g);
+    if (s != SF_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return s != SF_OK ? s : cuda_fail(e == cudaSuccess ? cudaErrorUnknown : e, "fit graph capture");
+    }
+    if (c->graph_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->graph_exec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+    }
+    if (!c->graph_exec) e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph_exec = nullptr;
+        return cuda_fail(e, "fit graph instantiate");
+    }
+    c->graph_key = key;
+    return SF_OK;
+}
+
+extern "C" {
 
 sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
                     int32_t* counts, void* stream) {
@@ -281,6 +319,7 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
             if (e == cudaSuccess) e = cudaMalloc(&c->queue_c, cap * sizeof(unsigned));
             if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "precision-fallback queue of %zu entries failed", cap);
             c->flags_cap = cap;
+            ++c->gen;
         }
         // the exact moments of queued windows: every window in mode 2, a quarter of
         // them in mode 1 (windows queued beyond that re-read their moments from
@@ -295,6 +334,20 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
             if (e != cudaSuccess)
                 return fail(SF_ERR_ALLOC, "precision-fallback moments of %zu entries failed", mcap);
             c->moments_cap = mcap;
+            ++c->gen;
+        }
+    }
+    if (n_frames <= per && !c->profiling) {
+        const sf_ctx::FitKey key{c->gen, n_frames, depth, normals, offsets, curvature, counts};
+        if (c->graph_exec && key == c->graph_key) {
+            SF_CUDA(cudaGraphLaunch(c->graph_exec, st));
+            return SF_OK;
+        }
+        const bool again = key == c->last_key;
+        c->last_key = key;
+        if (again && capture_fit(c, key, n_frames, depth, normals, offsets, curvature, counts) == SF_OK) {
+            SF_CUDA(cudaGraphLaunch(c->graph_exec, st));
+            return SF_OK;
         }
     }
     for (int f0 = 0; f0 < n_frames; f0 += per) {
@@ -456,6 +509,7 @@ sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_
 
 sf_status sf_set_delta_table(sf_ctx* c, const float* ddx, const float* ddy) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    ++c->gen;  // a captured fit graph no longer applies
     if (!ddx != !ddy) return fail(SF_ERR_INVALID_ARG, "give both tables or neither");
     // fits already queued on the context's device may still read the old table
     {
@@ -494,8 +548,9 @@ sf_status sf_set_delta_table(sf_ctx* c, const float* ddx, const float* ddy) {
 
 sf_status sf_set_tiles(sf_ctx* c, int hseg, int vband) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    ++c->gen;  // a captured fit graph no longer applies
     if (hseg != 32 && hseg != 64 && hseg != 128) return fail(SF_ERR_INVALID_ARG, "hseg must be 32, 64 or 128");
-    if (vband != 0 && (vband < 8 || vband > 1024)) return fail(SF_ERR_INVALID_ARG, "vband must be 0 or in [8, 1024]");
+    if (vband != 0 && (vband < 2 || vband > 1024)) return fail(SF_ERR_INVALID_ARG, "vband must be 0 or in [2, 1024]");
     c->hseg = hseg;
     c->vband = vband;
     return SF_OK;
@@ -503,6 +558,7 @@ sf_status sf_set_tiles(sf_ctx* c, int hseg, int vband) {
 
 sf_status sf_set_precision(sf_ctx* c, int mode, float tau) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    ++c->gen;  // a captured fit graph no longer applies
     if (mode < 0 || mode > 2) return fail(SF_ERR_INVALID_ARG, "precision mode %d must be 0, 1 or 2", mode);
     if (mode == 1 && !(tau > 0.f && tau <= 1.f)) return fail(SF_ERR_INVALID_ARG, "tau must be in (0, 1]");
     c->precision_mode = mode;
@@ -512,6 +568,7 @@ sf_status sf_set_precision(sf_ctx* c, int mode, float tau) {
 
 sf_status sf_set_constraint(sf_ctx* c, int constraint) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    ++c->gen;  // a captured fit graph no longer applies
     if (constraint != SF_CONSTRAINT_UNIT3 && constraint != SF_CONSTRAINT_UNIT4)
         return fail(SF_ERR_INVALID_ARG, "constraint %d must be SF_CONSTRAINT_UNIT3 or SF_CONSTRAINT_UNIT4", constraint);
     c->constraint = constraint;
@@ -520,6 +577,7 @@ sf_status sf_set_constraint(sf_ctx* c, int constraint) {
 
 sf_status sf_set_disparity_model(sf_ctx* c, double alpha, double beta) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
+    ++c->gen;  // a captured fit graph no longer applies
     if (!(alpha != 0.0) || !std::isfinite(alpha) || !std::isfinite(beta))
         return fail(SF_ERR_INVALID_ARG, "alpha must be finite and nonzero, beta finite");
     const double k = 128.0 * beta / std::fabs(alpha);
@@ -646,6 +704,8 @@ sf_status sf_destroy(sf_ctx* c) {
     if (c->flags) cudaFree(c->flags);
     if (c->moments_q) cudaFree(c->moments_q);
     if (c->queue_c) cudaFree(c->queue_c);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
     if (c->flag_count) cudaFree(c->flag_count);
     if (c->rays64) cudaFree(c->rays64);
     for (int i = 0; i < 2; ++i)
