@@ -84,11 +84,13 @@ int vertical_band(const sf_ctx* c, int nfr) {
     const size_t cols = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * sf::kVThreads * nfr;
     // at least 152 x 2048 threads (about 2.7 waves of 24 resident warps per
     // SM): short bands cost a 2r-row warm-up each, but with fewer waves the
-    // tail of the last one costs more.  Small frames go down to 4-row bands:
-    // there the serial chain of solves per thread, not the warm-up, bounds
-    // the pass (one 640 x 480 frame at k = 7: 12.8 us at 4 rows, 16.9 at 16)
+    // tail of the last one costs more.  Small frames with small windows go
+    // down to 4-row bands: there the serial chain of solves per thread, not
+    // the warm-up, bounds the pass (one 640 x 480 frame at k = 7: 12.8 us at
+    // 4 rows, 16.9 at 16); larger windows keep bands of at least r + 1 rows
+    const int min_band = std::max(4, std::min(16, c->r + 1));
     int band = 256;
-    while (band > 4 && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 64 * 32) band /= 2;
+    while (band > min_band && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 64 * 32) band /= 2;
     return band;
 }
 
