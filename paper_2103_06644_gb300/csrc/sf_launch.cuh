@@ -90,7 +90,7 @@ int vertical_band(const sf_ctx* c, int nfr) {
     // 4 rows, 16.9 at 16); larger windows keep bands of at least r + 1 rows
     const int min_band = std::max(4, std::min(16, c->r + 1));
     int band = 256;
-    while (band > min_band && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 64 * 32) band /= 2;
+    while (band / 2 >= min_band && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 64 * 32) band /= 2;
     return band;
 }
 
