@@ -452,6 +452,17 @@ sf_status sf_quadtree(sf_ctx* ctx, int n_frames, const void* depth, const sf_qua
 const char* sf_version(void);
 
 /*
+ * sf_debug_fail_allocs -- test hook for the error paths: the next `after`
+ * device allocations of the library succeed and every later one fails as if
+ * the device were out of memory (SF_ERR_ALLOC, every partial allocation
+ * freed), until called again with a negative value (the default: no limit).
+ * Process-wide; not for concurrent use with working contexts.
+ */
+sf_status sf_debug_fail_allocs(long long after);
+/* sf_debug_live_allocs -- the number of the library's device allocations not yet freed (all contexts and batches). */
+sf_status sf_debug_live_allocs(long long* n);
+
+/*
  * sf_eval_acos -- diagnostics: the float32 arccos that the per-pixel solve's
  * trigonometric eigenvalue estimate uses (the closed-form roots of the 3x3
  * characteristic polynomial behind Eq. 4-5), evaluated on the device for n

@@ -26,8 +26,23 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def _defines():
+    """Extra compile definitions: SF_CHECK_BOUNDS=1 in the environment builds the bounds-checked
+    library (every moment-plane access checked, the first bad one reported by the entry points)."""
+    return ["-DSF_CHECK_BOUNDS=1"] if os.environ.get("SF_CHECK_BOUNDS", "0") not in ("", "0") else []
+
+
+STAMP = os.path.join(BUILD, "defines.txt")
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    try:
+        with open(STAMP) as fh:
+            if fh.read() != " ".join(_defines()):
+                return True
+    except OSError:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
@@ -41,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-I" + INCLUDE, "-I" + CSRC, "-Xcompiler", "-fPIC",
-                     "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
+                     "-Xcompiler", "-O2", "--expt-relaxed-constexpr"] + _defines()
     objs = []
     cmds = []
     for src in sources():
@@ -63,6 +78,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + ".tmp%d" % os.getpid()
     subprocess.check_call([nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread", "-ldl", "-lrt"])
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(" ".join(_defines()))
     return LIB
 
 

@@ -149,7 +149,8 @@ constexpr size_t kMomentEntryBytes = 80;
                             sf_quad_node* nodes, int capacity, int32_t* n_nodes, size_t roots, cudaStream_t st);      \
     sf_status batch_enqueue_##dt(sf_batch* b, cudaStream_t st);                                                       \
     void batch_grids_##dt(sf_batch* b, int sms);                                                                      \
-    void set_kernel_smem_##dt();
+    void set_kernel_smem_##dt();                                                                                      \
+    unsigned long long bounds_word_##dt();
 SF_DECLARE_LAUNCHERS(f32)
 SF_DECLARE_LAUNCHERS(u16)
 SF_DECLARE_LAUNCHERS(disp)

@@ -283,6 +283,22 @@ __device__ __forceinline__ size_t plane_index(size_t pofs, int x, int y, int H) 
 template <int M>
 __host__ __device__ constexpr int planes32() { return base_method(M) == SF_METHOD_DISPARITY ? 3 : 1; }
 
+// Bounds-checked build (SF_CHECK_BOUNDS=1): every access of a moment plane
+// checks its index against the plane's length; one out of range is skipped
+// (a load reads 0) and the first one is recorded in this translation unit's
+// bounds word -- bit 63, the access site in bits 56-62, the index below --
+// which the library's entry points read after the work and report.
+#ifndef SF_CHECK_BOUNDS
+#define SF_CHECK_BOUNDS 0
+#endif
+static __device__ unsigned long long sf_bounds_word;
+enum BoundsSite : int { kSiteColumnLoad = 1, kSiteRowStore = 2 };
+__device__ __forceinline__ bool plane_index_ok(size_t o, size_t limit, int site) {
+    if (!SF_CHECK_BOUNDS || o < limit) return true;
+    atomicCAS(&sf_bounds_word, 0ull, (1ull << 63) | ((unsigned long long)site << 56) | (o & ((1ull << 56) - 1)));
+    return false;
+}
+
 struct Planes {
     int32_t* p32;       // first int32 plane (the packed mask); plane c is p32 + c * stride
     int64_t* p64;       // first int64 plane; plane c is p64 + c * stride
@@ -448,6 +464,7 @@ __device__ __forceinline__ void hpass_row(const int* row, int x0, int xend, int 
                 if (xs + u + 1 < xe) S.step(row, xs + u - x0, r);
             }
             const size_t o = plane_index(pofs, xs, y, H);  // xs % 4 == 0: 4 entries in one group
+            if (!plane_index_ok(o + 3, P.stride, kSiteRowStore)) continue;
             if (base_method(M) == SF_METHOD_DISPARITY) {
                 if (xs + 4 <= xe) {
                     *reinterpret_cast<int4*>(P.p32 + o) = make_int4(hmv[0], hmv[1], hmv[2], hmv[3]);
@@ -544,13 +561,15 @@ struct Calib {
     float a, b;       // 1/fx, 1/fy
 };
 
-// Load of a horizontal-moment plane entry: through the read-only cache, or
-// (kCoh) coherently from L2, for a kernel that also writes the planes (the
-// merged batch kernel, whose column items read what its tile items wrote).
+// Load of a horizontal-moment plane entry (entry o of a plane of `limit`
+// entries): through the read-only cache, or (kCoh) coherently from L2, for a
+// kernel that also writes the planes (the merged batch kernel, whose column
+// items read what its tile items wrote).
 template <bool kCoh, typename T>
-__device__ __forceinline__ T load_plane(const T* p) {
-    if constexpr (kCoh) return __ldcg(p);
-    else return __ldg(p);
+__device__ __forceinline__ T load_plane(const T* base, size_t o, size_t limit) {
+    if (!plane_index_ok(o, limit, kSiteColumnLoad)) return T(0);
+    if constexpr (kCoh) return __ldcg(base + o);
+    else return __ldg(base + o);
 }
 
 // Vertical running sums of the disparity form's moments for one column.
@@ -560,7 +579,9 @@ struct DispStateT {
     // mask moments: exact small integers, kept in float32 (all < 2^24)
     float n = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;
     int64_t Sw = 0, Swj = 0, Swi = 0, Sww = 0;
-    __device__ DispStateT(const Planes& P) : hm(P.p32), g0(P.c32(1)), g1(P.c32(2)), q0(P.c64(0)) {}
+    size_t lim;  // entries per plane
+    __device__ DispStateT(const Planes& P)
+        : hm(P.p32), g0(P.c32(1)), g1(P.c32(2)), q0(P.c64(0)), lim(P.stride) {}
     // window of output row y0 from rows y0 - r .. y0 + r (clipped to the
     // image), in batches of kInitRows rows whose loads are all issued before
     // any is used; rows past the end of a batch read as empty
@@ -575,8 +596,8 @@ struct DispStateT {
                 hv[u] = kEmptyMask; av[u] = 0; bv[u] = 0; qv[u] = 0;
                 if (yb + u <= yhi) {
                     const size_t o = pb + (size_t)(yb + u) * rs;
-                    hv[u] = load_plane<kCoh>(hm + o); av[u] = load_plane<kCoh>(g0 + o);
-                    bv[u] = load_plane<kCoh>(g1 + o); qv[u] = load_plane<kCoh>(q0 + o);
+                    hv[u] = load_plane<kCoh>(hm, o, lim); av[u] = load_plane<kCoh>(g0, o, lim);
+                    bv[u] = load_plane<kCoh>(g1, o, lim); qv[u] = load_plane<kCoh>(q0, o, lim);
                 }
             }
 #pragma unroll
@@ -605,13 +626,13 @@ struct DispStateT {
         R = Rows();
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * rs;
-            R.m_o = load_plane<kCoh>(hm + o); R.w_o = load_plane<kCoh>(g0 + o);
-            R.wj_o = load_plane<kCoh>(g1 + o); R.ww_o = load_plane<kCoh>(q0 + o);
+            R.m_o = load_plane<kCoh>(hm, o, lim); R.w_o = load_plane<kCoh>(g0, o, lim);
+            R.wj_o = load_plane<kCoh>(g1, o, lim); R.ww_o = load_plane<kCoh>(q0, o, lim);
         }
         if (yi < H) {
             const size_t o = pb + (size_t)yi * rs;
-            R.m_i = load_plane<kCoh>(hm + o); R.w_i = load_plane<kCoh>(g0 + o);
-            R.wj_i = load_plane<kCoh>(g1 + o); R.ww_i = load_plane<kCoh>(q0 + o);
+            R.m_i = load_plane<kCoh>(hm, o, lim); R.w_i = load_plane<kCoh>(g0, o, lim);
+            R.wj_i = load_plane<kCoh>(g1, o, lim); R.ww_i = load_plane<kCoh>(q0, o, lim);
         }
     }
     __device__ __forceinline__ void apply_rows(const Rows& R, int r) {
@@ -646,8 +667,9 @@ struct StdStateT {
     int n = 0;
     float fn = 0.f, Sj = 0.f, Sjj = 0.f, Si = 0.f, Sji = 0.f, Sii = 0.f;  // kMask only
     int64_t Sz = 0, Szi = 0, Szj = 0, Szz = 0, Szzi = 0, Szzii = 0, Szzj = 0, Szzji = 0, Szzjj = 0;
+    size_t lim;  // entries per plane
     __device__ StdStateT(const Planes& P)
-        : hc(P.p32), z0(P.c64(0)), z1(P.c64(1)), b0(P.c64(2)), b1(P.c64(3)), b2(P.c64(4)) {}
+        : hc(P.p32), z0(P.c64(0)), z1(P.c64(1)), b0(P.c64(2)), b1(P.c64(3)), b2(P.c64(4)), lim(P.stride) {}
     // as DispState::init, in batches of kInitRows rows
     static constexpr int kInitRows = 4;
     __device__ __forceinline__ void init(size_t pb, int rs, int H, int y0, int r) {
@@ -660,8 +682,8 @@ struct StdStateT {
                 hv[u] = kEmptyMask; zv[u] = zjv[u] = q0v[u] = q1v[u] = q2v[u] = 0;
                 if (yb + u <= yhi) {
                     const size_t o = pb + (size_t)(yb + u) * rs;
-                    hv[u] = load_plane<kCoh>(hc + o); zv[u] = load_plane<kCoh>(z0 + o); zjv[u] = load_plane<kCoh>(z1 + o);
-                    q0v[u] = load_plane<kCoh>(b0 + o); q1v[u] = load_plane<kCoh>(b1 + o); q2v[u] = load_plane<kCoh>(b2 + o);
+                    hv[u] = load_plane<kCoh>(hc, o, lim); zv[u] = load_plane<kCoh>(z0, o, lim); zjv[u] = load_plane<kCoh>(z1, o, lim);
+                    q0v[u] = load_plane<kCoh>(b0, o, lim); q1v[u] = load_plane<kCoh>(b1, o, lim); q2v[u] = load_plane<kCoh>(b2, o, lim);
                 }
             }
 #pragma unroll
@@ -693,13 +715,13 @@ struct StdStateT {
         R = Rows();
         if (yo >= 0) {
             const size_t o = pb + (size_t)yo * rs;
-            R.m_o = load_plane<kCoh>(hc + o); R.zo = load_plane<kCoh>(z0 + o); R.zjo = load_plane<kCoh>(z1 + o);
-            R.qo0 = load_plane<kCoh>(b0 + o); R.qo1 = load_plane<kCoh>(b1 + o); R.qo2 = load_plane<kCoh>(b2 + o);
+            R.m_o = load_plane<kCoh>(hc, o, lim); R.zo = load_plane<kCoh>(z0, o, lim); R.zjo = load_plane<kCoh>(z1, o, lim);
+            R.qo0 = load_plane<kCoh>(b0, o, lim); R.qo1 = load_plane<kCoh>(b1, o, lim); R.qo2 = load_plane<kCoh>(b2, o, lim);
         }
         if (yi < H) {
             const size_t o = pb + (size_t)yi * rs;
-            R.m_i = load_plane<kCoh>(hc + o); R.zi = load_plane<kCoh>(z0 + o); R.zji = load_plane<kCoh>(z1 + o);
-            R.qi0 = load_plane<kCoh>(b0 + o); R.qi1 = load_plane<kCoh>(b1 + o); R.qi2 = load_plane<kCoh>(b2 + o);
+            R.m_i = load_plane<kCoh>(hc, o, lim); R.zi = load_plane<kCoh>(z0, o, lim); R.zji = load_plane<kCoh>(z1, o, lim);
+            R.qi0 = load_plane<kCoh>(b0, o, lim); R.qi1 = load_plane<kCoh>(b1, o, lim); R.qi2 = load_plane<kCoh>(b2, o, lim);
         }
     }
     __device__ __forceinline__ void apply_rows(const Rows& R, int r) {

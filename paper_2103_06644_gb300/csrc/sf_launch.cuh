@@ -431,4 +431,13 @@ void set_kernel_smem_t() {
         }                                                                                                              \
     }                                                                                                                  \
     void set_kernel_smem_##dt() { set_kernel_smem_t<DT>(); }                                                          \
+    unsigned long long bounds_word_##dt() {                                                                            \
+        unsigned long long v = 0;                                                                                      \
+        if (cudaMemcpyFromSymbol(&v, sf::sf_bounds_word, sizeof(v)) != cudaSuccess) return 0;                          \
+        if (v) {                                                                                                       \
+            const unsigned long long z = 0;                                                                            \
+            cudaMemcpyToSymbol(sf::sf_bounds_word, &z, sizeof(z));                                                     \
+        }                                                                                                              \
+        return v;                                                                                                      \
+    }                                                                                                                  \
     }

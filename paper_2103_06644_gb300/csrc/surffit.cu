@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -40,7 +41,8 @@ sf_status fail(sf_status s, const char* fmt, ...) {
 }
 
 sf_status cuda_fail(cudaError_t e, const char* what) {
-    return fail(SF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    // running out of device memory is an allocation failure, whichever call met it
+    return fail(e == cudaErrorMemoryAllocation ? SF_ERR_ALLOC : SF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
 size_t plane_bytes_per_frame(int method, size_t plane_elems) {
@@ -100,16 +102,48 @@ sf_status fit_pass(sf_ctx* c, int nfr, const void* depth, float* normals, float*
 
 }  // namespace
 
+// Every device allocation of the library goes through dev_alloc.  A test can
+// make the allocations after the next n fail (sf_debug_fail_allocs) and so run
+// each SF_ERR_ALLOC path, and its clean-up, without exhausting the device.
+static std::atomic<long long> g_alloc_budget{-1};  // allocations left before failing; < 0: no limit
+static std::atomic<long long> g_live_allocs{0};    // device allocations of the library not yet freed
+
+template <class T>
+static cudaError_t dev_alloc(T** p, size_t bytes) {
+    long long b = g_alloc_budget.load();
+    while (b >= 0) {
+        if (b == 0) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+    }
+    const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();  // not sticky: clear it so that no later launch check reports it
+    } else {
+        ++g_live_allocs;
+    }
+    return e;
+}
+
+static void dev_free(void* p) {
+    if (!p) return;
+    cudaFree(p);
+    --g_live_allocs;
+}
+
 static sf_status ensure_planes(sf_ctx* c, int frames) {
     const size_t delta_bytes = (sf::kDeltaPlanes32 * 4 + sf::kDeltaPlanes64 * 8) * c->plane_elems;
     const size_t need = std::max(sfh::plane_bytes_per_frame(SF_METHOD_STANDARD, c->plane_elems),
                                  c->dtab ? delta_bytes : (size_t)0) * (size_t)frames;
     if (c->planes && c->planes_bytes >= need && c->planes_frames >= frames) return SF_OK;
-    if (c->planes) cudaFree(c->planes);
+    if (c->planes) dev_free(c->planes);
     c->planes = nullptr;
     c->planes_bytes = 0;
     c->planes_frames = 0;
-    cudaError_t e = cudaMalloc(&c->planes, need);
+    cudaError_t e = dev_alloc(&c->planes, need);
     if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "scratch allocation of %zu bytes failed: %s", need,
                                       cudaGetErrorString(e));
     c->planes_bytes = need;
@@ -141,6 +175,17 @@ sf_status sf_eval_acos(const float* x, float* y, int n, void* stream) {
     if (misaligned(x, 4) || misaligned(y, 4)) return fail(SF_ERR_INVALID_ARG, "buffers must be 4-byte aligned");
     acos_eval_kernel<<<(n + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, y, n);
     SF_CUDA(cudaGetLastError());
+    return SF_OK;
+}
+
+sf_status sf_debug_fail_allocs(long long after) {
+    g_alloc_budget.store(after < 0 ? -1 : after);
+    return SF_OK;
+}
+
+sf_status sf_debug_live_allocs(long long* n) {
+    if (!n) return fail(SF_ERR_INVALID_ARG, "null output");
+    *n = g_live_allocs.load();
     return SF_OK;
 }
 
@@ -187,8 +232,8 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
     if (!htx || !hty) { free(htx); free(hty); delete c; return fail(SF_ERR_ALLOC, "host table allocation failed"); }
     for (int x = 0; x < W; ++x) htx[x] = (float)((x + K->dx - K->cx) / K->fx);
     for (int y = 0; y < H; ++y) hty[y] = (float)((y + K->dy - K->cy) / K->fy);
-    cudaError_t e = cudaMalloc(&c->tx, sizeof(float) * W);
-    if (e == cudaSuccess) e = cudaMalloc(&c->ty, sizeof(float) * H);
+    cudaError_t e = dev_alloc(&c->tx, sizeof(float) * W);
+    if (e == cudaSuccess) e = dev_alloc(&c->ty, sizeof(float) * H);
     if (e == cudaSuccess) e = cudaMemcpy(c->tx, htx, sizeof(float) * W, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->ty, hty, sizeof(float) * H, cudaMemcpyHostToDevice);
     free(htx); free(hty);
@@ -196,9 +241,9 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
     // Frames per pass: every frame of a call in one launch (up to 64), so the
     // grid fills the GPU; the scratch moments are sized for them on demand.
     c->max_frames_per_pass = 64;
-    e = cudaMalloc(&c->vmax, sizeof(unsigned) * 64);
+    e = dev_alloc(&c->vmax, sizeof(unsigned) * 64);
     if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create vmax"); }
-    e = cudaMalloc(&c->flag_count, 2 * sizeof(unsigned));
+    e = dev_alloc(&c->flag_count, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->flag_count, 0, 2 * sizeof(unsigned));
     if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create flag counter"); }
     {
@@ -209,7 +254,7 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
         for (int y = 0; y < H; ++y) h[W + y] = (y + K->dy - K->cy) / K->fy;
         h[W + H] = 1.0 / K->fx;
         h[W + H + 1] = 1.0 / K->fy;
-        e = cudaMalloc(&c->rays64, sizeof(double) * (W + H + 2));
+        e = dev_alloc(&c->rays64, sizeof(double) * (W + H + 2));
         if (e == cudaSuccess) e = cudaMemcpy(c->rays64, h, sizeof(double) * (W + H + 2), cudaMemcpyHostToDevice);
         free(h);
         if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create FP64 rays"); }
@@ -282,7 +327,7 @@ static sf_status capture_fit(sf_ctx* c, const sf_ctx::FitKey& key, int n, const 
 
 extern "C" {
 
-sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
+static sf_status fit_ex_impl(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
                     int32_t* counts, void* stream) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
@@ -310,13 +355,13 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
     if (c->precision_mode > 0) {
         const size_t cap = fe * (size_t)std::min(per, n_frames);  // every pixel may be queued
         if (c->flags_cap < cap) {
-            if (c->flags) cudaFree(c->flags);
+            if (c->flags) dev_free(c->flags);
             c->flags = nullptr;
             c->flags_cap = 0;
-            if (c->queue_c) cudaFree(c->queue_c);
+            if (c->queue_c) dev_free(c->queue_c);
             c->queue_c = nullptr;
-            cudaError_t e = cudaMalloc(&c->flags, cap * sizeof(unsigned long long));
-            if (e == cudaSuccess) e = cudaMalloc(&c->queue_c, cap * sizeof(unsigned));
+            cudaError_t e = dev_alloc(&c->flags, cap * sizeof(unsigned long long));
+            if (e == cudaSuccess) e = dev_alloc(&c->queue_c, cap * sizeof(unsigned));
             if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "precision-fallback queue of %zu entries failed", cap);
             c->flags_cap = cap;
             ++c->gen;
@@ -327,10 +372,10 @@ sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, 
         // (the delta-table path solves from the depth and keeps no moments)
         const size_t mcap = c->dtab ? 0 : c->precision_mode == 2 ? cap : (cap + 3) / 4;
         if (c->moments_cap < mcap) {
-            if (c->moments_q) cudaFree(c->moments_q);
+            if (c->moments_q) dev_free(c->moments_q);
             c->moments_q = nullptr;
             c->moments_cap = 0;
-            cudaError_t e = cudaMalloc(&c->moments_q, mcap * sfh::kMomentEntryBytes);
+            cudaError_t e = dev_alloc(&c->moments_q, mcap * sfh::kMomentEntryBytes);
             if (e != cudaSuccess)
                 return fail(SF_ERR_ALLOC, "precision-fallback moments of %zu entries failed", mcap);
             c->moments_cap = mcap;
@@ -367,7 +412,7 @@ sf_status sf_fit(sf_ctx* c, const void* depth, float* normals, float* offsets, f
     return sf_fit_ex(c, 1, depth, normals, offsets, curvature, nullptr, stream);
 }
 
-sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
+static sf_status fit_host_impl(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
                       int32_t* counts, void* stream) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
@@ -393,12 +438,12 @@ sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals
     }
     if (c->d_io_bytes < need) {
         for (int i = 0; i < 2; ++i) {
-            if (c->d_io[i]) cudaFree(c->d_io[i]);
+            if (c->d_io[i]) dev_free(c->d_io[i]);
             c->d_io[i] = nullptr;
         }
         c->d_io_bytes = 0;
         for (int i = 0; i < 2; ++i) {
-            cudaError_t e = cudaMalloc(&c->d_io[i], need);
+            cudaError_t e = dev_alloc(&c->d_io[i], need);
             if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "device staging of 2 x %zu bytes failed", need);
         }
         c->d_io_bytes = need;
@@ -448,7 +493,7 @@ sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals
     return SF_OK;
 }
 
-sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_params* p, sf_quad_node* nodes,
+static sf_status quadtree_impl(sf_ctx* c, int n_frames, const void* depth, const sf_quad_params* p, sf_quad_node* nodes,
                       int capacity, int32_t* n_nodes, void* stream) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (!p || !n_nodes) return fail(SF_ERR_INVALID_ARG, "null params or n_nodes");
@@ -477,18 +522,18 @@ sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_
     if (cap > ((size_t)1 << 28)) return fail(SF_ERR_INVALID_ARG, "quadtree too large: %zu nodes per level", cap);
     if (c->quad_cap < cap) {
         for (int i = 0; i < 2; ++i) {
-            if (c->quad_q[i]) cudaFree(c->quad_q[i]);
+            if (c->quad_q[i]) dev_free(c->quad_q[i]);
             c->quad_q[i] = nullptr;
         }
         c->quad_cap = 0;
         for (int i = 0; i < 2; ++i) {
-            cudaError_t e = cudaMalloc(&c->quad_q[i], sizeof(sf::QuadRect) * cap);
+            cudaError_t e = dev_alloc(&c->quad_q[i], sizeof(sf::QuadRect) * cap);
             if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "quadtree queue of %zu nodes failed", cap);
         }
         c->quad_cap = cap;
     }
     if (!c->quad_cnt) {
-        cudaError_t e = cudaMalloc(&c->quad_cnt, sizeof(int) * 8);
+        cudaError_t e = dev_alloc(&c->quad_cnt, sizeof(int) * 8);
         if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "quadtree counters failed");
     }
     const size_t fe = (size_t)c->W * c->H;
@@ -521,7 +566,7 @@ sf_status sf_set_delta_table(sf_ctx* c, const float* ddx, const float* ddy) {
         if (e != cudaSuccess) return cuda_fail(e, "sf_set_delta_table: synchronise");
     }
     if (!ddx) {
-        if (c->dtab) cudaFree(c->dtab);
+        if (c->dtab) dev_free(c->dtab);
         c->dtab = nullptr;
         return SF_OK;
     }
@@ -538,7 +583,7 @@ sf_status sf_set_delta_table(sf_ctx* c, const float* ddx, const float* ddy) {
         planes[n + i] = (int)std::lrint((double)b * sf::kDeltaScale);
     }
     if (!c->dtab) {
-        cudaError_t e = cudaMalloc(&c->dtab, 2 * n * sizeof(int));
+        cudaError_t e = dev_alloc(&c->dtab, 2 * n * sizeof(int));
         if (e != cudaSuccess) { c->dtab = nullptr; return fail(SF_ERR_ALLOC, "delta table of %zu bytes", n * 8); }
     }
     SF_CUDA(cudaMemcpy(c->dtab, planes.data(), 2 * n * sizeof(int), cudaMemcpyHostToDevice));
@@ -592,7 +637,7 @@ sf_status sf_set_disparity_model(sf_ctx* c, double alpha, double beta) {
     return SF_OK;
 }
 
-sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const float* g_normals, const float* g_offsets,
+static sf_status fit_backward_impl(sf_ctx* c, int n_frames, const void* depth, const float* g_normals, const float* g_offsets,
                           const float* g_curvature, float* g_depth, void* stream) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
@@ -620,11 +665,11 @@ sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const floa
     const size_t planes_bytes = sizeof(float) * 12 * fe * (size_t)first;
     const size_t need = planes_bytes + sizeof(float) * 3 * 64;
     if (c->adj_bytes < need) {
-        if (c->adj) cudaFree(c->adj);
+        if (c->adj) dev_free(c->adj);
         c->adj = nullptr;
         c->adj_max = nullptr;
         c->adj_bytes = 0;
-        cudaError_t e = cudaMalloc(&c->adj, need);
+        cudaError_t e = dev_alloc(&c->adj, need);
         if (e != cudaSuccess) return fail(SF_ERR_ALLOC, "adjoint scratch of %zu bytes failed", need);
         c->adj_bytes = need;
     }
@@ -689,28 +734,28 @@ sf_status sf_destroy(sf_ctx* c) {
     if (!c) return SF_OK;
     for (auto& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->event_pool) cudaEventDestroy(e);
-    if (c->tx) cudaFree(c->tx);
-    if (c->ty) cudaFree(c->ty);
-    if (c->vmax) cudaFree(c->vmax);
-    if (c->planes) cudaFree(c->planes);
+    if (c->tx) dev_free(c->tx);
+    if (c->ty) dev_free(c->ty);
+    if (c->vmax) dev_free(c->vmax);
+    if (c->planes) dev_free(c->planes);
     for (int i = 0; i < 2; ++i) {
-        if (c->d_io[i]) cudaFree(c->d_io[i]);
+        if (c->d_io[i]) dev_free(c->d_io[i]);
         if (c->io_stream[i]) cudaStreamDestroy(c->io_stream[i]);
         if (c->io_fit_done[i]) cudaEventDestroy(c->io_fit_done[i]);
     }
     if (c->io_entry) cudaEventDestroy(c->io_entry);
-    if (c->adj) cudaFree(c->adj);
-    if (c->dtab) cudaFree(c->dtab);
-    if (c->flags) cudaFree(c->flags);
-    if (c->moments_q) cudaFree(c->moments_q);
-    if (c->queue_c) cudaFree(c->queue_c);
+    if (c->adj) dev_free(c->adj);
+    if (c->dtab) dev_free(c->dtab);
+    if (c->flags) dev_free(c->flags);
+    if (c->moments_q) dev_free(c->moments_q);
+    if (c->queue_c) dev_free(c->queue_c);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph_stream) cudaStreamDestroy(c->graph_stream);
-    if (c->flag_count) cudaFree(c->flag_count);
-    if (c->rays64) cudaFree(c->rays64);
+    if (c->flag_count) dev_free(c->flag_count);
+    if (c->rays64) dev_free(c->rays64);
     for (int i = 0; i < 2; ++i)
-        if (c->quad_q[i]) cudaFree(c->quad_q[i]);
-    if (c->quad_cnt) cudaFree(c->quad_cnt);
+        if (c->quad_q[i]) dev_free(c->quad_q[i]);
+    if (c->quad_cnt) dev_free(c->quad_cnt);
     delete c;
     return SF_OK;
 }
@@ -735,12 +780,12 @@ sf_status sf_batch_destroy(sf_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
-    cudaFree(b->d_desc);
-    cudaFree(b->d_items);
-    cudaFree(b->d_sync);
+    dev_free(b->d_desc);
+    dev_free(b->d_items);
+    dev_free(b->d_sync);
     if (b->done) cudaEventDestroy(b->done);
-    cudaFree(b->d_rays);
-    cudaFree(b->d_planes);
+    dev_free(b->d_rays);
+    dev_free(b->d_planes);
     delete b;
     return SF_OK;
 }
@@ -835,26 +880,26 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
     std::vector<int3> items(ritems);
     items.insert(items.end(), hitems.begin(), hitems.end());
     items.insert(items.end(), vitems.begin(), vitems.end());
-    cudaError_t e = cudaMalloc(&b->d_rays, sizeof(float) * std::max<size_t>(rays, 1));
+    cudaError_t e = dev_alloc(&b->d_rays, sizeof(float) * std::max<size_t>(rays, 1));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_rays, hr.data(), sizeof(float) * rays, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         for (int f = 0; f < n_frames; ++f) {
             desc[f].tx = b->d_rays + rofs[f];
             desc[f].ty = b->d_rays + rofs[f] + desc[f].W;
         }
-        e = cudaMalloc(&b->d_desc, sizeof(sf::FrameDesc) * n_frames);
+        e = dev_alloc(&b->d_desc, sizeof(sf::FrameDesc) * n_frames);
     }
     if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, desc.data(), sizeof(sf::FrameDesc) * n_frames, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int3) * items.size());
+    if (e == cudaSuccess) e = dev_alloc(&b->d_items, sizeof(int3) * items.size());
     if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(int3) * items.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_sync, sizeof(unsigned) * (3 + 3 * (size_t)n_frames));
+    if (e == cudaSuccess) e = dev_alloc(&b->d_sync, sizeof(unsigned) * (3 + 3 * (size_t)n_frames));
     if (e == cudaSuccess) e = cudaMemset(b->d_sync, 0, sizeof(unsigned) * (3 + 3 * (size_t)n_frames));
     if (e == cudaSuccess) {
         const unsigned limit = kBatchWaitPolls;
         e = cudaMemcpy(b->d_sync + 2, &limit, sizeof(unsigned), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_planes, sfh::plane_bytes_per_frame(method, stride));
+    if (e == cudaSuccess) e = dev_alloc(&b->d_planes, sfh::plane_bytes_per_frame(method, stride));
     if (e != cudaSuccess) { sf_batch_destroy(b); return fail(SF_ERR_ALLOC, "batch buffers: %s", cudaGetErrorString(e)); }
     b->hsmem = sizeof(int) * sf::kHThreads * (size_t)((max_seg + 2 * max_r) | 1);
     int dev = 0, sms = 152;
@@ -885,7 +930,7 @@ sf_status sf_batch_create(const sf_batch_frame* frames, int n_frames, int method
     return SF_OK;
 }
 
-sf_status sf_batch_run(sf_batch* b, void* stream) {
+static sf_status batch_run_impl(sf_batch* b, void* stream) {
     if (!b) return fail(SF_ERR_INVALID_ARG, "null batch");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (b->use_graph) {
@@ -983,9 +1028,9 @@ sf_status static_scratch_base(void** out) {
 
 }  // namespace
 
-extern "C" sf_status sf_fit_static(const sf_intrinsics* K, int W, int H, int window, int method, int depth_type,
-                                   float depth_scale, int min_valid, int require_center_valid, const void* depth,
-                                   float* normals, float* offsets, float* curvature, void* stream) {
+static sf_status fit_static_impl(const sf_intrinsics* K, int W, int H, int window, int method, int depth_type,
+                                 float depth_scale, int min_valid, int require_center_valid, const void* depth,
+                                 float* normals, float* offsets, float* curvature, void* stream) {
     if (!K) return fail(SF_ERR_INVALID_ARG, "null intrinsics");
     if (!depth || !normals || !offsets || !curvature) return fail(SF_ERR_INVALID_ARG, "null buffer");
     if (misaligned(depth, depth_type == SF_DEPTH_F32 ? 4 : 2) || misaligned(normals, 4) || misaligned(offsets, 4) ||
@@ -1048,4 +1093,49 @@ extern "C" sf_status sf_fit_static(const sf_intrinsics* K, int W, int H, int win
     // c points into the static array: nothing to free
     c.tx = nullptr; c.ty = nullptr; c.vmax = nullptr; c.planes = nullptr;
     return s;
+}
+
+// Bounds-checked build: after the work, report the first out-of-range moment
+// plane access any kernel recorded (SF_ERR_CUDA).  Synchronises the device.
+static sf_status check_bounds(sf_status s) {
+#if SF_CHECK_BOUNDS
+    if (s != SF_OK) return s;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "bounds check synchronise");
+    const unsigned long long w[3] = {sfh::bounds_word_f32(), sfh::bounds_word_u16(), sfh::bounds_word_disp()};
+    for (unsigned long long v : w)
+        if (v)
+            return fail(SF_ERR_CUDA, "out-of-range moment plane access (site %d, entry %llu)", (int)((v >> 56) & 127),
+                        v & ((1ull << 56) - 1));
+#endif
+    return s;
+}
+
+extern "C" {
+
+sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
+                    int32_t* counts, void* stream) {
+    return check_bounds(fit_ex_impl(c, n_frames, depth, normals, offsets, curvature, counts, stream));
+}
+sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
+                      int32_t* counts, void* stream) {
+    return check_bounds(fit_host_impl(c, n_frames, depth, normals, offsets, curvature, counts, stream));
+}
+sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const float* g_normals, const float* g_offsets,
+                          const float* g_curvature, float* g_depth, void* stream) {
+    return check_bounds(fit_backward_impl(c, n_frames, depth, g_normals, g_offsets, g_curvature, g_depth, stream));
+}
+sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_params* params, sf_quad_node* nodes,
+                      int capacity, int32_t* n_nodes, void* stream) {
+    return check_bounds(quadtree_impl(c, n_frames, depth, params, nodes, capacity, n_nodes, stream));
+}
+sf_status sf_batch_run(sf_batch* b, void* stream) { return check_bounds(batch_run_impl(b, stream)); }
+
+}  // extern "C"
+
+extern "C" sf_status sf_fit_static(const sf_intrinsics* K, int W, int H, int window, int method, int depth_type,
+                                   float depth_scale, int min_valid, int require_center_valid, const void* depth,
+                                   float* normals, float* offsets, float* curvature, void* stream) {
+    return check_bounds(fit_static_impl(K, W, H, window, method, depth_type, depth_scale, min_valid,
+                                        require_center_valid, depth, normals, offsets, curvature, stream));
 }
