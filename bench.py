@@ -436,6 +436,32 @@ def run_single_case(args):
     print(json.dumps({"case": "single1080", "method": args.method, "fits": max(1, args.steps)}))
 
 
+def run_diff_case(args):
+    """16 x 640x480 f32 frames, k=9 (or --window): forward, upstream gradient and backward, --steps times
+    (for ncu captures of the backward kernels)."""
+    import torch
+
+    from paper_2103_06644_gb300 import SurfaceFitter
+
+    intr = scenes.Intrinsics(525.0, 525.0, 319.5, 239.5)
+    nd = 16
+    dd = torch.from_numpy(np.stack([scenes.kinect_frame(scenes.BASE_SEED + 600 + i, intr, 640, 480)
+                                    for i in range(nd)])).cuda()
+    tgt = torch.from_numpy(np.stack([scenes.target_normals(scenes.BASE_SEED + 700 + i, 480, 640)
+                                     for i in range(nd)]).astype(np.float32)).cuda()
+    zero = torch.zeros((nd, 480, 640), device="cuda")
+    fd = SurfaceFitter(intr.as_tuple(), 640, 480, args.window, method=args.method)
+    for _ in range(max(1, args.steps)):
+        n_, o_, c_ = fd.fit(dd)
+        valid = torch.isfinite(o_)
+        gn = torch.where(valid[..., None], 2.0 * (n_ - tgt), torch.zeros_like(n_))
+        gk = torch.where(valid, torch.full_like(c_, 0.1), torch.zeros_like(c_))
+        fd.backward(dd, gn, zero, gk)
+    torch.cuda.synchronize()
+    fd.close()
+    print(json.dumps({"case": "diff16", "method": args.method, "window": args.window, "steps": max(1, args.steps)}))
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle on bounded samples of the workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -479,12 +505,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="few steps, no extras (for ncu)")
-    ap.add_argument("--case", default=None, choices=["single1080"],
-                    help="small profiling case instead of the benchmark: one 1920x1080 frame, --steps fits")
+    ap.add_argument("--case", default=None, choices=["single1080", "diff16"],
+                    help="small profiling case instead of the benchmark: one 1920x1080 frame, --steps fits "
+                         "(single1080), or 16 x 640x480 frames fitted and differentiated --steps times (diff16)")
+    ap.add_argument("--window", type=int, default=9, help="window of the diff16 case")
     ap.add_argument("--method", default="disparity", choices=["disparity", "standard"])
     args = ap.parse_args()
     if args.case == "single1080":
         run_single_case(args)
+        return
+    if args.case == "diff16":
+        run_diff_case(args)
         return
     args.warmup = max(args.warmup, 3) if not args.profile_only else args.warmup
     if args.impl == "reference":
