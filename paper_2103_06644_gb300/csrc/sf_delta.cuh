@@ -318,9 +318,10 @@ __global__ void __launch_bounds__(kVThreads) vpass_delta_kernel(const void* __re
                     queue = !(fo.gap >= tau);
                     if (!queue && !fixed_quantum<DT, SF_METHOD_DISPARITY>()) {
                         const float tr = w.R11 + w.R22 + w.R33, iw = 1.f / w.what;
-                        queue = rounding_error2<float>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, fo.nx, fo.ny, fo.nz,
-                                                       w.mx * iw, w.my * iw, iw, l0 * tr, (l0 + fo.gap * l2n) * tr,
-                                                       l2n * tr) > kRefineRounding * kRefineRounding;
+                        const float thr2 = kRefineRounding * kRefineRounding;
+                        queue = rounding_error2_screened<float>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, fo.nx,
+                                                                fo.ny, fo.nz, w.mx * iw, w.my * iw, iw, l0 * tr,
+                                                                (l0 + fo.gap * l2n) * tr, l2n * tr, thr2) > thr2;
                     }
                 }
                 fo.d = -(fo.nx * w.mx + fo.ny * w.my + fo.nz) * Fn<float>::rcp(w.what * q);
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(kVThreads) vpass_delta_kernel(const void* __re
 // Precision modes with a table: the queued windows solved again in FP64 from
 // sums of the unrounded depth and the table's rays, as the paper defines the
 // fit (Eq. 14 with the rays of Eq. 1 / Eq. 10), with no fixed point.  Each
-// warp takes 32 windows; for each in turn its lanes sum the window's columns
+// warp takes up to 32 windows; for each in turn its lanes sum the window's columns
 // (lane l: column offset j = l - r), first the count and the disparity to
 // centre on, then the moments of the shifted offsets jh = j + D/S,
 // ih = i + E/S and of w' = w - wc; every lane then solves its own window.
@@ -464,11 +465,13 @@ __global__ void __launch_bounds__(128) direct_delta_kernel(const void* __restric
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
     const size_t fe = (size_t)W * H;
     const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
-    for (unsigned base = warp * 32u; base < count; base += nwarps * 32u) {
-        const bool active = base + lane < count;
+    // lane l of warp w: window w + l W (W warps), so that a short queue spreads over every warp
+    for (unsigned base = warp; base < count; base += nwarps * 32u) {
+        const unsigned mine_idx = base + (unsigned)lane * nwarps;
+        const bool active = mine_idx < count && flags[mine_idx] != kQueueHole;
         int f = 0, x = 0, y = 0;
         if (active) {
-            const unsigned long long e = flags[base + lane];
+            const unsigned long long e = flags[mine_idx];
             f = (int)(e >> 48); y = (int)((e >> 24) & 0xffffff); x = (int)(e & 0xffffff);
         }
         double mine[kDirectSums + 1];

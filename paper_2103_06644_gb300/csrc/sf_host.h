@@ -59,7 +59,7 @@ struct sf_ctx {
     float tau = 1e-3f;
     unsigned long long* flags = nullptr;   // queue of flagged windows (frame, y, x)
     size_t flags_cap = 0;      // entries
-    unsigned* flag_count = nullptr;        // [2]: queue length, windows to re-sum
+    unsigned* flag_count = nullptr;        // [3]: queue slots reserved, windows to re-sum, windows queued
     unsigned* queue_c = nullptr;           // queue indices of the windows to re-sum (flags_cap)
     void* moments_q = nullptr; // exact window moments of the first moments_cap queued windows
     size_t moments_cap = 0;    // entries
@@ -128,6 +128,9 @@ sf_status cuda_fail(cudaError_t e, const char* what);
         if (_e != cudaSuccess) return ::sfh::cuda_fail(_e, #call); \
     } while (0)
 
+// Rows per band of the vertical pass of nfr frames (the context's vband, else
+// chosen from the grid size and the window).
+int vertical_band(const sf_ctx* c, int nfr);
 // Bytes of horizontal-moment scratch per frame of plane_elems entries.
 size_t plane_bytes_per_frame(int method, size_t plane_elems);
 // Fixed-point bits of a method and window (the most that keeps every exact

@@ -46,9 +46,14 @@ __host__ __device__ constexpr int base_method(int M) {
 // latency hiding; at 8 blocks (64 registers) the per-column pass spills.
 constexpr int kVBlocks = 6;
 
-// Normal error (rad) above which a window's fixed-point rounding sends it to
-// the refinement of precision modes 1 and 2 (the tier-C threshold there).
-constexpr float kRefineRounding = 3e-5f;
+// The precision modes' window queue: entries (frame << 48 | y << 24 | x).  A
+// warp of the column pass reserves kQueueChunk slots at a time (one atomic per
+// chunk instead of one per row: a single counter hammered by every warp cost
+// the pass a fifth of its time) and marks the slots it leaves unused as holes,
+// which the queue's readers skip.
+constexpr unsigned long long kQueueHole = ~0ull;
+constexpr unsigned kQueueChunk = 32;
+
 
 // ---------------------------------------------------------------------------
 // Depth decoding.  Codec: how a stored value becomes depth.
@@ -780,6 +785,8 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
     int32_t* pk = counts ? counts + oi : nullptr;
     float zc = load_depth<DT>(depth, oi, scale);
     float tyn = tyt[y0];
+    unsigned q_next = 0, q_end = 0, q_count = 0;  // this warp's reserved queue slots, windows queued
+    const unsigned act = __activemask();           // the lanes running this column loop
     for (int y = y0; y < y1; ++y) {
         const bool cvalid = depth_valid(zc);
         const float ty = tyn;
@@ -811,40 +818,56 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
                                               S.Szz, S.Szzj, S.Szzi, S.Szzjj, S.Szzji, S.Szzii, q, tx, ty, a, b,
                                               ok);
         }
+        bool queue = false;
         if (ok) {
             nx = fo_.nx; ny = fo_.ny; nz = fo_.nz; d = fo_.d; cu = fo_.curv;
             // queue a near-degenerate window, and (kGuard) one whose fixed-point
             // rounding could move its normal by more than the refinement's threshold
-            bool queue = flags && !(fo_.gap >= tau);
+            queue = flags && !(fo_.gap >= tau);
             if constexpr (kGuard) queue = queue || (flags && fo_.qerr2 > kRefineRounding * kRefineRounding);
-            if (queue) {
-                // near-degenerate window: queue it for the FP64 re-solve
-                const unsigned mask = __activemask();
-                const int leader = __ffs(mask) - 1;
-                const int lane = threadIdx.x & 31;
-                unsigned base = 0;
-                if (lane == leader) base = atomicAdd(flag_count, (unsigned)__popc(mask));
-                base = __shfl_sync(mask, base, leader);
-                const unsigned slot = base + __popc(mask & ((1u << lane) - 1u));
-                flags[slot] = ((unsigned long long)frame_tag << 48) | ((unsigned long long)y << 24) |
-                              (unsigned long long)x;
-                if (slot < mcap) {
-                    // the window's exact moments travel with it (80 B, five 16-byte stores)
-                    longlong2* e = reinterpret_cast<longlong2*>(static_cast<char*>(mq) + (size_t)slot * 80);
-                    if constexpr (B == SF_METHOD_DISPARITY) {
-                        e[0] = make_longlong2((long long)S.n, (long long)S.Sj);
-                        e[1] = make_longlong2((long long)S.Si, (long long)S.Sjj);
-                        e[2] = make_longlong2((long long)S.Sji, (long long)S.Sii);
-                        e[3] = make_longlong2(S.Sw, S.Swj);
-                        e[4] = make_longlong2(S.Swi, S.Sww);
-                    } else {
-                        e[0] = make_longlong2((long long)S.n, S.Sz);
-                        e[1] = make_longlong2(S.Szj, S.Szi);
-                        e[2] = make_longlong2(S.Szz, S.Szzj);
-                        e[3] = make_longlong2(S.Szzi, S.Szzjj);
-                        e[4] = make_longlong2(S.Szzji, S.Szzii);
+        }
+        if (flags) {
+            // all the loop's lanes take part (the chunk state stays the same in every lane)
+            const unsigned qm = __ballot_sync(act, queue);
+            if (qm) {
+                const unsigned k = __popc(qm), rem = q_end - q_next;
+                const int leader = __ffs(act) - 1;
+                unsigned s = 0;
+                if (k > rem) {
+                    if ((int)(threadIdx.x & 31) == leader) s = atomicAdd(flag_count, kQueueChunk);
+                    s = __shfl_sync(act, s, leader);
+                }
+                if (queue) {
+                    const int lane = threadIdx.x & 31;
+                    const unsigned rank = __popc(qm & ((1u << lane) - 1u));
+                    const unsigned slot = rank < rem ? q_next + rank : s + (rank - rem);
+                    flags[slot] = ((unsigned long long)frame_tag << 48) | ((unsigned long long)y << 24) |
+                                  (unsigned long long)x;
+                    if (slot < mcap) {
+                        // the window's exact moments travel with it (80 B, five 16-byte stores)
+                        longlong2* e = reinterpret_cast<longlong2*>(static_cast<char*>(mq) + (size_t)slot * 80);
+                        if constexpr (B == SF_METHOD_DISPARITY) {
+                            e[0] = make_longlong2((long long)S.n, (long long)S.Sj);
+                            e[1] = make_longlong2((long long)S.Si, (long long)S.Sjj);
+                            e[2] = make_longlong2((long long)S.Sji, (long long)S.Sii);
+                            e[3] = make_longlong2(S.Sw, S.Swj);
+                            e[4] = make_longlong2(S.Swi, S.Sww);
+                        } else {
+                            e[0] = make_longlong2((long long)S.n, S.Sz);
+                            e[1] = make_longlong2(S.Szj, S.Szi);
+                            e[2] = make_longlong2(S.Szz, S.Szzj);
+                            e[3] = make_longlong2(S.Szzi, S.Szzjj);
+                            e[4] = make_longlong2(S.Szzji, S.Szzii);
+                        }
                     }
                 }
+                if (k > rem) {
+                    q_next = s + (k - rem);
+                    q_end = s + kQueueChunk;
+                } else {
+                    q_next += k;
+                }
+                q_count += k;
             }
         }
         pn[0] = nx; pn[1] = ny; pn[2] = nz;
@@ -852,6 +875,13 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
         if (pk) { *pk = n; pk += W; }
         pn += 3 * (size_t)W; po += W; pc += W;
         if (more) S.apply(r);
+    }
+    if (flags) {
+        __syncwarp(act);
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1) {
+            for (unsigned i = q_next; i < q_end; ++i) flags[i] = kQueueHole;
+            if (q_count) atomicAdd(flag_count + 2, q_count);
+        }
     }
 }
 
@@ -1058,6 +1088,7 @@ __global__ void __launch_bounds__(128) resolve_kernel(int W, int H, int r, Codec
     const Planes P(planes_base, (size_t)nframes * plane_elems, planes32<M>());
     for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
         const unsigned long long e = flags[idx];
+        if (e == kQueueHole) continue;
         const int f = (int)(e >> 48), y = (int)((e >> 24) & 0xffffff), x = (int)(e & 0xffffff);
         const size_t pb = plane_index((size_t)f * plane_elems, x, 0, H);
         const double q = (double)quantum<DT, M>(vmax_bits[f], bits, scale);

@@ -77,23 +77,6 @@ int range_blocks(const sf_ctx* c, size_t fe, int nfr) {
     return (int)std::max<size_t>(1, std::min((fe + 4095) / 4096, per_frame));
 }
 
-// Band height of the vertical pass: long bands amortise the 2r-row warm-up,
-// short bands give enough threads to fill the GPU.
-int vertical_band(const sf_ctx* c, int nfr) {
-    if (c->vband > 0) return c->vband;
-    const size_t cols = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * sf::kVThreads * nfr;
-    // at least 152 x 2048 threads (about 2.7 waves of 24 resident warps per
-    // SM): short bands cost a 2r-row warm-up each, but with fewer waves the
-    // tail of the last one costs more.  Small frames with small windows go
-    // down to 4-row bands: there the serial chain of solves per thread, not
-    // the warm-up, bounds the pass (one 640 x 480 frame at k = 7: 12.8 us at
-    // 4 rows, 16.9 at 16); larger windows keep bands of at least r + 1 rows
-    const int min_band = std::max(4, std::min(16, c->r + 1));
-    int band = 256;
-    while (band / 2 >= min_band && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 64 * 32) band /= 2;
-    return band;
-}
-
 // One wave of resident blocks of a kernel (persistent grid-stride kernels).
 template <typename K>
 int resident_blocks(const sf_ctx* c, K kernel, int threads) {
@@ -131,7 +114,7 @@ sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* normals, flo
     const bool fb = c->precision_mode > 0 && c->flags;
     // the implicit |(a,b,c)| = 1 fits queue their exact moments with each flagged window
     constexpr bool kRich = !U4 && (M == SF_METHOD_DISPARITY || M == SF_METHOD_STANDARD);
-    if (fb) SF_CUDA(cudaMemsetAsync(c->flag_count, 0, 2 * sizeof(unsigned), st));
+    if (fb) SF_CUDA(cudaMemsetAsync(c->flag_count, 0, 3 * sizeof(unsigned), st));
     {
         StageTimer t(c, 2, st);
         const int band = vertical_band(c, nfr);
@@ -284,7 +267,7 @@ sf_status launch_pass_delta(sf_ctx* c, int nfr, const void* depth, float* normal
     // (mode 1) or every window (mode 2), and the direct kernel solves them again
     // in FP64 from the unrounded depth
     const bool fb = c->precision_mode > 0 && c->flags;
-    if (fb) SF_CUDA(cudaMemsetAsync(c->flag_count, 0, 2 * sizeof(unsigned), st));
+    if (fb) SF_CUDA(cudaMemsetAsync(c->flag_count, 0, 3 * sizeof(unsigned), st));
     {
         StageTimer t(c, 2, st);
         const int band = vertical_band(c, nfr);

@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(128) refine_kernel(const void* __restrict__ de
     const df a = df_d(rays[W + H]), b = df_d(rays[W + H + 1]);
     for (unsigned base = warp * 32u; base < count; base += nwarps * 32u) {
         const unsigned idx = base + lane;
-        const bool active = idx < count;
+        const bool active = idx < count && flags[idx] != kQueueHole;
         int f = 0, x = 0, y = 0;
         int64_t mo[10];
         if (active) load_window<M>(idx, flags, moments, moments_cap, P, plane_elems, H, r, f, x, y, mo);
@@ -718,9 +718,11 @@ __global__ void __launch_bounds__(128) refine_kernel(const void* __restrict__ de
 }
 
 // ---------------------------------------------------------------------------
-// Tier C for the windows of the second queue: each warp takes 32 windows,
-// sums the fixed-point residuals of each in turn with all its lanes, then
-// every lane corrects its window's moments and refines it again.
+// Tier C for the windows of the second queue: each warp takes up to 32
+// windows (lane l of warp w: window w + l W for W warps, so that a short
+// queue spreads over every warp of the grid), sums the fixed-point residuals
+// of each in turn with all its lanes, then every lane corrects its window's
+// moments and refines it again.
 // ---------------------------------------------------------------------------
 template <int DT, int M>
 __global__ void __launch_bounds__(128) resum_kernel(const void* __restrict__ depth, int W, int H, int r, Codec cd,
@@ -743,12 +745,14 @@ __global__ void __launch_bounds__(128) resum_kernel(const void* __restrict__ dep
     const size_t fe = (size_t)W * H;
     const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
     const df a = df_d(rays[W + H]), b = df_d(rays[W + H + 1]);
-    for (unsigned base = warp * 32u; base < count; base += nwarps * 32u) {
-        const bool active = base + lane < count;
+    for (unsigned base = warp; base < count; base += nwarps * 32u) {
+        const unsigned mine_idx = base + (unsigned)lane * nwarps;
+        // (the second queue holds windows; the first may hold holes)
+        const bool active = mine_idx < count && (queue_c || flags[mine_idx] != kQueueHole);
         int f = 0, x = 0, y = 0;
         int64_t mo[10];
         if (active) {
-            const unsigned idx = queue_c ? queue_c[base + lane] : base + lane;
+            const unsigned idx = queue_c ? queue_c[mine_idx] : mine_idx;
             load_window<M>(idx, flags, moments, moments_cap, P, plane_elems, H, r, f, x, y, mo);
         }
         typename std::conditional<B == SF_METHOD_DISPARITY, DispCentred, StdCentred>::type wc{};

@@ -117,6 +117,25 @@ __device__ __forceinline__ T rounding_error2(T r11, T r12, T r13, T r22, T r23, 
     return T(2.5208333) * num * Fn<T>::rcp(dl * dl);
 }
 
+// Normal error (rad) above which a window's fixed-point rounding sends it to
+// the refinement of precision modes 1 and 2 (the tier-C threshold there).
+constexpr float kRefineRounding = 3e-5f;
+
+// rounding_error2 where it can exceed thr2, else 0: a cheap upper bound (|cp|^2
+// in place of (n1 . c)^2, no reciprocal) screens out the windows it clears,
+// and only the others pay for the full estimate.
+template <typename T>
+__device__ __forceinline__ T rounding_error2_screened(T r11, T r12, T r13, T r22, T r23, T r33, T nx, T ny, T nz,
+                                                      T cx, T cy, T cz, T l0, T l1, T l2, T thr2) {
+    const T d = -(nx * cx + ny * cy + nz * cz);
+    const T px = cx + d * nx, py = cy + d * ny, pz = cz + d * nz;
+    const T p2 = px * px + py * py + pz * pz;
+    const T dl = l1 - l0;
+    const T loose = T(2.5208333) * (d * d * (l1 > T(0) ? l1 : T(0)) + p2 * (l0 > T(0) ? l0 : T(0)));
+    if (dl > T(0) && loose <= thr2 * dl * dl) return T(0);
+    return rounding_error2<T>(r11, r12, r13, r22, r23, r33, nx, ny, nz, cx, cy, cz, l0, l1, l2);
+}
+
 // Null vector of the symmetric matrix M = R - l I: the column of the
 // cofactor matrix adj(M) with the largest diagonal entry (each column is a
 // cross product of two rows of M; adj(M) = det(M) M^{-1} is dominated by
@@ -446,8 +465,9 @@ __device__ __forceinline__ FitOutT<T> solve_disparity(T nf, T fSj, T fSi, T fSjj
     if constexpr (kEst) {
         // the weighted centroid mhat / (what qw) in units of 1 / qw
         const T iw = Fn<T>::rcp(w.what);
-        o.qerr2 = rounding_error2<T>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz, w.mx * iw,
-                                     w.my * iw, iw, l0 * o.tr, (l0 + o.gap * l2n) * o.tr, l2n * o.tr);
+        o.qerr2 = rounding_error2_screened<T>(w.R11, w.R12, w.R13, w.R22, w.R23, w.R33, o.nx, o.ny, o.nz,
+                                              w.mx * iw, w.my * iw, iw, l0 * o.tr, (l0 + o.gap * l2n) * o.tr,
+                                              l2n * o.tr, T(kRefineRounding) * T(kRefineRounding));
     }
     o.d = -(o.nx * w.mx + o.ny * w.my + o.nz) * Fn<T>::rcp(w.what * qw);
     orient<T>(o.nx, o.ny, o.nz, o.d);
@@ -523,8 +543,9 @@ __device__ __forceinline__ FitOutT<T> solve_standard(T nf, int64_t Sz, int64_t S
         // the centroid (px, py, zb) qz over its depth zb qz: a rounding of half a
         // unit of z perturbs P by m / 2, m = P / Z the pixel's ray
         const T iz = Fn<T>::rcp(zb);
-        o.qerr2 = rounding_error2<T>(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, px * iz, py * iz, T(1),
-                                     l0 * trR, (l0 + o.gap * l2n) * trR, l2n * trR);
+        o.qerr2 = rounding_error2_screened<T>(R11, R12, R13, R22, R23, R33, o.nx, o.ny, o.nz, px * iz, py * iz,
+                                              T(1), l0 * trR, (l0 + o.gap * l2n) * trR, l2n * trR,
+                                              T(kRefineRounding) * T(kRefineRounding));
     }
     o.d = -(o.nx * px + o.ny * py + o.nz * zb) * qz;
     orient<T>(o.nx, o.ny, o.nz, o.d);

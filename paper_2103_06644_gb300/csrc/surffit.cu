@@ -102,6 +102,25 @@ sf_status fit_pass(sf_ctx* c, int nfr, const void* depth, float* normals, float*
 
 }  // namespace
 
+namespace sfh {
+// Band height of the vertical pass: long bands amortise the 2r-row warm-up,
+// short bands give enough threads to fill the GPU.
+int vertical_band(const sf_ctx* c, int nfr) {
+    if (c->vband > 0) return c->vband;
+    const size_t cols = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * sf::kVThreads * nfr;
+    // at least 152 x 2048 threads (about 2.7 waves of 24 resident warps per
+    // SM): short bands cost a 2r-row warm-up each, but with fewer waves the
+    // tail of the last one costs more.  Small frames with small windows go
+    // down to 4-row bands: there the serial chain of solves per thread, not
+    // the warm-up, bounds the pass (one 640 x 480 frame at k = 7: 12.8 us at
+    // 4 rows, 16.9 at 16); larger windows keep bands of at least r + 1 rows
+    const int min_band = std::max(4, std::min(16, c->r + 1));
+    int band = 256;
+    while (band / 2 >= min_band && cols * (size_t)((c->H + band - 1) / band) < (size_t)152 * 64 * 32) band /= 2;
+    return band;
+}
+}  // namespace sfh
+
 // Every device allocation of the library goes through dev_alloc.  A test can
 // make the allocations after the next n fail (sf_debug_fail_allocs) and so run
 // each SF_ERR_ALLOC path, and its clean-up, without exhausting the device.
@@ -243,8 +262,8 @@ sf_status sf_create(const sf_intrinsics* K, int W, int H, int window, sf_ctx** o
     c->max_frames_per_pass = 64;
     e = dev_alloc(&c->vmax, sizeof(unsigned) * 64);
     if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create vmax"); }
-    e = dev_alloc(&c->flag_count, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(c->flag_count, 0, 2 * sizeof(unsigned));
+    e = dev_alloc(&c->flag_count, 3 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->flag_count, 0, 3 * sizeof(unsigned));
     if (e != cudaSuccess) { sf_destroy(c); return cuda_fail(e, "sf_create flag counter"); }
     {
         // FP64 ray tables for the precision fallback
@@ -353,7 +372,12 @@ static sf_status fit_ex_impl(sf_ctx* c, int n_frames, const void* depth, float* 
     sf_status s = ensure_planes(c, std::min(per, n_frames));
     if (s != SF_OK) return s;
     if (c->precision_mode > 0) {
-        const size_t cap = fe * (size_t)std::min(per, n_frames);  // every pixel may be queued
+        // every pixel may be queued, plus one partly used chunk of slots per warp of the column pass
+        const int nfr1 = std::min(per, n_frames);
+        const size_t vwarps = (size_t)((c->W + sf::kVThreads - 1) / sf::kVThreads) * (sf::kVThreads / 32) *
+                              (size_t)((c->H + sfh::vertical_band(c, nfr1) - 1) / sfh::vertical_band(c, nfr1)) *
+                              (size_t)nfr1;
+        const size_t cap = fe * (size_t)nfr1 + sf::kQueueChunk * vwarps;
         if (c->flags_cap < cap) {
             if (c->flags) dev_free(c->flags);
             c->flags = nullptr;
@@ -690,7 +714,7 @@ static sf_status fit_backward_impl(sf_ctx* c, int n_frames, const void* depth, c
 
 sf_status sf_precision_stats(sf_ctx* c, unsigned long long* queued, unsigned long long* resummed) {
     if (!c || !queued || !resummed) return fail(SF_ERR_INVALID_ARG, "null argument");
-    unsigned h[2] = {0u, 0u};
+    unsigned h[3] = {0u, 0u, 0u};
     if (c->precision_mode > 0) {
         int prev = 0;
         SF_CUDA(cudaGetDevice(&prev));
@@ -700,8 +724,10 @@ sf_status sf_precision_stats(sf_ctx* c, unsigned long long* queued, unsigned lon
         if (prev != c->device) cudaSetDevice(prev);
         if (e != cudaSuccess) return cuda_fail(e, "sf_precision_stats");
     }
-    *queued = h[0];
-    *resummed = c->precision_mode == 2 ? h[0] : h[1];  // mode 2 re-sums every queued window
+    // [0] counts reserved queue slots (holes included) except on the ray-table path, which
+    // reserves no chunks; [2] counts the windows queued
+    *queued = c->dtab ? h[0] : h[2];
+    *resummed = c->precision_mode == 2 ? *queued : h[1];  // mode 2 re-sums every queued window
     return SF_OK;
 }
 
