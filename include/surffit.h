@@ -336,6 +336,7 @@ sf_status sf_set_delta_table(sf_ctx* ctx, const float* ddx, const float* ddy);
  */
 sf_status sf_set_tiles(sf_ctx* ctx, int hseg, int vband);
 
+
 /* sf_destroy -- free the context and everything it owns (NULL is a no-op). */
 sf_status sf_destroy(sf_ctx* ctx);
 

@@ -760,7 +760,7 @@ using StdState = StdStateT<false>;
 // Not inlined: the single-context and the batch kernels then run the same
 // machine code, so their results agree bit for bit (inlined copies may be
 // contracted into FMAs differently); one call covers a whole band.
-template <int DT, int M, bool U4 = false, bool kGuard = false, bool kCoh = false>
+template <int DT, int M, bool U4 = false, bool kGuard = false>
 __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W, int H, int r, Codec scale, float q,
                                              const Planes P, size_t pofs, int x, int y0, int band,
                                              const float* __restrict__ txt, const float* __restrict__ tyt, float a,
@@ -774,8 +774,12 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
     const float tx = txt[x];
     constexpr int B = base_method(M);
     const float wfrac = DT == SF_DEPTH_DISPARITY_U16 ? scale.frac : 0.f;  // disparity input offset
-    typename std::conditional<B == SF_METHOD_DISPARITY, DispStateT<kCoh>,
-                              StdStateT<M == SF_METHOD_EXPLICIT_STANDARD, kCoh>>::type S(P);
+    // the scratch is read coherently from L2 in every kernel that runs this
+    // function (the batch kernel writes it in the same launch), so that all of
+    // them run one compiled copy: the compiler may fuse a float32 multiply and
+    // add differently in each copy of a function
+    typename std::conditional<B == SF_METHOD_DISPARITY, DispStateT<true>,
+                              StdStateT<M == SF_METHOD_EXPLICIT_STANDARD, true>>::type S(P);
     S.init(pb, kGroup, H, y0, r);
     // row pointers, advanced by one image row per output row
     size_t oi = (size_t)y0 * W + x;
@@ -1059,7 +1063,7 @@ __global__ void __launch_bounds__(kVThreads, kVBlocks - 1) batch_kernel(const Fr
             const int x = w.y + threadIdx.x;
             if (x < d.W) {
                 const float q = quantum<DT, M>(__ldcg(sync.vmax(w.x)), d.bits, scale);
-                vpass_column<DT, M, false, false, true>(d.depth, d.W, d.H, d.r, scale, q, P, d.pofs, x, w.z, d.band,
+                vpass_column<DT, M>(d.depth, d.W, d.H, d.r, scale, q, P, d.pofs, x, w.z, d.band,
                                                         d.tx, d.ty, d.a, d.b, min_valid, require_center, d.normals,
                                                         d.offsets, d.curvature, nullptr, INFINITY, nullptr, nullptr,
                                                         w.x, nullptr, 0u);
