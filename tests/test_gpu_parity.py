@@ -222,7 +222,7 @@ def test_tile_shapes_do_not_change_results(method):
     t = torch.from_numpy(np.stack([depth, depth[::-1].copy()])).cuda()
     f = SurfaceFitter(intr.as_tuple(), W, H, k, method=method)
     base = [x.clone() for x in f.fit(t, counts=True)]
-    for hseg, vband in [(64, 0), (128, 0), (32, 8), (64, 48), (128, 1024)]:
+    for hseg, vband in [(64, 0), (128, 0), (32, 2), (32, 8), (64, 4), (64, 48), (128, 1024)]:
         f.set_tiles(hseg, vband)
         out = f.fit(t, counts=True)
         torch.cuda.synchronize()
@@ -275,3 +275,20 @@ def test_repeated_calls_replay_a_graph():
     assert torch.isnan(out[1]).sum() > torch.isnan(ref1[1]).sum()
     f.close()
     fresh.close()
+
+
+def test_more_frames_than_one_pass():
+    """A call of 70 frames runs as two passes (at most 64 frames each); every frame matches its own fit
+    bit for bit, including the first frame of the second pass."""
+    W, H, k = 40, 30, 5
+    intr = scenes.Intrinsics.scaled(W, H)
+    frames = np.stack([scenes.kinect_frame(scenes.BASE_SEED + 300 + i, intr, W, H) for i in range(70)])
+    f = SurfaceFitter(intr.as_tuple(), W, H, k)
+    t = torch.from_numpy(frames).cuda()
+    nb, db, cb, kb = f.fit(t, counts=True)
+    for i in (0, 37, 63, 64, 69):
+        n1, d1, c1, k1 = f.fit(t[i], counts=True)
+        torch.cuda.synchronize()
+        for a, b in zip((nb[i], db[i], cb[i], kb[i]), (n1, d1, c1, k1)):
+            assert torch.equal(torch.nan_to_num(a.float(), nan=7.0), torch.nan_to_num(b.float(), nan=7.0)), i
+    f.close()
