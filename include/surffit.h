@@ -358,7 +358,8 @@ sf_status sf_channel_counts(int method, int* depth_channels, int* mask_channels)
  * waits for the recorded events, writes for each stage s < n_stages the
  * summed milliseconds ms[s] and the launch count launches[s], and clears the
  * record.  Stages: 0 range (quantum), 1 horizontal moments, 2 vertical
- * moments + solve, 3 FP64 re-solve (precision modes 1-2).  Enabling again
+ * moments + solve, 3 precision fallback (modes 1-2: refinement, re-sums and
+ * FP64 re-solves of the queued windows).  Enabling again
  * clears the record.
  */
 sf_status sf_profile_enable(sf_ctx* ctx, int on);

@@ -108,7 +108,7 @@ def test_structured_light_30x720p_u16(method):
 
 
 def test_mixed_batch_64_frames_graph():
-    """The 64-frame mixed batch with autotuned tiles, one persistent launch per stage from a CUDA graph."""
+    """The 64-frame mixed batch with autotuned tiles, one persistent launch per pass from a CUDA graph."""
     spec = scenes.mixed_batch_spec(64)
     frames, host = [], []
     for i, (W, H, k) in enumerate(spec):
