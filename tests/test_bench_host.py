@@ -90,3 +90,43 @@ def test_issue_roofline_arithmetic(monkeypatch):
     assert r["frac"] == pytest.approx(16 / 25.6)
     # without a sampled clock the recipe's maximum SM clock stands in
     assert bench.issue_roofline("vpass_solve", 0.25, None, 100)["sm_mhz"] == 2070.0
+
+
+class _FakeNvml:
+    """Stands in for bench._Nvml: a fixed SM clock and the throttle-reason bits the test sets."""
+
+    bits = 0
+
+    def __init__(self, uuid, pci_bus_id, index):
+        self.max_mhz = 2070.0
+
+    def sample(self):
+        return (1995.0, 800.0, _FakeNvml.bits)
+
+    def close(self):
+        pass
+
+
+def test_nvml_sampler_every_2ms_inside_the_window(monkeypatch):
+    monkeypatch.setattr(bench, "_Nvml", _FakeNvml)
+    _FakeNvml.bits = 0
+    s = bench.ClockSampler(0)
+    assert s.nvml is not None and s.source.startswith("nvml")
+    time.sleep(0.05)
+    t0 = time.time()
+    time.sleep(0.1)
+    t1 = time.time()
+    out = s.stop((t0, t1))
+    assert out["sm_mhz"] == 1995.0 and out["sm_max_mhz"] == 2070.0 and out["reasons"] == []
+    # 2 ms sampling over a 0.1 s window: tens of samples, all inside it
+    assert 20 <= out["samples"] == out["samples_in_timed_region"] <= 60
+
+
+def test_nvml_sampler_decodes_throttle_bits(monkeypatch):
+    monkeypatch.setattr(bench, "_Nvml", _FakeNvml)
+    _FakeNvml.bits = 0x4 | 0x8 | 0x1  # power cap, hardware slowdown, idle (not a throttle reason kept)
+    s = bench.ClockSampler(0)
+    t0 = time.time()
+    time.sleep(0.05)
+    out = s.stop((t0, time.time()))
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
