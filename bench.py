@@ -60,11 +60,14 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+# NVML clock-event (throttle) reason bits kept in the record
+NVML_REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown", 0x4: "sw_power_cap"}
+
+
 class _Nvml:
     """Read-only NVML queries through ctypes (the driver's libnvidia-ml; no Python package needed)."""
 
     SM = 1  # NVML_CLOCK_SM
-    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown", 0x4: "sw_power_cap"}
 
     def __init__(self, uuid, pci_bus_id, index):
         import ctypes
@@ -142,7 +145,7 @@ class ClockSampler:
                 while not self.halt.is_set():
                     mhz, _, bits = self.nvml.sample()
                     self.rows.append((time.time(), mhz, self.nvml.max_mhz,
-                                      [n for m, n in _Nvml.REASONS.items() if bits & m]))
+                                      [n for m, n in NVML_REASONS.items() if bits & m]))
                     time.sleep(self.PERIOD_S)
 
             self.thread = threading.Thread(target=run, daemon=True)
