@@ -292,3 +292,42 @@ def test_more_frames_than_one_pass():
         for a, b in zip((nb[i], db[i], cb[i], kb[i]), (n1, d1, c1, k1)):
             assert torch.equal(torch.nan_to_num(a.float(), nan=7.0), torch.nan_to_num(b.float(), nan=7.0)), i
     f.close()
+
+
+def test_concurrent_contexts_on_two_streams():
+    """Two host threads, each with its own context and stream, fitting different frames at the same time
+    (the library releases no global state between them): every result equals the same fit run alone."""
+    import threading
+
+    cfgs = [(320, 240, 7, "disparity", scenes.BASE_SEED + 250), (200, 150, 15, "standard", scenes.BASE_SEED + 251)]
+    jobs = []
+    for W, H, k, method, seed in cfgs:
+        intr = scenes.Intrinsics.scaled(W, H)
+        t = torch.from_numpy(np.stack([scenes.kinect_frame(seed + i, intr, W, H) for i in range(3)])).cuda()
+        f = SurfaceFitter(intr.as_tuple(), W, H, k, method=method)
+        ref = [x.clone() for x in f.fit(t, counts=True)]
+        torch.cuda.synchronize()
+        jobs.append((f, t, ref, torch.cuda.Stream()))
+    errors = []
+
+    def work(f, t, ref, stream):
+        try:
+            with torch.cuda.stream(stream):
+                for _ in range(20):
+                    out = f.fit(t, counts=True, stream=stream)
+                    stream.synchronize()
+                    for a, b in zip(out, ref):
+                        if not torch.equal(torch.nan_to_num(a.float(), nan=7.0), torch.nan_to_num(b.float(), nan=7.0)):
+                            errors.append("mismatch")
+                            return
+        except Exception as exc:  # pragma: no cover - reported below
+            errors.append(repr(exc))
+
+    threads = [threading.Thread(target=work, args=job) for job in jobs]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert errors == []
+    for f, _, _, _ in jobs:
+        f.close()
