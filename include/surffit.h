@@ -329,10 +329,12 @@ sf_status sf_batch_destroy(sf_batch* batch);
 sf_status sf_set_delta_table(sf_ctx* ctx, const float* ddx, const float* ddy);
 
 /*
- * sf_set_tiles -- tile shape of a context: hseg in {32, 64, 128} columns per
- * horizontal tile (default 32), vband rows per vertical band (0 = chosen
- * from the grid size, else 2..1024).  Results do not depend on the tiles:
- * the window sums are exact.
+ * sf_set_tiles -- tile shape of a context: hseg in {8, 16, 32, 64, 128}
+ * output columns per thread of the horizontal pass (0, the default: 32, or
+ * 16 / 8 for calls with too few rows to fill the GPU), vband rows per
+ * vertical band (0 = chosen from the grid size, else 2..1024).  Results do
+ * not depend on the tiles: the window sums are exact.  SF_ERR_INVALID_ARG
+ * for any other value.
  */
 sf_status sf_set_tiles(sf_ctx* ctx, int hseg, int vband);
 

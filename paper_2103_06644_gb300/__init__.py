@@ -90,8 +90,9 @@ class SurfaceFitter:
                                                   float(depth_scale), int(min_valid), int(bool(require_center))))
         self.method, self.depth_type, self.depth_scale = method, depth_type, float(depth_scale)
 
-    def set_tiles(self, hseg: int = 32, vband: int = 0) -> None:
-        """Tile shape: hseg in {32, 64, 128} columns, vband rows per band (0 = automatic)."""
+    def set_tiles(self, hseg: int = 0, vband: int = 0) -> None:
+        """Tile shape: hseg in {8, 16, 32, 64, 128} columns per row-pass thread, vband rows per band
+        (0 = automatic for either)."""
         _native.check(_native.lib().sf_set_tiles(self._h, int(hseg), int(vband)))
 
     def set_delta_table(self, ddx=None, ddy=None) -> None:

@@ -24,7 +24,7 @@ struct sf_ctx {
     size_t plane_elems;
     int method = SF_METHOD_DISPARITY;
     int depth_type = SF_DEPTH_F32;
-    int hseg = 32;        // horizontal tile width (32, 64 or 128)
+    int hseg = 0;         // horizontal tile width (8, 16, 32, 64 or 128; 0: automatic)
     int vband = 0;        // vertical band height (0: chosen from the grid size)
     float depth_scale = 1e-3f;
     // SF_DEPTH_DISPARITY_U16: 1/Z = disp_q * (disp_mul * D + disp_add + disp_frac)
@@ -128,8 +128,10 @@ sf_status cuda_fail(cudaError_t e, const char* what);
         if (_e != cudaSuccess) return ::sfh::cuda_fail(_e, #call); \
     } while (0)
 
-// Rows per band of the vertical pass of nfr frames (the context's vband, else
-// chosen from the grid size and the window).
+// Output columns per thread of the horizontal pass and rows per band of the
+// vertical pass for nfr frames (the context's hseg / vband, else chosen from
+// the grid size and the window).
+int horizontal_seg(const sf_ctx* c, int nfr);
 int vertical_band(const sf_ctx* c, int nfr);
 // Bytes of horizontal-moment scratch per frame of plane_elems entries.
 size_t plane_bytes_per_frame(int method, size_t plane_elems);

@@ -31,7 +31,7 @@ namespace sf {
 
 constexpr int kMaxR = (SF_MAX_WINDOW - 1) / 2;
 constexpr int kHThreads = 128;   // rows per hpass block
-constexpr int kHSeg = 32;        // default output columns per hpass thread (runtime: 32..128)
+constexpr int kHSeg = 32;        // default output columns per hpass thread (runtime: 8..128)
 constexpr int kVThreads = 128;   // columns per vpass block
 
 
@@ -440,13 +440,14 @@ struct HRowState {
     }
 };
 
-// One row of a tile: L independent 32-column output segments [x0 + 32 l,
-// x0 + 32 (l + 1)) clipped to xend, slid in lock step (L independent
-// dependency chains per thread), four columns per store.
-template <int M, int L>
+// One row of a tile: L independent kSub-column output segments [x0 + kSub l,
+// x0 + kSub (l + 1)) clipped to xend, slid in lock step (L independent
+// dependency chains per thread), four columns per store.  kSub is 32, or 16
+// or 8 for small frames (more threads, shorter serial chains).
+template <int M, int L, int kSub = 32>
 __device__ __forceinline__ void hpass_row(const int* row, int x0, int xend, int y, int H, int r, const Planes& P,
                                           size_t pofs) {
-    constexpr int kSub = 32;
+    static_assert(kSub % 4 == 0 && (L == 1 || kSub == 32), "segments of 8, 16 or 32 L columns");
     HRowState<M> st[L];
 #pragma unroll
     for (int l = 0; l < L; ++l)
@@ -516,23 +517,23 @@ __device__ __forceinline__ void hpass_row(const int* row, int x0, int xend, int 
 }
 
 // Horizontal moments of one tile: rows [y0, y0 + 128) x output columns
-// [x0, x0 + 32 L) of one frame.  `depth` points at the frame, `pofs` is the
+// [x0, x0 + kSub L) of one frame.  `depth` points at the frame, `pofs` is the
 // frame's offset in the planes; `tile` is shared memory of
-// kHThreads * ((32 L + 2r) | 1) ints.
-template <int DT, int M, int L>
+// kHThreads * ((kSub L + 2r) | 1) ints.
+template <int DT, int M, int L, int kSub = 32>
 __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W, int H, int r, float sc,
                                            const Codec& cd, const Planes& P, size_t pofs, int x0, int y0,
                                            int* tile) {
-    constexpr int seg = 32 * L;
+    constexpr int seg = kSub * L;
     const int IW = seg + 2 * r;
     const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
     const int rows = min(kHThreads, H - y0);
     // the tile's raw depth, quantised; ceil(IW / 32) column chunks per row
-    // (IW <= seg + 30): 2 for seg 32, 3 for 64, 5 for 128
+    // (IW <= seg + 30): 2 for seg 8 to 32, 3 for 64, 5 for 128
     load_tile<DT, M, L + 1 + (L == 4)>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
     __syncthreads();
     if ((int)threadIdx.x < rows)
-        hpass_row<M, L>(tile + threadIdx.x * pitch, x0, min(x0 + seg, W), y0 + threadIdx.x, H, r, P, pofs);
+        hpass_row<M, L, kSub>(tile + threadIdx.x * pitch, x0, min(x0 + seg, W), y0 + threadIdx.x, H, r, P, pofs);
 }
 
 // Resident blocks per SM of the horizontal pass for 32 L-column tiles (shared
@@ -543,7 +544,7 @@ __host__ __device__ constexpr int hpass_blocks() {
     return L == 1 ? (base_method(M) == SF_METHOD_STANDARD ? 6 : 7) : (L == 2 ? 4 : 2);
 }
 
-template <int DT, int M, int L>
+template <int DT, int M, int L, int kSub = 32>
 __global__ void __launch_bounds__(kHThreads, hpass_blocks<M, L>()) hpass_kernel(
     const void* __restrict__ depth, int W, int H, int r, Codec scale, const unsigned* __restrict__ vmax_bits, int bits,
     int raw_z, int Wp, size_t plane_elems, void* planes_base) {
@@ -553,8 +554,8 @@ __global__ void __launch_bounds__(kHThreads, hpass_blocks<M, L>()) hpass_kernel(
     const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
     const void* dframe = static_cast<const char*>(depth) + dbytes * (size_t)f * W * H;
     const Planes P(planes_base, (size_t)gridDim.z * plane_elems, planes32<M>());
-    hpass_tile<DT, M, L>(dframe, W, H, r, sc, scale, P, (size_t)f * plane_elems, blockIdx.x * 32 * L,
-                         blockIdx.y * kHThreads, tile);
+    hpass_tile<DT, M, L, kSub>(dframe, W, H, r, sc, scale, P, (size_t)f * plane_elems, blockIdx.x * kSub * L,
+                               blockIdx.y * kHThreads, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -1003,10 +1004,21 @@ template <int DT, int M>
 __device__ __forceinline__ void range_chunk(const FrameDesc& d, int chunk, unsigned* vmax_bits, float* red) {
     const size_t fe = (size_t)d.W * d.H;
     const size_t i0 = (size_t)chunk * kRangeChunk, i1 = min(fe, i0 + kRangeChunk);
+    // kFly loads per thread in flight before any is used (issue is in order:
+    // a load consumed right away would expose its whole latency, 128 times
+    // per chunk); the maximum does not depend on the order
+    constexpr int kFly = 16;
     float vmax = 0.f;
-    for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const float z = load_raw<DT>(d.depth, i);
-        if (depth_valid(z)) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z));
+    for (size_t ib = i0 + threadIdx.x; ib < i1; ib += (size_t)kFly * blockDim.x) {
+        float z[kFly];
+#pragma unroll
+        for (int u = 0; u < kFly; ++u) {
+            const size_t i = ib + (size_t)u * blockDim.x;
+            z[u] = i < i1 ? load_raw<DT>(d.depth, i) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kFly; ++u)
+            if (depth_valid(z[u])) vmax = fmaxf(vmax, fit_variable_of<DT, M>(z[u]));
     }
     for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

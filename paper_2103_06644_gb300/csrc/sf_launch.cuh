@@ -47,12 +47,20 @@ struct StageTimer {
     }
 };
 
-// The horizontal pass for tiles of seg = 32, 64 or 128 columns (one kernel
-// each: their register budgets differ).
+// The horizontal pass for tiles of seg = 8, 16, 32, 64 or 128 columns (one
+// kernel each: their register budgets and serial chains differ).
 template <int DT, int M>
 void launch_hpass(dim3 grid, size_t smem, cudaStream_t st, const void* depth, const sf_ctx* c, int bits, int raw_z,
                   int seg) {
-    if (seg <= 32)
+    if (seg <= 8)
+        sf::hpass_kernel<DT, M, 1, 8><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c),
+                                                                        c->vmax, bits, raw_z, c->Wp, c->plane_elems,
+                                                                        c->planes);
+    else if (seg <= 16)
+        sf::hpass_kernel<DT, M, 1, 16><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c),
+                                                                         c->vmax, bits, raw_z, c->Wp, c->plane_elems,
+                                                                         c->planes);
+    else if (seg <= 32)
         sf::hpass_kernel<DT, M, 1><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
                                                                      bits, raw_z, c->Wp, c->plane_elems, c->planes);
     else if (seg <= 64)
@@ -65,6 +73,8 @@ void launch_hpass(dim3 grid, size_t smem, cudaStream_t st, const void* depth, co
 
 template <int DT, int M>
 void set_hpass_smem_one(int smem) {
+    cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 1, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(sf::hpass_kernel<DT, M, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -104,7 +114,7 @@ sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* normals, flo
     }
     {
         StageTimer t(c, 1, st);
-        const int seg = c->hseg;
+        const int seg = horizontal_seg(c, nfr);
         dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
         const int IW = seg + 2 * c->r;
         const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);
@@ -302,7 +312,7 @@ sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const float* gn
         sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
     }
     {
-        const int seg = c->hseg;
+        const int seg = horizontal_seg(c, nfr);
         dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
         const int IW = seg + 2 * c->r;
         const size_t smem = sizeof(int) * sf::kHThreads * (size_t)(IW | 1);

@@ -103,6 +103,16 @@ sf_status fit_pass(sf_ctx* c, int nfr, const void* depth, float* normals, float*
 }  // namespace
 
 namespace sfh {
+// Output columns per thread of the horizontal pass: 32, unless the call has
+// too few rows x segments to fill the GPU (a single small frame), where
+// narrower segments give more threads and shorter serial chains (each thread
+// slides seg + 2r columns).
+int horizontal_seg(const sf_ctx* c, int nfr) {
+    if (c->hseg > 0) return c->hseg;
+    int seg = sf::kHSeg;
+    while (seg > 8 && (size_t)((c->W + seg - 1) / seg) * c->H * nfr < (size_t)152 * 256) seg /= 2;
+    return seg;
+}
 // Band height of the vertical pass: long bands amortise the 2r-row warm-up,
 // short bands give enough threads to fill the GPU.
 int vertical_band(const sf_ctx* c, int nfr) {
@@ -618,7 +628,8 @@ sf_status sf_set_delta_table(sf_ctx* c, const float* ddx, const float* ddy) {
 sf_status sf_set_tiles(sf_ctx* c, int hseg, int vband) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     ++c->gen;  // a captured fit graph no longer applies
-    if (hseg != 32 && hseg != 64 && hseg != 128) return fail(SF_ERR_INVALID_ARG, "hseg must be 32, 64 or 128");
+    if (hseg != 0 && hseg != 8 && hseg != 16 && hseg != 32 && hseg != 64 && hseg != 128)
+        return fail(SF_ERR_INVALID_ARG, "hseg must be 0, 8, 16, 32, 64 or 128");
     if (vband != 0 && (vband < 2 || vband > 1024)) return fail(SF_ERR_INVALID_ARG, "vband must be 0 or in [2, 1024]");
     c->hseg = hseg;
     c->vband = vband;

@@ -214,15 +214,17 @@ def test_row_sums_beyond_32_bits(method):
 
 @pytest.mark.parametrize("method", ["disparity", "standard", "explicit_disparity", "explicit_standard"])
 def test_tile_shapes_do_not_change_results(method):
-    """Every horizontal tile width (32, 64, 128 columns: one kernel each) and vertical band height gives
-    bit-identical results: the window sums are exact integers whatever the tiling."""
+    """Every horizontal segment width (8, 16, 32, 64, 128 columns per thread: one kernel each; the
+    automatic choice for these small frames is 8) and vertical band height gives bit-identical results:
+    the window sums are exact integers whatever the tiling."""
     W, H, k = 300, 170, 15
     intr = scenes.Intrinsics.scaled(W, H)
     depth = scenes.kinect_frame(scenes.BASE_SEED + 91, intr, W, H)
     t = torch.from_numpy(np.stack([depth, depth[::-1].copy()])).cuda()
     f = SurfaceFitter(intr.as_tuple(), W, H, k, method=method)
     base = [x.clone() for x in f.fit(t, counts=True)]
-    for hseg, vband in [(64, 0), (128, 0), (32, 2), (32, 8), (64, 4), (64, 48), (128, 1024)]:
+    for hseg, vband in [(32, 0), (16, 0), (8, 3), (64, 0), (128, 0), (32, 2), (32, 8), (64, 4), (64, 48),
+                        (128, 1024)]:
         f.set_tiles(hseg, vband)
         out = f.fit(t, counts=True)
         torch.cuda.synchronize()
