@@ -1030,10 +1030,12 @@ __device__ __forceinline__ void range_chunk(const FrameDesc& d, int chunk, unsig
     }
 }
 
-// One block fewer per SM than vpass_kernel: the claim loop's state stays live
-// across the column calls, and at 80 registers the calls would spill.
+// Two blocks fewer per SM than vpass_kernel: the claim loop's state stays
+// live across the column calls, which spill at 5 blocks (96 registers) and
+// not at 4 (128); 4 blocks run the mixed batches fastest (3 lose latency
+// hiding).
 template <int DT, int M>
-__global__ void __launch_bounds__(kVThreads, kVBlocks - 1) batch_kernel(const FrameDesc* __restrict__ descs,
+__global__ void __launch_bounds__(kVThreads, kVBlocks - 2) batch_kernel(const FrameDesc* __restrict__ descs,
                                                                         const int3* __restrict__ items, int n_r,
                                                                         int n_h, int n_v, BatchSync sync,
                                                                         void* planes_base, size_t stride,
