@@ -447,7 +447,7 @@ struct HRowState {
 template <int M, int L, int kSub = 32>
 __device__ __forceinline__ void hpass_row(const int* row, int x0, int xend, int y, int H, int r, const Planes& P,
                                           size_t pofs) {
-    static_assert(kSub % 4 == 0 && (L == 1 || kSub == 32), "segments of 8, 16 or 32 L columns");
+    static_assert(kSub % 4 == 0 && (L == 1 || kSub == 32), "L segments of 32 columns, or one of kSub");
     HRowState<M> st[L];
 #pragma unroll
     for (int l = 0; l < L; ++l)
@@ -529,8 +529,8 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
     const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
     const int rows = min(kHThreads, H - y0);
     // the tile's raw depth, quantised; ceil(IW / 32) column chunks per row
-    // (IW <= seg + 30): 2 for seg 8 to 32, 3 for 64, 5 for 128
-    load_tile<DT, M, L + 1 + (L == 4)>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
+    // (IW <= seg + 2 kMaxR): 2 for seg 8 to 32, 3 for 48 and 64, 5 for 128
+    load_tile<DT, M, (seg + 2 * kMaxR + 31) / 32>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
     __syncthreads();
     if ((int)threadIdx.x < rows)
         hpass_row<M, L, kSub>(tile + threadIdx.x * pitch, x0, min(x0 + seg, W), y0 + threadIdx.x, H, r, P, pofs);
