@@ -892,8 +892,17 @@ __device__ __noinline__ void vpass_column(const void* __restrict__ depth, int W,
 
 // kGuard: the instantiation of precision modes 1 and 2 (implicit |(a,b,c)| = 1
 // fits), which also queues windows by their estimated rounding error.
+// Resident blocks per SM of the column pass: 6 (80 registers), except the
+// standard forms' implicit and explicit fits, whose int64 running sums spill
+// there: 5 (96 registers; on the benchmark batch 3-10 % faster than 6).  The
+// |(a,b,c,d)| = 1 fits, which spill at 6 as well, measured no faster at 5.
+template <int M, bool U4>
+__host__ __device__ constexpr int vpass_blocks() {
+    return (base_method(M) == SF_METHOD_STANDARD && !U4) ? kVBlocks - 1 : kVBlocks;
+}
+
 template <int DT, int M, bool U4 = false, bool kGuard = false>
-__global__ void __launch_bounds__(kVThreads, kVBlocks) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
+__global__ void __launch_bounds__(kVThreads, vpass_blocks<M, U4>()) vpass_kernel(const void* __restrict__ depth, int W, int H, int r,
                                                           Codec scale, const unsigned* __restrict__ vmax_bits,
                                                           int bits, int raw_z, int Wp, size_t plane_elems,
                                                           void* __restrict__ planes_base, Calib cal,
