@@ -1330,25 +1330,42 @@ __device__ __forceinline__ long long round_i64(float t) {
     return ((long long)(int)hi << 32) + (long long)__float2uint_rn(lo);
 }
 
-// The boxed terms of one window (adjoint channels at element o of the frame).
+// Adjoint channels of one window read by the gather (all that the adjoint
+// kernel writes: 7 for the disparity form, 12 for the standard form).
 template <int M>
-__device__ __forceinline__ void gather_terms(const float* __restrict__ src, size_t cstride, size_t o, float p0x,
-                                             float p0y, float p0z, float* v) {
-    if constexpr (M == SF_METHOD_DISPARITY) {
-        const float g0 = src[o], g1 = src[cstride + o], g2 = src[2 * cstride + o];
-        const float ux = src[3 * cstride + o] - p0x, uy = src[4 * cstride + o] - p0y, uz = src[5 * cstride + o] - p0z;
-        v[0] = g0; v[1] = g1; v[2] = g2;
-        v[3] = fmaf(ux, g0, fmaf(uy, g1, fmaf(uz, g2, src[6 * cstride + o])));
-    } else {
-        float a[6];
+__host__ __device__ constexpr int gather_channels_read() { return M == SF_METHOD_DISPARITY ? 7 : 12; }
+
+// The adjoint channels of the two staged columns lane and lane + 32 of staged
+// row ty_ (ok: inside the staged tile and the frame; 0 elsewhere).
+template <int M>
+__device__ __forceinline__ void gather_fetch(const float* __restrict__ src, size_t cstride, int W, int H, int x0,
+                                             int y0, int r, int T, int lane, int ty_,
+                                             float (&a)[2][gather_channels_read<M>()], bool (&ok)[2]) {
+    const int yy = y0 - r + ty_;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) a[c] = src[c * cstride + o];
-        const float ux = src[6 * cstride + o] - p0x, uy = src[7 * cstride + o] - p0y, uz = src[8 * cstride + o] - p0z;
+    for (int h = 0; h < 2; ++h) {
+        const int xx = x0 - r + lane + 32 * h;
+        ok[h] = ty_ < T && lane + 32 * h < T && xx >= 0 && xx < W && yy >= 0 && yy < H;
+        const size_t o = ok[h] ? (size_t)yy * W + xx : 0;
+#pragma unroll
+        for (int c = 0; c < gather_channels_read<M>(); ++c) a[h][c] = ok[h] ? src[c * cstride + o] : 0.f;
+    }
+}
+
+// The boxed terms of one window from its adjoint channels a.
+template <int M>
+__device__ __forceinline__ void gather_terms(const float* a, float p0x, float p0y, float p0z, float* v) {
+    if constexpr (M == SF_METHOD_DISPARITY) {
+        const float ux = a[3] - p0x, uy = a[4] - p0y, uz = a[5] - p0z;
+        v[0] = a[0]; v[1] = a[1]; v[2] = a[2];
+        v[3] = fmaf(ux, a[0], fmaf(uy, a[1], fmaf(uz, a[2], a[6])));
+    } else {
+        const float ux = a[6] - p0x, uy = a[7] - p0y, uz = a[8] - p0z;
 #pragma unroll
         for (int c = 0; c < 6; ++c) v[c] = a[c];
-        v[6] = fmaf(a[0], ux, fmaf(a[1], uy, fmaf(a[2], uz, src[9 * cstride + o])));
-        v[7] = fmaf(a[1], ux, fmaf(a[3], uy, fmaf(a[4], uz, src[10 * cstride + o])));
-        v[8] = fmaf(a[2], ux, fmaf(a[4], uy, fmaf(a[5], uz, src[11 * cstride + o])));
+        v[6] = fmaf(a[0], ux, fmaf(a[1], uy, fmaf(a[2], uz, a[9])));
+        v[7] = fmaf(a[1], ux, fmaf(a[3], uy, fmaf(a[4], uz, a[10])));
+        v[8] = fmaf(a[2], ux, fmaf(a[4], uy, fmaf(a[5], uz, a[11])));
     }
 }
 
@@ -1415,16 +1432,21 @@ __global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ de
     // |group 0| <= gm; |group 1| <= |mu - P0|_max |gbar|_1 + |c| <= 2 mm 3 gm + cm (likewise 2 Rbar, e)
     const float gm = adj_max[3 * f], mm = adj_max[3 * f + 1], cm = adj_max[3 * f + 2];
     const float s0 = gather_scale(gm), s1 = gather_scale(6.f * mm * gm + cm);
+    // the loads of the warp's next staged row are issued before this row's
+    // arithmetic (issue is in order: a load consumed right away would expose
+    // its whole latency on every row)
+    constexpr int NR = gather_channels_read<M>();
+    float cur[2][NR], nxt[2][NR];
+    bool cok[2], nok[2];
+    gather_fetch<M>(src, cstride, W, H, x0, y0, r, T, lane, warp, cur, cok);
     for (int ty_ = warp; ty_ < T; ty_ += 8) {
-        const int yy = y0 - r + ty_;
+        gather_fetch<M>(src, cstride, W, H, x0, y0, r, T, lane, ty_ + 8, nxt, nok);
         float v[2][NB];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int xx = x0 - r + lane + 32 * h;
 #pragma unroll
             for (int c = 0; c < NB; ++c) v[h][c] = 0.f;
-            if (lane + 32 * h < T && xx >= 0 && xx < W && yy >= 0 && yy < H)
-                gather_terms<M>(src, cstride, (size_t)yy * W + xx, p0x, p0y, p0z, v[h]);
+            if (cok[h]) gather_terms<M>(cur[h], p0x, p0y, p0z, v[h]);
         }
         const int hi = lane + 2 * r;  // last staged column of output column `lane`'s window (< 64)
 #pragma unroll
@@ -1441,6 +1463,12 @@ __global__ void __launch_bounds__(256) gather_kernel(const void* __restrict__ de
             const long long pa = __shfl_sync(0xffffffffu, a, hi & 31), pb = __shfl_sync(0xffffffffu, b, hi & 31);
             const long long pl = __shfl_sync(0xffffffffu, a, (lane + 31) & 31);
             hs[((size_t)c * T + ty_) * kGTile + lane] = (hi < 32 ? pa : pb) - (lane > 0 ? pl : 0ll);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            cok[h] = nok[h];
+#pragma unroll
+            for (int c = 0; c < NR; ++c) cur[h][c] = nxt[h][c];
         }
     }
     __syncthreads();
