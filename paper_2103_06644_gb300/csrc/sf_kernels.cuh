@@ -1569,15 +1569,31 @@ __global__ void __launch_bounds__(256) quad_level_kernel(const void* __restrict_
     int64_t c0 = 0, cj = 0, ci = 0, c2 = 0, c2j = 0, c2i = 0, c2jj = 0, c2ji = 0, c2ii = 0;
     const int area = q.w * q.h;
     const int xc = q.x0 + (q.w >> 1), yc = q.y0 + (q.h >> 1);
-    for (int p = lane; p < area; p += 32) {
-        const int ri = p / q.w, rj = p - ri * q.w;
-        const int i = q.y0 + ri - yc, j = q.x0 + rj - xc;
-        const int v = quantize_raw<DT, M>(load_raw<DT>(dframe, (size_t)(q.y0 + ri) * W + q.x0 + rj), sc, scale);
-        if (v < 0) continue;
-        n += 1; Sj += j; Si += i; Sjj += j * j; Sji += j * i; Sii += i * i;
-        const int64_t vv = (int64_t)v * v;
-        c0 += v; cj += (int64_t)v * j; ci += (int64_t)v * i; c2 += vv;
-        if (B == SF_METHOD_STANDARD) { c2j += vv * j; c2i += vv * i; c2jj += vv * (j * j); c2ji += vv * (j * i); c2ii += vv * (i * i); }
+    // kFly pixels per lane loaded before any is used (issue is in order: a
+    // load consumed right away would expose its whole latency, up to 128
+    // times per lane for a 64 x 64 node); the sums are exact, in any order
+    constexpr int kFly = 8;
+    for (int p0 = lane; p0 < area; p0 += 32 * kFly) {
+        float raw[kFly];
+        int pi[kFly], pj[kFly];
+#pragma unroll
+        for (int u = 0; u < kFly; ++u) {
+            const int p = p0 + 32 * u;
+            pi[u] = p / q.w;
+            pj[u] = p - pi[u] * q.w;
+            raw[u] = p < area ? load_raw<DT>(dframe, (size_t)(q.y0 + pi[u]) * W + q.x0 + pj[u]) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kFly; ++u) {
+            if (p0 + 32 * u >= area) break;
+            const int i = q.y0 + pi[u] - yc, j = q.x0 + pj[u] - xc;
+            const int v = quantize_raw<DT, M>(raw[u], sc, scale);
+            if (v < 0) continue;
+            n += 1; Sj += j; Si += i; Sjj += j * j; Sji += j * i; Sii += i * i;
+            const int64_t vv = (int64_t)v * v;
+            c0 += v; cj += (int64_t)v * j; ci += (int64_t)v * i; c2 += vv;
+            if (B == SF_METHOD_STANDARD) { c2j += vv * j; c2i += vv * i; c2jj += vv * (j * j); c2ji += vv * (j * i); c2ii += vv * (i * i); }
+        }
     }
     n = warp_sum(n); Sj = warp_sum(Sj); Si = warp_sum(Si); Sjj = warp_sum(Sjj); Sji = warp_sum(Sji); Sii = warp_sum(Sii);
     c0 = warp_sum(c0); cj = warp_sum(cj); ci = warp_sum(ci); c2 = warp_sum(c2);
