@@ -75,6 +75,12 @@ struct Codec {
     float frac;
 };
 
+// A kernel launched with programmatic dependent launch may start while the
+// previous kernel of its stream is still finishing; it waits here until that
+// kernel has completed and its writes are visible (a no-op for a kernel
+// launched without it).
+__device__ __forceinline__ void wait_for_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Raw stored value: metres for float32, raw units for uint16 (0 = missing).
 template <int DT>
 __device__ __forceinline__ float load_raw(const void* base, size_t idx) {
@@ -549,6 +555,7 @@ __global__ void __launch_bounds__(kHThreads, hpass_blocks<M, L>()) hpass_kernel(
     const void* __restrict__ depth, int W, int H, int r, Codec scale, const unsigned* __restrict__ vmax_bits, int bits,
     int raw_z, int Wp, size_t plane_elems, void* planes_base) {
     extern __shared__ int tile[];
+    wait_for_prior_grid();  // the range pass's maximum
     const int f = blockIdx.z;
     const float sc = ldexpf(1.f, quant_exponent(vmax_bits[f], bits));  // 2^e, exact
     const size_t dbytes = (DT == SF_DEPTH_F32) ? 4 : 2;
@@ -912,6 +919,7 @@ __global__ void __launch_bounds__(kVThreads, vpass_blocks<M, U4>()) vpass_kernel
                                                           float tau, unsigned long long* __restrict__ flags,
                                                           unsigned* __restrict__ flag_count, void* __restrict__ mq,
                                                           unsigned mcap) {
+    wait_for_prior_grid();  // the horizontal pass's scratch
     const int f = blockIdx.z;
     const int x = blockIdx.x * kVThreads + threadIdx.x;
     if (x >= W) return;

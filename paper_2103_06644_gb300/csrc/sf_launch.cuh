@@ -47,28 +47,40 @@ struct StageTimer {
     }
 };
 
+// Launch with programmatic dependent launch: the kernel may be scheduled while
+// the previous kernel of the stream finishes (its blocks wait in
+// wait_for_prior_grid before reading that kernel's results), which hides the
+// gap between the two launches.  After a copy or memset it is an ordinary
+// launch.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);  // errors surface through cudaGetLastError
+}
+
 // The horizontal pass for tiles of seg = 8, 16, 32, 64 or 128 columns (one
 // kernel each: their register budgets and serial chains differ).
 template <int DT, int M>
 void launch_hpass(dim3 grid, size_t smem, cudaStream_t st, const void* depth, const sf_ctx* c, int bits, int raw_z,
                   int seg) {
-    if (seg <= 8)
-        sf::hpass_kernel<DT, M, 1, 8><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c),
-                                                                        c->vmax, bits, raw_z, c->Wp, c->plane_elems,
-                                                                        c->planes);
-    else if (seg <= 16)
-        sf::hpass_kernel<DT, M, 1, 16><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c),
-                                                                         c->vmax, bits, raw_z, c->Wp, c->plane_elems,
-                                                                         c->planes);
-    else if (seg <= 32)
-        sf::hpass_kernel<DT, M, 1><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
-                                                                     bits, raw_z, c->Wp, c->plane_elems, c->planes);
-    else if (seg <= 64)
-        sf::hpass_kernel<DT, M, 2><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
-                                                                     bits, raw_z, c->Wp, c->plane_elems, c->planes);
-    else
-        sf::hpass_kernel<DT, M, 4><<<grid, sf::kHThreads, smem, st>>>(depth, c->W, c->H, c->r, codec_of(c), c->vmax,
-                                                                     bits, raw_z, c->Wp, c->plane_elems, c->planes);
+    auto go = [&](auto kernel) {
+        launch_pdl(kernel, grid, dim3(sf::kHThreads), smem, st, depth, c->W, c->H, c->r, codec_of(c),
+                   (const unsigned*)c->vmax, bits, raw_z, c->Wp, c->plane_elems, (void*)c->planes);
+    };
+    if (seg <= 8) go(sf::hpass_kernel<DT, M, 1, 8>);
+    else if (seg <= 16) go(sf::hpass_kernel<DT, M, 1, 16>);
+    else if (seg <= 32) go(sf::hpass_kernel<DT, M, 1>);
+    else if (seg <= 64) go(sf::hpass_kernel<DT, M, 2>);
+    else go(sf::hpass_kernel<DT, M, 4>);
 }
 
 template <int DT, int M>
@@ -132,20 +144,20 @@ sf_status launch_pass(sf_ctx* c, int nfr, const void* depth, float* normals, flo
         const float tau = c->precision_mode == 2 ? INFINITY : c->tau;
         if constexpr (kRich) {
             if (fb)
-                sf::vpass_kernel<DT, M, U4, true><<<grid, sf::kVThreads, 0, st>>>(
-                    depth, c->W, c->H, c->r, codec_of(c), c->vmax, bits, raw_z, c->Wp, c->plane_elems, c->planes, cal,
-                    c->min_valid, c->require_center, band, normals, offsets, curv, counts, tau, c->flags,
-                    c->flag_count, c->moments_q, (unsigned)c->moments_cap);
+                launch_pdl(sf::vpass_kernel<DT, M, U4, true>, grid, dim3(sf::kVThreads), 0, st, depth, c->W, c->H,
+                           c->r, codec_of(c), c->vmax, bits, raw_z, c->Wp, c->plane_elems, c->planes, cal,
+                           c->min_valid, c->require_center, band, normals, offsets, curv, counts, tau, c->flags,
+                           c->flag_count, c->moments_q, (unsigned)c->moments_cap);
             else
-                sf::vpass_kernel<DT, M, U4><<<grid, sf::kVThreads, 0, st>>>(
-                    depth, c->W, c->H, c->r, codec_of(c), c->vmax, bits, raw_z, c->Wp, c->plane_elems, c->planes, cal,
-                    c->min_valid, c->require_center, band, normals, offsets, curv, counts, tau, nullptr,
-                    c->flag_count, nullptr, 0u);
+                launch_pdl(sf::vpass_kernel<DT, M, U4>, grid, dim3(sf::kVThreads), 0, st, depth, c->W, c->H, c->r,
+                           codec_of(c), c->vmax, bits, raw_z, c->Wp, c->plane_elems, c->planes, cal, c->min_valid,
+                           c->require_center, band, normals, offsets, curv, counts, tau,
+                           (unsigned long long*)nullptr, c->flag_count, (void*)nullptr, 0u);
         } else {
-            sf::vpass_kernel<DT, M, U4><<<grid, sf::kVThreads, 0, st>>>(
-                depth, c->W, c->H, c->r, codec_of(c), c->vmax, bits, raw_z, c->Wp, c->plane_elems, c->planes, cal,
-                c->min_valid, c->require_center, band, normals, offsets, curv, counts, tau, fb ? c->flags : nullptr,
-                c->flag_count, nullptr, 0u);
+            launch_pdl(sf::vpass_kernel<DT, M, U4>, grid, dim3(sf::kVThreads), 0, st, depth, c->W, c->H, c->r,
+                       codec_of(c), c->vmax, bits, raw_z, c->Wp, c->plane_elems, c->planes, cal, c->min_valid,
+                       c->require_center, band, normals, offsets, curv, counts, tau, fb ? c->flags : nullptr,
+                       c->flag_count, (void*)nullptr, 0u);
         }
     }
     {
