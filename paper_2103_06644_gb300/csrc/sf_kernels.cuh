@@ -371,14 +371,13 @@ __device__ __forceinline__ void slide2(T& S0, T& S1, T out, T in, int r) {
 // ---------------------------------------------------------------------------
 // Load and quantise the raw depth of a horizontal tile into shared memory:
 // rows [y0, y0 + rows), columns [x0 - r, x0 - r + IW), at row pitch `pitch`.
-// Warp w takes rows w, w + 4, ...; lanes sweep a row (coalesced).  Eight rows x
-// CHUNKS 32-column chunks are loaded before any is used, so 8 * CHUNKS loads
-// per thread are in flight at once (issue is in order: a load consumed right
-// away would expose its whole latency).
-template <int DT, int M, int CHUNKS>
+// Warp w takes rows w, w + 4, ...; lanes sweep a row (coalesced).
+// kRowsPerBatch rows x CHUNKS 32-column chunks are loaded before any is used,
+// so that many loads per thread are in flight at once (issue is in order: a
+// load consumed right away would expose its whole latency).
+template <int DT, int M, int CHUNKS, int kRowsPerBatch = 8>
 __device__ __forceinline__ void load_tile(const void* __restrict__ depth, int W, int r, float sc, const Codec& cd,
                                           int x0, int y0, int rows, int IW, int pitch, int* tile) {
-    constexpr int kRowsPerBatch = 8;
     constexpr int kWarps = kHThreads / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int rb = warp; rb < rows; rb += kWarps * kRowsPerBatch) {
@@ -535,8 +534,15 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
     const int pitch = IW | 1;  // odd pitch: the 32 rows of a warp hit 32 banks
     const int rows = min(kHThreads, H - y0);
     // the tile's raw depth, quantised; ceil(IW / 32) column chunks per row
-    // (IW <= seg + 2 kMaxR): 2 for seg 8 to 32, 3 for 48 and 64, 5 for 128
-    load_tile<DT, M, (seg + 2 * kMaxR + 31) / 32>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
+    // (IW <= seg + 2 kMaxR): 2 for seg 8 to 32, 3 for 48 and 64, 5 for 128.
+    // The narrow segments of small calls with small windows (IW <= 32) take
+    // each warp's 32 rows in one batch: one memory round trip instead of four
+    if constexpr (kSub <= 16) {
+        if (IW <= 32) load_tile<DT, M, 1, 32>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
+        else load_tile<DT, M, 2>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
+    } else {
+        load_tile<DT, M, (seg + 2 * kMaxR + 31) / 32>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
+    }
     __syncthreads();
     if ((int)threadIdx.x < rows)
         hpass_row<M, L, kSub>(tile + threadIdx.x * pitch, x0, min(x0 + seg, W), y0 + threadIdx.x, H, r, P, pofs);
