@@ -463,6 +463,13 @@ const char* sf_version(void);
  * Process-wide; not for concurrent use with working contexts.
  */
 sf_status sf_debug_fail_allocs(long long after);
+/*
+ * sf_graph_replays -- the number of sf_fit_ex calls on this context that were
+ * served by replaying its captured CUDA graph (a call that repeats the
+ * previous one's frames, buffers and settings is captured, and later such
+ * calls replay it); the other calls launched their kernels one by one.
+ */
+sf_status sf_graph_replays(const sf_ctx* ctx, long long* n);
 /* sf_debug_live_allocs -- the number of the library's device allocations not yet freed (all contexts and batches). */
 sf_status sf_debug_live_allocs(long long* n);
 

@@ -124,6 +124,12 @@ class SurfaceFitter:
         _native.check(_native.lib().sf_precision_stats(self._h, ctypes.byref(q), ctypes.byref(r)))
         return int(q.value), int(r.value)
 
+    def graph_replays(self) -> int:
+        """How many fit calls of this context replayed its captured CUDA graph."""
+        n = ctypes.c_longlong(0)
+        _native.check(_native.lib().sf_graph_replays(self._h, ctypes.byref(n)))
+        return int(n.value)
+
     # -- device API -------------------------------------------------------------
     def _check_depth(self, depth):
         import torch

@@ -73,6 +73,7 @@ SIGNATURES = {
     "sf_batch_check": (_I, [_VP]),
     "sf_debug_fail_allocs": (_I, [ctypes.c_longlong]),
     "sf_debug_live_allocs": (_I, [ctypes.POINTER(ctypes.c_longlong)]),
+    "sf_graph_replays": (_I, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     "sf_batch_set_wait_limit": (_I, [_VP, ctypes.c_uint]),
     "sf_profile_enable": (_I, [_VP, _I]),
     "sf_profile_read": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I)]),

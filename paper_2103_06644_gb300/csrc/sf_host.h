@@ -87,6 +87,7 @@ struct sf_ctx {
     FitKey last_key{}, graph_key{};
     cudaStream_t graph_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    long long graph_replays = 0;  // fit calls served by replaying graph_exec
     // profiling: (stage, start event, stop event) per recorded launch
     bool profiling = false;
     struct Rec { int stage; cudaEvent_t a, b; };

@@ -212,6 +212,12 @@ sf_status sf_debug_fail_allocs(long long after) {
     return SF_OK;
 }
 
+sf_status sf_graph_replays(const sf_ctx* c, long long* n) {
+    if (!c || !n) return fail(SF_ERR_INVALID_ARG, "null context or output");
+    *n = c->graph_replays;
+    return SF_OK;
+}
+
 sf_status sf_debug_live_allocs(long long* n) {
     if (!n) return fail(SF_ERR_INVALID_ARG, "null output");
     *n = g_live_allocs.load();
@@ -420,12 +426,14 @@ static sf_status fit_ex_impl(sf_ctx* c, int n_frames, const void* depth, float* 
         const sf_ctx::FitKey key{c->gen, n_frames, depth, normals, offsets, curvature, counts};
         if (c->graph_exec && key == c->graph_key) {
             SF_CUDA(cudaGraphLaunch(c->graph_exec, st));
+            ++c->graph_replays;
             return SF_OK;
         }
         const bool again = key == c->last_key;
         c->last_key = key;
         if (again && capture_fit(c, key, n_frames, depth, normals, offsets, curvature, counts) == SF_OK) {
             SF_CUDA(cudaGraphLaunch(c->graph_exec, st));
+            ++c->graph_replays;
             return SF_OK;
         }
     }

@@ -260,6 +260,9 @@ def test_repeated_calls_replay_a_graph():
         torch.cuda.synchronize()
         for a, b in zip(out, ref0):
             assert torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
+    # the first call launches its kernels; the second repeats it, is captured and runs as the graph;
+    # the third and fourth replay that graph
+    assert f.graph_replays() == 3
     t.copy_(torch.from_numpy(d1))
     f.fit(t, out=out)
     ref1 = fresh.fit(t)
