@@ -742,7 +742,8 @@ def main():
             valid = torch.isfinite(o_)
             gn = torch.where(valid[..., None], 2.0 * (n_ - tgt), torch.zeros_like(n_))
             gk = torch.where(valid, torch.full_like(c_, 0.1), torch.zeros_like(c_))
-            return fd.backward(dd, gn, zero, gk)
+            # the depth is the one just fitted: the backward may reuse that fit's row pass
+            return fd.backward(dd, gn, zero, gk, after_fit=True)
 
         for _ in range(3):
             diff_step()
@@ -757,7 +758,8 @@ def main():
         t_f31 = timed(10, lambda: fd.fit(dd))
         line["mixed_batch"] = mixed_batch_report(dev, timed, world)
         line["segmentation_512x424"] = segmentation_report(dev, timed, world)
-        line["differentiation_k9"] = {"workload": "16x640x480 f32, k=9, loss |n-n*|^2 + 0.1 kappa",
+        line["differentiation_k9"] = {"workload": "16x640x480 f32, k=9, loss |n-n*|^2 + 0.1 kappa; the backward "
+                                                  "reuses the fit's row pass (SF_BACKWARD_AFTER_FIT)",
                                       "value": whole_job_rate(world, nd * 307200, t_fb), "unit": UNIT,
                                       "ms_per_step_fwd_bwd": t_fb, "ms_forward": t_f,
                                       "k31": {"value": whole_job_rate(world, nd * 307200, t_fb31), "unit": UNIT,

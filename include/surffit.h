@@ -250,6 +250,28 @@ sf_status sf_fit_backward(sf_ctx* ctx, int n_frames, const void* depth, const fl
                           const float* g_curvature, float* g_depth, void* stream);
 
 /*
+ * sf_fit_backward_ex -- sf_fit_backward with flags.  SF_BACKWARD_AFTER_FIT:
+ * the caller promises that `depth` holds the same values as when the last
+ * sf_fit_ex call on this context fitted it (that call ordered before this
+ * one on the device); the backward then reuses that fit's quantum and row
+ * sums (the forward's range and row passes, Section II.C's window sums)
+ * instead of computing them again.  The library itself checks the rest: the
+ * same buffer, frame count and settings, at most 64 frames (one pass), no
+ * per-pixel delta table and no call on the context in between that wrote its
+ * scratch (another fit, sf_fit_host, a backward of other frames,
+ * sf_quadtree); when any of that fails the row pass runs as without the flag
+ * (results are the same either way).  The promise itself cannot be checked:
+ * a depth changed in between gives the gradient of a mixture.  flags = 0 is
+ * sf_fit_backward.  Errors as sf_fit_backward.
+ */
+#define SF_BACKWARD_AFTER_FIT 1u
+sf_status sf_fit_backward_ex(sf_ctx* ctx, int n_frames, const void* depth, const float* g_normals,
+                             const float* g_offsets, const float* g_curvature, float* g_depth, unsigned flags,
+                             void* stream);
+/* sf_backward_reuses -- how many backward calls on this context reused the last fit's row pass. */
+sf_status sf_backward_reuses(const sf_ctx* ctx, long long* n);
+
+/*
  * Mixed-resolution batches.  One frame of a batch: its size, window and
  * intrinsics, its device buffers (layouts as for sf_fit), and optionally its
  * tile shape (0 = default): hseg in {32, 64, 128} columns per horizontal

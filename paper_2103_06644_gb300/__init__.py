@@ -163,8 +163,11 @@ class SurfaceFitter:
                                               _stream_handle(stream)))
         return (normals, offsets, curv, cnt) if counts else (normals, offsets, curv)
 
-    def backward(self, depth, g_normals, g_offsets, g_curvature, stream=None):
-        """dL/dZ [.., H, W] for L = sum(g_normals . n + g_offsets d + g_curvature kappa) (``sf_fit_backward``)."""
+    def backward(self, depth, g_normals, g_offsets, g_curvature, stream=None, after_fit: bool = False):
+        """dL/dZ [.., H, W] for L = sum(g_normals . n + g_offsets d + g_curvature kappa) (``sf_fit_backward_ex``).
+
+        ``after_fit=True`` promises that ``depth`` is unchanged since this fitter last fitted it: the
+        backward then reuses that fit's row pass when the library finds it still in place."""
         import torch
 
         self._check_depth(depth)
@@ -173,9 +176,16 @@ class SurfaceFitter:
         gd = torch.nan_to_num(g_offsets.float()).contiguous()
         gk = torch.nan_to_num(g_curvature.float()).contiguous()
         g = torch.empty(depth.shape, dtype=torch.float32, device=depth.device)
-        _native.check(_native.lib().sf_fit_backward(self._h, n, depth.data_ptr(), gn.data_ptr(), gd.data_ptr(),
-                                                    gk.data_ptr(), g.data_ptr(), _stream_handle(stream)))
+        flags = 1 if after_fit else 0  # SF_BACKWARD_AFTER_FIT
+        _native.check(_native.lib().sf_fit_backward_ex(self._h, n, depth.data_ptr(), gn.data_ptr(), gd.data_ptr(),
+                                                       gk.data_ptr(), g.data_ptr(), flags, _stream_handle(stream)))
         return g
+
+    def backward_reuses(self) -> int:
+        """How many backward calls of this fitter reused the last fit's row pass."""
+        n = ctypes.c_longlong(0)
+        _native.check(_native.lib().sf_backward_reuses(self._h, ctypes.byref(n)))
+        return int(n.value)
 
     def fit_differentiable(self, depth):
         """(normals, offsets, curvature) with a backward to the float32 depth (torch.autograd)."""
@@ -366,7 +376,8 @@ def _make_function():
                 g_offsets = torch.zeros(shape, device=depth.device)
             if g_curv is None:
                 g_curv = torch.zeros(shape, device=depth.device)
-            return ctx.fitter.backward(depth, g_normals, g_offsets, g_curv), None
+            # autograd refuses saved tensors modified in place, so the depth is the one fitted
+            return ctx.fitter.backward(depth, g_normals, g_offsets, g_curv, after_fit=True), None
 
     return FitFunction
 

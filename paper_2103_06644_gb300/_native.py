@@ -66,6 +66,8 @@ SIGNATURES = {
     "sf_batch_info": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I)]),
     "sf_batch_destroy": (_I, [_VP]),
     "sf_fit_backward": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sf_fit_backward_ex": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP, ctypes.c_uint, _VP]),
+    "sf_backward_reuses": (_I, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
     "sf_last_error": (ctypes.c_char_p, []),
     "sf_channel_counts": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "sf_version": (ctypes.c_char_p, []),

@@ -88,6 +88,14 @@ struct sf_ctx {
     cudaStream_t graph_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_replays = 0;  // fit calls served by replaying graph_exec
+    long long backward_reuses = 0;  // backward calls that reused the last fit's row pass
+    // what the scratch planes and per-frame quanta hold: the row pass of the n
+    // frames at `depth` under settings generation gen (n == 0: unknown)
+    struct PlanesFrom {
+        unsigned long long gen = 0;
+        const void* depth = nullptr;
+        int n = 0;
+    } planes_from;
     // profiling: (stage, start event, stop event) per recorded launch
     bool profiling = false;
     struct Rec { int stage; cudaEvent_t a, b; };
@@ -150,7 +158,7 @@ constexpr size_t kMomentEntryBytes = 80;
     sf_status delta_pass_##dt(sf_ctx* c, int nfr, const void* depth, float* normals, float* offsets, float* curv,    \
                               int32_t* counts, cudaStream_t st);                                                       \
     sf_status backward_##dt(sf_ctx* c, int nfr, const void* depth, const float* gn, const float* gd, const float* gk, \
-                            float* g_depth, cudaStream_t st);                                                          \
+                            float* g_depth, bool reuse, cudaStream_t st);                                              \
     sf_status quadtree_##dt(sf_ctx* c, int nfr, int frame_base, const void* depth, const sf_quad_params* p,         \
                             sf_quad_node* nodes, int capacity, int32_t* n_nodes, size_t roots, cudaStream_t st);      \
     sf_status batch_enqueue_##dt(sf_batch* b, cudaStream_t st);                                                       \

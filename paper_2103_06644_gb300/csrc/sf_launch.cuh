@@ -312,18 +312,20 @@ sf_status launch_pass_delta(sf_ctx* c, int nfr, const void* depth, float* normal
     return SF_OK;
 }
 
+// reuse: the scratch planes and quanta already hold the row pass of these
+// frames (the forward fit's), so only the adjoint and the gather run.
 template <int DT, int M>
 sf_status launch_backward(sf_ctx* c, int nfr, const void* depth, const float* gn, const float* gd, const float* gk,
-                          float* g_depth, cudaStream_t st) {
+                          float* g_depth, bool reuse, cudaStream_t st) {
     const size_t fe = (size_t)c->W * c->H;
     const int raw_z = sf::fixed_quantum<DT, M>() ? 1 : 0;
     const int bits = quant_bits(M, c->k);
-    SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
-    if (!raw_z) {
+    if (!reuse) SF_CUDA(cudaMemsetAsync(c->vmax, 0, sizeof(unsigned) * nfr, st));
+    if (!reuse && !raw_z) {
         const int blocks = range_blocks(c, fe, nfr);
         sf::range_kernel<DT, M><<<dim3(blocks, nfr), 256, 0, st>>>(depth, fe, codec_of(c), c->vmax);
     }
-    {
+    if (!reuse) {
         const int seg = horizontal_seg(c, nfr);
         dim3 grid((c->W + seg - 1) / seg, (c->H + sf::kHThreads - 1) / sf::kHThreads, nfr);
         const int IW = seg + 2 * c->r;
@@ -408,13 +410,13 @@ void set_kernel_smem_t() {
                    : launch_pass_delta<DT, false>(c, nfr, depth, normals, offsets, curv, counts, st);                  \
     }                                                                                                                  \
     sf_status backward_##dt(sf_ctx* c, int nfr, const void* depth, const float* gn, const float* gd, const float* gk, \
-                            float* g_depth, cudaStream_t st) {                                                         \
+                            float* g_depth, bool reuse, cudaStream_t st) {                                             \
         if constexpr (DT == SF_DEPTH_DISPARITY_U16) {                                                                  \
             return fail(SF_ERR_UNSUPPORTED, "the backward takes depth input (f32 or u16)");                           \
         } else {                                                                                                       \
             return c->method == SF_METHOD_DISPARITY                                                                    \
-                       ? launch_backward<DT, SF_METHOD_DISPARITY>(c, nfr, depth, gn, gd, gk, g_depth, st)              \
-                       : launch_backward<DT, SF_METHOD_STANDARD>(c, nfr, depth, gn, gd, gk, g_depth, st);              \
+                       ? launch_backward<DT, SF_METHOD_DISPARITY>(c, nfr, depth, gn, gd, gk, g_depth, reuse, st)       \
+                       : launch_backward<DT, SF_METHOD_STANDARD>(c, nfr, depth, gn, gd, gk, g_depth, reuse, st);       \
         }                                                                                                              \
     }                                                                                                                  \
     sf_status quadtree_##dt(sf_ctx* c, int nfr, int frame_base, const void* depth, const sf_quad_params* p,         \

@@ -212,6 +212,12 @@ sf_status sf_debug_fail_allocs(long long after) {
     return SF_OK;
 }
 
+sf_status sf_backward_reuses(const sf_ctx* c, long long* n) {
+    if (!c || !n) return fail(SF_ERR_INVALID_ARG, "null context or output");
+    *n = c->backward_reuses;
+    return SF_OK;
+}
+
 sf_status sf_graph_replays(const sf_ctx* c, long long* n) {
     if (!c || !n) return fail(SF_ERR_INVALID_ARG, "null context or output");
     *n = c->graph_replays;
@@ -681,7 +687,7 @@ sf_status sf_set_disparity_model(sf_ctx* c, double alpha, double beta) {
 }
 
 static sf_status fit_backward_impl(sf_ctx* c, int n_frames, const void* depth, const float* g_normals, const float* g_offsets,
-                          const float* g_curvature, float* g_depth, void* stream) {
+                          const float* g_curvature, float* g_depth, unsigned flags, void* stream) {
     if (!c) return fail(SF_ERR_INVALID_ARG, "null context");
     if (n_frames < 0) return fail(SF_ERR_INVALID_ARG, "n_frames must be >= 0");
     if (n_frames == 0) return SF_OK;
@@ -717,6 +723,13 @@ static sf_status fit_backward_impl(sf_ctx* c, int n_frames, const void* depth, c
         c->adj_bytes = need;
     }
     c->adj_max = reinterpret_cast<float*>(reinterpret_cast<char*>(c->adj) + c->adj_bytes - sizeof(float) * 3 * 64);
+    // the caller vouches for the depth being unchanged since the last fit; the
+    // rest (settings, buffer, frame count, one pass, no other call since that
+    // wrote the scratch) is checked here, else the row pass runs again
+    const sf_ctx::PlanesFrom& pf = c->planes_from;
+    const bool reuse = (flags & SF_BACKWARD_AFTER_FIT) && n_frames <= per && pf.n == n_frames &&
+                       pf.depth == depth && pf.gen == c->gen;
+    if (reuse) ++c->backward_reuses;
     for (int f0 = 0; f0 < n_frames; f0 += per) {
         const int nfr = std::min(per, n_frames - f0);
         const void* dp = static_cast<const char*>(depth) + dbytes * fe * f0;
@@ -724,8 +737,8 @@ static sf_status fit_backward_impl(sf_ctx* c, int n_frames, const void* depth, c
         const float* gd = g_offsets + fe * f0;
         const float* gk = g_curvature + fe * f0;
         float* gz = g_depth + fe * f0;
-        s = c->depth_type == SF_DEPTH_F32 ? sfh::backward_f32(c, nfr, dp, gn, gd, gk, gz, st)
-                                           : sfh::backward_u16(c, nfr, dp, gn, gd, gk, gz, st);
+        s = c->depth_type == SF_DEPTH_F32 ? sfh::backward_f32(c, nfr, dp, gn, gd, gk, gz, reuse, st)
+                                           : sfh::backward_u16(c, nfr, dp, gn, gd, gk, gz, reuse, st);
         if (s != SF_OK) return s;
     }
     return SF_OK;
@@ -1158,20 +1171,41 @@ static sf_status check_bounds(sf_status s) {
 
 extern "C" {
 
+// Every call that writes the scratch planes or the per-frame quanta records
+// what they hold afterwards (a fit or backward of at most one pass of frames
+// without a delta table), or that they hold nothing known.
+static void note_planes(sf_ctx* c, int n_frames, const void* depth, sf_status s) {
+    if (!c) return;
+    const bool one_pass = n_frames > 0 && n_frames <= std::min(c->max_frames_per_pass, 64);
+    if (s == SF_OK && one_pass && depth && !c->dtab) c->planes_from = sf_ctx::PlanesFrom{c->gen, depth, n_frames};
+    else c->planes_from = sf_ctx::PlanesFrom{};
+}
+
 sf_status sf_fit_ex(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
                     int32_t* counts, void* stream) {
-    return check_bounds(fit_ex_impl(c, n_frames, depth, normals, offsets, curvature, counts, stream));
+    const sf_status s = check_bounds(fit_ex_impl(c, n_frames, depth, normals, offsets, curvature, counts, stream));
+    note_planes(c, n_frames, depth, s);
+    return s;
 }
 sf_status sf_fit_host(sf_ctx* c, int n_frames, const void* depth, float* normals, float* offsets, float* curvature,
                       int32_t* counts, void* stream) {
     return check_bounds(fit_host_impl(c, n_frames, depth, normals, offsets, curvature, counts, stream));
 }
+sf_status sf_fit_backward_ex(sf_ctx* c, int n_frames, const void* depth, const float* g_normals,
+                             const float* g_offsets, const float* g_curvature, float* g_depth, unsigned flags,
+                             void* stream) {
+    const sf_status s = check_bounds(
+        fit_backward_impl(c, n_frames, depth, g_normals, g_offsets, g_curvature, g_depth, flags, stream));
+    note_planes(c, n_frames, depth, s);
+    return s;
+}
 sf_status sf_fit_backward(sf_ctx* c, int n_frames, const void* depth, const float* g_normals, const float* g_offsets,
                           const float* g_curvature, float* g_depth, void* stream) {
-    return check_bounds(fit_backward_impl(c, n_frames, depth, g_normals, g_offsets, g_curvature, g_depth, stream));
+    return sf_fit_backward_ex(c, n_frames, depth, g_normals, g_offsets, g_curvature, g_depth, 0u, stream);
 }
 sf_status sf_quadtree(sf_ctx* c, int n_frames, const void* depth, const sf_quad_params* params, sf_quad_node* nodes,
                       int capacity, int32_t* n_nodes, void* stream) {
+    if (c) c->planes_from = sf_ctx::PlanesFrom{};  // its range pass overwrites the quanta
     return check_bounds(quadtree_impl(c, n_frames, depth, params, nodes, capacity, n_nodes, stream));
 }
 sf_status sf_batch_run(sf_batch* b, void* stream) { return check_bounds(batch_run_impl(b, stream)); }

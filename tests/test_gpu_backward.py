@@ -128,11 +128,50 @@ def test_autograd_function_matches_direct_backward():
     diff = torch.where(valid[..., None], n - tgt, torch.zeros_like(n))
     loss = (diff ** 2).sum() + 0.1 * torch.where(valid, cu, torch.zeros_like(cu)).sum()
     loss.backward()
+    # the autograd backward follows the fit of the same (unmodified) tensor: it reuses the fit's row pass
+    assert f.backward_reuses() == 1
     gn = torch.where(valid[..., None], 2 * (n.detach() - tgt), torch.zeros_like(n))
     gk = torch.where(valid, torch.full_like(cu, 0.1), torch.zeros_like(cu))
     direct = f.backward(d.detach(), gn, torch.zeros_like(off), gk)
     torch.cuda.synchronize()
     assert torch.allclose(d.grad, direct, rtol=1e-5, atol=1e-6 * direct.abs().max().item())
+    f.close()
+
+
+@pytest.mark.parametrize("method", ["disparity", "standard"])
+def test_backward_after_fit_reuses_the_row_pass(method):
+    """SF_BACKWARD_AFTER_FIT: a backward that follows the fit of the same frames takes that fit's quantum and
+    row sums instead of computing them again, and gives the same gradient bit for bit; where the scratch no
+    longer holds those frames (another fit, changed settings) the library runs the row pass itself."""
+    W, H, k = 200, 150, 9
+    intr = scenes.Intrinsics.scaled(W, H)
+    d = torch.from_numpy(np.stack([scenes.kinect_frame(scenes.BASE_SEED + 210 + i, intr, W, H)
+                                   for i in range(3)])).cuda()
+    other = torch.from_numpy(np.stack([scenes.kinect_frame(scenes.BASE_SEED + 220 + i, intr, W, H)
+                                       for i in range(3)])).cuda()
+    rng = np.random.Generator(np.random.PCG64(23))
+    gn = torch.from_numpy(rng.standard_normal((3, H, W, 3)).astype(np.float32)).cuda()
+    gd = torch.from_numpy(rng.standard_normal((3, H, W)).astype(np.float32)).cuda()
+    gk = torch.from_numpy(rng.standard_normal((3, H, W)).astype(np.float32)).cuda()
+    f = SurfaceFitter(intr.as_tuple(), W, H, k, method=method)
+    ref = f.backward(d, gn, gd, gk).clone()           # no promise: the row pass runs
+    f.fit(d)
+    got = f.backward(d, gn, gd, gk, after_fit=True)   # reuses the fit's row pass
+    torch.cuda.synchronize()
+    assert f.backward_reuses() == 1 and torch.equal(got, ref)
+    f.fit(d)
+    f.fit(other)                                      # the scratch now holds other frames
+    got = f.backward(d, gn, gd, gk, after_fit=True)
+    torch.cuda.synchronize()
+    assert f.backward_reuses() == 1 and torch.equal(got, ref)
+    got = f.backward(d, gn, gd, gk, after_fit=True)   # the previous backward left d's row pass in place
+    torch.cuda.synchronize()
+    assert f.backward_reuses() == 2 and torch.equal(got, ref)
+    f.fit(d)
+    f.set_params(method, min_valid=3)                 # a settings call: the context's generation moves on
+    got = f.backward(d, gn, gd, gk, after_fit=True)
+    torch.cuda.synchronize()
+    assert f.backward_reuses() == 2 and torch.equal(got, ref)
     f.close()
 
 
