@@ -1209,21 +1209,36 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
     typename std::conditional<M == SF_METHOD_DISPARITY, DispState, StdState>::type S(P);
     S.init(pb, kGroup, H, y0, r);
     float tmax[3] = {0.f, 0.f, 0.f};
+    // the row's centre depth, upstream gradients and ray; those of the next
+    // row and the loads of the slide are issued before this row's solve (issue
+    // is in order: loads consumed right away would expose their latency on
+    // every row)
+    size_t oin = fo + (size_t)y0 * W + x;
+    float zn = load_depth<DT>(depth, oin, scale);
+    float gnxn = g_normals[3 * oin], gnyn = g_normals[3 * oin + 1], gnzn = g_normals[3 * oin + 2];
+    float gdn = g_offsets[oin], gkn = g_curv[oin], tyn = cal.ty[y0];
     for (int y = y0; y < y1; ++y) {
-        const size_t oi = fo + (size_t)y * W + x;
-        const bool cvalid = depth_valid(load_depth<DT>(depth, oi, scale));
+        const size_t oi = oin;
+        const bool cvalid = depth_valid(zn);
+        const float gnx = gnxn, gny = gnyn, gnz = gnzn, gd = gdn, gk = gkn, ty = tyn;
+        const bool more = y + 1 < y1;
+        if (more) {
+            S.fetch(pb, kGroup, H, y, r);
+            oin += W;
+            zn = load_depth<DT>(depth, oin, scale);
+            gnxn = g_normals[3 * oin]; gnyn = g_normals[3 * oin + 1]; gnzn = g_normals[3 * oin + 2];
+            gdn = g_offsets[oin]; gkn = g_curv[oin]; tyn = cal.ty[y + 1];
+        }
         const int n = S.count();
         const bool ok = n >= min_valid && n > 0 && (cvalid || !require_center);
         float out[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) out[c] = 0.f;
         if (ok) {
-            const float gnx = g_normals[3 * oi], gny = g_normals[3 * oi + 1], gnz = g_normals[3 * oi + 2];
-            const float gd = g_offsets[oi], gk = g_curv[oi];
             float R11, R12, R13, R22, R23, R33, mux, muy, muz, s_or_n;
             if constexpr (M == SF_METHOD_DISPARITY) {
                 const DispWindow w = build_disparity(S.n, S.Sj, S.Si, S.Sjj, S.Sji, S.Sii, S.Sw, S.Swj, S.Swi,
-                                                     S.Sww, tx, cal.ty[y], cal.a, cal.b);
+                                                     S.Sww, tx, ty, cal.a, cal.b);
                 R11 = w.R11; R12 = w.R12; R13 = w.R13; R22 = w.R22; R23 = w.R23; R33 = w.R33;
                 const float iwm = 1.f / (w.what * q);  // 1 / what_metric
                 mux = w.mx * iwm; muy = w.my * iwm; muz = iwm;
@@ -1246,7 +1261,7 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
                 const float Cjj = (Fn<float>::from_i64(S.Szzjj) - fSzj * qj) * q2;
                 const float Cji = (Fn<float>::from_i64(S.Szzji) - fSzj * qi) * q2;
                 const float Cii = (Fn<float>::from_i64(S.Szzii) - fSzi * qi) * q2;
-                const float a = cal.a, b = cal.b, ty = cal.ty[y];
+                const float a = cal.a, b = cal.b;
                 R11 = a * a * Cjj + 2.f * a * tx * Cjz + tx * tx * Czz;
                 R12 = a * b * Cji + a * ty * Cjz + b * tx * Ciz + tx * ty * Czz;
                 R13 = a * Cjz + tx * Czz;
@@ -1289,7 +1304,7 @@ __global__ void __launch_bounds__(kVThreads) vadjoint_kernel(const void* __restr
             const int grp = M == SF_METHOD_DISPARITY ? (c < 3 ? 0 : (c < 6 ? 1 : 2)) : (c < 6 ? 0 : (c < 9 ? 1 : 2));
             tmax[grp] = fmaxf(tmax[grp], fabsf(out[c]));
         }
-        if (y + 1 < y1) S.slide(pb, kGroup, H, y, r);
+        if (more) S.apply(r);
     }
     // non-negative floats order as their bit patterns
     const unsigned mask = __activemask();
