@@ -439,6 +439,29 @@ def run_single_case(args):
     print(json.dumps({"case": "single1080", "method": args.method, "fits": max(1, args.steps)}))
 
 
+def run_vga_case(args):
+    """One seeded 640x480 frame, k=7, fitted --steps times through the C ABI with fixed arguments (repeated
+    calls replay the context's captured graph), for ncu captures of the small-frame case."""
+    import torch
+
+    from paper_2103_06644_gb300 import SurfaceFitter, _native
+
+    intr = scenes.Intrinsics(525.0, 525.0, 319.5, 239.5)
+    d = torch.from_numpy(scenes.kinect_frame(scenes.BASE_SEED, intr, 640, 480)).cuda()
+    out = (torch.empty((480, 640, 3), device="cuda"), torch.empty((480, 640), device="cuda"),
+           torch.empty((480, 640), device="cuda"))
+    f = SurfaceFitter(intr.as_tuple(), 640, 480, 7, method=args.method)
+    cargs = (f._h, 1, d.data_ptr(), out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), None,
+             torch.cuda.current_stream().cuda_stream)
+    lib = _native.lib()
+    for _ in range(max(1, args.steps)):
+        _native.check(lib.sf_fit_ex(*cargs))
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "vga", "method": args.method, "fits": max(1, args.steps),
+                      "graph_replays": f.graph_replays()}))
+    f.close()
+
+
 def run_diff_case(args):
     """16 x 640x480 f32 frames, k=9 (or --window): forward, upstream gradient and backward, --steps times
     (for ncu captures of the backward kernels)."""
@@ -508,9 +531,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="few steps, no extras (for ncu)")
-    ap.add_argument("--case", default=None, choices=["single1080", "diff16"],
+    ap.add_argument("--case", default=None, choices=["single1080", "diff16", "vga"],
                     help="small profiling case instead of the benchmark: one 1920x1080 frame, --steps fits "
-                         "(single1080), or 16 x 640x480 frames fitted and differentiated --steps times (diff16)")
+                         "(single1080), 16 x 640x480 frames fitted and differentiated --steps times (diff16), or "
+                         "one 640x480 frame at k=7, --steps fits through the C ABI (vga)")
     ap.add_argument("--window", type=int, default=9, help="window of the diff16 case")
     ap.add_argument("--method", default="disparity", choices=["disparity", "standard"])
     args = ap.parse_args()
@@ -519,6 +543,9 @@ def main():
         return
     if args.case == "diff16":
         run_diff_case(args)
+        return
+    if args.case == "vga":
+        run_vga_case(args)
         return
     args.warmup = max(args.warmup, 3) if not args.profile_only else args.warmup
     if args.impl == "reference":
