@@ -462,6 +462,25 @@ def run_vga_case(args):
     f.close()
 
 
+def run_mixed_case(args):
+    """The 64-frame mixed batch of `mixed_batch`, tuned, then run --steps times (one persistent launch per
+    pass, replayed from a CUDA graph), for ncu captures of the batch kernel."""
+    import torch
+
+    from paper_2103_06644_gb300 import SurfaceFitBatch, autotune
+
+    frames = []
+    for i, (W, H, k) in enumerate(scenes.mixed_batch_spec(64)):
+        depth, intr = scenes.mixed_frame(scenes.BASE_SEED + 800 + i, W, H)
+        frames.append(dict(W=W, H=H, window=k, intrinsics=intr.as_tuple(), depth=torch.from_numpy(depth).cuda()))
+    b = SurfaceFitBatch(autotune.tune(frames), use_graph=True)
+    for _ in range(max(1, args.steps)):
+        b.run()
+    b.check()
+    print(json.dumps({"case": "mixed", "passes": max(1, args.steps), "pixels": b.pixels, "launches": b.launches}))
+    b.close()
+
+
 def run_diff_case(args):
     """16 x 640x480 f32 frames, k=9 (or --window): forward, upstream gradient and backward, --steps times
     (for ncu captures of the backward kernels)."""
@@ -531,10 +550,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="few steps, no extras (for ncu)")
-    ap.add_argument("--case", default=None, choices=["single1080", "diff16", "vga"],
+    ap.add_argument("--case", default=None, choices=["single1080", "diff16", "vga", "mixed"],
                     help="small profiling case instead of the benchmark: one 1920x1080 frame, --steps fits "
                          "(single1080), 16 x 640x480 frames fitted and differentiated --steps times (diff16), or "
-                         "one 640x480 frame at k=7, --steps fits through the C ABI (vga)")
+                         "one 640x480 frame at k=7, --steps fits through the C ABI (vga), or the 64-frame "
+                         "mixed batch run --steps times (mixed)")
     ap.add_argument("--window", type=int, default=9, help="window of the diff16 case")
     ap.add_argument("--method", default="disparity", choices=["disparity", "standard"])
     args = ap.parse_args()
@@ -546,6 +566,9 @@ def main():
         return
     if args.case == "vga":
         run_vga_case(args)
+        return
+    if args.case == "mixed":
+        run_mixed_case(args)
         return
     args.warmup = max(args.warmup, 3) if not args.profile_only else args.warmup
     if args.impl == "reference":
