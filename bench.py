@@ -481,6 +481,28 @@ def run_mixed_case(args):
     b.close()
 
 
+def run_tolerance_case(args):
+    """The benchmark batch (8 x 1080p + 2 x 4K, k=31) in precision mode 1, tau 1e-3 (the configuration of
+    `tolerance_met_config`), fitted --steps times, for ncu captures of the refinement kernels."""
+    import torch
+
+    from paper_2103_06644_gb300 import SurfaceFitter
+
+    fits = []
+    for (W, H, intr, frames) in workload_frames():
+        f = SurfaceFitter(intr.as_tuple(), W, H, K, method=args.method)
+        f.set_precision(1, 1e-3)
+        fits.append((f, torch.from_numpy(np.stack(frames)).cuda()))
+    for _ in range(max(1, args.steps)):
+        for f, t in fits:
+            f.fit(t)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "tolerance", "method": args.method, "steps": max(1, args.steps),
+                      "queued_resummed": [f.precision_stats() for f, _ in fits]}))
+    for f, _ in fits:
+        f.close()
+
+
 def run_diff_case(args):
     """16 x 640x480 f32 frames, k=9 (or --window): forward, upstream gradient and backward, --steps times
     (for ncu captures of the backward kernels)."""
@@ -550,11 +572,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="few steps, no extras (for ncu)")
-    ap.add_argument("--case", default=None, choices=["single1080", "diff16", "vga", "mixed"],
+    ap.add_argument("--case", default=None, choices=["single1080", "diff16", "vga", "mixed", "tolerance"],
                     help="small profiling case instead of the benchmark: one 1920x1080 frame, --steps fits "
                          "(single1080), 16 x 640x480 frames fitted and differentiated --steps times (diff16), or "
                          "one 640x480 frame at k=7, --steps fits through the C ABI (vga), or the 64-frame "
-                         "mixed batch run --steps times (mixed)")
+                         "mixed batch run --steps times (mixed), or the benchmark batch in precision mode 1 "
+                         "(tolerance)")
     ap.add_argument("--window", type=int, default=9, help="window of the diff16 case")
     ap.add_argument("--method", default="disparity", choices=["disparity", "standard"])
     args = ap.parse_args()
@@ -569,6 +592,9 @@ def main():
         return
     if args.case == "mixed":
         run_mixed_case(args)
+        return
+    if args.case == "tolerance":
+        run_tolerance_case(args)
         return
     args.warmup = max(args.warmup, 3) if not args.profile_only else args.warmup
     if args.impl == "reference":
