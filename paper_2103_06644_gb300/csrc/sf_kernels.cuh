@@ -404,6 +404,32 @@ __device__ __forceinline__ void load_tile(const void* __restrict__ depth, int W,
     }
 }
 
+// load_tile for tiles at most 16 columns wide: the two halves of a warp take
+// two rows at once (lanes 0-15 and 16-31), so that each lane loads and
+// quantises 16 values instead of 32 with half its lanes idle.  Warp w still
+// fills rows w, w + 4, ..., w + 124, with the same values as load_tile.
+template <int DT, int M>
+__device__ __forceinline__ void load_tile_pairs(const void* __restrict__ depth, int W, int r, float sc,
+                                                const Codec& cd, int x0, int y0, int rows, int IW, int pitch,
+                                                int* tile) {
+    constexpr int kWarps = kHThreads / 32;
+    constexpr int kPerLane = kHThreads / (2 * kWarps);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int half = lane >> 4, cx = lane & 15, x = x0 - r + cx;
+    const bool col = cx < IW && x >= 0 && x < W;
+    float raw[kPerLane];
+#pragma unroll
+    for (int k = 0; k < kPerLane; ++k) {
+        const int ry = warp + kWarps * (2 * k + half);
+        raw[k] = (ry < rows && col) ? load_raw<DT>(depth, (size_t)(y0 + ry) * W + x) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kPerLane; ++k) {
+        const int ry = warp + kWarps * (2 * k + half);
+        if (ry < rows && cx < IW) tile[ry * pitch + cx] = quantize_raw<DT, M>(raw[k], sc, cd);
+    }
+}
+
 // Running horizontal sums of one row over one 32-column output segment:
 // mask moments (count, sum j, sum j^2) and value moments.  The disparity
 // form's row sum of v fits 31 bits (the fixed-point bits are chosen so): it
@@ -536,9 +562,11 @@ __device__ __forceinline__ void hpass_tile(const void* __restrict__ depth, int W
     // the tile's raw depth, quantised; ceil(IW / 32) column chunks per row
     // (IW <= seg + 2 kMaxR): 2 for seg 8 to 32, 3 for 48 and 64, 5 for 128.
     // The narrow segments of small calls with small windows (IW <= 32) take
-    // each warp's 32 rows in one batch: one memory round trip instead of four
+    // each warp's 32 rows in one batch: one memory round trip instead of four;
+    // tiles at most 16 wide take two rows per warp instruction
     if constexpr (kSub <= 16) {
-        if (IW <= 32) load_tile<DT, M, 1, 32>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
+        if (IW <= 16) load_tile_pairs<DT, M>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
+        else if (IW <= 32) load_tile<DT, M, 1, 32>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
         else load_tile<DT, M, 2>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
     } else {
         load_tile<DT, M, (seg + 2 * kMaxR + 31) / 32>(depth, W, r, sc, cd, x0, y0, rows, IW, pitch, tile);
